@@ -1,0 +1,79 @@
+/*
+ * Plain FP64 CPU oracle for the multiple-resolution scalar path of
+ * Chong, Ding & Xia, "Multiple-resolution scheme in finite-volume code for
+ * active or passive scalar turbulence" (arXiv:1805.03426).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only the test-suite, the smoke check and the
+ * CPU-baseline leg of the benchmark may load this library.  It shares no code,
+ * header or table with the CUDA library under paper_1805_03426_gb300/csrc.
+ *
+ * Layout of every 3-D array: [z][y][x], x contiguous.
+ *   dense cells       Nz x Ny x Nx           (Nx = mx*nx, ...)
+ *   U faces (x-normal) Nz x Ny x (Nx + w)    w = 1 with side walls, 0 periodic
+ *   V faces (y-normal) Nz x (Ny + w) x Nx
+ *   W faces (z-normal) (Nz + 1) x Ny x Nx    planes 0 and Nz are the plates
+ * Coarse arrays use the same layout with nx, ny, nz.
+ */
+#ifndef MR_ORACLE_H
+#define MR_ORACLE_H
+#include <stdint.h>
+
+typedef struct {
+    int32_t nx, ny, nz;       /* coarse cells                                   */
+    int32_t mx, my, mz;       /* refinement factors M_x, M_y, M_z (Section 3.1) */
+    double  lx, ly;           /* horizontal extent; the height is 1             */
+    double  gamma;            /* tanh clustering of the dense z faces, 0=uniform */
+    double  kappa;            /* (Ra Pr)^-1/2 or (Ra Sc)^-1/2, Eq. (2)          */
+    double  dt;
+    int32_t np_average;       /* N_p of the averaging step, Section 2.2; <=0 off */
+    int32_t plates_dirichlet; /* 1: T=+0.5 at z=0, -0.5 at z=1; 0: adiabatic    */
+    int32_t walls_xy;         /* 0: periodic in x,y; 1: impermeable adiabatic   */
+    int32_t implicit_z;       /* 1: vertical diffusion Crank-Nicolson (opt-in)  */
+} or_cfg;
+
+/* Grid (Section 3.1): dense faces first, coarse faces = every M-th dense face. */
+int  or_zfaces(int32_t nz_dense, double gamma, double* zf /* nz_dense+1 */);
+/* R = A_s A^-1 for every coarse cell of one axis (Section 3.2).
+ * Xc: n+1 coarse faces, Xd: n*m+1 dense faces, R out [n][m][3], win out [n][3]. */
+int  or_rmatrix(int32_t n, int32_t m, const double* Xc, const double* Xd,
+                int32_t periodic, double length, double* R, int32_t* win);
+
+/* Divergence-free refinement coarse -> dense (Section 3.2). */
+int  or_refine(const or_cfg* c, const double* U, const double* V, const double* W,
+               double* Us, double* Vs, double* Ws);
+/* Transpose of or_refine: coarse gradient from dense face gradient. */
+int  or_refine_adjoint(const or_cfg* c, const double* gUs, const double* gVs,
+                       const double* gWs, double* gU, double* gV, double* gW);
+
+/* One time step s (s = 0 is the forward-Euler start), Section 2.2. */
+int  or_step(const or_cfg* c, const double* Us, const double* Vs, const double* Ws,
+             const double* Tm1, const double* T, int64_t s, double* Tp1);
+/* Explicit right-hand sides: C(Tc) (advection) and D(Td) (diffusion), Eq. (5). */
+int  or_rhs(const or_cfg* c, const double* Us, const double* Vs, const double* Ws,
+            const double* Tc, const double* Td, double* rhsC, double* rhsD);
+/* nsteps steps from T0; on return Tprev = T^{n-1}, Tcur = T^n. */
+int  or_run(const or_cfg* c, const double* Us, const double* Vs, const double* Ws,
+            const double* T0, int64_t nsteps, double* Tprev, double* Tcur);
+
+/* out[0..5] = Nu_bottom, Nu_top, volume mean, volume variance, integral,
+ * max |div u| over dense cells (Section 4.1 and the divergence check, 3.2). */
+int  or_stats(const or_cfg* c, const double* T, const double* Us, const double* Vs,
+              const double* Ws, double* out);
+double or_max_divergence(const or_cfg* c, const double* Us, const double* Vs,
+                         const double* Ws);
+double or_cfl_dt(const or_cfg* c, const double* Us, const double* Vs, const double* Ws,
+                 double cfl);
+
+/* Discrete adjoint of or_run for L = sum_s wnu[s] Nu_bot(T^s) + wvar[s] Var(T^s),
+ * s = 0..nsteps.  Returns dL/dT^0 and dL/d(dense faces); the coarse gradient is
+ * or_refine_adjoint of the latter.  Stores every state (small grids only).    */
+int  or_adjoint(const or_cfg* c, const double* Us, const double* Vs, const double* Ws,
+                const double* T0, int64_t nsteps, const double* wnu, const double* wvar,
+                double* loss, double* gT0, double* gUs, double* gVs, double* gWs);
+
+/* Integer maps for the bit-exact comparison: the coarse cell of every dense
+ * cell along x, y, z, then the three coarse cells of the R window of every
+ * coarse cell along x, y, z.  out: Nx + Ny + Nz + 3*(nx + ny + nz) ints.     */
+int  or_index_maps(const or_cfg* c, int32_t* out);
+
+#endif

@@ -1,0 +1,458 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix.
+
+Every check here is independent of the oracle's own code: exact rationals
+derived by hand (tests/golden), polynomial exactness of the third-order
+mass-conserving interpolation (Section 3.2), discrete divergence at round-off
+(Section 3.2, the paper's ~1e-17 check), closed-form eigenvalues of the
+discrete Laplacian and advection operator, the Euler-leapfrog amplitude
+recurrence (Section 2.2), exact conservation of the finite-volume integral form
+(Eq. 5), the steady conduction profile with Nu = 1 (Section 4.1), and the
+transpose identities of the hand-written adjoints.
+"""
+import os
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+from paper_1805_03426_gb300 import synth
+from tests import polyfield
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _cfg(O, **kw):
+    base = dict(nx=8, ny=6, nz=5, mx=2, my=2, mz=2, lx=1.0, ly=1.0, gamma=0.0, kappa=1e-3,
+                dt=1e-3, np_average=50, plates_dirichlet=1, walls_xy=0, implicit_z=0)
+    base.update(kw)
+    return O.Config(**base)
+
+
+def _velocity(O, cfg, seed=1805, rms=0.2):
+    g = O.grid(cfg)
+    return synth.coarse_velocity(seed, g["Xf"], g["Yf"], g["Zf"], cfg.lx, cfg.ly, rms=rms,
+                                 walls=bool(cfg.walls_xy))
+
+
+# ----------------------------------------------------------------------------- R matrices
+
+def _golden_r():
+    rows = {}
+    with open(os.path.join(GOLDEN, "r_uniform.txt")) as f:
+        for line in f:
+            if line.startswith("#") or not line.strip():
+                continue
+            m, r, *vals = line.split()
+            rows.setdefault(int(m), {})[int(r)] = [float(Fraction(v)) for v in vals]
+    return {m: np.array([d[r] for r in range(m)]) for m, d in rows.items()}
+
+
+@pytest.mark.parametrize("m", [2, 3, 4])
+def test_r_uniform_matches_exact_rationals(oracle_mod, m):
+    O = oracle_mod
+    n = 7
+    Xd = np.arange(n * m + 1) / (n * m)
+    R, win = O.rmatrix(n, m, Xd[::m], Xd, periodic=True)
+    gold = _golden_r()[m]
+    for i in range(n):
+        np.testing.assert_allclose(R[i], gold, rtol=0, atol=1e-14)
+        assert list(win[i]) == [(i - 1) % n, i, (i + 1) % n]
+
+
+def _quad_cell_means(coef, lo, hi):
+    a, b, c = coef
+    return a + b * 0.5 * (lo + hi) + c * (lo * lo + lo * hi + hi * hi) / 3.0
+
+
+@pytest.mark.parametrize("periodic", [True, False])
+@pytest.mark.parametrize("m", [2, 3, 4])
+def test_r_reproduces_quadratics_and_conserves(oracle_mod, periodic, m):
+    """The defining property of R: cell averages of any quadratic map to its
+    sub-cell averages, and the sub-cell fluxes sum to the coarse flux."""
+    O = oracle_mod
+    n = 9
+    rng = np.random.default_rng(3)
+    # a stretched axis (tanh clustering) to exercise non-uniform cells
+    Xd = O.zfaces(n * m, 1.7)
+    Xc = Xd[::m]
+    R, win = O.rmatrix(n, m, Xc, Xd, periodic=periodic, length=1.0)
+    for trial in range(5):
+        coef = rng.standard_normal(3)
+        for i in range(n):
+            means = []
+            for cell in win[i]:
+                lo, hi = Xc[cell], Xc[cell + 1]
+                if periodic:  # unwrap the neighbour next to i
+                    if i == 0 and cell == n - 1:
+                        lo, hi = lo - 1.0, hi - 1.0
+                    if i == n - 1 and cell == 0:
+                        lo, hi = lo + 1.0, hi + 1.0
+                means.append(_quad_cell_means(coef, lo, hi))
+            sub = R[i] @ np.array(means)
+            exact = [_quad_cell_means(coef, Xd[i * m + s], Xd[i * m + s + 1]) for s in range(m)]
+            np.testing.assert_allclose(sub, exact, rtol=0, atol=1e-12)
+    # conservation: sum_s dXs_s R[s, :] = dX e_centre, rows sum to one
+    for i in range(n):
+        dxs = np.diff(Xd[i * m:(i + 1) * m + 1])
+        w = dxs @ R[i] / (Xc[i + 1] - Xc[i])
+        centre = list(win[i]).index(i)
+        e = np.zeros(3)
+        e[centre] = 1.0
+        np.testing.assert_allclose(w, e, atol=1e-13)
+        np.testing.assert_allclose(R[i].sum(axis=1), 1.0, atol=1e-13)
+
+
+def test_r_one_sided_windows_at_walls(oracle_mod):
+    O = oracle_mod
+    n, m = 6, 3
+    Xd = np.arange(n * m + 1) / (n * m)
+    _, win = O.rmatrix(n, m, Xd[::m], Xd, periodic=False)
+    assert list(win[0]) == [0, 1, 2]
+    assert list(win[n - 1]) == [n - 3, n - 2, n - 1]
+    for i in range(1, n - 1):
+        assert list(win[i]) == [i - 1, i, i + 1]
+
+
+# ----------------------------------------------------------------------------- grid
+
+def test_stretched_grid_values(oracle_mod):
+    """The tanh grid: symmetric, clustered, with the minimum spacings that the
+    stretched workloads (gamma = 1.5) produce."""
+    O = oracle_mod
+    for N, dzmin in ((96, 3.21e-3), (192, 1.58e-3), (384, 7.85e-4), (1024, 2.93e-4)):
+        zf = O.zfaces(N, 1.5)
+        assert zf[0] == 0.0 and zf[-1] == 1.0
+        np.testing.assert_allclose(zf + zf[::-1], 1.0, atol=1e-15)
+        dz = np.diff(zf)
+        assert np.all(dz > 0)
+        assert abs(dz.min() / dzmin - 1) < 5e-3
+        assert dz.argmin() in (0, N - 1)
+
+
+def test_index_maps_closed_form(oracle_mod):
+    O = oracle_mod
+    for walls in (0, 1):
+        cfg = _cfg(O, nx=5, ny=4, nz=3, mx=3, my=2, mz=4, walls_xy=walls)
+        out = O.index_maps(cfg)
+        Nx, Ny, Nz = cfg.dense
+        exp = [i // 3 for i in range(Nx)] + [j // 2 for j in range(Ny)] + [k // 4 for k in range(Nz)]
+        for n, periodic in ((5, not walls), (4, not walls), (3, False)):
+            for i in range(n):
+                if periodic:
+                    exp += [(i - 1) % n, i, (i + 1) % n]
+                else:
+                    w0 = min(max(i - 1, 0), n - 3)
+                    exp += [w0, w0 + 1, w0 + 2]
+        assert out.tolist() == exp
+
+
+# ----------------------------------------------------------------------------- refinement
+
+@pytest.mark.parametrize("walls", [0, 1])
+@pytest.mark.parametrize("gamma", [0.0, 1.5])
+@pytest.mark.parametrize("m", [(2, 2, 2), (3, 2, 4), (4, 4, 4)])
+def test_refined_velocity_divergence_free(oracle_mod, walls, gamma, m):
+    """Section 3.2: the stepwise refinement leaves every dense cell with zero
+    net flux up to double-precision round-off."""
+    O = oracle_mod
+    cfg = _cfg(O, nx=8, ny=7, nz=5, mx=m[0], my=m[1], mz=m[2], gamma=gamma, walls_xy=walls, ly=1.3)
+    U, V, W = _velocity(O, cfg)
+    Us, Vs, Ws = O.refine(cfg, U, V, W)
+    Nx, Ny, Nz = cfg.dense
+    scale = max(np.abs(Us).max() * Nx / cfg.lx, np.abs(Vs).max() * Ny / cfg.ly,
+                np.abs(Ws).max() / np.diff(O.zfaces(Nz, gamma)).min())
+    assert O.max_divergence(cfg, (Us, Vs, Ws)) <= 1e-14 * scale
+    # the coarse faces (every M-th dense face) keep the coarse flux
+    dzs = np.diff(O.zfaces(Nz, gamma))
+    for K in range(cfg.nz):
+        sl = slice(K * cfg.mz, (K + 1) * cfg.mz)
+        dy = cfg.ly / Ny
+        flux = (Us[sl, :, ::cfg.mx] * dzs[sl, None, None] * dy).reshape(cfg.mz, cfg.ny, cfg.my, -1).sum(axis=(0, 2))
+        coarse = U[K] * dzs[sl].sum() * (cfg.ly / cfg.ny)
+        np.testing.assert_allclose(flux, coarse, atol=1e-13)
+    assert np.all(Ws[0] == 0.0) and np.all(Ws[-1] == 0.0)
+
+
+@pytest.mark.parametrize("gamma", [0.0, 1.2])
+@pytest.mark.parametrize("m", [(2, 2, 2), (3, 2, 4), (4, 3, 2)])
+def test_refinement_exact_for_quadratic_velocity(oracle_mod, gamma, m):
+    """Third-order interpolation: a velocity of degree <= 2 (curl of a cubic
+    potential) is refined to its exact dense face averages."""
+    O = oracle_mod
+    cfg = _cfg(O, nx=5, ny=4, nz=6, mx=m[0], my=m[1], mz=m[2], gamma=gamma, walls_xy=1, lx=1.0, ly=0.8)
+    g = O.grid(cfg)
+    A = polyfield.random_potential(11)
+    U, V, W = polyfield.face_velocities(A, g["Xf"], g["Yf"], g["Zf"])
+    Ue, Ve, We = polyfield.face_velocities(A, g["xf"], g["yf"], g["zf"])
+    Us, Vs, Ws = O.refine(cfg, U, V, W)
+    big = max(np.abs(Ue).max(), np.abs(Ve).max(), np.abs(We).max())
+    for got, exp in ((Us, Ue), (Vs, Ve), (Ws, We)):
+        np.testing.assert_allclose(got, exp, rtol=0, atol=1e-12 * big)
+
+
+def test_refinement_uniform_flow(oracle_mod):
+    O = oracle_mod
+    cfg = _cfg(O, nx=6, ny=5, nz=4, mx=3, my=2, mz=4, gamma=1.5)
+    sh = cfg.shapes()
+    U = np.full(sh["U"], 0.37)
+    V = np.full(sh["V"], -0.21)
+    W = np.zeros(sh["W"])
+    Us, Vs, Ws = O.refine(cfg, U, V, W)
+    np.testing.assert_allclose(Us, 0.37, atol=1e-15)
+    np.testing.assert_allclose(Vs, -0.21, atol=1e-15)
+    np.testing.assert_allclose(Ws, 0.0, atol=1e-15)
+
+
+def test_refinement_linear(oracle_mod):
+    O = oracle_mod
+    cfg = _cfg(O, nx=6, ny=6, nz=4, mx=2, my=3, mz=2, gamma=1.5)
+    v1 = _velocity(O, cfg, seed=1)
+    v2 = _velocity(O, cfg, seed=2)
+    a, b = 0.7, -1.9
+    r1, r2 = O.refine(cfg, *v1), O.refine(cfg, *v2)
+    r12 = O.refine(cfg, *(a * x + b * y for x, y in zip(v1, v2)))
+    for x, y, z in zip(r1, r2, r12):
+        np.testing.assert_allclose(z, a * x + b * y, atol=1e-14)
+
+
+@pytest.mark.parametrize("walls", [0, 1])
+def test_refine_adjoint_dot_product(oracle_mod, walls):
+    O = oracle_mod
+    cfg = _cfg(O, nx=5, ny=4, nz=4, mx=3, my=2, mz=2, gamma=1.5, walls_xy=walls)
+    sh = cfg.shapes()
+    rng = np.random.default_rng(5)
+    x = [rng.standard_normal(sh[k]) for k in ("U", "V", "W")]
+    y = [rng.standard_normal(sh[k]) for k in ("Us", "Vs", "Ws")]
+    Px = O.refine(cfg, *x)
+    Pty = O.refine_adjoint(cfg, *y)
+    lhs = sum(np.vdot(a, b) for a, b in zip(Px, y))
+    rhs = sum(np.vdot(a, b) for a, b in zip(x, Pty))
+    assert abs(lhs - rhs) <= 1e-12 * max(abs(lhs), 1.0)
+
+
+# ----------------------------------------------------------------------------- step
+
+def test_advection_rhs_of_linear_profile(oracle_mod):
+    """For T = 0.5 - z_c and a divergence-free u, the second-order flux form
+    gives C(T) = (w_bottom + w_top)/2 exactly (linear interpolation reproduces
+    the linear profile at every face, on any stretched grid)."""
+    O = oracle_mod
+    cfg = _cfg(O, nx=6, ny=6, nz=6, mx=2, my=2, mz=3, gamma=1.5, kappa=0.0)
+    vel = O.refine(cfg, *_velocity(O, cfg))
+    g = O.grid(cfg)
+    Nx, Ny, Nz = cfg.dense
+    T = np.broadcast_to((0.5 - g["zc"])[:, None, None], (Nz, Ny, Nx)).copy()
+    rC, rD = O.rhs(cfg, vel, T, T)
+    Ws = vel[2]
+    np.testing.assert_allclose(rC, 0.5 * (Ws[:-1] + Ws[1:]), atol=1e-12)
+    np.testing.assert_allclose(rD, 0.0, atol=1e-15)
+
+
+def test_advection_rhs_closed_form(oracle_mod):
+    """Uniform (U, V) on a periodic box, T = cos(2 pi k x) cos(2 pi l y):
+    central flux form gives C = U sin(phi_x)/dx * sin(.)cos(.) + ..."""
+    O = oracle_mod
+    cfg = _cfg(O, nx=8, ny=6, nz=3, mx=2, my=2, mz=2, gamma=0.0, lx=1.0, ly=1.5)
+    sh = cfg.shapes()
+    U0, V0 = 0.3, -0.45
+    vel = O.refine(cfg, np.full(sh["U"], U0), np.full(sh["V"], V0), np.zeros(sh["W"]))
+    g = O.grid(cfg)
+    Nx, Ny, Nz = cfg.dense
+    k, l = 3, 2
+    ax = 2 * np.pi * k * g["xc"] / cfg.lx
+    ay = 2 * np.pi * l * g["yc"] / cfg.ly
+    T = np.broadcast_to(np.cos(ax)[None, None, :] * np.cos(ay)[None, :, None], (Nz, Ny, Nx)).copy()
+    rC, _ = O.rhs(cfg, vel, T, T)
+    dx, dy = cfg.lx / Nx, cfg.ly / Ny
+    phx, phy = 2 * np.pi * k * dx / cfg.lx, 2 * np.pi * l * dy / cfg.ly
+    exp = (U0 * np.sin(phx) / dx * np.sin(ax)[None, :] * np.cos(ay)[:, None]
+           + V0 * np.sin(phy) / dy * np.cos(ax)[None, :] * np.sin(ay)[:, None])
+    np.testing.assert_allclose(rC, np.broadcast_to(exp, (Nz, Ny, Nx)), atol=1e-12)
+
+
+def _amplitude_recurrence(lam, dt, nsteps, np_average, implicit=False):
+    """Scalar Euler-leapfrog recurrence (Section 2.2) for dT/dt = lam T."""
+    a = [1.0]
+    if implicit:
+        a.append((1.0 + 0.5 * dt * lam) / (1.0 - 0.5 * dt * lam))
+    else:
+        a.append(1.0 + dt * lam)
+    for s in range(1, nsteps):
+        if np_average > 0 and (s + 1) % np_average == 0:
+            al, be, ga = 0.5, 0.5, 1.5
+        else:
+            al, be, ga = 1.0, 0.0, 2.0
+        if implicit:
+            a.append((al * a[s - 1] + be * a[s] + ga * dt * 0.5 * lam * a[s - 1]) / (1.0 - 0.5 * ga * dt * lam))
+        else:
+            a.append(al * a[s - 1] + be * a[s] + ga * dt * lam * a[s - 1])
+    return np.array(a)
+
+
+@pytest.mark.parametrize("k", [1, 3])
+def test_x_eigenmode_decay(oracle_mod, k):
+    O = oracle_mod
+    cfg = _cfg(O, nx=8, ny=3, nz=3, mx=2, my=1, mz=1, gamma=0.0, kappa=2e-3, dt=0.02,
+               np_average=7, plates_dirichlet=0)
+    sh = cfg.shapes()
+    vel = O.refine(cfg, np.zeros(sh["U"]), np.zeros(sh["V"]), np.zeros(sh["W"]))
+    g = O.grid(cfg)
+    Nx, Ny, Nz = cfg.dense
+    dx = cfg.lx / Nx
+    mode = np.cos(2 * np.pi * k * g["xc"])
+    T0 = np.broadcast_to(mode, (Nz, Ny, Nx)).copy()
+    lam = -4 * cfg.kappa * np.sin(np.pi * k * dx) ** 2 / dx ** 2
+    nsteps = 30
+    amp = _amplitude_recurrence(lam, cfg.dt, nsteps, cfg.np_average)
+    Tm1, T = T0, T0
+    for s in range(nsteps):
+        Tm1, T = T, O.step(cfg, vel, Tm1, T, s)
+        np.testing.assert_allclose(T, amp[s + 1] * T0, atol=1e-14)
+
+
+@pytest.mark.parametrize("implicit", [0, 1])
+def test_z_eigenmode_decay(oracle_mod, implicit):
+    """Neumann cosine mode in z on a uniform grid with adiabatic plates; with
+    the opt-in Crank-Nicolson vertical diffusion the recurrence changes."""
+    O = oracle_mod
+    cfg = _cfg(O, nx=3, ny=3, nz=8, mx=1, my=1, mz=2, gamma=0.0, kappa=5e-3, dt=0.05,
+               np_average=5, plates_dirichlet=0, implicit_z=implicit)
+    sh = cfg.shapes()
+    vel = O.refine(cfg, np.zeros(sh["U"]), np.zeros(sh["V"]), np.zeros(sh["W"]))
+    Nx, Ny, Nz = cfg.dense
+    m = 2
+    kk = np.arange(Nz)
+    mode = np.cos(np.pi * m * (kk + 0.5) / Nz)
+    T0 = np.broadcast_to(mode[:, None, None], (Nz, Ny, Nx)).copy()
+    dz = 1.0 / Nz
+    lam = -4 * cfg.kappa * np.sin(np.pi * m / (2 * Nz)) ** 2 / dz ** 2
+    nsteps = 23
+    amp = _amplitude_recurrence(lam, cfg.dt, nsteps, cfg.np_average, implicit=bool(implicit))
+    _, T = O.run(cfg, vel, T0, nsteps)
+    np.testing.assert_allclose(T, amp[-1] * T0, atol=1e-13)
+
+
+@pytest.mark.parametrize("gamma", [0.0, 1.5])
+@pytest.mark.parametrize("implicit", [0, 1])
+def test_conduction_profile_is_steady_with_nu_one(oracle_mod, gamma, implicit):
+    O = oracle_mod
+    cfg = _cfg(O, nx=4, ny=4, nz=6, mx=2, my=2, mz=2, gamma=gamma, kappa=1e-2, dt=2e-3,
+               np_average=4, implicit_z=implicit)
+    sh = cfg.shapes()
+    vel = O.refine(cfg, np.zeros(sh["U"]), np.zeros(sh["V"]), np.zeros(sh["W"]))
+    g = O.grid(cfg)
+    Nx, Ny, Nz = cfg.dense
+    T0 = np.broadcast_to((0.5 - g["zc"])[:, None, None], (Nz, Ny, Nx)).copy()
+    _, T = O.run(cfg, vel, T0, 25)
+    np.testing.assert_allclose(T, T0, atol=1e-14)
+    st = O.stats(cfg, T)
+    assert abs(st["nu_bot"] - 1.0) < 1e-12 and abs(st["nu_top"] - 1.0) < 1e-12
+
+
+@pytest.mark.parametrize("walls", [0, 1])
+@pytest.mark.parametrize("implicit", [0, 1])
+def test_scalar_integral_conserved_adiabatic(oracle_mod, walls, implicit):
+    """Eq. (5) in flux form: with adiabatic plates (and impermeable adiabatic
+    side walls) sum T Vol is unchanged by every step, including the Euler start
+    and the averaging steps."""
+    O = oracle_mod
+    cfg = _cfg(O, nx=6, ny=5, nz=4, mx=2, my=2, mz=3, gamma=1.5, kappa=3e-3, dt=4e-3,
+               np_average=3, plates_dirichlet=0, walls_xy=walls, implicit_z=implicit)
+    vel = O.refine(cfg, *_velocity(O, cfg))
+    g = O.grid(cfg)
+    Nx, Ny, Nz = cfg.dense
+    T0 = synth.initial_scalar(7, g["zc"], Ny, Nx, noise=0.1)
+    vol = (cfg.lx / Nx) * (cfg.ly / Ny) * g["dz"][:, None, None]
+    I0 = float((T0 * vol).sum())
+    Tm1, T = T0, T0
+    for s in range(12):
+        Tm1, T = T, O.step(cfg, vel, Tm1, T, s)
+        assert abs(float((T * vol).sum()) - I0) < 1e-14
+        assert abs(O.stats(cfg, T)["integral"] - I0) < 1e-14
+
+
+def test_stats_moments_and_plate_nu(oracle_mod):
+    O = oracle_mod
+    cfg = _cfg(O, nx=4, ny=3, nz=5, mx=2, my=2, mz=2, gamma=1.5, lx=1.0, ly=0.75)
+    g = O.grid(cfg)
+    Nx, Ny, Nz = cfg.dense
+    rng = np.random.default_rng(1)
+    T = rng.standard_normal((Nz, Ny, Nx))
+    st = O.stats(cfg, T)
+    w = np.broadcast_to(g["dz"][:, None, None] * (cfg.lx / Nx) * (cfg.ly / Ny), T.shape)
+    mean = np.average(T, weights=w)
+    assert abs(st["mean"] - mean) < 1e-14
+    assert abs(st["var"] - np.average((T - mean) ** 2, weights=w)) < 1e-14
+    assert abs(st["integral"] - (T * w).sum()) < 1e-14
+    zb = g["zc"][0]
+    assert abs(st["nu_bot"] - np.mean((0.5 - T[0]) / zb)) < 1e-10
+    assert abs(st["nu_top"] - np.mean((T[-1] + 0.5) / (1 - g["zc"][-1]))) < 1e-10
+
+
+def test_cfl_dt_uniform_flow(oracle_mod):
+    O = oracle_mod
+    cfg = _cfg(O, nx=4, ny=4, nz=4, mx=2, my=2, mz=2)
+    sh = cfg.shapes()
+    vel = O.refine(cfg, np.full(sh["U"], -0.5), np.full(sh["V"], 0.25), np.zeros(sh["W"]))
+    dt = O.cfl_dt(cfg, vel, 0.3)
+    Nx, Ny, _ = cfg.dense
+    assert abs(dt - 0.3 / (0.5 * Nx + 0.25 * Ny)) < 1e-15
+
+
+# ----------------------------------------------------------------------------- adjoint
+
+@pytest.mark.parametrize("walls", [0, 1])
+def test_adjoint_matches_central_differences(oracle_mod, walls):
+    """Loss = weighted plate Nu and variance over the last steps.  Nu is
+    affine in T0, so its central difference is exact up to round-off; the
+    variance and the velocity directions are O(eps^2)."""
+    O = oracle_mod
+    cfg = _cfg(O, nx=4, ny=4, nz=4, mx=2, my=2, mz=2, gamma=1.5, kappa=5e-3, dt=5e-3,
+               np_average=4, walls_xy=walls)
+    coarse = _velocity(O, cfg)
+    vel = O.refine(cfg, *coarse)
+    g = O.grid(cfg)
+    Nx, Ny, Nz = cfg.dense
+    T0 = synth.initial_scalar(3, g["zc"], Ny, Nx)
+    S = 10
+    wnu = np.zeros(S + 1)
+    wnu[-4:] = 0.25
+    wvar = np.zeros(S + 1)
+    wvar[-1] = 3.0
+    L, gT0, gUs, gVs, gWs = O.adjoint(cfg, vel, T0, S, wnu, wvar)
+    gU, gV, gW = O.refine_adjoint(cfg, gUs, gVs, gWs)
+
+    def loss(T0_, coarse_):
+        v = O.refine(cfg, *coarse_)
+        return O.adjoint(cfg, v, T0_, S, wnu, wvar)[0]
+
+    assert abs(loss(T0, coarse) - L) < 1e-14
+    rng = np.random.default_rng(9)
+    eps = 1e-6
+    for _ in range(4):
+        d = rng.standard_normal(T0.shape)
+        fd = (loss(T0 + eps * d, coarse) - loss(T0 - eps * d, coarse)) / (2 * eps)
+        assert abs(fd - np.vdot(gT0, d)) <= 1e-7 * max(1.0, abs(fd))
+        dc = [rng.standard_normal(a.shape) for a in coarse]
+        cp = [a + eps * b for a, b in zip(coarse, dc)]
+        cm = [a - eps * b for a, b in zip(coarse, dc)]
+        fd = (loss(T0, cp) - loss(T0, cm)) / (2 * eps)
+        an = sum(np.vdot(a, b) for a, b in zip((gU, gV, gW), dc))
+        assert abs(fd - an) <= 1e-6 * max(1.0, abs(fd))
+
+
+def test_adjoint_dot_product_nu_is_affine(oracle_mod):
+    """<dL/dT0, d> equals L(T0 + d) - L(T0) exactly (up to round-off) when the
+    loss is plate Nu only: the scheme is affine in T for fixed velocity."""
+    O = oracle_mod
+    cfg = _cfg(O, nx=5, ny=4, nz=4, mx=2, my=2, mz=2, gamma=1.5, kappa=2e-3, dt=4e-3, np_average=6)
+    vel = O.refine(cfg, *_velocity(O, cfg))
+    g = O.grid(cfg)
+    Nx, Ny, Nz = cfg.dense
+    T0 = synth.initial_scalar(4, g["zc"], Ny, Nx)
+    S = 14
+    wnu = np.linspace(0.0, 1.0, S + 1)
+    L0, gT0, *_ = O.adjoint(cfg, vel, T0, S, wnu, None)
+    d = np.random.default_rng(2).standard_normal(T0.shape)
+    L1 = O.adjoint(cfg, vel, T0 + d, S, wnu, None)[0]
+    assert abs((L1 - L0) - np.vdot(gT0, d)) < 1e-11
