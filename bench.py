@@ -1,0 +1,328 @@
+"""Benchmark of the multiple-resolution scalar path on GB300.
+
+Workload (default): the FP32 precision form -- coarse 128x128x96 (tanh-stretched
+z, gamma 1.5), refinement 4 -> dense 512x512x384 (100,663,296 cells), Sc = 100,
+Ra = 1e9, dt from CFL 0.3 on the refined synthetic velocity.  One step = one
+pass of the whole hot path over the grid: the divergence-free refinement of
+the coarse velocity and the finite-volume scalar update (fused into one kernel
+in MR_VEL_FUSED mode, the refinement amortised in MR_VEL_STORED mode).
+
+Prints one JSON line (rank 0).  Metric: dense cell-updates per second.  Beside
+it: the FP64 path on the same grid, the roofline fraction of the dominant
+kernel (CUDA events, algorithmic bytes), the end-to-end rate through the C-ABI
+with host buffers, and the FP64 CPU oracle timed on this host's cores.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl mr|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOADS = {
+    # name: coarse grid, refinement, stretching, Ra, Pr/Sc, rms velocity
+    "rb512_stretched_f32": dict(nx=128, ny=128, nz=96, m=4, gamma=1.5, ra=1e9, pr=100.0, rms=0.1,
+                                label="coarse 128x128x96 -> dense 512x512x384, stretched z (gamma 1.5), "
+                                      "Ra=1e9, Sc=100, CFL 0.3"),
+    "rb256_stretched_f64": dict(nx=128, ny=128, nz=96, m=2, gamma=1.5, ra=1e8, pr=7.0, rms=0.1,
+                                label="coarse 128x128x96 -> dense 256x256x192, stretched z (gamma 1.5), "
+                                      "Ra=1e8, Pr=7, CFL 0.3"),
+}
+SEED = 1805
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        rows = []
+        try:
+            for line in open(self.path):
+                f = [x.strip() for x in line.split(",")]
+                if len(f) >= 9 and f[1].replace(".", "").isdigit():
+                    rows.append(f)
+        except Exception:
+            pass
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        sm = [float(r[1]) for r in rows]
+        smax = max(float(r[2]) for r in rows)
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        reasons = sorted({n for r in rows for n, v in zip(names, r[5:9]) if v.lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": smax, "reasons": reasons,
+                "samples": len(rows), "power_w_max": max(float(r[3]) for r in rows if r[3].replace(".", "").isdigit())}
+
+
+def _dist():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def _inputs(mr, h, w):
+    """Seeded synthetic coarse velocity and initial scalar for handle h."""
+    from paper_1805_03426_gb300 import synth
+    (Nx, Ny, Nz), zf = mr.mr_grid(h)
+    m = w["m"]
+    Xf = np.arange(w["nx"] + 1) / w["nx"]
+    Yf = np.arange(w["ny"] + 1) / w["ny"]
+    Zf = zf[::m].copy()
+    U, V, W = synth.coarse_velocity(SEED, Xf, Yf, Zf, 1.0, 1.0, rms=w["rms"])
+    zc = 0.5 * (zf[1:] + zf[:-1])
+    T0 = synth.initial_scalar(SEED, zc, Ny, Nx)
+    return U, V, W, T0
+
+
+def _make(mr, w, precision, mode, dt=1e-3):
+    c = mr.mr_config_default(nx=w["nx"], ny=w["ny"], nz=w["nz"], mx=w["m"], my=w["m"], mz=w["m"],
+                             stretch_gamma=w["gamma"], ra=w["ra"], pr_or_sc=w["pr"], dt=dt,
+                             precision=precision, velocity_mode=mode)
+    return mr.mr_create(c)
+
+
+def _time_steps(torch, mr, h, steps, warmup, stream):
+    for _ in range(warmup):
+        mr.mr_scalar_step(h, 1, stream=stream)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        mr.mr_scalar_step(h, 1, stream=stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / 1e3
+
+
+def run_mr(args):
+    import torch
+    import torch.distributed as dist
+    import paper_1805_03426_gb300.mr as mr
+
+    world, rank, local = _dist()
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl")
+    w = WORKLOADS[args.workload]
+    Nx, Ny, Nz = w["nx"] * w["m"], w["ny"] * w["m"], w["nz"] * w["m"]
+    cells = Nx * Ny * Nz
+    prec = mr.MR_F32 if args.precision == "f32" else mr.MR_F64
+    mode = {"stored": mr.MR_VEL_STORED, "fused": mr.MR_VEL_FUSED}[args.mode]
+    stream = torch.cuda.Stream()
+    h = _make(mr, w, prec, mode)
+    U, V, W, T0 = _inputs(mr, h, w)
+    dU, dV, dW = (torch.from_numpy(a).cuda() for a in (U, V, W))
+    dT0 = torch.from_numpy(T0).cuda()
+    torch.cuda.synchronize()
+    mr.mr_refine_velocity(h, dU, dV, dW, stream=stream)
+    dt = mr.mr_cfl_dt(h, 0.3, stream=stream)
+    mr.mr_set_dt(h, dt)
+    mr.mr_set_scalar(h, dT0, stream=stream)
+    torch.cuda.synchronize()
+
+    if world > 1:
+        dist.barrier()
+    with ClockSampler(local) as clk:
+        t = _time_steps(torch, mr, h, args.steps, args.warmup, stream)
+    if world > 1:
+        tt = torch.tensor([t], device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t = float(tt.item())
+    value = world * cells * args.steps / t / 1e9
+    st = mr.mr_scalar_stats(h, stream=stream, allow_nonfinite=True)
+
+    # roofline of the dominant (only) kernel of the step: one launch per step
+    elt = 4 if prec == mr.MR_F32 else 8
+    M3 = w["m"] ** 3
+    bytes_per_cell = (3 * elt + 3 * elt / M3) if mode == mr.MR_VEL_FUSED else 6 * elt
+    per_launch = t / args.steps
+    peak, peak_kind = _peaks()
+    achieved = bytes_per_cell * cells / per_launch / 1e9
+    roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+            "frac": round(achieved / peak, 4), "traffic": None, "peak_source": peak_kind,
+            "kernel": "k_step_fused_f32" if mode == mr.MR_VEL_FUSED else "k_step_stored",
+            "bytes_per_cell": round(bytes_per_cell, 3), "launch_ms": round(per_launch * 1e3, 4)}
+
+    # FP64 path on the same grid (stored velocity), for the FP32/FP64 ratio
+    fp64 = None
+    if rank == 0 and prec == mr.MR_F32 and not args.no_fp64:
+        h64 = _make(mr, w, mr.MR_F64, mr.MR_VEL_STORED, dt=dt)
+        mr.mr_refine_velocity(h64, dU, dV, dW, stream=stream)
+        mr.mr_set_scalar(h64, dT0, stream=stream)
+        k64 = max(10, args.steps // 10)
+        t64 = _time_steps(torch, mr, h64, k64, 3, stream)
+        v64 = cells * k64 / t64 / 1e9
+        fp64 = {"value": round(v64, 3), "unit": "Gcell-updates/s", "steps": k64,
+                "ms_per_step": round(t64 / k64 * 1e3, 4), "fp32_over_fp64": round(value / world / v64, 2)}
+        h64.close()
+
+    # end to end through the C-ABI with host buffers: per step the coarse
+    # velocity goes host -> device (pinned), the step runs, plate Nu comes back
+    e2e = None
+    if rank == 0 and not args.no_e2e:
+        Uh, Vh, Wh = (torch.from_numpy(a).pin_memory() for a in (U, V, W))
+        nu = torch.zeros(2, dtype=torch.float64).pin_memory()
+        ke = max(20, args.steps // 5)
+        for _ in range(3):
+            mr.mr_refine_velocity(h, Uh, Vh, Wh, stream=stream)
+            mr.mr_scalar_step(h, 1, stream=stream)
+            mr.mr_plate_nu(h, nu, stream=stream)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(ke):
+            mr.mr_refine_velocity(h, Uh, Vh, Wh, stream=stream)
+            mr.mr_scalar_step(h, 1, stream=stream)
+            mr.mr_plate_nu(h, nu, stream=stream)
+            stream.synchronize()
+        te = time.perf_counter() - t0
+        e2e = {"value": round(cells * ke / te / 1e9, 3), "unit": "Gcell-updates/s",
+               "h2d_bytes_per_step": int(U.nbytes + V.nbytes + W.nbytes), "d2h_bytes_per_step": 16,
+               "steps": ke}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        cpu = cpu_baseline(w, dt, budget_s=args.cpu_budget)
+
+    h.close()
+    if rank == 0:
+        line = {
+            "metric": "dense-grid scalar cell-updates/s (refine + finite-volume step)",
+            "value": round(value, 3), "unit": "Gcell-updates/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(t / args.steps * 1e3, 4), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32" if prec == mr.MR_F32 else "f64", "data": "synthetic",
+            "config": {"workload": args.workload, "description": w["label"], "dense_cells": cells,
+                       "velocity_mode": args.mode, "dt": dt, "parallelism": f"replicas{world}",
+                       "l2": "inputs larger than L2 (3 scalar levels of %.0f MB)" % (cells * elt / 2**20)},
+            "roofline": roof, "fp64_path": fp64, "e2e": e2e, "cpu_baseline": cpu,
+            "gpu_launches": args.steps, "clocks": clk.summary(),
+            "final_stats": {k: st[k] for k in ("nu_bot", "nu_top", "mean", "var")},
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def cpu_baseline(w, dt, budget_s=30.0, max_steps=None):
+    """FP64 oracle on this host's cores: one refinement, then whole-grid steps
+    until the time budget is spent (at least one)."""
+    import oracle as O
+    from paper_1805_03426_gb300 import synth
+    cfg = O.Config(nx=w["nx"], ny=w["ny"], nz=w["nz"], mx=w["m"], my=w["m"], mz=w["m"], gamma=w["gamma"],
+                   kappa=(w["ra"] * w["pr"]) ** -0.5, dt=dt)
+    g = O.grid(cfg)
+    U, V, W = synth.coarse_velocity(SEED, g["Xf"], g["Yf"], g["Zf"], rms=w["rms"])
+    Nx, Ny, Nz = cfg.dense
+    T0 = synth.initial_scalar(SEED, g["zc"], Ny, Nx)
+    t0 = time.perf_counter()
+    vel = O.refine(cfg, U, V, W)
+    t_ref = time.perf_counter() - t0
+    Tm, T = T0, T0
+    n, t_steps = 0, 0.0
+    while True:
+        t0 = time.perf_counter()
+        Tm, T = T, O.step(cfg, vel, Tm, T, n)
+        t_steps += time.perf_counter() - t0
+        n += 1
+        if t_steps >= budget_s or (max_steps and n >= max_steps):
+            break
+    cores = len(os.sched_getaffinity(0))
+    return {"value": round(Nx * Ny * Nz * n / t_steps / 1e9, 5), "unit": "Gcell-updates/s", "cores": cores,
+            "kind": "oracle", "sample": f"{n} FP64 oracle steps on the full {Nx}x{Ny}x{Nz} grid after one "
+                                        f"refinement ({t_ref:.1f} s, not counted); OpenMP over {cores} threads",
+            "steps": n, "seconds": round(t_steps, 2)}
+
+
+def run_reference(args):
+    """The FP64 CPU oracle as the reference arm (rank 0 only)."""
+    world, rank, _ = _dist()
+    if rank != 0:
+        return
+    w = WORKLOADS[args.workload]
+    dt = 1e-4
+    budget = min(120.0, 10.0 * (args.steps + args.warmup))
+    cpu = cpu_baseline(w, dt, budget_s=budget, max_steps=args.steps + args.warmup)
+    line = {"impl": "reference", "metric": "dense-grid scalar cell-updates/s (refine + finite-volume step)",
+            "value": cpu["value"], "unit": "Gcell-updates/s", "n_gpus": 0, "steps": cpu["steps"],
+            "warmup": 0, "ms_per_step": round(cpu["seconds"] / cpu["steps"] * 1e3, 2), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": args.workload, "description": w["label"]},
+            "cpu_baseline": cpu,
+            "e2e": {"value": cpu["value"], "unit": "Gcell-updates/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", default="mr", choices=["mr", "reference"])
+    ap.add_argument("--workload", default="rb512_stretched_f32", choices=sorted(WORKLOADS))
+    ap.add_argument("--precision", default="f32", choices=["f32", "f64"])
+    ap.add_argument("--mode", default="stored", choices=["stored", "fused"])
+    ap.add_argument("--cpu-budget", type=float, default=20.0)
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_mr(args)
+
+
+if __name__ == "__main__":
+    main()

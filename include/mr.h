@@ -1,0 +1,168 @@
+/*
+ * mr.h -- C-ABI of the GB300 (sm_103a) multiple-resolution scalar library.
+ *
+ * The library advances a scalar (temperature or concentration) on a dense
+ * staggered grid whose velocity is held on an M-times coarser grid, following
+ * Chong, Ding & Xia, "Multiple-resolution scheme in finite-volume code for
+ * active or passive scalar turbulence" (arXiv:1805.03426):
+ *   - Section 3.1: the dense grid is generated first (tanh clustering toward
+ *     the plates in z, uniform in x and y); coarse faces are every M-th face.
+ *   - Section 3.2: the coarse face velocity is refined onto the dense faces by
+ *     the mass-conserving third-order interpolation R = A_s A^-1 and the
+ *     stepwise flux balance of the inner faces (divergence-free to round-off).
+ *   - Eq. (2)/(5): second-order finite-volume advection-diffusion,
+ *     kappa = (Ra Pr)^-1/2 (or Sc in place of Pr for a passive scalar).
+ *   - Section 2.2: Euler-leapfrog time integration with the averaging step
+ *     every N_p steps; the first step after mr_set_scalar is forward Euler.
+ *
+ * Conventions shared by every call
+ *   Arrays are [z][y][x] with x contiguous (row-major, no padding).
+ *     dense cells   Nz x Ny x Nx            Nx = mx*nx, Ny = my*ny, Nz = mz*nz
+ *     U faces       nz x ny x (nx + w)      x-normal; face i is the west face
+ *     V faces       nz x (ny + w) x nx      y-normal; face j is the south face
+ *     W faces       (nz + 1) x ny x nx      z-normal; planes 0 and nz are plates
+ *   (dense face arrays likewise with Nx, Ny, Nz); w = 1 with MR_WALLS, 0 with
+ *   MR_PERIODIC.  The domain is [0,lx] x [0,ly] x [0,1].
+ *   Plates: T = +0.5 at z = 0 and -0.5 at z = 1 (MR_DIRICHLET) or zero flux.
+ *   Every pointer may be host or device memory unless stated; the library
+ *   detects which and copies on the given stream.  Device pointers must be
+ *   on the handle's device.  The library keeps no caller pointer after a call.
+ *   A stream argument of NULL means the legacy default stream.  Calls are
+ *   asynchronous on the stream except where "synchronises" is stated.
+ *   Return value: MR_OK (0) or a negative MR_ERR_* code; mr_last_error() then
+ *   holds a message for the calling thread.
+ */
+#ifndef MR_H
+#define MR_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct mr_handle_s* mr_handle;
+typedef void* mr_stream; /* a cudaStream_t */
+
+enum {
+    MR_OK = 0,
+    MR_ERR_ARG = -1,       /* invalid argument or configuration            */
+    MR_ERR_CUDA = -2,      /* a CUDA runtime call or kernel launch failed  */
+    MR_ERR_NONFINITE = -3, /* a reduction met NaN or Inf                   */
+    MR_ERR_TIMEOUT = -4,   /* a bounded device wait gave up                */
+    MR_ERR_OOM = -5,       /* device allocation failed                     */
+    MR_ERR_STATE = -6      /* call out of order (e.g. step before set)     */
+};
+enum { MR_F64 = 0, MR_F32 = 1 };               /* precision / buffer dtype */
+enum { MR_VEL_STORED = 0, MR_VEL_FUSED = 1 };  /* dense velocity handling  */
+enum { MR_DIRICHLET = 0, MR_ADIABATIC = 1 };   /* plates                   */
+enum { MR_PERIODIC = 0, MR_WALLS = 1 };        /* x and y boundaries       */
+
+/* Problem statement (Sections 2.1, 3.1).  Fill with mr_config_default first. */
+typedef struct {
+    uint32_t struct_size;     /* sizeof(mr_config): ABI version check         */
+    int32_t nx, ny, nz;       /* coarse cells (>= 3 along any refined axis)   */
+    int32_t mx, my, mz;       /* refinement factors M_x, M_y, M_z (1..8)      */
+    double lx, ly;            /* horizontal extent; height is 1               */
+    double stretch_gamma;     /* 0: uniform z; > 0: tanh clustering of the
+                                 dense z faces, z_k = (1 + tanh(g(2k/Nz-1))/tanh g)/2 */
+    double ra, pr_or_sc;      /* kappa = (ra * pr_or_sc)^-1/2                  */
+    double dt;                /* time step (see mr_cfl_dt / mr_set_dt)        */
+    int32_t precision;        /* MR_F64: FP64 storage and flux arithmetic;
+                                 MR_F32: FP32 storage and flux arithmetic.
+                                 Reductions are FP64 in both.                 */
+    int32_t velocity_mode;    /* MR_VEL_STORED: dense faces kept in HBM;
+                                 MR_VEL_FUSED: refined inside the step kernel
+                                 from the coarse faces, never stored
+                                 (MR_F32, MR_PERIODIC and mx=my=mz only).     */
+    int32_t np_average;       /* N_p of the averaging step (Section 2.2);
+                                 <= 0 disables it; default 50                 */
+    int32_t bc_plates;        /* MR_DIRICHLET | MR_ADIABATIC                  */
+    int32_t bc_horizontal;    /* MR_PERIODIC | MR_WALLS (impermeable, adiabatic) */
+    int32_t diffz_implicit;   /* 0: explicit (the paper's scheme); 1: opt-in
+                                 Crank-Nicolson for vertical diffusion with one
+                                 tridiagonal solve per (x, y) column           */
+} mr_config;
+
+typedef struct {
+    double nu_bot;    /* <(0.5 - T(z_c0)) / z_c0>_xy: bottom-plate Nusselt number  */
+    double nu_top;    /* <(T(z_cN-1) + 0.5) / (1 - z_cN-1)>_xy: top-plate Nusselt  */
+    double mean;      /* volume-weighted mean of T                                 */
+    double var;       /* volume-weighted variance of T (two-pass)                  */
+    double integral;  /* sum of T * cell volume                                    */
+    double max_div;   /* max over dense cells of |sum of outward face fluxes|/volume
+                         of the refined velocity (Section 3.2 divergence check)   */
+} mr_stats;
+
+/* Fill *cfg with defaults: 16^3 coarse, M = 2, uniform, Ra = 1e6, Pr = 7,
+ * dt = 1e-3, MR_F64, MR_VEL_STORED, N_p = 50, Dirichlet plates, periodic. */
+int mr_config_default(mr_config* cfg);
+
+/* Validate *cfg, build the grid and R matrices (Section 3.2: R depends on the
+ * grid only and is computed once), and allocate every device buffer on the
+ * current CUDA device.  *out receives the handle; mr_destroy frees it.
+ * Errors: MR_ERR_ARG (bad sizes, unsupported combination), MR_ERR_OOM. */
+int mr_create(const mr_config* cfg, mr_handle* out);
+
+/* Free every buffer of the handle (synchronises the device first).  NULL is ignored. */
+void mr_destroy(mr_handle h);
+
+/* Message of the last failed call on this thread ("" if none). */
+const char* mr_last_error(void);
+
+/* Dense sizes and the dense z-face coordinates (host array of Nz + 1 doubles,
+ * may be NULL).  dims3 (may be NULL) receives Nx, Ny, Nz. */
+int mr_grid(mr_handle h, int32_t* dims3, double* zf_host);
+
+/* Refinement, Section 3.2.  U, V, W: coarse face velocities in FP64 (host or
+ * device).  The handle keeps its own copy.  In MR_VEL_STORED mode the dense
+ * faces are computed now and kept; Us, Vs, Ws (device, handle precision, may
+ * be NULL) receive a copy of them.  In MR_VEL_FUSED mode the step kernel
+ * refines on the fly; non-NULL Us, Vs, Ws are still filled for inspection.
+ * The coarse field must be discretely divergence-free and zero on the plates;
+ * the library does not check this (mr_scalar_stats reports max_div). */
+int mr_refine_velocity(mr_handle h, const double* U, const double* V, const double* W,
+                       void* Us, void* Vs, void* Ws, mr_stream stream);
+
+/* Copy the scalar in (dtype MR_F64 or MR_F32, host or device) and restart the
+ * time integration: the next step is the forward-Euler start. */
+int mr_set_scalar(mr_handle h, const void* T0, int32_t dtype, mr_stream stream);
+
+/* Copy T^n (and T^{n-1} if Tprev != NULL) out, converted to dtype. */
+int mr_get_scalar(mr_handle h, void* T, void* Tprev, int32_t dtype, mr_stream stream);
+
+/* Advance nsteps time steps (Section 2.2, Eq. 5): one fused kernel launch per
+ * step.  Needs mr_refine_velocity and mr_set_scalar first (MR_ERR_STATE). */
+int mr_scalar_step(mr_handle h, int64_t nsteps, mr_stream stream);
+
+/* Number of steps taken since the last mr_set_scalar. */
+int mr_step_index(mr_handle h, int64_t* s);
+
+/* FP64 reductions of T^n and the refined velocity (Section 4.1 plate Nusselt
+ * numbers, volume moments, divergence check).  Synchronises the stream.
+ * Returns MR_ERR_NONFINITE (and still fills *out) if T holds NaN or Inf. */
+int mr_scalar_stats(mr_handle h, mr_stats* out, mr_stream stream);
+
+/* Plate Nusselt numbers only (nu2[0] bottom, nu2[1] top; host or device
+ * pointer to 2 doubles).  Asynchronous; a cheap reduction over two planes. */
+int mr_plate_nu(mr_handle h, double* nu2, mr_stream stream);
+
+/* dt = cfl / max over dense cells of (max(|u_w|,|u_e|)/dx + max(|v_s|,|v_n|)/dy
+ * + max(|w_b|,|w_t|)/dz) on the refined velocity.  Synchronises.  Does not
+ * change the handle's dt (use mr_set_dt). */
+int mr_cfl_dt(mr_handle h, double cfl, double* dt_out, mr_stream stream);
+
+/* Replace the time step. */
+int mr_set_dt(mr_handle h, double dt);
+
+/* Integer index maps for testing (synchronous, host buffer): coarse cell of
+ * every dense cell along x, y, z, then the three coarse cells of the R window
+ * of every coarse cell along x, y, z: Nx+Ny+Nz+3(nx+ny+nz) int32 values.
+ * MR_ERR_ARG if cap (in elements) is too small. */
+int mr_debug_index_maps(mr_handle h, int32_t* out, size_t cap);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MR_H */

@@ -1,0 +1,702 @@
+// C-ABI entry points (include/mr.h) and the host-side metric setup.
+//
+// Metric setup (Sections 3.1, 3.2): the dense grid is generated first (z by
+// tanh clustering toward both plates, x and y uniform); coarse faces are every
+// M-th dense face.  For every coarse cell of every axis the mass-conserving
+// third-order interpolation matrix R = A_s A^-1 is formed once, in FP64, in
+// coordinates local to the cell ((x - x_centre) / dX, the same matrix as in
+// absolute coordinates but well conditioned).  The 3x3 system is inverted by
+// its adjugate.  Near a wall the three-cell window is one-sided.
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <string>
+#include <vector>
+
+#include "mr_internal.cuh"
+
+namespace mr {
+
+static thread_local std::string g_last_error;
+
+int set_error(int code, const std::string& msg)
+{
+    g_last_error = msg;
+    return code;
+}
+
+int cuda_check(cudaError_t e, const char* what)
+{
+    if (e == cudaSuccess) return MR_OK;
+    std::string m = std::string(what) + ": " + cudaGetErrorString(e);
+    if (e == cudaErrorMemoryAllocation) return set_error(MR_ERR_OOM, m);
+    return set_error(MR_ERR_CUDA, m);
+}
+
+bool is_device_pointer(const void* p)
+{
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+StepCoef step_coef(const mr_config& cfg, int64_t s)
+{
+    // Section 2.2: leapfrog, averaging every N_p steps; s = 0 starts with Euler.
+    if (s == 0) return {0.0, 1.0, cfg.dt};
+    if (cfg.np_average > 0 && (s + 1) % cfg.np_average == 0) return {0.5, 0.5, 1.5 * cfg.dt};
+    return {1.0, 0.0, 2.0 * cfg.dt};
+}
+
+// ---------------------------------------------------------------- metric setup
+
+static void dense_z_faces(int N, double gamma, std::vector<double>& zf)
+{
+    zf.resize(N + 1);
+    const double tg = gamma > 0.0 ? tanh(gamma) : 1.0;
+    for (int k = 0; k <= N; ++k) {
+        const double eta = (double)k / (double)N;
+        zf[k] = gamma > 0.0 ? 0.5 * (1.0 + tanh(gamma * (2.0 * eta - 1.0)) / tg) : eta;
+    }
+    zf[0] = 0.0;
+    zf[N] = 1.0;
+}
+
+// Row of cell means of 1, t, t^2 over [a, b] (the rows of A and A_s).
+static void means3(double a, double b, double out[3])
+{
+    out[0] = 1.0;
+    out[1] = 0.5 * (a + b);
+    out[2] = (a * a + a * b + b * b) / 3.0;
+}
+
+static bool invert3(const double A[3][3], double inv[3][3])
+{
+    const double c00 = A[1][1] * A[2][2] - A[1][2] * A[2][1];
+    const double c01 = A[1][2] * A[2][0] - A[1][0] * A[2][2];
+    const double c02 = A[1][0] * A[2][1] - A[1][1] * A[2][0];
+    const double det = A[0][0] * c00 + A[0][1] * c01 + A[0][2] * c02;
+    if (det == 0.0 || !isfinite(det)) return false;
+    const double r = 1.0 / det;
+    inv[0][0] = c00 * r;
+    inv[1][0] = c01 * r;
+    inv[2][0] = c02 * r;
+    inv[0][1] = (A[0][2] * A[2][1] - A[0][1] * A[2][2]) * r;
+    inv[1][1] = (A[0][0] * A[2][2] - A[0][2] * A[2][0]) * r;
+    inv[2][1] = (A[0][1] * A[2][0] - A[0][0] * A[2][1]) * r;
+    inv[0][2] = (A[0][1] * A[1][2] - A[0][2] * A[1][1]) * r;
+    inv[1][2] = (A[0][2] * A[1][0] - A[0][0] * A[1][2]) * r;
+    inv[2][2] = (A[0][0] * A[1][1] - A[0][1] * A[1][0]) * r;
+    return true;
+}
+
+// R for every coarse cell of one axis; R out [n*m][3] (one row per dense
+// index), window out [n][3].
+static bool axis_r(int n, int m, const std::vector<double>& dense_faces, bool periodic, double length,
+                   std::vector<double>& R, std::vector<int>& win)
+{
+    R.assign((size_t)n * m * 3, 0.0);
+    win.assign((size_t)n * 3, 0);
+    for (int i = 0; i < n; ++i) {
+        int first = i - 1;
+        if (!periodic) first = std::min(std::max(first, 0), std::max(n - 3, 0));
+        if (n < 3) first = i;  // only reachable with m == 1
+        const double lo_i = dense_faces[(size_t)i * m], hi_i = dense_faces[(size_t)(i + 1) * m];
+        const double ctr = 0.5 * (lo_i + hi_i), wid = hi_i - lo_i;
+        double A[3][3];
+        int centre_pos = 1;
+        for (int r = 0; r < 3; ++r) {
+            int cell = first + r;
+            double off = 0.0;
+            if (periodic) {
+                if (cell < 0) { cell += n; off = -length; }
+                if (cell >= n) { cell -= n; off = length; }
+            }
+            if (n < 3) cell = i;
+            win[3 * i + r] = cell;
+            if (first + r == i) centre_pos = r;
+            const double a = (dense_faces[(size_t)cell * m] + off - ctr) / wid;
+            const double b = (dense_faces[(size_t)(cell + 1) * m] + off - ctr) / wid;
+            means3(a, b, A[r]);
+        }
+        if (m == 1) {
+            R[3 * (size_t)i + centre_pos] = 1.0;
+            continue;
+        }
+        double inv[3][3];
+        if (!invert3(A, inv)) return false;
+        for (int s = 0; s < m; ++s) {
+            double As[3];
+            means3((dense_faces[(size_t)i * m + s] - ctr) / wid, (dense_faces[(size_t)i * m + s + 1] - ctr) / wid, As);
+            for (int c = 0; c < 3; ++c)
+                R[((size_t)i * m + s) * 3 + c] = As[0] * inv[0][c] + As[1] * inv[1][c] + As[2] * inv[2][c];
+        }
+    }
+    return true;
+}
+
+template <typename P>
+static size_t metric_bytes(const mr_handle_s* h)
+{
+    const size_t nP = (size_t)h->Nz * 4 + 2 * ((size_t)h->Nz + 1) + 3 * ((size_t)h->Nx + h->Ny + h->Nz);
+    return ((nP * sizeof(P) + 255) / 256) * 256;
+}
+
+// Copy the FP64 host metric, cast to P, into dst (device) and point g at it.
+template <typename P>
+static int upload_metric(mr_handle_s* h, char* dst, const int* dwin, Grid<P>& g)
+{
+    const mr_config& c = h->cfg;
+    const int Nz = h->Nz;
+    std::vector<P> host;
+    host.reserve(metric_bytes<P>(h) / sizeof(P));
+    std::vector<size_t> off;
+    auto push = [&](const std::vector<double>& v) {
+        off.push_back(host.size());
+        for (double x : v) host.push_back((P)x);
+    };
+    std::vector<double> inv_dz(Nz), wlo(Nz + 1, 0.0), whi(Nz + 1, 0.0), cdn(Nz), cup(Nz);
+    for (int k = 0; k < Nz; ++k) inv_dz[k] = 1.0 / h->dz[k];
+    for (int k = 1; k < Nz; ++k) {
+        wlo[k] = h->dz[k] / (h->dz[k - 1] + h->dz[k]);
+        whi[k] = h->dz[k - 1] / (h->dz[k - 1] + h->dz[k]);
+    }
+    const bool dir = c.bc_plates == MR_DIRICHLET;
+    for (int k = 0; k < Nz; ++k) {
+        const double below = k > 0 ? h->zc[k] - h->zc[k - 1] : h->zc[0] - h->zf[0];
+        const double above = k < Nz - 1 ? h->zc[k + 1] - h->zc[k] : h->zf[Nz] - h->zc[Nz - 1];
+        cdn[k] = (k > 0 || dir) ? h->kappa / (h->dz[k] * below) : 0.0;
+        cup[k] = (k < Nz - 1 || dir) ? h->kappa / (h->dz[k] * above) : 0.0;
+    }
+    push(h->dz); push(inv_dz); push(wlo); push(whi); push(cdn); push(cup);
+    push(h->Rx); push(h->Ry); push(h->Rz);
+    cudaError_t e = cudaMemcpy(dst, host.data(), host.size() * sizeof(P), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return cuda_check(e, "upload metric");
+    const P* base = (const P*)dst;
+    g.nx = c.nx; g.ny = c.ny; g.nz = c.nz; g.mx = c.mx; g.my = c.my; g.mz = c.mz;
+    g.Nx = h->Nx; g.Ny = h->Ny; g.Nz = h->Nz; g.walls = h->w;
+    g.ufx = h->Nx + h->w; g.vfy = h->Ny + h->w; g.cux = c.nx + h->w; g.cvy = c.ny + h->w;
+    g.dirichlet = dir ? 1 : 0;
+    const double dx = c.lx / h->Nx, dy = c.ly / h->Ny;
+    g.dx = (P)dx; g.dy = (P)dy; g.DX = (P)(c.lx / c.nx); g.DY = (P)(c.ly / c.ny);
+    g.inv_dx = (P)(1.0 / dx); g.inv_dy = (P)(1.0 / dy);
+    g.kx2 = (P)(h->kappa / (dx * dx)); g.ky2 = (P)(h->kappa / (dy * dy));
+    g.dz = base + off[0]; g.inv_dz = base + off[1]; g.wlo = base + off[2]; g.whi = base + off[3];
+    g.cdn = base + off[4]; g.cup = base + off[5]; g.Rx = base + off[6]; g.Ry = base + off[7]; g.Rz = base + off[8];
+    g.wx = dwin; g.wy = dwin + 3 * c.nx; g.wz = dwin + 3 * (c.nx + c.ny);
+    return MR_OK;
+}
+
+static int validate(const mr_config* c, std::string* why)
+{
+    char b[256];
+    if (c->struct_size != sizeof(mr_config)) {
+        snprintf(b, sizeof b, "mr_config.struct_size %u != %zu", c->struct_size, sizeof(mr_config));
+        *why = b;
+        return MR_ERR_ARG;
+    }
+    const int n[3] = {c->nx, c->ny, c->nz}, m[3] = {c->mx, c->my, c->mz};
+    for (int a = 0; a < 3; ++a) {
+        if (n[a] < 1 || m[a] < 1 || m[a] > 8) { *why = "coarse sizes must be >= 1 and refinement in 1..8"; return MR_ERR_ARG; }
+        if (m[a] > 1 && n[a] < 3) { *why = "an axis with refinement > 1 needs >= 3 coarse cells (R window)"; return MR_ERR_ARG; }
+        if (a < 2 && c->bc_horizontal == MR_PERIODIC && n[a] < 3) { *why = "periodic axes need >= 3 coarse cells"; return MR_ERR_ARG; }
+        if ((long long)n[a] * m[a] > (1LL << 20)) { *why = "dense size too large"; return MR_ERR_ARG; }
+    }
+    const long long cells = (long long)c->nx * c->mx * c->ny * c->my * c->nz * c->mz;
+    if (cells > (1LL << 36)) { *why = "dense grid too large"; return MR_ERR_ARG; }
+    if (!(c->lx > 0) || !(c->ly > 0) || !isfinite(c->lx) || !isfinite(c->ly)) { *why = "lx, ly must be positive"; return MR_ERR_ARG; }
+    if (!(c->stretch_gamma >= 0) || c->stretch_gamma > 20) { *why = "stretch_gamma must be in [0, 20]"; return MR_ERR_ARG; }
+    if (!(c->ra > 0) || !(c->pr_or_sc > 0) || !isfinite(c->ra * c->pr_or_sc)) { *why = "ra and pr_or_sc must be positive"; return MR_ERR_ARG; }
+    if (!(c->dt > 0) || !isfinite(c->dt)) { *why = "dt must be positive"; return MR_ERR_ARG; }
+    if (c->precision != MR_F64 && c->precision != MR_F32) { *why = "precision must be MR_F64 or MR_F32"; return MR_ERR_ARG; }
+    if (c->velocity_mode != MR_VEL_STORED && c->velocity_mode != MR_VEL_FUSED) { *why = "bad velocity_mode"; return MR_ERR_ARG; }
+    if (c->bc_plates != MR_DIRICHLET && c->bc_plates != MR_ADIABATIC) { *why = "bad bc_plates"; return MR_ERR_ARG; }
+    if (c->bc_horizontal != MR_PERIODIC && c->bc_horizontal != MR_WALLS) { *why = "bad bc_horizontal"; return MR_ERR_ARG; }
+    if (c->diffz_implicit != 0 && c->diffz_implicit != 1) { *why = "diffz_implicit must be 0 or 1"; return MR_ERR_ARG; }
+    if (c->velocity_mode == MR_VEL_FUSED && !fused_supported(*c, why)) return MR_ERR_ARG;
+    return MR_OK;
+}
+
+}  // namespace mr
+
+using namespace mr;
+
+// ---------------------------------------------------------------- ABI
+
+extern "C" {
+
+const char* mr_last_error(void) { return g_last_error.c_str(); }
+
+int mr_config_default(mr_config* c)
+{
+    if (!c) return set_error(MR_ERR_ARG, "mr_config_default: NULL");
+    memset(c, 0, sizeof(*c));
+    c->struct_size = sizeof(mr_config);
+    c->nx = c->ny = c->nz = 16;
+    c->mx = c->my = c->mz = 2;
+    c->lx = c->ly = 1.0;
+    c->stretch_gamma = 0.0;
+    c->ra = 1e6;
+    c->pr_or_sc = 7.0;
+    c->dt = 1e-3;
+    c->precision = MR_F64;
+    c->velocity_mode = MR_VEL_STORED;
+    c->np_average = 50;
+    c->bc_plates = MR_DIRICHLET;
+    c->bc_horizontal = MR_PERIODIC;
+    c->diffz_implicit = 0;
+    return MR_OK;
+}
+
+void mr_destroy(mr_handle h)
+{
+    if (!h) return;
+    int cur = 0;
+    cudaGetDevice(&cur);
+    cudaSetDevice(h->device);
+    cudaDeviceSynchronize();
+    DeviceBuffers& b = h->buf;
+    void* ptrs[] = {b.T[0], b.T[1], b.T[2], b.U64, b.V64, b.W64, b.Us, b.Vs, b.Ws, b.scrW, b.scrV,
+                    b.metric, b.red, b.nu2, b.stage, b.tri};
+    for (void* p : ptrs)
+        if (p) cudaFree(p);
+    if (h->elt == 4) {
+        if (b.Uc) cudaFree(b.Uc);
+        if (b.Vc) cudaFree(b.Vc);
+        if (b.Wc) cudaFree(b.Wc);
+    }
+    cudaSetDevice(cur);
+    delete h;
+}
+
+int mr_create(const mr_config* cfg, mr_handle* out)
+{
+    if (!cfg || !out) return set_error(MR_ERR_ARG, "mr_create: NULL argument");
+    *out = nullptr;
+    std::string why;
+    int rc = validate(cfg, &why);
+    if (rc) return set_error(rc, "mr_create: " + why);
+    mr_handle_s* h = new mr_handle_s();
+    h->cfg = *cfg;
+    cudaGetDevice(&h->device);
+    const mr_config& c = h->cfg;
+    h->w = c.bc_horizontal == MR_WALLS ? 1 : 0;
+    h->Nx = c.nx * c.mx; h->Ny = c.ny * c.my; h->Nz = c.nz * c.mz;
+    h->ncell = (size_t)h->Nx * h->Ny * h->Nz;
+    h->nU = (size_t)h->Nz * h->Ny * (h->Nx + h->w);
+    h->nV = (size_t)h->Nz * (h->Ny + h->w) * h->Nx;
+    h->nW = (size_t)(h->Nz + 1) * h->Ny * h->Nx;
+    h->ncU = (size_t)c.nz * c.ny * (c.nx + h->w);
+    h->ncV = (size_t)c.nz * (c.ny + h->w) * c.nx;
+    h->ncW = (size_t)(c.nz + 1) * c.ny * c.nx;
+    h->elt = c.precision == MR_F64 ? 8 : 4;
+    h->kappa = 1.0 / sqrt(c.ra * c.pr_or_sc);
+
+    // Section 3.1 grid, Section 3.2 R matrices (FP64, host)
+    dense_z_faces(h->Nz, c.stretch_gamma, h->zf);
+    h->zc.resize(h->Nz);
+    h->dz.resize(h->Nz);
+    for (int k = 0; k < h->Nz; ++k) {
+        h->zc[k] = 0.5 * (h->zf[k] + h->zf[k + 1]);
+        h->dz[k] = h->zf[k + 1] - h->zf[k];
+    }
+    std::vector<double> xf(h->Nx + 1), yf(h->Ny + 1);
+    for (int i = 0; i <= h->Nx; ++i) xf[i] = c.lx * i / h->Nx;
+    for (int j = 0; j <= h->Ny; ++j) yf[j] = c.ly * j / h->Ny;
+    const bool per = c.bc_horizontal == MR_PERIODIC;
+    if (!axis_r(c.nx, c.mx, xf, per, c.lx, h->Rx, h->wx) || !axis_r(c.ny, c.my, yf, per, c.ly, h->Ry, h->wy) ||
+        !axis_r(c.nz, c.mz, h->zf, false, 1.0, h->Rz, h->wz)) {
+        delete h;
+        return set_error(MR_ERR_ARG, "mr_create: singular interpolation matrix (degenerate grid)");
+    }
+
+    DeviceBuffers& b = h->buf;
+    cudaError_t e = cudaSuccess;
+    auto alloc = [&](void** p, size_t bytes) {
+        if (e == cudaSuccess && bytes) e = cudaMalloc(p, bytes);
+    };
+    for (int q = 0; q < 3; ++q) alloc(&b.T[q], h->ncell * h->elt);
+    alloc((void**)&b.U64, h->ncU * 8);
+    alloc((void**)&b.V64, h->ncV * 8);
+    alloc((void**)&b.W64, h->ncW * 8);
+    if (h->elt == 4) {
+        alloc(&b.Uc, h->ncU * 4);
+        alloc(&b.Vc, h->ncV * 4);
+        alloc(&b.Wc, h->ncW * 4);
+    } else {
+        b.Uc = b.U64; b.Vc = b.V64; b.Wc = b.W64;
+    }
+    if (c.velocity_mode == MR_VEL_STORED) {
+        alloc(&b.Us, h->nU * h->elt);
+        alloc(&b.Vs, h->nV * h->elt);
+        alloc(&b.Ws, h->nW * h->elt);
+        alloc(&b.scrW, (size_t)(h->Nz + 1) * c.ny * c.nx * h->elt);
+        alloc(&b.scrV, (size_t)h->Nz * (h->Ny + h->w) * c.nx * h->elt);
+    }
+    const size_t mb64 = metric_bytes<double>(h), mb32 = metric_bytes<float>(h);
+    const size_t nwin = 3 * ((size_t)c.nx + c.ny + c.nz);
+    alloc(&b.metric, mb64 + mb32 + nwin * sizeof(int));
+    h->red_blocks = 152 * 8;
+    alloc((void**)&b.red, (size_t)h->red_blocks * 2 * sizeof(double));
+    alloc((void**)&b.nu2, 4 * sizeof(double));
+    h->stage_bytes = std::min<size_t>((size_t)64 << 20, std::max<size_t>(h->ncell * 8, 1 << 16));
+    alloc(&b.stage, h->stage_bytes);
+    if (c.diffz_implicit) alloc(&b.tri, h->ncell * h->elt);
+    if (e != cudaSuccess) {
+        int r = cuda_check(e, "mr_create: device allocation");
+        mr_destroy(h);
+        return r;
+    }
+    std::vector<int> win;
+    win.insert(win.end(), h->wx.begin(), h->wx.end());
+    win.insert(win.end(), h->wy.begin(), h->wy.end());
+    win.insert(win.end(), h->wz.begin(), h->wz.end());
+    int* dwin = (int*)((char*)b.metric + mb64 + mb32);
+    e = cudaMemcpy(dwin, win.data(), win.size() * sizeof(int), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        int r = cuda_check(e, "mr_create: upload windows");
+        mr_destroy(h);
+        return r;
+    }
+    rc = upload_metric<double>(h, (char*)b.metric, dwin, h->g64);
+    if (!rc) rc = upload_metric<float>(h, (char*)b.metric + mb64, dwin, h->g32);
+    if (rc) {
+        mr_destroy(h);
+        return rc;
+    }
+    *out = h;
+    return MR_OK;
+}
+
+int mr_grid(mr_handle h, int32_t* dims3, double* zf_host)
+{
+    if (!h) return set_error(MR_ERR_ARG, "mr_grid: NULL handle");
+    if (dims3) { dims3[0] = h->Nx; dims3[1] = h->Ny; dims3[2] = h->Nz; }
+    if (zf_host) memcpy(zf_host, h->zf.data(), h->zf.size() * sizeof(double));
+    return MR_OK;
+}
+
+int mr_set_dt(mr_handle h, double dt)
+{
+    if (!h) return set_error(MR_ERR_ARG, "mr_set_dt: NULL handle");
+    if (!(dt > 0) || !isfinite(dt)) return set_error(MR_ERR_ARG, "mr_set_dt: dt must be positive");
+    h->cfg.dt = dt;
+    return MR_OK;
+}
+
+int mr_step_index(mr_handle h, int64_t* s)
+{
+    if (!h || !s) return set_error(MR_ERR_ARG, "mr_step_index: NULL argument");
+    *s = h->step;
+    return MR_OK;
+}
+
+// Copy n elements of dtype sd at src (host or device) into the device buffer
+// dst of dtype dd, converting through the staging buffer when needed.
+static int copy_in(mr_handle h, const void* src, int sd, void* dst, int dd, size_t n, cudaStream_t st)
+{
+    const size_t se = sd == MR_F64 ? 8 : 4, de = dd == MR_F64 ? 8 : 4;
+    cudaError_t e;
+    if (sd == dd) {
+        e = cudaMemcpyAsync(dst, src, n * se, cudaMemcpyDefault, st);
+        return cuda_check(e, "copy in");
+    }
+    if (is_device_pointer(src)) return cuda_check(launch_convert<double>(src, sd, dst, dd, n, st), "convert");
+    const size_t chunk = h->stage_bytes / se;
+    for (size_t o = 0; o < n; o += chunk) {
+        const size_t c = std::min(chunk, n - o);
+        e = cudaMemcpyAsync(h->buf.stage, (const char*)src + o * se, c * se, cudaMemcpyDefault, st);
+        if (e != cudaSuccess) return cuda_check(e, "copy in (stage)");
+        e = launch_convert<double>(h->buf.stage, sd, (char*)dst + o * de, dd, c, st);
+        if (e != cudaSuccess) return cuda_check(e, "convert (stage)");
+    }
+    return MR_OK;
+}
+
+static int copy_out(mr_handle h, const void* src, int sd, void* dst, int dd, size_t n, cudaStream_t st)
+{
+    const size_t se = sd == MR_F64 ? 8 : 4, de = dd == MR_F64 ? 8 : 4;
+    cudaError_t e;
+    if (sd == dd) return cuda_check(cudaMemcpyAsync(dst, src, n * se, cudaMemcpyDefault, st), "copy out");
+    if (is_device_pointer(dst)) return cuda_check(launch_convert<double>(src, sd, dst, dd, n, st), "convert");
+    const size_t chunk = h->stage_bytes / de;
+    for (size_t o = 0; o < n; o += chunk) {
+        const size_t c = std::min(chunk, n - o);
+        e = launch_convert<double>((const char*)src + o * se, sd, h->buf.stage, dd, c, st);
+        if (e != cudaSuccess) return cuda_check(e, "convert (stage)");
+        e = cudaMemcpyAsync((char*)dst + o * de, h->buf.stage, c * de, cudaMemcpyDefault, st);
+        if (e != cudaSuccess) return cuda_check(e, "copy out (stage)");
+    }
+    return MR_OK;
+}
+
+// Refine the handle's coarse faces into device dense-face buffers (Section 3.2).
+static int refine_into(mr_handle h, void* dUs, void* dVs, void* dWs, cudaStream_t st)
+{
+    DeviceBuffers& b = h->buf;
+    cudaError_t e = cudaSuccess;
+    if (!b.scrW) e = cudaMalloc(&b.scrW, (size_t)(h->Nz + 1) * h->cfg.ny * h->cfg.nx * h->elt);
+    if (e == cudaSuccess && !b.scrV) e = cudaMalloc(&b.scrV, (size_t)h->Nz * (h->Ny + h->w) * h->cfg.nx * h->elt);
+    if (e != cudaSuccess) return cuda_check(e, "refinement scratch");
+    if (h->cfg.precision == MR_F64)
+        e = launch_refine<double>(h->g64, (const double*)b.Uc, (const double*)b.Vc, (const double*)b.Wc,
+                                  (double*)dUs, (double*)dVs, (double*)dWs, (double*)b.scrW, (double*)b.scrV, st);
+    else
+        e = launch_refine<float>(h->g32, (const float*)b.Uc, (const float*)b.Vc, (const float*)b.Wc,
+                                 (float*)dUs, (float*)dVs, (float*)dWs, (float*)b.scrW, (float*)b.scrV, st);
+    return cuda_check(e, "refinement launch");
+}
+
+int mr_refine_velocity(mr_handle h, const double* U, const double* V, const double* W, void* Us, void* Vs,
+                       void* Ws, mr_stream stream)
+{
+    if (!h || !U || !V || !W) return set_error(MR_ERR_ARG, "mr_refine_velocity: NULL argument");
+    if ((Us || Vs || Ws) && !(Us && Vs && Ws))
+        return set_error(MR_ERR_ARG, "mr_refine_velocity: Us, Vs, Ws must be all NULL or all set");
+    cudaStream_t st = (cudaStream_t)stream;
+    DeviceBuffers& b = h->buf;
+    int rc;
+    if ((rc = copy_in(h, U, MR_F64, b.U64, MR_F64, h->ncU, st))) return rc;
+    if ((rc = copy_in(h, V, MR_F64, b.V64, MR_F64, h->ncV, st))) return rc;
+    if ((rc = copy_in(h, W, MR_F64, b.W64, MR_F64, h->ncW, st))) return rc;
+    const int P = h->cfg.precision;
+    if (P == MR_F32) {
+        if ((rc = copy_in(h, b.U64, MR_F64, b.Uc, MR_F32, h->ncU, st))) return rc;
+        if ((rc = copy_in(h, b.V64, MR_F64, b.Vc, MR_F32, h->ncV, st))) return rc;
+        if ((rc = copy_in(h, b.W64, MR_F64, b.Wc, MR_F32, h->ncW, st))) return rc;
+    }
+    void *dUs = b.Us, *dVs = b.Vs, *dWs = b.Ws;
+    if (h->cfg.velocity_mode == MR_VEL_FUSED) {
+        if (!Us) {
+            h->have_velocity = true;
+            return MR_OK;
+        }
+        if (!is_device_pointer(Us) || !is_device_pointer(Vs) || !is_device_pointer(Ws))
+            return set_error(MR_ERR_ARG, "mr_refine_velocity: in fused mode Us, Vs, Ws must be device memory");
+        dUs = Us; dVs = Vs; dWs = Ws;
+    }
+    if ((rc = refine_into(h, dUs, dVs, dWs, st))) return rc;
+    if (h->cfg.velocity_mode == MR_VEL_STORED && Us) {
+        if ((rc = copy_out(h, b.Us, P, Us, P, h->nU, st))) return rc;
+        if ((rc = copy_out(h, b.Vs, P, Vs, P, h->nV, st))) return rc;
+        if ((rc = copy_out(h, b.Ws, P, Ws, P, h->nW, st))) return rc;
+    }
+    h->have_velocity = true;
+    return MR_OK;
+}
+
+int mr_set_scalar(mr_handle h, const void* T0, int32_t dtype, mr_stream stream)
+{
+    if (!h || !T0) return set_error(MR_ERR_ARG, "mr_set_scalar: NULL argument");
+    if (dtype != MR_F64 && dtype != MR_F32) return set_error(MR_ERR_ARG, "mr_set_scalar: bad dtype");
+    cudaStream_t st = (cudaStream_t)stream;
+    h->ip = 0;
+    h->ic = 1;
+    int rc = copy_in(h, T0, dtype, h->buf.T[h->ic], h->cfg.precision, h->ncell, st);
+    if (rc) return rc;
+    rc = cuda_check(cudaMemcpyAsync(h->buf.T[h->ip], h->buf.T[h->ic], h->ncell * h->elt,
+                                    cudaMemcpyDeviceToDevice, st), "mr_set_scalar");
+    if (rc) return rc;
+    h->step = 0;
+    h->have_scalar = true;
+    return MR_OK;
+}
+
+int mr_get_scalar(mr_handle h, void* T, void* Tprev, int32_t dtype, mr_stream stream)
+{
+    if (!h || (!T && !Tprev)) return set_error(MR_ERR_ARG, "mr_get_scalar: NULL argument");
+    if (dtype != MR_F64 && dtype != MR_F32) return set_error(MR_ERR_ARG, "mr_get_scalar: bad dtype");
+    if (!h->have_scalar) return set_error(MR_ERR_STATE, "mr_get_scalar: no scalar set");
+    cudaStream_t st = (cudaStream_t)stream;
+    int rc;
+    if (T && (rc = copy_out(h, h->buf.T[h->ic], h->cfg.precision, T, dtype, h->ncell, st))) return rc;
+    if (Tprev && (rc = copy_out(h, h->buf.T[h->ip], h->cfg.precision, Tprev, dtype, h->ncell, st))) return rc;
+    return MR_OK;
+}
+
+int mr_scalar_step(mr_handle h, int64_t nsteps, mr_stream stream)
+{
+    if (!h) return set_error(MR_ERR_ARG, "mr_scalar_step: NULL handle");
+    if (nsteps < 0) return set_error(MR_ERR_ARG, "mr_scalar_step: nsteps < 0");
+    if (!h->have_velocity || !h->have_scalar)
+        return set_error(MR_ERR_STATE, "mr_scalar_step: call mr_refine_velocity and mr_set_scalar first");
+    cudaStream_t st = (cudaStream_t)stream;
+    DeviceBuffers& b = h->buf;
+    const bool implz = h->cfg.diffz_implicit != 0;
+    for (int64_t q = 0; q < nsteps; ++q) {
+        const StepCoef c = step_coef(h->cfg, h->step);
+        const int in = 3 - h->ip - h->ic;
+        const void* Tm1 = h->step == 0 ? b.T[h->ic] : b.T[h->ip];
+        cudaError_t e;
+        if (h->cfg.precision == MR_F64) {
+            e = launch_step_stored<double>(h->g64, (const double*)b.Us, (const double*)b.Vs, (const double*)b.Ws,
+                                           (const double*)Tm1, (const double*)b.T[h->ic], (double*)b.T[in], c,
+                                           implz, st);
+            if (e == cudaSuccess && implz) e = launch_zsolve<double>(h->g64, (double*)b.T[in], 0.5 * c.gdt, (double*)b.tri, st);
+        } else if (h->cfg.velocity_mode == MR_VEL_FUSED) {
+            e = launch_step_fused_f32(h->g32, (const float*)b.Uc, (const float*)b.Vc, (const float*)b.Wc,
+                                      (const float*)Tm1, (const float*)b.T[h->ic], (float*)b.T[in], c, st);
+        } else {
+            e = launch_step_stored<float>(h->g32, (const float*)b.Us, (const float*)b.Vs, (const float*)b.Ws,
+                                          (const float*)Tm1, (const float*)b.T[h->ic], (float*)b.T[in], c, implz,
+                                          st);
+            if (e == cudaSuccess && implz) e = launch_zsolve<float>(h->g32, (float*)b.T[in], 0.5 * c.gdt, (float*)b.tri, st);
+        }
+        if (e != cudaSuccess) return cuda_check(e, "mr_scalar_step: launch");
+        h->ip = h->ic;
+        h->ic = in;
+        ++h->step;
+    }
+    return MR_OK;
+}
+
+int mr_plate_nu(mr_handle h, double* nu2, mr_stream stream)
+{
+    if (!h || !nu2) return set_error(MR_ERR_ARG, "mr_plate_nu: NULL argument");
+    if (!h->have_scalar) return set_error(MR_ERR_STATE, "mr_plate_nu: no scalar set");
+    cudaStream_t st = (cudaStream_t)stream;
+    const double zz[2] = {h->zc[0] - h->zf[0], h->zf[h->Nz] - h->zc[h->Nz - 1]};
+    const bool dev = is_device_pointer(nu2);
+    double* out = dev ? nu2 : h->buf.nu2;
+    cudaError_t e = h->cfg.precision == MR_F64
+                        ? launch_plate_nu<double>(h->g64, (const double*)h->buf.T[h->ic], zz, out, st)
+                        : launch_plate_nu<float>(h->g32, (const float*)h->buf.T[h->ic], zz, out, st);
+    if (e != cudaSuccess) return cuda_check(e, "mr_plate_nu: launch");
+    if (!dev) return cuda_check(cudaMemcpyAsync(nu2, out, 2 * sizeof(double), cudaMemcpyDeviceToHost, st), "mr_plate_nu: copy");
+    return MR_OK;
+}
+
+static int reduce_partials(mr_handle h, int nper, std::vector<double>& out, cudaStream_t st)
+{
+    out.resize((size_t)h->red_blocks * nper);
+    cudaError_t e = cudaMemcpyAsync(out.data(), h->buf.red, out.size() * sizeof(double), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    return cuda_check(e, "reduction");
+}
+
+static int max_divergence(mr_handle h, double* out, cudaStream_t st)
+{
+    cudaError_t e;
+    const DeviceBuffers& b = h->buf;
+    if (h->cfg.velocity_mode == MR_VEL_FUSED)
+        e = launch_maxdiv_fused_f32(h->g32, (const float*)b.Uc, (const float*)b.Vc, (const float*)b.Wc, b.red,
+                                    h->red_blocks, st);
+    else if (h->cfg.precision == MR_F64)
+        e = launch_maxdiv<double>(h->g64, (const double*)b.Us, (const double*)b.Vs, (const double*)b.Ws, b.red,
+                                  h->red_blocks, st);
+    else
+        e = launch_maxdiv<float>(h->g32, (const float*)b.Us, (const float*)b.Vs, (const float*)b.Ws, b.red,
+                                 h->red_blocks, st);
+    if (e != cudaSuccess) return cuda_check(e, "max divergence: launch");
+    std::vector<double> p;
+    int rc = reduce_partials(h, 1, p, st);
+    if (rc) return rc;
+    double m = 0.0;
+    for (double v : p) m = std::max(m, v);
+    *out = m;
+    return MR_OK;
+}
+
+int mr_scalar_stats(mr_handle h, mr_stats* out, mr_stream stream)
+{
+    if (!h || !out) return set_error(MR_ERR_ARG, "mr_scalar_stats: NULL argument");
+    if (!h->have_scalar) return set_error(MR_ERR_STATE, "mr_scalar_stats: no scalar set");
+    cudaStream_t st = (cudaStream_t)stream;
+    const void* T = h->buf.T[h->ic];
+    const double dxdy = (h->cfg.lx / h->Nx) * (h->cfg.ly / h->Ny);
+    double vtot = 0.0;
+    for (int k = 0; k < h->Nz; ++k) vtot += h->dz[k];
+    vtot *= dxdy * (double)h->Nx * (double)h->Ny;
+    std::vector<double> p;
+    cudaError_t e;
+    e = h->cfg.precision == MR_F64 ? launch_moments<double>(h->g64, (const double*)T, 0.0, 0, h->buf.red, h->red_blocks, st)
+                                   : launch_moments<float>(h->g32, (const float*)T, 0.0, 0, h->buf.red, h->red_blocks, st);
+    if (e != cudaSuccess) return cuda_check(e, "mr_scalar_stats: launch");
+    int rc = reduce_partials(h, 2, p, st);
+    if (rc) return rc;
+    double s = 0.0, bad = 0.0;
+    for (int q = 0; q < h->red_blocks; ++q) { s += p[2 * q]; bad += p[2 * q + 1]; }
+    out->integral = s * dxdy;
+    out->mean = out->integral / vtot;
+    e = h->cfg.precision == MR_F64
+            ? launch_moments<double>(h->g64, (const double*)T, out->mean, 1, h->buf.red, h->red_blocks, st)
+            : launch_moments<float>(h->g32, (const float*)T, out->mean, 1, h->buf.red, h->red_blocks, st);
+    if (e != cudaSuccess) return cuda_check(e, "mr_scalar_stats: launch");
+    if ((rc = reduce_partials(h, 2, p, st))) return rc;
+    double v = 0.0;
+    for (int q = 0; q < h->red_blocks; ++q) v += p[2 * q];
+    out->var = v * dxdy / vtot;
+    double nu[2];
+    if ((rc = mr_plate_nu(h, nu, stream))) return rc;
+    if ((rc = cuda_check(cudaStreamSynchronize(st), "mr_scalar_stats: sync"))) return rc;
+    out->nu_bot = nu[0];
+    out->nu_top = nu[1];
+    out->max_div = 0.0;
+    if (h->have_velocity && (rc = max_divergence(h, &out->max_div, st))) return rc;
+    if (bad > 0.0) return set_error(MR_ERR_NONFINITE, "mr_scalar_stats: the scalar holds NaN or Inf");
+    return MR_OK;
+}
+
+int mr_cfl_dt(mr_handle h, double cfl, double* dt_out, mr_stream stream)
+{
+    if (!h || !dt_out) return set_error(MR_ERR_ARG, "mr_cfl_dt: NULL argument");
+    if (!(cfl > 0)) return set_error(MR_ERR_ARG, "mr_cfl_dt: cfl must be positive");
+    if (!h->have_velocity) return set_error(MR_ERR_STATE, "mr_cfl_dt: call mr_refine_velocity first");
+    cudaStream_t st = (cudaStream_t)stream;
+    DeviceBuffers& b = h->buf;
+    const void *us = b.Us, *vs = b.Vs, *ws = b.Ws;
+    bool tmp = false;
+    if (h->cfg.velocity_mode == MR_VEL_FUSED) {
+        // dense faces are not kept: refine into temporary buffers once
+        void *a = nullptr, *bb = nullptr, *c = nullptr;
+        cudaError_t e = cudaMalloc(&a, h->nU * h->elt);
+        if (e == cudaSuccess) e = cudaMalloc(&bb, h->nV * h->elt);
+        if (e == cudaSuccess) e = cudaMalloc(&c, h->nW * h->elt);
+        if (e != cudaSuccess) {
+            cudaFree(a); cudaFree(bb); cudaFree(c);
+            return cuda_check(e, "mr_cfl_dt: temporary dense faces");
+        }
+        int rc = refine_into(h, a, bb, c, st);
+        if (rc) { cudaFree(a); cudaFree(bb); cudaFree(c); return rc; }
+        us = a; vs = bb; ws = c;
+        tmp = true;
+    }
+    cudaError_t e = h->cfg.precision == MR_F64
+                        ? launch_cfl<double>(h->g64, (const double*)us, (const double*)vs, (const double*)ws, b.red, h->red_blocks, st)
+                        : launch_cfl<float>(h->g32, (const float*)us, (const float*)vs, (const float*)ws, b.red, h->red_blocks, st);
+    std::vector<double> p;
+    int rc = e != cudaSuccess ? cuda_check(e, "mr_cfl_dt: launch") : reduce_partials(h, 1, p, st);
+    if (tmp) { cudaFree((void*)us); cudaFree((void*)vs); cudaFree((void*)ws); }
+    if (rc) return rc;
+    double m = 0.0;
+    for (double v : p) m = std::max(m, v);
+    if (!(m > 0)) return set_error(MR_ERR_ARG, "mr_cfl_dt: zero velocity");
+    *dt_out = cfl / m;
+    return MR_OK;
+}
+
+int mr_debug_index_maps(mr_handle h, int32_t* out, size_t cap)
+{
+    if (!h || !out) return set_error(MR_ERR_ARG, "mr_debug_index_maps: NULL argument");
+    const mr_config& c = h->cfg;
+    const size_t need = (size_t)h->Nx + h->Ny + h->Nz + 3 * ((size_t)c.nx + c.ny + c.nz);
+    if (cap < need) return set_error(MR_ERR_ARG, "mr_debug_index_maps: buffer too small");
+    // the maps are read back from the device copy the kernels use
+    std::vector<int> win(3 * ((size_t)c.nx + c.ny + c.nz));
+    const char* base = (const char*)h->buf.metric + metric_bytes<double>(h) + metric_bytes<float>(h);
+    cudaError_t e = cudaMemcpy(win.data(), base, win.size() * sizeof(int), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_check(e, "mr_debug_index_maps");
+    int32_t* p = out;
+    for (int i = 0; i < h->Nx; ++i) *p++ = i / c.mx;
+    for (int j = 0; j < h->Ny; ++j) *p++ = j / c.my;
+    for (int k = 0; k < h->Nz; ++k) *p++ = k / c.mz;
+    for (int v : win) *p++ = v;
+    return MR_OK;
+}
+
+}  // extern "C"

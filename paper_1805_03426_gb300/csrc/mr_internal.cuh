@@ -1,0 +1,127 @@
+// Internal declarations of the multiple-resolution scalar library (sm_103a).
+// The public boundary is include/mr.h; everything here is private.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/mr.h"
+
+namespace mr {
+
+// Device view of the grid and of the per-layer coefficients, in precision P.
+// Built once per handle from the FP64 host grid (Sections 3.1, 3.2).
+template <typename P>
+struct Grid {
+    int nx, ny, nz, mx, my, mz;  // coarse cells, refinement factors
+    int Nx, Ny, Nz;              // dense cells
+    int walls;                   // 1: impermeable adiabatic side walls
+    int ufx, vfy;                // dense U row length (Nx+w), V rows (Ny+w)
+    int cux, cvy;                // coarse U row length, V rows
+    int dirichlet;               // plates: 1 Dirichlet (+-0.5), 0 adiabatic
+    P dx, dy, DX, DY;
+    P inv_dx, inv_dy;            // A_x / Vol and A_y / Vol
+    P kx2, ky2;                  // kappa / dx^2, kappa / dy^2
+    const P* dz;                 // [Nz] dense layer widths
+    const P* inv_dz;             // [Nz] A_z / Vol
+    const P* wlo;                // [Nz+1] weight of T_{k-1} at z-face k (linear interpolation)
+    const P* whi;                // [Nz+1] weight of T_k at z-face k
+    const P* cdn;                // [Nz] kappa / (dz_k * distance to the centre or plate below)
+    const P* cup;                // [Nz] kappa / (dz_k * distance to the centre or plate above)
+    const P* Rx;                 // [Nx][3] R row of every dense x index (Section 3.2)
+    const P* Ry;                 // [Ny][3]
+    const P* Rz;                 // [Nz][3]
+    const int* wx;               // [nx][3] coarse cells of the R window
+    const int* wy;               // [ny][3]
+    const int* wz;               // [nz][3]
+};
+
+// Coefficients of one step: T^{s+1} = a T^{s-1} + b T^s + gdt [C(T^s) + D(T^{s-1})].
+struct StepCoef {
+    double a, b, gdt;
+};
+
+struct DeviceBuffers {
+    void* T[3] = {nullptr, nullptr, nullptr};  // rotating scalar levels, precision P
+    double* U64 = nullptr;                     // coarse faces, FP64 copy
+    double* V64 = nullptr;
+    double* W64 = nullptr;
+    void* Uc = nullptr;                        // coarse faces in precision P (alias of *64 for FP64)
+    void* Vc = nullptr;
+    void* Wc = nullptr;
+    void* Us = nullptr;                        // dense faces (MR_VEL_STORED)
+    void* Vs = nullptr;
+    void* Ws = nullptr;
+    void* scrW = nullptr;                      // refinement scratch: full-coarse-area W per dense plane
+    void* scrV = nullptr;                      // refinement scratch: full-coarse-width V per dense row
+    void* metric = nullptr;                    // one block holding every Grid array
+    double* red = nullptr;                     // reduction partials
+    double* nu2 = nullptr;                     // plate Nusselt numbers (2 doubles)
+    void* stage = nullptr;                     // conversion staging buffer
+    void* tri = nullptr;                       // implicit-z work (2 * Nz per column)
+};
+
+}  // namespace mr
+
+struct mr_handle_s {
+    mr_config cfg;
+    int device = 0;
+    int Nx = 0, Ny = 0, Nz = 0, w = 0;
+    size_t ncell = 0, nU = 0, nV = 0, nW = 0, ncU = 0, ncV = 0, ncW = 0;
+    size_t elt = 8;          // bytes per element of precision P
+    double kappa = 0.0;
+    int64_t step = 0;        // steps taken since mr_set_scalar
+    int ip = 0, ic = 1;      // indices of T^{n-1}, T^n in buf.T
+    bool have_velocity = false, have_scalar = false;
+    // host FP64 grid (Section 3.1) and R matrices (Section 3.2)
+    std::vector<double> zf, zc, dz, Rx, Ry, Rz;
+    std::vector<int> wx, wy, wz;
+    mr::DeviceBuffers buf;
+    mr::Grid<double> g64;
+    mr::Grid<float> g32;
+    size_t stage_bytes = 0;
+    int red_blocks = 0;
+};
+
+namespace mr {
+
+int set_error(int code, const std::string& msg);
+int cuda_check(cudaError_t e, const char* what);
+bool is_device_pointer(const void* p);
+StepCoef step_coef(const mr_config& cfg, int64_t s);
+
+// launchers (return cudaError_t of the launch)
+template <typename P>
+cudaError_t launch_refine(const Grid<P>& g, const P* U, const P* V, const P* W, P* Us, P* Vs, P* Ws,
+                          P* scrW, P* scrV, cudaStream_t st);
+template <typename P>
+cudaError_t launch_step_stored(const Grid<P>& g, const P* Us, const P* Vs, const P* Ws, const P* Tm1,
+                               const P* T, P* Tp1, StepCoef c, bool implz, cudaStream_t st);
+template <typename P>
+cudaError_t launch_zsolve(const Grid<P>& g, P* Tp1, double half_gdt, P* work, cudaStream_t st);
+template <typename P>
+cudaError_t launch_convert(const void* src, int src_dtype, void* dst, int dst_dtype, size_t n,
+                           cudaStream_t st);
+template <typename P>
+cudaError_t launch_moments(const Grid<P>& g, const P* T, double mean, int pass, double* partials,
+                           int blocks, cudaStream_t st);
+template <typename P>
+cudaError_t launch_plate_nu(const Grid<P>& g, const P* T, const double* zb_zt, double* out2,
+                            cudaStream_t st);
+template <typename P>
+cudaError_t launch_maxdiv(const Grid<P>& g, const P* Us, const P* Vs, const P* Ws, double* partials,
+                          int blocks, cudaStream_t st);
+template <typename P>
+cudaError_t launch_cfl(const Grid<P>& g, const P* Us, const P* Vs, const P* Ws, double* partials,
+                       int blocks, cudaStream_t st);
+cudaError_t launch_step_fused_f32(const Grid<float>& g, const float* U, const float* V, const float* W,
+                                  const float* Tm1, const float* T, float* Tp1, StepCoef c,
+                                  cudaStream_t st);
+cudaError_t launch_maxdiv_fused_f32(const Grid<float>& g, const float* U, const float* V,
+                                    const float* W, double* partials, int blocks, cudaStream_t st);
+bool fused_supported(const mr_config& cfg, std::string* why);
+
+}  // namespace mr

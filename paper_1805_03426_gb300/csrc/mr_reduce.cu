@@ -1,0 +1,212 @@
+// FP64 reductions (Section 4.1 plate Nusselt numbers, volume moments, the
+// divergence check of Section 3.2, the CFL limit) and dtype conversion.
+// Each block reduces with warp shuffles into one FP64 partial; the host sums
+// the partials in block order, so every result is deterministic.
+#include <math.h>
+
+#include "mr_internal.cuh"
+
+namespace mr {
+namespace {
+
+constexpr int kRedThreads = 256;
+
+__device__ __forceinline__ double warp_sum(double v)
+{
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    return v;
+}
+__device__ __forceinline__ double warp_max(double v)
+{
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_down_sync(0xffffffffu, v, o));
+    return v;
+}
+
+// Block reduction of NV values per thread (sum or max); thread 0 writes them.
+template <int NV, bool MAX>
+__device__ void block_reduce_store(double (&v)[NV], double* out)
+{
+    __shared__ double sh[NV][kRedThreads / 32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    for (int q = 0; q < NV; ++q) {
+        double r = MAX ? warp_max(v[q]) : warp_sum(v[q]);
+        if (lane == 0) sh[q][wid] = r;
+    }
+    __syncthreads();
+    if (wid == 0) {
+        for (int q = 0; q < NV; ++q) {
+            double r = (lane < kRedThreads / 32) ? sh[q][lane] : (MAX ? 0.0 : 0.0);
+            r = MAX ? warp_max(r) : warp_sum(r);
+            if (lane == 0) out[q] = r;
+        }
+    }
+}
+
+// pass 0: (sum T vol, count of non-finite T); pass 1: sum (T - mean)^2 vol.
+// vol is dx dy dz_k; the dx dy factor is applied on the host.
+template <typename P>
+__global__ void __launch_bounds__(kRedThreads) k_moments(Grid<P> g, const P* __restrict__ T, double mean,
+                                                         int pass, double* __restrict__ partials)
+{
+    const size_t plane = (size_t)g.Nx * g.Ny;
+    const size_t n = plane * g.Nz;
+    double v[2] = {0.0, 0.0};
+    for (size_t m = (size_t)blockIdx.x * blockDim.x + threadIdx.x; m < n; m += (size_t)gridDim.x * blockDim.x) {
+        const int k = (int)(m / plane);
+        const double t = (double)T[m];
+        const double dzk = (double)g.dz[k];
+        if (pass == 0) {
+            if (isfinite(t)) v[0] += t * dzk;
+            else v[1] += 1.0;
+        } else {
+            const double d = t - mean;
+            v[0] += d * d * dzk;
+        }
+    }
+    block_reduce_store<2, false>(v, partials + 2 * blockIdx.x);
+}
+
+// Plate Nusselt numbers: one block sums both plates in a fixed order.
+template <typename P>
+__global__ void __launch_bounds__(1024) k_plate_nu(Grid<P> g, const P* __restrict__ T, double zb, double zt,
+                                                   double* __restrict__ out2)
+{
+    const size_t plane = (size_t)g.Nx * g.Ny;
+    const P* top = T + (size_t)(g.Nz - 1) * plane;
+    double sb = 0.0, st = 0.0;
+    for (size_t m = threadIdx.x; m < plane; m += blockDim.x) {
+        sb += (0.5 - (double)T[m]) / zb;
+        st += ((double)top[m] + 0.5) / zt;
+    }
+    __shared__ double sh[2][32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    sb = warp_sum(sb);
+    st = warp_sum(st);
+    if (lane == 0) { sh[0][wid] = sb; sh[1][wid] = st; }
+    __syncthreads();
+    if (wid == 0) {
+        const int nw = blockDim.x >> 5;
+        double b = lane < nw ? sh[0][lane] : 0.0, t = lane < nw ? sh[1][lane] : 0.0;
+        b = warp_sum(b);
+        t = warp_sum(t);
+        if (lane == 0) { out2[0] = b / (double)plane; out2[1] = t / (double)plane; }
+    }
+}
+
+// Max |divergence| of the dense refined faces (outward flux sum / volume).
+template <typename P>
+__global__ void __launch_bounds__(kRedThreads) k_maxdiv(Grid<P> g, const P* __restrict__ Us,
+                                                        const P* __restrict__ Vs, const P* __restrict__ Ws,
+                                                        double* __restrict__ partials)
+{
+    const size_t plane = (size_t)g.Nx * g.Ny;
+    const size_t n = plane * g.Nz;
+    double v[1] = {0.0};
+    for (size_t m = (size_t)blockIdx.x * blockDim.x + threadIdx.x; m < n; m += (size_t)gridDim.x * blockDim.x) {
+        const int i = (int)(m % g.Nx), j = (int)((m / g.Nx) % g.Ny), k = (int)(m / plane);
+        const int fe = g.walls ? i + 1 : (i + 1 == g.Nx ? 0 : i + 1);
+        const int fn = g.walls ? j + 1 : (j + 1 == g.Ny ? 0 : j + 1);
+        const size_t ur = ((size_t)k * g.Ny + j) * g.ufx;
+        const double d = ((double)Us[ur + fe] - (double)Us[ur + i]) * (double)g.inv_dx
+                       + ((double)Vs[((size_t)k * g.vfy + fn) * g.Nx + i] - (double)Vs[((size_t)k * g.vfy + j) * g.Nx + i]) * (double)g.inv_dy
+                       + ((double)Ws[m + plane] - (double)Ws[m]) * (double)g.inv_dz[k];
+        v[0] = fmax(v[0], fabs(d));
+    }
+    block_reduce_store<1, true>(v, partials + blockIdx.x);
+}
+
+// CFL rate max(|u|)/dx + max(|v|)/dy + max(|w|)/dz over the cell's faces.
+template <typename P>
+__global__ void __launch_bounds__(kRedThreads) k_cfl(Grid<P> g, const P* __restrict__ Us,
+                                                     const P* __restrict__ Vs, const P* __restrict__ Ws,
+                                                     double* __restrict__ partials)
+{
+    const size_t plane = (size_t)g.Nx * g.Ny;
+    const size_t n = plane * g.Nz;
+    double v[1] = {0.0};
+    for (size_t m = (size_t)blockIdx.x * blockDim.x + threadIdx.x; m < n; m += (size_t)gridDim.x * blockDim.x) {
+        const int i = (int)(m % g.Nx), j = (int)((m / g.Nx) % g.Ny), k = (int)(m / plane);
+        const int fe = g.walls ? i + 1 : (i + 1 == g.Nx ? 0 : i + 1);
+        const int fn = g.walls ? j + 1 : (j + 1 == g.Ny ? 0 : j + 1);
+        const size_t ur = ((size_t)k * g.Ny + j) * g.ufx;
+        const double u = fmax(fabs((double)Us[ur + i]), fabs((double)Us[ur + fe]));
+        const double vv = fmax(fabs((double)Vs[((size_t)k * g.vfy + j) * g.Nx + i]),
+                               fabs((double)Vs[((size_t)k * g.vfy + fn) * g.Nx + i]));
+        const double w = fmax(fabs((double)Ws[m]), fabs((double)Ws[m + plane]));
+        const double r = u / (double)g.dx + vv / (double)g.dy + w / (double)g.dz[k];
+        v[0] = fmax(v[0], r);
+    }
+    block_reduce_store<1, true>(v, partials + blockIdx.x);
+}
+
+template <typename S, typename D>
+__global__ void k_convert(const S* __restrict__ src, D* __restrict__ dst, size_t n)
+{
+    for (size_t m = (size_t)blockIdx.x * blockDim.x + threadIdx.x; m < n; m += (size_t)gridDim.x * blockDim.x)
+        dst[m] = (D)src[m];
+}
+
+}  // namespace
+
+template <typename P>
+cudaError_t launch_moments(const Grid<P>& g, const P* T, double mean, int pass, double* partials, int blocks,
+                           cudaStream_t st)
+{
+    k_moments<P><<<blocks, kRedThreads, 0, st>>>(g, T, mean, pass, partials);
+    return cudaGetLastError();
+}
+
+template <typename P>
+cudaError_t launch_plate_nu(const Grid<P>& g, const P* T, const double* zb_zt, double* out2, cudaStream_t st)
+{
+    k_plate_nu<P><<<1, 1024, 0, st>>>(g, T, zb_zt[0], zb_zt[1], out2);
+    return cudaGetLastError();
+}
+
+template <typename P>
+cudaError_t launch_maxdiv(const Grid<P>& g, const P* Us, const P* Vs, const P* Ws, double* partials, int blocks,
+                          cudaStream_t st)
+{
+    k_maxdiv<P><<<blocks, kRedThreads, 0, st>>>(g, Us, Vs, Ws, partials);
+    return cudaGetLastError();
+}
+
+template <typename P>
+cudaError_t launch_cfl(const Grid<P>& g, const P* Us, const P* Vs, const P* Ws, double* partials, int blocks,
+                       cudaStream_t st)
+{
+    k_cfl<P><<<blocks, kRedThreads, 0, st>>>(g, Us, Vs, Ws, partials);
+    return cudaGetLastError();
+}
+
+// src/dst dtypes: MR_F64 or MR_F32.  P is unused (kept for a uniform launcher signature).
+template <typename P>
+cudaError_t launch_convert(const void* src, int sd, void* dst, int dd, size_t n, cudaStream_t st)
+{
+    if (n == 0) return cudaSuccess;
+    const int threads = 256;
+    size_t want = (n + threads - 1) / threads;
+    const unsigned blocks = (unsigned)(want < 152 * 16 ? want : 152 * 16);
+    if (sd == MR_F64 && dd == MR_F32)
+        k_convert<double, float><<<blocks, threads, 0, st>>>((const double*)src, (float*)dst, n);
+    else if (sd == MR_F32 && dd == MR_F64)
+        k_convert<float, double><<<blocks, threads, 0, st>>>((const float*)src, (double*)dst, n);
+    else if (sd == MR_F64 && dd == MR_F64)
+        return cudaMemcpyAsync(dst, src, n * 8, cudaMemcpyDeviceToDevice, st);
+    else
+        return cudaMemcpyAsync(dst, src, n * 4, cudaMemcpyDeviceToDevice, st);
+    return cudaGetLastError();
+}
+
+#define MR_INST(P)                                                                                           \
+    template cudaError_t launch_moments<P>(const Grid<P>&, const P*, double, int, double*, int, cudaStream_t); \
+    template cudaError_t launch_plate_nu<P>(const Grid<P>&, const P*, const double*, double*, cudaStream_t);    \
+    template cudaError_t launch_maxdiv<P>(const Grid<P>&, const P*, const P*, const P*, double*, int,          \
+                                          cudaStream_t);                                                     \
+    template cudaError_t launch_cfl<P>(const Grid<P>&, const P*, const P*, const P*, double*, int, cudaStream_t);
+MR_INST(double)
+MR_INST(float)
+#undef MR_INST
+template cudaError_t launch_convert<double>(const void*, int, void*, int, size_t, cudaStream_t);
+
+}  // namespace mr

@@ -1,0 +1,155 @@
+// Scalar time step with the dense velocity read from HBM (MR_VEL_STORED),
+// FP64 or FP32.  Eq. (5) in flux form, second-order (linear) face values,
+// Euler-leapfrog with the averaging step (Section 2.2):
+//   T^{s+1} = a T^{s-1} + b T^s + gdt [C(T^s) + D(T^{s-1})]
+// C = -(1/Vol) sum_faces u_f T_f A_f (outward), D = (1/Vol) sum kappa A dT/dn.
+// Per-layer coefficients (1/dz, interpolation weights, kappa/(dz d)) come
+// from the handle's grid, so a stretched z costs no extra arithmetic.
+#include "mr_internal.cuh"
+
+namespace mr {
+namespace {
+
+constexpr double kTBottom = 0.5;
+constexpr double kTTop = -0.5;
+
+// One thread per dense cell.  IMPLZ: vertical diffusion enters as
+// (D_z(T^{s-1}) + plate terms) / 2; the implicit half follows in k_zsolve.
+template <typename P, bool IMPLZ>
+__global__ void __launch_bounds__(256) k_step_stored(Grid<P> g, const P* __restrict__ Us,
+                                                     const P* __restrict__ Vs, const P* __restrict__ Ws,
+                                                     const P* __restrict__ Tm1, const P* __restrict__ T,
+                                                     P* __restrict__ Tp1, P a, P b, P gdt)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y * blockDim.y + threadIdx.y;
+    const int k = blockIdx.z;
+    if (i >= g.Nx || j >= g.Ny) return;
+    const size_t plane = (size_t)g.Nx * g.Ny;
+    const size_t m = (size_t)k * plane + (size_t)j * g.Nx + i;
+    const P Tc = T[m], Dc = Tm1[m];
+    const P half = P(0.5);
+    P cx = 0, dx_ = 0, cy = 0, dy_ = 0;
+    // x faces
+    const size_t urow = ((size_t)k * g.Ny + j) * g.ufx;
+    if (!(g.walls && i == 0)) {
+        const int iw = (i == 0) ? g.Nx - 1 : i - 1;
+        const size_t mw = m - i + iw;
+        cx += Us[urow + i] * half * (T[mw] + Tc);
+        dx_ -= Dc - Tm1[mw];
+    }
+    if (!(g.walls && i == g.Nx - 1)) {
+        const int ie = (i == g.Nx - 1) ? 0 : i + 1;
+        const int fe = g.walls ? i + 1 : ie;
+        const size_t me = m - i + ie;
+        cx -= Us[urow + fe] * half * (Tc + T[me]);
+        dx_ += Tm1[me] - Dc;
+    }
+    // y faces
+    if (!(g.walls && j == 0)) {
+        const int js = (j == 0) ? g.Ny - 1 : j - 1;
+        const size_t ms = m + ((ptrdiff_t)js - j) * g.Nx;
+        cy += Vs[((size_t)k * g.vfy + j) * g.Nx + i] * half * (T[ms] + Tc);
+        dy_ -= Dc - Tm1[ms];
+    }
+    if (!(g.walls && j == g.Ny - 1)) {
+        const int jn = (j == g.Ny - 1) ? 0 : j + 1;
+        const int fn = g.walls ? j + 1 : jn;
+        const size_t mn = m + ((ptrdiff_t)jn - j) * g.Nx;
+        cy -= Vs[((size_t)k * g.vfy + fn) * g.Nx + i] * half * (Tc + T[mn]);
+        dy_ += Tm1[mn] - Dc;
+    }
+    // z faces (plates: no advective flux; Dirichlet or zero diffusive flux)
+    P cz = 0, dz_ = 0;
+    if (k > 0) {
+        const P Tb = T[m - plane];
+        cz += Ws[m] * (g.wlo[k] * Tb + g.whi[k] * Tc);
+        dz_ -= g.cdn[k] * (Dc - Tm1[m - plane]);
+    } else {
+        dz_ -= g.cdn[0] * (Dc - P(kTBottom));    // cdn[0] = 0 when adiabatic
+    }
+    if (k < g.Nz - 1) {
+        const P Tt = T[m + plane];
+        cz -= Ws[m + plane] * (g.wlo[k + 1] * Tc + g.whi[k + 1] * Tt);
+        dz_ += g.cup[k] * (Tm1[m + plane] - Dc);
+    } else {
+        dz_ += g.cup[k] * (P(kTTop) - Dc);        // cup[Nz-1] = 0 when adiabatic
+    }
+    if (IMPLZ) {
+        // (Lz T^{s-1} + bz)/2 + bz/2: the plate terms count in full
+        P bz = 0;
+        if (k == 0) bz += g.cdn[0] * P(kTBottom);
+        if (k == g.Nz - 1) bz += g.cup[k] * P(kTTop);
+        dz_ = half * dz_ + half * bz;
+    }
+    const P C = cx * g.inv_dx + cy * g.inv_dy + cz * g.inv_dz[k];
+    const P D = g.kx2 * dx_ + g.ky2 * dy_ + dz_;
+    Tp1[m] = a * Dc + b * Tc + gdt * (C + D);
+}
+
+// Opt-in implicit vertical diffusion: per (x, y) column solve
+//   (1 + h (cup + cdn)) x_k - h cdn_k x_{k-1} - h cup_k x_{k+1} = r_k,
+// h = gdt / 2, by the Thomas algorithm; work holds the eliminated
+// super-diagonal (one value per cell).
+template <typename P>
+__global__ void k_zsolve(Grid<P> g, P* __restrict__ X, P h, P* __restrict__ work)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y;
+    if (i >= g.Nx) return;
+    const size_t plane = (size_t)g.Nx * g.Ny;
+    const size_t base = (size_t)j * g.Nx + i;
+    const int N = g.Nz;
+    P prev_c = 0, prev_x = 0;
+    for (int k = 0; k < N; ++k) {
+        const P lo = (k > 0) ? -h * g.cdn[k] : P(0);
+        const P up = (k < N - 1) ? -h * g.cup[k] : P(0);
+        const P di = P(1) + h * (g.cup[k] + g.cdn[k]);
+        const P den = di - lo * prev_c;
+        const P c = up / den;
+        const P x = (X[base + k * plane] - lo * prev_x) / den;
+        work[base + k * plane] = c;
+        X[base + k * plane] = x;
+        prev_c = c;
+        prev_x = x;
+    }
+    for (int k = N - 2; k >= 0; --k) {
+        prev_x = X[base + k * plane] - work[base + k * plane] * prev_x;
+        X[base + k * plane] = prev_x;
+    }
+}
+
+}  // namespace
+
+template <typename P>
+cudaError_t launch_step_stored(const Grid<P>& g, const P* Us, const P* Vs, const P* Ws, const P* Tm1,
+                               const P* T, P* Tp1, StepCoef c, bool implz, cudaStream_t st)
+{
+    dim3 blk(64, 4);
+    dim3 grd((g.Nx + blk.x - 1) / blk.x, (g.Ny + blk.y - 1) / blk.y, g.Nz);
+    if (implz)
+        k_step_stored<P, true><<<grd, blk, 0, st>>>(g, Us, Vs, Ws, Tm1, T, Tp1, (P)c.a, (P)c.b, (P)c.gdt);
+    else
+        k_step_stored<P, false><<<grd, blk, 0, st>>>(g, Us, Vs, Ws, Tm1, T, Tp1, (P)c.a, (P)c.b, (P)c.gdt);
+    return cudaGetLastError();
+}
+
+template <typename P>
+cudaError_t launch_zsolve(const Grid<P>& g, P* Tp1, double half_gdt, P* work, cudaStream_t st)
+{
+    dim3 blk(128);
+    dim3 grd((g.Nx + 127) / 128, g.Ny);
+    k_zsolve<P><<<grd, blk, 0, st>>>(g, Tp1, (P)half_gdt, work);
+    return cudaGetLastError();
+}
+
+template cudaError_t launch_step_stored<double>(const Grid<double>&, const double*, const double*,
+                                                const double*, const double*, const double*, double*,
+                                                StepCoef, bool, cudaStream_t);
+template cudaError_t launch_step_stored<float>(const Grid<float>&, const float*, const float*, const float*,
+                                               const float*, const float*, float*, StepCoef, bool,
+                                               cudaStream_t);
+template cudaError_t launch_zsolve<double>(const Grid<double>&, double*, double, double*, cudaStream_t);
+template cudaError_t launch_zsolve<float>(const Grid<float>&, float*, double, float*, cudaStream_t);
+
+}  // namespace mr

@@ -1,0 +1,285 @@
+"""ctypes binding of libmr.so (include/mr.h): same names, argument marshalling only.
+
+Every computation runs in the CUDA library; this module checks shapes and
+dtypes, extracts raw pointers from torch tensors (device) or numpy arrays
+(host) and raises ``MRError`` on a non-zero return code.  There is no CPU
+fallback: if ``libmr.so`` is missing, importing the binding fails loudly.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libmr.so")
+
+MR_OK, MR_ERR_ARG, MR_ERR_CUDA, MR_ERR_NONFINITE, MR_ERR_TIMEOUT, MR_ERR_OOM, MR_ERR_STATE = 0, -1, -2, -3, -4, -5, -6
+MR_F64, MR_F32 = 0, 1
+MR_VEL_STORED, MR_VEL_FUSED = 0, 1
+MR_DIRICHLET, MR_ADIABATIC = 0, 1
+MR_PERIODIC, MR_WALLS = 0, 1
+
+
+class MRError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"[{code}] {msg}")
+        self.code = code
+
+
+class mr_config(ctypes.Structure):
+    _fields_ = [
+        ("struct_size", ctypes.c_uint32),
+        ("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("nz", ctypes.c_int32),
+        ("mx", ctypes.c_int32), ("my", ctypes.c_int32), ("mz", ctypes.c_int32),
+        ("lx", ctypes.c_double), ("ly", ctypes.c_double),
+        ("stretch_gamma", ctypes.c_double),
+        ("ra", ctypes.c_double), ("pr_or_sc", ctypes.c_double), ("dt", ctypes.c_double),
+        ("precision", ctypes.c_int32), ("velocity_mode", ctypes.c_int32),
+        ("np_average", ctypes.c_int32), ("bc_plates", ctypes.c_int32),
+        ("bc_horizontal", ctypes.c_int32), ("diffz_implicit", ctypes.c_int32),
+    ]
+
+
+class mr_stats(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_double) for n in ("nu_bot", "nu_top", "mean", "var", "integral", "max_div")]
+
+    def as_dict(self):
+        return {n: getattr(self, n) for n, _ in self._fields_}
+
+
+_lib = None
+_VP, _I32, _I64, _D = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_double
+_SIGS = {
+    "mr_config_default": (ctypes.c_int, [ctypes.POINTER(mr_config)]),
+    "mr_create": (ctypes.c_int, [ctypes.POINTER(mr_config), ctypes.POINTER(_VP)]),
+    "mr_destroy": (None, [_VP]),
+    "mr_last_error": (ctypes.c_char_p, []),
+    "mr_grid": (ctypes.c_int, [_VP, _VP, _VP]),
+    "mr_refine_velocity": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP]),
+    "mr_set_scalar": (ctypes.c_int, [_VP, _VP, _I32, _VP]),
+    "mr_get_scalar": (ctypes.c_int, [_VP, _VP, _VP, _I32, _VP]),
+    "mr_scalar_step": (ctypes.c_int, [_VP, _I64, _VP]),
+    "mr_step_index": (ctypes.c_int, [_VP, ctypes.POINTER(_I64)]),
+    "mr_scalar_stats": (ctypes.c_int, [_VP, ctypes.POINTER(mr_stats), _VP]),
+    "mr_plate_nu": (ctypes.c_int, [_VP, _VP, _VP]),
+    "mr_cfl_dt": (ctypes.c_int, [_VP, _D, ctypes.POINTER(_D), _VP]),
+    "mr_set_dt": (ctypes.c_int, [_VP, _D]),
+    "mr_debug_index_maps": (ctypes.c_int, [_VP, _VP, ctypes.c_size_t]),
+}
+
+
+def lib():
+    """Load libmr.so (built by ``paper_1805_03426_gb300.build``); raise if absent."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"libmr.so not built ({LIB_PATH}); run __graft_entry__.build()")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in _SIGS.items():
+            f = getattr(L, name)
+            f.restype, f.argtypes = res, args
+        _lib = L
+    return _lib
+
+
+def _check(rc):
+    if rc != MR_OK:
+        raise MRError(rc, lib().mr_last_error().decode())
+
+
+def _ptr(a, n=None, dtype=None, what="array"):
+    """Raw pointer of a contiguous torch tensor or numpy array (None -> NULL)."""
+    if a is None:
+        return None
+    try:
+        import torch
+        is_t = isinstance(a, torch.Tensor)
+    except ImportError:  # pragma: no cover
+        is_t = False
+    if is_t:
+        if not a.is_contiguous():
+            raise ValueError(f"{what}: tensor must be contiguous")
+        size, dt = a.numel(), {a.dtype}
+        ok = {np.float64: "torch.float64", np.float32: "torch.float32"}
+        if dtype is not None and str(a.dtype) != ok[dtype]:
+            raise TypeError(f"{what}: expected {ok[dtype]}, got {a.dtype}")
+        p = a.data_ptr()
+    else:
+        if not isinstance(a, np.ndarray) or not a.flags["C_CONTIGUOUS"]:
+            raise ValueError(f"{what}: numpy array must be C-contiguous")
+        if dtype is not None and a.dtype != dtype:
+            raise TypeError(f"{what}: expected {np.dtype(dtype)}, got {a.dtype}")
+        size, dt = a.size, None
+        p = a.ctypes.data
+    del dt
+    if n is not None and size != n:
+        raise ValueError(f"{what}: {size} elements, expected {n}")
+    return p
+
+
+def _stream(stream):
+    if stream is not None:
+        return stream if isinstance(stream, int) else stream.cuda_stream
+    try:
+        import torch
+        if torch.cuda.is_available():
+            return torch.cuda.current_stream().cuda_stream
+    except ImportError:  # pragma: no cover
+        pass
+    return None
+
+
+def mr_config_default(**overrides) -> mr_config:
+    c = mr_config()
+    _check(lib().mr_config_default(ctypes.byref(c)))
+    for k, v in overrides.items():
+        if not hasattr(c, k):
+            raise AttributeError(k)
+        setattr(c, k, v)
+    return c
+
+
+class Handle:
+    """Owns an mr_handle; also records the sizes the binding checks against."""
+
+    def __init__(self, cfg: mr_config):
+        self.cfg = cfg
+        h = _VP()
+        _check(lib().mr_create(ctypes.byref(cfg), ctypes.byref(h)))
+        self._h = h
+        w = 1 if cfg.bc_horizontal == MR_WALLS else 0
+        self.dense = (cfg.nx * cfg.mx, cfg.ny * cfg.my, cfg.nz * cfg.mz)
+        Nx, Ny, Nz = self.dense
+        self.shapes = {
+            "U": (cfg.nz, cfg.ny, cfg.nx + w), "V": (cfg.nz, cfg.ny + w, cfg.nx),
+            "W": (cfg.nz + 1, cfg.ny, cfg.nx),
+            "Us": (Nz, Ny, Nx + w), "Vs": (Nz, Ny + w, Nx), "Ws": (Nz + 1, Ny, Nx),
+            "T": (Nz, Ny, Nx),
+        }
+        self.np_dtype = np.float64 if cfg.precision == MR_F64 else np.float32
+
+    @property
+    def ptr(self):
+        if self._h is None:
+            raise MRError(MR_ERR_STATE, "handle destroyed")
+        return self._h
+
+    def close(self):
+        if getattr(self, "_h", None) is not None:
+            lib().mr_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _n(shape):
+    return int(np.prod(shape))
+
+
+def mr_create(cfg: mr_config) -> Handle:
+    return Handle(cfg)
+
+
+def mr_destroy(h: Handle) -> None:
+    h.close()
+
+
+def mr_last_error() -> str:
+    return lib().mr_last_error().decode()
+
+
+def mr_grid(h: Handle):
+    dims = np.zeros(3, dtype=np.int32)
+    zf = np.zeros(h.dense[2] + 1)
+    _check(lib().mr_grid(h.ptr, dims.ctypes.data, zf.ctypes.data))
+    return tuple(int(d) for d in dims), zf
+
+
+def mr_refine_velocity(h: Handle, U, V, W, Us=None, Vs=None, Ws=None, stream=None):
+    s = h.shapes
+    pu = _ptr(U, _n(s["U"]), np.float64, "U")
+    pv = _ptr(V, _n(s["V"]), np.float64, "V")
+    pw = _ptr(W, _n(s["W"]), np.float64, "W")
+    qu = _ptr(Us, _n(s["Us"]), h.np_dtype, "Us")
+    qv = _ptr(Vs, _n(s["Vs"]), h.np_dtype, "Vs")
+    qw = _ptr(Ws, _n(s["Ws"]), h.np_dtype, "Ws")
+    _check(lib().mr_refine_velocity(h.ptr, pu, pv, pw, qu, qv, qw, _stream(stream)))
+
+
+def _dtype_code(a):
+    try:
+        import torch
+        if isinstance(a, torch.Tensor):
+            return {torch.float64: MR_F64, torch.float32: MR_F32}[a.dtype]
+    except ImportError:  # pragma: no cover
+        pass
+    return {np.dtype(np.float64): MR_F64, np.dtype(np.float32): MR_F32}[a.dtype]
+
+
+def mr_set_scalar(h: Handle, T0, stream=None):
+    _check(lib().mr_set_scalar(h.ptr, _ptr(T0, _n(h.shapes["T"]), None, "T0"), _dtype_code(T0), _stream(stream)))
+
+
+def mr_get_scalar(h: Handle, T, Tprev=None, stream=None):
+    code = _dtype_code(T)
+    if Tprev is not None and _dtype_code(Tprev) != code:
+        raise TypeError("T and Tprev must share a dtype")
+    n = _n(h.shapes["T"])
+    _check(lib().mr_get_scalar(h.ptr, _ptr(T, n, None, "T"), _ptr(Tprev, n, None, "Tprev"), code, _stream(stream)))
+
+
+def mr_scalar_step(h: Handle, nsteps: int, stream=None):
+    _check(lib().mr_scalar_step(h.ptr, int(nsteps), _stream(stream)))
+
+
+def mr_step_index(h: Handle) -> int:
+    s = _I64()
+    _check(lib().mr_step_index(h.ptr, ctypes.byref(s)))
+    return s.value
+
+
+def mr_scalar_stats(h: Handle, stream=None, allow_nonfinite=False) -> dict:
+    out = mr_stats()
+    rc = lib().mr_scalar_stats(h.ptr, ctypes.byref(out), _stream(stream))
+    if rc == MR_ERR_NONFINITE and allow_nonfinite:
+        d = out.as_dict()
+        d["nonfinite"] = True
+        return d
+    _check(rc)
+    return out.as_dict()
+
+
+def mr_plate_nu(h: Handle, out=None, stream=None):
+    """Plate Nusselt numbers; with ``out`` (2 doubles, device or host) asynchronous."""
+    if out is None:
+        buf = np.zeros(2)
+        _check(lib().mr_plate_nu(h.ptr, buf.ctypes.data, _stream(stream)))
+        return float(buf[0]), float(buf[1])
+    _check(lib().mr_plate_nu(h.ptr, _ptr(out, 2, np.float64, "nu2"), _stream(stream)))
+    return out
+
+
+def mr_cfl_dt(h: Handle, cfl: float, stream=None) -> float:
+    dt = _D()
+    _check(lib().mr_cfl_dt(h.ptr, float(cfl), ctypes.byref(dt), _stream(stream)))
+    return dt.value
+
+
+def mr_set_dt(h: Handle, dt: float):
+    _check(lib().mr_set_dt(h.ptr, float(dt)))
+    h.cfg.dt = dt
+
+
+def mr_debug_index_maps(h: Handle) -> np.ndarray:
+    c = h.cfg
+    Nx, Ny, Nz = h.dense
+    n = Nx + Ny + Nz + 3 * (c.nx + c.ny + c.nz)
+    out = np.zeros(n, dtype=np.int32)
+    _check(lib().mr_debug_index_maps(h.ptr, out.ctypes.data, n))
+    return out
