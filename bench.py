@@ -188,7 +188,7 @@ def run_mr(args):
     achieved = bytes_per_cell * cells / per_launch / 1e9
     roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
             "frac": round(achieved / peak, 4), "traffic": None, "peak_source": peak_kind,
-            "kernel": "k_step_fused_f32" if mode == mr.MR_VEL_FUSED else "k_step_stored",
+            "kernel": "k_fused" if mode == mr.MR_VEL_FUSED else "k_step_stored",
             "bytes_per_cell": round(bytes_per_cell, 3), "launch_ms": round(per_launch * 1e3, 4)}
 
     # FP64 path on the same grid (stored velocity), for the FP32/FP64 ratio
@@ -310,7 +310,7 @@ def main():
     ap.add_argument("--impl", default="mr", choices=["mr", "reference"])
     ap.add_argument("--workload", default="rb512_stretched_f32", choices=sorted(WORKLOADS))
     ap.add_argument("--precision", default="f32", choices=["f32", "f64"])
-    ap.add_argument("--mode", default="stored", choices=["stored", "fused"])
+    ap.add_argument("--mode", default="fused", choices=["stored", "fused"])
     ap.add_argument("--cpu-budget", type=float, default=20.0)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")

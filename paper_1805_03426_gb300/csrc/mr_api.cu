@@ -514,6 +514,8 @@ int mr_get_scalar(mr_handle h, void* T, void* Tprev, int32_t dtype, mr_stream st
     if (!h->have_scalar) return set_error(MR_ERR_STATE, "mr_get_scalar: no scalar set");
     cudaStream_t st = (cudaStream_t)stream;
     int rc;
+    if (h->cfg.velocity_mode == MR_VEL_FUSED && fused_take_error(st) == MR_ERR_TIMEOUT)
+        return set_error(MR_ERR_TIMEOUT, "mr_get_scalar: a fused step kernel gave up a bounded wait");
     if (T && (rc = copy_out(h, h->buf.T[h->ic], h->cfg.precision, T, dtype, h->ncell, st))) return rc;
     if (Tprev && (rc = copy_out(h, h->buf.T[h->ip], h->cfg.precision, Tprev, dtype, h->ncell, st))) return rc;
     return MR_OK;
@@ -607,6 +609,8 @@ int mr_scalar_stats(mr_handle h, mr_stats* out, mr_stream stream)
     if (!h || !out) return set_error(MR_ERR_ARG, "mr_scalar_stats: NULL argument");
     if (!h->have_scalar) return set_error(MR_ERR_STATE, "mr_scalar_stats: no scalar set");
     cudaStream_t st = (cudaStream_t)stream;
+    if (h->cfg.velocity_mode == MR_VEL_FUSED && fused_take_error(st) == MR_ERR_TIMEOUT)
+        return set_error(MR_ERR_TIMEOUT, "mr_scalar_stats: a fused step kernel gave up a bounded wait");
     const void* T = h->buf.T[h->ic];
     const double dxdy = (h->cfg.lx / h->Nx) * (h->cfg.ly / h->Ny);
     double vtot = 0.0;

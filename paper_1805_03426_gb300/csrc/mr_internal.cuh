@@ -123,5 +123,6 @@ cudaError_t launch_step_fused_f32(const Grid<float>& g, const float* U, const fl
 cudaError_t launch_maxdiv_fused_f32(const Grid<float>& g, const float* U, const float* V,
                                     const float* W, double* partials, int blocks, cudaStream_t st);
 bool fused_supported(const mr_config& cfg, std::string* why);
+int fused_take_error(cudaStream_t st);   // MR_ERR_TIMEOUT if a fused kernel gave up a wait
 
 }  // namespace mr

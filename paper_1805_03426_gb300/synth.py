@@ -6,7 +6,7 @@ feed the CUDA library and the FP64 oracle.
 
 Velocity recipe.  A vector potential A is a random sum of Fourier modes with
 a shell spectrum chosen so that u = curl A has kinetic energy E(k) ~ k^-5/3
-for 1 <= |k| <= kmax (kmax = nx/4 by default).  Each component of A is
+for 1/2 <= |k| <= kmax (|k| in units of 2 pi / L; kmax = max(2, nx/4)).  Each component of A is
 multiplied by a weight that vanishes on the walls that component's circulation
 touches (z^2 (1-z)^2 for the horizontal components; with side walls also the
 x- and y- counterparts), so the wall-normal velocity is exactly zero there.
@@ -82,13 +82,15 @@ def coarse_velocity(seed, Xf, Yf, Zf, lx=1.0, ly=1.0, rms=0.2, walls=False, kmax
     nx, ny, nz = len(Xf) - 1, len(Yf) - 1, len(Zf) - 1
     periodic = not walls
     if kmax is None:
-        kmax = max(1, nx // 4)
+        kmax = max(2, nx // 4)
     rng = np.random.default_rng(seed)
     kl = list(range(0, kmax + 1))
     kx_, ky_ = _wavenumbers(kl, periodic), _wavenumbers(kl, periodic)
     kz_ = _wavenumbers(kl, False)
     kmag = np.sqrt(kz_[:, None, None] ** 2 + ky_[None, :, None] ** 2 + kx_[None, None, :] ** 2)
-    amp = np.where((kmag >= 1.0) & (kmag <= kmax), np.maximum(kmag, 1.0) ** (-17.0 / 6.0), 0.0)
+    # shell 1/2 <= |k| <= kmax: the lowest mode along a wall-bounded axis
+    # (sin / cos of pi x / L) has wavenumber 1/2 in units of 2 pi / L
+    amp = np.where((kmag >= 0.5) & (kmag <= kmax), np.maximum(kmag, 0.5) ** (-17.0 / 6.0), 0.0)
 
     # edge positions: faces along the two transverse axes, cells along the edge
     xe = Xf if walls else Xf[:-1]          # x positions of faces (periodic: nx distinct)

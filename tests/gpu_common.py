@@ -18,6 +18,7 @@ class Problem:
         g = self.grid
         self.U, self.V, self.W = synth.coarse_velocity(seed, g["Xf"], g["Yf"], g["Zf"], lx, ly, rms=rms,
                                                        walls=bool(walls))
+        assert np.abs(self.U).max() > 0.01 * rms and np.abs(self.W).max() > 0.01 * rms, "trivial velocity"
         Nx, Ny, Nz = self.cfg.dense
         self.T0 = synth.initial_scalar(seed, g["zc"], Ny, Nx)
 

@@ -1,0 +1,107 @@
+"""GPU parity of the fused FP32 refine + step kernel (MR_VEL_FUSED) against
+the FP64 oracle and against the FP32 stored-velocity path.
+
+Bars (FP32 path): scalar within 1e-5 max-norm of the oracle, plate Nu within
+1e-4 relative; the fused and stored FP32 paths agree to a few FP32 ulps of the
+O(1) scalar; the divergence of the on-the-fly refined velocity is FP32
+round-off."""
+import numpy as np
+import pytest
+
+import oracle as O
+from tests.gpu_common import Problem
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+F32_T_TOL = 1e-5
+F32_NU_TOL = 1e-4
+
+
+@pytest.fixture(scope="module")
+def mr():
+    import paper_1805_03426_gb300.mr as m
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    m.lib()
+    return m
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+FUSED = {
+    # one 64x16 tile: both periodic edges patched in the same CTA
+    "m4_one_tile": dict(nx=16, ny=4, nz=6, mx=4, my=4, mz=4, gamma=1.5, np_average=5),
+    # 2 x 2 tiles, several z chunks
+    "m4_2x2": dict(nx=32, ny=8, nz=7, mx=4, my=4, mz=4, gamma=1.5, np_average=4),
+    "m2_2x2": dict(nx=64, ny=16, nz=9, mx=2, my=2, mz=2, gamma=1.5, np_average=6),
+    "m2_uniform": dict(nx=32, ny=8, nz=8, mx=2, my=2, mz=2, gamma=0.0, adiabatic=1),
+}
+
+
+@pytest.fixture(scope="module", params=sorted(FUSED))
+def prob(request):
+    return Problem(**FUSED[request.param], ra=1e6, pr=7.0, dt=2e-3)
+
+
+def _run(mr, p, mode, nsteps):
+    h = mr.mr_create(p.mr_config(mr, mr.MR_F32, mode))
+    mr.mr_refine_velocity(h, dev(p.U), dev(p.V), dev(p.W))
+    mr.mr_set_scalar(h, dev(p.T0))
+    mr.mr_scalar_step(h, nsteps)
+    T = torch.empty(p.T0.shape, dtype=torch.float64, device="cuda")
+    Tp = torch.empty_like(T)
+    mr.mr_get_scalar(h, T, Tp)
+    torch.cuda.synchronize()
+    return h, T.cpu().numpy(), Tp.cpu().numpy()
+
+
+def test_fused_matches_oracle_and_stored(mr, prob):
+    n = 17   # Euler start, leapfrog and averaging steps
+    hf, Tf, Tpf = _run(mr, prob, mr.MR_VEL_FUSED, n)
+    hs, Ts, _ = _run(mr, prob, mr.MR_VEL_STORED, n)
+    vel = O.refine(prob.cfg, prob.U, prob.V, prob.W)
+    Tp_ref, T_ref = O.run(prob.cfg, vel, prob.T0, n)
+    assert np.abs(Tf - T_ref).max() <= F32_T_TOL
+    assert np.abs(Tpf - Tp_ref).max() <= F32_T_TOL
+    assert np.abs(Tf - Ts).max() <= 2e-6
+    st = mr.mr_scalar_stats(hf)
+    ref = O.stats(prob.cfg, T_ref)
+    for k in ("nu_bot", "nu_top"):
+        assert abs(st[k] - ref[k]) <= F32_NU_TOL * abs(ref[k]), k
+    # divergence of the velocity refined inside the fused kernel: FP32 round-off
+    Nx, Ny, Nz = prob.cfg.dense
+    scale = np.abs(prob.U).max() * max(Nx, Ny) + np.abs(prob.W).max() / np.diff(prob.grid["zf"]).min()
+    assert 0.0 < st["max_div"] <= 2e-5 * scale
+
+
+def test_fused_cfl_and_dense_faces(mr, prob):
+    h = mr.mr_create(prob.mr_config(mr, mr.MR_F32, mr.MR_VEL_FUSED))
+    sh = h.shapes
+    out = [torch.empty(sh[k], dtype=torch.float32, device="cuda") for k in ("Us", "Vs", "Ws")]
+    mr.mr_refine_velocity(h, dev(prob.U), dev(prob.V), dev(prob.W), *out)
+    vel = O.refine(prob.cfg, prob.U, prob.V, prob.W)
+    for got, r in zip(out, vel):
+        assert np.abs(got.cpu().numpy() - r).max() <= F32_T_TOL * np.abs(r).max()
+    assert abs(mr.mr_cfl_dt(h, 0.3) / O.cfl_dt(prob.cfg, vel, 0.3) - 1) <= 1e-5
+
+
+def test_fused_full_size_precision_form(mr):
+    """512x512x384 dense (coarse 128x128x96, refinement 4), Sc=100, Ra=1e9:
+    three fused FP32 steps (Euler, leapfrog, averaging) against the oracle."""
+    p = Problem(128, 128, 96, mx=4, my=4, mz=4, gamma=1.5, ra=1e9, pr=100.0, rms=0.1, dt=2e-4, np_average=3)
+    h, T, _ = _run(mr, p, mr.MR_VEL_FUSED, 3)
+    vel = O.refine(p.cfg, p.U, p.V, p.W)
+    _, T_ref = O.run(p.cfg, vel, p.T0, 3)
+    assert np.abs(T - T_ref).max() <= F32_T_TOL
+
+
+def test_fused_rejects_unsupported_shapes(mr):
+    p = Problem(6, 5, 4, mx=2, my=2, mz=2)
+    with pytest.raises(mr.MRError) as e:
+        mr.mr_create(p.mr_config(mr, mr.MR_F32, mr.MR_VEL_FUSED))
+    assert e.value.code == mr.MR_ERR_ARG
+    with pytest.raises(mr.MRError):
+        mr.mr_create(Problem(32, 8, 4, mx=2, my=2, mz=2).mr_config(mr, mr.MR_F64, mr.MR_VEL_FUSED))

@@ -69,7 +69,7 @@ def test_refine_matches_oracle(mr, prob, precision):
     mr.mr_refine_velocity(h, dev(prob.U), dev(prob.V), dev(prob.W), *out)
     torch.cuda.synchronize()
     ref = O.refine(prob.cfg, prob.U, prob.V, prob.W)
-    tol = F64_TOL if precision == "f64" else 2e-6
+    tol = F64_TOL if precision == "f64" else F32_T_TOL   # FP32: ~3 recursion stages, O(100) u_32
     for got, r in zip(out, ref):
         assert rel_err(got.cpu().numpy(), r) <= tol
     # host pointers give the same faces (the library copies them in first)
