@@ -35,8 +35,8 @@ constexpr int kTX = 64, kTY = 16;
 constexpr int kBX = kTX + 8, kBY = kTY + 2;           // TMA box (floats)
 constexpr int kPlaneFloats = kBX * kBY;                // 1296
 constexpr int kSlotFloats = ((kPlaneFloats * 4 + 127) / 128) * 128 / 4;  // 128-byte aligned slot
-constexpr int kNB = 5;                                 // planes resident per field
-constexpr int kThreads = 256;
+constexpr int kThreads = 256;                          // consumer threads (8 warps)
+constexpr int kThreadsAll = kThreads + 32;             // + one producer warp
 constexpr uint32_t kPlaneBytes = kPlaneFloats * 4;
 constexpr long kWaitLimit = 1L << 26;                  // bounded mbarrier wait: iterations ...
 constexpr unsigned long long kWaitNs = 1000000000ull;  // ... and wall time (1 s)
@@ -48,25 +48,23 @@ struct Tile {
     static constexpr int UX = CX + 3, UY = CY + 2;     // U faces I0-1..I0+CX+1, rows J0-1..J0+CY
     static constexpr int VX = CX + 2, VY = CY + 3;     // V cells I0-1..I0+CX, faces J0-1..J0+CY+1
     static constexpr int WX = CX + 2, WY = CY + 2;     // W columns I0-1..I0+CX, J0-1..J0+CY
+    static constexpr int NB = (M == 4) ? 6 : 5;        // dense planes resident per field
     // shared-memory layout (floats), T ring first (128-byte aligned slots)
     static constexpr int oT = 0;
-    static constexpr int oCU = oT + kNB * 2 * kSlotFloats;
+    static constexpr int oCU = oT + NB * 2 * kSlotFloats;
     static constexpr int oCV = oCU + 2 * 3 * UY * UX;
     static constexpr int oCW = oCV + 2 * 3 * VY * VX;
     static constexpr int oUz = oCW + 2 * 2 * WY * WX;
     static constexpr int oVz = oUz + M * UY * UX;
     static constexpr int oWc = oVz + M * VY * VX;
     static constexpr int oWy = oWc + (M + 1) * WY * WX;
-    static constexpr int oWs = oWy + 2 * kTY * WX;
-    static constexpr int oUo = oWs + 2 * kTY * kTX;
-    static constexpr int oUs = oUo + kTY * UX;
-    static constexpr int oVr = oUs + kTY * (kTX + 1);
-    static constexpr int oVs = oVr + (kTY + 1) * VX;
-    static constexpr int oRx = oVs + (kTY + 1) * kTX;
-    static constexpr int oRy = oRx + kTX * 3;
-    static constexpr int oRed = oRy + kTY * 3;
-    static constexpr int oBar = ((oRed + 64) * 4 + 7) / 8;  // in uint64 units
-    static constexpr size_t bytes = (size_t)(oBar + kNB) * 8;
+    static constexpr int oUo = oWy + (M + 1) * kTY * WX;
+    static constexpr int oVr = oUo + M * kTY * UX;
+    static constexpr int oRy = oVr + M * (kTY + 1) * VX;
+    static constexpr int oLc = oRy + kTY * 3;          // [M][kLc] per-layer constants of the slab
+    static constexpr int oRed = oLc + M * 12;
+    static constexpr int oBar = ((oRed + 64) * 4 + 7) / 8;  // in uint64 units: full[NB], empty[NB]
+    static constexpr size_t bytes = (size_t)(oBar + 2 * NB) * 8;
 };
 
 __device__ __forceinline__ uint32_t sa(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -79,15 +77,37 @@ __device__ __forceinline__ void mbar_expect_tx(uint64_t* b, uint32_t bytes)
 {
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(sa(b)), "r"(bytes) : "memory");
 }
+__device__ __forceinline__ void mbar_arrive(uint64_t* b)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(sa(b)) : "memory");
+}
+// Barrier among the consumer warps only (the producer warp never joins).
+__device__ __forceinline__ void consumers_sync()
+{
+    asm volatile("barrier.cta.sync 1, %0;" ::"n"(kThreads) : "memory");
+}
+__device__ __forceinline__ bool consumers_sync_or(bool v)
+{
+    uint32_t r;
+    asm volatile(
+        "{\n\t.reg .pred p, q;\n\t"
+        "setp.ne.u32 q, %1, 0;\n\t"
+        "barrier.cta.red.or.pred p, 1, %2, q;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(r)
+        : "r"((uint32_t)v), "n"(kThreads)
+        : "memory");
+    return r != 0;
+}
 __device__ __forceinline__ bool mbar_test(uint64_t* b, uint32_t parity)
 {
     uint32_t ok;
     asm volatile(
         "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
         "selp.u32 %0, 1, 0, p;\n\t}"
         : "=r"(ok)
-        : "r"(sa(b)), "r"(parity)
+        : "r"(sa(b)), "r"(parity), "n"(20000)
         : "memory");
     return ok != 0;
 }
@@ -149,113 +169,148 @@ __device__ __forceinline__ void issue_plane(float* sT, uint64_t* bar, const CUte
 }
 
 template <int M, bool DIVONLY>
-__global__ void __launch_bounds__(kThreads, 2)
+__global__ void __launch_bounds__(kThreadsAll, 2)
 k_fused(const __grid_constant__ CUtensorMap tmn, const __grid_constant__ CUtensorMap tmm, const FusedArgs A)
 {
     using L = Tile<M>;
-    constexpr int CX = L::CX, CY = L::CY, UX = L::UX, UY = L::UY, VX = L::VX, VY = L::VY, WX = L::WX, WY = L::WY;
+    constexpr int UX = L::UX, UY = L::UY, VX = L::VX, VY = L::VY, WX = L::WX, WY = L::WY, NB = L::NB;
+    constexpr int NC = 4 / M;                  // coarse cells per 4-cell segment
+    constexpr int NW = kThreads / 32;          // consumer warps
     extern __shared__ __align__(128) float sm[];
     float* sT = sm + L::oT;
-    float* cu = sm + L::oCU;   // [2][3][UY][UX]
+    float* cu = sm + L::oCU;   // [2][3][UY][UX]  coarse U of the slab's z-window
     float* cv = sm + L::oCV;   // [2][3][VY][VX]
-    float* cw = sm + L::oCW;   // [2][2][WY][WX]
-    float* Uz = sm + L::oUz;   // [M][UY][UX]
+    float* cw = sm + L::oCW;   // [2][2][WY][WX]  coarse W below / above the slab
+    float* Uz = sm + L::oUz;   // [M][UY][UX]     z-split of U per dense layer (R_z)
     float* Vz = sm + L::oVz;   // [M][VY][VX]
-    float* Wc = sm + L::oWc;   // [M+1][WY][WX]
-    float* Wy = sm + L::oWy;   // [2][TY][WX]
-    float* Ws = sm + L::oWs;   // [2][TY][TX]
-    float* Uo = sm + L::oUo;   // [TY][UX]
-    float* Us = sm + L::oUs;   // [TY][TX+1]
-    float* Vr = sm + L::oVr;   // [TY+1][VX]
-    float* Vs = sm + L::oVs;   // [TY+1][TX]
-    float* sRx = sm + L::oRx;  // [TX][3]
+    float* Wc = sm + L::oWc;   // [M+1][WY][WX]   full-area W per dense plane of the slab
+    float* Wy = sm + L::oWy;   // [M+1][TY][WX]   y-split of Wc
+    float* Uo = sm + L::oUo;   // [M][TY][UX]     outer U sub-faces (R_y of Uz)
+    float* Vr = sm + L::oVr;   // [M][TY+1][VX]   full-coarse-width V of every dense row
     float* sRy = sm + L::oRy;  // [TY][3]
+    float* Lc = sm + L::oLc;   // [M][12] layer constants: dz, 1/dz, wlo_b, whi_b, wlo_t, whi_t, cdn, cup, dx/dz
     float* red = sm + L::oRed;
-    uint64_t* bar = reinterpret_cast<uint64_t*>(sm) + L::oBar;
+    uint64_t* full = reinterpret_cast<uint64_t*>(sm) + L::oBar;
+    uint64_t* empty = full + NB;
 
     const Grid<float>& g = A.g;
-    const int tid = threadIdx.x;
-    const int chunk = blockIdx.x;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int i0 = blockIdx.y * kTX, j0 = blockIdx.z * kTY;
     const int I0 = i0 / M, J0 = j0 / M;
-    const int K0 = chunk * A.kc;
+    const int K0 = blockIdx.x * A.kc;
     const int K1 = min(K0 + A.kc, g.nz);
     if (K0 >= K1) return;
     const int k0 = K0 * M, k1 = K1 * M;          // dense layers [k0, k1)
-    const int nplanes = k1 - k0 + 2;             // planes k0-1 .. k1
-    const float DX = g.DX, DY = g.DY, dx = g.dx, dy = g.dy;
-    const bool xedge = (i0 == 0) || (i0 + kTX == g.Nx);
-    const bool yedge = (j0 == 0) || (j0 + kTY == g.Ny);
+    const int nplanes = k1 - k0 + 2;             // ring planes k0-1 .. k1
 
-    for (int t = tid; t < kTX * 3; t += kThreads) sRx[t] = g.Rx[(size_t)i0 * 3 + t];
-    for (int t = tid; t < kTY * 3; t += kThreads) sRy[t] = g.Ry[(size_t)j0 * 3 + t];
     if (!DIVONLY && tid == 0) {
-        for (int s = 0; s < kNB; ++s) mbar_init(&bar[s], 1);
+        for (int s = 0; s < NB; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], kThreads);
+        }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     __syncthreads();
-    if (!DIVONLY && tid == 0)
-        for (int r = 0; r < kNB && r < nplanes; ++r) issue_plane(sT, bar, &tmn, &tmm, r, i0, j0, k0 - 1 + r);
 
-    // coarse tile of layer K into buffer bb (cp.async, periodic wrap in x, y)
+    // ---------------------------------------------------------------- producer warp
+    if (warp == NW) {
+        if (DIVONLY || lane != 0) return;
+        for (int r = 0; r < nplanes; ++r) {
+            const int s = r % NB;
+            if (r >= NB && !mbar_wait(&empty[s], ((r / NB) - 1) & 1)) {
+                atomicExch(A.err, MR_ERR_TIMEOUT);    // consumers then time out on full[]
+                break;
+            }
+            issue_plane(sT, full, &tmn, &tmm, s, i0, j0, k0 - 1 + r);
+        }
+        return;
+    }
+
+    // ---------------------------------------------------------------- consumer warps
+    const float DX = g.DX, DY = g.DY, dx = g.dx, dy = g.dy;
+    const int seg = tid & 15, jl = tid >> 4;     // this thread's 4-cell segment of dense row jl
+    const int il0 = seg * 4;
+    float rx[4][3];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int p = 0; p < 3; ++p) rx[a][p] = g.Rx[(size_t)(i0 + il0 + a) * 3 + p];
+    for (int t = tid; t < kTY * 3; t += kThreads) sRy[t] = g.Ry[(size_t)j0 * 3 + t];
+    // periodic wrap of the in-plane halo, for the threads on the domain edge
+    const bool wrap_w = (i0 == 0 && seg == 0), wrap_e = (i0 + kTX == g.Nx && seg == 15);
+    const bool wrap_s = (j0 == 0 && jl == 0), wrap_n = (j0 + kTY == g.Ny && jl == kTY - 1);
+    const size_t plane = (size_t)g.Nx * g.Ny;
+
+    // coarse tile of layer K into buffer bb (cp.async; one warp per row)
     auto load_coarse = [&](int K, int bb) {
-        constexpr int nU = 3 * UY * UX, nV = 3 * VY * VX, nW = 2 * WY * WX;
-        for (int t = tid; t < nU + nV + nW; t += kThreads) {
-            if (t < nU) {
-                const int q = t / (UY * UX), r = t % (UY * UX), uj = r / UX, ui = r % UX;
-                const int Kq = g.wz[3 * K + q];
-                const int I = wrap(I0 - 1 + ui, g.nx), J = wrap(J0 - 1 + uj, g.ny);
-                cp_async4(cu + bb * nU + t, A.U + ((size_t)Kq * g.ny + J) * g.nx + I);
-            } else if (t < nU + nV) {
-                const int u = t - nU;
-                const int q = u / (VY * VX), r = u % (VY * VX), vj = r / VX, vi = r % VX;
-                const int Kq = g.wz[3 * K + q];
-                const int I = wrap(I0 - 1 + vi, g.nx), J = wrap(J0 - 1 + vj, g.ny);
-                cp_async4(cv + bb * nV + u, A.V + ((size_t)Kq * g.ny + J) * g.nx + I);
+        constexpr int RU = 3 * UY, RV = 3 * VY, RW = 2 * WY;
+        for (int row = warp; row < RU + RV + RW; row += NW) {
+            if (row < RU) {
+                const int q = row / UY, uj = row % UY;
+                const float* src = A.U + ((size_t)g.wz[3 * K + q] * g.ny + wrap(J0 - 1 + uj, g.ny)) * g.nx;
+                float* dst = cu + (bb * RU + row) * UX;
+                for (int x = lane; x < UX; x += 32) cp_async4(dst + x, src + wrap(I0 - 1 + x, g.nx));
+            } else if (row < RU + RV) {
+                const int r2 = row - RU, q = r2 / VY, vj = r2 % VY;
+                const float* src = A.V + ((size_t)g.wz[3 * K + q] * g.ny + wrap(J0 - 1 + vj, g.ny)) * g.nx;
+                float* dst = cv + (bb * RV + r2) * VX;
+                for (int x = lane; x < VX; x += 32) cp_async4(dst + x, src + wrap(I0 - 1 + x, g.nx));
             } else {
-                const int u = t - nU - nV;
-                const int q = u / (WY * WX), r = u % (WY * WX), wj = r / WX, wi = r % WX;
-                const int I = wrap(I0 - 1 + wi, g.nx), J = wrap(J0 - 1 + wj, g.ny);
-                cp_async4(cw + bb * nW + u, A.W + ((size_t)(K + q) * g.ny + J) * g.nx + I);
+                const int r2 = row - RU - RV, q = r2 / WY, wj = r2 % WY;
+                const float* src = A.W + ((size_t)(K + q) * g.ny + wrap(J0 - 1 + wj, g.ny)) * g.nx;
+                float* dst = cw + (bb * RW + r2) * WX;
+                for (int x = lane; x < WX; x += 32) cp_async4(dst + x, src + wrap(I0 - 1 + x, g.nx));
             }
         }
         cp_async_commit();
     };
 
     load_coarse(K0, 0);
-    int waited = 0;            // ring planes waited for and patched
+    int waited = 0;            // ring planes this thread has waited for
     bool fail = false;
     float dmax = 0.f;
 
     for (int K = K0; K < K1; ++K) {
         const int bb = (K - K0) & 1;
         cp_async_wait_all();
-        __syncthreads();
+        if (consumers_sync_or(fail)) break;       // uniform exit of every consumer
         if (K + 1 < K1) load_coarse(K + 1, bb ^ 1);
         const float* ccu = cu + bb * 3 * UY * UX;
         const float* ccv = cv + bb * 3 * VY * VX;
         const float* ccw = cw + bb * 2 * WY * WX;
-        // A1: z-splits of the U and V faces for the M dense layers of the slab
-        for (int t = tid; t < M * UY * UX + M * VY * VX; t += kThreads) {
-            if (t < M * UY * UX) {
-                const int c = t / (UY * UX), r = t % (UY * UX);
+        // per-layer constants of the slab, read by every thread of every layer
+        if (tid < M) {
+            const int k = K * M + tid;
+            float* lc = Lc + tid * 12;
+            lc[0] = g.dz[k]; lc[1] = g.inv_dz[k];
+            lc[2] = g.wlo[k]; lc[3] = g.whi[k]; lc[4] = g.wlo[k + 1]; lc[5] = g.whi[k + 1];
+            lc[6] = g.cdn[k]; lc[7] = g.cup[k]; lc[8] = dx / g.dz[k];
+        }
+        // A1: z-splits of the U and V faces for the M dense layers (R_z)
+        for (int row = warp; row < M * UY + M * VY; row += NW) {
+            if (row < M * UY) {
+                const int c = row / UY, uj = row % UY;
                 const float* rz = g.Rz + 3 * (K * M + c);
-                Uz[t] = rz[0] * ccu[r] + rz[1] * ccu[UY * UX + r] + rz[2] * ccu[2 * UY * UX + r];
+                const float r0 = rz[0], r1 = rz[1], r2 = rz[2];
+                for (int x = lane; x < UX; x += 32)
+                    Uz[row * UX + x] = r0 * ccu[uj * UX + x] + r1 * ccu[(UY + uj) * UX + x] + r2 * ccu[(2 * UY + uj) * UX + x];
             } else {
-                const int u = t - M * UY * UX;
-                const int c = u / (VY * VX), r = u % (VY * VX);
+                const int rr = row - M * UY, c = rr / VY, vj = rr % VY;
                 const float* rz = g.Rz + 3 * (K * M + c);
-                Vz[u] = rz[0] * ccv[r] + rz[1] * ccv[VY * VX + r] + rz[2] * ccv[2 * VY * VX + r];
+                const float r0 = rz[0], r1 = rz[1], r2 = rz[2];
+                for (int x = lane; x < VX; x += 32)
+                    Vz[rr * VX + x] = r0 * ccv[vj * VX + x] + r1 * ccv[(VY + vj) * VX + x] + r2 * ccv[(2 * VY + vj) * VX + x];
             }
         }
-        __syncthreads();
-        // A2: stage Z slab balance, top-down, one thread per column
+        consumers_sync();
+        // A2: stage Z slab balance, top-down, one thread per coarse column
         for (int t = tid; t < WY * WX; t += kThreads) {
             const int wj = t / WX, wi = t % WX;
-            const float wbot = ccw[t], wtop = ccw[WY * WX + t];
-            Wc[t] = wbot;
+            const float wtop = ccw[WY * WX + t];
+            Wc[t] = ccw[t];
             Wc[M * WY * WX + t] = wtop;
             float F = wtop * DX * DY;
+#pragma unroll
             for (int c = M - 1; c >= 1; --c) {
                 const float dzk = g.dz[K * M + c];
                 const float* uz = Uz + c * UY * UX + wj * UX + wi;
@@ -264,173 +319,195 @@ k_fused(const __grid_constant__ CUtensorMap tmn, const __grid_constant__ CUtenso
                 Wc[c * WY * WX + t] = F / (DX * DY);
             }
         }
-        __syncthreads();
+        consumers_sync();
+        // S1: y-split of Wc on the M+1 planes; outer U sub-faces of the M layers (R_y)
+        for (int row = warp; row < (M + 1) * kTY + M * kTY; row += NW) {
+            if (row < (M + 1) * kTY) {
+                const int c = row / kTY, j = row % kTY;
+                const float* ry = sRy + 3 * j;
+                const float* wc = Wc + c * WY * WX + (j / M) * WX;
+                for (int x = lane; x < WX; x += 32)
+                    Wy[row * WX + x] = ry[0] * wc[x] + ry[1] * wc[WX + x] + ry[2] * wc[2 * WX + x];
+            } else {
+                const int rr = row - (M + 1) * kTY, c = rr / kTY, j = rr % kTY;
+                const float* ry = sRy + 3 * j;
+                const float* uz = Uz + c * UY * UX + (j / M) * UX;
+                for (int x = lane; x < UX; x += 32)
+                    Uo[rr * UX + x] = ry[0] * uz[x] + ry[1] * uz[UX + x] + ry[2] * uz[2 * UX + x];
+            }
+        }
+        consumers_sync();
+        // S2: stage Y, full-width V of every dense row by row balance (running
+        // sum from the coarse south face), for the M layers
+        for (int row = warp; row < M * (kTY + 1); row += NW) {
+            const int c = row / (kTY + 1), jr = row % (kTY + 1);
+            const int Jl = jr / M, b = jr % M;
+            const float dzk = g.dz[K * M + c];
+            const float* vz = Vz + (c * VY + Jl + 1) * VX;
+            const float* uo = Uo + c * kTY * UX;
+            const float* wyb = Wy + c * kTY * WX;
+            const float* wyt = Wy + (c + 1) * kTY * WX;
+            for (int x = lane; x < VX; x += 32) {
+                float G = vz[x] * DX * dzk;
+                for (int q = 0; q < b; ++q) {
+                    const int j2 = Jl * M + q;
+                    G = G - (uo[j2 * UX + x + 1] - uo[j2 * UX + x]) * dy * dzk
+                          - (wyt[j2 * WX + x] - wyb[j2 * WX + x]) * DX * dy;
+                }
+                Vr[row * VX + x] = b == 0 ? vz[x] : G / (DX * dzk);
+            }
+        }
+        consumers_sync();
 
+        // the M dense layers of the slab, free-running (no block barrier)
         for (int c = 0; c < M; ++c) {
             const int k = K * M + c;
-            const int pb = k & 1, pt = pb ^ 1;       // Wy / Ws buffers of the bottom / top plane
-            const float dzk = g.dz[k];
-            // B1: y-split of the full-area W on the top plane (and the bottom
-            // plane at the start of the chunk)
-            const int first = (k == k0) ? 0 : 1;
-            for (int t = tid; t < (2 - first) * kTY * WX; t += kThreads) {
-                const int pp = first + t / (kTY * WX);            // 0 bottom, 1 top
-                const int r = t % (kTY * WX), jl = r / WX, wi = r % WX;
-                const float* wc = Wc + (c + pp) * WY * WX + (jl / M) * WX + wi;
-                const float* ry = sRy + 3 * jl;
-                Wy[(pp ? pt : pb) * kTY * WX + r] = ry[0] * wc[0] + ry[1] * wc[WX] + ry[2] * wc[2 * WX];
-            }
-            __syncthreads();
-            if (!DIVONLY && tid == 0 && k > k0) {
-                // the ring slot of plane k-2 is free: fetch plane k-2+NB
-                const int r = (k - 2) - (k0 - 1) + kNB;
-                if (r < nplanes) issue_plane(sT, bar, &tmn, &tmm, r % kNB, i0, j0, k0 - 1 + r);
-            }
-            // B2: x-split into the refined W; B3: outer U sub-faces (R_y of the z-split)
-            for (int t = tid; t < (2 - first) * kTY * kTX + kTY * UX; t += kThreads) {
-                if (t < (2 - first) * kTY * kTX) {
-                    const int pp = first + t / (kTY * kTX);
-                    const int r = t % (kTY * kTX), jl = r / kTX, il = r % kTX;
-                    const float* wy = Wy + (pp ? pt : pb) * kTY * WX + jl * WX + il / M;
-                    const float* rx = sRx + 3 * il;
-                    Ws[(pp ? pt : pb) * kTY * kTX + r] = rx[0] * wy[0] + rx[1] * wy[1] + rx[2] * wy[2];
-                } else {
-                    const int u = t - (2 - first) * kTY * kTX;
-                    const int jl = u / UX, ui = u % UX;
-                    const float* uz = Uz + c * UY * UX + (jl / M) * UX + ui;
-                    const float* ry = sRy + 3 * jl;
-                    Uo[u] = ry[0] * uz[0] + ry[1] * uz[UX] + ry[2] * uz[2 * UX];
-                }
-            }
-            __syncthreads();
-            // B4: stage Y row balance, south to north, per (column, coarse row)
-            for (int t = tid; t < VX * CY; t += kThreads) {
-                const int Jl = t / VX, vi = t % VX;
-                const float vs0 = Vz[c * VY * VX + (Jl + 1) * VX + vi];
-                float G = vs0 * DX * dzk;
-                Vr[(Jl * M) * VX + vi] = vs0;
-                for (int b = 0; b < M - 1; ++b) {
-                    const int jl = Jl * M + b;
-                    const float uw = Uo[jl * UX + vi], ue = Uo[jl * UX + vi + 1];
-                    const float wb = Wy[pb * kTY * WX + jl * WX + vi] * DX;
-                    const float wt = Wy[pt * kTY * WX + jl * WX + vi] * DX;
-                    G = G - (ue - uw) * dy * dzk - (wt - wb) * dy;
-                    Vr[(jl + 1) * VX + vi] = G / (DX * dzk);
-                }
-                if (Jl == CY - 1) Vr[kTY * VX + vi] = Vz[c * VY * VX + (CY + 1) * VX + vi];
-            }
-            __syncthreads();
-            // B5: refined V (R_x over the neighbouring columns' rows)
-            for (int t = tid; t < (kTY + 1) * kTX; t += kThreads) {
-                const int jl = t / kTX, il = t % kTX;
-                const float* vr = Vr + jl * VX + il / M;
-                const float* rx = sRx + 3 * il;
-                Vs[t] = rx[0] * vr[0] + rx[1] * vr[1] + rx[2] * vr[2];
-            }
-            __syncthreads();
-            // B6: stage X cell balance, west to east, per (coarse column, dense row)
-            for (int t = tid; t < CX * kTY; t += kThreads) {
-                const int jl = t / CX, Il = t % CX;
-                const float uo = Uo[jl * UX + Il + 1];
-                float H = uo * dy * dzk;
-                Us[jl * (kTX + 1) + Il * M] = uo;
-                for (int a = 0; a < M - 1; ++a) {
-                    const int il = Il * M + a;
-                    H = H - (Vs[(jl + 1) * kTX + il] - Vs[jl * kTX + il]) * dx * dzk
-                          - (Ws[pt * kTY * kTX + jl * kTX + il] - Ws[pb * kTY * kTX + jl * kTX + il]) * dx * dy;
-                    Us[jl * (kTX + 1) + il + 1] = H / (dy * dzk);
-                }
-                if (Il == CX - 1) Us[jl * (kTX + 1) + kTX] = Uo[jl * UX + CX + 1];
-            }
-            if (!DIVONLY) {
-                // planes k-1, k, k+1 must be resident: wait (bounded) and patch the wrap halo
+            if (!DIVONLY && !fail) {
                 const int need = k + 1 - (k0 - 1);             // ring index of plane k+1
-                while (waited <= need && !fail) {
-                    const int s = waited % kNB;
-                    if (!mbar_wait(&bar[s], (waited / kNB) & 1)) { fail = true; break; }
-                    const int z = k0 - 1 + waited;
-                    if ((xedge || yedge) && z >= 0 && z < g.Nz) {
-                        for (int f = 0; f < 2; ++f) {
-                            float* P = sT + (2 * s + f) * kSlotFloats;
-                            const float* src = (f == 0 ? A.Tn : A.Tm) + (size_t)z * g.Nx * g.Ny;
-                            if (xedge)
-                                for (int t = tid; t < kBY; t += kThreads) {
-                                    const int j = wrap(j0 - 1 + t, g.Ny);
-                                    if (i0 == 0) P[t * kBX + 3] = src[(size_t)j * g.Nx + g.Nx - 1];
-                                    if (i0 + kTX == g.Nx) P[t * kBX + kTX + 4] = src[(size_t)j * g.Nx];
-                                }
-                            if (yedge)
-                                for (int t = tid; t < kBX; t += kThreads) {
-                                    const int i = wrap(i0 - 4 + t, g.Nx);
-                                    if (j0 == 0) P[t] = src[(size_t)(g.Ny - 1) * g.Nx + i];
-                                    if (j0 + kTY == g.Ny) P[(kTY + 1) * kBX + t] = src[i];
-                                }
-                        }
-                    }
+                while (waited <= need) {
+                    if (!mbar_wait(&full[waited % NB], (waited / NB) & 1)) { fail = true; break; }
                     ++waited;
                 }
-                // generic writes above precede later asynchronous (TMA) writes of the slot
-                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             }
-            if (__syncthreads_or(fail)) {
-                if (tid == 0) atomicExch(A.err, MR_ERR_TIMEOUT);
-                return;
-            }
-            // B7: the finite-volume update of this dense layer (or its divergence)
-            const float inv_dz = g.inv_dz[k];
-            const int rb = k - 1 - (k0 - 1), rc = k - (k0 - 1), rt = k + 1 - (k0 - 1);
-            const float* Pn_b = sT + (2 * (rb % kNB) + 0) * kSlotFloats;
-            const float* Pm_b = sT + (2 * (rb % kNB) + 1) * kSlotFloats;
-            const float* Pn_c = sT + (2 * (rc % kNB) + 0) * kSlotFloats;
-            const float* Pm_c = sT + (2 * (rc % kNB) + 1) * kSlotFloats;
-            const float* Pn_t = sT + (2 * (rt % kNB) + 0) * kSlotFloats;
-            const float* Pm_t = sT + (2 * (rt % kNB) + 1) * kSlotFloats;
-            const float wlo_b = g.wlo[k], whi_b = g.whi[k], wlo_t = g.wlo[k + 1], whi_t = g.whi[k + 1];
-            const float cdn = g.cdn[k], cup = g.cup[k];
-            const bool bot = (k == 0), top = (k == g.Nz - 1);
-            const int il = tid % kTX;
-            for (int jl = tid / kTX; jl < kTY; jl += kThreads / kTX) {
-                const float uw = Us[jl * (kTX + 1) + il], ue = Us[jl * (kTX + 1) + il + 1];
-                const float vs = Vs[jl * kTX + il], vn = Vs[(jl + 1) * kTX + il];
-                const float wb = Ws[pb * kTY * kTX + jl * kTX + il], wt = Ws[pt * kTY * kTX + jl * kTX + il];
-                if (DIVONLY) {
-                    const float d = (ue - uw) * g.inv_dx + (vn - vs) * g.inv_dy + (wt - wb) * inv_dz;
-                    dmax = fmaxf(dmax, fabsf(d));
-                    continue;
+            if (!fail) {
+            const float* lc = Lc + c * 12;
+            // refined faces of this thread's 4 cells, in registers
+            float wb[4], wt[4], vs[4], vn[4], us[5];
+            {
+                const float* yb = Wy + (c * kTY + jl) * WX;
+                const float* yt = Wy + ((c + 1) * kTY + jl) * WX;
+                const float* rs = Vr + (c * (kTY + 1) + jl) * VX;
+                const float* rn = rs + VX;
+                const int cb0 = il0 / M;                      // first coarse column of the window
+#pragma unroll
+                for (int a = 0; a < 4; ++a) {
+                    const int cb = cb0 + a / M;
+                    wb[a] = rx[a][0] * yb[cb] + rx[a][1] * yb[cb + 1] + rx[a][2] * yb[cb + 2];
+                    wt[a] = rx[a][0] * yt[cb] + rx[a][1] * yt[cb + 1] + rx[a][2] * yt[cb + 2];
+                    vs[a] = rx[a][0] * rs[cb] + rx[a][1] * rs[cb + 1] + rx[a][2] * rs[cb + 2];
+                    vn[a] = rx[a][0] * rn[cb] + rx[a][1] * rn[cb + 1] + rx[a][2] * rn[cb + 2];
                 }
-                const int o = (jl + 1) * kBX + il + 4;
-                const float tc = Pn_c[o], tw = Pn_c[o - 1], te = Pn_c[o + 1], ts = Pn_c[o - kBX], tn = Pn_c[o + kBX];
-                const float dc = Pm_c[o], dw = Pm_c[o - 1], de = Pm_c[o + 1], ds = Pm_c[o - kBX], dn = Pm_c[o + kBX];
+                // stage X: cell balance, west to east (velocity units: h = H / (dy dz))
+                const float* ur = Uo + (c * kTY + jl) * UX;
+                const float fx_y = dx / dy, fx_z = lc[8];
+#pragma unroll
+                for (int q = 0; q < NC; ++q) {
+                    float h = ur[cb0 + q + 1];                // outer west face of the coarse cell
+                    us[q * M] = h;
+#pragma unroll
+                    for (int a = 0; a < M - 1; ++a) {
+                        const int m = q * M + a;
+                        h = h - (vn[m] - vs[m]) * fx_y - (wt[m] - wb[m]) * fx_z;
+                        us[m + 1] = h;
+                    }
+                }
+                us[4] = ur[cb0 + NC + 1];                     // outer east face of the segment
+            }
+            const float inv_dz = lc[1];
+            if (DIVONLY) {
+#pragma unroll
+                for (int a = 0; a < 4; ++a) {
+                    const float d = (us[a + 1] - us[a]) * g.inv_dx + (vn[a] - vs[a]) * g.inv_dy + (wt[a] - wb[a]) * inv_dz;
+                    dmax = fmaxf(dmax, fabsf(d));
+                }
+                continue;
+            }
+            const int rb = k - k0, rc = rb + 1, rt = rb + 2;   // ring indices of planes k-1, k, k+1
+            const float* Pn_b = sT + (2 * (rb % NB) + 0) * kSlotFloats;
+            const float* Pm_b = sT + (2 * (rb % NB) + 1) * kSlotFloats;
+            const float* Pn_c = sT + (2 * (rc % NB) + 0) * kSlotFloats;
+            const float* Pm_c = sT + (2 * (rc % NB) + 1) * kSlotFloats;
+            const float* Pn_t = sT + (2 * (rt % NB) + 0) * kSlotFloats;
+            const float* Pm_t = sT + (2 * (rt % NB) + 1) * kSlotFloats;
+            const int o = (jl + 1) * kBX + il0 + 4;
+            float4 tc4 = *reinterpret_cast<const float4*>(Pn_c + o);
+            float4 ts4 = *reinterpret_cast<const float4*>(Pn_c + o - kBX);
+            float4 tn4 = *reinterpret_cast<const float4*>(Pn_c + o + kBX);
+            float4 dc4 = *reinterpret_cast<const float4*>(Pm_c + o);
+            float4 ds4 = *reinterpret_cast<const float4*>(Pm_c + o - kBX);
+            float4 dn4 = *reinterpret_cast<const float4*>(Pm_c + o + kBX);
+            float tw = Pn_c[o - 1], te = Pn_c[o + 4], dw = Pm_c[o - 1], de = Pm_c[o + 4];
+            if (wrap_w | wrap_e | wrap_s | wrap_n) {
+                // the box holds zeros beyond the domain: fetch the periodic images
+                const size_t row = (size_t)k * plane + (size_t)(j0 + jl) * g.Nx;
+                if (wrap_w) { tw = A.Tn[row + g.Nx - 1]; dw = A.Tm[row + g.Nx - 1]; }
+                if (wrap_e) { te = A.Tn[row]; de = A.Tm[row]; }
+                if (wrap_s) {
+                    const size_t r2 = (size_t)k * plane + (size_t)(g.Ny - 1) * g.Nx + i0 + il0;
+                    ts4 = *reinterpret_cast<const float4*>(A.Tn + r2);
+                    ds4 = *reinterpret_cast<const float4*>(A.Tm + r2);
+                }
+                if (wrap_n) {
+                    const size_t r2 = (size_t)k * plane + i0 + il0;
+                    tn4 = *reinterpret_cast<const float4*>(A.Tn + r2);
+                    dn4 = *reinterpret_cast<const float4*>(A.Tm + r2);
+                }
+            }
+            const float tcv[6] = {tw, tc4.x, tc4.y, tc4.z, tc4.w, te};
+            const float dcv[6] = {dw, dc4.x, dc4.y, dc4.z, dc4.w, de};
+            const float tsv[4] = {ts4.x, ts4.y, ts4.z, ts4.w}, tnv[4] = {tn4.x, tn4.y, tn4.z, tn4.w};
+            const float dsv[4] = {ds4.x, ds4.y, ds4.z, ds4.w}, dnv[4] = {dn4.x, dn4.y, dn4.z, dn4.w};
+            float tbv[4] = {0.f, 0.f, 0.f, 0.f}, dbv[4] = {0.f, 0.f, 0.f, 0.f};
+            float ttv[4] = {0.f, 0.f, 0.f, 0.f}, dtv[4] = {0.f, 0.f, 0.f, 0.f};
+            const bool bot = (k == 0), top = (k == g.Nz - 1);
+            if (!bot) {
+                const float4 b4 = *reinterpret_cast<const float4*>(Pn_b + o);
+                const float4 e4 = *reinterpret_cast<const float4*>(Pm_b + o);
+                tbv[0] = b4.x; tbv[1] = b4.y; tbv[2] = b4.z; tbv[3] = b4.w;
+                dbv[0] = e4.x; dbv[1] = e4.y; dbv[2] = e4.z; dbv[3] = e4.w;
+            }
+            if (!top) {
+                const float4 b4 = *reinterpret_cast<const float4*>(Pn_t + o);
+                const float4 e4 = *reinterpret_cast<const float4*>(Pm_t + o);
+                ttv[0] = b4.x; ttv[1] = b4.y; ttv[2] = b4.z; ttv[3] = b4.w;
+                dtv[0] = e4.x; dtv[1] = e4.y; dtv[2] = e4.z; dtv[3] = e4.w;
+            }
+            // plane k-1 is no longer needed by this thread: release its ring slot
+            mbar_arrive(&empty[rb % NB]);
+            const float wlo_b = lc[2], whi_b = lc[3], wlo_t = lc[4], whi_t = lc[5];
+            const float cdn = lc[6], cup = lc[7];
+            float res[4];
+#pragma unroll
+            for (int a = 0; a < 4; ++a) {
+                const float tc = tcv[a + 1], dc = dcv[a + 1];
                 float cz = 0.f, dz_ = 0.f;
                 if (!bot) {
-                    cz += wb * (wlo_b * Pn_b[o] + whi_b * tc);
-                    dz_ -= cdn * (dc - Pm_b[o]);
+                    cz += wb[a] * (wlo_b * tbv[a] + whi_b * tc);
+                    dz_ -= cdn * (dc - dbv[a]);
                 } else {
                     dz_ -= cdn * (dc - kTBottom);
                 }
                 if (!top) {
-                    cz -= wt * (wlo_t * tc + whi_t * Pn_t[o]);
-                    dz_ += cup * (Pm_t[o] - dc);
+                    cz -= wt[a] * (wlo_t * tc + whi_t * ttv[a]);
+                    dz_ += cup * (dtv[a] - dc);
                 } else {
                     dz_ += cup * (kTTop - dc);
                 }
-                const float cx = uw * 0.5f * (tw + tc) - ue * 0.5f * (tc + te);
-                const float cy = vs * 0.5f * (ts + tc) - vn * 0.5f * (tc + tn);
+                const float cx = us[a] * 0.5f * (tcv[a] + tc) - us[a + 1] * 0.5f * (tc + tcv[a + 2]);
+                const float cy = vs[a] * 0.5f * (tsv[a] + tc) - vn[a] * 0.5f * (tc + tnv[a]);
                 const float C = cx * g.inv_dx + cy * g.inv_dy + cz * inv_dz;
-                const float D = g.kx2 * ((de - dc) - (dc - dw)) + g.ky2 * ((dn - dc) - (dc - ds)) + dz_;
-                A.Tp1[((size_t)k * g.Ny + j0 + jl) * g.Nx + i0 + il] = A.a * dc + A.b * tc + A.gdt * (C + D);
+                const float D = g.kx2 * ((dcv[a + 2] - dc) - (dc - dcv[a])) + g.ky2 * ((dnv[a] - dc) - (dc - dsv[a])) + dz_;
+                res[a] = A.a * dc + A.b * tc + A.gdt * (C + D);
             }
-            // next layer reuses Ws/Wy of this top plane as its bottom plane
+            *reinterpret_cast<float4*>(A.Tp1 + (size_t)k * plane + (size_t)(j0 + jl) * g.Nx + i0 + il0) =
+                make_float4(res[0], res[1], res[2], res[3]);
+            } else if (!DIVONLY) {
+                mbar_arrive(&empty[(k - k0) % NB]);
+            }
         }
+    }
+    if (consumers_sync_or(fail)) {
+        if (tid == 0) atomicExch(A.err, MR_ERR_TIMEOUT);
+        return;
     }
     if (DIVONLY) {
         // block max -> device max (non-negative doubles order as their bit patterns)
         for (int o = 16; o > 0; o >>= 1) dmax = fmaxf(dmax, __shfl_down_sync(0xffffffffu, dmax, o));
-        if ((tid & 31) == 0) red[tid >> 5] = dmax;
-        __syncthreads();
+        if (lane == 0) red[warp] = dmax;
+        consumers_sync();
         if (tid == 0) {
             float m = 0.f;
-            for (int w = 0; w < kThreads / 32; ++w) m = fmaxf(m, red[w]);
+            for (int w = 0; w < NW; ++w) m = fmaxf(m, red[w]);
             atomicMax(A.divmax, (unsigned long long)__double_as_longlong((double)m));
         }
     }
@@ -467,6 +544,23 @@ bool make_map(CUtensorMap* m, const float* base, const Grid<float>& g)
               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
+// Tensor maps of the (few) scalar buffers in use, encoded once each.
+bool cached_map(CUtensorMap* m, const float* base, const Grid<float>& g)
+{
+    struct Entry { const float* p; int nx, ny, nz; CUtensorMap map; };
+    static Entry cache[16];
+    static int n = 0;
+    for (int q = 0; q < n; ++q)
+        if (cache[q].p == base && cache[q].nx == g.Nx && cache[q].ny == g.Ny && cache[q].nz == g.Nz) {
+            *m = cache[q].map;
+            return true;
+        }
+    if (!make_map(m, base, g)) return false;
+    Entry& e = cache[n < 16 ? n++ : (n = 1, 0)];
+    e.p = base; e.nx = g.Nx; e.ny = g.Ny; e.nz = g.Nz; e.map = *m;
+    return true;
+}
+
 // Coarse layers per CTA chunk; MR_FUSED_KC in the environment overrides the
 // automatic choice (used for tuning).
 int chunk_override()
@@ -494,7 +588,7 @@ cudaError_t launch_fused(const Grid<float>& g, const float* U, const float* V, c
     }
     CUtensorMap mn, mm;
     if (!DIVONLY) {
-        if (!make_map(&mn, T, g) || !make_map(&mm, Tm1, g)) return cudaErrorInvalidValue;
+        if (!cached_map(&mn, T, g) || !cached_map(&mm, Tm1, g)) return cudaErrorInvalidValue;
     } else {
         memset(&mn, 0, sizeof mn);
         memset(&mm, 0, sizeof mm);
@@ -503,7 +597,7 @@ cudaError_t launch_fused(const Grid<float>& g, const float* U, const float* V, c
     const int tiles = (g.Nx / kTX) * (g.Ny / kTY);
     int kc = chunk_override();
     if (kc <= 0) {
-        const int want = 152 * 2 * 4;                     // ~4 waves at 2 CTAs / SM
+        const int want = 152 * 2 * 8;                     // ~8 waves at 2 CTAs / SM
         int chunks = (want + tiles - 1) / tiles;
         chunks = max(1, min(chunks, g.nz));
         kc = (g.nz + chunks - 1) / chunks;
@@ -512,7 +606,7 @@ cudaError_t launch_fused(const Grid<float>& g, const float* U, const float* V, c
     const int chunks = (g.nz + kc - 1) / kc;
     FusedArgs A{g, U, V, W, T, Tm1, Tp1, (float)c.a, (float)c.b, (float)c.gdt, kc, err, divmax};
     dim3 grid(chunks, g.Nx / kTX, g.Ny / kTY);
-    k_fused<M, DIVONLY><<<grid, kThreads, L::bytes, st>>>(mn, mm, A);
+    k_fused<M, DIVONLY><<<grid, kThreadsAll, L::bytes, st>>>(mn, mm, A);
     return cudaGetLastError();
 }
 

@@ -83,8 +83,9 @@ def test_fused_cfl_and_dense_faces(mr, prob):
     out = [torch.empty(sh[k], dtype=torch.float32, device="cuda") for k in ("Us", "Vs", "Ws")]
     mr.mr_refine_velocity(h, dev(prob.U), dev(prob.V), dev(prob.W), *out)
     vel = O.refine(prob.cfg, prob.U, prob.V, prob.W)
+    scale = max(np.abs(r).max() for r in vel)     # FP32 error scales with the largest fluxes
     for got, r in zip(out, vel):
-        assert np.abs(got.cpu().numpy() - r).max() <= F32_T_TOL * np.abs(r).max()
+        assert np.abs(got.cpu().numpy() - r).max() <= F32_T_TOL * scale
     assert abs(mr.mr_cfl_dt(h, 0.3) / O.cfl_dt(prob.cfg, vel, 0.3) - 1) <= 1e-5
 
 

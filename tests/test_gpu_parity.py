@@ -69,9 +69,12 @@ def test_refine_matches_oracle(mr, prob, precision):
     mr.mr_refine_velocity(h, dev(prob.U), dev(prob.V), dev(prob.W), *out)
     torch.cuda.synchronize()
     ref = O.refine(prob.cfg, prob.U, prob.V, prob.W)
-    tol = F64_TOL if precision == "f64" else F32_T_TOL   # FP32: ~3 recursion stages, O(100) u_32
+    # relative to the largest face velocity: the balance stages subtract fluxes
+    # of all three components, so FP32 round-off scales with the largest one
+    tol = F64_TOL if precision == "f64" else F32_T_TOL
+    scale = max(np.abs(r).max() for r in ref)
     for got, r in zip(out, ref):
-        assert rel_err(got.cpu().numpy(), r) <= tol
+        assert np.abs(got.cpu().numpy() - r).max() <= tol * scale
     # host pointers give the same faces (the library copies them in first)
     h2 = _handle(mr, prob, P)
     out2 = [torch.empty_like(o) for o in out]
