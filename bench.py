@@ -35,6 +35,9 @@ WORKLOADS = {
     "rb512_stretched_f32": dict(nx=128, ny=128, nz=96, m=4, gamma=1.5, ra=1e9, pr=100.0, rms=0.1,
                                 label="coarse 128x128x96 -> dense 512x512x384, stretched z (gamma 1.5), "
                                       "Ra=1e9, Sc=100, CFL 0.3"),
+    "rb128_adjoint": dict(nx=64, ny=64, nz=48, m=2, gamma=1.5, ra=1e7, pr=7.0, rms=0.1,
+                          label="coarse 64x64x48 -> dense 128x128x96, stretched z (gamma 1.5), Ra=1e7, Pr=7, "
+                                "200 steps, checkpoints every 20, loss = bottom Nu over the last 50 steps"),
     "rb256_stretched_f64": dict(nx=128, ny=128, nz=96, m=2, gamma=1.5, ra=1e8, pr=7.0, rms=0.1,
                                 label="coarse 128x128x96 -> dense 256x256x192, stretched z (gamma 1.5), "
                                       "Ra=1e8, Pr=7, CFL 0.3"),
@@ -227,6 +230,10 @@ def run_mr(args):
                "h2d_bytes_per_step": int(U.nbytes + V.nbytes + W.nbytes), "d2h_bytes_per_step": 16,
                "steps": ke}
 
+    adj = None
+    if rank == 0 and not args.no_adjoint:
+        adj = adjoint_cost(torch, mr, stream)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         cpu = cpu_baseline(w, dt, budget_s=args.cpu_budget)
@@ -242,7 +249,7 @@ def run_mr(args):
             "config": {"workload": args.workload, "description": w["label"], "dense_cells": cells,
                        "velocity_mode": args.mode, "dt": dt, "parallelism": f"replicas{world}",
                        "l2": "inputs larger than L2 (3 scalar levels of %.0f MB)" % (cells * elt / 2**20)},
-            "roofline": roof, "fp64_path": fp64, "e2e": e2e, "cpu_baseline": cpu,
+            "roofline": roof, "fp64_path": fp64, "adjoint": adj, "e2e": e2e, "cpu_baseline": cpu,
             "gpu_launches": args.steps, "clocks": clk.summary(),
             "final_stats": {k: st[k] for k in ("nu_bot", "nu_top", "mean", "var")},
         }
@@ -250,6 +257,38 @@ def run_mr(args):
     if world > 1:
         dist.barrier()
         dist.destroy_process_group()
+
+
+def adjoint_cost(torch, mr, stream, S=200, ck=20):
+    """Backward (segment recompute + adjoint sweep + refinement transpose) over
+    forward time on the 128x128x96 differentiation workload, FP64 and FP32."""
+    w = WORKLOADS["rb128_adjoint"]
+    out = {"workload": "rb128_adjoint", "steps": S, "checkpoint_every": ck}
+    wnu = np.zeros(S + 1)
+    wnu[-50:] = 1.0 / 50
+    for name, prec in (("f64", mr.MR_F64), ("f32", mr.MR_F32)):
+        h = _make(mr, w, prec, mr.MR_VEL_STORED)
+        U, V, W, T0 = _inputs(mr, h, w)
+        dU, dV, dW, dT0 = (torch.from_numpy(a).cuda() for a in (U, V, W, T0))
+        mr.mr_refine_velocity(h, dU, dV, dW, stream=stream)
+        mr.mr_set_dt(h, mr.mr_cfl_dt(h, 0.3, stream=stream))
+        mr.mr_set_scalar(h, dT0, stream=stream)
+        fwd = _time_steps(torch, mr, h, S, 3, stream)            # plain forward steps
+        mr.mr_set_scalar(h, dT0, stream=stream)
+        mr.mr_adjoint_forward(h, S, ck, wnu, None, stream=stream)
+        sh = h.shapes
+        g = [torch.empty(sh[k], dtype=torch.float64, device="cuda") for k in ("T", "U", "V", "W")]
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        mr.mr_adjoint_backward(h, 1.0, *g, stream=stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        bwd = e0.elapsed_time(e1) / 1e3
+        out[name] = {"forward_ms": round(fwd * 1e3, 3), "backward_ms": round(bwd * 1e3, 3),
+                     "backward_over_forward": round(bwd / fwd, 3)}
+        h.close()
+    return out
 
 
 def cpu_baseline(w, dt, budget_s=30.0, max_steps=None):
@@ -315,6 +354,7 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-adjoint", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

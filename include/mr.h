@@ -156,6 +156,24 @@ int mr_cfl_dt(mr_handle h, double cfl, double* dt_out, mr_stream stream);
 /* Replace the time step. */
 int mr_set_dt(mr_handle h, double dt);
 
+/* Gradients (hand-written discrete adjoint of the scheme above).
+ * mr_adjoint_forward runs nsteps steps from the scalar just set by
+ * mr_set_scalar (MR_ERR_STATE otherwise), storing the pair (T^{s-1}, T^s)
+ * every checkpoint_every steps in library memory, and returns
+ *   L = sum_{s=0..nsteps} wnu[s] Nu_bot(T^s) + wvar[s] Var(T^s)
+ * (wnu, wvar: host arrays of nsteps + 1 doubles; either may be NULL = 0).
+ * mr_adjoint_backward then recomputes each segment from its checkpoint,
+ * sweeps the adjoint back to s = 0 and writes gscale * dL/dT^0 (dense, dtype
+ * MR_F64 or MR_F32) and gscale * dL/dU, dL/dV, dL/dW (coarse, FP64, through
+ * the transpose of the refinement of Section 3.2); any output may be NULL.
+ * Pointers may be host or device.  Both synchronise.  Needs MR_VEL_STORED and
+ * explicit diffusion (MR_ERR_ARG otherwise).  The time step is not
+ * differentiated.  After the backward the handle holds T^nsteps. */
+int mr_adjoint_forward(mr_handle h, int64_t nsteps, int32_t checkpoint_every, const double* wnu,
+                       const double* wvar, double* loss, mr_stream stream);
+int mr_adjoint_backward(mr_handle h, double gscale, void* gT0, int32_t gT0_dtype, double* gU, double* gV,
+                        double* gW, mr_stream stream);
+
 /* Integer index maps for testing (synchronous, host buffer): coarse cell of
  * every dense cell along x, y, z, then the three coarse cells of the R window
  * of every coarse cell along x, y, z: Nx+Ny+Nz+3(nx+ny+nz) int32 values.

@@ -265,6 +265,9 @@ void mr_destroy(mr_handle h)
                     b.metric, b.red, b.nu2, b.stage, b.tri};
     for (void* p : ptrs)
         if (p) cudaFree(p);
+    void* aptrs[] = {h->adj.cp, h->adj.seg, h->adj.mu, h->adj.face, h->adj.scr, h->adj.out};
+    for (void* p : aptrs)
+        if (p) cudaFree(p);
     if (h->elt == 4) {
         if (b.Uc) cudaFree(b.Uc);
         if (b.Vc) cudaFree(b.Vc);
@@ -701,6 +704,237 @@ int mr_debug_index_maps(mr_handle h, int32_t* out, size_t cap)
     for (int k = 0; k < h->Nz; ++k) *p++ = k / c.mz;
     for (int v : win) *p++ = v;
     return MR_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------- adjoint (host orchestration)
+
+namespace {
+
+using namespace mr;
+
+// FP64 volume mean and variance of a dense field in precision P (two-pass).
+int field_moments(mr_handle h, const void* T, double* mean, double* var, cudaStream_t st)
+{
+    const double dxdy = (h->cfg.lx / h->Nx) * (h->cfg.ly / h->Ny);
+    double vtot = 0.0;
+    for (int k = 0; k < h->Nz; ++k) vtot += h->dz[k];
+    vtot *= dxdy * (double)h->Nx * (double)h->Ny;
+    std::vector<double> p;
+    for (int pass = 0; pass < 2; ++pass) {
+        cudaError_t e = h->cfg.precision == MR_F64
+                            ? launch_moments<double>(h->g64, (const double*)T, *mean, pass, h->buf.red, h->red_blocks, st)
+                            : launch_moments<float>(h->g32, (const float*)T, *mean, pass, h->buf.red, h->red_blocks, st);
+        if (e != cudaSuccess) return cuda_check(e, "moments");
+        int rc = reduce_partials(h, 2, p, st);
+        if (rc) return rc;
+        double s = 0.0;
+        for (int q = 0; q < h->red_blocks; ++q) s += p[2 * q];
+        if (pass == 0) *mean = s * dxdy / vtot;
+        else *var = s * dxdy / vtot;
+    }
+    return MR_OK;
+}
+
+int field_nu(mr_handle h, const void* T, double nu[2], cudaStream_t st)
+{
+    const double zz[2] = {h->zc[0] - h->zf[0], h->zf[h->Nz] - h->zc[h->Nz - 1]};
+    cudaError_t e = h->cfg.precision == MR_F64 ? launch_plate_nu<double>(h->g64, (const double*)T, zz, h->buf.nu2, st)
+                                               : launch_plate_nu<float>(h->g32, (const float*)T, zz, h->buf.nu2, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(nu, h->buf.nu2, 2 * sizeof(double), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    return cuda_check(e, "plate Nusselt");
+}
+
+cudaError_t step_buffers(mr_handle h, const void* Tm1, const void* T, void* Tp1, int64_t s, cudaStream_t st)
+{
+    const StepCoef c = step_coef(h->cfg, s);
+    const void* tm = s == 0 ? T : Tm1;
+    const DeviceBuffers& b = h->buf;
+    if (h->cfg.precision == MR_F64)
+        return launch_step_stored<double>(h->g64, (const double*)b.Us, (const double*)b.Vs, (const double*)b.Ws,
+                                          (const double*)tm, (const double*)T, (double*)Tp1, c, false, st);
+    return launch_step_stored<float>(h->g32, (const float*)b.Us, (const float*)b.Vs, (const float*)b.Ws,
+                                     (const float*)tm, (const float*)T, (float*)Tp1, c, false, st);
+}
+
+void adj_free(mr_handle h)
+{
+    auto& a = h->adj;
+    void* ptrs[] = {a.cp, a.seg, a.mu, a.face, a.scr, a.out};
+    for (void* p : ptrs)
+        if (p) cudaFree(p);
+    a.cp = a.seg = a.mu = nullptr;
+    a.face = a.scr = a.out = nullptr;
+    a.cp_pairs = 0;
+    a.ready = false;
+}
+
+}  // namespace
+
+extern "C" {
+
+int mr_adjoint_forward(mr_handle h, int64_t nsteps, int32_t ck, const double* wnu, const double* wvar, double* loss,
+                       mr_stream stream)
+{
+    if (!h || !loss) return set_error(MR_ERR_ARG, "mr_adjoint_forward: NULL argument");
+    if (nsteps < 1 || ck < 1) return set_error(MR_ERR_ARG, "mr_adjoint_forward: nsteps and checkpoint_every must be >= 1");
+    if (h->cfg.velocity_mode != MR_VEL_STORED || h->cfg.diffz_implicit)
+        return set_error(MR_ERR_ARG, "mr_adjoint_forward: needs MR_VEL_STORED and explicit diffusion");
+    if (!h->have_velocity || !h->have_scalar || h->step != 0)
+        return set_error(MR_ERR_STATE, "mr_adjoint_forward: call mr_refine_velocity and mr_set_scalar first");
+    cudaStream_t st = (cudaStream_t)stream;
+    auto& a = h->adj;
+    const size_t cpairs = (size_t)((nsteps + ck - 1) / ck);
+    const size_t fb = h->ncell * h->elt;
+    if (a.cp && (a.cp_pairs < cpairs || a.ck < ck)) adj_free(h);
+    cudaError_t e = cudaSuccess;
+    if (!a.cp) {
+        e = cudaMalloc(&a.cp, cpairs * 2 * fb);
+        if (e == cudaSuccess) e = cudaMalloc(&a.seg, ((size_t)ck + 1) * fb);
+        if (e == cudaSuccess) e = cudaMalloc(&a.mu, 3 * fb);
+        if (e == cudaSuccess) e = cudaMalloc((void**)&a.face, (h->nU + h->nV + h->nW) * sizeof(double));
+        const size_t nscr = (size_t)(h->Nz + 1) * h->cfg.ny * h->cfg.nx + (size_t)h->Nz * (h->Ny + h->w) * h->cfg.nx;
+        if (e == cudaSuccess) e = cudaMalloc((void**)&a.scr, nscr * sizeof(double));
+        if (e == cudaSuccess) e = cudaMalloc((void**)&a.out, (h->ncell + h->ncU + h->ncV + h->ncW) * sizeof(double));
+        if (e != cudaSuccess) {
+            adj_free(h);
+            return cuda_check(e, "mr_adjoint_forward: checkpoint store");
+        }
+        a.cp_pairs = cpairs;
+        a.ck = ck;
+    }
+    a.ready = false;
+    a.S = nsteps;
+    a.ck = ck;
+    a.wnu.assign(wnu ? wnu : nullptr, wnu ? wnu + nsteps + 1 : nullptr);
+    a.wvar.assign(wvar ? wvar : nullptr, wvar ? wvar + nsteps + 1 : nullptr);
+    if (a.wnu.empty()) a.wnu.assign(nsteps + 1, 0.0);
+    if (a.wvar.empty()) a.wvar.assign(nsteps + 1, 0.0);
+    a.mean.assign(nsteps + 1, 0.0);
+    double L = 0.0;
+    for (int64_t s = 0; s <= nsteps; ++s) {
+        const void* Tc = h->buf.T[h->ic];
+        if (s < nsteps && s % ck == 0) {
+            char* pair = (char*)a.cp + (size_t)(s / ck) * 2 * fb;
+            e = cudaMemcpyAsync(pair, h->buf.T[h->ip], fb, cudaMemcpyDeviceToDevice, st);
+            if (e == cudaSuccess) e = cudaMemcpyAsync(pair + fb, Tc, fb, cudaMemcpyDeviceToDevice, st);
+            if (e != cudaSuccess) return cuda_check(e, "mr_adjoint_forward: checkpoint");
+        }
+        int rc;
+        if (a.wnu[s] != 0.0) {
+            double nu[2];
+            if ((rc = field_nu(h, Tc, nu, st))) return rc;
+            L += a.wnu[s] * nu[0];
+        }
+        if (a.wvar[s] != 0.0) {
+            double mean = 0.0, var = 0.0;
+            if ((rc = field_moments(h, Tc, &mean, &var, st))) return rc;
+            a.mean[s] = mean;
+            L += a.wvar[s] * var;
+        }
+        if (s < nsteps && (rc = mr_scalar_step(h, 1, stream))) return rc;
+    }
+    *loss = L;
+    a.ready = true;
+    return cuda_check(cudaStreamSynchronize(st), "mr_adjoint_forward");
+}
+
+int mr_adjoint_backward(mr_handle h, double gscale, void* gT0, int32_t gT0_dtype, double* gU, double* gV, double* gW,
+                        mr_stream stream)
+{
+    if (!h) return set_error(MR_ERR_ARG, "mr_adjoint_backward: NULL handle");
+    if (gT0 && gT0_dtype != MR_F64 && gT0_dtype != MR_F32) return set_error(MR_ERR_ARG, "mr_adjoint_backward: bad dtype");
+    auto& a = h->adj;
+    if (!a.ready) return set_error(MR_ERR_STATE, "mr_adjoint_backward: call mr_adjoint_forward first");
+    cudaStream_t st = (cudaStream_t)stream;
+    const int P = h->cfg.precision;
+    const size_t fb = h->ncell * h->elt;
+    const int64_t S = a.S;
+    const int ck = a.ck;
+    const double dxdy = (h->cfg.lx / h->Nx) * (h->cfg.ly / h->Ny);
+    double vtot = 0.0;
+    for (int k = 0; k < h->Nz; ++k) vtot += h->dz[k];
+    vtot *= dxdy * (double)h->Nx * (double)h->Ny;
+    const double zb = h->zc[0] - h->zf[0];
+    // direct terms in adjoint-density units (per unit volume)
+    auto s_nu = [&](int64_t s) { return -gscale * a.wnu[s] / ((double)h->Nx * h->Ny * zb * dxdy * h->dz[0]); };
+    auto s_var = [&](int64_t s) { return gscale * a.wvar[s] * 2.0 / vtot; };
+    char* mu[3] = {(char*)a.mu, (char*)a.mu + fb, (char*)a.mu + 2 * fb};
+    int in = 0, ic = 1, ip = 2;     // mu^{s+1}, mu^s, mu^{s-1}
+    cudaError_t e = cudaMemsetAsync(a.face, 0, (h->nU + h->nV + h->nW) * sizeof(double), st);
+    // levels S and S-1 start from their direct terms (T^S, T^{S-1} are the handle's current pair)
+    auto direct = [&](const void* T, int64_t s, void* out) {
+        return P == MR_F64 ? launch_adj_direct<double>(h->g64, (const double*)T, s_nu(s), s_var(s), a.mean[s], (double*)out, st)
+                           : launch_adj_direct<float>(h->g32, (const float*)T, s_nu(s), s_var(s), a.mean[s], (float*)out, st);
+    };
+    if (e == cudaSuccess) e = direct(h->buf.T[h->ic], S, mu[in]);
+    if (e == cudaSuccess) e = direct(h->buf.T[h->ip], S - 1, mu[ic]);
+    if (e != cudaSuccess) return cuda_check(e, "mr_adjoint_backward: init");
+    double* fU = a.face;
+    double* fV = a.face + h->nU;
+    double* fW = a.face + h->nU + h->nV;
+    const DeviceBuffers& b = h->buf;
+    const int64_t nseg = (S + ck - 1) / ck;
+    for (int64_t c = nseg - 1; c >= 0; --c) {
+        const int64_t c0 = c * ck, e1 = std::min<int64_t>(c0 + ck, S);
+        // recompute T^{c0-1} .. T^{e1-1} into seg[0 .. e1-c0]
+        char* seg = (char*)a.seg;
+        const char* pair = (const char*)a.cp + (size_t)c * 2 * fb;
+        e = cudaMemcpyAsync(seg, pair, 2 * fb, cudaMemcpyDeviceToDevice, st);
+        for (int64_t s = c0; e == cudaSuccess && s < e1 - 1; ++s)
+            e = step_buffers(h, seg + (s - c0) * fb, seg + (s - c0 + 1) * fb, seg + (s - c0 + 2) * fb, s, st);
+        if (e != cudaSuccess) return cuda_check(e, "mr_adjoint_backward: recompute");
+        for (int64_t s = e1 - 1; s >= c0; --s) {
+            const void* Ts = seg + (s - c0 + 1) * fb;
+            const void* Tsm = seg + (s - c0) * fb;
+            const StepCoef co = step_coef(h->cfg, s);
+            const bool euler = (s == 0);
+            const int64_t sp = euler ? 0 : s - 1;
+            if (P == MR_F64)
+                e = launch_adj_step<double>(h->g64, (const double*)b.Us, (const double*)b.Vs, (const double*)b.Ws,
+                                            (const double*)Ts, (const double*)Tsm, (const double*)mu[in],
+                                            (double*)mu[ic], (double*)mu[ip], s_nu(sp), s_var(sp), a.mean[sp], fU, fV,
+                                            fW, co, euler, st);
+            else
+                e = launch_adj_step<float>(h->g32, (const float*)b.Us, (const float*)b.Vs, (const float*)b.Ws,
+                                           (const float*)Ts, (const float*)Tsm, (const float*)mu[in], (float*)mu[ic],
+                                           (float*)mu[ip], s_nu(sp), s_var(sp), a.mean[sp], fU, fV, fW, co, euler, st);
+            if (e != cudaSuccess) return cuda_check(e, "mr_adjoint_backward: launch");
+            if (!euler) {
+                const int t = in;
+                in = ic;
+                ic = ip;
+                ip = t;
+            }
+        }
+    }
+    // after the Euler step the level-0 adjoint density is mu[ic]
+    int rc;
+    double* out = a.out;
+    if (gT0) {
+        const bool dev = is_device_pointer(gT0);
+        void* dst = dev ? gT0 : (void*)out;
+        const int dd = dev ? gT0_dtype : MR_F64;
+        e = P == MR_F64 ? launch_times_volume<double>(h->g64, (const double*)mu[ic], dd, dst, st)
+                        : launch_times_volume<float>(h->g32, (const float*)mu[ic], dd, dst, st);
+        if (e != cudaSuccess) return cuda_check(e, "mr_adjoint_backward: dL/dT0");
+        if (!dev && (rc = copy_out(h, out, MR_F64, gT0, gT0_dtype, h->ncell, st))) return rc;
+    }
+    if (gU || gV || gW) {
+        double* cU = out + h->ncell;
+        double* cV = cU + h->ncU;
+        double* cW = cV + h->ncV;
+        double* aWc = a.scr;
+        double* aVrow = a.scr + (size_t)(h->Nz + 1) * h->cfg.ny * h->cfg.nx;
+        e = launch_refine_transpose(h->g64, fU, fV, fW, aWc, aVrow, cU, cV, cW, h->ncU, h->ncV, h->ncW, st);
+        if (e != cudaSuccess) return cuda_check(e, "mr_adjoint_backward: refinement transpose");
+        if (gU && (rc = copy_out(h, cU, MR_F64, gU, MR_F64, h->ncU, st))) return rc;
+        if (gV && (rc = copy_out(h, cV, MR_F64, gV, MR_F64, h->ncV, st))) return rc;
+        if (gW && (rc = copy_out(h, cW, MR_F64, gW, MR_F64, h->ncW, st))) return rc;
+    }
+    return cuda_check(cudaStreamSynchronize(st), "mr_adjoint_backward");
 }
 
 }  // extern "C"

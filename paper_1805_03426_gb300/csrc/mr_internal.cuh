@@ -84,6 +84,20 @@ struct mr_handle_s {
     mr::Grid<float> g32;
     size_t stage_bytes = 0;
     int red_blocks = 0;
+    // adjoint state between mr_adjoint_forward and mr_adjoint_backward
+    struct Adjoint {
+        bool ready = false;
+        int64_t S = 0;
+        int ck = 0;
+        std::vector<double> wnu, wvar, mean;   // weights and FP64 means of every level (s = 0..S)
+        void* cp = nullptr;                    // checkpoints: pairs (T^{s-1}, T^s) every ck steps
+        size_t cp_pairs = 0;
+        void* seg = nullptr;                   // recomputed levels of one segment (ck + 1)
+        void* mu = nullptr;                    // three adjoint levels
+        double* face = nullptr;                // dense face gradients (U, V, W), FP64
+        double* scr = nullptr;                 // transpose scratch (full-area W, full-width V), FP64
+        double* out = nullptr;                 // FP64 staging of the outputs (dense T0, coarse U, V, W)
+    } adj;
 };
 
 namespace mr {
@@ -123,6 +137,18 @@ cudaError_t launch_step_fused_f32(const Grid<float>& g, const float* U, const fl
 cudaError_t launch_maxdiv_fused_f32(const Grid<float>& g, const float* U, const float* V,
                                     const float* W, double* partials, int blocks, cudaStream_t st);
 bool fused_supported(const mr_config& cfg, std::string* why);
+cudaError_t launch_refine_transpose(const Grid<double>& g, double* aUs, double* aVs, double* aWs, double* aWc,
+                                    double* aVrow, double* gU, double* gV, double* gW, size_t ncU, size_t ncV,
+                                    size_t ncW, cudaStream_t st);
+template <typename P>
+cudaError_t launch_adj_step(const Grid<P>& g, const P* Us, const P* Vs, const P* Ws, const P* T, const P* Tprev,
+                            const P* Mn, P* Mc, P* Mp, double s_nu, double s_var, double mean_prev, double* gU,
+                            double* gV, double* gW, StepCoef c, bool euler, cudaStream_t st);
+template <typename P>
+cudaError_t launch_adj_direct(const Grid<P>& g, const P* T, double s_nu_bottom, double s_var, double mean, P* mu,
+                              cudaStream_t st);
+template <typename P>
+cudaError_t launch_times_volume(const Grid<P>& g, const P* mu, int dst_dtype, void* out, cudaStream_t st);
 int fused_take_error(cudaStream_t st);   // MR_ERR_TIMEOUT if a fused kernel gave up a wait
 
 }  // namespace mr

@@ -67,6 +67,8 @@ _SIGS = {
     "mr_cfl_dt": (ctypes.c_int, [_VP, _D, ctypes.POINTER(_D), _VP]),
     "mr_set_dt": (ctypes.c_int, [_VP, _D]),
     "mr_debug_index_maps": (ctypes.c_int, [_VP, _VP, ctypes.c_size_t]),
+    "mr_adjoint_forward": (ctypes.c_int, [_VP, _I64, _I32, _VP, _VP, ctypes.POINTER(_D), _VP]),
+    "mr_adjoint_backward": (ctypes.c_int, [_VP, _D, _VP, _I32, _VP, _VP, _VP, _VP]),
 }
 
 
@@ -283,3 +285,27 @@ def mr_debug_index_maps(h: Handle) -> np.ndarray:
     out = np.zeros(n, dtype=np.int32)
     _check(lib().mr_debug_index_maps(h.ptr, out.ctypes.data, n))
     return out
+
+
+def mr_adjoint_forward(h: Handle, nsteps: int, checkpoint_every: int, wnu=None, wvar=None, stream=None) -> float:
+    """Checkpointed forward of nsteps steps; returns the loss (see include/mr.h)."""
+    n = int(nsteps) + 1
+    wnu = None if wnu is None else np.ascontiguousarray(wnu, dtype=np.float64)
+    wvar = None if wvar is None else np.ascontiguousarray(wvar, dtype=np.float64)
+    for w in (wnu, wvar):
+        if w is not None and w.size != n:
+            raise ValueError(f"loss weights need {n} entries")
+    loss = _D()
+    _check(lib().mr_adjoint_forward(h.ptr, int(nsteps), int(checkpoint_every), _ptr(wnu), _ptr(wvar),
+                                    ctypes.byref(loss), _stream(stream)))
+    return loss.value
+
+
+def mr_adjoint_backward(h: Handle, gscale=1.0, gT0=None, gU=None, gV=None, gW=None, stream=None):
+    """Backward sweep: gscale * dL/dT0 (dense) and dL/d(U, V, W) (coarse, FP64)."""
+    s = h.shapes
+    code = MR_F64 if gT0 is None else _dtype_code(gT0)
+    _check(lib().mr_adjoint_backward(
+        h.ptr, float(gscale), _ptr(gT0, _n(s["T"]), None, "gT0"), code,
+        _ptr(gU, _n(s["U"]), np.float64, "gU"), _ptr(gV, _n(s["V"]), np.float64, "gV"),
+        _ptr(gW, _n(s["W"]), np.float64, "gW"), _stream(stream)))
