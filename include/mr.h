@@ -174,6 +174,25 @@ int mr_adjoint_forward(mr_handle h, int64_t nsteps, int32_t checkpoint_every, co
 int mr_adjoint_backward(mr_handle h, double gscale, void* gT0, int32_t gT0_dtype, double* gU, double* gV,
                         double* gW, mr_stream stream);
 
+/* Allocation-free refinement (no counterpart in the paper: an interface for
+ * callers that cannot allocate device memory, e.g. code running inside a
+ * framework whose caching allocator owns the whole device, or a plug-in
+ * forbidden to call cudaMalloc).  Computes the same dense faces as
+ * mr_refine_velocity (FP64 in, FP64 out, Section 3.2) from *cfg alone -- no
+ * handle -- using only a file-scope device scratch array of 32 MiB that every
+ * GPU loading this library holds until the process exits; it allocates nothing.
+ * Its grid and R matrices are rebuilt into that array at every call.  Sizes
+ * whose grid, R matrices and work arrays exceed the 32 MiB give MR_ERR_ARG with
+ * the needed size in mr_last_error().  U, V, W, Us, Vs, Ws must be device
+ * memory (MR_ERR_ARG otherwise); cfg's precision, velocity_mode, Ra, Pr, dt and
+ * plate settings are ignored.  The first call on a device looks the array's
+ * device address up (cudaGetSymbolAddress, with that device current), so make
+ * that first call before any stream capture.  Every call shares the one array:
+ * calls that overlap on the GPU (different streams, or devices sharing nothing
+ * but the host thread's current device) race and corrupt each other. */
+int mr_refine_velocity_noalloc(const mr_config* cfg, const double* U, const double* V, const double* W,
+                               double* Us, double* Vs, double* Ws, mr_stream stream);
+
 /* Integer index maps for testing (synchronous, host buffer): coarse cell of
  * every dense cell along x, y, z, then the three coarse cells of the R window
  * of every coarse cell along x, y, z: Nx+Ny+Nz+3(nx+ny+nz) int32 values.

@@ -69,6 +69,7 @@ _SIGS = {
     "mr_debug_index_maps": (ctypes.c_int, [_VP, _VP, ctypes.c_size_t]),
     "mr_adjoint_forward": (ctypes.c_int, [_VP, _I64, _I32, _VP, _VP, ctypes.POINTER(_D), _VP]),
     "mr_adjoint_backward": (ctypes.c_int, [_VP, _D, _VP, _I32, _VP, _VP, _VP, _VP]),
+    "mr_refine_velocity_noalloc": (ctypes.c_int, [ctypes.POINTER(mr_config), _VP, _VP, _VP, _VP, _VP, _VP, _VP]),
 }
 
 
@@ -309,3 +310,13 @@ def mr_adjoint_backward(h: Handle, gscale=1.0, gT0=None, gU=None, gV=None, gW=No
         h.ptr, float(gscale), _ptr(gT0, _n(s["T"]), None, "gT0"), code,
         _ptr(gU, _n(s["U"]), np.float64, "gU"), _ptr(gV, _n(s["V"]), np.float64, "gV"),
         _ptr(gW, _n(s["W"]), np.float64, "gW"), _stream(stream)))
+
+
+def mr_refine_velocity_noalloc(cfg: mr_config, U, V, W, Us, Vs, Ws, stream=None):
+    """Allocation-free FP64 refinement into caller-owned device arrays (no handle)."""
+    w = 1 if cfg.bc_horizontal == MR_WALLS else 0
+    Nx, Ny, Nz = cfg.nx * cfg.mx, cfg.ny * cfg.my, cfg.nz * cfg.mz
+    n = {"U": cfg.nz * cfg.ny * (cfg.nx + w), "V": cfg.nz * (cfg.ny + w) * cfg.nx, "W": (cfg.nz + 1) * cfg.ny * cfg.nx,
+         "Us": Nz * Ny * (Nx + w), "Vs": Nz * (Ny + w) * Nx, "Ws": (Nz + 1) * Ny * Nx}
+    args = [_ptr(a, n[k], np.float64, k) for a, k in zip((U, V, W, Us, Vs, Ws), ("U", "V", "W", "Us", "Vs", "Ws"))]
+    _check(lib().mr_refine_velocity_noalloc(ctypes.byref(cfg), *args, _stream(stream)))
