@@ -158,7 +158,7 @@ def run_mr(args):
     Nx, Ny, Nz = w["nx"] * w["m"], w["ny"] * w["m"], w["nz"] * w["m"]
     cells = Nx * Ny * Nz
     prec = mr.MR_F32 if args.precision == "f32" else mr.MR_F64
-    mode = {"stored": mr.MR_VEL_STORED, "fused": mr.MR_VEL_FUSED}[args.mode]
+    mode = {"stored": mr.MR_VEL_STORED, "fused": mr.MR_VEL_FUSED, "xfused": mr.MR_VEL_XFUSED}[args.mode]
     stream = torch.cuda.Stream()
     h = _make(mr, w, prec, mode)
     U, V, W, T0 = _inputs(mr, h, w)
@@ -185,13 +185,19 @@ def run_mr(args):
     # roofline of the dominant (only) kernel of the step: one launch per step
     elt = 4 if prec == mr.MR_F32 else 8
     M3 = w["m"] ** 3
-    bytes_per_cell = (3 * elt + 3 * elt / M3) if mode == mr.MR_VEL_FUSED else 6 * elt
+    if mode == mr.MR_VEL_FUSED:      # two scalar levels in, one out, coarse faces
+        bytes_per_cell = 3 * elt + 3 * elt / M3
+    elif mode == mr.MR_VEL_XFUSED:   # two levels in, one out, three coarse-x intermediates (4 ghost columns each side)
+        nx = w["nx"]
+        bytes_per_cell = 3 * elt + 3 * elt * (nx + 8) / (nx * w["m"])
+    else:                            # two levels in, one out, three dense faces
+        bytes_per_cell = 6 * elt
     per_launch = t / args.steps
     peak, peak_kind = _peaks()
     achieved = bytes_per_cell * cells / per_launch / 1e9
     roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
             "frac": round(achieved / peak, 4), "traffic": None, "peak_source": peak_kind,
-            "kernel": "k_fused" if mode == mr.MR_VEL_FUSED else "k_step_stored",
+            "kernel": {mr.MR_VEL_FUSED: "k_fused", mr.MR_VEL_XFUSED: "k_xfused"}.get(mode, "k_step_stored"),
             "bytes_per_cell": round(bytes_per_cell, 3), "launch_ms": round(per_launch * 1e3, 4)}
 
     # FP64 path on the same grid (stored velocity), for the FP32/FP64 ratio
@@ -349,7 +355,7 @@ def main():
     ap.add_argument("--impl", default="mr", choices=["mr", "reference"])
     ap.add_argument("--workload", default="rb512_stretched_f32", choices=sorted(WORKLOADS))
     ap.add_argument("--precision", default="f32", choices=["f32", "f64"])
-    ap.add_argument("--mode", default="fused", choices=["stored", "fused"])
+    ap.add_argument("--mode", default="xfused", choices=["stored", "fused", "xfused"])
     ap.add_argument("--cpu-budget", type=float, default=20.0)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")

@@ -55,7 +55,7 @@ enum {
     MR_ERR_STATE = -6      /* call out of order (e.g. step before set)     */
 };
 enum { MR_F64 = 0, MR_F32 = 1 };               /* precision / buffer dtype */
-enum { MR_VEL_STORED = 0, MR_VEL_FUSED = 1 };  /* dense velocity handling  */
+enum { MR_VEL_STORED = 0, MR_VEL_FUSED = 1, MR_VEL_XFUSED = 2 };  /* dense velocity handling */
 enum { MR_DIRICHLET = 0, MR_ADIABATIC = 1 };   /* plates                   */
 enum { MR_PERIODIC = 0, MR_WALLS = 1 };        /* x and y boundaries       */
 
@@ -73,9 +73,15 @@ typedef struct {
                                  MR_F32: FP32 storage and flux arithmetic.
                                  Reductions are FP64 in both.                 */
     int32_t velocity_mode;    /* MR_VEL_STORED: dense faces kept in HBM;
-                                 MR_VEL_FUSED: refined inside the step kernel
-                                 from the coarse faces, never stored
-                                 (MR_F32, MR_PERIODIC and mx=my=mz only).     */
+                                 MR_VEL_FUSED: every stage of the refinement
+                                 inside the step kernel, from the coarse faces;
+                                 MR_VEL_XFUSED: the z- and y-stages are kept at
+                                 coarse resolution in x (1/mx of the dense face
+                                 count, computed by mr_refine_velocity) and the
+                                 x-stage runs inside the step kernel.  In both
+                                 fused modes the dense faces are never stored
+                                 (MR_F32, MR_PERIODIC, mx=my=mz in {2,4},
+                                 Nx % 64 == 0, Ny % 16 == 0).                 */
     int32_t np_average;       /* N_p of the averaging step (Section 2.2);
                                  <= 0 disables it; default 50                 */
     int32_t bc_plates;        /* MR_DIRICHLET | MR_ADIABATIC                  */

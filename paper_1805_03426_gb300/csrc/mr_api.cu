@@ -214,11 +214,14 @@ static int validate(const mr_config* c, std::string* why)
     if (!(c->ra > 0) || !(c->pr_or_sc > 0) || !isfinite(c->ra * c->pr_or_sc)) { *why = "ra and pr_or_sc must be positive"; return MR_ERR_ARG; }
     if (!(c->dt > 0) || !isfinite(c->dt)) { *why = "dt must be positive"; return MR_ERR_ARG; }
     if (c->precision != MR_F64 && c->precision != MR_F32) { *why = "precision must be MR_F64 or MR_F32"; return MR_ERR_ARG; }
-    if (c->velocity_mode != MR_VEL_STORED && c->velocity_mode != MR_VEL_FUSED) { *why = "bad velocity_mode"; return MR_ERR_ARG; }
+    if (c->velocity_mode != MR_VEL_STORED && c->velocity_mode != MR_VEL_FUSED && c->velocity_mode != MR_VEL_XFUSED) {
+        *why = "bad velocity_mode";
+        return MR_ERR_ARG;
+    }
     if (c->bc_plates != MR_DIRICHLET && c->bc_plates != MR_ADIABATIC) { *why = "bad bc_plates"; return MR_ERR_ARG; }
     if (c->bc_horizontal != MR_PERIODIC && c->bc_horizontal != MR_WALLS) { *why = "bad bc_horizontal"; return MR_ERR_ARG; }
     if (c->diffz_implicit != 0 && c->diffz_implicit != 1) { *why = "diffz_implicit must be 0 or 1"; return MR_ERR_ARG; }
-    if (c->velocity_mode == MR_VEL_FUSED && !fused_supported(*c, why)) return MR_ERR_ARG;
+    if (c->velocity_mode != MR_VEL_STORED && !fused_supported(*c, why)) return MR_ERR_ARG;
     return MR_OK;
 }
 
@@ -264,6 +267,9 @@ void mr_destroy(mr_handle h)
     void* ptrs[] = {b.T[0], b.T[1], b.T[2], b.U64, b.V64, b.W64, b.Us, b.Vs, b.Ws, b.scrW, b.scrV,
                     b.metric, b.red, b.nu2, b.stage, b.tri};
     for (void* p : ptrs)
+        if (p) cudaFree(p);
+    void* xptrs[] = {b.xwy, b.xuo, b.xvr, b.xlc};
+    for (void* p : xptrs)
         if (p) cudaFree(p);
     void* aptrs[] = {h->adj.cp, h->adj.seg, h->adj.mu, h->adj.face, h->adj.scr, h->adj.out};
     for (void* p : aptrs)
@@ -350,6 +356,14 @@ int mr_create(const mr_config* cfg, mr_handle* out)
     h->stage_bytes = std::min<size_t>((size_t)64 << 20, std::max<size_t>(h->ncell * 8, 1 << 16));
     alloc(&b.stage, h->stage_bytes);
     if (c.diffz_implicit) alloc(&b.tri, h->ncell * h->elt);
+    if (c.velocity_mode == MR_VEL_XFUSED) {
+        b.nxg = c.nx + 8;
+        alloc((void**)&b.xwy, (size_t)(h->Nz + 1) * h->Ny * b.nxg * 4);
+        alloc((void**)&b.xuo, (size_t)h->Nz * h->Ny * b.nxg * 4);
+        alloc((void**)&b.xvr, (size_t)h->Nz * (h->Ny + 1) * b.nxg * 4);
+        alloc((void**)&b.xlc, (size_t)h->Nz * 12 * 4);
+        alloc(&b.scrW, (size_t)(h->Nz + 1) * c.ny * c.nx * h->elt);
+    }
     if (e != cudaSuccess) {
         int r = cuda_check(e, "mr_create: device allocation");
         mr_destroy(h);
@@ -368,6 +382,35 @@ int mr_create(const mr_config* cfg, mr_handle* out)
     }
     rc = upload_metric<double>(h, (char*)b.metric, dwin, h->g64);
     if (!rc) rc = upload_metric<float>(h, (char*)b.metric + mb64, dwin, h->g32);
+    if (!rc && b.xlc) {
+        // per-layer constants of the split-x fused kernel: dz, 1/dz, the two face
+        // interpolation weights below and above, kappa/(dz d) below and above, dx/dz
+        std::vector<float> lc((size_t)h->Nz * 12, 0.f);
+        const bool dir = c.bc_plates == MR_DIRICHLET;
+        const double dx = c.lx / h->Nx;
+        for (int k = 0; k < h->Nz; ++k) {
+            float* q = &lc[(size_t)k * 12];
+            const double dzk = h->dz[k];
+            const double below = k > 0 ? h->zc[k] - h->zc[k - 1] : h->zc[0] - h->zf[0];
+            const double above = k < h->Nz - 1 ? h->zc[k + 1] - h->zc[k] : h->zf[h->Nz] - h->zc[h->Nz - 1];
+            q[0] = (float)dzk;
+            q[1] = (float)(1.0 / dzk);
+            if (k > 0) {
+                q[2] = (float)(dzk / (h->dz[k - 1] + dzk));
+                q[3] = (float)(h->dz[k - 1] / (h->dz[k - 1] + dzk));
+            }
+            if (k < h->Nz - 1) {
+                q[4] = (float)(h->dz[k + 1] / (dzk + h->dz[k + 1]));
+                q[5] = (float)(dzk / (dzk + h->dz[k + 1]));
+            }
+            q[6] = (k > 0 || dir) ? (float)(h->kappa / (dzk * below)) : 0.f;
+            q[7] = (k < h->Nz - 1 || dir) ? (float)(h->kappa / (dzk * above)) : 0.f;
+            q[8] = (float)(dx / dzk);
+        }
+        rc = cuda_check(cudaMemcpy(b.xlc, lc.data(), lc.size() * 4, cudaMemcpyHostToDevice), "mr_create: layer constants");
+        // x is uniform and periodic: every coarse cell has the same R_x rows
+        for (int q = 0; q < 12; ++q) b.xrx[q] = (float)h->Rx[(size_t)(q / 3) * 3 + q % 3];
+    }
     if (rc) {
         mr_destroy(h);
         return rc;
@@ -473,8 +516,13 @@ int mr_refine_velocity(mr_handle h, const double* U, const double* V, const doub
         if ((rc = copy_in(h, b.V64, MR_F64, b.Vc, MR_F32, h->ncV, st))) return rc;
         if ((rc = copy_in(h, b.W64, MR_F64, b.Wc, MR_F32, h->ncW, st))) return rc;
     }
+    if (h->cfg.velocity_mode == MR_VEL_XFUSED) {
+        cudaError_t e = launch_xfused_prep(h->g32, (const float*)b.Uc, (const float*)b.Vc, (const float*)b.Wc,
+                                           (float*)b.scrW, b.xwy, b.xuo, b.xvr, b.nxg, st);
+        if (e != cudaSuccess) return cuda_check(e, "mr_refine_velocity: split-x intermediates");
+    }
     void *dUs = b.Us, *dVs = b.Vs, *dWs = b.Ws;
-    if (h->cfg.velocity_mode == MR_VEL_FUSED) {
+    if (h->cfg.velocity_mode != MR_VEL_STORED) {
         if (!Us) {
             h->have_velocity = true;
             return MR_OK;
@@ -517,7 +565,7 @@ int mr_get_scalar(mr_handle h, void* T, void* Tprev, int32_t dtype, mr_stream st
     if (!h->have_scalar) return set_error(MR_ERR_STATE, "mr_get_scalar: no scalar set");
     cudaStream_t st = (cudaStream_t)stream;
     int rc;
-    if (h->cfg.velocity_mode == MR_VEL_FUSED && fused_take_error(st) == MR_ERR_TIMEOUT)
+    if (h->cfg.velocity_mode != MR_VEL_STORED && fused_take_error(st) == MR_ERR_TIMEOUT)
         return set_error(MR_ERR_TIMEOUT, "mr_get_scalar: a fused step kernel gave up a bounded wait");
     if (T && (rc = copy_out(h, h->buf.T[h->ic], h->cfg.precision, T, dtype, h->ncell, st))) return rc;
     if (Tprev && (rc = copy_out(h, h->buf.T[h->ip], h->cfg.precision, Tprev, dtype, h->ncell, st))) return rc;
@@ -543,6 +591,9 @@ int mr_scalar_step(mr_handle h, int64_t nsteps, mr_stream stream)
                                            (const double*)Tm1, (const double*)b.T[h->ic], (double*)b.T[in], c,
                                            implz, st);
             if (e == cudaSuccess && implz) e = launch_zsolve<double>(h->g64, (double*)b.T[in], 0.5 * c.gdt, (double*)b.tri, st);
+        } else if (h->cfg.velocity_mode == MR_VEL_XFUSED) {
+            e = launch_step_xfused_f32(h->g32, b.xwy, b.xuo, b.xvr, b.nxg, b.xlc, b.xrx, (const float*)Tm1,
+                                       (const float*)b.T[h->ic], (float*)b.T[in], c, st);
         } else if (h->cfg.velocity_mode == MR_VEL_FUSED) {
             e = launch_step_fused_f32(h->g32, (const float*)b.Uc, (const float*)b.Vc, (const float*)b.Wc,
                                       (const float*)Tm1, (const float*)b.T[h->ic], (float*)b.T[in], c, st);
@@ -588,7 +639,9 @@ static int max_divergence(mr_handle h, double* out, cudaStream_t st)
 {
     cudaError_t e;
     const DeviceBuffers& b = h->buf;
-    if (h->cfg.velocity_mode == MR_VEL_FUSED)
+    if (h->cfg.velocity_mode == MR_VEL_XFUSED)
+        e = launch_maxdiv_xfused_f32(h->g32, b.xwy, b.xuo, b.xvr, b.nxg, b.xlc, b.xrx, b.red, h->red_blocks, st);
+    else if (h->cfg.velocity_mode == MR_VEL_FUSED)
         e = launch_maxdiv_fused_f32(h->g32, (const float*)b.Uc, (const float*)b.Vc, (const float*)b.Wc, b.red,
                                     h->red_blocks, st);
     else if (h->cfg.precision == MR_F64)
@@ -612,7 +665,7 @@ int mr_scalar_stats(mr_handle h, mr_stats* out, mr_stream stream)
     if (!h || !out) return set_error(MR_ERR_ARG, "mr_scalar_stats: NULL argument");
     if (!h->have_scalar) return set_error(MR_ERR_STATE, "mr_scalar_stats: no scalar set");
     cudaStream_t st = (cudaStream_t)stream;
-    if (h->cfg.velocity_mode == MR_VEL_FUSED && fused_take_error(st) == MR_ERR_TIMEOUT)
+    if (h->cfg.velocity_mode != MR_VEL_STORED && fused_take_error(st) == MR_ERR_TIMEOUT)
         return set_error(MR_ERR_TIMEOUT, "mr_scalar_stats: a fused step kernel gave up a bounded wait");
     const void* T = h->buf.T[h->ic];
     const double dxdy = (h->cfg.lx / h->Nx) * (h->cfg.ly / h->Ny);
@@ -658,7 +711,7 @@ int mr_cfl_dt(mr_handle h, double cfl, double* dt_out, mr_stream stream)
     DeviceBuffers& b = h->buf;
     const void *us = b.Us, *vs = b.Vs, *ws = b.Ws;
     bool tmp = false;
-    if (h->cfg.velocity_mode == MR_VEL_FUSED) {
+    if (h->cfg.velocity_mode != MR_VEL_STORED) {
         // dense faces are not kept: refine into temporary buffers once
         void *a = nullptr, *bb = nullptr, *c = nullptr;
         cudaError_t e = cudaMalloc(&a, h->nU * h->elt);

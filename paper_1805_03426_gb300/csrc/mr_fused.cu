@@ -27,9 +27,12 @@
 #include <string.h>
 
 #include "mr_internal.cuh"
+#include "mr_ptx.cuh"
 
 namespace mr {
 namespace {
+
+using namespace ptx;
 
 constexpr int kTX = 64, kTY = 16;
 constexpr int kBX = kTX + 8, kBY = kTY + 2;           // TMA box (floats)
@@ -38,8 +41,6 @@ constexpr int kSlotFloats = ((kPlaneFloats * 4 + 127) / 128) * 128 / 4;  // 128-
 constexpr int kThreads = 256;                          // consumer threads (8 warps)
 constexpr int kThreadsAll = kThreads + 32;             // + one producer warp
 constexpr uint32_t kPlaneBytes = kPlaneFloats * 4;
-constexpr long kWaitLimit = 1L << 26;                  // bounded mbarrier wait: iterations ...
-constexpr unsigned long long kWaitNs = 1000000000ull;  // ... and wall time (1 s)
 constexpr float kTBottom = 0.5f, kTTop = -0.5f;
 
 template <int M>
@@ -67,83 +68,6 @@ struct Tile {
     static constexpr size_t bytes = (size_t)(oBar + 2 * NB) * 8;
 };
 
-__device__ __forceinline__ uint32_t sa(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ void mbar_init(uint64_t* b, uint32_t n)
-{
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(sa(b)), "r"(n) : "memory");
-}
-__device__ __forceinline__ void mbar_expect_tx(uint64_t* b, uint32_t bytes)
-{
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(sa(b)), "r"(bytes) : "memory");
-}
-__device__ __forceinline__ void mbar_arrive(uint64_t* b)
-{
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(sa(b)) : "memory");
-}
-// Barrier among the consumer warps only (the producer warp never joins).
-__device__ __forceinline__ void consumers_sync()
-{
-    asm volatile("barrier.cta.sync 1, %0;" ::"n"(kThreads) : "memory");
-}
-__device__ __forceinline__ bool consumers_sync_or(bool v)
-{
-    uint32_t r;
-    asm volatile(
-        "{\n\t.reg .pred p, q;\n\t"
-        "setp.ne.u32 q, %1, 0;\n\t"
-        "barrier.cta.red.or.pred p, 1, %2, q;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(r)
-        : "r"((uint32_t)v), "n"(kThreads)
-        : "memory");
-    return r != 0;
-}
-__device__ __forceinline__ bool mbar_test(uint64_t* b, uint32_t parity)
-{
-    uint32_t ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(ok)
-        : "r"(sa(b)), "r"(parity), "n"(20000)
-        : "memory");
-    return ok != 0;
-}
-__device__ __forceinline__ unsigned long long global_ns()
-{
-    unsigned long long t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
-// Bounded wait (iteration count and wall time); true on success.
-__device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity)
-{
-    if (mbar_test(b, parity)) return true;
-    const unsigned long long t0 = global_ns();
-    for (long it = 0; it < kWaitLimit; ++it) {
-        if (mbar_test(b, parity)) return true;
-        if ((it & 255) == 0 && global_ns() - t0 > kWaitNs) break;
-    }
-    return false;
-}
-__device__ __forceinline__ void tma_plane(float* dst, const CUtensorMap* map, int x, int y, int z, uint64_t* bar)
-{
-    asm volatile(
-        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];"
-        ::"r"(sa(dst)), "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(sa(bar))
-        : "memory");
-}
-__device__ __forceinline__ void cp_async4(float* dst, const float* src)
-{
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(sa(dst)), "l"(src) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
-
-__device__ __forceinline__ int wrap(int i, int n) { return i < 0 ? i + n : (i >= n ? i - n : i); }
-
 struct FusedArgs {
     Grid<float> g;
     const float* U;      // coarse faces [nz][ny][nx], [nz+1][ny][nx] for W
@@ -164,8 +88,8 @@ __device__ __forceinline__ void issue_plane(float* sT, uint64_t* bar, const CUte
 {
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     mbar_expect_tx(&bar[s], 2 * kPlaneBytes);
-    tma_plane(sT + (2 * s + 0) * kSlotFloats, mn, i0 - 4, j0 - 1, z, &bar[s]);
-    tma_plane(sT + (2 * s + 1) * kSlotFloats, mm, i0 - 4, j0 - 1, z, &bar[s]);
+    tma_3d(sT + (2 * s + 0) * kSlotFloats, mn, i0 - 4, j0 - 1, z, &bar[s]);
+    tma_3d(sT + (2 * s + 1) * kSlotFloats, mm, i0 - 4, j0 - 1, z, &bar[s]);
 }
 
 template <int M, bool DIVONLY>
@@ -273,7 +197,7 @@ k_fused(const __grid_constant__ CUtensorMap tmn, const __grid_constant__ CUtenso
     for (int K = K0; K < K1; ++K) {
         const int bb = (K - K0) & 1;
         cp_async_wait_all();
-        if (consumers_sync_or(fail)) break;       // uniform exit of every consumer
+        if (consumers_sync_or<kThreads>(fail)) break;       // uniform exit of every consumer
         if (K + 1 < K1) load_coarse(K + 1, bb ^ 1);
         const float* ccu = cu + bb * 3 * UY * UX;
         const float* ccv = cv + bb * 3 * VY * VX;
@@ -302,7 +226,7 @@ k_fused(const __grid_constant__ CUtensorMap tmn, const __grid_constant__ CUtenso
                     Vz[rr * VX + x] = r0 * ccv[vj * VX + x] + r1 * ccv[(VY + vj) * VX + x] + r2 * ccv[(2 * VY + vj) * VX + x];
             }
         }
-        consumers_sync();
+        consumers_sync<kThreads>();
         // A2: stage Z slab balance, top-down, one thread per coarse column
         for (int t = tid; t < WY * WX; t += kThreads) {
             const int wj = t / WX, wi = t % WX;
@@ -319,7 +243,7 @@ k_fused(const __grid_constant__ CUtensorMap tmn, const __grid_constant__ CUtenso
                 Wc[c * WY * WX + t] = F / (DX * DY);
             }
         }
-        consumers_sync();
+        consumers_sync<kThreads>();
         // S1: y-split of Wc on the M+1 planes; outer U sub-faces of the M layers (R_y)
         for (int row = warp; row < (M + 1) * kTY + M * kTY; row += NW) {
             if (row < (M + 1) * kTY) {
@@ -336,7 +260,7 @@ k_fused(const __grid_constant__ CUtensorMap tmn, const __grid_constant__ CUtenso
                     Uo[rr * UX + x] = ry[0] * uz[x] + ry[1] * uz[UX + x] + ry[2] * uz[2 * UX + x];
             }
         }
-        consumers_sync();
+        consumers_sync<kThreads>();
         // S2: stage Y, full-width V of every dense row by row balance (running
         // sum from the coarse south face), for the M layers
         for (int row = warp; row < M * (kTY + 1); row += NW) {
@@ -357,7 +281,7 @@ k_fused(const __grid_constant__ CUtensorMap tmn, const __grid_constant__ CUtenso
                 Vr[row * VX + x] = b == 0 ? vz[x] : G / (DX * dzk);
             }
         }
-        consumers_sync();
+        consumers_sync<kThreads>();
 
         // the M dense layers of the slab, free-running (no block barrier)
         for (int c = 0; c < M; ++c) {
@@ -496,7 +420,7 @@ k_fused(const __grid_constant__ CUtensorMap tmn, const __grid_constant__ CUtenso
             }
         }
     }
-    if (consumers_sync_or(fail)) {
+    if (consumers_sync_or<kThreads>(fail)) {
         if (tid == 0) atomicExch(A.err, MR_ERR_TIMEOUT);
         return;
     }
@@ -504,7 +428,7 @@ k_fused(const __grid_constant__ CUtensorMap tmn, const __grid_constant__ CUtenso
         // block max -> device max (non-negative doubles order as their bit patterns)
         for (int o = 16; o > 0; o >>= 1) dmax = fmaxf(dmax, __shfl_down_sync(0xffffffffu, dmax, o));
         if (lane == 0) red[warp] = dmax;
-        consumers_sync();
+        consumers_sync<kThreads>();
         if (tid == 0) {
             float m = 0.f;
             for (int w = 0; w < NW; ++w) m = fmaxf(m, red[w]);

@@ -62,6 +62,14 @@ struct DeviceBuffers {
     double* nu2 = nullptr;                     // plate Nusselt numbers (2 doubles)
     void* stage = nullptr;                     // conversion staging buffer
     void* tri = nullptr;                       // implicit-z work (2 * Nz per column)
+    // MR_VEL_XFUSED: coarse-x intermediates of the z- and y-stages (FP32,
+    // nxg = nx + 8 columns with 4 periodic ghosts each side) and layer constants
+    float* xwy = nullptr;                      // [Nz+1][Ny][nxg]
+    float* xuo = nullptr;                      // [Nz][Ny][nxg]
+    float* xvr = nullptr;                      // [Nz][Ny+1][nxg]
+    float* xlc = nullptr;                      // [Nz][12]
+    float xrx[12] = {0};                       // R_x rows of the 4 cells of a 4-cell segment
+    int nxg = 0;
 };
 
 }  // namespace mr
@@ -137,6 +145,16 @@ cudaError_t launch_step_fused_f32(const Grid<float>& g, const float* U, const fl
 cudaError_t launch_maxdiv_fused_f32(const Grid<float>& g, const float* U, const float* V,
                                     const float* W, double* partials, int blocks, cudaStream_t st);
 bool fused_supported(const mr_config& cfg, std::string* why);
+int* fused_error_flag();
+template <typename P>
+cudaError_t launch_column_balance(const Grid<P>& g, const P* U, const P* V, const P* W, P* scrW, cudaStream_t st);
+cudaError_t launch_xfused_prep(const Grid<float>& g, const float* U, const float* V, const float* W, float* scrW,
+                               float* WY, float* UO, float* VR, int nxg, cudaStream_t st);
+cudaError_t launch_step_xfused_f32(const Grid<float>& g, const float* WY, const float* UO, const float* VR, int nxg,
+                                   const float* lc, const float* rx12, const float* Tm1, const float* T, float* Tp1,
+                                   StepCoef c, cudaStream_t st);
+cudaError_t launch_maxdiv_xfused_f32(const Grid<float>& g, const float* WY, const float* UO, const float* VR, int nxg,
+                                     const float* lc, const float* rx12, double* partials, int blocks, cudaStream_t st);
 cudaError_t launch_refine_transpose(const Grid<double>& g, double* aUs, double* aVs, double* aWs, double* aWc,
                                     double* aVrow, double* gU, double* gV, double* gW, size_t ncU, size_t ncV,
                                     size_t ncW, cudaStream_t st);

@@ -245,6 +245,20 @@ cudaError_t launch_refine(const Grid<P>& g, const P* U, const P* V, const P* W, 
     return cudaGetLastError();
 }
 
+// Stage Z slab balance alone (full-area W on the inner planes), for the
+// split-x fused path.
+template <typename P>
+cudaError_t launch_column_balance(const Grid<P>& g, const P* U, const P* V, const P* W, P* scrW, cudaStream_t st)
+{
+    if (g.mz > 1) {
+        const size_t n = (size_t)g.nz * g.ny * g.nx;
+        k_column_balance<P><<<blocks_for(n), kThreads, 0, st>>>(g, U, V, W, scrW);
+    }
+    return cudaGetLastError();
+}
+template cudaError_t launch_column_balance<float>(const Grid<float>&, const float*, const float*, const float*,
+                                                  float*, cudaStream_t);
+
 template cudaError_t launch_refine<double>(const Grid<double>&, const double*, const double*, const double*,
                                            double*, double*, double*, double*, double*, cudaStream_t);
 template cudaError_t launch_refine<float>(const Grid<float>&, const float*, const float*, const float*,

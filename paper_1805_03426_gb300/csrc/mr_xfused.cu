@@ -1,0 +1,497 @@
+// MR_VEL_XFUSED: the FP32 step kernel with the x-stage of the refinement fused
+// in, fed by stored coarse-x intermediates of the z- and y-stages.
+//
+// The refinement (Section 3.2) is separable by stage.  Its z- and y-stages
+// (slab balance, y-splits, row balance) produce, at coarse resolution in x,
+//   WY[k][j][I]  full-coarse-width W on dense plane k, dense row j (R_y of the
+//                slab-balanced full-area W),
+//   UO[k][j][I]  the outer U sub-face of coarse x-face I (R_y R_z of U),
+//   VR[k][j][I]  the full-coarse-width V on dense y-face j (row balance),
+// which depend on the coarse velocity only; they are computed once per
+// mr_refine_velocity (1/M_x of the dense face count, with 4 periodic ghost
+// columns each side so that every TMA box stays in bounds and 16-byte
+// aligned).  The step kernel streams them with the two scalar levels through
+// one TMA ring (one producer warp, full/empty mbarriers) and performs the
+// x-stage -- R_x splits of W and V and the west-to-east cell balance for U --
+// in registers, followed by the finite-volume update (Eq. 5) with the
+// Euler-leapfrog coefficients (Section 2.2).  The dense velocity is never
+// stored and the layer loop has no block-wide barrier.
+//
+// Supported: FP32, periodic x and y, mx = my = mz = M in {2, 4},
+// Nx % 64 == 0, Ny % 16 == 0, explicit diffusion.
+#include <stdlib.h>
+#include <string.h>
+
+#include "mr_internal.cuh"
+#include "mr_ptx.cuh"
+
+namespace mr {
+namespace {
+
+using namespace ptx;
+
+constexpr int kTX = 64, kTY = 16;
+constexpr int kBX = kTX + 8, kBY = kTY + 2;            // scalar plane box (floats)
+constexpr int kPlaneFloats = kBX * kBY;
+constexpr int kPlaneSlot = ((kPlaneFloats * 4 + 127) / 128) * 128 / 4;
+constexpr uint32_t kPlaneBytes = kPlaneFloats * 4;
+constexpr int kThreads = 256;                           // consumer threads (8 warps)
+constexpr int kThreadsAll = kThreads + 32;              // + one producer warp
+constexpr float kTBottom = 0.5f, kTTop = -0.5f;
+
+template <int M>
+struct XT {
+    static constexpr int CX = kTX / M;
+    static constexpr int BXC = CX + 8;                  // coarse box width: columns I0-4 .. I0+CX+3
+    static constexpr int NB = (M == 4) ? 6 : 5;         // ring slots
+    // one ring slot (floats): T^n plane, T^{n-1} plane, then the bundle of one layer
+    static constexpr int oTn = 0, oTm = kPlaneSlot;
+    static constexpr int oWY = 2 * kPlaneSlot;          // [2][TY][BXC]   planes k, k+1
+    static constexpr int oUO = oWY + 2 * kTY * BXC;     // [TY][BXC]
+    static constexpr int oVR = oUO + kTY * BXC;         // [TY+1][BXC]
+    static constexpr int slot = (((oVR + (kTY + 1) * BXC) * 4 + 127) / 128) * 128 / 4;
+    static constexpr uint32_t bundle_bytes = (uint32_t)(2 * kTY * BXC + kTY * BXC + (kTY + 1) * BXC) * 4;
+    static constexpr int oRed = NB * slot;              // 64 floats
+    static constexpr int oBar = ((oRed + 64) * 4 + 7) / 8;
+    static constexpr size_t bytes = (size_t)(oBar + 2 * NB) * 8;
+};
+
+struct XArgs {
+    Grid<float> g;
+    const float* Tn;     // T^s (global, for the periodic halo of edge threads)
+    const float* Tm;     // T^{s-1}
+    float* Tp1;          // T^{s+1}
+    const float* lc;     // [Nz][12] per-layer constants
+    float a, b, gdt;
+    int kcl;             // dense layers per CTA chunk
+    int* err;
+    unsigned long long* divmax;
+    float rx[4][3];      // R_x rows of the 4 cells of a segment (x is uniform and the
+                         // segment starts on a coarse cell boundary, so these are the
+                         // same for every thread: kept in the constant bank)
+};
+
+template <int M, bool DIVONLY>
+__global__ void __launch_bounds__(kThreadsAll, 2)
+k_xfused(const __grid_constant__ CUtensorMap tmn, const __grid_constant__ CUtensorMap tmm,
+         const __grid_constant__ CUtensorMap twy, const __grid_constant__ CUtensorMap tuo,
+         const __grid_constant__ CUtensorMap tvr, const XArgs A)
+{
+    using L = XT<M>;
+    constexpr int NB = L::NB, BXC = L::BXC, NC = 4 / M, NW = kThreads / 32;
+    extern __shared__ __align__(128) float sm[];
+    float* red = sm + L::oRed;
+    uint64_t* full = reinterpret_cast<uint64_t*>(sm) + L::oBar;
+    uint64_t* empty = full + NB;
+
+    const Grid<float>& g = A.g;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int i0 = blockIdx.y * kTX, j0 = blockIdx.z * kTY;
+    const int I0 = i0 / M;
+    const int k0 = blockIdx.x * A.kcl;
+    const int k1 = min(k0 + A.kcl, g.Nz);
+    if (k0 >= k1) return;
+    const int nrings = k1 - k0 + 2;              // ring r: plane k0-1+r and the bundle of layer k0+r-2
+
+    if (tid == 0) {
+        for (int s = 0; s < NB; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], kThreads);
+        }
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+
+    // ---------------------------------------------------------------- producer warp
+    if (warp == NW) {
+        if (lane != 0) return;
+        for (int r = 0; r < nrings; ++r) {
+            const int s = r % NB;
+            if (r >= NB && !mbar_wait(&empty[s], ((r / NB) - 1) & 1)) {
+                atomicExch(A.err, MR_ERR_TIMEOUT);   // consumers then time out on full[]
+                break;
+            }
+            float* slot = sm + s * L::slot;
+            const bool bundle = (r >= 2);
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            mbar_expect_tx(&full[s], (DIVONLY ? 0u : 2 * kPlaneBytes) + (bundle ? L::bundle_bytes : 0u));
+            if (!DIVONLY) {
+                tma_3d(slot + L::oTn, &tmn, i0 - 4, j0 - 1, k0 - 1 + r, &full[s]);
+                tma_3d(slot + L::oTm, &tmm, i0 - 4, j0 - 1, k0 - 1 + r, &full[s]);
+            }
+            if (bundle) {
+                const int kb = k0 + r - 2;
+                tma_3d(slot + L::oWY, &twy, I0, j0, kb, &full[s]);
+                tma_3d(slot + L::oUO, &tuo, I0, j0, kb, &full[s]);
+                tma_3d(slot + L::oVR, &tvr, I0, j0, kb, &full[s]);
+            }
+        }
+        return;
+    }
+
+    // ---------------------------------------------------------------- consumer warps
+    const float dx = g.dx, dy = g.dy, fx_y = dx / dy;
+    const int seg = tid & 15, jl = tid >> 4;     // this thread's 4-cell segment of dense row jl
+    const int il0 = seg * 4, cb0 = il0 / M;      // first coarse column of the segment (tile-local)
+    const auto& rx = A.rx;
+    const bool wrap_w = (i0 == 0 && seg == 0), wrap_e = (i0 + kTX == g.Nx && seg == 15);
+    const bool wrap_s = (j0 == 0 && jl == 0), wrap_n = (j0 + kTY == g.Ny && jl == kTY - 1);
+
+    bool fail = false;
+    float dmax = 0.f;
+    const float hix = 0.5f * g.inv_dx, hiy = 0.5f * g.inv_dy, kx2 = g.kx2, ky2 = g.ky2;
+    const float ca = A.a, cbb = A.b, gdt = A.gdt;
+    // ring bookkeeping without divisions: slots of planes k-1, k, k+1 and the
+    // next (slot, parity) to wait for
+    int sb = 0, sc = 1, st = 2;
+    int wslot = 0, wpar = 0, waited = 0;
+    const size_t plane = (size_t)g.Nx * g.Ny;
+    float* outp = A.Tp1 + (size_t)k0 * plane + (size_t)(j0 + jl) * g.Nx + i0 + il0;
+    const float* gn = A.Tn + (size_t)k0 * plane;
+    const float* gm = A.Tm + (size_t)k0 * plane;
+    const int o = (jl + 1) * kBX + il0 + 4;          // this segment's first cell in a plane box
+
+    for (int k = k0; k < k1; ++k) {
+        // layer constants: dz, 1/dz, wlo_b, whi_b | wlo_t, whi_t, cdn, cup | dx/dz
+        const float4* lq = reinterpret_cast<const float4*>(A.lc + 12 * k);
+        const float4 c0 = __ldg(lq), c1 = __ldg(lq + 1);
+        const float inv_dz = c0.y, wlo_b = c0.z, whi_b = c0.w, wlo_t = c1.x, whi_t = c1.y, cdn = c1.z, cup = c1.w;
+        const float fx_z = __ldg(A.lc + 12 * k + 8);
+        const int need = k - k0 + 2;             // ring of plane k+1 and of this layer's bundle
+        while (!fail && waited <= need) {
+            if (!mbar_wait(&full[wslot], wpar)) { fail = true; break; }
+            ++waited;
+            if (++wslot == NB) { wslot = 0; wpar ^= 1; }
+        }
+        if (!fail) {
+            const float* bun = sm + st * L::slot;
+            float wb[4], wt[4], vs[4], vn[4], us[5];
+            {
+                // R_x splits of the full-width W (planes k, k+1) and V (faces jl, jl+1);
+                // bundle column xb holds coarse column I0 - 4 + xb
+                const float* yb = bun + L::oWY + jl * BXC + cb0 + 3;
+                const float* yt = yb + kTY * BXC;
+                const float* rs = bun + L::oVR + jl * BXC + cb0 + 3;
+                const float* rn = rs + BXC;
+#pragma unroll
+                for (int a = 0; a < 4; ++a) {
+                    const int cb = a / M;
+                    wb[a] = rx[a][0] * yb[cb] + rx[a][1] * yb[cb + 1] + rx[a][2] * yb[cb + 2];
+                    wt[a] = rx[a][0] * yt[cb] + rx[a][1] * yt[cb + 1] + rx[a][2] * yt[cb + 2];
+                    vs[a] = rx[a][0] * rs[cb] + rx[a][1] * rs[cb + 1] + rx[a][2] * rs[cb + 2];
+                    vn[a] = rx[a][0] * rn[cb] + rx[a][1] * rn[cb + 1] + rx[a][2] * rn[cb + 2];
+                }
+                // stage X: cell balance, west to east, in velocity units
+                const float* ur = bun + L::oUO + jl * BXC + cb0 + 4;   // outer face of coarse column cb0
+#pragma unroll
+                for (int q = 0; q < NC; ++q) {
+                    float h = ur[q];
+                    us[q * M] = h;
+#pragma unroll
+                    for (int a = 0; a < M - 1; ++a) {
+                        const int m = q * M + a;
+                        h = h - (vn[m] - vs[m]) * fx_y - (wt[m] - wb[m]) * fx_z;
+                        us[m + 1] = h;
+                    }
+                }
+                us[4] = ur[NC];
+            }
+            if (DIVONLY) {
+#pragma unroll
+                for (int a = 0; a < 4; ++a) {
+                    const float d = (us[a + 1] - us[a]) * g.inv_dx + (vn[a] - vs[a]) * g.inv_dy + (wt[a] - wb[a]) * inv_dz;
+                    dmax = fmaxf(dmax, fabsf(d));
+                }
+            } else {
+                const float* Pn_b = sm + sb * L::slot + L::oTn;
+                const float* Pm_b = sm + sb * L::slot + L::oTm;
+                const float* Pn_c = sm + sc * L::slot + L::oTn;
+                const float* Pm_c = sm + sc * L::slot + L::oTm;
+                const float* Pn_t = sm + st * L::slot + L::oTn;
+                const float* Pm_t = sm + st * L::slot + L::oTm;
+                const float4 tc4 = *reinterpret_cast<const float4*>(Pn_c + o);
+                float4 ts4 = *reinterpret_cast<const float4*>(Pn_c + o - kBX);
+                float4 tn4 = *reinterpret_cast<const float4*>(Pn_c + o + kBX);
+                const float4 dc4 = *reinterpret_cast<const float4*>(Pm_c + o);
+                float4 ds4 = *reinterpret_cast<const float4*>(Pm_c + o - kBX);
+                float4 dn4 = *reinterpret_cast<const float4*>(Pm_c + o + kBX);
+                // in-row neighbours from the adjacent segments (16 lanes per row)
+                float tw = __shfl_up_sync(0xffffffffu, tc4.w, 1), te = __shfl_down_sync(0xffffffffu, tc4.x, 1);
+                float dw = __shfl_up_sync(0xffffffffu, dc4.w, 1), de = __shfl_down_sync(0xffffffffu, dc4.x, 1);
+                if (seg == 0) { tw = Pn_c[o - 1]; dw = Pm_c[o - 1]; }
+                if (seg == 15) { te = Pn_c[o + 4]; de = Pm_c[o + 4]; }
+                if (wrap_w | wrap_e | wrap_s | wrap_n) {
+                    // the box holds zeros beyond the domain: fetch the periodic images
+                    const size_t row = (size_t)(j0 + jl) * g.Nx;
+                    if (wrap_w) { tw = gn[row + g.Nx - 1]; dw = gm[row + g.Nx - 1]; }
+                    if (wrap_e) { te = gn[row]; de = gm[row]; }
+                    if (wrap_s) {
+                        const size_t r2 = (size_t)(g.Ny - 1) * g.Nx + i0 + il0;
+                        ts4 = *reinterpret_cast<const float4*>(gn + r2);
+                        ds4 = *reinterpret_cast<const float4*>(gm + r2);
+                    }
+                    if (wrap_n) {
+                        tn4 = *reinterpret_cast<const float4*>(gn + i0 + il0);
+                        dn4 = *reinterpret_cast<const float4*>(gm + i0 + il0);
+                    }
+                }
+                // planes below / above: zero-filled beyond the plates, where the plate
+                // W is exactly zero and the plate value enters the diffusion below
+                const float4 tb4 = *reinterpret_cast<const float4*>(Pn_b + o);
+                const float4 db4 = *reinterpret_cast<const float4*>(Pm_b + o);
+                const float4 tt4 = *reinterpret_cast<const float4*>(Pn_t + o);
+                const float4 dt4 = *reinterpret_cast<const float4*>(Pm_t + o);
+                const bool bot = (k == 0), top = (k == g.Nz - 1);
+                const float tcv[6] = {tw, tc4.x, tc4.y, tc4.z, tc4.w, te};
+                const float dcv[6] = {dw, dc4.x, dc4.y, dc4.z, dc4.w, de};
+                const float tsv[4] = {ts4.x, ts4.y, ts4.z, ts4.w}, tnv[4] = {tn4.x, tn4.y, tn4.z, tn4.w};
+                const float dsv[4] = {ds4.x, ds4.y, ds4.z, ds4.w}, dnv[4] = {dn4.x, dn4.y, dn4.z, dn4.w};
+                const float tbv[4] = {tb4.x, tb4.y, tb4.z, tb4.w}, ttv[4] = {tt4.x, tt4.y, tt4.z, tt4.w};
+                float dbv[4] = {db4.x, db4.y, db4.z, db4.w}, dtv[4] = {dt4.x, dt4.y, dt4.z, dt4.w};
+                if (bot) { dbv[0] = dbv[1] = dbv[2] = dbv[3] = kTBottom; }
+                if (top) { dtv[0] = dtv[1] = dtv[2] = dtv[3] = kTTop; }
+                // D = kx2 (dw + de) + ky2 (ds + dn) + cdn db + cup dt - diag dc
+                const float diag = 2.f * kx2 + 2.f * ky2 + cdn + cup;
+                const float bwlo = wlo_b * inv_dz, bwhi = whi_b * inv_dz, twlo = wlo_t * inv_dz, twhi = whi_t * inv_dz;
+                float res[4];
+#pragma unroll
+                for (int a = 0; a < 4; ++a) {
+                    const float tc = tcv[a + 1], dc = dcv[a + 1];
+                    const float cx = (us[a] * hix) * (tcv[a] + tc) - (us[a + 1] * hix) * (tc + tcv[a + 2]);
+                    const float cy = (vs[a] * hiy) * (tsv[a] + tc) - (vn[a] * hiy) * (tc + tnv[a]);
+                    const float cz = wb[a] * (bwlo * tbv[a] + bwhi * tc) - wt[a] * (twlo * tc + twhi * ttv[a]);
+                    const float D = kx2 * (dcv[a] + dcv[a + 2]) + ky2 * (dsv[a] + dnv[a]) + cdn * dbv[a] + cup * dtv[a] - diag * dc;
+                    res[a] = ca * dc + cbb * tc + gdt * ((cx + cy + cz) + D);
+                }
+                *reinterpret_cast<float4*>(outp) = make_float4(res[0], res[1], res[2], res[3]);
+            }
+        }
+        // plane k-1 (and the bundle of layer k-2) are no longer needed by this thread
+        mbar_arrive(&empty[sb]);
+        sb = sc;
+        sc = st;
+        st = (st + 1 == NB) ? 0 : st + 1;
+        outp += plane;
+        gn += plane;
+        gm += plane;
+    }
+    if (consumers_sync_or<kThreads>(fail)) {
+        if (tid == 0) atomicExch(A.err, MR_ERR_TIMEOUT);
+        return;
+    }
+    if (DIVONLY) {
+        for (int o = 16; o > 0; o >>= 1) dmax = fmaxf(dmax, __shfl_down_sync(0xffffffffu, dmax, o));
+        if (lane == 0) red[warp] = dmax;
+        consumers_sync<kThreads>();
+        if (tid == 0) {
+            float m = 0.f;
+            for (int w = 0; w < NW; ++w) m = fmaxf(m, red[w]);
+            atomicMax(A.divmax, (unsigned long long)__double_as_longlong((double)m));
+        }
+    }
+}
+
+// ------------------------------------------------------------- intermediates (once per velocity)
+
+__device__ __forceinline__ int pwrap(int i, int n) { return ((i % n) + n) % n; }
+
+// WY[k][j][gx]: R_y of the full-area W on every dense plane (coarse W on the
+// coarse planes, slab-balanced scrW on the inner ones).
+__global__ void k_xprep_wy(Grid<float> g, const float* __restrict__ W, const float* __restrict__ scrW,
+                           float* __restrict__ WY, int nxg)
+{
+    const size_t n = (size_t)(g.Nz + 1) * g.Ny * nxg;
+    for (size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (size_t)gridDim.x * blockDim.x) {
+        const int gx = (int)(t % nxg), j = (int)((t / nxg) % g.Ny), k = (int)(t / ((size_t)nxg * g.Ny));
+        const int I = pwrap(gx - 4, g.nx), J = j / g.my;
+        float s = 0.f;
+        for (int q = 0; q < 3; ++q) {
+            const int Jq = g.wy[3 * J + q];
+            const float v = (k % g.mz == 0) ? W[((size_t)(k / g.mz) * g.ny + Jq) * g.nx + I]
+                                            : scrW[((size_t)k * g.ny + Jq) * g.nx + I];
+            s += g.Ry[3 * j + q] * v;
+        }
+        WY[t] = s;
+    }
+}
+
+// UO[k][j][gx]: the outer U sub-face of coarse x-face I (R_y R_z of U).
+__global__ void k_xprep_uo(Grid<float> g, const float* __restrict__ U, float* __restrict__ UO, int nxg)
+{
+    const size_t n = (size_t)g.Nz * g.Ny * nxg;
+    for (size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (size_t)gridDim.x * blockDim.x) {
+        const int gx = (int)(t % nxg), j = (int)((t / nxg) % g.Ny), k = (int)(t / ((size_t)nxg * g.Ny));
+        const int I = pwrap(gx - 4, g.nx), J = j / g.my, K = k / g.mz;
+        float s = 0.f;
+        for (int p = 0; p < 3; ++p)
+            for (int q = 0; q < 3; ++q)
+                s += g.Ry[3 * j + p] * g.Rz[3 * k + q] * U[((size_t)g.wz[3 * K + q] * g.ny + g.wy[3 * J + p]) * g.nx + I];
+        UO[t] = s;
+    }
+}
+
+// VR[k][j][gx]: full-coarse-width V on every dense y-face, by the row balance
+// (south to north) of stage Y; row Ny repeats row 0 (periodic).
+__global__ void k_xprep_vr(Grid<float> g, const float* __restrict__ V, const float* __restrict__ UO,
+                           const float* __restrict__ WY, float* __restrict__ VR, int nxg)
+{
+    const size_t n = (size_t)g.Nz * (g.ny + 1) * nxg;
+    for (size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (size_t)gridDim.x * blockDim.x) {
+        const int gx = (int)(t % nxg), J = (int)((t / nxg) % (g.ny + 1)), k = (int)(t / ((size_t)nxg * (g.ny + 1)));
+        const int I = pwrap(gx - 4, g.nx), K = k / g.mz, Jf = (J == g.ny) ? 0 : J;
+        float vz = 0.f;
+        for (int q = 0; q < 3; ++q) vz += g.Rz[3 * k + q] * V[((size_t)g.wz[3 * K + q] * g.ny + Jf) * g.nx + I];
+        const size_t vrow = (size_t)g.Ny + 1;
+        VR[((size_t)k * vrow + (size_t)J * g.my) * nxg + gx] = vz;
+        if (J == g.ny) continue;
+        const float dzk = g.dz[k];
+        const int xi = I + 4, xe = pwrap(I + 1, g.nx) + 4;
+        float G = vz * g.DX * dzk;
+        for (int b = 0; b < g.my - 1; ++b) {
+            const int j = J * g.my + b;
+            const float uw = UO[((size_t)k * g.Ny + j) * nxg + xi], ue = UO[((size_t)k * g.Ny + j) * nxg + xe];
+            const float wb = WY[((size_t)k * g.Ny + j) * nxg + xi], wt = WY[((size_t)(k + 1) * g.Ny + j) * nxg + xi];
+            G = G - (ue - uw) * g.dy * dzk - (wt - wb) * g.DX * g.dy;
+            VR[((size_t)k * vrow + j + 1) * nxg + gx] = G / (g.DX * dzk);
+        }
+    }
+}
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode()
+{
+    static EncodeTiledFn fn = nullptr;
+    if (!fn) {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess && q == cudaDriverEntryPointSuccess)
+            fn = (EncodeTiledFn)p;
+    }
+    return fn;
+}
+
+// 3-D FP32 tensor map of a [d2][d1][d0] array with a (b0, b1, b2) box.
+bool map3(CUtensorMap* m, const float* base, int d0, int d1, int d2, int b0, int b1, int b2)
+{
+    EncodeTiledFn fn = encode();
+    if (!fn) return false;
+    cuuint64_t dims[3] = {(cuuint64_t)d0, (cuuint64_t)d1, (cuuint64_t)d2};
+    cuuint64_t strides[2] = {(cuuint64_t)d0 * 4, (cuuint64_t)d0 * d1 * 4};
+    cuuint32_t box[3] = {(cuuint32_t)b0, (cuuint32_t)b1, (cuuint32_t)b2};
+    cuuint32_t es[3] = {1, 1, 1};
+    return fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, (void*)base, dims, strides, box, es,
+              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// Tensor maps encoded once per (buffer, shape, box); the scalar buffers rotate
+// through a handful of pointers, the intermediates are fixed.
+bool cached_map3(CUtensorMap* out, const float* base, int d0, int d1, int d2, int b0, int b1, int b2)
+{
+    struct Entry { const float* p; int d[6]; CUtensorMap m; };
+    static Entry cache[32];
+    static int n = 0, next = 0;
+    const int key[6] = {d0, d1, d2, b0, b1, b2};
+    for (int q = 0; q < n; ++q)
+        if (cache[q].p == base && !memcmp(cache[q].d, key, sizeof key)) {
+            *out = cache[q].m;
+            return true;
+        }
+    if (!map3(out, base, d0, d1, d2, b0, b1, b2)) return false;
+    Entry& e = cache[n < 32 ? n++ : (next = (next + 1) % 32)];
+    e.p = base;
+    memcpy(e.d, key, sizeof key);
+    e.m = *out;
+    return true;
+}
+
+int kcl_override()
+{
+    static int v = -1;
+    if (v < 0) {
+        const char* e = getenv("MR_XFUSED_KC");
+        v = e ? atoi(e) : 0;
+    }
+    return v;
+}
+
+template <int M, bool DIVONLY>
+cudaError_t launch_x(const Grid<float>& g, const float* WY, const float* UO, const float* VR, int nxg, const float* lc,
+                     const float* rx12, const float* Tm1, const float* T, float* Tp1, StepCoef c, int* err,
+                     unsigned long long* divmax, cudaStream_t st)
+{
+    using L = XT<M>;
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(k_xfused<M, DIVONLY>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L::bytes);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    CUtensorMap mn, mm, mwy, muo, mvr;
+    memset(&mn, 0, sizeof mn);
+    memset(&mm, 0, sizeof mm);
+    if (!DIVONLY && (!cached_map3(&mn, T, g.Nx, g.Ny, g.Nz, kBX, kBY, 1) ||
+                     !cached_map3(&mm, Tm1, g.Nx, g.Ny, g.Nz, kBX, kBY, 1)))
+        return cudaErrorInvalidValue;
+    if (!cached_map3(&mwy, WY, nxg, g.Ny, g.Nz + 1, L::BXC, kTY, 2) ||
+        !cached_map3(&muo, UO, nxg, g.Ny, g.Nz, L::BXC, kTY, 1) ||
+        !cached_map3(&mvr, VR, nxg, g.Ny + 1, g.Nz, L::BXC, kTY + 1, 1))
+        return cudaErrorInvalidValue;
+    const int tiles = (g.Nx / kTX) * (g.Ny / kTY);
+    int kcl = kcl_override();
+    if (kcl <= 0) {
+        const int want = 152 * 2 * 8;                     // ~8 waves at 2 CTAs / SM
+        int chunks = (want + tiles - 1) / tiles;
+        chunks = max(1, min(chunks, g.Nz / 4));
+        kcl = (g.Nz + chunks - 1) / chunks;
+    }
+    const int chunks = (g.Nz + kcl - 1) / kcl;
+    XArgs A{g, T, Tm1, Tp1, lc, (float)c.a, (float)c.b, (float)c.gdt, kcl, err, divmax, {}};
+    memcpy(A.rx, rx12, sizeof A.rx);
+    dim3 grid(chunks, g.Nx / kTX, g.Ny / kTY);
+    k_xfused<M, DIVONLY><<<grid, kThreadsAll, L::bytes, st>>>(mn, mm, mwy, muo, mvr, A);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_xfused_prep(const Grid<float>& g, const float* U, const float* V, const float* W, float* scrW,
+                               float* WY, float* UO, float* VR, int nxg, cudaStream_t st)
+{
+    cudaError_t e = launch_column_balance<float>(g, U, V, W, scrW, st);
+    if (e != cudaSuccess) return e;
+    const unsigned blocks = 152 * 16;
+    k_xprep_wy<<<blocks, 256, 0, st>>>(g, W, scrW, WY, nxg);
+    k_xprep_uo<<<blocks, 256, 0, st>>>(g, U, UO, nxg);
+    k_xprep_vr<<<blocks, 256, 0, st>>>(g, V, UO, WY, VR, nxg);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_step_xfused_f32(const Grid<float>& g, const float* WY, const float* UO, const float* VR, int nxg,
+                                   const float* lc, const float* rx12, const float* Tm1, const float* T, float* Tp1,
+                                   StepCoef c, cudaStream_t st)
+{
+    int* err = fused_error_flag();
+    if (!err) return cudaErrorMemoryAllocation;
+    if (g.mx == 4) return launch_x<4, false>(g, WY, UO, VR, nxg, lc, rx12, Tm1, T, Tp1, c, err, nullptr, st);
+    return launch_x<2, false>(g, WY, UO, VR, nxg, lc, rx12, Tm1, T, Tp1, c, err, nullptr, st);
+}
+
+cudaError_t launch_maxdiv_xfused_f32(const Grid<float>& g, const float* WY, const float* UO, const float* VR, int nxg,
+                                     const float* lc, const float* rx12, double* partials, int blocks, cudaStream_t st)
+{
+    int* err = fused_error_flag();
+    if (!err) return cudaErrorMemoryAllocation;
+    cudaError_t e = cudaMemsetAsync(partials, 0, (size_t)blocks * sizeof(double), st);
+    if (e != cudaSuccess) return e;
+    unsigned long long* dm = reinterpret_cast<unsigned long long*>(partials);
+    StepCoef c{0, 0, 0};
+    if (g.mx == 4) return launch_x<4, true>(g, WY, UO, VR, nxg, lc, rx12, nullptr, nullptr, nullptr, c, err, dm, st);
+    return launch_x<2, true>(g, WY, UO, VR, nxg, lc, rx12, nullptr, nullptr, nullptr, c, err, dm, st);
+}
+
+}  // namespace mr

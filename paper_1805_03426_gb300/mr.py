@@ -17,7 +17,7 @@ LIB_PATH = os.path.join(_PKG, "libmr.so")
 
 MR_OK, MR_ERR_ARG, MR_ERR_CUDA, MR_ERR_NONFINITE, MR_ERR_TIMEOUT, MR_ERR_OOM, MR_ERR_STATE = 0, -1, -2, -3, -4, -5, -6
 MR_F64, MR_F32 = 0, 1
-MR_VEL_STORED, MR_VEL_FUSED = 0, 1
+MR_VEL_STORED, MR_VEL_FUSED, MR_VEL_XFUSED = 0, 1, 2
 MR_DIRICHLET, MR_ADIABATIC = 0, 1
 MR_PERIODIC, MR_WALLS = 0, 1
 

@@ -46,6 +46,11 @@ def prob(request):
     return Problem(**FUSED[request.param], ra=1e6, pr=7.0, dt=2e-3)
 
 
+@pytest.fixture(params=["fused", "xfused"])
+def mode(request, mr):
+    return {"fused": mr.MR_VEL_FUSED, "xfused": mr.MR_VEL_XFUSED}[request.param]
+
+
 def _run(mr, p, mode, nsteps):
     h = mr.mr_create(p.mr_config(mr, mr.MR_F32, mode))
     mr.mr_refine_velocity(h, dev(p.U), dev(p.V), dev(p.W))
@@ -58,9 +63,9 @@ def _run(mr, p, mode, nsteps):
     return h, T.cpu().numpy(), Tp.cpu().numpy()
 
 
-def test_fused_matches_oracle_and_stored(mr, prob):
+def test_fused_matches_oracle_and_stored(mr, prob, mode):
     n = 17   # Euler start, leapfrog and averaging steps
-    hf, Tf, Tpf = _run(mr, prob, mr.MR_VEL_FUSED, n)
+    hf, Tf, Tpf = _run(mr, prob, mode, n)
     hs, Ts, _ = _run(mr, prob, mr.MR_VEL_STORED, n)
     vel = O.refine(prob.cfg, prob.U, prob.V, prob.W)
     Tp_ref, T_ref = O.run(prob.cfg, vel, prob.T0, n)
@@ -77,8 +82,8 @@ def test_fused_matches_oracle_and_stored(mr, prob):
     assert 0.0 < st["max_div"] <= 2e-5 * scale
 
 
-def test_fused_cfl_and_dense_faces(mr, prob):
-    h = mr.mr_create(prob.mr_config(mr, mr.MR_F32, mr.MR_VEL_FUSED))
+def test_fused_cfl_and_dense_faces(mr, prob, mode):
+    h = mr.mr_create(prob.mr_config(mr, mr.MR_F32, mode))
     sh = h.shapes
     out = [torch.empty(sh[k], dtype=torch.float32, device="cuda") for k in ("Us", "Vs", "Ws")]
     mr.mr_refine_velocity(h, dev(prob.U), dev(prob.V), dev(prob.W), *out)
@@ -89,20 +94,20 @@ def test_fused_cfl_and_dense_faces(mr, prob):
     assert abs(mr.mr_cfl_dt(h, 0.3) / O.cfl_dt(prob.cfg, vel, 0.3) - 1) <= 1e-5
 
 
-def test_fused_full_size_precision_form(mr):
+def test_fused_full_size_precision_form(mr, mode):
     """512x512x384 dense (coarse 128x128x96, refinement 4), Sc=100, Ra=1e9:
     three fused FP32 steps (Euler, leapfrog, averaging) against the oracle."""
     p = Problem(128, 128, 96, mx=4, my=4, mz=4, gamma=1.5, ra=1e9, pr=100.0, rms=0.1, dt=2e-4, np_average=3)
-    h, T, _ = _run(mr, p, mr.MR_VEL_FUSED, 3)
+    h, T, _ = _run(mr, p, mode, 3)
     vel = O.refine(p.cfg, p.U, p.V, p.W)
     _, T_ref = O.run(p.cfg, vel, p.T0, 3)
     assert np.abs(T - T_ref).max() <= F32_T_TOL
 
 
-def test_fused_rejects_unsupported_shapes(mr):
+def test_fused_rejects_unsupported_shapes(mr, mode):
     p = Problem(6, 5, 4, mx=2, my=2, mz=2)
     with pytest.raises(mr.MRError) as e:
-        mr.mr_create(p.mr_config(mr, mr.MR_F32, mr.MR_VEL_FUSED))
+        mr.mr_create(p.mr_config(mr, mr.MR_F32, mode))
     assert e.value.code == mr.MR_ERR_ARG
     with pytest.raises(mr.MRError):
-        mr.mr_create(Problem(32, 8, 4, mx=2, my=2, mz=2).mr_config(mr, mr.MR_F64, mr.MR_VEL_FUSED))
+        mr.mr_create(Problem(32, 8, 4, mx=2, my=2, mz=2).mr_config(mr, mr.MR_F64, mode))
