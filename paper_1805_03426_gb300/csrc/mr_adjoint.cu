@@ -13,8 +13,10 @@
 //   (C^T mu)_c = sum_faces (A_f / Vol_c) u_f w_{c,f} (mu_R - mu_L),
 // w_{c,f} being the weight of T_c in the face value T_f.  The face gradient is
 //   dL/du_f += g_s dt A_f T^s_f (mu_R - mu_L),
-// accumulated in FP64 by the cell that owns the face (its west, south and
-// bottom faces), so no atomics are needed.  The coarse gradient is the
+// accumulated by the cell that owns the face (its west, south and bottom
+// faces), so no atomics are needed: in the working precision over one
+// checkpoint segment, then added into FP64 totals (GB300's FP64 pipe is a
+// small fraction of its FP32 one).  The coarse gradient is the
 // transpose of the refinement (Section 3.2), applied once at the end (it is
 // linear and fixed, so sum_s P^T g_s = P^T sum_s g_s).
 //
@@ -56,8 +58,8 @@ __global__ void __launch_bounds__(256) k_adj_step(Grid<P> g, const P* __restrict
                                                   const P* __restrict__ Ws, const P* __restrict__ T,
                                                   const P* __restrict__ Tprev, const P* __restrict__ Mn,
                                                   P* __restrict__ Mc, P* __restrict__ Mp, double s_nu, double s_var,
-                                                  double mean_prev, double* __restrict__ gU,
-                                                  double* __restrict__ gV, double* __restrict__ gW, P a, P b, P gdt)
+                                                  double mean_prev, P* __restrict__ gU,
+                                                  P* __restrict__ gV, P* __restrict__ gW, P a, P b, P gdt)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const int j = blockIdx.y * blockDim.y + threadIdx.y;
@@ -67,7 +69,6 @@ __global__ void __launch_bounds__(256) k_adj_step(Grid<P> g, const P* __restrict
     const size_t m = (size_t)k * plane + (size_t)j * g.Nx + i;
     const P half = P(0.5);
     const P mc = Mn[m], tc = T[m];
-    const double gd = (double)gdt;
     P ct = 0, dxs = 0, dys = 0, dzs = 0, cy = 0, cz = 0;
     const size_t urow = ((size_t)k * g.Ny + j) * g.ufx;
     // x faces
@@ -77,7 +78,7 @@ __global__ void __launch_bounds__(256) k_adj_step(Grid<P> g, const P* __restrict
         const P uw = Us[urow + i], mw_ = Mn[mw];
         ct += uw * half * (mc - mw_);
         dxs -= mc - mw_;
-        gU[urow + i] += gd * (double)(g.dy * g.dz[k]) * (double)(half * (T[mw] + tc)) * (double)(mc - mw_);
+        gU[urow + i] += gdt * (g.dy * g.dz[k]) * (half * (T[mw] + tc)) * (mc - mw_);
     }
     if (!(g.walls && i == g.Nx - 1)) {
         const int ie = (i == g.Nx - 1) ? 0 : i + 1;
@@ -94,7 +95,7 @@ __global__ void __launch_bounds__(256) k_adj_step(Grid<P> g, const P* __restrict
         const P ms_ = Mn[ms];
         cy += Vs[vrow] * half * (mc - ms_);
         dys -= mc - ms_;
-        gV[vrow] += gd * (double)(g.dx * g.dz[k]) * (double)(half * (T[ms] + tc)) * (double)(mc - ms_);
+        gV[vrow] += gdt * (g.dx * g.dz[k]) * (half * (T[ms] + tc)) * (mc - ms_);
     }
     if (!(g.walls && j == g.Ny - 1)) {
         const int jn = (j == g.Ny - 1) ? 0 : j + 1;
@@ -108,7 +109,7 @@ __global__ void __launch_bounds__(256) k_adj_step(Grid<P> g, const P* __restrict
         const P mb_ = Mn[m - plane];
         cz += Ws[m] * g.whi[k] * (mc - mb_);
         dzs -= g.cdn[k] * (mc - mb_);
-        gW[m] += gd * (double)(g.dx * g.dy) * (double)(g.wlo[k] * T[m - plane] + g.whi[k] * tc) * (double)(mc - mb_);
+        gW[m] += gdt * (g.dx * g.dy) * (g.wlo[k] * T[m - plane] + g.whi[k] * tc) * (mc - mb_);
     } else {
         dzs -= g.cdn[0] * mc;
     }
@@ -128,6 +129,15 @@ __global__ void __launch_bounds__(256) k_adj_step(Grid<P> g, const P* __restrict
         double d = (k == 0) ? s_nu : 0.0;
         if (s_var != 0.0) d += s_var * ((double)Tprev[m] - mean_prev);
         Mp[m] = (P)d + a * mc + gdt * DT;
+    }
+}
+
+// totals (FP64) += segment sums (FP32), which are cleared
+__global__ void k_flush_faces(float* __restrict__ seg, double* __restrict__ tot, size_t n)
+{
+    for (size_t m = (size_t)blockIdx.x * blockDim.x + threadIdx.x; m < n; m += (size_t)gridDim.x * blockDim.x) {
+        tot[m] += (double)seg[m];
+        seg[m] = 0.f;
     }
 }
 
@@ -334,10 +344,16 @@ cudaError_t launch_adj_direct(const Grid<P>& g, const P* T, double s_nu_bottom, 
     return cudaGetLastError();
 }
 
+cudaError_t launch_flush_faces(float* seg, double* tot, size_t n, cudaStream_t st)
+{
+    k_flush_faces<<<152 * 8, kThreads, 0, st>>>(seg, tot, n);
+    return cudaGetLastError();
+}
+
 template <typename P>
 cudaError_t launch_adj_step(const Grid<P>& g, const P* Us, const P* Vs, const P* Ws, const P* T, const P* Tprev,
-                            const P* Mn, P* Mc, P* Mp, double s_nu, double s_var, double mean_prev, double* gU,
-                            double* gV, double* gW, StepCoef c, bool euler, cudaStream_t st)
+                            const P* Mn, P* Mc, P* Mp, double s_nu, double s_var, double mean_prev, P* gU,
+                            P* gV, P* gW, StepCoef c, bool euler, cudaStream_t st)
 {
     dim3 blk(64, 4);
     dim3 grd((g.Nx + blk.x - 1) / blk.x, (g.Ny + blk.y - 1) / blk.y, g.Nz);
@@ -360,7 +376,7 @@ cudaError_t launch_times_volume(const Grid<P>& g, const P* mu, int dst_dtype, vo
 #define MR_INST(P)                                                                                                 \
     template cudaError_t launch_adj_direct<P>(const Grid<P>&, const P*, double, double, double, P*, cudaStream_t); \
     template cudaError_t launch_adj_step<P>(const Grid<P>&, const P*, const P*, const P*, const P*, const P*,        \
-                                            const P*, P*, P*, double, double, double, double*, double*, double*,   \
+                                            const P*, P*, P*, double, double, double, P*, P*, P*,                  \
                                             StepCoef, bool, cudaStream_t);                                         \
     template cudaError_t launch_times_volume<P>(const Grid<P>&, const P*, int, void*, cudaStream_t);
 MR_INST(double)

@@ -815,11 +815,12 @@ cudaError_t step_buffers(mr_handle h, const void* Tm1, const void* T, void* Tp1,
 void adj_free(mr_handle h)
 {
     auto& a = h->adj;
-    void* ptrs[] = {a.cp, a.seg, a.mu, a.face, a.scr, a.out};
+    void* ptrs[] = {a.cp, a.seg, a.mu, a.face, a.scr, a.out, a.face32};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     a.cp = a.seg = a.mu = nullptr;
     a.face = a.scr = a.out = nullptr;
+    a.face32 = nullptr;
     a.cp_pairs = 0;
     a.ready = false;
 }
@@ -851,6 +852,10 @@ int mr_adjoint_forward(mr_handle h, int64_t nsteps, int32_t ck, const double* wn
         const size_t nscr = (size_t)(h->Nz + 1) * h->cfg.ny * h->cfg.nx + (size_t)h->Nz * (h->Ny + h->w) * h->cfg.nx;
         if (e == cudaSuccess) e = cudaMalloc((void**)&a.scr, nscr * sizeof(double));
         if (e == cudaSuccess) e = cudaMalloc((void**)&a.out, (h->ncell + h->ncU + h->ncV + h->ncW) * sizeof(double));
+        if (e == cudaSuccess && h->cfg.precision == MR_F32) {
+            e = cudaMalloc((void**)&a.face32, (h->nU + h->nV + h->nW) * sizeof(float));
+            if (e == cudaSuccess) e = cudaMemset(a.face32, 0, (h->nU + h->nV + h->nW) * sizeof(float));
+        }
         if (e != cudaSuccess) {
             adj_free(h);
             return cuda_check(e, "mr_adjoint_forward: checkpoint store");
@@ -917,6 +922,7 @@ int mr_adjoint_backward(mr_handle h, double gscale, void* gT0, int32_t gT0_dtype
     char* mu[3] = {(char*)a.mu, (char*)a.mu + fb, (char*)a.mu + 2 * fb};
     int in = 0, ic = 1, ip = 2;     // mu^{s+1}, mu^s, mu^{s-1}
     cudaError_t e = cudaMemsetAsync(a.face, 0, (h->nU + h->nV + h->nW) * sizeof(double), st);
+    if (e == cudaSuccess && a.face32) e = cudaMemsetAsync(a.face32, 0, (h->nU + h->nV + h->nW) * sizeof(float), st);
     // levels S and S-1 start from their direct terms (T^S, T^{S-1} are the handle's current pair)
     auto direct = [&](const void* T, int64_t s, void* out) {
         return P == MR_F64 ? launch_adj_direct<double>(h->g64, (const double*)T, s_nu(s), s_var(s), a.mean[s], (double*)out, st)
@@ -953,7 +959,8 @@ int mr_adjoint_backward(mr_handle h, double gscale, void* gT0, int32_t gT0_dtype
             else
                 e = launch_adj_step<float>(h->g32, (const float*)b.Us, (const float*)b.Vs, (const float*)b.Ws,
                                            (const float*)Ts, (const float*)Tsm, (const float*)mu[in], (float*)mu[ic],
-                                           (float*)mu[ip], s_nu(sp), s_var(sp), a.mean[sp], fU, fV, fW, co, euler, st);
+                                           (float*)mu[ip], s_nu(sp), s_var(sp), a.mean[sp], a.face32,
+                                           a.face32 + h->nU, a.face32 + h->nU + h->nV, co, euler, st);
             if (e != cudaSuccess) return cuda_check(e, "mr_adjoint_backward: launch");
             if (!euler) {
                 const int t = in;
@@ -961,6 +968,11 @@ int mr_adjoint_backward(mr_handle h, double gscale, void* gT0, int32_t gT0_dtype
                 ic = ip;
                 ip = t;
             }
+        }
+        if (P == MR_F32) {
+            // the segment's FP32 face-gradient sums into the FP64 totals
+            e = launch_flush_faces(a.face32, a.face, h->nU + h->nV + h->nW, st);
+            if (e != cudaSuccess) return cuda_check(e, "mr_adjoint_backward: flush");
         }
     }
     // after the Euler step the level-0 adjoint density is mu[ic]

@@ -103,6 +103,7 @@ struct mr_handle_s {
         void* seg = nullptr;                   // recomputed levels of one segment (ck + 1)
         void* mu = nullptr;                    // three adjoint levels
         double* face = nullptr;                // dense face gradients (U, V, W), FP64
+        float* face32 = nullptr;               // MR_F32: per-segment FP32 sums, flushed into face
         double* scr = nullptr;                 // transpose scratch (full-area W, full-width V), FP64
         double* out = nullptr;                 // FP64 staging of the outputs (dense T0, coarse U, V, W)
     } adj;
@@ -160,8 +161,9 @@ cudaError_t launch_refine_transpose(const Grid<double>& g, double* aUs, double* 
                                     size_t ncW, cudaStream_t st);
 template <typename P>
 cudaError_t launch_adj_step(const Grid<P>& g, const P* Us, const P* Vs, const P* Ws, const P* T, const P* Tprev,
-                            const P* Mn, P* Mc, P* Mp, double s_nu, double s_var, double mean_prev, double* gU,
-                            double* gV, double* gW, StepCoef c, bool euler, cudaStream_t st);
+                            const P* Mn, P* Mc, P* Mp, double s_nu, double s_var, double mean_prev, P* gU,
+                            P* gV, P* gW, StepCoef c, bool euler, cudaStream_t st);
+cudaError_t launch_flush_faces(float* seg, double* tot, size_t n, cudaStream_t st);
 template <typename P>
 cudaError_t launch_adj_direct(const Grid<P>& g, const P* T, double s_nu_bottom, double s_var, double mean, P* mu,
                               cudaStream_t st);
