@@ -38,11 +38,31 @@ WORKLOADS = {
     "rb128_adjoint": dict(nx=64, ny=64, nz=48, m=2, gamma=1.5, ra=1e7, pr=7.0, rms=0.1,
                           label="coarse 64x64x48 -> dense 128x128x96, stretched z (gamma 1.5), Ra=1e7, Pr=7, "
                                 "200 steps, checkpoints every 20, loss = bottom Nu over the last 50 steps"),
+    "rb1536_stretched_f32": dict(nx=384, ny=384, nz=256, m=4, gamma=1.5, ra=1e10, pr=100.0, rms=0.1,
+                                 label="coarse 384x384x256 -> dense 1536x1536x1024 (2.42 G cells), stretched z "
+                                       "(gamma 1.5), Ra=1e10, Sc=100, CFL 0.3"),
     "rb256_stretched_f64": dict(nx=128, ny=128, nz=96, m=2, gamma=1.5, ra=1e8, pr=7.0, rms=0.1,
                                 label="coarse 128x128x96 -> dense 256x256x192, stretched z (gamma 1.5), "
                                       "Ra=1e8, Pr=7, CFL 0.3"),
 }
 SEED = 1805
+
+# DRAM bytes (read + write) per launch of the dominant kernel from one ncu capture of the
+# workload (summarised in profiles/), valid only for the kernel sources they were measured on.
+NCU_TRAFFIC = {
+    ("k_xfused", "rb512_stretched_f32"): {"bytes": 1272083000 + 385997312, "sources": "3cafd14bc6381294.8945e0b384d6ff21",
+                                          "files": ("mr_xfused.cu", "mr_ptx.cuh")},
+}
+
+
+def _traffic(kernel, workload):
+    import hashlib
+    e = NCU_TRAFFIC.get((kernel, workload))
+    if not e:
+        return None
+    d = os.path.join(ROOT, "paper_1805_03426_gb300", "csrc")
+    h = ".".join(hashlib.sha256(open(os.path.join(d, f), "rb").read()).hexdigest()[:16] for f in e["files"])
+    return e["bytes"] if h == e["sources"] else None
 
 
 def _peaks():
@@ -121,7 +141,10 @@ def _inputs(mr, h, w):
     Zf = zf[::m].copy()
     U, V, W = synth.coarse_velocity(SEED, Xf, Yf, Zf, 1.0, 1.0, rms=w["rms"])
     zc = 0.5 * (zf[1:] + zf[:-1])
-    T0 = synth.initial_scalar(SEED, zc, Ny, Nx)
+    if Nx * Ny * Nz > 400_000_000:     # drawn on the device (FP32) for the largest grid
+        T0 = synth.initial_scalar_device(SEED, zc, Ny, Nx)
+    else:
+        T0 = synth.initial_scalar(SEED, zc, Ny, Nx)
     return U, V, W, T0
 
 
@@ -163,7 +186,7 @@ def run_mr(args):
     h = _make(mr, w, prec, mode)
     U, V, W, T0 = _inputs(mr, h, w)
     dU, dV, dW = (torch.from_numpy(a).cuda() for a in (U, V, W))
-    dT0 = torch.from_numpy(T0).cuda()
+    dT0 = T0 if isinstance(T0, torch.Tensor) else torch.from_numpy(T0).cuda()
     torch.cuda.synchronize()
     mr.mr_refine_velocity(h, dU, dV, dW, stream=stream)
     dt = mr.mr_cfl_dt(h, 0.3, stream=stream)
@@ -195,9 +218,10 @@ def run_mr(args):
     per_launch = t / args.steps
     peak, peak_kind = _peaks()
     achieved = bytes_per_cell * cells / per_launch / 1e9
+    kname = {mr.MR_VEL_FUSED: "k_fused", mr.MR_VEL_XFUSED: "k_xfused"}.get(mode, "k_step_stored")
     roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-            "frac": round(achieved / peak, 4), "traffic": None, "peak_source": peak_kind,
-            "kernel": {mr.MR_VEL_FUSED: "k_fused", mr.MR_VEL_XFUSED: "k_xfused"}.get(mode, "k_step_stored"),
+            "frac": round(achieved / peak, 4), "traffic": _traffic(kname, args.workload), "peak_source": peak_kind,
+            "kernel": kname,
             "bytes_per_cell": round(bytes_per_cell, 3), "launch_ms": round(per_launch * 1e3, 4)}
 
     # FP64 path on the same grid (stored velocity), for the FP32/FP64 ratio
@@ -254,7 +278,8 @@ def run_mr(args):
             "dtype": "f32" if prec == mr.MR_F32 else "f64", "data": "synthetic",
             "config": {"workload": args.workload, "description": w["label"], "dense_cells": cells,
                        "velocity_mode": args.mode, "dt": dt, "parallelism": f"replicas{world}",
-                       "l2": "inputs larger than L2 (3 scalar levels of %.0f MB)" % (cells * elt / 2**20)},
+                       "l2": "inputs larger than L2 (3 scalar levels of %.0f MB)" % (cells * elt / 2**20),
+            "bytes_per_cell": round(bytes_per_cell, 3)},
             "roofline": roof, "fp64_path": fp64, "adjoint": adj, "e2e": e2e, "cpu_baseline": cpu,
             "gpu_launches": args.steps, "clocks": clk.summary(),
             "final_stats": {k: st[k] for k in ("nu_bot", "nu_top", "mean", "var")},

@@ -145,6 +145,19 @@ def initial_scalar(seed, zc, Ny, Nx, noise=1e-2):
     return T
 
 
+def initial_scalar_device(seed, zc, Ny, Nx, noise=1e-2, device="cuda"):
+    """Same recipe drawn on the device in FP32 with torch's generator (for
+    grids too large to stage on the host); not bitwise equal to the numpy draw."""
+    import torch
+    gen = torch.Generator(device=device)
+    gen.manual_seed(seed + 1)
+    zc_t = torch.as_tensor(np.asarray(zc), dtype=torch.float32, device=device)
+    T = torch.randn((len(zc), Ny, Nx), generator=gen, device=device, dtype=torch.float32)
+    T.mul_(noise)
+    T.add_((0.5 - zc_t)[:, None, None])
+    return T
+
+
 def workload(name: str) -> dict:
     """The named synthetic workloads (dense grid = coarse grid x refinement)."""
     table = {

@@ -1,0 +1,66 @@
+"""The 1536x1536x1024 FP32 grid (coarse 384x384x256, refinement 4, 2.42 G
+cells) in the split-x fused mode: properties that hold at any size, since the
+oracle cannot hold this grid.  Conduction is steady with Nu = 1 at zero
+velocity; with adiabatic plates the scalar integral is conserved through the
+Euler start, leapfrog and averaging steps; the refined velocity is
+divergence-free to FP32 round-off."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def mr():
+    import paper_1805_03426_gb300.mr as m
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    if torch.cuda.get_device_properties(0).total_memory < 80e9:
+        pytest.skip("needs ~50 GB of device memory")
+    m.lib()
+    return m
+
+
+def _cfg(mr, **kw):
+    base = dict(nx=384, ny=384, nz=256, mx=4, my=4, mz=4, stretch_gamma=1.5, ra=1e10, pr_or_sc=100.0,
+                dt=2e-4, precision=mr.MR_F32, velocity_mode=mr.MR_VEL_XFUSED, np_average=3)
+    base.update(kw)
+    return mr.mr_config_default(**base)
+
+
+def test_large_grid_conservation_and_divergence(mr):
+    from paper_1805_03426_gb300 import synth
+    h = mr.mr_create(_cfg(mr, bc_plates=mr.MR_ADIABATIC))
+    (Nx, Ny, Nz), zf = mr.mr_grid(h)
+    U, V, W = synth.coarse_velocity(1805, np.arange(385) / 384, np.arange(385) / 384, zf[::4], rms=0.1)
+    mr.mr_refine_velocity(h, torch.from_numpy(U).cuda(), torch.from_numpy(V).cuda(), torch.from_numpy(W).cuda())
+    zc = 0.5 * (zf[1:] + zf[:-1])
+    T0 = synth.initial_scalar_device(1805, zc, Ny, Nx)
+    mr.mr_set_scalar(h, T0)
+    del T0
+    s0 = mr.mr_scalar_stats(h)
+    mr.mr_scalar_step(h, 4)          # Euler, leapfrog, averaging (N_p = 3), leapfrog
+    s1 = mr.mr_scalar_stats(h)
+    vol_abs = 0.5                     # sum |T| Vol is about 1/4 of the box; bound the FP32 sum error generously
+    assert abs(s1["integral"] - s0["integral"]) <= 1e-5 * vol_abs
+    dz_min = float(np.diff(zf).min())
+    scale = float(np.abs(U).max()) * Nx + float(np.abs(W).max()) / dz_min
+    assert 0.0 < s1["max_div"] <= 2e-5 * scale
+    assert np.isfinite(s1["var"]) and s1["var"] > 0.0
+
+
+def test_large_grid_conduction_steady_nu_one(mr):
+    h = mr.mr_create(_cfg(mr))
+    (Nx, Ny, Nz), zf = mr.mr_grid(h)
+    z = lambda n: np.zeros(n)
+    mr.mr_refine_velocity(h, z((256, 384, 384)), z((256, 384, 384)), z((257, 384, 384)))
+    zc = 0.5 * (zf[1:] + zf[:-1])
+    T0 = torch.from_numpy((0.5 - zc).astype(np.float32)).cuda()[:, None, None].expand(Nz, Ny, Nx).contiguous()
+    mr.mr_set_scalar(h, T0)
+    mr.mr_scalar_step(h, 3)
+    st = mr.mr_scalar_stats(h)
+    assert abs(st["nu_bot"] - 1.0) < 1e-4 and abs(st["nu_top"] - 1.0) < 1e-4
+    T = torch.empty_like(T0)
+    mr.mr_get_scalar(h, T)
+    assert float((T - T0).abs().max()) <= 1e-6
