@@ -352,7 +352,7 @@ int mr_create(const mr_config* cfg, mr_handle* out)
     alloc(&b.metric, mb64 + mb32 + nwin * sizeof(int));
     h->red_blocks = 152 * 8;
     alloc((void**)&b.red, (size_t)h->red_blocks * 2 * sizeof(double));
-    alloc((void**)&b.nu2, 4 * sizeof(double));
+    alloc((void**)&b.nu2, (2 + 2 * kPlateBlocks) * sizeof(double));
     h->stage_bytes = std::min<size_t>((size_t)64 << 20, std::max<size_t>(h->ncell * 8, 1 << 16));
     alloc(&b.stage, h->stage_bytes);
     if (c.diffz_implicit) alloc(&b.tri, h->ncell * h->elt);
@@ -617,14 +617,11 @@ int mr_plate_nu(mr_handle h, double* nu2, mr_stream stream)
     if (!h->have_scalar) return set_error(MR_ERR_STATE, "mr_plate_nu: no scalar set");
     cudaStream_t st = (cudaStream_t)stream;
     const double zz[2] = {h->zc[0] - h->zf[0], h->zf[h->Nz] - h->zc[h->Nz - 1]};
-    const bool dev = is_device_pointer(nu2);
-    double* out = dev ? nu2 : h->buf.nu2;
     cudaError_t e = h->cfg.precision == MR_F64
-                        ? launch_plate_nu<double>(h->g64, (const double*)h->buf.T[h->ic], zz, out, st)
-                        : launch_plate_nu<float>(h->g32, (const float*)h->buf.T[h->ic], zz, out, st);
+                        ? launch_plate_nu<double>(h->g64, (const double*)h->buf.T[h->ic], zz, h->buf.nu2, st)
+                        : launch_plate_nu<float>(h->g32, (const float*)h->buf.T[h->ic], zz, h->buf.nu2, st);
     if (e != cudaSuccess) return cuda_check(e, "mr_plate_nu: launch");
-    if (!dev) return cuda_check(cudaMemcpyAsync(nu2, out, 2 * sizeof(double), cudaMemcpyDeviceToHost, st), "mr_plate_nu: copy");
-    return MR_OK;
+    return cuda_check(cudaMemcpyAsync(nu2, h->buf.nu2, 2 * sizeof(double), cudaMemcpyDefault, st), "mr_plate_nu: copy");
 }
 
 static int reduce_partials(mr_handle h, int nper, std::vector<double>& out, cudaStream_t st)

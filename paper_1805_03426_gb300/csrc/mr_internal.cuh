@@ -12,6 +12,8 @@
 
 namespace mr {
 
+constexpr int kPlateBlocks = 64;   // blocks of the plate Nusselt reduction
+
 // Device view of the grid and of the per-layer coefficients, in precision P.
 // Built once per handle from the FP64 host grid (Sections 3.1, 3.2).
 template <typename P>
@@ -59,7 +61,7 @@ struct DeviceBuffers {
     void* scrV = nullptr;                      // refinement scratch: full-coarse-width V per dense row
     void* metric = nullptr;                    // one block holding every Grid array
     double* red = nullptr;                     // reduction partials
-    double* nu2 = nullptr;                     // plate Nusselt numbers (2 doubles)
+    double* nu2 = nullptr;                     // plate Nusselt numbers (2 doubles + partials)
     void* stage = nullptr;                     // conversion staging buffer
     void* tri = nullptr;                       // implicit-z work (2 * Nz per column)
     // MR_VEL_XFUSED: coarse-x intermediates of the z- and y-stages (FP32,

@@ -66,31 +66,31 @@ __global__ void __launch_bounds__(kRedThreads) k_moments(Grid<P> g, const P* __r
     block_reduce_store<2, false>(v, partials + 2 * blockIdx.x);
 }
 
-// Plate Nusselt numbers: one block sums both plates in a fixed order.
+// Plate Nusselt numbers, stage 1: every block sums a fixed slice of both
+// plates into two FP64 partials (deterministic order).
 template <typename P>
-__global__ void __launch_bounds__(1024) k_plate_nu(Grid<P> g, const P* __restrict__ T, double zb, double zt,
-                                                   double* __restrict__ out2)
+__global__ void __launch_bounds__(256) k_plate_partials(Grid<P> g, const P* __restrict__ T, double zb, double zt,
+                                                        double* __restrict__ partials)
 {
     const size_t plane = (size_t)g.Nx * g.Ny;
     const P* top = T + (size_t)(g.Nz - 1) * plane;
-    double sb = 0.0, st = 0.0;
-    for (size_t m = threadIdx.x; m < plane; m += blockDim.x) {
-        sb += (0.5 - (double)T[m]) / zb;
-        st += ((double)top[m] + 0.5) / zt;
+    double v[2] = {0.0, 0.0};
+    for (size_t m = (size_t)blockIdx.x * blockDim.x + threadIdx.x; m < plane; m += (size_t)gridDim.x * blockDim.x) {
+        v[0] += (0.5 - (double)T[m]) / zb;
+        v[1] += ((double)top[m] + 0.5) / zt;
     }
-    __shared__ double sh[2][32];
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    sb = warp_sum(sb);
-    st = warp_sum(st);
-    if (lane == 0) { sh[0][wid] = sb; sh[1][wid] = st; }
-    __syncthreads();
-    if (wid == 0) {
-        const int nw = blockDim.x >> 5;
-        double b = lane < nw ? sh[0][lane] : 0.0, t = lane < nw ? sh[1][lane] : 0.0;
-        b = warp_sum(b);
-        t = warp_sum(t);
-        if (lane == 0) { out2[0] = b / (double)plane; out2[1] = t / (double)plane; }
-    }
+    block_reduce_store<2, false>(v, partials + 2 * blockIdx.x);
+}
+
+// Stage 2: one block adds the partials in block order and writes the means.
+__global__ void __launch_bounds__(32) k_plate_final(const double* __restrict__ partials, int blocks, double inv_plane,
+                                                    double* __restrict__ out2)
+{
+    if (threadIdx.x != 0) return;
+    double b = 0.0, t = 0.0;
+    for (int q = 0; q < blocks; ++q) { b += partials[2 * q]; t += partials[2 * q + 1]; }
+    out2[0] = b * inv_plane;
+    out2[1] = t * inv_plane;
 }
 
 // Max |divergence| of the dense refined faces (outward flux sum / volume).
@@ -159,7 +159,9 @@ cudaError_t launch_moments(const Grid<P>& g, const P* T, double mean, int pass, 
 template <typename P>
 cudaError_t launch_plate_nu(const Grid<P>& g, const P* T, const double* zb_zt, double* out2, cudaStream_t st)
 {
-    k_plate_nu<P><<<1, 1024, 0, st>>>(g, T, zb_zt[0], zb_zt[1], out2);
+    // the partials live in out2[2..]: the caller's buffer holds 2 + 2 * kPlateBlocks doubles
+    k_plate_partials<P><<<kPlateBlocks, 256, 0, st>>>(g, T, zb_zt[0], zb_zt[1], out2 + 2);
+    k_plate_final<<<1, 32, 0, st>>>(out2 + 2, kPlateBlocks, 1.0 / ((double)g.Nx * g.Ny), out2);
     return cudaGetLastError();
 }
 

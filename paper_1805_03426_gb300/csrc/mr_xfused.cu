@@ -49,8 +49,9 @@ struct XT {
     static constexpr int oWY = 2 * kPlaneSlot;          // [2][TY][BXC]   planes k, k+1
     static constexpr int oUO = oWY + 2 * kTY * BXC;     // [TY][BXC]
     static constexpr int oVR = oUO + kTY * BXC;         // [TY+1][BXC]
-    static constexpr int slot = (((oVR + (kTY + 1) * BXC) * 4 + 127) / 128) * 128 / 4;
-    static constexpr uint32_t bundle_bytes = (uint32_t)(2 * kTY * BXC + kTY * BXC + (kTY + 1) * BXC) * 4;
+    static constexpr int oLC = ((oVR + (kTY + 1) * BXC) + 31) / 32 * 32;   // [12] layer constants (128-B aligned)
+    static constexpr int slot = (((oLC + 16) * 4 + 127) / 128) * 128 / 4;
+    static constexpr uint32_t bundle_bytes = (uint32_t)(2 * kTY * BXC + kTY * BXC + (kTY + 1) * BXC + 12) * 4;
     static constexpr int oRed = NB * slot;              // 64 floats
     static constexpr int oBar = ((oRed + 64) * 4 + 7) / 8;
     static constexpr size_t bytes = (size_t)(oBar + 2 * NB) * 8;
@@ -75,7 +76,7 @@ template <int M, bool DIVONLY>
 __global__ void __launch_bounds__(kThreadsAll, 2)
 k_xfused(const __grid_constant__ CUtensorMap tmn, const __grid_constant__ CUtensorMap tmm,
          const __grid_constant__ CUtensorMap twy, const __grid_constant__ CUtensorMap tuo,
-         const __grid_constant__ CUtensorMap tvr, const XArgs A)
+         const __grid_constant__ CUtensorMap tvr, const __grid_constant__ CUtensorMap tlc, const XArgs A)
 {
     using L = XT<M>;
     constexpr int NB = L::NB, BXC = L::BXC, NC = 4 / M, NW = kThreads / 32;
@@ -124,6 +125,7 @@ k_xfused(const __grid_constant__ CUtensorMap tmn, const __grid_constant__ CUtens
                 tma_3d(slot + L::oWY, &twy, I0, j0, kb, &full[s]);
                 tma_3d(slot + L::oUO, &tuo, I0, j0, kb, &full[s]);
                 tma_3d(slot + L::oVR, &tvr, I0, j0, kb, &full[s]);
+                tma_3d(slot + L::oLC, &tlc, 0, kb, 0, &full[s]);
             }
         }
         return;
@@ -152,11 +154,6 @@ k_xfused(const __grid_constant__ CUtensorMap tmn, const __grid_constant__ CUtens
     const int o = (jl + 1) * kBX + il0 + 4;          // this segment's first cell in a plane box
 
     for (int k = k0; k < k1; ++k) {
-        // layer constants: dz, 1/dz, wlo_b, whi_b | wlo_t, whi_t, cdn, cup | dx/dz
-        const float4* lq = reinterpret_cast<const float4*>(A.lc + 12 * k);
-        const float4 c0 = __ldg(lq), c1 = __ldg(lq + 1);
-        const float inv_dz = c0.y, wlo_b = c0.z, whi_b = c0.w, wlo_t = c1.x, whi_t = c1.y, cdn = c1.z, cup = c1.w;
-        const float fx_z = __ldg(A.lc + 12 * k + 8);
         const int need = k - k0 + 2;             // ring of plane k+1 and of this layer's bundle
         while (!fail && waited <= need) {
             if (!mbar_wait(&full[wslot], wpar)) { fail = true; break; }
@@ -165,6 +162,11 @@ k_xfused(const __grid_constant__ CUtensorMap tmn, const __grid_constant__ CUtens
         }
         if (!fail) {
             const float* bun = sm + st * L::slot;
+            // layer constants (from the bundle): dz, 1/dz, wlo_b, whi_b | wlo_t, whi_t, cdn, cup | dx/dz
+            const float4 c0 = *reinterpret_cast<const float4*>(bun + L::oLC);
+            const float4 c1 = *reinterpret_cast<const float4*>(bun + L::oLC + 4);
+            const float inv_dz = c0.y, wlo_b = c0.z, whi_b = c0.w, wlo_t = c1.x, whi_t = c1.y, cdn = c1.z, cup = c1.w;
+            const float fx_z = bun[L::oLC + 8];
             float wb[4], wt[4], vs[4], vn[4], us[5];
             {
                 // R_x splits of the full-width W (planes k, k+1) and V (faces jl, jl+1);
@@ -431,7 +433,7 @@ cudaError_t launch_x(const Grid<float>& g, const float* WY, const float* UO, con
         if (e != cudaSuccess) return e;
         attr = true;
     }
-    CUtensorMap mn, mm, mwy, muo, mvr;
+    CUtensorMap mn, mm, mwy, muo, mvr, mlc;
     memset(&mn, 0, sizeof mn);
     memset(&mm, 0, sizeof mm);
     if (!DIVONLY && (!cached_map3(&mn, T, g.Nx, g.Ny, g.Nz, kBX, kBY, 1) ||
@@ -439,7 +441,8 @@ cudaError_t launch_x(const Grid<float>& g, const float* WY, const float* UO, con
         return cudaErrorInvalidValue;
     if (!cached_map3(&mwy, WY, nxg, g.Ny, g.Nz + 1, L::BXC, kTY, 2) ||
         !cached_map3(&muo, UO, nxg, g.Ny, g.Nz, L::BXC, kTY, 1) ||
-        !cached_map3(&mvr, VR, nxg, g.Ny + 1, g.Nz, L::BXC, kTY + 1, 1))
+        !cached_map3(&mvr, VR, nxg, g.Ny + 1, g.Nz, L::BXC, kTY + 1, 1) ||
+        !cached_map3(&mlc, lc, 12, g.Nz, 1, 12, 1, 1))
         return cudaErrorInvalidValue;
     const int tiles = (g.Nx / kTX) * (g.Ny / kTY);
     int kcl = kcl_override();
@@ -453,7 +456,7 @@ cudaError_t launch_x(const Grid<float>& g, const float* WY, const float* UO, con
     XArgs A{g, T, Tm1, Tp1, lc, (float)c.a, (float)c.b, (float)c.gdt, kcl, err, divmax, {}};
     memcpy(A.rx, rx12, sizeof A.rx);
     dim3 grid(chunks, g.Nx / kTX, g.Ny / kTY);
-    k_xfused<M, DIVONLY><<<grid, kThreadsAll, L::bytes, st>>>(mn, mm, mwy, muo, mvr, A);
+    k_xfused<M, DIVONLY><<<grid, kThreadsAll, L::bytes, st>>>(mn, mm, mwy, muo, mvr, mlc, A);
     return cudaGetLastError();
 }
 
