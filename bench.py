@@ -131,6 +131,22 @@ def _dist():
     return world, rank, local
 
 
+def max_over_ranks(t, device):
+    """The slowest rank's time: the job ends when every replica has."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return t
+    tt = torch.tensor([t], dtype=torch.float64, device=device)
+    dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+    return float(tt.item())
+
+
+def job_rate(cells, steps, world, t):
+    """Whole-job rate: every replica advances its own grid (weak scaling)."""
+    return world * cells * steps / t / 1e9
+
+
 def _inputs(mr, h, w):
     """Seeded synthetic coarse velocity and initial scalar for handle h."""
     from paper_1805_03426_gb300 import synth
@@ -198,11 +214,8 @@ def run_mr(args):
         dist.barrier()
     with ClockSampler(local) as clk:
         t = _time_steps(torch, mr, h, args.steps, args.warmup, stream)
-    if world > 1:
-        tt = torch.tensor([t], device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t = float(tt.item())
-    value = world * cells * args.steps / t / 1e9
+    t = max_over_ranks(t, "cuda")
+    value = job_rate(cells, args.steps, world, t)
     st = mr.mr_scalar_stats(h, stream=stream, allow_nonfinite=True)
 
     # roofline of the dominant (only) kernel of the step: one launch per step

@@ -162,6 +162,20 @@ int mr_cfl_dt(mr_handle h, double cfl, double* dt_out, mr_stream stream);
 /* Replace the time step. */
 int mr_set_dt(mr_handle h, double dt);
 
+/* Upscale integration (Section 3.3): Tc (nz x ny x nx doubles, host or
+ * device) receives the volume-weighted average of T^n over every coarse cell,
+ * the value the coarse momentum solver of a coupled run consumes.  Synchronises. */
+int mr_upscale_scalar(mr_handle h, double* Tc, mr_stream stream);
+
+/* Heat-flux diagnostics (Section 4.1).  nu_z (host, Nz + 1 doubles, may be
+ * NULL): the plane average of Nu(z) = (Ra Pr)^1/2 w T - dT/dz on every dense
+ * z-face, with the face value and gradient of the step's discretisation (at the
+ * plates the conductive flux alone).  nu_T (host, may be NULL): Nu_T =
+ * eps_T (Ra Pr)^1/2 = <|grad T|^2>, the volume average of the squared face
+ * gradients weighted by each face's dual volume, plates at their Dirichlet
+ * values.  FP64; synchronises.  Fused modes refine into temporary dense faces. */
+int mr_scalar_profiles(mr_handle h, double* nu_z, double* nu_T, mr_stream stream);
+
 /* Gradients (hand-written discrete adjoint of the scheme above).
  * mr_adjoint_forward runs nsteps steps from the scalar just set by
  * mr_set_scalar (MR_ERR_STATE otherwise), storing the pair (T^{s-1}, T^s)

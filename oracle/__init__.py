@@ -112,6 +112,8 @@ def _load():
             "or_cfl_dt": (d, [cp, dp, dp, dp, d]),
             "or_adjoint": (ctypes.c_int, [cp, dp, dp, dp, dp, i64, dp, dp, dp, dp, dp, dp, dp]),
             "or_index_maps": (ctypes.c_int, [cp, ip]),
+            "or_upscale": (ctypes.c_int, [cp, dp, dp]),
+            "or_nusselt_profile": (ctypes.c_int, [cp, dp, dp, dp, dp]),
         }
         for name, (res, args) in sig.items():
             f = getattr(_lib, name)
@@ -282,3 +284,23 @@ def index_maps(cfg: Config) -> np.ndarray:
     c = cfg._c()
     _check(_load().or_index_maps(ctypes.byref(c), _p(out)), "index_maps")
     return out
+
+
+def upscale(cfg: Config, T):
+    """Volume-weighted average of the dense scalar over each coarse cell (Section 3.3)."""
+    T = _f64(T, cfg.shapes()["T"])
+    Tc = np.empty((cfg.nz, cfg.ny, cfg.nx))
+    c = cfg._c()
+    _check(_load().or_upscale(ctypes.byref(c), _p(T), _p(Tc)), "upscale")
+    return Tc
+
+
+def nusselt_profile(cfg: Config, T, Ws):
+    """(Nu(z) on the Nz+1 dense z-faces, Nu_T from the thermal dissipation), Section 4.1."""
+    sh = cfg.shapes()
+    T, Ws = _f64(T, sh["T"]), _f64(Ws, sh["Ws"])
+    nu_z = np.empty(cfg.dense[2] + 1)
+    nu_T = ctypes.c_double(0.0)
+    c = cfg._c()
+    _check(_load().or_nusselt_profile(ctypes.byref(c), _p(T), _p(Ws), _p(nu_z), ctypes.byref(nu_T)), "nusselt_profile")
+    return nu_z, nu_T.value

@@ -976,3 +976,88 @@ int or_index_maps(const or_cfg* c, int32_t* out)
     geom_free(g);
     return 0;
 }
+
+/* ------------------------------------------------------------------------ */
+/* Upscale integration and heat-flux diagnostics                             */
+/* ------------------------------------------------------------------------ */
+
+int or_upscale(const or_cfg* c, const double* T, double* Tc)
+{
+    geom G, *g = &G;
+    if (geom_init(c, g)) return -1;
+    for (int K = 0; K < c->nz; ++K)
+        for (int J = 0; J < c->ny; ++J)
+            for (int I = 0; I < c->nx; ++I) {
+                double s = 0.0, v = 0.0;
+                for (int k = K * c->mz; k < (K + 1) * c->mz; ++k)
+                    for (int j = J * c->my; j < (J + 1) * c->my; ++j)
+                        for (int i = I * c->mx; i < (I + 1) * c->mx; ++i) {
+                            double vol = g->dx * g->dy * g->dz[k];
+                            s += T[IDX_C(g, k, j, i)] * vol;
+                            v += vol;
+                        }
+                Tc[((size_t)K * c->ny + J) * c->nx + I] = s / v;
+            }
+    geom_free(g);
+    return 0;
+}
+
+int or_nusselt_profile(const or_cfg* c, const double* T, const double* Ws, double* nu_z, double* nu_T)
+{
+    geom G, *g = &G;
+    if (geom_init(c, g)) return -1;
+    const int Nx = g->Nx, Ny = g->Ny, Nz = g->Nz, walls = c->walls_xy;
+    const double inv_area = 1.0 / ((double)Nx * Ny);
+    /* Nu(z) on every z-face: advective heat flux / kappa minus the mean gradient */
+    for (int k = 0; k <= Nz; ++k) {
+        double s = 0.0;
+        for (int j = 0; j < Ny; ++j)
+            for (int i = 0; i < Nx; ++i) {
+                if (k == 0) s += (T_BOTTOM - T[IDX_C(g, 0, j, i)]) / (g->zc[0] - g->zf[0]);
+                else if (k == Nz) s += (T[IDX_C(g, Nz - 1, j, i)] - T_TOP) / (g->zf[Nz] - g->zc[Nz - 1]);
+                else {
+                    double Tl = T[IDX_C(g, k - 1, j, i)], Tr = T[IDX_C(g, k, j, i)];
+                    double Tf = (g->dz[k] * Tl + g->dz[k - 1] * Tr) / (g->dz[k - 1] + g->dz[k]);
+                    double grad = (Tr - Tl) / (g->zc[k] - g->zc[k - 1]);
+                    s += Ws[IDX_W(g, k, j, i)] * Tf / c->kappa - grad;
+                }
+            }
+        nu_z[k] = s * inv_area;
+    }
+    /* thermal dissipation: kappa sum_faces A d (dT/d)^2 / V, plates at their Dirichlet values */
+    double e = 0.0, vt = 0.0;
+    for (int k = 0; k < Nz; ++k) {
+        vt += g->dx * g->dy * g->dz[k] * Nx * Ny;
+        for (int j = 0; j < Ny; ++j)
+            for (int i = 0; i < Nx; ++i) {
+                double t = T[IDX_C(g, k, j, i)];
+                if (!(walls && i == 0)) {
+                    double d = t - T[IDX_C(g, k, j, walls ? i - 1 : (i - 1 + Nx) % Nx)];
+                    e += d * d / (g->dx * g->dx) * g->dx * g->dy * g->dz[k];
+                }
+                if (!(walls && j == 0)) {
+                    double d = t - T[IDX_C(g, k, walls ? j - 1 : (j - 1 + Ny) % Ny, i)];
+                    e += d * d / (g->dy * g->dy) * g->dx * g->dy * g->dz[k];
+                }
+                double dist, d;
+                if (k > 0) {
+                    dist = g->zc[k] - g->zc[k - 1];
+                    d = t - T[IDX_C(g, k - 1, j, i)];
+                    e += d * d / (dist * dist) * g->dx * g->dy * dist;
+                } else if (c->plates_dirichlet) {
+                    dist = g->zc[0] - g->zf[0];
+                    d = t - T_BOTTOM;
+                    e += d * d / (dist * dist) * g->dx * g->dy * dist;
+                }
+                if (k == Nz - 1 && c->plates_dirichlet) {
+                    dist = g->zf[Nz] - g->zc[Nz - 1];
+                    d = T_TOP - t;
+                    e += d * d / (dist * dist) * g->dx * g->dy * dist;
+                }
+            }
+    }
+    /* Nu_T = eps_T (Ra Pr)^1/2 = kappa <|grad T|^2> / kappa */
+    *nu_T = e / vt;
+    geom_free(g);
+    return 0;
+}

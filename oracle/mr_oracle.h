@@ -71,6 +71,15 @@ int  or_adjoint(const or_cfg* c, const double* Us, const double* Vs, const doubl
                 const double* T0, int64_t nsteps, const double* wnu, const double* wvar,
                 double* loss, double* gT0, double* gUs, double* gVs, double* gWs);
 
+/* Upscale integration (Section 3.3): the volume-weighted average of the dense
+ * scalar over every coarse cell.  Tc: nz x ny x nx. */
+int  or_upscale(const or_cfg* c, const double* T, double* Tc);
+/* Heat-flux diagnostics (Section 4.1): nu_z[k], k = 0..Nz, the plane-averaged
+ * Nu(z) = (Ra Pr)^1/2 <w T> - <dT/dz> on every dense z-face (plates: the
+ * conductive flux only), and Nu_T = eps_T (Ra Pr)^1/2 with eps_T the volume-
+ * averaged thermal dissipation kappa <|grad T|^2> from face gradients. */
+int  or_nusselt_profile(const or_cfg* c, const double* T, const double* Ws, double* nu_z, double* nu_T);
+
 /* Integer maps for the bit-exact comparison: the coarse cell of every dense
  * cell along x, y, z, then the three coarse cells of the R window of every
  * coarse cell along x, y, z.  out: Nx + Ny + Nz + 3*(nx + ny + nz) ints.     */

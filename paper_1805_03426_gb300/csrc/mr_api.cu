@@ -268,7 +268,7 @@ void mr_destroy(mr_handle h)
                     b.metric, b.red, b.nu2, b.stage, b.tri};
     for (void* p : ptrs)
         if (p) cudaFree(p);
-    void* xptrs[] = {b.xwy, b.xuo, b.xvr, b.xlc};
+    void* xptrs[] = {b.xwy, b.xuo, b.xvr, b.xlc, b.diag};
     for (void* p : xptrs)
         if (p) cudaFree(p);
     void* aptrs[] = {h->adj.cp, h->adj.seg, h->adj.mu, h->adj.face, h->adj.scr, h->adj.out};
@@ -997,6 +997,86 @@ int mr_adjoint_backward(mr_handle h, double gscale, void* gT0, int32_t gT0_dtype
         if (gW && (rc = copy_out(h, cW, MR_F64, gW, MR_F64, h->ncW, st))) return rc;
     }
     return cuda_check(cudaStreamSynchronize(st), "mr_adjoint_backward");
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------- diagnostics
+
+extern "C" {
+
+int mr_upscale_scalar(mr_handle h, double* Tc, mr_stream stream)
+{
+    if (!h || !Tc) return set_error(MR_ERR_ARG, "mr_upscale_scalar: NULL argument");
+    if (!h->have_scalar) return set_error(MR_ERR_STATE, "mr_upscale_scalar: no scalar set");
+    cudaStream_t st = (cudaStream_t)stream;
+    DeviceBuffers& b = h->buf;
+    const size_t nc = (size_t)h->cfg.nx * h->cfg.ny * h->cfg.nz;
+    const size_t need = nc + (size_t)h->Nz + 1 + (size_t)h->Nz;
+    if (!b.diag) {
+        cudaError_t e = cudaMalloc((void**)&b.diag, need * sizeof(double));
+        if (e != cudaSuccess) return cuda_check(e, "mr_upscale_scalar: buffer");
+    }
+    const bool dev = is_device_pointer(Tc);
+    double* out = dev ? Tc : b.diag;
+    cudaError_t e = h->cfg.precision == MR_F64 ? launch_upscale<double>(h->g64, (const double*)b.T[h->ic], out, st)
+                                               : launch_upscale<float>(h->g32, (const float*)b.T[h->ic], out, st);
+    if (e != cudaSuccess) return cuda_check(e, "mr_upscale_scalar: launch");
+    if (!dev) e = cudaMemcpyAsync(Tc, out, nc * sizeof(double), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    return cuda_check(e, "mr_upscale_scalar");
+}
+
+int mr_scalar_profiles(mr_handle h, double* nu_z, double* nu_T, mr_stream stream)
+{
+    if (!h || (!nu_z && !nu_T)) return set_error(MR_ERR_ARG, "mr_scalar_profiles: NULL argument");
+    if (!h->have_scalar || !h->have_velocity)
+        return set_error(MR_ERR_STATE, "mr_scalar_profiles: call mr_refine_velocity and mr_set_scalar first");
+    cudaStream_t st = (cudaStream_t)stream;
+    DeviceBuffers& b = h->buf;
+    const size_t nc = (size_t)h->cfg.nx * h->cfg.ny * h->cfg.nz;
+    if (!b.diag) {
+        cudaError_t e = cudaMalloc((void**)&b.diag, (nc + 2 * (size_t)h->Nz + 1) * sizeof(double));
+        if (e != cudaSuccess) return cuda_check(e, "mr_scalar_profiles: buffer");
+    }
+    double* dnu = b.diag + nc;
+    double* dzc = dnu + h->Nz + 1;
+    cudaError_t e = cudaMemcpyAsync(dzc, h->zc.data(), h->Nz * sizeof(double), cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return cuda_check(e, "mr_scalar_profiles: centres");
+    // dense W of the refinement: stored, or refined into a temporary for the fused modes
+    const void* ws = b.Ws;
+    void *tu = nullptr, *tv = nullptr, *tw = nullptr;
+    if (h->cfg.velocity_mode != MR_VEL_STORED) {
+        e = cudaMalloc(&tu, h->nU * h->elt);
+        if (e == cudaSuccess) e = cudaMalloc(&tv, h->nV * h->elt);
+        if (e == cudaSuccess) e = cudaMalloc(&tw, h->nW * h->elt);
+        int rc = e != cudaSuccess ? cuda_check(e, "mr_scalar_profiles: temporary faces") : refine_into(h, tu, tv, tw, st);
+        if (rc) { cudaFree(tu); cudaFree(tv); cudaFree(tw); return rc; }
+        ws = tw;
+    }
+    const double zb = h->zc[0] - h->zf[0], zt = h->zf[h->Nz] - h->zc[h->Nz - 1];
+    e = h->cfg.precision == MR_F64
+            ? launch_nu_profile<double>(h->g64, (const double*)b.T[h->ic], (const double*)ws, dzc, 1.0 / h->kappa, zb, zt,
+                                        dnu, b.red, h->red_blocks, st)
+            : launch_nu_profile<float>(h->g32, (const float*)b.T[h->ic], (const float*)ws, dzc, 1.0 / h->kappa, zb, zt,
+                                       dnu, b.red, h->red_blocks, st);
+    std::vector<double> p;
+    int rc = e != cudaSuccess ? cuda_check(e, "mr_scalar_profiles: launch") : reduce_partials(h, 1, p, st);
+    if (tu) { cudaFree(tu); cudaFree(tv); cudaFree(tw); }
+    if (rc) return rc;
+    if (nu_T) {
+        double s = 0.0, vt = 0.0;
+        for (int q = 0; q < h->red_blocks; ++q) s += p[q];
+        for (int k = 0; k < h->Nz; ++k) vt += h->dz[k];
+        vt *= h->cfg.lx * h->cfg.ly;
+        *nu_T = s / vt;
+    }
+    if (nu_z) {
+        e = cudaMemcpy(nu_z, dnu, (h->Nz + 1) * sizeof(double), cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) return cuda_check(e, "mr_scalar_profiles: copy");
+        for (int k = 0; k <= h->Nz; ++k) nu_z[k] /= (double)h->Nx * (double)h->Ny;
+    }
+    return MR_OK;
 }
 
 }  // extern "C"

@@ -71,6 +71,7 @@ struct DeviceBuffers {
     float* xvr = nullptr;                      // [Nz][Ny+1][nxg]
     float* xlc = nullptr;                      // [Nz][12]
     float xrx[12] = {0};                       // R_x rows of the 4 cells of a 4-cell segment
+    double* diag = nullptr;                    // diagnostics: coarse T, Nu(z), dense z centres (lazy)
     int nxg = 0;
 };
 
@@ -139,6 +140,11 @@ cudaError_t launch_plate_nu(const Grid<P>& g, const P* T, const double* zb_zt, d
 template <typename P>
 cudaError_t launch_maxdiv(const Grid<P>& g, const P* Us, const P* Vs, const P* Ws, double* partials,
                           int blocks, cudaStream_t st);
+template <typename P>
+cudaError_t launch_upscale(const Grid<P>& g, const P* T, double* Tc, cudaStream_t st);
+template <typename P>
+cudaError_t launch_nu_profile(const Grid<P>& g, const P* T, const P* Ws, const double* zc, double inv_kappa, double zb,
+                              double zt, double* nu_z, double* partials, int blocks, cudaStream_t st);
 template <typename P>
 cudaError_t launch_cfl(const Grid<P>& g, const P* Us, const P* Vs, const P* Ws, double* partials,
                        int blocks, cudaStream_t st);

@@ -139,6 +139,84 @@ __global__ void __launch_bounds__(kRedThreads) k_cfl(Grid<P> g, const P* __restr
     block_reduce_store<1, true>(v, partials + blockIdx.x);
 }
 
+// Upscale integration (Section 3.3): volume average over every coarse cell.
+template <typename P>
+__global__ void k_upscale(Grid<P> g, const P* __restrict__ T, double* __restrict__ Tc)
+{
+    const size_t n = (size_t)g.nz * g.ny * g.nx;
+    for (size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (size_t)gridDim.x * blockDim.x) {
+        const int I = (int)(t % g.nx), J = (int)((t / g.nx) % g.ny), K = (int)(t / ((size_t)g.nx * g.ny));
+        double s = 0.0, h = 0.0;
+        for (int k = K * g.mz; k < (K + 1) * g.mz; ++k) {
+            double r = 0.0;
+            for (int j = J * g.my; j < (J + 1) * g.my; ++j)
+                for (int i = I * g.mx; i < (I + 1) * g.mx; ++i) r += (double)T[((size_t)k * g.Ny + j) * g.Nx + i];
+            s += r * (double)g.dz[k];
+            h += (double)g.dz[k];
+        }
+        Tc[t] = s / (h * g.mx * g.my);
+    }
+}
+
+// Nu(z) (Section 4.1) on dense z-face k = blockIdx.x: plane average of
+// w T_f / kappa - dT/dz (the plates: conductive flux only).
+template <typename P>
+__global__ void __launch_bounds__(256) k_nu_profile(Grid<P> g, const P* __restrict__ T, const P* __restrict__ Ws,
+                                                    const double* __restrict__ zc, double inv_kappa, double zb,
+                                                    double zt, double* __restrict__ nu_z)
+{
+    const int k = blockIdx.x;
+    const size_t plane = (size_t)g.Nx * g.Ny;
+    double v[1] = {0.0};
+    for (size_t m = threadIdx.x; m < plane; m += blockDim.x) {
+        if (k == 0) {
+            v[0] += (0.5 - (double)T[m]) / zb;
+        } else if (k == g.Nz) {
+            v[0] += ((double)T[(size_t)(g.Nz - 1) * plane + m] + 0.5) / zt;
+        } else {
+            const double tl = (double)T[(size_t)(k - 1) * plane + m], tr = (double)T[(size_t)k * plane + m];
+            const double tf = (double)g.wlo[k] * tl + (double)g.whi[k] * tr;
+            v[0] += (double)Ws[(size_t)k * plane + m] * tf * inv_kappa - (tr - tl) / (zc[k] - zc[k - 1]);
+        }
+    }
+    block_reduce_store<1, false>(v, nu_z + k);
+}
+
+// <|grad T|^2> from face gradients weighted by the face's dual volume (A d),
+// plates at their Dirichlet values: partial sums per block.
+template <typename P>
+__global__ void __launch_bounds__(kRedThreads) k_grad2(Grid<P> g, const P* __restrict__ T, const double* __restrict__ zc,
+                                                       double zb, double zt, double* __restrict__ partials)
+{
+    const size_t plane = (size_t)g.Nx * g.Ny, n = plane * g.Nz;
+    const double dx = (double)g.dx, dy = (double)g.dy;
+    double v[1] = {0.0};
+    for (size_t m = (size_t)blockIdx.x * blockDim.x + threadIdx.x; m < n; m += (size_t)gridDim.x * blockDim.x) {
+        const int i = (int)(m % g.Nx), j = (int)((m / g.Nx) % g.Ny), k = (int)(m / plane);
+        const double t = (double)T[m], dzk = (double)g.dz[k];
+        if (!(g.walls && i == 0)) {
+            const double d = t - (double)T[m - i + (i == 0 ? g.Nx - 1 : i - 1)];
+            v[0] += d * d * dy * dzk / dx;
+        }
+        if (!(g.walls && j == 0)) {
+            const double d = t - (double)T[m + ((ptrdiff_t)(j == 0 ? g.Ny - 1 : j - 1) - j) * g.Nx];
+            v[0] += d * d * dx * dzk / dy;
+        }
+        if (k > 0) {
+            const double d = t - (double)T[m - plane];
+            v[0] += d * d * dx * dy / (zc[k] - zc[k - 1]);
+        } else if (g.dirichlet) {
+            const double d = t - 0.5;
+            v[0] += d * d * dx * dy / zb;
+        }
+        if (k == g.Nz - 1 && g.dirichlet) {
+            const double d = -0.5 - t;
+            v[0] += d * d * dx * dy / zt;
+        }
+    }
+    block_reduce_store<1, false>(v, partials + blockIdx.x);
+}
+
 template <typename S, typename D>
 __global__ void k_convert(const S* __restrict__ src, D* __restrict__ dst, size_t n)
 {
@@ -162,6 +240,22 @@ cudaError_t launch_plate_nu(const Grid<P>& g, const P* T, const double* zb_zt, d
     // the partials live in out2[2..]: the caller's buffer holds 2 + 2 * kPlateBlocks doubles
     k_plate_partials<P><<<kPlateBlocks, 256, 0, st>>>(g, T, zb_zt[0], zb_zt[1], out2 + 2);
     k_plate_final<<<1, 32, 0, st>>>(out2 + 2, kPlateBlocks, 1.0 / ((double)g.Nx * g.Ny), out2);
+    return cudaGetLastError();
+}
+
+template <typename P>
+cudaError_t launch_upscale(const Grid<P>& g, const P* T, double* Tc, cudaStream_t st)
+{
+    k_upscale<P><<<152 * 8, kRedThreads, 0, st>>>(g, T, Tc);
+    return cudaGetLastError();
+}
+
+template <typename P>
+cudaError_t launch_nu_profile(const Grid<P>& g, const P* T, const P* Ws, const double* zc, double inv_kappa, double zb,
+                              double zt, double* nu_z, double* partials, int blocks, cudaStream_t st)
+{
+    k_nu_profile<P><<<g.Nz + 1, 256, 0, st>>>(g, T, Ws, zc, inv_kappa, zb, zt, nu_z);
+    k_grad2<P><<<blocks, kRedThreads, 0, st>>>(g, T, zc, zb, zt, partials);
     return cudaGetLastError();
 }
 
@@ -205,7 +299,10 @@ cudaError_t launch_convert(const void* src, int sd, void* dst, int dd, size_t n,
     template cudaError_t launch_plate_nu<P>(const Grid<P>&, const P*, const double*, double*, cudaStream_t);    \
     template cudaError_t launch_maxdiv<P>(const Grid<P>&, const P*, const P*, const P*, double*, int,          \
                                           cudaStream_t);                                                     \
-    template cudaError_t launch_cfl<P>(const Grid<P>&, const P*, const P*, const P*, double*, int, cudaStream_t);
+    template cudaError_t launch_cfl<P>(const Grid<P>&, const P*, const P*, const P*, double*, int, cudaStream_t);    \
+    template cudaError_t launch_upscale<P>(const Grid<P>&, const P*, double*, cudaStream_t);                       \
+    template cudaError_t launch_nu_profile<P>(const Grid<P>&, const P*, const P*, const double*, double, double,   \
+                                              double, double*, double*, int, cudaStream_t);
 MR_INST(double)
 MR_INST(float)
 #undef MR_INST

@@ -69,6 +69,8 @@ _SIGS = {
     "mr_debug_index_maps": (ctypes.c_int, [_VP, _VP, ctypes.c_size_t]),
     "mr_adjoint_forward": (ctypes.c_int, [_VP, _I64, _I32, _VP, _VP, ctypes.POINTER(_D), _VP]),
     "mr_adjoint_backward": (ctypes.c_int, [_VP, _D, _VP, _I32, _VP, _VP, _VP, _VP]),
+    "mr_upscale_scalar": (ctypes.c_int, [_VP, _VP, _VP]),
+    "mr_scalar_profiles": (ctypes.c_int, [_VP, _VP, ctypes.POINTER(_D), _VP]),
     "mr_refine_velocity_noalloc": (ctypes.c_int, [ctypes.POINTER(mr_config), _VP, _VP, _VP, _VP, _VP, _VP, _VP]),
 }
 
@@ -320,3 +322,20 @@ def mr_refine_velocity_noalloc(cfg: mr_config, U, V, W, Us, Vs, Ws, stream=None)
          "Us": Nz * Ny * (Nx + w), "Vs": Nz * (Ny + w) * Nx, "Ws": (Nz + 1) * Ny * Nx}
     args = [_ptr(a, n[k], np.float64, k) for a, k in zip((U, V, W, Us, Vs, Ws), ("U", "V", "W", "Us", "Vs", "Ws"))]
     _check(lib().mr_refine_velocity_noalloc(ctypes.byref(cfg), *args, _stream(stream)))
+
+
+def mr_upscale_scalar(h: Handle, Tc=None, stream=None):
+    """Volume-weighted coarse-cell averages of T^n (Section 3.3), FP64."""
+    c = h.cfg
+    if Tc is None:
+        Tc = np.empty((c.nz, c.ny, c.nx))
+    _check(lib().mr_upscale_scalar(h.ptr, _ptr(Tc, c.nz * c.ny * c.nx, np.float64, "Tc"), _stream(stream)))
+    return Tc
+
+
+def mr_scalar_profiles(h: Handle, stream=None):
+    """(Nu(z) on the Nz + 1 dense z-faces, Nu_T), Section 4.1."""
+    nu_z = np.empty(h.dense[2] + 1)
+    nu_T = _D()
+    _check(lib().mr_scalar_profiles(h.ptr, nu_z.ctypes.data, ctypes.byref(nu_T), _stream(stream)))
+    return nu_z, nu_T.value

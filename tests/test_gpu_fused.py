@@ -111,3 +111,16 @@ def test_fused_rejects_unsupported_shapes(mr, mode):
     assert e.value.code == mr.MR_ERR_ARG
     with pytest.raises(mr.MRError):
         mr.mr_create(Problem(32, 8, 4, mx=2, my=2, mz=2).mr_config(mr, mr.MR_F64, mode))
+
+
+def test_fused_diagnostics_fp32(mr, prob, mode):
+    """Upscale and Nu(z)/Nu_T from the FP32 fused state against the oracle."""
+    n = 11
+    h, T, _ = _run(mr, prob, mode, n)
+    vel = O.refine(prob.cfg, prob.U, prob.V, prob.W)
+    _, T_ref = O.run(prob.cfg, vel, prob.T0, n)
+    assert np.abs(mr.mr_upscale_scalar(h) - O.upscale(prob.cfg, T_ref)).max() <= F32_T_TOL
+    nu_z, nu_T = mr.mr_scalar_profiles(h)
+    nz_ref, nT_ref = O.nusselt_profile(prob.cfg, T_ref, vel[2])
+    assert np.abs(nu_z - nz_ref).max() <= F32_NU_TOL * np.abs(nz_ref).max() * 10
+    assert abs(nu_T - nT_ref) <= F32_NU_TOL * abs(nT_ref)

@@ -214,3 +214,18 @@ def test_nonfinite_scalar_reported(mr):
     with pytest.raises(mr.MRError) as e:
         mr.mr_scalar_stats(h)
     assert e.value.code == mr.MR_ERR_NONFINITE
+
+
+def test_upscale_and_profiles_match_oracle(mr, prob):
+    """Section 3.3 upscale integration and Section 4.1 Nu(z), Nu_T (FP64)."""
+    n = 9
+    h, T, _ = _run_gpu(mr, prob, "f64", n)
+    vel = O.refine(prob.cfg, prob.U, prob.V, prob.W)
+    _, T_ref = O.run(prob.cfg, vel, prob.T0, n)
+    Tc = mr.mr_upscale_scalar(h)
+    Tc_ref = O.upscale(prob.cfg, T_ref)
+    assert rel_err(Tc, Tc_ref) <= F64_TOL
+    nu_z, nu_T = mr.mr_scalar_profiles(h)
+    nz_ref, nT_ref = O.nusselt_profile(prob.cfg, T_ref, vel[2])
+    assert np.abs(nu_z - nz_ref).max() <= 1e-10 * np.abs(nz_ref).max()
+    assert abs(nu_T - nT_ref) <= 1e-10 * abs(nT_ref)

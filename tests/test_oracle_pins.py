@@ -456,3 +456,57 @@ def test_adjoint_dot_product_nu_is_affine(oracle_mod):
     d = np.random.default_rng(2).standard_normal(T0.shape)
     L1 = O.adjoint(cfg, vel, T0 + d, S, wnu, None)[0]
     assert abs((L1 - L0) - np.vdot(gT0, d)) < 1e-11
+
+
+# ----------------------------------------------------------------------------- upscale, Nu(z), Nu_T
+
+def test_upscale_conserves_and_averages_linear_profile(oracle_mod):
+    """Section 3.3: the coarse value is the volume average of its dense cells:
+    the integral is unchanged, and the cell-centre height z_c averages to the
+    coarse cell's midpoint (sum (z_k+z_k+1)/2 dz / sum dz) on any stretching."""
+    O = oracle_mod
+    cfg = _cfg(O, nx=4, ny=3, nz=5, mx=2, my=3, mz=4, gamma=1.5, ly=0.9)
+    g = O.grid(cfg)
+    Nx, Ny, Nz = cfg.dense
+    T = np.random.default_rng(4).standard_normal((Nz, Ny, Nx))
+    Tc = O.upscale(cfg, T)
+    vol = (cfg.lx / Nx) * (cfg.ly / Ny) * g["dz"][:, None, None]
+    Vc = (cfg.lx / cfg.nx) * (cfg.ly / cfg.ny) * np.diff(g["Zf"])[:, None, None]
+    assert abs((Tc * Vc).sum() - (T * vol).sum()) < 1e-13
+    Tz = np.broadcast_to(g["zc"][:, None, None], (Nz, Ny, Nx)).copy()
+    Zc = O.upscale(cfg, Tz)
+    mid = 0.5 * (g["Zf"][1:] + g["Zf"][:-1])
+    np.testing.assert_allclose(Zc, np.broadcast_to(mid[:, None, None], Zc.shape), atol=1e-15)
+
+
+@pytest.mark.parametrize("gamma", [0.0, 1.5])
+def test_nusselt_profile_conduction_is_one(oracle_mod, gamma):
+    """Conduction (T = 0.5 - z_c, no flow): Nu(z) = 1 on every face and
+    Nu_T = <|grad T|^2> = 1, including the half cells at the plates."""
+    O = oracle_mod
+    cfg = _cfg(O, nx=3, ny=3, nz=5, mx=2, my=2, mz=3, gamma=gamma)
+    g = O.grid(cfg)
+    Nx, Ny, Nz = cfg.dense
+    T = np.broadcast_to((0.5 - g["zc"])[:, None, None], (Nz, Ny, Nx)).copy()
+    nu_z, nu_T = O.nusselt_profile(cfg, T, np.zeros(cfg.shapes()["Ws"]))
+    np.testing.assert_allclose(nu_z, 1.0, atol=1e-12)
+    assert abs(nu_T - 1.0) < 1e-12
+
+
+def test_nusselt_profile_advective_part_on_linear_profile(oracle_mod):
+    """For T = 0.5 - z_c the face value is exactly 0.5 - z_face (linear
+    interpolation reproduces linear profiles on any stretching), so on every
+    interior face Nu(z) = 1 + <w (0.5 - z_face)> / kappa: pins the advective
+    term's face value, sign and 1/kappa scaling."""
+    O = oracle_mod
+    cfg = _cfg(O, nx=3, ny=3, nz=4, mx=1, my=1, mz=4, gamma=1.2)
+    g = O.grid(cfg)
+    Nx, Ny, Nz = cfg.dense
+    T = np.broadcast_to((0.5 - g["zc"])[:, None, None], (Nz, Ny, Nx)).copy()
+    W = np.random.default_rng(2).standard_normal(cfg.shapes()["Ws"])
+    W[0] = W[-1] = 0.0
+    nu_z, _ = O.nusselt_profile(cfg, T, W)
+    # the advective part is <w T_f>/kappa with T_f = 0.5 - z_face exactly (linear interpolation)
+    zf = g["zf"]
+    adv = (W[1:-1] * (0.5 - zf[1:-1])[:, None, None]).mean(axis=(1, 2)) / cfg.kappa
+    np.testing.assert_allclose(nu_z[1:-1], 1.0 + adv, rtol=1e-12, atol=1e-12)
