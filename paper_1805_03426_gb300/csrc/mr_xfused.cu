@@ -43,15 +43,18 @@ template <int M>
 struct XT {
     static constexpr int CX = kTX / M;
     static constexpr int BXC = CX + 8;                  // coarse box width: columns I0-4 .. I0+CX+3
-    static constexpr int NB = (M == 4) ? 6 : 5;         // ring slots
-    // one ring slot (floats): T^n plane, T^{n-1} plane, then the bundle of one layer
+    static constexpr int NB = (M == 4) ? 7 : 6;         // ring slots
+    // one ring slot (floats): T^n plane, T^{n-1} plane, then the bundle of one
+    // layer k: WY of its upper plane k+1 (its lower plane k is the previous
+    // slot's), UO and VR of layer k, the layer constants
     static constexpr int oTn = 0, oTm = kPlaneSlot;
-    static constexpr int oWY = 2 * kPlaneSlot;          // [2][TY][BXC]   planes k, k+1
-    static constexpr int oUO = oWY + 2 * kTY * BXC;     // [TY][BXC]
+    static constexpr int oWY = 2 * kPlaneSlot;          // [TY][BXC]      plane k+1
+    static constexpr int oUO = oWY + kTY * BXC;         // [TY][BXC]
     static constexpr int oVR = oUO + kTY * BXC;         // [TY+1][BXC]
     static constexpr int oLC = ((oVR + (kTY + 1) * BXC) + 31) / 32 * 32;   // [12] layer constants (128-B aligned)
     static constexpr int slot = (((oLC + 16) * 4 + 127) / 128) * 128 / 4;
-    static constexpr uint32_t bundle_bytes = (uint32_t)(2 * kTY * BXC + kTY * BXC + (kTY + 1) * BXC + 12) * 4;
+    static constexpr uint32_t wy_bytes = (uint32_t)(kTY * BXC) * 4;
+    static constexpr uint32_t bundle_bytes = (uint32_t)(kTY * BXC + (kTY + 1) * BXC + 12) * 4;   // UO, VR, LC
     static constexpr int oRed = NB * slot;              // 64 floats
     static constexpr int oBar = ((oRed + 64) * 4 + 7) / 8;
     static constexpr size_t bytes = (size_t)(oBar + 2 * NB) * 8;
@@ -72,7 +75,8 @@ struct XArgs {
                          // same for every thread: kept in the constant bank)
 };
 
-template <int M, bool DIVONLY>
+// LF: a plain leapfrog step (a = 1, b = 0), by far the most frequent kind.
+template <int M, bool DIVONLY, bool LF>
 __global__ void __launch_bounds__(kThreadsAll, 2)
 k_xfused(const __grid_constant__ CUtensorMap tmn, const __grid_constant__ CUtensorMap tmm,
          const __grid_constant__ CUtensorMap twy, const __grid_constant__ CUtensorMap tuo,
@@ -93,6 +97,7 @@ k_xfused(const __grid_constant__ CUtensorMap tmn, const __grid_constant__ CUtens
     const int k1 = min(k0 + A.kcl, g.Nz);
     if (k0 >= k1) return;
     const int nrings = k1 - k0 + 2;              // ring r: plane k0-1+r and the bundle of layer k0+r-2
+                                                 // (ring 1 carries only WY of plane k0)
 
     if (tid == 0) {
         for (int s = 0; s < NB; ++s) {
@@ -115,14 +120,15 @@ k_xfused(const __grid_constant__ CUtensorMap tmn, const __grid_constant__ CUtens
             float* slot = sm + s * L::slot;
             const bool bundle = (r >= 2);
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-            mbar_expect_tx(&full[s], (DIVONLY ? 0u : 2 * kPlaneBytes) + (bundle ? L::bundle_bytes : 0u));
+            mbar_expect_tx(&full[s], (DIVONLY ? 0u : 2 * kPlaneBytes) + (r >= 1 ? L::wy_bytes : 0u) +
+                                         (bundle ? L::bundle_bytes : 0u));
             if (!DIVONLY) {
                 tma_3d(slot + L::oTn, &tmn, i0 - 4, j0 - 1, k0 - 1 + r, &full[s]);
                 tma_3d(slot + L::oTm, &tmm, i0 - 4, j0 - 1, k0 - 1 + r, &full[s]);
             }
+            if (r >= 1) tma_3d(slot + L::oWY, &twy, I0, j0, k0 - 1 + r, &full[s]);   // WY plane k0-1+r
             if (bundle) {
                 const int kb = k0 + r - 2;
-                tma_3d(slot + L::oWY, &twy, I0, j0, kb, &full[s]);
                 tma_3d(slot + L::oUO, &tuo, I0, j0, kb, &full[s]);
                 tma_3d(slot + L::oVR, &tvr, I0, j0, kb, &full[s]);
                 tma_3d(slot + L::oLC, &tlc, 0, kb, 0, &full[s]);
@@ -171,8 +177,8 @@ k_xfused(const __grid_constant__ CUtensorMap tmn, const __grid_constant__ CUtens
             {
                 // R_x splits of the full-width W (planes k, k+1) and V (faces jl, jl+1);
                 // bundle column xb holds coarse column I0 - 4 + xb
-                const float* yb = bun + L::oWY + jl * BXC + cb0 + 3;
-                const float* yt = yb + kTY * BXC;
+                const float* yb = sm + sc * L::slot + L::oWY + jl * BXC + cb0 + 3;   // plane k (previous slot)
+                const float* yt = bun + L::oWY + jl * BXC + cb0 + 3;                  // plane k+1
                 const float* rs = bun + L::oVR + jl * BXC + cb0 + 3;
                 const float* rn = rs + BXC;
 #pragma unroll
@@ -263,7 +269,7 @@ k_xfused(const __grid_constant__ CUtensorMap tmn, const __grid_constant__ CUtens
                     const float cy = (vs[a] * hiy) * (tsv[a] + tc) - (vn[a] * hiy) * (tc + tnv[a]);
                     const float cz = wb[a] * (bwlo * tbv[a] + bwhi * tc) - wt[a] * (twlo * tc + twhi * ttv[a]);
                     const float D = kx2 * (dcv[a] + dcv[a + 2]) + ky2 * (dsv[a] + dnv[a]) + cdn * dbv[a] + cup * dtv[a] - diag * dc;
-                    res[a] = ca * dc + cbb * tc + gdt * ((cx + cy + cz) + D);
+                    res[a] = LF ? dc + gdt * ((cx + cy + cz) + D) : ca * dc + cbb * tc + gdt * ((cx + cy + cz) + D);
                 }
                 *reinterpret_cast<float4*>(outp) = make_float4(res[0], res[1], res[2], res[3]);
             }
@@ -421,7 +427,7 @@ int kcl_override()
     return v;
 }
 
-template <int M, bool DIVONLY>
+template <int M, bool DIVONLY, bool LF>
 cudaError_t launch_x(const Grid<float>& g, const float* WY, const float* UO, const float* VR, int nxg, const float* lc,
                      const float* rx12, const float* Tm1, const float* T, float* Tp1, StepCoef c, int* err,
                      unsigned long long* divmax, cudaStream_t st)
@@ -429,7 +435,7 @@ cudaError_t launch_x(const Grid<float>& g, const float* WY, const float* UO, con
     using L = XT<M>;
     static bool attr = false;
     if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(k_xfused<M, DIVONLY>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L::bytes);
+        cudaError_t e = cudaFuncSetAttribute(k_xfused<M, DIVONLY, LF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L::bytes);
         if (e != cudaSuccess) return e;
         attr = true;
     }
@@ -439,7 +445,7 @@ cudaError_t launch_x(const Grid<float>& g, const float* WY, const float* UO, con
     if (!DIVONLY && (!cached_map3(&mn, T, g.Nx, g.Ny, g.Nz, kBX, kBY, 1) ||
                      !cached_map3(&mm, Tm1, g.Nx, g.Ny, g.Nz, kBX, kBY, 1)))
         return cudaErrorInvalidValue;
-    if (!cached_map3(&mwy, WY, nxg, g.Ny, g.Nz + 1, L::BXC, kTY, 2) ||
+    if (!cached_map3(&mwy, WY, nxg, g.Ny, g.Nz + 1, L::BXC, kTY, 1) ||
         !cached_map3(&muo, UO, nxg, g.Ny, g.Nz, L::BXC, kTY, 1) ||
         !cached_map3(&mvr, VR, nxg, g.Ny + 1, g.Nz, L::BXC, kTY + 1, 1) ||
         !cached_map3(&mlc, lc, 12, g.Nz, 1, 12, 1, 1))
@@ -447,7 +453,7 @@ cudaError_t launch_x(const Grid<float>& g, const float* WY, const float* UO, con
     const int tiles = (g.Nx / kTX) * (g.Ny / kTY);
     int kcl = kcl_override();
     if (kcl <= 0) {
-        const int want = 152 * 2 * 8;                     // ~8 waves at 2 CTAs / SM
+        const int want = 152 * 2 * 12;                    // ~12 waves at 2 CTAs / SM
         int chunks = (want + tiles - 1) / tiles;
         chunks = max(1, min(chunks, g.Nz / 4));
         kcl = (g.Nz + chunks - 1) / chunks;
@@ -456,7 +462,7 @@ cudaError_t launch_x(const Grid<float>& g, const float* WY, const float* UO, con
     XArgs A{g, T, Tm1, Tp1, lc, (float)c.a, (float)c.b, (float)c.gdt, kcl, err, divmax, {}};
     memcpy(A.rx, rx12, sizeof A.rx);
     dim3 grid(chunks, g.Nx / kTX, g.Ny / kTY);
-    k_xfused<M, DIVONLY><<<grid, kThreadsAll, L::bytes, st>>>(mn, mm, mwy, muo, mvr, mlc, A);
+    k_xfused<M, DIVONLY, LF><<<grid, kThreadsAll, L::bytes, st>>>(mn, mm, mwy, muo, mvr, mlc, A);
     return cudaGetLastError();
 }
 
@@ -480,8 +486,12 @@ cudaError_t launch_step_xfused_f32(const Grid<float>& g, const float* WY, const 
 {
     int* err = fused_error_flag();
     if (!err) return cudaErrorMemoryAllocation;
-    if (g.mx == 4) return launch_x<4, false>(g, WY, UO, VR, nxg, lc, rx12, Tm1, T, Tp1, c, err, nullptr, st);
-    return launch_x<2, false>(g, WY, UO, VR, nxg, lc, rx12, Tm1, T, Tp1, c, err, nullptr, st);
+    const bool lf = (c.a == 1.0 && c.b == 0.0);
+    if (g.mx == 4)
+        return lf ? launch_x<4, false, true>(g, WY, UO, VR, nxg, lc, rx12, Tm1, T, Tp1, c, err, nullptr, st)
+                  : launch_x<4, false, false>(g, WY, UO, VR, nxg, lc, rx12, Tm1, T, Tp1, c, err, nullptr, st);
+    return lf ? launch_x<2, false, true>(g, WY, UO, VR, nxg, lc, rx12, Tm1, T, Tp1, c, err, nullptr, st)
+              : launch_x<2, false, false>(g, WY, UO, VR, nxg, lc, rx12, Tm1, T, Tp1, c, err, nullptr, st);
 }
 
 cudaError_t launch_maxdiv_xfused_f32(const Grid<float>& g, const float* WY, const float* UO, const float* VR, int nxg,
@@ -493,8 +503,8 @@ cudaError_t launch_maxdiv_xfused_f32(const Grid<float>& g, const float* WY, cons
     if (e != cudaSuccess) return e;
     unsigned long long* dm = reinterpret_cast<unsigned long long*>(partials);
     StepCoef c{0, 0, 0};
-    if (g.mx == 4) return launch_x<4, true>(g, WY, UO, VR, nxg, lc, rx12, nullptr, nullptr, nullptr, c, err, dm, st);
-    return launch_x<2, true>(g, WY, UO, VR, nxg, lc, rx12, nullptr, nullptr, nullptr, c, err, dm, st);
+    if (g.mx == 4) return launch_x<4, true, false>(g, WY, UO, VR, nxg, lc, rx12, nullptr, nullptr, nullptr, c, err, dm, st);
+    return launch_x<2, true, false>(g, WY, UO, VR, nxg, lc, rx12, nullptr, nullptr, nullptr, c, err, dm, st);
 }
 
 }  // namespace mr
