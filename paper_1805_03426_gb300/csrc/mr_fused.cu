@@ -26,6 +26,8 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <mutex>
+
 #include "mr_internal.cuh"
 #include "mr_ptx.cuh"
 
@@ -468,12 +470,34 @@ bool make_map(CUtensorMap* m, const float* base, const Grid<float>& g)
               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
+}  // namespace
+
+// Raise a kernel's dynamic shared-memory limit once per device; *done holds
+// one bit per device index.
+cudaError_t smem_optin(const void* kernel, int bytes, unsigned long long* done)
+{
+    static std::mutex mu;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(mu);
+    if (*done >> dev & 1ull) return cudaSuccess;
+    e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e == cudaSuccess) *done |= 1ull << dev;
+    return e;
+}
+
+namespace {
+
 // Tensor maps of the (few) scalar buffers in use, encoded once each.
 bool cached_map(CUtensorMap* m, const float* base, const Grid<float>& g)
 {
     struct Entry { const float* p; int nx, ny, nz; CUtensorMap map; };
     static Entry cache[16];
     static int n = 0;
+    static std::mutex mu;
+    std::lock_guard<std::mutex> lock(mu);
     for (int q = 0; q < n; ++q)
         if (cache[q].p == base && cache[q].nx == g.Nx && cache[q].ny == g.Ny && cache[q].nz == g.Nz) {
             *m = cache[q].map;
@@ -503,13 +527,9 @@ cudaError_t launch_fused(const Grid<float>& g, const float* U, const float* V, c
                          cudaStream_t st)
 {
     using L = Tile<M>;
-    static bool attr = false;
-    if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(k_fused<M, DIVONLY>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)L::bytes);
-        if (e != cudaSuccess) return e;
-        attr = true;
-    }
+    static unsigned long long attr = 0;                   // one bit per device
+    cudaError_t e = smem_optin(reinterpret_cast<const void*>(k_fused<M, DIVONLY>), (int)L::bytes, &attr);
+    if (e != cudaSuccess) return e;
     CUtensorMap mn, mm;
     if (!DIVONLY) {
         if (!cached_map(&mn, T, g) || !cached_map(&mm, Tm1, g)) return cudaErrorInvalidValue;
@@ -554,24 +574,45 @@ bool fused_supported(const mr_config& cfg, std::string* why)
 }
 
 // Device error flag of the fused kernels (MR_ERR_TIMEOUT after a bounded wait
-// gave up).  One per process; read and cleared by fused_take_error.
-static int* g_err = nullptr;
+// gave up).  One per device, allocated on first use; read and cleared by
+// fused_take_error on the caller's stream.
+static int* g_err[64] = {};
+static std::mutex g_err_mu;
+
+static int** err_slot()
+{
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+    return &g_err[dev];
+}
+
 int* fused_error_flag()
 {
-    if (!g_err) {
-        if (cudaMalloc(&g_err, sizeof(int)) != cudaSuccess) return nullptr;
-        cudaMemset(g_err, 0, sizeof(int));
+    std::lock_guard<std::mutex> lock(g_err_mu);
+    int** slot = err_slot();
+    if (!slot) return nullptr;
+    if (!*slot) {
+        int* p = nullptr;
+        if (cudaMalloc(&p, sizeof(int)) != cudaSuccess) return nullptr;
+        if (cudaMemset(p, 0, sizeof(int)) != cudaSuccess) { cudaFree(p); return nullptr; }
+        *slot = p;
     }
-    return g_err;
+    return *slot;
 }
 
 int fused_take_error(cudaStream_t st)
 {
-    if (!g_err) return 0;
+    int* flag = nullptr;
+    {
+        std::lock_guard<std::mutex> lock(g_err_mu);
+        int** slot = err_slot();
+        if (slot) flag = *slot;
+    }
+    if (!flag) return 0;
     int v = 0;
-    if (cudaMemcpyAsync(&v, g_err, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess) return MR_ERR_CUDA;
-    cudaStreamSynchronize(st);
-    if (v) cudaMemsetAsync(g_err, 0, sizeof(int), st);
+    if (cudaMemcpyAsync(&v, flag, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess) return MR_ERR_CUDA;
+    if (cudaStreamSynchronize(st) != cudaSuccess) return MR_ERR_CUDA;
+    if (v) cudaMemsetAsync(flag, 0, sizeof(int), st);
     return v;
 }
 

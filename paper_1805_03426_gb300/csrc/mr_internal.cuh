@@ -155,6 +155,8 @@ cudaError_t launch_maxdiv_fused_f32(const Grid<float>& g, const float* U, const 
                                     const float* W, double* partials, int blocks, cudaStream_t st);
 bool fused_supported(const mr_config& cfg, std::string* why);
 int* fused_error_flag();
+// Raise a kernel's dynamic shared-memory limit once per device (*done: one bit per device).
+cudaError_t smem_optin(const void* kernel, int bytes, unsigned long long* done);
 template <typename P>
 cudaError_t launch_column_balance(const Grid<P>& g, const P* U, const P* V, const P* W, P* scrW, cudaStream_t st);
 cudaError_t launch_xfused_prep(const Grid<float>& g, const float* U, const float* V, const float* W, float* scrW,

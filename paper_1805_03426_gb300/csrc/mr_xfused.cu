@@ -22,6 +22,8 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <mutex>
+
 #include "mr_internal.cuh"
 #include "mr_ptx.cuh"
 
@@ -403,6 +405,8 @@ bool cached_map3(CUtensorMap* out, const float* base, int d0, int d1, int d2, in
     struct Entry { const float* p; int d[6]; CUtensorMap m; };
     static Entry cache[32];
     static int n = 0, next = 0;
+    static std::mutex mu;
+    std::lock_guard<std::mutex> lock(mu);
     const int key[6] = {d0, d1, d2, b0, b1, b2};
     for (int q = 0; q < n; ++q)
         if (cache[q].p == base && !memcmp(cache[q].d, key, sizeof key)) {
@@ -433,12 +437,9 @@ cudaError_t launch_x(const Grid<float>& g, const float* WY, const float* UO, con
                      unsigned long long* divmax, cudaStream_t st)
 {
     using L = XT<M>;
-    static bool attr = false;
-    if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(k_xfused<M, DIVONLY, LF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L::bytes);
-        if (e != cudaSuccess) return e;
-        attr = true;
-    }
+    static unsigned long long attr = 0;                   // one bit per device
+    cudaError_t e = smem_optin(reinterpret_cast<const void*>(k_xfused<M, DIVONLY, LF>), (int)L::bytes, &attr);
+    if (e != cudaSuccess) return e;
     CUtensorMap mn, mm, mwy, muo, mvr, mlc;
     memset(&mn, 0, sizeof mn);
     memset(&mm, 0, sizeof mm);
