@@ -237,6 +237,12 @@ def run_mr(args):
             "kernel": kname,
             "bytes_per_cell": round(bytes_per_cell, 3), "launch_ms": round(per_launch * 1e3, 4)}
 
+    # temporal refinement (Section 3.4): coarse steps of mt dense steps each,
+    # the next coarse velocity resident on the device
+    temporal = None
+    if rank == 0 and not args.no_temporal:
+        temporal = temporal_cost(torch, mr, h, w, (dU, dV, dW), cells, stream)
+
     # FP64 path on the same grid (stored velocity), for the FP32/FP64 ratio
     fp64 = None
     if rank == 0 and prec == mr.MR_F32 and not args.no_fp64:
@@ -293,7 +299,8 @@ def run_mr(args):
                        "velocity_mode": args.mode, "dt": dt, "parallelism": f"replicas{world}",
                        "l2": "inputs larger than L2 (3 scalar levels of %.0f MB)" % (cells * elt / 2**20),
             "bytes_per_cell": round(bytes_per_cell, 3)},
-            "roofline": roof, "fp64_path": fp64, "adjoint": adj, "e2e": e2e, "cpu_baseline": cpu,
+            "roofline": roof, "fp64_path": fp64, "adjoint": adj, "temporal": temporal, "e2e": e2e,
+            "cpu_baseline": cpu,
             "gpu_launches": args.steps, "clocks": clk.summary(),
             "final_stats": {k: st[k] for k in ("nu_bot", "nu_top", "mean", "var")},
         }
@@ -301,6 +308,39 @@ def run_mr(args):
     if world > 1:
         dist.barrier()
         dist.destroy_process_group()
+
+
+def temporal_cost(torch, mr, h, w, vel0, cells, stream, mt=4, K=20):
+    """Coarse steps with temporal refinement on the bench workload: each one
+    refines the next coarse velocity (device-resident FP64) and runs mt dense
+    steps, steps 1..mt-1 on the velocity interpolated in time.  Also times
+    mr_refine_velocity alone (the per-velocity work of the step's mode)."""
+    from paper_1805_03426_gb300 import synth
+    (_, _, _), zf = mr.mr_grid(h)
+    m = w["m"]
+    Xf = np.arange(w["nx"] + 1) / w["nx"]
+    Yf = np.arange(w["ny"] + 1) / w["ny"]
+    vel1 = tuple(torch.from_numpy(a).cuda()
+                 for a in synth.coarse_velocity(SEED + 1, Xf, Yf, zf[::m].copy(), 1.0, 1.0, rms=w["rms"]))
+    levels = (vel1, vel0)
+    for q in range(2):
+        mr.mr_scalar_coarse_step(h, *levels[q % 2], mt, stream=stream)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for q in range(K):
+        mr.mr_scalar_coarse_step(h, *levels[q % 2], mt, stream=stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t = e0.elapsed_time(e1) / 1e3
+    e0.record(stream)
+    for q in range(K):
+        mr.mr_refine_velocity(h, *levels[q % 2], stream=stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    tr = e0.elapsed_time(e1) / 1e3
+    return {"mt": mt, "coarse_steps": K, "value": round(cells * mt * K / t / 1e9, 3), "unit": "Gcell-updates/s",
+            "ms_per_coarse_step": round(t / K * 1e3, 4), "refine_velocity_ms": round(tr / K * 1e3, 4)}
 
 
 def adjoint_cost(torch, mr, stream, S=200, ck=20):
@@ -399,6 +439,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
+    ap.add_argument("--no-temporal", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

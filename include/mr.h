@@ -142,6 +142,20 @@ int mr_get_scalar(mr_handle h, void* T, void* Tprev, int32_t dtype, mr_stream st
  * step.  Needs mr_refine_velocity and mr_set_scalar first (MR_ERR_STATE). */
 int mr_scalar_step(mr_handle h, int64_t nsteps, mr_stream stream);
 
+/* One coarse time step with temporal refinement (Section 3.4, Eq. 18): the
+ * velocity set by mr_refine_velocity (or by the previous call) is U^{n-1};
+ * U, V, W (FP64, host or device, coarse layout as in mr_refine_velocity) are
+ * U^n.  Refines U^n, then advances mt >= 1 scalar steps, step i = 0..mt-1
+ * using the velocity U^{n-1} + (i/mt)(U^n - U^{n-1}) (a convex combination of
+ * two divergence-free fields, so divergence-free), with the handle's dt as the
+ * dense step (the coarse step being mt dt).  On return U^n is the current
+ * velocity.  The step count and the leapfrog state carry over.  The first
+ * call allocates a second velocity level (MR_ERR_OOM/MR_ERR_CUDA if that
+ * fails).  MR_ERR_ARG on NULL or mt < 1; MR_ERR_STATE before mr_refine_velocity
+ * and mr_set_scalar.  Asynchronous on stream. */
+int mr_scalar_coarse_step(mr_handle h, const double* U, const double* V, const double* W, int32_t mt,
+                          mr_stream stream);
+
 /* Number of steps taken since the last mr_set_scalar. */
 int mr_step_index(mr_handle h, int64_t* s);
 

@@ -10,6 +10,7 @@ Functions follow the paper's sections:
   * grid / R matrices       -- Section 3.1 and 3.2 (R = A_s A^-1)
   * refine / refine_adjoint -- Section 3.2 stepwise divergence-free refinement
   * rhs / step / run        -- Eq. (5) with the Euler-leapfrog scheme, Section 2.2
+  * coarse_step             -- temporal refinement M_t, Section 3.4 (Eq. 18)
   * stats                   -- plate Nusselt numbers (Section 4.1), volume moments
   * adjoint                 -- discrete adjoint of ``run`` (test of the gradients)
 """
@@ -227,6 +228,26 @@ def run(cfg: Config, vel, T0, nsteps: int):
     c = cfg._c()
     _check(_load().or_run(ctypes.byref(c), _p(Us), _p(Vs), _p(Ws), _p(T0), nsteps, _p(Tp), _p(Tc)), "run")
     return Tp, Tc
+
+
+def coarse_step(cfg: Config, vel_prev, vel_next, Tm1, T, s0: int, mt: int):
+    """One coarse time step with temporal refinement, Section 3.4 (Eq. 18).
+
+    The velocity of dense step i = 0..mt-1 is the linear interpolation between
+    the refined velocities of the two coarse time levels,
+        u_i = u^{n-1} + (i / mt) (u^n - u^{n-1}),
+    (Eq. 18 prints the second term as (i/M_t) U^n, which is no interpolation;
+    the difference is the reading taken here).  Each dense step is ``step``
+    with global index s0 + i.  Returns (T^{s0+mt-1}, T^{s0+mt})."""
+    sh = cfg.shapes()
+    prev = [_f64(a, sh[k]) for a, k in zip(vel_prev, ("Us", "Vs", "Ws"))]
+    nxt = [_f64(a, sh[k]) for a, k in zip(vel_next, ("Us", "Vs", "Ws"))]
+    Tm1, T = _f64(Tm1, sh["T"]), _f64(T, sh["T"])
+    for i in range(mt):
+        w = i / mt
+        vel = tuple(a + w * (b - a) for a, b in zip(prev, nxt))
+        Tm1, T = T, step(cfg, vel, Tm1, T, s0 + i)
+    return Tm1, T
 
 
 def stats(cfg: Config, T, vel=None) -> dict:

@@ -268,6 +268,15 @@ void mr_destroy(mr_handle h)
                     b.metric, b.red, b.nu2, b.stage, b.tri};
     for (void* p : ptrs)
         if (p) cudaFree(p);
+    DeviceBuffers::Level& n = b.next;
+    void* nptrs[] = {n.U64, n.V64, n.W64, n.Us, n.Vs, n.Ws, n.xwy, n.xuo, n.xvr, b.lerpc};
+    for (void* p : nptrs)
+        if (p) cudaFree(p);
+    if (h->elt == 4) {
+        void* cptrs[] = {n.Uc, n.Vc, n.Wc};
+        for (void* p : cptrs)
+            if (p) cudaFree(p);
+    }
     void* xptrs[] = {b.xwy, b.xuo, b.xvr, b.xlc, b.diag};
     for (void* p : xptrs)
         if (p) cudaFree(p);
@@ -498,20 +507,19 @@ static int refine_into(mr_handle h, void* dUs, void* dVs, void* dWs, cudaStream_
     return cuda_check(e, "refinement launch");
 }
 
-int mr_refine_velocity(mr_handle h, const double* U, const double* V, const double* W, void* Us, void* Vs,
-                       void* Ws, mr_stream stream)
+}  // extern "C"
+
+// Load a coarse velocity into the handle's current level: FP64 copy, the
+// precision-P coarse faces, and what the velocity mode steps from (dense faces
+// for MR_VEL_STORED, the split-x intermediates for MR_VEL_XFUSED).
+static int load_velocity(mr_handle h, const double* U, const double* V, const double* W, cudaStream_t st)
 {
-    if (!h || !U || !V || !W) return set_error(MR_ERR_ARG, "mr_refine_velocity: NULL argument");
-    if ((Us || Vs || Ws) && !(Us && Vs && Ws))
-        return set_error(MR_ERR_ARG, "mr_refine_velocity: Us, Vs, Ws must be all NULL or all set");
-    cudaStream_t st = (cudaStream_t)stream;
     DeviceBuffers& b = h->buf;
     int rc;
     if ((rc = copy_in(h, U, MR_F64, b.U64, MR_F64, h->ncU, st))) return rc;
     if ((rc = copy_in(h, V, MR_F64, b.V64, MR_F64, h->ncV, st))) return rc;
     if ((rc = copy_in(h, W, MR_F64, b.W64, MR_F64, h->ncW, st))) return rc;
-    const int P = h->cfg.precision;
-    if (P == MR_F32) {
+    if (h->cfg.precision == MR_F32) {
         if ((rc = copy_in(h, b.U64, MR_F64, b.Uc, MR_F32, h->ncU, st))) return rc;
         if ((rc = copy_in(h, b.V64, MR_F64, b.Vc, MR_F32, h->ncV, st))) return rc;
         if ((rc = copy_in(h, b.W64, MR_F64, b.Wc, MR_F32, h->ncW, st))) return rc;
@@ -519,25 +527,170 @@ int mr_refine_velocity(mr_handle h, const double* U, const double* V, const doub
     if (h->cfg.velocity_mode == MR_VEL_XFUSED) {
         cudaError_t e = launch_xfused_prep(h->g32, (const float*)b.Uc, (const float*)b.Vc, (const float*)b.Wc,
                                            (float*)b.scrW, b.xwy, b.xuo, b.xvr, b.nxg, st);
-        if (e != cudaSuccess) return cuda_check(e, "mr_refine_velocity: split-x intermediates");
+        if (e != cudaSuccess) return cuda_check(e, "split-x intermediates");
     }
-    void *dUs = b.Us, *dVs = b.Vs, *dWs = b.Ws;
-    if (h->cfg.velocity_mode != MR_VEL_STORED) {
-        if (!Us) {
-            h->have_velocity = true;
-            return MR_OK;
+    if (h->cfg.velocity_mode == MR_VEL_STORED) return refine_into(h, b.Us, b.Vs, b.Ws, st);
+    return MR_OK;
+}
+
+// One time step of the scalar.  alpha = 0: the current velocity; otherwise the
+// velocity (1 - alpha) U^{n-1} + alpha U^n between the current level and the
+// next one (temporal refinement, Section 3.4).
+static int one_step(mr_handle h, double alpha, cudaStream_t st)
+{
+    DeviceBuffers& b = h->buf;
+    const DeviceBuffers::Level& nx = b.next;
+    const bool lerp = alpha != 0.0, implz = h->cfg.diffz_implicit != 0;
+    const StepCoef c = step_coef(h->cfg, h->step);
+    const int in = 3 - h->ip - h->ic;
+    const void* Tm1 = h->step == 0 ? b.T[h->ic] : b.T[h->ip];
+    cudaError_t e;
+    if (h->cfg.precision == MR_F64) {
+        const double* A[3] = {(const double*)b.Us, (const double*)b.Vs, (const double*)b.Ws};
+        const double* B[3] = {(const double*)nx.Us, (const double*)nx.Vs, (const double*)nx.Ws};
+        e = lerp ? launch_step_stored_lerp<double>(h->g64, A, B, alpha, (const double*)Tm1, (const double*)b.T[h->ic],
+                                                   (double*)b.T[in], c, implz, st)
+                 : launch_step_stored<double>(h->g64, A[0], A[1], A[2], (const double*)Tm1, (const double*)b.T[h->ic],
+                                              (double*)b.T[in], c, implz, st);
+        if (e == cudaSuccess && implz) e = launch_zsolve<double>(h->g64, (double*)b.T[in], 0.5 * c.gdt, (double*)b.tri, st);
+    } else if (h->cfg.velocity_mode == MR_VEL_XFUSED) {
+        const float* A[3] = {b.xwy, b.xuo, b.xvr};
+        const float* B[3] = {nx.xwy, nx.xuo, nx.xvr};
+        e = launch_step_xfused_f32(h->g32, A, lerp ? B : nullptr, alpha, b.nxg, b.xlc, b.xrx, (const float*)Tm1,
+                                   (const float*)b.T[h->ic], (float*)b.T[in], c, st);
+    } else if (h->cfg.velocity_mode == MR_VEL_FUSED) {
+        const float *U = (const float*)b.Uc, *V = (const float*)b.Vc, *W = (const float*)b.Wc;
+        e = cudaSuccess;
+        if (lerp) {
+            // the refinement is linear: refining the interpolated coarse faces
+            // interpolates the refined ones
+            float* Lu = b.lerpc;
+            float* Lv = Lu + h->ncU;
+            float* Lw = Lv + h->ncV;
+            e = launch_lerp_f32(U, (const float*)nx.Uc, alpha, Lu, h->ncU, st);
+            if (e == cudaSuccess) e = launch_lerp_f32(V, (const float*)nx.Vc, alpha, Lv, h->ncV, st);
+            if (e == cudaSuccess) e = launch_lerp_f32(W, (const float*)nx.Wc, alpha, Lw, h->ncW, st);
+            U = Lu; V = Lv; W = Lw;
         }
-        if (!is_device_pointer(Us) || !is_device_pointer(Vs) || !is_device_pointer(Ws))
-            return set_error(MR_ERR_ARG, "mr_refine_velocity: in fused mode Us, Vs, Ws must be device memory");
-        dUs = Us; dVs = Vs; dWs = Ws;
+        if (e == cudaSuccess)
+            e = launch_step_fused_f32(h->g32, U, V, W, (const float*)Tm1, (const float*)b.T[h->ic], (float*)b.T[in], c, st);
+    } else {
+        const float* A[3] = {(const float*)b.Us, (const float*)b.Vs, (const float*)b.Ws};
+        const float* B[3] = {(const float*)nx.Us, (const float*)nx.Vs, (const float*)nx.Ws};
+        e = lerp ? launch_step_stored_lerp<float>(h->g32, A, B, alpha, (const float*)Tm1, (const float*)b.T[h->ic],
+                                                  (float*)b.T[in], c, implz, st)
+                 : launch_step_stored<float>(h->g32, A[0], A[1], A[2], (const float*)Tm1, (const float*)b.T[h->ic],
+                                             (float*)b.T[in], c, implz, st);
+        if (e == cudaSuccess && implz) e = launch_zsolve<float>(h->g32, (float*)b.T[in], 0.5 * c.gdt, (float*)b.tri, st);
     }
-    if ((rc = refine_into(h, dUs, dVs, dWs, st))) return rc;
-    if (h->cfg.velocity_mode == MR_VEL_STORED && Us) {
-        if ((rc = copy_out(h, b.Us, P, Us, P, h->nU, st))) return rc;
-        if ((rc = copy_out(h, b.Vs, P, Vs, P, h->nV, st))) return rc;
-        if ((rc = copy_out(h, b.Ws, P, Ws, P, h->nW, st))) return rc;
+    if (e != cudaSuccess) return cuda_check(e, "scalar step launch");
+    h->ip = h->ic;
+    h->ic = in;
+    ++h->step;
+    return MR_OK;
+}
+
+// Exchange the current velocity level with the next one.
+static void swap_levels(DeviceBuffers& b)
+{
+    DeviceBuffers::Level& n = b.next;
+    std::swap(b.U64, n.U64); std::swap(b.V64, n.V64); std::swap(b.W64, n.W64);
+    std::swap(b.Uc, n.Uc); std::swap(b.Vc, n.Vc); std::swap(b.Wc, n.Wc);
+    std::swap(b.Us, n.Us); std::swap(b.Vs, n.Vs); std::swap(b.Ws, n.Ws);
+    std::swap(b.xwy, n.xwy); std::swap(b.xuo, n.xuo); std::swap(b.xvr, n.xvr);
+}
+
+// Allocate the next velocity level (once per handle).
+static int alloc_next(mr_handle h)
+{
+    DeviceBuffers& b = h->buf;
+    DeviceBuffers::Level& n = b.next;
+    if (n.U64) return MR_OK;
+    cudaError_t e = cudaSuccess;
+    auto alloc = [&](void** p, size_t bytes) {
+        if (e == cudaSuccess && bytes) e = cudaMalloc(p, bytes);
+    };
+    alloc((void**)&n.U64, h->ncU * 8);
+    alloc((void**)&n.V64, h->ncV * 8);
+    alloc((void**)&n.W64, h->ncW * 8);
+    if (h->elt == 4) {
+        alloc(&n.Uc, h->ncU * 4);
+        alloc(&n.Vc, h->ncV * 4);
+        alloc(&n.Wc, h->ncW * 4);
     }
+    const int mode = h->cfg.velocity_mode;
+    if (mode == MR_VEL_STORED) {
+        alloc(&n.Us, h->nU * h->elt);
+        alloc(&n.Vs, h->nV * h->elt);
+        alloc(&n.Ws, h->nW * h->elt);
+    } else if (mode == MR_VEL_XFUSED) {
+        alloc((void**)&n.xwy, (size_t)(h->Nz + 1) * h->Ny * b.nxg * 4);
+        alloc((void**)&n.xuo, (size_t)h->Nz * h->Ny * b.nxg * 4);
+        alloc((void**)&n.xvr, (size_t)h->Nz * (h->Ny + 1) * b.nxg * 4);
+    } else {
+        alloc((void**)&b.lerpc, (h->ncU + h->ncV + h->ncW) * 4);
+    }
+    if (e != cudaSuccess) {
+        void* ptrs[] = {n.U64, n.V64, n.W64, n.Us, n.Vs, n.Ws, n.xwy, n.xuo, n.xvr, b.lerpc};
+        for (void* p : ptrs)
+            if (p) cudaFree(p);
+        if (h->elt == 4) {
+            void* cptrs[] = {n.Uc, n.Vc, n.Wc};
+            for (void* p : cptrs)
+                if (p) cudaFree(p);
+        }
+        n = DeviceBuffers::Level();
+        b.lerpc = nullptr;
+        return cuda_check(e, "mr_scalar_coarse_step: device allocation");
+    }
+    if (h->elt == 8) {
+        n.Uc = n.U64; n.Vc = n.V64; n.Wc = n.W64;
+    }
+    return MR_OK;
+}
+
+extern "C" {
+
+int mr_refine_velocity(mr_handle h, const double* U, const double* V, const double* W, void* Us, void* Vs,
+                       void* Ws, mr_stream stream)
+{
+    if (!h || !U || !V || !W) return set_error(MR_ERR_ARG, "mr_refine_velocity: NULL argument");
+    if ((Us || Vs || Ws) && !(Us && Vs && Ws))
+        return set_error(MR_ERR_ARG, "mr_refine_velocity: Us, Vs, Ws must be all NULL or all set");
+    if (Us && h->cfg.velocity_mode != MR_VEL_STORED &&
+        (!is_device_pointer(Us) || !is_device_pointer(Vs) || !is_device_pointer(Ws)))
+        return set_error(MR_ERR_ARG, "mr_refine_velocity: in fused mode Us, Vs, Ws must be device memory");
+    cudaStream_t st = (cudaStream_t)stream;
+    DeviceBuffers& b = h->buf;
+    int rc = load_velocity(h, U, V, W, st);
+    if (rc) return rc;
     h->have_velocity = true;
+    if (!Us) return MR_OK;
+    const int P = h->cfg.precision;
+    if (h->cfg.velocity_mode != MR_VEL_STORED) return refine_into(h, Us, Vs, Ws, st);
+    if ((rc = copy_out(h, b.Us, P, Us, P, h->nU, st))) return rc;
+    if ((rc = copy_out(h, b.Vs, P, Vs, P, h->nV, st))) return rc;
+    return copy_out(h, b.Ws, P, Ws, P, h->nW, st);
+}
+
+int mr_scalar_coarse_step(mr_handle h, const double* U, const double* V, const double* W, int32_t mt,
+                          mr_stream stream)
+{
+    if (!h || !U || !V || !W) return set_error(MR_ERR_ARG, "mr_scalar_coarse_step: NULL argument");
+    if (mt < 1) return set_error(MR_ERR_ARG, "mr_scalar_coarse_step: mt must be >= 1");
+    if (!h->have_velocity || !h->have_scalar)
+        return set_error(MR_ERR_STATE, "mr_scalar_coarse_step: call mr_refine_velocity and mr_set_scalar first");
+    cudaStream_t st = (cudaStream_t)stream;
+    DeviceBuffers& b = h->buf;
+    int rc = alloc_next(h);
+    if (rc) return rc;
+    swap_levels(b);                    // load U^n into the next level's buffers
+    rc = load_velocity(h, U, V, W, st);
+    swap_levels(b);
+    if (rc) return rc;
+    for (int32_t i = 0; i < mt; ++i)
+        if ((rc = one_step(h, (double)i / (double)mt, st))) return rc;
+    swap_levels(b);                    // U^n is now the current velocity
     return MR_OK;
 }
 
@@ -579,34 +732,9 @@ int mr_scalar_step(mr_handle h, int64_t nsteps, mr_stream stream)
     if (!h->have_velocity || !h->have_scalar)
         return set_error(MR_ERR_STATE, "mr_scalar_step: call mr_refine_velocity and mr_set_scalar first");
     cudaStream_t st = (cudaStream_t)stream;
-    DeviceBuffers& b = h->buf;
-    const bool implz = h->cfg.diffz_implicit != 0;
     for (int64_t q = 0; q < nsteps; ++q) {
-        const StepCoef c = step_coef(h->cfg, h->step);
-        const int in = 3 - h->ip - h->ic;
-        const void* Tm1 = h->step == 0 ? b.T[h->ic] : b.T[h->ip];
-        cudaError_t e;
-        if (h->cfg.precision == MR_F64) {
-            e = launch_step_stored<double>(h->g64, (const double*)b.Us, (const double*)b.Vs, (const double*)b.Ws,
-                                           (const double*)Tm1, (const double*)b.T[h->ic], (double*)b.T[in], c,
-                                           implz, st);
-            if (e == cudaSuccess && implz) e = launch_zsolve<double>(h->g64, (double*)b.T[in], 0.5 * c.gdt, (double*)b.tri, st);
-        } else if (h->cfg.velocity_mode == MR_VEL_XFUSED) {
-            e = launch_step_xfused_f32(h->g32, b.xwy, b.xuo, b.xvr, b.nxg, b.xlc, b.xrx, (const float*)Tm1,
-                                       (const float*)b.T[h->ic], (float*)b.T[in], c, st);
-        } else if (h->cfg.velocity_mode == MR_VEL_FUSED) {
-            e = launch_step_fused_f32(h->g32, (const float*)b.Uc, (const float*)b.Vc, (const float*)b.Wc,
-                                      (const float*)Tm1, (const float*)b.T[h->ic], (float*)b.T[in], c, st);
-        } else {
-            e = launch_step_stored<float>(h->g32, (const float*)b.Us, (const float*)b.Vs, (const float*)b.Ws,
-                                          (const float*)Tm1, (const float*)b.T[h->ic], (float*)b.T[in], c, implz,
-                                          st);
-            if (e == cudaSuccess && implz) e = launch_zsolve<float>(h->g32, (float*)b.T[in], 0.5 * c.gdt, (float*)b.tri, st);
-        }
-        if (e != cudaSuccess) return cuda_check(e, "mr_scalar_step: launch");
-        h->ip = h->ic;
-        h->ic = in;
-        ++h->step;
+        const int rc = one_step(h, 0.0, st);
+        if (rc) return rc;
     }
     return MR_OK;
 }

@@ -73,6 +73,16 @@ struct DeviceBuffers {
     float xrx[12] = {0};                       // R_x rows of the 4 cells of a 4-cell segment
     double* diag = nullptr;                    // diagnostics: coarse T, Nu(z), dense z centres (lazy)
     int nxg = 0;
+    // Temporal refinement (Section 3.4): the velocity of the next coarse time
+    // level, in the same layout as the current one above (allocated by the
+    // first mr_scalar_coarse_step; swapped with the current level after it).
+    struct Level {
+        double *U64 = nullptr, *V64 = nullptr, *W64 = nullptr;
+        void *Uc = nullptr, *Vc = nullptr, *Wc = nullptr;
+        void *Us = nullptr, *Vs = nullptr, *Ws = nullptr;
+        float *xwy = nullptr, *xuo = nullptr, *xvr = nullptr;
+    } next;
+    float* lerpc = nullptr;                    // MR_VEL_FUSED: interpolated coarse faces (U, V, W)
 };
 
 }  // namespace mr
@@ -126,6 +136,12 @@ cudaError_t launch_refine(const Grid<P>& g, const P* U, const P* V, const P* W, 
 template <typename P>
 cudaError_t launch_step_stored(const Grid<P>& g, const P* Us, const P* Vs, const P* Ws, const P* Tm1,
                                const P* T, P* Tp1, StepCoef c, bool implz, cudaStream_t st);
+// the same step with the velocity A + alpha (B - A) of two stored dense fields
+template <typename P>
+cudaError_t launch_step_stored_lerp(const Grid<P>& g, const P* const velA[3], const P* const velB[3], double alpha,
+                                    const P* Tm1, const P* T, P* Tp1, StepCoef c, bool implz, cudaStream_t st);
+// out = A + alpha (B - A), elementwise (coarse faces of two time levels)
+cudaError_t launch_lerp_f32(const float* A, const float* B, double alpha, float* out, size_t n, cudaStream_t st);
 template <typename P>
 cudaError_t launch_zsolve(const Grid<P>& g, P* Tp1, double half_gdt, P* work, cudaStream_t st);
 template <typename P>
@@ -161,9 +177,11 @@ template <typename P>
 cudaError_t launch_column_balance(const Grid<P>& g, const P* U, const P* V, const P* W, P* scrW, cudaStream_t st);
 cudaError_t launch_xfused_prep(const Grid<float>& g, const float* U, const float* V, const float* W, float* scrW,
                                float* WY, float* UO, float* VR, int nxg, cudaStream_t st);
-cudaError_t launch_step_xfused_f32(const Grid<float>& g, const float* WY, const float* UO, const float* VR, int nxg,
-                                   const float* lc, const float* rx12, const float* Tm1, const float* T, float* Tp1,
-                                   StepCoef c, cudaStream_t st);
+// setA = {WY, UO, VR} of the current velocity; setB (or NULL) those of the next
+// coarse time level, interpolated with weight alpha (temporal refinement)
+cudaError_t launch_step_xfused_f32(const Grid<float>& g, const float* const setA[3], const float* const setB[3],
+                                   double alpha, int nxg, const float* lc, const float* rx12, const float* Tm1,
+                                   const float* T, float* Tp1, StepCoef c, cudaStream_t st);
 cudaError_t launch_maxdiv_xfused_f32(const Grid<float>& g, const float* WY, const float* UO, const float* VR, int nxg,
                                      const float* lc, const float* rx12, double* partials, int blocks, cudaStream_t st);
 cudaError_t launch_refine_transpose(const Grid<double>& g, double* aUs, double* aVs, double* aWs, double* aWc,

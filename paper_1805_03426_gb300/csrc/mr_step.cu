@@ -13,11 +13,27 @@ namespace {
 constexpr double kTBottom = 0.5;
 constexpr double kTTop = -0.5;
 
+// Dense face velocity of a step: one stored field, or (LERP) the linear
+// interpolation A + alpha (B - A) between the fields of two coarse time
+// levels (temporal refinement, Section 3.4).
+template <typename P, bool LERP>
+struct FaceVel {
+    const P* __restrict__ A;
+    const P* __restrict__ B;
+    P alpha;
+    __device__ __forceinline__ P operator[](size_t f) const
+    {
+        if (!LERP) return A[f];
+        const P a = A[f];
+        return a + alpha * (B[f] - a);
+    }
+};
+
 // One thread per dense cell.  IMPLZ: vertical diffusion enters as
 // (D_z(T^{s-1}) + plate terms) / 2; the implicit half follows in k_zsolve.
-template <typename P, bool IMPLZ>
-__global__ void __launch_bounds__(256) k_step_stored(Grid<P> g, const P* __restrict__ Us,
-                                                     const P* __restrict__ Vs, const P* __restrict__ Ws,
+template <typename P, bool IMPLZ, bool LERP>
+__global__ void __launch_bounds__(256) k_step_stored(Grid<P> g, const FaceVel<P, LERP> Us,
+                                                     const FaceVel<P, LERP> Vs, const FaceVel<P, LERP> Ws,
                                                      const P* __restrict__ Tm1, const P* __restrict__ T,
                                                      P* __restrict__ Tp1, P a, P b, P gdt)
 {
@@ -119,19 +135,55 @@ __global__ void k_zsolve(Grid<P> g, P* __restrict__ X, P h, P* __restrict__ work
     }
 }
 
+template <typename P, bool LERP>
+cudaError_t step_stored(const Grid<P>& g, const FaceVel<P, LERP>& u, const FaceVel<P, LERP>& v,
+                        const FaceVel<P, LERP>& w, const P* Tm1, const P* T, P* Tp1, StepCoef c, bool implz,
+                        cudaStream_t st)
+{
+    dim3 blk(64, 4);
+    dim3 grd((g.Nx + blk.x - 1) / blk.x, (g.Ny + blk.y - 1) / blk.y, g.Nz);
+    if (implz)
+        k_step_stored<P, true, LERP><<<grd, blk, 0, st>>>(g, u, v, w, Tm1, T, Tp1, (P)c.a, (P)c.b, (P)c.gdt);
+    else
+        k_step_stored<P, false, LERP><<<grd, blk, 0, st>>>(g, u, v, w, Tm1, T, Tp1, (P)c.a, (P)c.b, (P)c.gdt);
+    return cudaGetLastError();
+}
+
+__global__ void k_lerp(const float* __restrict__ A, const float* __restrict__ B, float alpha, float* __restrict__ out,
+                       size_t n)
+{
+    for (size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (size_t)gridDim.x * blockDim.x) {
+        const float a = A[t];
+        out[t] = a + alpha * (B[t] - a);
+    }
+}
+
 }  // namespace
+
+cudaError_t launch_lerp_f32(const float* A, const float* B, double alpha, float* out, size_t n, cudaStream_t st)
+{
+    if (!n) return cudaSuccess;
+    const size_t want = (n + 255) / 256;
+    const unsigned blocks = (unsigned)(want < 152 * 16 ? want : 152 * 16);
+    k_lerp<<<blocks, 256, 0, st>>>(A, B, (float)alpha, out, n);
+    return cudaGetLastError();
+}
 
 template <typename P>
 cudaError_t launch_step_stored(const Grid<P>& g, const P* Us, const P* Vs, const P* Ws, const P* Tm1,
                                const P* T, P* Tp1, StepCoef c, bool implz, cudaStream_t st)
 {
-    dim3 blk(64, 4);
-    dim3 grd((g.Nx + blk.x - 1) / blk.x, (g.Ny + blk.y - 1) / blk.y, g.Nz);
-    if (implz)
-        k_step_stored<P, true><<<grd, blk, 0, st>>>(g, Us, Vs, Ws, Tm1, T, Tp1, (P)c.a, (P)c.b, (P)c.gdt);
-    else
-        k_step_stored<P, false><<<grd, blk, 0, st>>>(g, Us, Vs, Ws, Tm1, T, Tp1, (P)c.a, (P)c.b, (P)c.gdt);
-    return cudaGetLastError();
+    return step_stored<P, false>(g, {Us, nullptr, P(0)}, {Vs, nullptr, P(0)}, {Ws, nullptr, P(0)}, Tm1, T, Tp1,
+                                 c, implz, st);
+}
+
+template <typename P>
+cudaError_t launch_step_stored_lerp(const Grid<P>& g, const P* const velA[3], const P* const velB[3], double alpha,
+                                    const P* Tm1, const P* T, P* Tp1, StepCoef c, bool implz, cudaStream_t st)
+{
+    const P al = (P)alpha;
+    return step_stored<P, true>(g, {velA[0], velB[0], al}, {velA[1], velB[1], al}, {velA[2], velB[2], al}, Tm1,
+                                T, Tp1, c, implz, st);
 }
 
 template <typename P>
@@ -149,6 +201,12 @@ template cudaError_t launch_step_stored<double>(const Grid<double>&, const doubl
 template cudaError_t launch_step_stored<float>(const Grid<float>&, const float*, const float*, const float*,
                                                const float*, const float*, float*, StepCoef, bool,
                                                cudaStream_t);
+template cudaError_t launch_step_stored_lerp<double>(const Grid<double>&, const double* const[3],
+                                                     const double* const[3], double, const double*,
+                                                     const double*, double*, StepCoef, bool, cudaStream_t);
+template cudaError_t launch_step_stored_lerp<float>(const Grid<float>&, const float* const[3], const float* const[3],
+                                                    double, const float*, const float*, float*, StepCoef, bool,
+                                                    cudaStream_t);
 template cudaError_t launch_zsolve<double>(const Grid<double>&, double*, double, double*, cudaStream_t);
 template cudaError_t launch_zsolve<float>(const Grid<float>&, float*, double, float*, cudaStream_t);
 

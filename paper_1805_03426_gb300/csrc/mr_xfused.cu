@@ -41,22 +41,27 @@ constexpr int kThreads = 256;                           // consumer threads (8 w
 constexpr int kThreadsAll = kThreads + 32;              // + one producer warp
 constexpr float kTBottom = 0.5f, kTTop = -0.5f;
 
-template <int M>
+template <int M, bool MT>
 struct XT {
     static constexpr int CX = kTX / M;
     static constexpr int BXC = CX + 8;                  // coarse box width: columns I0-4 .. I0+CX+3
-    static constexpr int NB = (M == 4) ? 7 : 6;         // ring slots
-    // one ring slot (floats): T^n plane, T^{n-1} plane, then the bundle of one
-    // layer k: WY of its upper plane k+1 (its lower plane k is the previous
-    // slot's), UO and VR of layer k, the layer constants
+    // ring slots; MT (two velocity sets per slot) keeps two CTAs per SM with fewer slots
+    static constexpr int NB = MT ? ((M == 4) ? 5 : 4) : ((M == 4) ? 7 : 6);
+    // one ring slot (floats): T^n plane, T^{n-1} plane, then the velocity set of
+    // one layer k: WY of its upper plane k+1 (its lower plane k is the previous
+    // slot's), UO and VR of layer k; with MT the set of the second coarse time
+    // level follows at offset DS; then the layer constants
     static constexpr int oTn = 0, oTm = kPlaneSlot;
     static constexpr int oWY = 2 * kPlaneSlot;          // [TY][BXC]      plane k+1
     static constexpr int oUO = oWY + kTY * BXC;         // [TY][BXC]
     static constexpr int oVR = oUO + kTY * BXC;         // [TY+1][BXC]
-    static constexpr int oLC = ((oVR + (kTY + 1) * BXC) + 31) / 32 * 32;   // [12] layer constants (128-B aligned)
+    static constexpr int SET = ((2 * kTY + kTY + 1) * BXC + 31) / 32 * 32;   // one set, 128-B multiple
+    static constexpr int DS = MT ? SET : 0;
+    static constexpr int oLC = oWY + (MT ? 2 : 1) * SET;                     // [12] layer constants
     static constexpr int slot = (((oLC + 16) * 4 + 127) / 128) * 128 / 4;
-    static constexpr uint32_t wy_bytes = (uint32_t)(kTY * BXC) * 4;
-    static constexpr uint32_t bundle_bytes = (uint32_t)(kTY * BXC + (kTY + 1) * BXC + 12) * 4;   // UO, VR, LC
+    static constexpr int NSET = MT ? 2 : 1;
+    static constexpr uint32_t wy_bytes = (uint32_t)(NSET * kTY * BXC) * 4;
+    static constexpr uint32_t bundle_bytes = (uint32_t)(NSET * (kTY * BXC + (kTY + 1) * BXC) + 12) * 4;  // UO, VR, LC
     static constexpr int oRed = NB * slot;              // 64 floats
     static constexpr int oBar = ((oRed + 64) * 4 + 7) / 8;
     static constexpr size_t bytes = (size_t)(oBar + 2 * NB) * 8;
@@ -75,16 +80,22 @@ struct XArgs {
     float rx[4][3];      // R_x rows of the 4 cells of a segment (x is uniform and the
                          // segment starts on a coarse cell boundary, so these are the
                          // same for every thread: kept in the constant bank)
+    float alpha;         // MT: weight of the second velocity set, i / M_t (Section 3.4)
 };
 
 // LF: a plain leapfrog step (a = 1, b = 0), by far the most frequent kind.
-template <int M, bool DIVONLY, bool LF>
+// MT: the velocity is A + alpha (B - A) between the intermediates of two
+// coarse time levels (temporal refinement; the refinement is linear, so
+// interpolating the intermediates interpolates the dense velocity).
+template <int M, bool DIVONLY, bool LF, bool MT>
 __global__ void __launch_bounds__(kThreadsAll, 2)
 k_xfused(const __grid_constant__ CUtensorMap tmn, const __grid_constant__ CUtensorMap tmm,
          const __grid_constant__ CUtensorMap twy, const __grid_constant__ CUtensorMap tuo,
-         const __grid_constant__ CUtensorMap tvr, const __grid_constant__ CUtensorMap tlc, const XArgs A)
+         const __grid_constant__ CUtensorMap tvr, const __grid_constant__ CUtensorMap tlc,
+         const __grid_constant__ CUtensorMap twy1, const __grid_constant__ CUtensorMap tuo1,
+         const __grid_constant__ CUtensorMap tvr1, const XArgs A)
 {
-    using L = XT<M>;
+    using L = XT<M, MT>;
     constexpr int NB = L::NB, BXC = L::BXC, NC = 4 / M, NW = kThreads / 32;
     extern __shared__ __align__(128) float sm[];
     float* red = sm + L::oRed;
@@ -128,11 +139,18 @@ k_xfused(const __grid_constant__ CUtensorMap tmn, const __grid_constant__ CUtens
                 tma_3d(slot + L::oTn, &tmn, i0 - 4, j0 - 1, k0 - 1 + r, &full[s]);
                 tma_3d(slot + L::oTm, &tmm, i0 - 4, j0 - 1, k0 - 1 + r, &full[s]);
             }
-            if (r >= 1) tma_3d(slot + L::oWY, &twy, I0, j0, k0 - 1 + r, &full[s]);   // WY plane k0-1+r
+            if (r >= 1) {
+                tma_3d(slot + L::oWY, &twy, I0, j0, k0 - 1 + r, &full[s]);   // WY plane k0-1+r
+                if (MT) tma_3d(slot + L::oWY + L::DS, &twy1, I0, j0, k0 - 1 + r, &full[s]);
+            }
             if (bundle) {
                 const int kb = k0 + r - 2;
                 tma_3d(slot + L::oUO, &tuo, I0, j0, kb, &full[s]);
                 tma_3d(slot + L::oVR, &tvr, I0, j0, kb, &full[s]);
+                if (MT) {
+                    tma_3d(slot + L::oUO + L::DS, &tuo1, I0, j0, kb, &full[s]);
+                    tma_3d(slot + L::oVR + L::DS, &tvr1, I0, j0, kb, &full[s]);
+                }
                 tma_3d(slot + L::oLC, &tlc, 0, kb, 0, &full[s]);
             }
         }
@@ -150,7 +168,7 @@ k_xfused(const __grid_constant__ CUtensorMap tmn, const __grid_constant__ CUtens
     bool fail = false;
     float dmax = 0.f;
     const float hix = 0.5f * g.inv_dx, hiy = 0.5f * g.inv_dy, kx2 = g.kx2, ky2 = g.ky2;
-    const float ca = A.a, cbb = A.b, gdt = A.gdt;
+    const float ca = A.a, cbb = A.b, gdt = A.gdt, alpha = A.alpha;
     // ring bookkeeping without divisions: slots of planes k-1, k, k+1 and the
     // next (slot, parity) to wait for
     int sb = 0, sc = 1, st = 2;
@@ -183,19 +201,40 @@ k_xfused(const __grid_constant__ CUtensorMap tmn, const __grid_constant__ CUtens
                 const float* yt = bun + L::oWY + jl * BXC + cb0 + 3;                  // plane k+1
                 const float* rs = bun + L::oVR + jl * BXC + cb0 + 3;
                 const float* rn = rs + BXC;
+                const float* ur = bun + L::oUO + jl * BXC + cb0 + 4;   // outer face of coarse column cb0
+                // the coarse columns a segment touches (interpolated in time with MT)
+                constexpr int NV = NC + 2;
+                float ybv[NV], ytv[NV], rsv[NV], rnv[NV], urv[NC + 1];
+#pragma unroll
+                for (int c = 0; c < NV; ++c) {
+                    ybv[c] = yb[c];
+                    ytv[c] = yt[c];
+                    rsv[c] = rs[c];
+                    rnv[c] = rn[c];
+                    if (MT) {
+                        ybv[c] += alpha * (yb[c + L::DS] - ybv[c]);
+                        ytv[c] += alpha * (yt[c + L::DS] - ytv[c]);
+                        rsv[c] += alpha * (rs[c + L::DS] - rsv[c]);
+                        rnv[c] += alpha * (rn[c + L::DS] - rnv[c]);
+                    }
+                }
+#pragma unroll
+                for (int q = 0; q <= NC; ++q) {
+                    urv[q] = ur[q];
+                    if (MT) urv[q] += alpha * (ur[q + L::DS] - urv[q]);
+                }
 #pragma unroll
                 for (int a = 0; a < 4; ++a) {
                     const int cb = a / M;
-                    wb[a] = rx[a][0] * yb[cb] + rx[a][1] * yb[cb + 1] + rx[a][2] * yb[cb + 2];
-                    wt[a] = rx[a][0] * yt[cb] + rx[a][1] * yt[cb + 1] + rx[a][2] * yt[cb + 2];
-                    vs[a] = rx[a][0] * rs[cb] + rx[a][1] * rs[cb + 1] + rx[a][2] * rs[cb + 2];
-                    vn[a] = rx[a][0] * rn[cb] + rx[a][1] * rn[cb + 1] + rx[a][2] * rn[cb + 2];
+                    wb[a] = rx[a][0] * ybv[cb] + rx[a][1] * ybv[cb + 1] + rx[a][2] * ybv[cb + 2];
+                    wt[a] = rx[a][0] * ytv[cb] + rx[a][1] * ytv[cb + 1] + rx[a][2] * ytv[cb + 2];
+                    vs[a] = rx[a][0] * rsv[cb] + rx[a][1] * rsv[cb + 1] + rx[a][2] * rsv[cb + 2];
+                    vn[a] = rx[a][0] * rnv[cb] + rx[a][1] * rnv[cb + 1] + rx[a][2] * rnv[cb + 2];
                 }
                 // stage X: cell balance, west to east, in velocity units
-                const float* ur = bun + L::oUO + jl * BXC + cb0 + 4;   // outer face of coarse column cb0
 #pragma unroll
                 for (int q = 0; q < NC; ++q) {
-                    float h = ur[q];
+                    float h = urv[q];
                     us[q * M] = h;
 #pragma unroll
                     for (int a = 0; a < M - 1; ++a) {
@@ -204,7 +243,7 @@ k_xfused(const __grid_constant__ CUtensorMap tmn, const __grid_constant__ CUtens
                         us[m + 1] = h;
                     }
                 }
-                us[4] = ur[NC];
+                us[4] = urv[NC];
             }
             if (DIVONLY) {
 #pragma unroll
@@ -303,67 +342,66 @@ k_xfused(const __grid_constant__ CUtensorMap tmn, const __grid_constant__ CUtens
 
 // ------------------------------------------------------------- intermediates (once per velocity)
 
-__device__ __forceinline__ int pwrap(int i, int n) { return ((i % n) + n) % n; }
+// Periodic wrap of a coarse column index that is at most one period outside.
+__device__ __forceinline__ int wrapc(int i, int n) { return i < 0 ? i + n : (i >= n ? i - n : i); }
+
+// The three kernels below run one thread per (gx, j) of one dense plane
+// k = blockIdx.y (32-bit index arithmetic; gx is the bundle column, coarse
+// column I = gx - 4 wrapped).
 
 // WY[k][j][gx]: R_y of the full-area W on every dense plane (coarse W on the
 // coarse planes, slab-balanced scrW on the inner ones).
 __global__ void k_xprep_wy(Grid<float> g, const float* __restrict__ W, const float* __restrict__ scrW,
                            float* __restrict__ WY, int nxg)
 {
-    const size_t n = (size_t)(g.Nz + 1) * g.Ny * nxg;
-    for (size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (size_t)gridDim.x * blockDim.x) {
-        const int gx = (int)(t % nxg), j = (int)((t / nxg) % g.Ny), k = (int)(t / ((size_t)nxg * g.Ny));
-        const int I = pwrap(gx - 4, g.nx), J = j / g.my;
-        float s = 0.f;
-        for (int q = 0; q < 3; ++q) {
-            const int Jq = g.wy[3 * J + q];
-            const float v = (k % g.mz == 0) ? W[((size_t)(k / g.mz) * g.ny + Jq) * g.nx + I]
-                                            : scrW[((size_t)k * g.ny + Jq) * g.nx + I];
-            s += g.Ry[3 * j + q] * v;
-        }
-        WY[t] = s;
-    }
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= nxg * g.Ny) return;
+    const int k = blockIdx.y, j = t / nxg, gx = t - j * nxg;
+    const int I = wrapc(gx - 4, g.nx), J = j / g.my, K = k / g.mz;
+    const float* src = (k == K * g.mz) ? W + (size_t)K * g.ny * g.nx : scrW + (size_t)k * g.ny * g.nx;
+    float s = 0.f;
+    for (int q = 0; q < 3; ++q) s += g.Ry[3 * j + q] * src[(size_t)g.wy[3 * J + q] * g.nx + I];
+    WY[(size_t)k * g.Ny * nxg + t] = s;
 }
 
 // UO[k][j][gx]: the outer U sub-face of coarse x-face I (R_y R_z of U).
 __global__ void k_xprep_uo(Grid<float> g, const float* __restrict__ U, float* __restrict__ UO, int nxg)
 {
-    const size_t n = (size_t)g.Nz * g.Ny * nxg;
-    for (size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (size_t)gridDim.x * blockDim.x) {
-        const int gx = (int)(t % nxg), j = (int)((t / nxg) % g.Ny), k = (int)(t / ((size_t)nxg * g.Ny));
-        const int I = pwrap(gx - 4, g.nx), J = j / g.my, K = k / g.mz;
-        float s = 0.f;
-        for (int p = 0; p < 3; ++p)
-            for (int q = 0; q < 3; ++q)
-                s += g.Ry[3 * j + p] * g.Rz[3 * k + q] * U[((size_t)g.wz[3 * K + q] * g.ny + g.wy[3 * J + p]) * g.nx + I];
-        UO[t] = s;
-    }
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= nxg * g.Ny) return;
+    const int k = blockIdx.y, j = t / nxg, gx = t - j * nxg;
+    const int I = wrapc(gx - 4, g.nx), J = j / g.my, K = k / g.mz;
+    float s = 0.f;
+    for (int p = 0; p < 3; ++p)
+        for (int q = 0; q < 3; ++q)
+            s += g.Ry[3 * j + p] * g.Rz[3 * k + q] * U[((size_t)g.wz[3 * K + q] * g.ny + g.wy[3 * J + p]) * g.nx + I];
+    UO[(size_t)k * g.Ny * nxg + t] = s;
 }
 
 // VR[k][j][gx]: full-coarse-width V on every dense y-face, by the row balance
-// (south to north) of stage Y; row Ny repeats row 0 (periodic).
+// (south to north) of stage Y; one thread per coarse row J (0..ny, row ny
+// repeating row 0, periodic) walks its M_y - 1 inner faces.
 __global__ void k_xprep_vr(Grid<float> g, const float* __restrict__ V, const float* __restrict__ UO,
                            const float* __restrict__ WY, float* __restrict__ VR, int nxg)
 {
-    const size_t n = (size_t)g.Nz * (g.ny + 1) * nxg;
-    for (size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (size_t)gridDim.x * blockDim.x) {
-        const int gx = (int)(t % nxg), J = (int)((t / nxg) % (g.ny + 1)), k = (int)(t / ((size_t)nxg * (g.ny + 1)));
-        const int I = pwrap(gx - 4, g.nx), K = k / g.mz, Jf = (J == g.ny) ? 0 : J;
-        float vz = 0.f;
-        for (int q = 0; q < 3; ++q) vz += g.Rz[3 * k + q] * V[((size_t)g.wz[3 * K + q] * g.ny + Jf) * g.nx + I];
-        const size_t vrow = (size_t)g.Ny + 1;
-        VR[((size_t)k * vrow + (size_t)J * g.my) * nxg + gx] = vz;
-        if (J == g.ny) continue;
-        const float dzk = g.dz[k];
-        const int xi = I + 4, xe = pwrap(I + 1, g.nx) + 4;
-        float G = vz * g.DX * dzk;
-        for (int b = 0; b < g.my - 1; ++b) {
-            const int j = J * g.my + b;
-            const float uw = UO[((size_t)k * g.Ny + j) * nxg + xi], ue = UO[((size_t)k * g.Ny + j) * nxg + xe];
-            const float wb = WY[((size_t)k * g.Ny + j) * nxg + xi], wt = WY[((size_t)(k + 1) * g.Ny + j) * nxg + xi];
-            G = G - (ue - uw) * g.dy * dzk - (wt - wb) * g.DX * g.dy;
-            VR[((size_t)k * vrow + j + 1) * nxg + gx] = G / (g.DX * dzk);
-        }
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= nxg * (g.ny + 1)) return;
+    const int k = blockIdx.y, J = t / nxg, gx = t - J * nxg;
+    const int I = wrapc(gx - 4, g.nx), K = k / g.mz, Jf = (J == g.ny) ? 0 : J;
+    float vz = 0.f;
+    for (int q = 0; q < 3; ++q) vz += g.Rz[3 * k + q] * V[((size_t)g.wz[3 * K + q] * g.ny + Jf) * g.nx + I];
+    const size_t vrow = (size_t)g.Ny + 1;
+    VR[((size_t)k * vrow + (size_t)J * g.my) * nxg + gx] = vz;
+    if (J == g.ny) return;
+    const float dzk = g.dz[k];
+    const int xi = I + 4, xe = wrapc(I + 1, g.nx) + 4;
+    float G = vz * g.DX * dzk;
+    for (int b = 0; b < g.my - 1; ++b) {
+        const int j = J * g.my + b;
+        const float uw = UO[((size_t)k * g.Ny + j) * nxg + xi], ue = UO[((size_t)k * g.Ny + j) * nxg + xe];
+        const float wb = WY[((size_t)k * g.Ny + j) * nxg + xi], wt = WY[((size_t)(k + 1) * g.Ny + j) * nxg + xi];
+        G = G - (ue - uw) * g.dy * dzk - (wt - wb) * g.DX * g.dy;
+        VR[((size_t)k * vrow + j + 1) * nxg + gx] = G / (g.DX * dzk);
     }
 }
 
@@ -431,24 +469,35 @@ int kcl_override()
     return v;
 }
 
-template <int M, bool DIVONLY, bool LF>
-cudaError_t launch_x(const Grid<float>& g, const float* WY, const float* UO, const float* VR, int nxg, const float* lc,
+// Velocity intermediates of one coarse time level.
+struct XSet {
+    const float *wy, *uo, *vr;
+};
+
+template <int M, bool DIVONLY, bool LF, bool MT>
+cudaError_t launch_x(const Grid<float>& g, XSet v0, XSet v1, float alpha, int nxg, const float* lc,
                      const float* rx12, const float* Tm1, const float* T, float* Tp1, StepCoef c, int* err,
                      unsigned long long* divmax, cudaStream_t st)
 {
-    using L = XT<M>;
+    using L = XT<M, MT>;
     static unsigned long long attr = 0;                   // one bit per device
-    cudaError_t e = smem_optin(reinterpret_cast<const void*>(k_xfused<M, DIVONLY, LF>), (int)L::bytes, &attr);
+    cudaError_t e = smem_optin(reinterpret_cast<const void*>(k_xfused<M, DIVONLY, LF, MT>), (int)L::bytes, &attr);
     if (e != cudaSuccess) return e;
-    CUtensorMap mn, mm, mwy, muo, mvr, mlc;
+    CUtensorMap mn, mm, mwy, muo, mvr, mlc, mwy1, muo1, mvr1;
     memset(&mn, 0, sizeof mn);
     memset(&mm, 0, sizeof mm);
+    memset(&mwy1, 0, sizeof mwy1);
+    memset(&muo1, 0, sizeof muo1);
+    memset(&mvr1, 0, sizeof mvr1);
     if (!DIVONLY && (!cached_map3(&mn, T, g.Nx, g.Ny, g.Nz, kBX, kBY, 1) ||
                      !cached_map3(&mm, Tm1, g.Nx, g.Ny, g.Nz, kBX, kBY, 1)))
         return cudaErrorInvalidValue;
-    if (!cached_map3(&mwy, WY, nxg, g.Ny, g.Nz + 1, L::BXC, kTY, 1) ||
-        !cached_map3(&muo, UO, nxg, g.Ny, g.Nz, L::BXC, kTY, 1) ||
-        !cached_map3(&mvr, VR, nxg, g.Ny + 1, g.Nz, L::BXC, kTY + 1, 1) ||
+    auto set_maps = [&](const XSet& v, CUtensorMap* wy, CUtensorMap* uo, CUtensorMap* vr) {
+        return cached_map3(wy, v.wy, nxg, g.Ny, g.Nz + 1, L::BXC, kTY, 1) &&
+               cached_map3(uo, v.uo, nxg, g.Ny, g.Nz, L::BXC, kTY, 1) &&
+               cached_map3(vr, v.vr, nxg, g.Ny + 1, g.Nz, L::BXC, kTY + 1, 1);
+    };
+    if (!set_maps(v0, &mwy, &muo, &mvr) || (MT && !set_maps(v1, &mwy1, &muo1, &mvr1)) ||
         !cached_map3(&mlc, lc, 12, g.Nz, 1, 12, 1, 1))
         return cudaErrorInvalidValue;
     const int tiles = (g.Nx / kTX) * (g.Ny / kTY);
@@ -460,11 +509,25 @@ cudaError_t launch_x(const Grid<float>& g, const float* WY, const float* UO, con
         kcl = (g.Nz + chunks - 1) / chunks;
     }
     const int chunks = (g.Nz + kcl - 1) / kcl;
-    XArgs A{g, T, Tm1, Tp1, lc, (float)c.a, (float)c.b, (float)c.gdt, kcl, err, divmax, {}};
+    XArgs A{g, T, Tm1, Tp1, lc, (float)c.a, (float)c.b, (float)c.gdt, kcl, err, divmax, {}, alpha};
     memcpy(A.rx, rx12, sizeof A.rx);
     dim3 grid(chunks, g.Nx / kTX, g.Ny / kTY);
-    k_xfused<M, DIVONLY, LF><<<grid, kThreadsAll, L::bytes, st>>>(mn, mm, mwy, muo, mvr, mlc, A);
+    k_xfused<M, DIVONLY, LF, MT><<<grid, kThreadsAll, L::bytes, st>>>(mn, mm, mwy, muo, mvr, mlc, mwy1, muo1, mvr1, A);
     return cudaGetLastError();
+}
+
+template <int M>
+cudaError_t launch_step_m(const Grid<float>& g, XSet v0, const XSet* v1, float alpha, int nxg, const float* lc,
+                          const float* rx12, const float* Tm1, const float* T, float* Tp1, StepCoef c, int* err,
+                          cudaStream_t st)
+{
+    const bool lf = (c.a == 1.0 && c.b == 0.0);
+    if (v1) {
+        return lf ? launch_x<M, false, true, true>(g, v0, *v1, alpha, nxg, lc, rx12, Tm1, T, Tp1, c, err, nullptr, st)
+                  : launch_x<M, false, false, true>(g, v0, *v1, alpha, nxg, lc, rx12, Tm1, T, Tp1, c, err, nullptr, st);
+    }
+    return lf ? launch_x<M, false, true, false>(g, v0, v0, 0.f, nxg, lc, rx12, Tm1, T, Tp1, c, err, nullptr, st)
+              : launch_x<M, false, false, false>(g, v0, v0, 0.f, nxg, lc, rx12, Tm1, T, Tp1, c, err, nullptr, st);
 }
 
 }  // namespace
@@ -474,25 +537,28 @@ cudaError_t launch_xfused_prep(const Grid<float>& g, const float* U, const float
 {
     cudaError_t e = launch_column_balance<float>(g, U, V, W, scrW, st);
     if (e != cudaSuccess) return e;
-    const unsigned blocks = 152 * 16;
-    k_xprep_wy<<<blocks, 256, 0, st>>>(g, W, scrW, WY, nxg);
-    k_xprep_uo<<<blocks, 256, 0, st>>>(g, U, UO, nxg);
-    k_xprep_vr<<<blocks, 256, 0, st>>>(g, V, UO, WY, VR, nxg);
+    const unsigned row = (unsigned)((nxg * g.Ny + 255) / 256), rowc = (unsigned)((nxg * (g.ny + 1) + 255) / 256);
+    k_xprep_wy<<<dim3(row, g.Nz + 1), 256, 0, st>>>(g, W, scrW, WY, nxg);
+    k_xprep_uo<<<dim3(row, g.Nz), 256, 0, st>>>(g, U, UO, nxg);
+    k_xprep_vr<<<dim3(rowc, g.Nz), 256, 0, st>>>(g, V, UO, WY, VR, nxg);
     return cudaGetLastError();
 }
 
-cudaError_t launch_step_xfused_f32(const Grid<float>& g, const float* WY, const float* UO, const float* VR, int nxg,
-                                   const float* lc, const float* rx12, const float* Tm1, const float* T, float* Tp1,
-                                   StepCoef c, cudaStream_t st)
+cudaError_t launch_step_xfused_f32(const Grid<float>& g, const float* const setA[3], const float* const setB[3],
+                                   double alpha, int nxg, const float* lc, const float* rx12, const float* Tm1,
+                                   const float* T, float* Tp1, StepCoef c, cudaStream_t st)
 {
     int* err = fused_error_flag();
     if (!err) return cudaErrorMemoryAllocation;
-    const bool lf = (c.a == 1.0 && c.b == 0.0);
-    if (g.mx == 4)
-        return lf ? launch_x<4, false, true>(g, WY, UO, VR, nxg, lc, rx12, Tm1, T, Tp1, c, err, nullptr, st)
-                  : launch_x<4, false, false>(g, WY, UO, VR, nxg, lc, rx12, Tm1, T, Tp1, c, err, nullptr, st);
-    return lf ? launch_x<2, false, true>(g, WY, UO, VR, nxg, lc, rx12, Tm1, T, Tp1, c, err, nullptr, st)
-              : launch_x<2, false, false>(g, WY, UO, VR, nxg, lc, rx12, Tm1, T, Tp1, c, err, nullptr, st);
+    const XSet v0{setA[0], setA[1], setA[2]};
+    XSet v1{};
+    const XSet* pv1 = nullptr;
+    if (setB && alpha != 0.0) {
+        v1 = XSet{setB[0], setB[1], setB[2]};
+        pv1 = &v1;
+    }
+    if (g.mx == 4) return launch_step_m<4>(g, v0, pv1, (float)alpha, nxg, lc, rx12, Tm1, T, Tp1, c, err, st);
+    return launch_step_m<2>(g, v0, pv1, (float)alpha, nxg, lc, rx12, Tm1, T, Tp1, c, err, st);
 }
 
 cudaError_t launch_maxdiv_xfused_f32(const Grid<float>& g, const float* WY, const float* UO, const float* VR, int nxg,
@@ -504,8 +570,10 @@ cudaError_t launch_maxdiv_xfused_f32(const Grid<float>& g, const float* WY, cons
     if (e != cudaSuccess) return e;
     unsigned long long* dm = reinterpret_cast<unsigned long long*>(partials);
     StepCoef c{0, 0, 0};
-    if (g.mx == 4) return launch_x<4, true, false>(g, WY, UO, VR, nxg, lc, rx12, nullptr, nullptr, nullptr, c, err, dm, st);
-    return launch_x<2, true, false>(g, WY, UO, VR, nxg, lc, rx12, nullptr, nullptr, nullptr, c, err, dm, st);
+    const XSet v{WY, UO, VR};
+    if (g.mx == 4)
+        return launch_x<4, true, false, false>(g, v, v, 0.f, nxg, lc, rx12, nullptr, nullptr, nullptr, c, err, dm, st);
+    return launch_x<2, true, false, false>(g, v, v, 0.f, nxg, lc, rx12, nullptr, nullptr, nullptr, c, err, dm, st);
 }
 
 }  // namespace mr

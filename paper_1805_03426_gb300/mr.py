@@ -61,6 +61,7 @@ _SIGS = {
     "mr_set_scalar": (ctypes.c_int, [_VP, _VP, _I32, _VP]),
     "mr_get_scalar": (ctypes.c_int, [_VP, _VP, _VP, _I32, _VP]),
     "mr_scalar_step": (ctypes.c_int, [_VP, _I64, _VP]),
+    "mr_scalar_coarse_step": (ctypes.c_int, [_VP, _VP, _VP, _VP, _I32, _VP]),
     "mr_step_index": (ctypes.c_int, [_VP, ctypes.POINTER(_I64)]),
     "mr_scalar_stats": (ctypes.c_int, [_VP, ctypes.POINTER(mr_stats), _VP]),
     "mr_plate_nu": (ctypes.c_int, [_VP, _VP, _VP]),
@@ -241,6 +242,17 @@ def mr_get_scalar(h: Handle, T, Tprev=None, stream=None):
 
 def mr_scalar_step(h: Handle, nsteps: int, stream=None):
     _check(lib().mr_scalar_step(h.ptr, int(nsteps), _stream(stream)))
+
+
+def mr_scalar_coarse_step(h: Handle, U, V, W, mt: int, stream=None):
+    """One coarse step with temporal refinement (Section 3.4): U, V, W are the
+    coarse velocity of the next coarse time level; mt scalar steps follow with
+    the velocity interpolated linearly in time from the current one."""
+    s = h.shapes
+    pu = _ptr(U, _n(s["U"]), np.float64, "U")
+    pv = _ptr(V, _n(s["V"]), np.float64, "V")
+    pw = _ptr(W, _n(s["W"]), np.float64, "W")
+    _check(lib().mr_scalar_coarse_step(h.ptr, pu, pv, pw, int(mt), _stream(stream)))
 
 
 def mr_step_index(h: Handle) -> int:

@@ -510,3 +510,97 @@ def test_nusselt_profile_advective_part_on_linear_profile(oracle_mod):
     zf = g["zf"]
     adv = (W[1:-1] * (0.5 - zf[1:-1])[:, None, None]).mean(axis=(1, 2)) / cfg.kappa
     np.testing.assert_allclose(nu_z[1:-1], 1.0 + adv, rtol=1e-12, atol=1e-12)
+
+
+# ----------------------------------------------------------------------------- temporal refinement (Section 3.4)
+
+def _temporal_case(O, walls=0, adiabatic=0):
+    cfg = _cfg(O, nx=6, ny=5, nz=4, mx=2, my=2, mz=2, gamma=1.5, kappa=3e-3, dt=4e-3, np_average=4,
+               plates_dirichlet=0 if adiabatic else 1, walls_xy=walls)
+    g = O.grid(cfg)
+    Nx, Ny, Nz = cfg.dense
+    T0 = synth.initial_scalar(11, g["zc"], Ny, Nx, noise=0.1)
+    return cfg, T0
+
+
+def test_coarse_step_with_a_constant_velocity_is_plain_stepping(oracle_mod):
+    """U^{n-1} = U^n: every interpolated field equals U exactly, so mt
+    sub-steps are mt plain steps (bit for bit)."""
+    O = oracle_mod
+    cfg, T0 = _temporal_case(O)
+    vel = O.refine(cfg, *_velocity(O, cfg))
+    Tp, Tc = O.coarse_step(cfg, vel, vel, T0, T0, 0, 5)
+    rp, rc = O.run(cfg, vel, T0, 5)
+    assert np.array_equal(Tp, rp) and np.array_equal(Tc, rc)
+
+
+def test_coarse_step_first_substep_uses_the_previous_level(oracle_mod):
+    """Sub-step i = 0 runs on U^{n-1} alone (weight 0 on U^n): with U^{n-1} = 0
+    the first sub-step is pure diffusion whatever U^n is; with mt = 1 the coarse
+    step is a single plain step on U^{n-1}."""
+    O = oracle_mod
+    cfg, T0 = _temporal_case(O)
+    vel = O.refine(cfg, *_velocity(O, cfg))
+    zero = tuple(np.zeros_like(a) for a in vel)
+    _, T1 = O.coarse_step(cfg, zero, vel, T0, T0, 0, 1)
+    assert np.array_equal(T1, O.step(cfg, zero, T0, T0, 0))
+    _, T1 = O.coarse_step(cfg, vel, zero, T0, T0, 0, 1)
+    assert np.array_equal(T1, O.step(cfg, vel, T0, T0, 0))
+    T2p, T2 = O.coarse_step(cfg, zero, vel, T0, T0, 0, 3)
+    assert not np.array_equal(T2, O.run(cfg, zero, T0, 3)[1])   # later sub-steps do see U^n
+
+
+@pytest.mark.parametrize("mt", [2, 4])
+def test_coarse_step_weights_reverse_flow(oracle_mod, mt):
+    """U^n = -U^{n-1}: the interpolated velocity is U^{n-1} (1 - 2 i/mt) (up to one
+    rounding at i = 3 of mt = 4).  It vanishes exactly at i = mt/2, so that
+    sub-step is pure diffusion: a wrong weight (an offset i + 1, or the printed
+    form U^{n-1} + (i/M_t) U^n) leaves a flow there and fails."""
+    O = oracle_mod
+    cfg, T0 = _temporal_case(O)
+    vel = O.refine(cfg, *_velocity(O, cfg))
+    neg = tuple(-a for a in vel)
+    zero = tuple(np.zeros_like(a) for a in vel)
+    Tm1, T = T0, T0
+    for i in range(mt):
+        f = 1.0 - 2.0 * i / mt
+        v = zero if i == mt // 2 else tuple(f * a for a in vel)
+        Tm1, T = T, O.step(cfg, v, Tm1, T, i)
+    got_p, got = O.coarse_step(cfg, vel, neg, T0, T0, 0, mt)
+    np.testing.assert_allclose(got_p, Tm1, rtol=0, atol=1e-14)
+    np.testing.assert_allclose(got, T, rtol=0, atol=1e-14)
+
+
+@pytest.mark.parametrize("walls", [0, 1])
+def test_coarse_steps_conserve_the_integral(oracle_mod, walls):
+    """Time-varying velocity: each interpolated field is a combination of two
+    divergence-free fields, so with adiabatic plates (and walls) sum T Vol stays
+    fixed through two coarse steps of three sub-steps each."""
+    O = oracle_mod
+    cfg, T0 = _temporal_case(O, walls=walls, adiabatic=1)
+    g = O.grid(cfg)
+    Nx, Ny, _ = cfg.dense
+    vol = (cfg.lx / Nx) * (cfg.ly / Ny) * g["dz"][:, None, None]
+    I0 = float((T0 * vol).sum())
+    vels = [O.refine(cfg, *_velocity(O, cfg, seed=s)) for s in (1, 2, 3)]
+    Tm1, T = T0, T0
+    for n in range(2):
+        Tm1, T = O.coarse_step(cfg, vels[n], vels[n + 1], Tm1, T, 3 * n, 3)
+        assert abs(float((T * vol).sum()) - I0) < 1e-14
+    assert np.abs(T - T0).max() > 1e-3                                   # the flow did move T
+
+
+@pytest.mark.parametrize("w", [1 / 3, 0.5, 0.8])
+def test_interpolated_velocity_is_divergence_free(oracle_mod, w):
+    """Section 3.4: a linear combination of two discretely divergence-free
+    refined fields is discretely divergence-free, and it equals the refinement
+    of the interpolated coarse field (the refinement is linear)."""
+    O = oracle_mod
+    cfg = _cfg(O, nx=6, ny=6, nz=4, mx=2, my=3, mz=2, gamma=1.5)
+    c1, c2 = _velocity(O, cfg, seed=4), _velocity(O, cfg, seed=5)
+    r1, r2 = O.refine(cfg, *c1), O.refine(cfg, *c2)
+    ri = tuple(a + w * (b - a) for a, b in zip(r1, r2))
+    assert O.max_divergence(cfg, ri) < 1e-13
+    rc = O.refine(cfg, *(a + w * (b - a) for a, b in zip(c1, c2)))
+    for x, y in zip(ri, rc):
+        np.testing.assert_allclose(x, y, atol=1e-14)
