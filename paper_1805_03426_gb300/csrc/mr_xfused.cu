@@ -159,7 +159,10 @@ k_xfused(const __grid_constant__ CUtensorMap tmn, const __grid_constant__ CUtens
 
     // ---------------------------------------------------------------- consumer warps
     const float dx = g.dx, dy = g.dy, fx_y = dx / dy;
-    const int seg = tid & 15, jl = tid >> 4;     // this thread's 4-cell segment of dense row jl
+    // this thread's 4-cell segment of dense row jl; the two half-warps take rows
+    // two apart (bundle rows 2 BXC floats apart fall 16 banks apart, so the
+    // half-warps' coarse-column reads do not conflict at M = 4)
+    const int seg = tid & 15, jl = ((warp >> 1) << 2) + (warp & 1) + 2 * ((tid >> 4) & 1);
     const int il0 = seg * 4, cb0 = il0 / M;      // first coarse column of the segment (tile-local)
     const auto& rx = A.rx;
     const bool wrap_w = (i0 == 0 && seg == 0), wrap_e = (i0 + kTX == g.Nx && seg == 15);
@@ -345,37 +348,42 @@ k_xfused(const __grid_constant__ CUtensorMap tmn, const __grid_constant__ CUtens
 // Periodic wrap of a coarse column index that is at most one period outside.
 __device__ __forceinline__ int wrapc(int i, int n) { return i < 0 ? i + n : (i >= n ? i - n : i); }
 
-// The three kernels below run one thread per (gx, j) of one dense plane
+// The kernels below run one thread per (gx, coarse row J) of one dense layer
 // k = blockIdx.y (32-bit index arithmetic; gx is the bundle column, coarse
 // column I = gx - 4 wrapped).
 
-// WY[k][j][gx]: R_y of the full-area W on every dense plane (coarse W on the
-// coarse planes, slab-balanced scrW on the inner ones).
-__global__ void k_xprep_wy(Grid<float> g, const float* __restrict__ W, const float* __restrict__ scrW,
-                           float* __restrict__ WY, int nxg)
+// UO[k][j][gx], the outer U sub-face of coarse x-face I (R_y R_z of U: the z
+// split first, shared by the M_y dense rows of J), and WY[k][j][gx], R_y of
+// the full-area W on dense plane k (coarse W on the coarse planes,
+// slab-balanced scrW on the inner ones); the top layer also writes plane Nz.
+__global__ void k_xprep_uowy(Grid<float> g, const float* __restrict__ U, const float* __restrict__ W,
+                             const float* __restrict__ scrW, float* __restrict__ UO, float* __restrict__ WY, int nxg)
 {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= nxg * g.Ny) return;
-    const int k = blockIdx.y, j = t / nxg, gx = t - j * nxg;
-    const int I = wrapc(gx - 4, g.nx), J = j / g.my, K = k / g.mz;
-    const float* src = (k == K * g.mz) ? W + (size_t)K * g.ny * g.nx : scrW + (size_t)k * g.ny * g.nx;
-    float s = 0.f;
-    for (int q = 0; q < 3; ++q) s += g.Ry[3 * j + q] * src[(size_t)g.wy[3 * J + q] * g.nx + I];
-    WY[(size_t)k * g.Ny * nxg + t] = s;
-}
-
-// UO[k][j][gx]: the outer U sub-face of coarse x-face I (R_y R_z of U).
-__global__ void k_xprep_uo(Grid<float> g, const float* __restrict__ U, float* __restrict__ UO, int nxg)
-{
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= nxg * g.Ny) return;
-    const int k = blockIdx.y, j = t / nxg, gx = t - j * nxg;
-    const int I = wrapc(gx - 4, g.nx), J = j / g.my, K = k / g.mz;
-    float s = 0.f;
-    for (int p = 0; p < 3; ++p)
-        for (int q = 0; q < 3; ++q)
-            s += g.Ry[3 * j + p] * g.Rz[3 * k + q] * U[((size_t)g.wz[3 * K + q] * g.ny + g.wy[3 * J + p]) * g.nx + I];
-    UO[(size_t)k * g.Ny * nxg + t] = s;
+    if (t >= nxg * g.ny) return;
+    const int k = blockIdx.y, J = t / nxg, gx = t - J * nxg;
+    const int I = wrapc(gx - 4, g.nx), K = k / g.mz;
+    float a[3];
+    for (int p = 0; p < 3; ++p) {
+        const int Jp = g.wy[3 * J + p];
+        float s = 0.f;
+        for (int q = 0; q < 3; ++q) s += g.Rz[3 * k + q] * U[((size_t)g.wz[3 * K + q] * g.ny + Jp) * g.nx + I];
+        a[p] = s;
+    }
+    for (int b = 0; b < g.my; ++b) {
+        const int j = J * g.my + b;
+        UO[((size_t)k * g.Ny + j) * nxg + gx] = g.Ry[3 * j] * a[0] + g.Ry[3 * j + 1] * a[1] + g.Ry[3 * j + 2] * a[2];
+    }
+    for (int kp = k; kp <= (k == g.Nz - 1 ? g.Nz : k); ++kp) {
+        const int Kp = kp / g.mz;
+        const float* src = (kp == Kp * g.mz) ? W + (size_t)Kp * g.ny * g.nx : scrW + (size_t)kp * g.ny * g.nx;
+        float c[3];
+        for (int p = 0; p < 3; ++p) c[p] = src[(size_t)g.wy[3 * J + p] * g.nx + I];
+        for (int b = 0; b < g.my; ++b) {
+            const int j = J * g.my + b;
+            WY[((size_t)kp * g.Ny + j) * nxg + gx] = g.Ry[3 * j] * c[0] + g.Ry[3 * j + 1] * c[1] + g.Ry[3 * j + 2] * c[2];
+        }
+    }
 }
 
 // VR[k][j][gx]: full-coarse-width V on every dense y-face, by the row balance
@@ -537,10 +545,9 @@ cudaError_t launch_xfused_prep(const Grid<float>& g, const float* U, const float
 {
     cudaError_t e = launch_column_balance<float>(g, U, V, W, scrW, st);
     if (e != cudaSuccess) return e;
-    const unsigned row = (unsigned)((nxg * g.Ny + 255) / 256), rowc = (unsigned)((nxg * (g.ny + 1) + 255) / 256);
-    k_xprep_wy<<<dim3(row, g.Nz + 1), 256, 0, st>>>(g, W, scrW, WY, nxg);
-    k_xprep_uo<<<dim3(row, g.Nz), 256, 0, st>>>(g, U, UO, nxg);
-    k_xprep_vr<<<dim3(rowc, g.Nz), 256, 0, st>>>(g, V, UO, WY, VR, nxg);
+    const unsigned row = (unsigned)((nxg * g.ny + 127) / 128), rowc = (unsigned)((nxg * (g.ny + 1) + 127) / 128);
+    k_xprep_uowy<<<dim3(row, g.Nz), 128, 0, st>>>(g, U, W, scrW, UO, WY, nxg);
+    k_xprep_vr<<<dim3(rowc, g.Nz), 128, 0, st>>>(g, V, UO, WY, VR, nxg);
     return cudaGetLastError();
 }
 
