@@ -392,30 +392,9 @@ int mr_create(const mr_config* cfg, mr_handle* out)
     rc = upload_metric<double>(h, (char*)b.metric, dwin, h->g64);
     if (!rc) rc = upload_metric<float>(h, (char*)b.metric + mb64, dwin, h->g32);
     if (!rc && b.xlc) {
-        // per-layer constants of the split-x fused kernel: dz, 1/dz, the two face
-        // interpolation weights below and above, kappa/(dz d) below and above, dx/dz
-        std::vector<float> lc((size_t)h->Nz * 12, 0.f);
-        const bool dir = c.bc_plates == MR_DIRICHLET;
-        const double dx = c.lx / h->Nx;
-        for (int k = 0; k < h->Nz; ++k) {
-            float* q = &lc[(size_t)k * 12];
-            const double dzk = h->dz[k];
-            const double below = k > 0 ? h->zc[k] - h->zc[k - 1] : h->zc[0] - h->zf[0];
-            const double above = k < h->Nz - 1 ? h->zc[k + 1] - h->zc[k] : h->zf[h->Nz] - h->zc[h->Nz - 1];
-            q[0] = (float)dzk;
-            q[1] = (float)(1.0 / dzk);
-            if (k > 0) {
-                q[2] = (float)(dzk / (h->dz[k - 1] + dzk));
-                q[3] = (float)(h->dz[k - 1] / (h->dz[k - 1] + dzk));
-            }
-            if (k < h->Nz - 1) {
-                q[4] = (float)(h->dz[k + 1] / (dzk + h->dz[k + 1]));
-                q[5] = (float)(dzk / (dzk + h->dz[k + 1]));
-            }
-            q[6] = (k > 0 || dir) ? (float)(h->kappa / (dzk * below)) : 0.f;
-            q[7] = (k < h->Nz - 1 || dir) ? (float)(h->kappa / (dzk * above)) : 0.f;
-            q[8] = (float)(dx / dzk);
-        }
+        const std::vector<float> lc =
+            xfused_layer_constants(h->Nz, h->zf.data(), h->zc.data(), h->dz.data(), h->kappa, c.lx / h->Nx,
+                                   c.ly / h->Ny, c.bc_plates == MR_DIRICHLET);
         rc = cuda_check(cudaMemcpy(b.xlc, lc.data(), lc.size() * 4, cudaMemcpyHostToDevice), "mr_create: layer constants");
         // x is uniform and periodic: every coarse cell has the same R_x rows
         for (int q = 0; q < 12; ++q) b.xrx[q] = (float)h->Rx[(size_t)(q / 3) * 3 + q % 3];

@@ -171,6 +171,9 @@ cudaError_t launch_maxdiv_fused_f32(const Grid<float>& g, const float* U, const 
                                     const float* W, double* partials, int blocks, cudaStream_t st);
 bool fused_supported(const mr_config& cfg, std::string* why);
 int* fused_error_flag();
+// per-layer constant table [Nz][12] of the split-x kernel (layout owned by mr_xfused.cu)
+std::vector<float> xfused_layer_constants(int Nz, const double* zf, const double* zc, const double* dz, double kappa,
+                                          double dx, double dy, bool dirichlet);
 // Raise a kernel's dynamic shared-memory limit once per device (*done: one bit per device).
 cudaError_t smem_optin(const void* kernel, int bytes, unsigned long long* done);
 template <typename P>

@@ -7,7 +7,9 @@
 //                slab-balanced full-area W),
 //   UO[k][j][I]  the outer U sub-face of coarse x-face I (R_y R_z of U),
 //   VR[k][j][I]  the full-coarse-width V on dense y-face j (row balance),
-// which depend on the coarse velocity only; they are computed once per
+// which depend on the coarse velocity only (UO and VR are stored multiplied by
+// 1/(2 dx) and 1/(2 dy), the factors with which they enter the advective
+// fluxes, so the x balance runs in those units); they are computed once per
 // mr_refine_velocity (1/M_x of the dense face count, with 4 periodic ghost
 // columns each side so that every TMA box stays in bounds and 16-byte
 // aligned).  The step kernel streams them with the two scalar levels through
@@ -82,6 +84,13 @@ struct XArgs {
                          // same for every thread: kept in the constant bank)
     float alpha;         // MT: weight of the second velocity set, i / M_t (Section 3.4)
 };
+
+// R_x split of three coarse values by one row of R (rows sum to one):
+// c1 + r0 (c0 - c1) + r2 (c2 - c1)
+__device__ __forceinline__ float rsplit(const float (&r)[3], float c0, float c1, float c2)
+{
+    return c1 + r[0] * (c0 - c1) + r[2] * (c2 - c1);
+}
 
 // LF: a plain leapfrog step (a = 1, b = 0), by far the most frequent kind.
 // MT: the velocity is A + alpha (B - A) between the intermediates of two
@@ -158,7 +167,6 @@ k_xfused(const __grid_constant__ CUtensorMap tmn, const __grid_constant__ CUtens
     }
 
     // ---------------------------------------------------------------- consumer warps
-    const float dx = g.dx, dy = g.dy, fx_y = dx / dy;
     // this thread's 4-cell segment of dense row jl; the two half-warps take rows
     // two apart (bundle rows 2 BXC floats apart fall 16 banks apart, so the
     // half-warps' coarse-column reads do not conflict at M = 4)
@@ -170,7 +178,7 @@ k_xfused(const __grid_constant__ CUtensorMap tmn, const __grid_constant__ CUtens
 
     bool fail = false;
     float dmax = 0.f;
-    const float hix = 0.5f * g.inv_dx, hiy = 0.5f * g.inv_dy, kx2 = g.kx2, ky2 = g.ky2;
+    const float kx2 = g.kx2, ky2 = g.ky2;
     const float ca = A.a, cbb = A.b, gdt = A.gdt, alpha = A.alpha;
     // ring bookkeeping without divisions: slots of planes k-1, k, k+1 and the
     // next (slot, parity) to wait for
@@ -178,10 +186,9 @@ k_xfused(const __grid_constant__ CUtensorMap tmn, const __grid_constant__ CUtens
     int wslot = 0, wpar = 0, waited = 0;
     const size_t plane = (size_t)g.Nx * g.Ny;
     float* outp = A.Tp1 + (size_t)k0 * plane + (size_t)(j0 + jl) * g.Nx + i0 + il0;
-    const float* gn = A.Tn + (size_t)k0 * plane;
-    const float* gm = A.Tm + (size_t)k0 * plane;
     const int o = (jl + 1) * kBX + il0 + 4;          // this segment's first cell in a plane box
 
+    float wcar[4] = {0.f, 0.f, 0.f, 0.f};            // R_x split of W on plane k (from layer k-1)
     for (int k = k0; k < k1; ++k) {
         const int need = k - k0 + 2;             // ring of plane k+1 and of this layer's bundle
         while (!fail && waited <= need) {
@@ -191,11 +198,12 @@ k_xfused(const __grid_constant__ CUtensorMap tmn, const __grid_constant__ CUtens
         }
         if (!fail) {
             const float* bun = sm + st * L::slot;
-            // layer constants (from the bundle): dz, 1/dz, wlo_b, whi_b | wlo_t, whi_t, cdn, cup | dx/dz
+            // layer constants (from the bundle, see xfused_layer_constants)
             const float4 c0 = *reinterpret_cast<const float4*>(bun + L::oLC);
             const float4 c1 = *reinterpret_cast<const float4*>(bun + L::oLC + 4);
-            const float inv_dz = c0.y, wlo_b = c0.z, whi_b = c0.w, wlo_t = c1.x, whi_t = c1.y, cdn = c1.z, cup = c1.w;
-            const float fx_z = bun[L::oLC + 8];
+            const float2 c2 = *reinterpret_cast<const float2*>(bun + L::oLC + 8);
+            const float inv_dz = c0.x, bwlo = c0.y, bwhi = c0.z, twlo = c0.w;
+            const float twhi = c1.x, cdn = c1.y, cup = c1.z, diag = c1.w, plate = c2.x, hz = c2.y;
             float wb[4], wt[4], vs[4], vn[4], us[5];
             {
                 // R_x splits of the full-width W (planes k, k+1) and V (faces jl, jl+1);
@@ -208,14 +216,24 @@ k_xfused(const __grid_constant__ CUtensorMap tmn, const __grid_constant__ CUtens
                 // the coarse columns a segment touches (interpolated in time with MT)
                 constexpr int NV = NC + 2;
                 float ybv[NV], ytv[NV], rsv[NV], rnv[NV], urv[NC + 1];
+                if (k == k0) {
+#pragma unroll
+                    for (int c = 0; c < NV; ++c) {
+                        ybv[c] = yb[c];
+                        if (MT) ybv[c] += alpha * (yb[c + L::DS] - ybv[c]);
+                    }
+#pragma unroll
+                    for (int a = 0; a < 4; ++a) {
+                        const int cb = a / M;
+                        wcar[a] = rsplit(rx[a], ybv[cb], ybv[cb + 1], ybv[cb + 2]);
+                    }
+                }
 #pragma unroll
                 for (int c = 0; c < NV; ++c) {
-                    ybv[c] = yb[c];
                     ytv[c] = yt[c];
                     rsv[c] = rs[c];
                     rnv[c] = rn[c];
                     if (MT) {
-                        ybv[c] += alpha * (yb[c + L::DS] - ybv[c]);
                         ytv[c] += alpha * (yt[c + L::DS] - ytv[c]);
                         rsv[c] += alpha * (rs[c + L::DS] - rsv[c]);
                         rnv[c] += alpha * (rn[c + L::DS] - rnv[c]);
@@ -229,12 +247,13 @@ k_xfused(const __grid_constant__ CUtensorMap tmn, const __grid_constant__ CUtens
 #pragma unroll
                 for (int a = 0; a < 4; ++a) {
                     const int cb = a / M;
-                    wb[a] = rx[a][0] * ybv[cb] + rx[a][1] * ybv[cb + 1] + rx[a][2] * ybv[cb + 2];
-                    wt[a] = rx[a][0] * ytv[cb] + rx[a][1] * ytv[cb + 1] + rx[a][2] * ytv[cb + 2];
-                    vs[a] = rx[a][0] * rsv[cb] + rx[a][1] * rsv[cb + 1] + rx[a][2] * rsv[cb + 2];
-                    vn[a] = rx[a][0] * rnv[cb] + rx[a][1] * rnv[cb + 1] + rx[a][2] * rnv[cb + 2];
+                    wb[a] = wcar[a];
+                    wt[a] = rsplit(rx[a], ytv[cb], ytv[cb + 1], ytv[cb + 2]);
+                    vs[a] = rsplit(rx[a], rsv[cb], rsv[cb + 1], rsv[cb + 2]);
+                    vn[a] = rsplit(rx[a], rnv[cb], rnv[cb + 1], rnv[cb + 2]);
                 }
-                // stage X: cell balance, west to east, in velocity units
+                // stage X: cell balance, west to east, in units of U / (2 dx) (V is in
+                // units of V / (2 dy): the dx/dy factor of the balance cancels)
 #pragma unroll
                 for (int q = 0; q < NC; ++q) {
                     float h = urv[q];
@@ -242,16 +261,18 @@ k_xfused(const __grid_constant__ CUtensorMap tmn, const __grid_constant__ CUtens
 #pragma unroll
                     for (int a = 0; a < M - 1; ++a) {
                         const int m = q * M + a;
-                        h = h - (vn[m] - vs[m]) * fx_y - (wt[m] - wb[m]) * fx_z;
+                        h = h - (vn[m] - vs[m]) - (wt[m] - wb[m]) * hz;
                         us[m + 1] = h;
                     }
                 }
                 us[4] = urv[NC];
+#pragma unroll
+                for (int a = 0; a < 4; ++a) wcar[a] = wt[a];
             }
             if (DIVONLY) {
 #pragma unroll
                 for (int a = 0; a < 4; ++a) {
-                    const float d = (us[a + 1] - us[a]) * g.inv_dx + (vn[a] - vs[a]) * g.inv_dy + (wt[a] - wb[a]) * inv_dz;
+                    const float d = 2.f * ((us[a + 1] - us[a]) + (vn[a] - vs[a])) + (wt[a] - wb[a]) * inv_dz;
                     dmax = fmaxf(dmax, fabsf(d));
                 }
             } else {
@@ -274,6 +295,8 @@ k_xfused(const __grid_constant__ CUtensorMap tmn, const __grid_constant__ CUtens
                 if (seg == 15) { te = Pn_c[o + 4]; de = Pm_c[o + 4]; }
                 if (wrap_w | wrap_e | wrap_s | wrap_n) {
                     // the box holds zeros beyond the domain: fetch the periodic images
+                    const float* gn = A.Tn + (size_t)k * plane;
+                    const float* gm = A.Tm + (size_t)k * plane;
                     const size_t row = (size_t)(j0 + jl) * g.Nx;
                     if (wrap_w) { tw = gn[row + g.Nx - 1]; dw = gm[row + g.Nx - 1]; }
                     if (wrap_e) { te = gn[row]; de = gm[row]; }
@@ -288,31 +311,27 @@ k_xfused(const __grid_constant__ CUtensorMap tmn, const __grid_constant__ CUtens
                     }
                 }
                 // planes below / above: zero-filled beyond the plates, where the plate
-                // W is exactly zero and the plate value enters the diffusion below
+                // W is exactly zero and the plate value enters D through `plate`
                 const float4 tb4 = *reinterpret_cast<const float4*>(Pn_b + o);
                 const float4 db4 = *reinterpret_cast<const float4*>(Pm_b + o);
                 const float4 tt4 = *reinterpret_cast<const float4*>(Pn_t + o);
                 const float4 dt4 = *reinterpret_cast<const float4*>(Pm_t + o);
-                const bool bot = (k == 0), top = (k == g.Nz - 1);
                 const float tcv[6] = {tw, tc4.x, tc4.y, tc4.z, tc4.w, te};
                 const float dcv[6] = {dw, dc4.x, dc4.y, dc4.z, dc4.w, de};
                 const float tsv[4] = {ts4.x, ts4.y, ts4.z, ts4.w}, tnv[4] = {tn4.x, tn4.y, tn4.z, tn4.w};
                 const float dsv[4] = {ds4.x, ds4.y, ds4.z, ds4.w}, dnv[4] = {dn4.x, dn4.y, dn4.z, dn4.w};
                 const float tbv[4] = {tb4.x, tb4.y, tb4.z, tb4.w}, ttv[4] = {tt4.x, tt4.y, tt4.z, tt4.w};
-                float dbv[4] = {db4.x, db4.y, db4.z, db4.w}, dtv[4] = {dt4.x, dt4.y, dt4.z, dt4.w};
-                if (bot) { dbv[0] = dbv[1] = dbv[2] = dbv[3] = kTBottom; }
-                if (top) { dtv[0] = dtv[1] = dtv[2] = dtv[3] = kTTop; }
-                // D = kx2 (dw + de) + ky2 (ds + dn) + cdn db + cup dt - diag dc
-                const float diag = 2.f * kx2 + 2.f * ky2 + cdn + cup;
-                const float bwlo = wlo_b * inv_dz, bwhi = whi_b * inv_dz, twlo = wlo_t * inv_dz, twhi = whi_t * inv_dz;
+                const float dbv[4] = {db4.x, db4.y, db4.z, db4.w}, dtv[4] = {dt4.x, dt4.y, dt4.z, dt4.w};
+                // D = kx2 (dw + de) + ky2 (ds + dn) + cdn db + cup dt - diag dc + plate
                 float res[4];
 #pragma unroll
                 for (int a = 0; a < 4; ++a) {
                     const float tc = tcv[a + 1], dc = dcv[a + 1];
-                    const float cx = (us[a] * hix) * (tcv[a] + tc) - (us[a + 1] * hix) * (tc + tcv[a + 2]);
-                    const float cy = (vs[a] * hiy) * (tsv[a] + tc) - (vn[a] * hiy) * (tc + tnv[a]);
+                    const float cx = us[a] * (tcv[a] + tc) - us[a + 1] * (tc + tcv[a + 2]);
+                    const float cy = vs[a] * (tsv[a] + tc) - vn[a] * (tc + tnv[a]);
                     const float cz = wb[a] * (bwlo * tbv[a] + bwhi * tc) - wt[a] * (twlo * tc + twhi * ttv[a]);
-                    const float D = kx2 * (dcv[a] + dcv[a + 2]) + ky2 * (dsv[a] + dnv[a]) + cdn * dbv[a] + cup * dtv[a] - diag * dc;
+                    const float D = kx2 * (dcv[a] + dcv[a + 2]) + ky2 * (dsv[a] + dnv[a]) + cdn * dbv[a] + cup * dtv[a] +
+                                    (plate - diag * dc);
                     res[a] = LF ? dc + gdt * ((cx + cy + cz) + D) : ca * dc + cbb * tc + gdt * ((cx + cy + cz) + D);
                 }
                 *reinterpret_cast<float4*>(outp) = make_float4(res[0], res[1], res[2], res[3]);
@@ -324,8 +343,6 @@ k_xfused(const __grid_constant__ CUtensorMap tmn, const __grid_constant__ CUtens
         sc = st;
         st = (st + 1 == NB) ? 0 : st + 1;
         outp += plane;
-        gn += plane;
-        gm += plane;
     }
     if (consumers_sync_or<kThreads>(fail)) {
         if (tid == 0) atomicExch(A.err, MR_ERR_TIMEOUT);
@@ -353,7 +370,7 @@ __device__ __forceinline__ int wrapc(int i, int n) { return i < 0 ? i + n : (i >
 // column I = gx - 4 wrapped).
 
 // UO[k][j][gx], the outer U sub-face of coarse x-face I (R_y R_z of U: the z
-// split first, shared by the M_y dense rows of J), and WY[k][j][gx], R_y of
+// split first, shared by the M_y dense rows of J) times 1/(2 dx), and WY[k][j][gx], R_y of
 // the full-area W on dense plane k (coarse W on the coarse planes,
 // slab-balanced scrW on the inner ones); the top layer also writes plane Nz.
 __global__ void k_xprep_uowy(Grid<float> g, const float* __restrict__ U, const float* __restrict__ W,
@@ -372,7 +389,8 @@ __global__ void k_xprep_uowy(Grid<float> g, const float* __restrict__ U, const f
     }
     for (int b = 0; b < g.my; ++b) {
         const int j = J * g.my + b;
-        UO[((size_t)k * g.Ny + j) * nxg + gx] = g.Ry[3 * j] * a[0] + g.Ry[3 * j + 1] * a[1] + g.Ry[3 * j + 2] * a[2];
+        UO[((size_t)k * g.Ny + j) * nxg + gx] =
+            (g.Ry[3 * j] * a[0] + g.Ry[3 * j + 1] * a[1] + g.Ry[3 * j + 2] * a[2]) * (0.5f * g.inv_dx);
     }
     for (int kp = k; kp <= (k == g.Nz - 1 ? g.Nz : k); ++kp) {
         const int Kp = kp / g.mz;
@@ -386,9 +404,9 @@ __global__ void k_xprep_uowy(Grid<float> g, const float* __restrict__ U, const f
     }
 }
 
-// VR[k][j][gx]: full-coarse-width V on every dense y-face, by the row balance
-// (south to north) of stage Y; one thread per coarse row J (0..ny, row ny
-// repeating row 0, periodic) walks its M_y - 1 inner faces.
+// VR[k][j][gx]: full-coarse-width V on every dense y-face times 1/(2 dy), by
+// the row balance (south to north) of stage Y; one thread per coarse row J
+// (0..ny, row ny repeating row 0, periodic) walks its M_y - 1 inner faces.
 __global__ void k_xprep_vr(Grid<float> g, const float* __restrict__ V, const float* __restrict__ UO,
                            const float* __restrict__ WY, float* __restrict__ VR, int nxg)
 {
@@ -399,17 +417,18 @@ __global__ void k_xprep_vr(Grid<float> g, const float* __restrict__ V, const flo
     float vz = 0.f;
     for (int q = 0; q < 3; ++q) vz += g.Rz[3 * k + q] * V[((size_t)g.wz[3 * K + q] * g.ny + Jf) * g.nx + I];
     const size_t vrow = (size_t)g.Ny + 1;
-    VR[((size_t)k * vrow + (size_t)J * g.my) * nxg + gx] = vz;
+    const float hiy = 0.5f * g.inv_dy, two_dx = 2.f * g.dx;   // UO holds U / (2 dx)
+    VR[((size_t)k * vrow + (size_t)J * g.my) * nxg + gx] = vz * hiy;
     if (J == g.ny) return;
     const float dzk = g.dz[k];
     const int xi = I + 4, xe = wrapc(I + 1, g.nx) + 4;
     float G = vz * g.DX * dzk;
     for (int b = 0; b < g.my - 1; ++b) {
         const int j = J * g.my + b;
-        const float uw = UO[((size_t)k * g.Ny + j) * nxg + xi], ue = UO[((size_t)k * g.Ny + j) * nxg + xe];
+        const float uw = UO[((size_t)k * g.Ny + j) * nxg + xi] * two_dx, ue = UO[((size_t)k * g.Ny + j) * nxg + xe] * two_dx;
         const float wb = WY[((size_t)k * g.Ny + j) * nxg + xi], wt = WY[((size_t)(k + 1) * g.Ny + j) * nxg + xi];
         G = G - (ue - uw) * g.dy * dzk - (wt - wb) * g.DX * g.dy;
-        VR[((size_t)k * vrow + j + 1) * nxg + gx] = G / (g.DX * dzk);
+        VR[((size_t)k * vrow + j + 1) * nxg + gx] = G / (g.DX * dzk) * hiy;
     }
 }
 
@@ -581,6 +600,46 @@ cudaError_t launch_maxdiv_xfused_f32(const Grid<float>& g, const float* WY, cons
     if (g.mx == 4)
         return launch_x<4, true, false, false>(g, v, v, 0.f, nxg, lc, rx12, nullptr, nullptr, nullptr, c, err, dm, st);
     return launch_x<2, true, false, false>(g, v, v, 0.f, nxg, lc, rx12, nullptr, nullptr, nullptr, c, err, dm, st);
+}
+
+// Per-layer constants of the split-x kernel, [Nz][12] floats, all folded on
+// the host in FP64: 1/dz; the linear-interpolation weights of T_{k-1}, T_k at
+// face k and of T_k, T_{k+1} at face k+1, each times 1/dz; kappa/(dz d) toward
+// the centre (or plate) below and above; the diagonal 2 kappa/dx^2 +
+// 2 kappa/dy^2 + cdn + cup; the plate term (Dirichlet plates: cdn T_bottom on
+// the first layer, cup T_top on the last); 1/(2 dz).  The kernel reads zeros
+// for the planes beyond the plates, where W is zero.
+std::vector<float> xfused_layer_constants(int Nz, const double* zf, const double* zc, const double* dz, double kappa,
+                                          double dx, double dy, bool dirichlet)
+{
+    std::vector<float> lc((size_t)Nz * 12, 0.f);
+    const double kx2 = kappa / (dx * dx), ky2 = kappa / (dy * dy);
+    for (int k = 0; k < Nz; ++k) {
+        float* q = &lc[(size_t)k * 12];
+        const double dzk = dz[k], idz = 1.0 / dzk;
+        const double below = k > 0 ? zc[k] - zc[k - 1] : zc[0] - zf[0];
+        const double above = k < Nz - 1 ? zc[k + 1] - zc[k] : zf[Nz] - zc[Nz - 1];
+        const double cdn = (k > 0 || dirichlet) ? kappa / (dzk * below) : 0.0;
+        const double cup = (k < Nz - 1 || dirichlet) ? kappa / (dzk * above) : 0.0;
+        q[0] = (float)idz;
+        if (k > 0) {
+            q[1] = (float)(dzk / (dz[k - 1] + dzk) * idz);
+            q[2] = (float)(dz[k - 1] / (dz[k - 1] + dzk) * idz);
+        }
+        if (k < Nz - 1) {
+            q[3] = (float)(dz[k + 1] / (dzk + dz[k + 1]) * idz);
+            q[4] = (float)(dzk / (dzk + dz[k + 1]) * idz);
+        }
+        q[5] = (float)cdn;
+        q[6] = (float)cup;
+        q[7] = (float)(2.0 * kx2 + 2.0 * ky2 + cdn + cup);
+        double plate = 0.0;
+        if (dirichlet && k == 0) plate += cdn * (double)kTBottom;
+        if (dirichlet && k == Nz - 1) plate += cup * (double)kTTop;
+        q[8] = (float)plate;
+        q[9] = (float)(0.5 * idz);
+    }
+    return lc;
 }
 
 }  // namespace mr
