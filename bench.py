@@ -339,8 +339,14 @@ def temporal_cost(torch, mr, h, w, vel0, cells, stream, mt=4, K=20):
     e1.record(stream)
     torch.cuda.synchronize()
     tr = e0.elapsed_time(e1) / 1e3
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for q in range(K):
+        mr.mr_cfl_dt(h, 0.3, stream=stream)
+    tc = time.perf_counter() - t0
     return {"mt": mt, "coarse_steps": K, "value": round(cells * mt * K / t / 1e9, 3), "unit": "Gcell-updates/s",
-            "ms_per_coarse_step": round(t / K * 1e3, 4), "refine_velocity_ms": round(tr / K * 1e3, 4)}
+            "ms_per_coarse_step": round(t / K * 1e3, 4), "refine_velocity_ms": round(tr / K * 1e3, 4),
+            "cfl_dt_ms": round(tc / K * 1e3, 4)}
 
 
 def adjoint_cost(torch, mr, stream, S=200, ck=20):

@@ -744,7 +744,7 @@ static int max_divergence(mr_handle h, double* out, cudaStream_t st)
     cudaError_t e;
     const DeviceBuffers& b = h->buf;
     if (h->cfg.velocity_mode == MR_VEL_XFUSED)
-        e = launch_maxdiv_xfused_f32(h->g32, b.xwy, b.xuo, b.xvr, b.nxg, b.xlc, b.xrx, b.red, h->red_blocks, st);
+        e = launch_xfused_max_f32(h->g32, 1, b.xwy, b.xuo, b.xvr, b.nxg, b.xlc, b.xrx, b.red, h->red_blocks, st);
     else if (h->cfg.velocity_mode == MR_VEL_FUSED)
         e = launch_maxdiv_fused_f32(h->g32, (const float*)b.Uc, (const float*)b.Vc, (const float*)b.Wc, b.red,
                                     h->red_blocks, st);
@@ -815,10 +815,14 @@ int mr_cfl_dt(mr_handle h, double cfl, double* dt_out, mr_stream stream)
     DeviceBuffers& b = h->buf;
     const void *us = b.Us, *vs = b.Vs, *ws = b.Ws;
     bool tmp = false;
-    if (h->cfg.velocity_mode != MR_VEL_STORED) {
+    cudaError_t e = cudaSuccess;
+    if (h->cfg.velocity_mode == MR_VEL_XFUSED) {
+        // the split-x kernel forms the dense faces in registers: one pass, no dense storage
+        e = launch_xfused_max_f32(h->g32, 2, b.xwy, b.xuo, b.xvr, b.nxg, b.xlc, b.xrx, b.red, h->red_blocks, st);
+    } else if (h->cfg.velocity_mode != MR_VEL_STORED) {
         // dense faces are not kept: refine into temporary buffers once
         void *a = nullptr, *bb = nullptr, *c = nullptr;
-        cudaError_t e = cudaMalloc(&a, h->nU * h->elt);
+        e = cudaMalloc(&a, h->nU * h->elt);
         if (e == cudaSuccess) e = cudaMalloc(&bb, h->nV * h->elt);
         if (e == cudaSuccess) e = cudaMalloc(&c, h->nW * h->elt);
         if (e != cudaSuccess) {
@@ -830,13 +834,16 @@ int mr_cfl_dt(mr_handle h, double cfl, double* dt_out, mr_stream stream)
         us = a; vs = bb; ws = c;
         tmp = true;
     }
-    cudaError_t e = h->cfg.precision == MR_F64
-                        ? launch_cfl<double>(h->g64, (const double*)us, (const double*)vs, (const double*)ws, b.red, h->red_blocks, st)
-                        : launch_cfl<float>(h->g32, (const float*)us, (const float*)vs, (const float*)ws, b.red, h->red_blocks, st);
+    if (h->cfg.velocity_mode != MR_VEL_XFUSED)
+        e = h->cfg.precision == MR_F64
+                ? launch_cfl<double>(h->g64, (const double*)us, (const double*)vs, (const double*)ws, b.red, h->red_blocks, st)
+                : launch_cfl<float>(h->g32, (const float*)us, (const float*)vs, (const float*)ws, b.red, h->red_blocks, st);
     std::vector<double> p;
     int rc = e != cudaSuccess ? cuda_check(e, "mr_cfl_dt: launch") : reduce_partials(h, 1, p, st);
     if (tmp) { cudaFree((void*)us); cudaFree((void*)vs); cudaFree((void*)ws); }
     if (rc) return rc;
+    if (h->cfg.velocity_mode == MR_VEL_XFUSED && fused_take_error(st) == MR_ERR_TIMEOUT)
+        return set_error(MR_ERR_TIMEOUT, "mr_cfl_dt: the split-x kernel gave up a bounded wait");
     double m = 0.0;
     for (double v : p) m = std::max(m, v);
     if (!(m > 0)) return set_error(MR_ERR_ARG, "mr_cfl_dt: zero velocity");

@@ -185,8 +185,10 @@ cudaError_t launch_xfused_prep(const Grid<float>& g, const float* U, const float
 cudaError_t launch_step_xfused_f32(const Grid<float>& g, const float* const setA[3], const float* const setB[3],
                                    double alpha, int nxg, const float* lc, const float* rx12, const float* Tm1,
                                    const float* T, float* Tp1, StepCoef c, cudaStream_t st);
-cudaError_t launch_maxdiv_xfused_f32(const Grid<float>& g, const float* WY, const float* UO, const float* VR, int nxg,
-                                     const float* lc, const float* rx12, double* partials, int blocks, cudaStream_t st);
+// kind 1: max |divergence| of the dense velocity, kind 2: max CFL rate (into partials[0])
+cudaError_t launch_xfused_max_f32(const Grid<float>& g, int kind, const float* WY, const float* UO, const float* VR,
+                                  int nxg, const float* lc, const float* rx12, double* partials, int blocks,
+                                  cudaStream_t st);
 cudaError_t launch_refine_transpose(const Grid<double>& g, double* aUs, double* aVs, double* aWs, double* aWc,
                                     double* aVrow, double* gU, double* gV, double* gW, size_t ncU, size_t ncV,
                                     size_t ncW, cudaStream_t st);

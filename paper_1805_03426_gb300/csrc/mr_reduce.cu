@@ -43,25 +43,33 @@ __device__ void block_reduce_store(double (&v)[NV], double* out)
 }
 
 // pass 0: (sum T vol, count of non-finite T); pass 1: sum (T - mean)^2 vol.
-// vol is dx dy dz_k; the dx dy factor is applied on the host.
+// vol is dx dy dz_k; the dx dy factor is applied on the host.  Blocks stride
+// over dense rows (j, k), threads over x; a thread sums its cells of a row in
+// precision P and adds the row sum times dz_k to its FP64 accumulator.
 template <typename P>
 __global__ void __launch_bounds__(kRedThreads) k_moments(Grid<P> g, const P* __restrict__ T, double mean,
                                                          int pass, double* __restrict__ partials)
 {
-    const size_t plane = (size_t)g.Nx * g.Ny;
-    const size_t n = plane * g.Nz;
+    const int rows = g.Ny * g.Nz;
+    const P mp = (P)mean;
     double v[2] = {0.0, 0.0};
-    for (size_t m = (size_t)blockIdx.x * blockDim.x + threadIdx.x; m < n; m += (size_t)gridDim.x * blockDim.x) {
-        const int k = (int)(m / plane);
-        const double t = (double)T[m];
-        const double dzk = (double)g.dz[k];
-        if (pass == 0) {
-            if (isfinite(t)) v[0] += t * dzk;
-            else v[1] += 1.0;
-        } else {
-            const double d = t - mean;
-            v[0] += d * d * dzk;
+    for (int row = blockIdx.x; row < rows; row += gridDim.x) {
+        const int k = row / g.Ny;
+        const P* r = T + (size_t)row * g.Nx;
+        P s = 0;
+        int bad = 0;
+        for (int i = threadIdx.x; i < g.Nx; i += blockDim.x) {
+            const P t = r[i];
+            if (pass == 0) {
+                if (isfinite(t)) s += t;
+                else ++bad;
+            } else {
+                const P d = t - mp;
+                s += d * d;
+            }
         }
+        v[0] += (double)s * (double)g.dz[k];
+        v[1] += (double)bad;
     }
     block_reduce_store<2, false>(v, partials + 2 * blockIdx.x);
 }
@@ -94,48 +102,62 @@ __global__ void __launch_bounds__(32) k_plate_final(const double* __restrict__ p
 }
 
 // Max |divergence| of the dense refined faces (outward flux sum / volume).
+// Blocks stride over dense rows (j, k), threads over x.
 template <typename P>
 __global__ void __launch_bounds__(kRedThreads) k_maxdiv(Grid<P> g, const P* __restrict__ Us,
                                                         const P* __restrict__ Vs, const P* __restrict__ Ws,
                                                         double* __restrict__ partials)
 {
     const size_t plane = (size_t)g.Nx * g.Ny;
-    const size_t n = plane * g.Nz;
+    const int rows = g.Ny * g.Nz;
     double v[1] = {0.0};
-    for (size_t m = (size_t)blockIdx.x * blockDim.x + threadIdx.x; m < n; m += (size_t)gridDim.x * blockDim.x) {
-        const int i = (int)(m % g.Nx), j = (int)((m / g.Nx) % g.Ny), k = (int)(m / plane);
-        const int fe = g.walls ? i + 1 : (i + 1 == g.Nx ? 0 : i + 1);
+    for (int row = blockIdx.x; row < rows; row += gridDim.x) {
+        const int k = row / g.Ny, j = row - k * g.Ny;
         const int fn = g.walls ? j + 1 : (j + 1 == g.Ny ? 0 : j + 1);
-        const size_t ur = ((size_t)k * g.Ny + j) * g.ufx;
-        const double d = ((double)Us[ur + fe] - (double)Us[ur + i]) * (double)g.inv_dx
-                       + ((double)Vs[((size_t)k * g.vfy + fn) * g.Nx + i] - (double)Vs[((size_t)k * g.vfy + j) * g.Nx + i]) * (double)g.inv_dy
-                       + ((double)Ws[m + plane] - (double)Ws[m]) * (double)g.inv_dz[k];
-        v[0] = fmax(v[0], fabs(d));
+        const P* ur = Us + ((size_t)k * g.Ny + j) * g.ufx;
+        const P* vs = Vs + ((size_t)k * g.vfy + j) * g.Nx;
+        const P* vn = Vs + ((size_t)k * g.vfy + fn) * g.Nx;
+        const P* wb = Ws + (size_t)row * g.Nx;
+        const P* wt = wb + plane;
+        const double idz = (double)g.inv_dz[k];
+        for (int i = threadIdx.x; i < g.Nx; i += blockDim.x) {
+            const int fe = g.walls ? i + 1 : (i + 1 == g.Nx ? 0 : i + 1);
+            const double d = ((double)ur[fe] - (double)ur[i]) * (double)g.inv_dx +
+                             ((double)vn[i] - (double)vs[i]) * (double)g.inv_dy + ((double)wt[i] - (double)wb[i]) * idz;
+            v[0] = fmax(v[0], fabs(d));
+        }
     }
     block_reduce_store<1, true>(v, partials + blockIdx.x);
 }
 
-// CFL rate max(|u|)/dx + max(|v|)/dy + max(|w|)/dz over the cell's faces.
+// CFL rate max(|u|)/dx + max(|v|)/dy + max(|w|)/dz over the cell's faces, in
+// precision P (|.| and max are exact; the rate is one sum of three products).
 template <typename P>
 __global__ void __launch_bounds__(kRedThreads) k_cfl(Grid<P> g, const P* __restrict__ Us,
                                                      const P* __restrict__ Vs, const P* __restrict__ Ws,
                                                      double* __restrict__ partials)
 {
     const size_t plane = (size_t)g.Nx * g.Ny;
-    const size_t n = plane * g.Nz;
-    double v[1] = {0.0};
-    for (size_t m = (size_t)blockIdx.x * blockDim.x + threadIdx.x; m < n; m += (size_t)gridDim.x * blockDim.x) {
-        const int i = (int)(m % g.Nx), j = (int)((m / g.Nx) % g.Ny), k = (int)(m / plane);
-        const int fe = g.walls ? i + 1 : (i + 1 == g.Nx ? 0 : i + 1);
+    const int rows = g.Ny * g.Nz;
+    P m = 0;
+    for (int row = blockIdx.x; row < rows; row += gridDim.x) {
+        const int k = row / g.Ny, j = row - k * g.Ny;
         const int fn = g.walls ? j + 1 : (j + 1 == g.Ny ? 0 : j + 1);
-        const size_t ur = ((size_t)k * g.Ny + j) * g.ufx;
-        const double u = fmax(fabs((double)Us[ur + i]), fabs((double)Us[ur + fe]));
-        const double vv = fmax(fabs((double)Vs[((size_t)k * g.vfy + j) * g.Nx + i]),
-                               fabs((double)Vs[((size_t)k * g.vfy + fn) * g.Nx + i]));
-        const double w = fmax(fabs((double)Ws[m]), fabs((double)Ws[m + plane]));
-        const double r = u / (double)g.dx + vv / (double)g.dy + w / (double)g.dz[k];
-        v[0] = fmax(v[0], r);
+        const P* ur = Us + ((size_t)k * g.Ny + j) * g.ufx;
+        const P* vs = Vs + ((size_t)k * g.vfy + j) * g.Nx;
+        const P* vn = Vs + ((size_t)k * g.vfy + fn) * g.Nx;
+        const P* wb = Ws + (size_t)row * g.Nx;
+        const P* wt = wb + plane;
+        const P idz = g.inv_dz[k];
+        for (int i = threadIdx.x; i < g.Nx; i += blockDim.x) {
+            const int fe = g.walls ? i + 1 : (i + 1 == g.Nx ? 0 : i + 1);
+            const P u = fmax(fabs(ur[i]), fabs(ur[fe]));
+            const P vv = fmax(fabs(vs[i]), fabs(vn[i]));
+            const P w = fmax(fabs(wb[i]), fabs(wt[i]));
+            m = fmax(m, u * g.inv_dx + vv * g.inv_dy + w * idz);
+        }
     }
+    double v[1] = {(double)m};
     block_reduce_store<1, true>(v, partials + blockIdx.x);
 }
 

@@ -96,7 +96,9 @@ __device__ __forceinline__ float rsplit(const float (&r)[3], float c0, float c1,
 // MT: the velocity is A + alpha (B - A) between the intermediates of two
 // coarse time levels (temporal refinement; the refinement is linear, so
 // interpolating the intermediates interpolates the dense velocity).
-template <int M, bool DIVONLY, bool LF, bool MT>
+// KIND 0: the step; 1: max |divergence| of the dense velocity; 2: max CFL
+// rate |u|/dx + |v|/dy + |w|/dz (the last two read no scalar).
+template <int M, int KIND, bool LF, bool MT>
 __global__ void __launch_bounds__(kThreadsAll, 2)
 k_xfused(const __grid_constant__ CUtensorMap tmn, const __grid_constant__ CUtensorMap tmm,
          const __grid_constant__ CUtensorMap twy, const __grid_constant__ CUtensorMap tuo,
@@ -106,6 +108,7 @@ k_xfused(const __grid_constant__ CUtensorMap tmn, const __grid_constant__ CUtens
 {
     using L = XT<M, MT>;
     constexpr int NB = L::NB, BXC = L::BXC, NC = 4 / M, NW = kThreads / 32;
+    constexpr bool DIVONLY = KIND != 0;
     extern __shared__ __align__(128) float sm[];
     float* red = sm + L::oRed;
     uint64_t* full = reinterpret_cast<uint64_t*>(sm) + L::oBar;
@@ -272,7 +275,10 @@ k_xfused(const __grid_constant__ CUtensorMap tmn, const __grid_constant__ CUtens
             if (DIVONLY) {
 #pragma unroll
                 for (int a = 0; a < 4; ++a) {
-                    const float d = 2.f * ((us[a + 1] - us[a]) + (vn[a] - vs[a])) + (wt[a] - wb[a]) * inv_dz;
+                    // us, vs, vn hold U/(2 dx), V/(2 dy)
+                    const float d = KIND == 2 ? 2.f * (fmaxf(fabsf(us[a]), fabsf(us[a + 1])) + fmaxf(fabsf(vs[a]), fabsf(vn[a]))) +
+                                                    fmaxf(fabsf(wb[a]), fabsf(wt[a])) * inv_dz
+                                              : 2.f * ((us[a + 1] - us[a]) + (vn[a] - vs[a])) + (wt[a] - wb[a]) * inv_dz;
                     dmax = fmaxf(dmax, fabsf(d));
                 }
             } else {
@@ -501,14 +507,15 @@ struct XSet {
     const float *wy, *uo, *vr;
 };
 
-template <int M, bool DIVONLY, bool LF, bool MT>
+template <int M, int KIND, bool LF, bool MT>
 cudaError_t launch_x(const Grid<float>& g, XSet v0, XSet v1, float alpha, int nxg, const float* lc,
                      const float* rx12, const float* Tm1, const float* T, float* Tp1, StepCoef c, int* err,
                      unsigned long long* divmax, cudaStream_t st)
 {
     using L = XT<M, MT>;
     static unsigned long long attr = 0;                   // one bit per device
-    cudaError_t e = smem_optin(reinterpret_cast<const void*>(k_xfused<M, DIVONLY, LF, MT>), (int)L::bytes, &attr);
+    constexpr bool DIVONLY = KIND != 0;
+    cudaError_t e = smem_optin(reinterpret_cast<const void*>(k_xfused<M, KIND, LF, MT>), (int)L::bytes, &attr);
     if (e != cudaSuccess) return e;
     CUtensorMap mn, mm, mwy, muo, mvr, mlc, mwy1, muo1, mvr1;
     memset(&mn, 0, sizeof mn);
@@ -539,7 +546,7 @@ cudaError_t launch_x(const Grid<float>& g, XSet v0, XSet v1, float alpha, int nx
     XArgs A{g, T, Tm1, Tp1, lc, (float)c.a, (float)c.b, (float)c.gdt, kcl, err, divmax, {}, alpha};
     memcpy(A.rx, rx12, sizeof A.rx);
     dim3 grid(chunks, g.Nx / kTX, g.Ny / kTY);
-    k_xfused<M, DIVONLY, LF, MT><<<grid, kThreadsAll, L::bytes, st>>>(mn, mm, mwy, muo, mvr, mlc, mwy1, muo1, mvr1, A);
+    k_xfused<M, KIND, LF, MT><<<grid, kThreadsAll, L::bytes, st>>>(mn, mm, mwy, muo, mvr, mlc, mwy1, muo1, mvr1, A);
     return cudaGetLastError();
 }
 
@@ -550,11 +557,11 @@ cudaError_t launch_step_m(const Grid<float>& g, XSet v0, const XSet* v1, float a
 {
     const bool lf = (c.a == 1.0 && c.b == 0.0);
     if (v1) {
-        return lf ? launch_x<M, false, true, true>(g, v0, *v1, alpha, nxg, lc, rx12, Tm1, T, Tp1, c, err, nullptr, st)
-                  : launch_x<M, false, false, true>(g, v0, *v1, alpha, nxg, lc, rx12, Tm1, T, Tp1, c, err, nullptr, st);
+        return lf ? launch_x<M, 0, true, true>(g, v0, *v1, alpha, nxg, lc, rx12, Tm1, T, Tp1, c, err, nullptr, st)
+                  : launch_x<M, 0, false, true>(g, v0, *v1, alpha, nxg, lc, rx12, Tm1, T, Tp1, c, err, nullptr, st);
     }
-    return lf ? launch_x<M, false, true, false>(g, v0, v0, 0.f, nxg, lc, rx12, Tm1, T, Tp1, c, err, nullptr, st)
-              : launch_x<M, false, false, false>(g, v0, v0, 0.f, nxg, lc, rx12, Tm1, T, Tp1, c, err, nullptr, st);
+    return lf ? launch_x<M, 0, true, false>(g, v0, v0, 0.f, nxg, lc, rx12, Tm1, T, Tp1, c, err, nullptr, st)
+              : launch_x<M, 0, false, false>(g, v0, v0, 0.f, nxg, lc, rx12, Tm1, T, Tp1, c, err, nullptr, st);
 }
 
 }  // namespace
@@ -587,8 +594,11 @@ cudaError_t launch_step_xfused_f32(const Grid<float>& g, const float* const setA
     return launch_step_m<2>(g, v0, pv1, (float)alpha, nxg, lc, rx12, Tm1, T, Tp1, c, err, st);
 }
 
-cudaError_t launch_maxdiv_xfused_f32(const Grid<float>& g, const float* WY, const float* UO, const float* VR, int nxg,
-                                     const float* lc, const float* rx12, double* partials, int blocks, cudaStream_t st)
+// kind 1: max |divergence|, kind 2: max CFL rate, as a double in partials[0]
+// (the other blocks - 1 partials are zeroed).
+cudaError_t launch_xfused_max_f32(const Grid<float>& g, int kind, const float* WY, const float* UO, const float* VR,
+                                  int nxg, const float* lc, const float* rx12, double* partials, int blocks,
+                                  cudaStream_t st)
 {
     int* err = fused_error_flag();
     if (!err) return cudaErrorMemoryAllocation;
@@ -598,8 +608,10 @@ cudaError_t launch_maxdiv_xfused_f32(const Grid<float>& g, const float* WY, cons
     StepCoef c{0, 0, 0};
     const XSet v{WY, UO, VR};
     if (g.mx == 4)
-        return launch_x<4, true, false, false>(g, v, v, 0.f, nxg, lc, rx12, nullptr, nullptr, nullptr, c, err, dm, st);
-    return launch_x<2, true, false, false>(g, v, v, 0.f, nxg, lc, rx12, nullptr, nullptr, nullptr, c, err, dm, st);
+        return kind == 2 ? launch_x<4, 2, false, false>(g, v, v, 0.f, nxg, lc, rx12, nullptr, nullptr, nullptr, c, err, dm, st)
+                         : launch_x<4, 1, false, false>(g, v, v, 0.f, nxg, lc, rx12, nullptr, nullptr, nullptr, c, err, dm, st);
+    return kind == 2 ? launch_x<2, 2, false, false>(g, v, v, 0.f, nxg, lc, rx12, nullptr, nullptr, nullptr, c, err, dm, st)
+                     : launch_x<2, 1, false, false>(g, v, v, 0.f, nxg, lc, rx12, nullptr, nullptr, nullptr, c, err, dm, st);
 }
 
 // Per-layer constants of the split-x kernel, [Nz][12] floats, all folded on
