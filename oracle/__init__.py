@@ -50,6 +50,7 @@ class _Cfg(ctypes.Structure):
         ("gamma", ctypes.c_double), ("kappa", ctypes.c_double), ("dt", ctypes.c_double),
         ("np_average", ctypes.c_int32), ("plates_dirichlet", ctypes.c_int32),
         ("walls_xy", ctypes.c_int32), ("implicit_z", ctypes.c_int32),
+        ("face_order", ctypes.c_int32),
     ]
 
 
@@ -71,6 +72,7 @@ class Config:
     plates_dirichlet: int = 1
     walls_xy: int = 0
     implicit_z: int = 0
+    face_order: int = 2
 
     @property
     def dense(self):
@@ -90,7 +92,7 @@ class Config:
     def _c(self):
         return _Cfg(self.nx, self.ny, self.nz, self.mx, self.my, self.mz, self.lx, self.ly,
                     self.gamma, self.kappa, self.dt, self.np_average, self.plates_dirichlet,
-                    self.walls_xy, self.implicit_z)
+                    self.walls_xy, self.implicit_z, self.face_order)
 
 
 def _load():
@@ -103,6 +105,7 @@ def _load():
         sig = {
             "or_zfaces": (ctypes.c_int, [i32, d, dp]),
             "or_rmatrix": (ctypes.c_int, [i32, i32, dp, dp, i32, d, dp, ip]),
+            "or_face4_weights": (ctypes.c_int, [i32, dp, i32, d, dp]),
             "or_refine": (ctypes.c_int, [cp, dp, dp, dp, dp, dp, dp]),
             "or_refine_adjoint": (ctypes.c_int, [cp, dp, dp, dp, dp, dp, dp]),
             "or_step": (ctypes.c_int, [cp, dp, dp, dp, dp, dp, i64, dp]),
@@ -164,6 +167,14 @@ def grid(cfg: Config) -> dict:
         "zc": 0.5 * (zf[1:] + zf[:-1]), "dz": np.diff(zf),
         "xc": 0.5 * (xf[1:] + xf[:-1]), "yc": 0.5 * (yf[1:] + yf[:-1]),
     }
+
+
+def face4_weights(N: int, X, periodic: bool, length: float = 1.0) -> np.ndarray:
+    """Fourth-order face-value weights (Section 2.2): [N+1][4], cells f-2..f+1."""
+    X = np.ascontiguousarray(X, dtype=np.float64)
+    w = np.empty((N + 1, 4))
+    _check(_load().or_face4_weights(N, _p(X), int(periodic), length, _p(w)), "face4_weights")
+    return w
 
 
 def rmatrix(n: int, m: int, Xc, Xd, periodic: bool, length: float = 1.0):

@@ -17,7 +17,12 @@
  *  - The 3-D stepwise refinement runs z (top-down slab balance), then y
  *    (south-to-north row balance), then x (west-to-east cell balance); the
  *    garbled 2-D balance formula of Section 3.2 is read as plain flux balance.
- *  - Second-order face values: linear interpolation between cell centres.
+ *  - Face values of the advected scalar: linear interpolation between cell
+ *    centres (second order), or, with face_order 4, the fourth-order
+ *    reconstruction of Section 2.2 read as: the cubic whose averages over the
+ *    four cells f-2..f+1 equal their values, evaluated at face f; next to a
+ *    wall the three cells on the domain side (quadratic).  Diffusive fluxes
+ *    stay two-point in both cases.
  *  - The leapfrog starts with one forward-Euler step; the averaging step is
  *    taken when (s+1) mod N_p == 0, with D kept at level n-1.
  */
@@ -40,6 +45,7 @@ typedef struct {
     double *zf, *zc, *dz;  /* dense z faces (Nz+1), centres (Nz), widths (Nz)   */
     double *Rx, *Ry, *Rz;  /* [n][m][3]                                         */
     int32_t *wx, *wy, *wz; /* [n][3] window cells                               */
+    double *f4x, *f4y, *f4z; /* face_order 4: [N+1][4] weights of cells f-2..f+1 */
 } geom;
 
 static void geom_free(geom* g)
@@ -47,6 +53,7 @@ static void geom_free(geom* g)
     free(g->zf); free(g->zc); free(g->dz);
     free(g->Rx); free(g->Ry); free(g->Rz);
     free(g->wx); free(g->wy); free(g->wz);
+    free(g->f4x); free(g->f4y); free(g->f4z);
     memset(g, 0, sizeof(*g));
 }
 
@@ -65,6 +72,69 @@ int or_zfaces(int32_t N, double gamma, double* zf)
 
 /* Mean of s^0, s^1, s^2 over [a, b]: one row of the paper's matrix A (or A_s),
  * i.e. (1/(b-a)) * integral of x^(n-1) dx, Section 3.2. */
+/* Fourth-order face values (Section 2.2).  For face f the stencil cells c
+ * (lo..lo+n-1) define the polynomial p of degree n-1 with
+ *   (1/h_c) int_c p = T_c,
+ * in the coordinate t = (x - X_f) / h_f; the face value is p(0) = a_0, a linear
+ * form sum_c w_c T_c with w the first row of A^-1, A[c][q] = mean of t^q over
+ * cell c.  Solved as A^T w = e_0 by Gaussian elimination with pivoting. */
+static int face_weights_one(int n, const double* lo, const double* hi, double* w)
+{
+    double M[4][5];
+    for (int q = 0; q < n; ++q) {          /* row q of A^T: means of t^q over each cell */
+        for (int c = 0; c < n; ++c) {
+            double a = lo[c], b = hi[c];
+            M[q][c] = (pow(b, q + 1) - pow(a, q + 1)) / ((q + 1) * (b - a));
+        }
+        M[q][n] = (q == 0) ? 1.0 : 0.0;
+    }
+    for (int col = 0; col < n; ++col) {
+        int piv = col;
+        for (int r = col + 1; r < n; ++r)
+            if (fabs(M[r][col]) > fabs(M[piv][col])) piv = r;
+        if (M[piv][col] == 0.0) return -1;
+        for (int k = 0; k <= n; ++k) { double t = M[col][k]; M[col][k] = M[piv][k]; M[piv][k] = t; }
+        for (int r = col + 1; r < n; ++r) {
+            double f = M[r][col] / M[col][col];
+            for (int k = col; k <= n; ++k) M[r][k] -= f * M[col][k];
+        }
+    }
+    for (int r = n - 1; r >= 0; --r) {
+        double v = M[r][n];
+        for (int k = r + 1; k < n; ++k) v -= M[r][k] * w[k];
+        w[r] = v / M[r][r];
+    }
+    return 0;
+}
+
+int or_face4_weights(int32_t N, const double* X, int32_t periodic, double length, double* w)
+{
+    memset(w, 0, sizeof(double) * 4 * (N + 1));
+    if (N < (periodic ? 4 : 3)) return -1;
+    for (int f = 0; f <= N; ++f) {
+        int first, n;
+        if (periodic) { if (f == N) continue; first = f - 2; n = 4; }
+        else if (f == 0 || f == N) continue;
+        else if (f == 1) { first = 0; n = 3; }
+        else if (f == N - 1) { first = N - 3; n = 3; }
+        else { first = f - 2; n = 4; }
+        double lo[4], hi[4], cw[4];
+        const double h = X[f + 1 <= N ? f + 1 : f] - X[f > 0 ? f - 1 : f];   /* a local length scale */
+        for (int c = 0; c < n; ++c) {
+            int cell = first + c;
+            double shift = 0.0;                      /* unwrap periodic cells */
+            if (cell < 0) { cell += N; shift = -length; }
+            if (cell >= N) { cell -= N; shift = length; }
+            lo[c] = (X[cell] + shift - X[f]) / h;
+            hi[c] = (X[cell + 1] + shift - X[f]) / h;
+        }
+        if (face_weights_one(n, lo, hi, cw)) return -1;
+        for (int c = 0; c < n; ++c) w[4 * f + (first + c) - (f - 2)] = cw[c];
+    }
+    if (periodic) memcpy(w + 4 * N, w, 4 * sizeof(double));
+    return 0;
+}
+
 static void monomial_means(double a, double b, double row[3])
 {
     row[0] = 1.0;
@@ -181,6 +251,16 @@ static int geom_init(const or_cfg* c, geom* g)
     rc |= or_rmatrix(c->nx, c->mx, xc, xd, periodic, c->lx, g->Rx, g->wx);
     rc |= or_rmatrix(c->ny, c->my, yc, yd, periodic, c->ly, g->Ry, g->wy);
     rc |= or_rmatrix(c->nz, c->mz, zcf, g->zf, 0, 1.0, g->Rz, g->wz);
+    if (c->face_order == 4) {
+        g->f4x = malloc(sizeof(double) * 4 * (g->Nx + 1));
+        g->f4y = malloc(sizeof(double) * 4 * (g->Ny + 1));
+        g->f4z = malloc(sizeof(double) * 4 * (g->Nz + 1));
+        rc |= or_face4_weights(g->Nx, xd, periodic, c->lx, g->f4x);
+        rc |= or_face4_weights(g->Ny, yd, periodic, c->ly, g->f4y);
+        rc |= or_face4_weights(g->Nz, g->zf, 0, 1.0, g->f4z);
+    } else if (c->face_order != 2) {
+        rc = -1;
+    }
     free(xd); free(xc); free(yd); free(yc); free(zcf);
     if (rc) { geom_free(g); return -1; }
     return 0;
@@ -516,6 +596,22 @@ int or_refine_adjoint(const or_cfg* c, const double* gUs, const double* gVs,
 #define T_BOTTOM  0.5
 #define T_TOP    -0.5
 
+/* Fourth-order value at face f of one axis: cells f-2 .. f+1 along the axis,
+ * starting at T[base] with the given stride; periodic cells wrap, cells
+ * outside a walled axis carry zero weight and are not read. */
+static double face4(const double* w, int f, int N, int periodic, const double* T, size_t base, size_t stride)
+{
+    double s = 0.0;
+    for (int q = 0; q < 4; ++q) {
+        double wq = w[4 * f + q];
+        if (wq == 0.0) continue;
+        int cell = f - 2 + q;
+        if (periodic) cell = ((cell % N) + N) % N;
+        s += wq * T[base + (size_t)cell * stride];
+    }
+    return s;
+}
+
 /* Per cell: rC = advection of Tc, rDh / rDz = horizontal / vertical diffusion
  * of Td (outward flux sums over the six faces divided by the cell volume).
  * Fluxes are positive in the +axis direction: P = u T_f A, G = kappa A dT/dn. */
@@ -524,12 +620,13 @@ static void rhs_fields(const or_cfg* c, const geom* g, const double* Us, const d
                        double* rC, double* rDh, double* rDz)
 {
     const int Nx = g->Nx, Ny = g->Ny, Nz = g->Nz;
-    const int walls = c->walls_xy, dir = c->plates_dirichlet;
+    const int walls = c->walls_xy, dir = c->plates_dirichlet, o4 = c->face_order == 4;
     const double kap = c->kappa, dx = g->dx, dy = g->dy;
     #pragma omp parallel for schedule(static)
     for (int k = 0; k < Nz; ++k)
         for (int j = 0; j < Ny; ++j)
             for (int i = 0; i < Nx; ++i) {
+                const size_t xrow = IDX_C(g, k, j, 0), ycol = IDX_C(g, k, 0, i), zcol = IDX_C(g, 0, j, i);
                 const size_t m = IDX_C(g, k, j, i);
                 const double dzk = g->dz[k], vol = dx * dy * dzk;
                 double Pw = 0, Pe = 0, Ps = 0, Pn = 0, Pb = 0, Pt = 0;
@@ -539,14 +636,16 @@ static void rhs_fields(const or_cfg* c, const geom* g, const double* Us, const d
                 if (!(walls && i == 0)) {
                     int iw = walls ? i - 1 : (i - 1 + Nx) % Nx;
                     size_t mw = IDX_C(g, k, j, iw);
-                    Pw = Us[IDX_U(g, k, j, i)] * 0.5 * (Tc[mw] + Tc[m]) * Ax;
+                    double Tf = o4 ? face4(g->f4x, i, Nx, !walls, Tc, xrow, 1) : 0.5 * (Tc[mw] + Tc[m]);
+                    Pw = Us[IDX_U(g, k, j, i)] * Tf * Ax;
                     Gw = kap * Ax * (Td[m] - Td[mw]) / dx;
                 }
                 if (!(walls && i == Nx - 1)) {
                     int ie = (i + 1) % Nx;
                     int fe = walls ? i + 1 : ie;
                     size_t me = IDX_C(g, k, j, ie);
-                    Pe = Us[IDX_U(g, k, j, fe)] * 0.5 * (Tc[m] + Tc[me]) * Ax;
+                    double Tf = o4 ? face4(g->f4x, i + 1, Nx, !walls, Tc, xrow, 1) : 0.5 * (Tc[m] + Tc[me]);
+                    Pe = Us[IDX_U(g, k, j, fe)] * Tf * Ax;
                     Ge = kap * Ax * (Td[me] - Td[m]) / dx;
                 }
                 /* y faces */
@@ -554,14 +653,16 @@ static void rhs_fields(const or_cfg* c, const geom* g, const double* Us, const d
                 if (!(walls && j == 0)) {
                     int js = walls ? j - 1 : (j - 1 + Ny) % Ny;
                     size_t ms = IDX_C(g, k, js, i);
-                    Ps = Vs[IDX_V(g, k, j, i)] * 0.5 * (Tc[ms] + Tc[m]) * Ay;
+                    double Tf = o4 ? face4(g->f4y, j, Ny, !walls, Tc, ycol, Nx) : 0.5 * (Tc[ms] + Tc[m]);
+                    Ps = Vs[IDX_V(g, k, j, i)] * Tf * Ay;
                     Gs = kap * Ay * (Td[m] - Td[ms]) / dy;
                 }
                 if (!(walls && j == Ny - 1)) {
                     int jn = (j + 1) % Ny;
                     int fn = walls ? j + 1 : jn;
                     size_t mn = IDX_C(g, k, jn, i);
-                    Pn = Vs[IDX_V(g, k, fn, i)] * 0.5 * (Tc[m] + Tc[mn]) * Ay;
+                    double Tf = o4 ? face4(g->f4y, j + 1, Ny, !walls, Tc, ycol, Nx) : 0.5 * (Tc[m] + Tc[mn]);
+                    Pn = Vs[IDX_V(g, k, fn, i)] * Tf * Ay;
                     Gn = kap * Ay * (Td[mn] - Td[m]) / dy;
                 }
                 /* z faces: linear interpolation between the two cell centres */
@@ -570,7 +671,8 @@ static void rhs_fields(const or_cfg* c, const geom* g, const double* Us, const d
                     if (dir) Gb = kap * Az * (Td[m] - T_BOTTOM) / (g->zc[0] - g->zf[0]);
                 } else {
                     size_t mb = IDX_C(g, k - 1, j, i);
-                    double Tf = (g->dz[k] * Tc[mb] + g->dz[k - 1] * Tc[m]) / (g->dz[k - 1] + g->dz[k]);
+                    double Tf = o4 ? face4(g->f4z, k, Nz, 0, Tc, zcol, (size_t)Nx * Ny)
+                                   : (g->dz[k] * Tc[mb] + g->dz[k - 1] * Tc[m]) / (g->dz[k - 1] + g->dz[k]);
                     Pb = Ws[IDX_W(g, k, j, i)] * Tf * Az;
                     Gb = kap * Az * (Td[m] - Td[mb]) / (g->zc[k] - g->zc[k - 1]);
                 }
@@ -578,7 +680,8 @@ static void rhs_fields(const or_cfg* c, const geom* g, const double* Us, const d
                     if (dir) Gt = kap * Az * (T_TOP - Td[m]) / (g->zf[Nz] - g->zc[Nz - 1]);
                 } else {
                     size_t mt = IDX_C(g, k + 1, j, i);
-                    double Tf = (g->dz[k + 1] * Tc[m] + g->dz[k] * Tc[mt]) / (g->dz[k] + g->dz[k + 1]);
+                    double Tf = o4 ? face4(g->f4z, k + 1, Nz, 0, Tc, zcol, (size_t)Nx * Ny)
+                                   : (g->dz[k + 1] * Tc[m] + g->dz[k] * Tc[mt]) / (g->dz[k] + g->dz[k + 1]);
                     Pt = Ws[IDX_W(g, k + 1, j, i)] * Tf * Az;
                     Gt = kap * Az * (Td[mt] - Td[m]) / (g->zc[k + 1] - g->zc[k]);
                 }
@@ -887,7 +990,7 @@ int or_adjoint(const or_cfg* c, const double* Us, const double* Vs, const double
                const double* T0, int64_t S, const double* wnu, const double* wvar,
                double* loss, double* gT0, double* gUs, double* gVs, double* gWs)
 {
-    if (c->implicit_z) return -4;       /* adjoint covers the explicit scheme */
+    if (c->implicit_z || c->face_order != 2) return -4;   /* adjoint of the explicit second-order scheme */
     geom G, *g = &G;
     if (geom_init(c, g)) return -1;
     const int Nx = g->Nx, Ny = g->Ny, Nz = g->Nz;
@@ -1017,7 +1120,9 @@ int or_nusselt_profile(const or_cfg* c, const double* T, const double* Ws, doubl
                 else if (k == Nz) s += (T[IDX_C(g, Nz - 1, j, i)] - T_TOP) / (g->zf[Nz] - g->zc[Nz - 1]);
                 else {
                     double Tl = T[IDX_C(g, k - 1, j, i)], Tr = T[IDX_C(g, k, j, i)];
-                    double Tf = (g->dz[k] * Tl + g->dz[k - 1] * Tr) / (g->dz[k - 1] + g->dz[k]);
+                    double Tf = c->face_order == 4
+                                    ? face4(g->f4z, k, Nz, 0, T, IDX_C(g, 0, j, i), (size_t)Nx * Ny)
+                                    : (g->dz[k] * Tl + g->dz[k - 1] * Tr) / (g->dz[k - 1] + g->dz[k]);
                     double grad = (Tr - Tl) / (g->zc[k] - g->zc[k - 1]);
                     s += Ws[IDX_W(g, k, j, i)] * Tf / c->kappa - grad;
                 }

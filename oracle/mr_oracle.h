@@ -29,7 +29,17 @@ typedef struct {
     int32_t plates_dirichlet; /* 1: T=+0.5 at z=0, -0.5 at z=1; 0: adiabatic    */
     int32_t walls_xy;         /* 0: periodic in x,y; 1: impermeable adiabatic   */
     int32_t implicit_z;       /* 1: vertical diffusion Crank-Nicolson (opt-in)  */
+    int32_t face_order;       /* 2: linear face values; 4: fourth-order face
+                                 values of the advected scalar (Section 2.2)    */
 } or_cfg;
+
+/* Fourth-order face value (Section 2.2) on one axis: weights w[f][0..3] of the
+ * cells f-2 .. f+1 for every face f = 0..N (periodic: face N is face 0), from
+ * the polynomial whose averages over the stencil cells equal the cell values,
+ * evaluated at the face.  Stencil: the four cells f-2..f+1; next to a wall
+ * (faces 1 and N-1) the three cells on the domain side, {0,1,2} or
+ * {N-3,N-2,N-1}; wall faces 0 and N get zero weights.  X: N+1 faces. */
+int  or_face4_weights(int32_t N, const double* X, int32_t periodic, double length, double* w);
 
 /* Grid (Section 3.1): dense faces first, coarse faces = every M-th dense face. */
 int  or_zfaces(int32_t nz_dense, double gamma, double* zf /* nz_dense+1 */);

@@ -604,3 +604,133 @@ def test_interpolated_velocity_is_divergence_free(oracle_mod, w):
     rc = O.refine(cfg, *(a + w * (b - a) for a, b in zip(c1, c2)))
     for x, y in zip(ri, rc):
         np.testing.assert_allclose(x, y, atol=1e-14)
+
+
+# ----------------------------------------------------------------------------- fourth-order face values (Section 2.2)
+
+def _cell_means_poly(coef, X):
+    """Exact averages of the polynomial sum coef[q] x^q over the cells of X."""
+    P = np.polynomial.polynomial.polyint(coef)
+    vals = np.polynomial.polynomial.polyval(X, P)
+    return np.diff(vals) / np.diff(X)
+
+
+@pytest.mark.parametrize("periodic", [False, True])
+def test_face4_weights_reproduce_polynomials(oracle_mod, periodic):
+    """The defining property of the reconstruction: from exact cell averages of
+    a cubic the four-cell stencils give the exact face value, on a stretched
+    axis; the three-cell stencils next to a wall are exact for quadratics."""
+    O = oracle_mod
+    N = 11
+    X = O.zfaces(N, 1.4) if not periodic else np.arange(N + 1) / N
+    w = O.face4_weights(N, X, periodic)
+    rng = np.random.default_rng(5)
+    for _ in range(4):
+        cub = rng.standard_normal(4)
+        abar = _cell_means_poly(cub, X)
+        for f in range(2, N - 1):                  # four-cell stencils clear of the ends
+            got = w[f] @ abar[f - 2:f + 2]
+            assert abs(got - np.polynomial.polynomial.polyval(X[f], cub)) < 1e-12
+        if not periodic:
+            quad = rng.standard_normal(3)
+            abar = _cell_means_poly(quad, X)
+            for f in (1, N - 1):
+                cells = np.arange(f - 2, f + 2)
+                ok = (cells >= 0) & (cells < N)
+                got = w[f][ok] @ abar[cells[ok]]
+                assert abs(got - np.polynomial.polynomial.polyval(X[f], quad)) < 1e-12
+            assert not w[0].any() and not w[N].any()     # wall faces carry no advective flux
+        else:
+            np.testing.assert_allclose(w, np.tile(w[0], (N + 1, 1)), atol=1e-14)   # uniform: one stencil
+
+
+def test_face4_uniform_stencil_is_the_textbook_one(oracle_mod):
+    """Uniform cells: (-1, 7, 7, -1)/12 in the interior and (1/3, 5/6, -1/6) at
+    the face next to a wall (the standard cell-average reconstructions)."""
+    O = oracle_mod
+    X = np.arange(9) / 8.0
+    w = O.face4_weights(8, X, True)
+    np.testing.assert_allclose(w[3], np.array([-1, 7, 7, -1]) / 12, atol=1e-14)
+    w = O.face4_weights(8, X, False)
+    np.testing.assert_allclose(w[1][1:], [1 / 3, 5 / 6, -1 / 6], atol=1e-14)
+    np.testing.assert_allclose(w[7][:3], [-1 / 6, 5 / 6, 1 / 3], atol=1e-14)
+
+
+def test_face4_advection_recovers_cubic_face_values(oracle_mod):
+    """The advective z fluxes of the step use the reconstruction: with W = 1 on
+    every inner z-face, the face values telescoped out of C(T) for T the cell
+    averages of a cubic in z are the cubic's values (four-cell faces) on a
+    stretched grid; a quadratic is recovered on every inner face."""
+    O = oracle_mod
+    cfg = _cfg(O, nx=4, ny=4, nz=4, mx=1, my=1, mz=3, gamma=1.5, face_order=4)
+    g = O.grid(cfg)
+    Nx, Ny, Nz = cfg.dense
+    zf, dz = g["zf"], g["dz"]
+    sh = cfg.shapes()
+    W = np.zeros(sh["Ws"])
+    W[1:-1] = 1.0
+    vel = (np.zeros(sh["Us"]), np.zeros(sh["Vs"]), W)
+    rng = np.random.default_rng(9)
+    for deg, faces in ((3, range(2, Nz - 1)), (2, range(1, Nz))):
+        coef = rng.standard_normal(deg + 1)
+        T = np.broadcast_to(_cell_means_poly(coef, zf)[:, None, None], (Nz, Ny, Nx)).copy()
+        rC, _ = O.rhs(cfg, vel, T, T)
+        c = rC[:, 0, 0]
+        # C_k dz_k = F_k - F_{k+1}, F_0 = 0: face values F_f (W = 1, unit area)
+        F = np.zeros(Nz + 1)
+        for k in range(Nz):
+            F[k + 1] = F[k] - c[k] * dz[k]
+        for f in faces:
+            assert abs(F[f] - np.polynomial.polynomial.polyval(zf[f], coef)) < 1e-12, (deg, f)
+
+
+@pytest.mark.parametrize("axis", ["x", "y"])
+@pytest.mark.parametrize("order,rate", [(2, 4.0), (4, 16.0)])
+def test_face_order_convergence_of_advection(oracle_mod, order, rate, axis):
+    """Uniform flow along a periodic axis over the cell averages of
+    sin(2 pi x / L): the exact rate of change of a cell average is
+    -U (T(x_e) - T(x_w)) / dx with point values at the faces.  Halving dx
+    divides the error by 4 (order 2) or 16 (order 4)."""
+    O = oracle_mod
+    errs = []
+    for n in (8, 16):
+        kw = dict(nx=n, ny=4, mx=2, my=1) if axis == "x" else dict(nx=4, ny=n, mx=1, my=2, ly=1.3)
+        cfg = _cfg(O, nz=3, mz=1, face_order=order, **kw)
+        g = O.grid(cfg)
+        Nx, Ny, Nz = cfg.dense
+        L = cfg.lx if axis == "x" else cfg.ly
+        xf = g["xf"] if axis == "x" else g["yf"]
+        abar = np.diff(-np.cos(2 * np.pi * xf / L) * L / (2 * np.pi)) / np.diff(xf)
+        sh = cfg.shapes()
+        if axis == "x":
+            T = np.broadcast_to(abar[None, None, :], (Nz, Ny, Nx)).copy()
+            vel = (np.full(sh["Us"], 0.7), np.zeros(sh["Vs"]), np.zeros(sh["Ws"]))
+        else:
+            T = np.broadcast_to(abar[None, :, None], (Nz, Ny, Nx)).copy()
+            vel = (np.zeros(sh["Us"]), np.full(sh["Vs"], 0.7), np.zeros(sh["Ws"]))
+        rC, _ = O.rhs(cfg, vel, T, T)
+        exact = -0.7 * np.diff(np.sin(2 * np.pi * xf / L)) / np.diff(xf)
+        got = rC[1, 1, :] if axis == "x" else rC[1, :, 1]
+        errs.append(np.abs(got - exact).max())
+    assert errs[0] / errs[1] == pytest.approx(rate, rel=0.08)
+
+
+@pytest.mark.parametrize("walls", [0, 1])
+def test_face4_scalar_integral_conserved(oracle_mod, walls):
+    """Flux form with fourth-order face values: sum T Vol is unchanged with
+    adiabatic plates (and walls), through the Euler start and averaging steps."""
+    O = oracle_mod
+    cfg = _cfg(O, nx=6, ny=5, nz=4, mx=2, my=2, mz=3, gamma=1.5, kappa=3e-3, dt=4e-3,
+               np_average=3, plates_dirichlet=0, walls_xy=walls, face_order=4)
+    vel = O.refine(cfg, *_velocity(O, cfg))
+    g = O.grid(cfg)
+    Nx, Ny, Nz = cfg.dense
+    T0 = synth.initial_scalar(7, g["zc"], Ny, Nx, noise=0.1)
+    vol = (cfg.lx / Nx) * (cfg.ly / Ny) * g["dz"][:, None, None]
+    I0 = float((T0 * vol).sum())
+    Tm1, T = T0, T0
+    for s in range(8):
+        Tm1, T = T, O.step(cfg, vel, Tm1, T, s)
+        assert abs(float((T * vol).sum()) - I0) < 1e-14
+    T2 = O.run(O.Config(**{**cfg.__dict__, "face_order": 2}), vel, T0, 8)[1]
+    assert np.abs(T - T2).max() > 1e-6                  # the order changes the result
