@@ -164,10 +164,10 @@ def _inputs(mr, h, w):
     return U, V, W, T0
 
 
-def _make(mr, w, precision, mode, dt=1e-3):
+def _make(mr, w, precision, mode, dt=1e-3, face_order=2):
     c = mr.mr_config_default(nx=w["nx"], ny=w["ny"], nz=w["nz"], mx=w["m"], my=w["m"], mz=w["m"],
                              stretch_gamma=w["gamma"], ra=w["ra"], pr_or_sc=w["pr"], dt=dt,
-                             precision=precision, velocity_mode=mode)
+                             precision=precision, velocity_mode=mode, face_order=face_order)
     return mr.mr_create(c)
 
 
@@ -243,6 +243,18 @@ def run_mr(args):
     if rank == 0 and not args.no_temporal:
         temporal = temporal_cost(torch, mr, h, w, (dU, dV, dW), cells, stream)
 
+    # the same step with the fourth-order face values of Section 2.2 (opt-in)
+    face4 = None
+    if rank == 0 and not args.no_face4 and mode != mr.MR_VEL_FUSED:
+        h4 = _make(mr, w, prec, mode, dt=dt, face_order=4)
+        mr.mr_refine_velocity(h4, dU, dV, dW, stream=stream)
+        mr.mr_set_scalar(h4, dT0, stream=stream)
+        k4 = max(20, args.steps // 5)
+        t4 = _time_steps(torch, mr, h4, k4, 3, stream)
+        face4 = {"value": round(cells * k4 / t4 / 1e9, 3), "unit": "Gcell-updates/s", "steps": k4,
+                 "ms_per_step": round(t4 / k4 * 1e3, 4)}
+        h4.close()
+
     # FP64 path on the same grid (stored velocity), for the FP32/FP64 ratio
     fp64 = None
     if rank == 0 and prec == mr.MR_F32 and not args.no_fp64:
@@ -299,7 +311,7 @@ def run_mr(args):
                        "velocity_mode": args.mode, "dt": dt, "parallelism": f"replicas{world}",
                        "l2": "inputs larger than L2 (3 scalar levels of %.0f MB)" % (cells * elt / 2**20),
             "bytes_per_cell": round(bytes_per_cell, 3)},
-            "roofline": roof, "fp64_path": fp64, "adjoint": adj, "temporal": temporal, "e2e": e2e,
+            "roofline": roof, "fp64_path": fp64, "adjoint": adj, "temporal": temporal, "face_order4": face4, "e2e": e2e,
             "cpu_baseline": cpu,
             "gpu_launches": args.steps, "clocks": clk.summary(),
             "final_stats": {k: st[k] for k in ("nu_bot", "nu_top", "mean", "var")},
@@ -446,6 +458,7 @@ def main():
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--no-temporal", action="store_true")
+    ap.add_argument("--no-face4", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -10,7 +10,8 @@
  *   - Section 3.2: the coarse face velocity is refined onto the dense faces by
  *     the mass-conserving third-order interpolation R = A_s A^-1 and the
  *     stepwise flux balance of the inner faces (divergence-free to round-off).
- *   - Eq. (2)/(5): second-order finite-volume advection-diffusion,
+ *   - Eq. (2)/(5): finite-volume advection-diffusion with second-order face
+ *     values (or, opt-in, the fourth-order face values of Section 2.2),
  *     kappa = (Ra Pr)^-1/2 (or Sc in place of Pr for a passive scalar).
  *   - Section 2.2: Euler-leapfrog time integration with the averaging step
  *     every N_p steps; the first step after mr_set_scalar is forward Euler.
@@ -89,6 +90,15 @@ typedef struct {
     int32_t diffz_implicit;   /* 0: explicit (the paper's scheme); 1: opt-in
                                  Crank-Nicolson for vertical diffusion with one
                                  tridiagonal solve per (x, y) column           */
+    int32_t face_order;       /* face values of the advected scalar: 2 (linear
+                                 between centres, default) or 4 (Section 2.2:
+                                 the cubic with the four nearest cell averages
+                                 along the face normal, evaluated at the face;
+                                 the three domain-side cells next to a wall).
+                                 Diffusive fluxes are two-point in both.  4 is
+                                 supported by MR_VEL_STORED and MR_VEL_XFUSED,
+                                 not by the adjoint; it needs >= 4 dense cells
+                                 on periodic axes and >= 3 between walls.     */
 } mr_config;
 
 typedef struct {
@@ -200,8 +210,8 @@ int mr_scalar_profiles(mr_handle h, double* nu_z, double* nu_T, mr_stream stream
  * sweeps the adjoint back to s = 0 and writes gscale * dL/dT^0 (dense, dtype
  * MR_F64 or MR_F32) and gscale * dL/dU, dL/dV, dL/dW (coarse, FP64, through
  * the transpose of the refinement of Section 3.2); any output may be NULL.
- * Pointers may be host or device.  Both synchronise.  Needs MR_VEL_STORED and
- * explicit diffusion (MR_ERR_ARG otherwise).  The time step is not
+ * Pointers may be host or device.  Both synchronise.  Needs MR_VEL_STORED,
+ * explicit diffusion and face_order 2 (MR_ERR_ARG otherwise).  The time step is not
  * differentiated.  After the backward the handle holds T^nsteps. */
 int mr_adjoint_forward(mr_handle h, int64_t nsteps, int32_t checkpoint_every, const double* wnu,
                        const double* wvar, double* loss, mr_stream stream);

@@ -140,10 +140,73 @@ static bool axis_r(int n, int m, const std::vector<double>& dense_faces, bool pe
     return true;
 }
 
+// Fourth-order face values (Section 2.2) along one axis of N cells with faces
+// X[0..N]: w[4 f + q] weighs cell f - 2 + q at face f.  The face value is the
+// derivative at X_f of the polynomial interpolating the primitive
+// P(X_m) = sum_{c < m} h_c T_c at the stencil's faces, which is the
+// polynomial whose cell averages over the stencil are the cell values:
+//   T_f = sum_c T_c h_c sum_{m > c} L_m'(X_f)
+// with L_m the Lagrange basis on the stencil faces.  Stencil: cells f-2..f+1;
+// next to a wall (faces 1, N-1) the three domain-side cells; wall faces none.
+static bool face4_axis(int N, const std::vector<double>& X, bool periodic, double length, std::vector<double>& w)
+{
+    w.assign(4 * ((size_t)N + 1), 0.0);
+    if (N < (periodic ? 4 : 3)) return false;
+    for (int f = 0; f <= N; ++f) {
+        int first, n;
+        if (periodic) {
+            first = f - 2;
+            n = 4;
+        } else if (f == 0 || f == N) {
+            continue;
+        } else if (f == 1 || f == N - 1) {
+            first = (f == 1) ? 0 : N - 3;
+            n = 3;
+        } else {
+            first = f - 2;
+            n = 4;
+        }
+        // stencil faces x_0..x_n relative to X_f, scaled by the stencil width
+        double x[5];
+        auto face = [&](int m) {            // unwrapped face m (may be < 0 or > N when periodic)
+            double off = 0.0;
+            while (m < 0) { m += N; off -= length; }
+            while (m > N) { m -= N; off += length; }
+            return X[m] + off;
+        };
+        const double xf = face(f), scale = face(first + n) - face(first);
+        for (int m = 0; m <= n; ++m) x[m] = (face(first + m) - xf) / scale;
+        const int t = f - first;            // the face is stencil node t
+        double dL[5];
+        for (int m = 0; m <= n; ++m) {
+            if (m == t) {
+                double sum = 0.0;
+                for (int j = 0; j <= n; ++j)
+                    if (j != t) sum += 1.0 / (x[t] - x[j]);
+                dL[m] = sum;
+            } else {
+                double num = 1.0, den = 1.0;
+                for (int j = 0; j <= n; ++j) {
+                    if (j != m) den *= x[m] - x[j];
+                    if (j != m && j != t) num *= x[t] - x[j];
+                }
+                dL[m] = num / den;
+            }
+        }
+        for (int c = 0; c < n; ++c) {
+            double tail = 0.0;
+            for (int m = c + 1; m <= n; ++m) tail += dL[m];
+            w[4 * (size_t)f + (first + c) - (f - 2)] = (x[c + 1] - x[c]) * tail;
+        }
+    }
+    return true;
+}
+
 template <typename P>
 static size_t metric_bytes(const mr_handle_s* h)
 {
-    const size_t nP = (size_t)h->Nz * 4 + 2 * ((size_t)h->Nz + 1) + 3 * ((size_t)h->Nx + h->Ny + h->Nz);
+    const size_t nP = (size_t)h->Nz * 4 + 2 * ((size_t)h->Nz + 1) + 3 * ((size_t)h->Nx + h->Ny + h->Nz) +
+                      4 * ((size_t)h->Nx + h->Ny + h->Nz + 3);
     return ((nP * sizeof(P) + 255) / 256) * 256;
 }
 
@@ -175,6 +238,7 @@ static int upload_metric(mr_handle_s* h, char* dst, const int* dwin, Grid<P>& g)
     }
     push(h->dz); push(inv_dz); push(wlo); push(whi); push(cdn); push(cup);
     push(h->Rx); push(h->Ry); push(h->Rz);
+    push(h->f4x); push(h->f4y); push(h->f4z);
     cudaError_t e = cudaMemcpy(dst, host.data(), host.size() * sizeof(P), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) return cuda_check(e, "upload metric");
     const P* base = (const P*)dst;
@@ -188,6 +252,8 @@ static int upload_metric(mr_handle_s* h, char* dst, const int* dwin, Grid<P>& g)
     g.kx2 = (P)(h->kappa / (dx * dx)); g.ky2 = (P)(h->kappa / (dy * dy));
     g.dz = base + off[0]; g.inv_dz = base + off[1]; g.wlo = base + off[2]; g.whi = base + off[3];
     g.cdn = base + off[4]; g.cup = base + off[5]; g.Rx = base + off[6]; g.Ry = base + off[7]; g.Rz = base + off[8];
+    g.f4x = base + off[9]; g.f4y = base + off[10]; g.f4z = base + off[11];
+    g.order4 = c.face_order == 4 ? 1 : 0;
     g.wx = dwin; g.wy = dwin + 3 * c.nx; g.wz = dwin + 3 * (c.nx + c.ny);
     return MR_OK;
 }
@@ -221,6 +287,16 @@ static int validate(const mr_config* c, std::string* why)
     if (c->bc_plates != MR_DIRICHLET && c->bc_plates != MR_ADIABATIC) { *why = "bad bc_plates"; return MR_ERR_ARG; }
     if (c->bc_horizontal != MR_PERIODIC && c->bc_horizontal != MR_WALLS) { *why = "bad bc_horizontal"; return MR_ERR_ARG; }
     if (c->diffz_implicit != 0 && c->diffz_implicit != 1) { *why = "diffz_implicit must be 0 or 1"; return MR_ERR_ARG; }
+    if (c->face_order != 2 && c->face_order != 4) { *why = "face_order must be 2 or 4"; return MR_ERR_ARG; }
+    if (c->face_order == 4) {
+        const bool per = c->bc_horizontal == MR_PERIODIC;
+        const int need = per ? 4 : 3;
+        if ((long long)c->nx * c->mx < need || (long long)c->ny * c->my < need || (long long)c->nz * c->mz < 3) {
+            *why = "face_order 4 needs >= 4 dense cells on periodic axes and >= 3 between walls";
+            return MR_ERR_ARG;
+        }
+        if (c->velocity_mode == MR_VEL_FUSED) { *why = "MR_VEL_FUSED supports face_order 2 only"; return MR_ERR_ARG; }
+    }
     if (c->velocity_mode != MR_VEL_STORED && !fused_supported(*c, why)) return MR_ERR_ARG;
     return MR_OK;
 }
@@ -253,6 +329,7 @@ int mr_config_default(mr_config* c)
     c->bc_plates = MR_DIRICHLET;
     c->bc_horizontal = MR_PERIODIC;
     c->diffz_implicit = 0;
+    c->face_order = 2;
     return MR_OK;
 }
 
@@ -332,6 +409,14 @@ int mr_create(const mr_config* cfg, mr_handle* out)
         delete h;
         return set_error(MR_ERR_ARG, "mr_create: singular interpolation matrix (degenerate grid)");
     }
+    h->f4x.assign(4 * ((size_t)h->Nx + 1), 0.0);
+    h->f4y.assign(4 * ((size_t)h->Ny + 1), 0.0);
+    h->f4z.assign(4 * ((size_t)h->Nz + 1), 0.0);
+    if (c.face_order == 4 && (!face4_axis(h->Nx, xf, per, c.lx, h->f4x) || !face4_axis(h->Ny, yf, per, c.ly, h->f4y) ||
+                              !face4_axis(h->Nz, h->zf, false, 1.0, h->f4z))) {
+        delete h;
+        return set_error(MR_ERR_ARG, "mr_create: fourth-order face stencil does not fit the grid");
+    }
 
     DeviceBuffers& b = h->buf;
     cudaError_t e = cudaSuccess;
@@ -370,7 +455,7 @@ int mr_create(const mr_config* cfg, mr_handle* out)
         alloc((void**)&b.xwy, (size_t)(h->Nz + 1) * h->Ny * b.nxg * 4);
         alloc((void**)&b.xuo, (size_t)h->Nz * h->Ny * b.nxg * 4);
         alloc((void**)&b.xvr, (size_t)h->Nz * (h->Ny + 1) * b.nxg * 4);
-        alloc((void**)&b.xlc, (size_t)h->Nz * 12 * 4);
+        alloc((void**)&b.xlc, (size_t)h->Nz * 20 * 4);
         alloc(&b.scrW, (size_t)(h->Nz + 1) * c.ny * c.nx * h->elt);
     }
     if (e != cudaSuccess) {
@@ -394,7 +479,13 @@ int mr_create(const mr_config* cfg, mr_handle* out)
     if (!rc && b.xlc) {
         const std::vector<float> lc =
             xfused_layer_constants(h->Nz, h->zf.data(), h->zc.data(), h->dz.data(), h->kappa, c.lx / h->Nx,
-                                   c.ly / h->Ny, c.bc_plates == MR_DIRICHLET);
+                                   c.ly / h->Ny, c.bc_plates == MR_DIRICHLET,
+                                   c.face_order == 4 ? h->f4z.data() : nullptr, &b.xlcw);
+        // periodic uniform x and y: every face has the same fourth-order weights
+        for (int q = 0; q < 4; ++q) {
+            b.xw4[q] = (float)(2.0 * h->f4x[q]);
+            b.xw4[4 + q] = (float)(2.0 * h->f4y[q]);
+        }
         rc = cuda_check(cudaMemcpy(b.xlc, lc.data(), lc.size() * 4, cudaMemcpyHostToDevice), "mr_create: layer constants");
         // x is uniform and periodic: every coarse cell has the same R_x rows
         for (int q = 0; q < 12; ++q) b.xrx[q] = (float)h->Rx[(size_t)(q / 3) * 3 + q % 3];
@@ -535,7 +626,8 @@ static int one_step(mr_handle h, double alpha, cudaStream_t st)
     } else if (h->cfg.velocity_mode == MR_VEL_XFUSED) {
         const float* A[3] = {b.xwy, b.xuo, b.xvr};
         const float* B[3] = {nx.xwy, nx.xuo, nx.xvr};
-        e = launch_step_xfused_f32(h->g32, A, lerp ? B : nullptr, alpha, b.nxg, b.xlc, b.xrx, (const float*)Tm1,
+        e = launch_step_xfused_f32(h->g32, A, lerp ? B : nullptr, alpha, b.nxg, b.xlc, b.xlcw, b.xrx, b.xw4,
+                                   (const float*)Tm1,
                                    (const float*)b.T[h->ic], (float*)b.T[in], c, st);
     } else if (h->cfg.velocity_mode == MR_VEL_FUSED) {
         const float *U = (const float*)b.Uc, *V = (const float*)b.Vc, *W = (const float*)b.Wc;
@@ -744,7 +836,7 @@ static int max_divergence(mr_handle h, double* out, cudaStream_t st)
     cudaError_t e;
     const DeviceBuffers& b = h->buf;
     if (h->cfg.velocity_mode == MR_VEL_XFUSED)
-        e = launch_xfused_max_f32(h->g32, 1, b.xwy, b.xuo, b.xvr, b.nxg, b.xlc, b.xrx, b.red, h->red_blocks, st);
+        e = launch_xfused_max_f32(h->g32, 1, b.xwy, b.xuo, b.xvr, b.nxg, b.xlc, b.xlcw, b.xrx, b.red, h->red_blocks, st);
     else if (h->cfg.velocity_mode == MR_VEL_FUSED)
         e = launch_maxdiv_fused_f32(h->g32, (const float*)b.Uc, (const float*)b.Vc, (const float*)b.Wc, b.red,
                                     h->red_blocks, st);
@@ -818,7 +910,7 @@ int mr_cfl_dt(mr_handle h, double cfl, double* dt_out, mr_stream stream)
     cudaError_t e = cudaSuccess;
     if (h->cfg.velocity_mode == MR_VEL_XFUSED) {
         // the split-x kernel forms the dense faces in registers: one pass, no dense storage
-        e = launch_xfused_max_f32(h->g32, 2, b.xwy, b.xuo, b.xvr, b.nxg, b.xlc, b.xrx, b.red, h->red_blocks, st);
+        e = launch_xfused_max_f32(h->g32, 2, b.xwy, b.xuo, b.xvr, b.nxg, b.xlc, b.xlcw, b.xrx, b.red, h->red_blocks, st);
     } else if (h->cfg.velocity_mode != MR_VEL_STORED) {
         // dense faces are not kept: refine into temporary buffers once
         void *a = nullptr, *bb = nullptr, *c = nullptr;
@@ -945,8 +1037,8 @@ int mr_adjoint_forward(mr_handle h, int64_t nsteps, int32_t ck, const double* wn
 {
     if (!h || !loss) return set_error(MR_ERR_ARG, "mr_adjoint_forward: NULL argument");
     if (nsteps < 1 || ck < 1) return set_error(MR_ERR_ARG, "mr_adjoint_forward: nsteps and checkpoint_every must be >= 1");
-    if (h->cfg.velocity_mode != MR_VEL_STORED || h->cfg.diffz_implicit)
-        return set_error(MR_ERR_ARG, "mr_adjoint_forward: needs MR_VEL_STORED and explicit diffusion");
+    if (h->cfg.velocity_mode != MR_VEL_STORED || h->cfg.diffz_implicit || h->cfg.face_order != 2)
+        return set_error(MR_ERR_ARG, "mr_adjoint_forward: needs MR_VEL_STORED, explicit diffusion and face_order 2");
     if (!h->have_velocity || !h->have_scalar || h->step != 0)
         return set_error(MR_ERR_STATE, "mr_adjoint_forward: call mr_refine_velocity and mr_set_scalar first");
     cudaStream_t st = (cudaStream_t)stream;

@@ -39,6 +39,10 @@ struct Grid {
     const int* wx;               // [nx][3] coarse cells of the R window
     const int* wy;               // [ny][3]
     const int* wz;               // [nz][3]
+    const P* f4x;                // [Nx+1][4] fourth-order face weights of cells f-2..f+1
+    const P* f4y;                // [Ny+1][4]
+    const P* f4z;                // [Nz+1][4]
+    int order4;                  // 1: fourth-order face values of the advected scalar
 };
 
 // Coefficients of one step: T^{s+1} = a T^{s-1} + b T^s + gdt [C(T^s) + D(T^{s-1})].
@@ -71,6 +75,8 @@ struct DeviceBuffers {
     float* xvr = nullptr;                      // [Nz][Ny+1][nxg]
     float* xlc = nullptr;                      // [Nz][12]
     float xrx[12] = {0};                       // R_x rows of the 4 cells of a 4-cell segment
+    float xw4[8] = {0};                        // fourth order: twice the x and y face weights (uniform)
+    int xlcw = 12;                             // row length of xlc
     double* diag = nullptr;                    // diagnostics: coarse T, Nu(z), dense z centres (lazy)
     int nxg = 0;
     // Temporal refinement (Section 3.4): the velocity of the next coarse time
@@ -99,6 +105,7 @@ struct mr_handle_s {
     bool have_velocity = false, have_scalar = false;
     // host FP64 grid (Section 3.1) and R matrices (Section 3.2)
     std::vector<double> zf, zc, dz, Rx, Ry, Rz;
+    std::vector<double> f4x, f4y, f4z;   // fourth-order face weights (zeros at face_order 2)
     std::vector<int> wx, wy, wz;
     mr::DeviceBuffers buf;
     mr::Grid<double> g64;
@@ -173,7 +180,7 @@ bool fused_supported(const mr_config& cfg, std::string* why);
 int* fused_error_flag();
 // per-layer constant table [Nz][12] of the split-x kernel (layout owned by mr_xfused.cu)
 std::vector<float> xfused_layer_constants(int Nz, const double* zf, const double* zc, const double* dz, double kappa,
-                                          double dx, double dy, bool dirichlet);
+                                          double dx, double dy, bool dirichlet, const double* f4z, int* lcw);
 // Raise a kernel's dynamic shared-memory limit once per device (*done: one bit per device).
 cudaError_t smem_optin(const void* kernel, int bytes, unsigned long long* done);
 template <typename P>
@@ -183,11 +190,11 @@ cudaError_t launch_xfused_prep(const Grid<float>& g, const float* U, const float
 // setA = {WY, UO, VR} of the current velocity; setB (or NULL) those of the next
 // coarse time level, interpolated with weight alpha (temporal refinement)
 cudaError_t launch_step_xfused_f32(const Grid<float>& g, const float* const setA[3], const float* const setB[3],
-                                   double alpha, int nxg, const float* lc, const float* rx12, const float* Tm1,
-                                   const float* T, float* Tp1, StepCoef c, cudaStream_t st);
+                                   double alpha, int nxg, const float* lc, int lcw, const float* rx12, const float* w4,
+                                   const float* Tm1, const float* T, float* Tp1, StepCoef c, cudaStream_t st);
 // kind 1: max |divergence| of the dense velocity, kind 2: max CFL rate (into partials[0])
 cudaError_t launch_xfused_max_f32(const Grid<float>& g, int kind, const float* WY, const float* UO, const float* VR,
-                                  int nxg, const float* lc, const float* rx12, double* partials, int blocks,
+                                  int nxg, const float* lc, int lcw, const float* rx12, double* partials, int blocks,
                                   cudaStream_t st);
 cudaError_t launch_refine_transpose(const Grid<double>& g, double* aUs, double* aVs, double* aWs, double* aWc,
                                     double* aVrow, double* gU, double* gV, double* gW, size_t ncU, size_t ncV,

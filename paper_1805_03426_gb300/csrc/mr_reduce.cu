@@ -197,7 +197,14 @@ __global__ void __launch_bounds__(256) k_nu_profile(Grid<P> g, const P* __restri
             v[0] += ((double)T[(size_t)(g.Nz - 1) * plane + m] + 0.5) / zt;
         } else {
             const double tl = (double)T[(size_t)(k - 1) * plane + m], tr = (double)T[(size_t)k * plane + m];
-            const double tf = (double)g.wlo[k] * tl + (double)g.whi[k] * tr;
+            double tf = (double)g.wlo[k] * tl + (double)g.whi[k] * tr;
+            if (g.order4) {                      // the step's fourth-order face value
+                tf = 0.0;
+                for (int q = 0; q < 4; ++q) {
+                    const int c = k - 2 + q;
+                    if (c >= 0 && c < g.Nz) tf += (double)g.f4z[4 * k + q] * (double)T[(size_t)c * plane + m];
+                }
+            }
             v[0] += (double)Ws[(size_t)k * plane + m] * tf * inv_kappa - (tr - tl) / (zc[k] - zc[k - 1]);
         }
     }

@@ -29,9 +29,28 @@ struct FaceVel {
     }
 };
 
+// Fourth-order value at face f of an axis of N cells (Section 2.2): the cells
+// f-2 .. f+1 at T[base + c * stride] with the grid's weights; periodic cells
+// wrap, cells beyond a wall carry zero weight and are not read.
+template <typename P>
+__device__ __forceinline__ P face4(const P* __restrict__ w, int f, int N, bool periodic, const P* __restrict__ T,
+                                   size_t base, size_t stride)
+{
+    P s = 0;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        int c = f - 2 + q;
+        if (periodic) c = c < 0 ? c + N : (c >= N ? c - N : c);
+        else if (c < 0 || c >= N) continue;
+        s += w[4 * f + q] * T[base + (size_t)c * stride];
+    }
+    return s;
+}
+
 // One thread per dense cell.  IMPLZ: vertical diffusion enters as
 // (D_z(T^{s-1}) + plate terms) / 2; the implicit half follows in k_zsolve.
-template <typename P, bool IMPLZ, bool LERP>
+// O4: fourth-order face values of the advected scalar.
+template <typename P, bool IMPLZ, bool LERP, bool O4>
 __global__ void __launch_bounds__(256) k_step_stored(Grid<P> g, const FaceVel<P, LERP> Us,
                                                      const FaceVel<P, LERP> Vs, const FaceVel<P, LERP> Ws,
                                                      const P* __restrict__ Tm1, const P* __restrict__ T,
@@ -51,42 +70,45 @@ __global__ void __launch_bounds__(256) k_step_stored(Grid<P> g, const FaceVel<P,
     if (!(g.walls && i == 0)) {
         const int iw = (i == 0) ? g.Nx - 1 : i - 1;
         const size_t mw = m - i + iw;
-        cx += Us[urow + i] * half * (T[mw] + Tc);
+        cx += Us[urow + i] * (O4 ? face4(g.f4x, i, g.Nx, !g.walls, T, m - i, 1) : half * (T[mw] + Tc));
         dx_ -= Dc - Tm1[mw];
     }
     if (!(g.walls && i == g.Nx - 1)) {
         const int ie = (i == g.Nx - 1) ? 0 : i + 1;
         const int fe = g.walls ? i + 1 : ie;
         const size_t me = m - i + ie;
-        cx -= Us[urow + fe] * half * (Tc + T[me]);
+        cx -= Us[urow + fe] * (O4 ? face4(g.f4x, i + 1, g.Nx, !g.walls, T, m - i, 1) : half * (Tc + T[me]));
         dx_ += Tm1[me] - Dc;
     }
     // y faces
     if (!(g.walls && j == 0)) {
         const int js = (j == 0) ? g.Ny - 1 : j - 1;
         const size_t ms = m + ((ptrdiff_t)js - j) * g.Nx;
-        cy += Vs[((size_t)k * g.vfy + j) * g.Nx + i] * half * (T[ms] + Tc);
+        cy += Vs[((size_t)k * g.vfy + j) * g.Nx + i] *
+              (O4 ? face4(g.f4y, j, g.Ny, !g.walls, T, m - (size_t)j * g.Nx, g.Nx) : half * (T[ms] + Tc));
         dy_ -= Dc - Tm1[ms];
     }
     if (!(g.walls && j == g.Ny - 1)) {
         const int jn = (j == g.Ny - 1) ? 0 : j + 1;
         const int fn = g.walls ? j + 1 : jn;
         const size_t mn = m + ((ptrdiff_t)jn - j) * g.Nx;
-        cy -= Vs[((size_t)k * g.vfy + fn) * g.Nx + i] * half * (Tc + T[mn]);
+        cy -= Vs[((size_t)k * g.vfy + fn) * g.Nx + i] *
+              (O4 ? face4(g.f4y, j + 1, g.Ny, !g.walls, T, m - (size_t)j * g.Nx, g.Nx) : half * (Tc + T[mn]));
         dy_ += Tm1[mn] - Dc;
     }
     // z faces (plates: no advective flux; Dirichlet or zero diffusive flux)
     P cz = 0, dz_ = 0;
     if (k > 0) {
         const P Tb = T[m - plane];
-        cz += Ws[m] * (g.wlo[k] * Tb + g.whi[k] * Tc);
+        cz += Ws[m] * (O4 ? face4(g.f4z, k, g.Nz, false, T, m - k * plane, plane) : g.wlo[k] * Tb + g.whi[k] * Tc);
         dz_ -= g.cdn[k] * (Dc - Tm1[m - plane]);
     } else {
         dz_ -= g.cdn[0] * (Dc - P(kTBottom));    // cdn[0] = 0 when adiabatic
     }
     if (k < g.Nz - 1) {
         const P Tt = T[m + plane];
-        cz -= Ws[m + plane] * (g.wlo[k + 1] * Tc + g.whi[k + 1] * Tt);
+        cz -= Ws[m + plane] *
+              (O4 ? face4(g.f4z, k + 1, g.Nz, false, T, m - k * plane, plane) : g.wlo[k + 1] * Tc + g.whi[k + 1] * Tt);
         dz_ += g.cup[k] * (Tm1[m + plane] - Dc);
     } else {
         dz_ += g.cup[k] * (P(kTTop) - Dc);        // cup[Nz-1] = 0 when adiabatic
@@ -142,10 +164,14 @@ cudaError_t step_stored(const Grid<P>& g, const FaceVel<P, LERP>& u, const FaceV
 {
     dim3 blk(64, 4);
     dim3 grd((g.Nx + blk.x - 1) / blk.x, (g.Ny + blk.y - 1) / blk.y, g.Nz);
-    if (implz)
-        k_step_stored<P, true, LERP><<<grd, blk, 0, st>>>(g, u, v, w, Tm1, T, Tp1, (P)c.a, (P)c.b, (P)c.gdt);
-    else
-        k_step_stored<P, false, LERP><<<grd, blk, 0, st>>>(g, u, v, w, Tm1, T, Tp1, (P)c.a, (P)c.b, (P)c.gdt);
+    const P a = (P)c.a, b = (P)c.b, gdt = (P)c.gdt;
+    if (g.order4) {
+        if (implz) k_step_stored<P, true, LERP, true><<<grd, blk, 0, st>>>(g, u, v, w, Tm1, T, Tp1, a, b, gdt);
+        else k_step_stored<P, false, LERP, true><<<grd, blk, 0, st>>>(g, u, v, w, Tm1, T, Tp1, a, b, gdt);
+    } else {
+        if (implz) k_step_stored<P, true, LERP, false><<<grd, blk, 0, st>>>(g, u, v, w, Tm1, T, Tp1, a, b, gdt);
+        else k_step_stored<P, false, LERP, false><<<grd, blk, 0, st>>>(g, u, v, w, Tm1, T, Tp1, a, b, gdt);
+    }
     return cudaGetLastError();
 }
 

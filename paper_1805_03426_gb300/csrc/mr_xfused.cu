@@ -43,27 +43,36 @@ constexpr int kThreads = 256;                           // consumer threads (8 w
 constexpr int kThreadsAll = kThreads + 32;              // + one producer warp
 constexpr float kTBottom = 0.5f, kTTop = -0.5f;
 
-template <int M, bool MT>
+// O4: fourth-order face values of T^s (Section 2.2): the T^s box has two halo
+// rows each side and the layer constants carry the z-face weights.
+template <int M, bool MT, bool O4 = false>
 struct XT {
     static constexpr int CX = kTX / M;
     static constexpr int BXC = CX + 8;                  // coarse box width: columns I0-4 .. I0+CX+3
-    // ring slots; MT (two velocity sets per slot) keeps two CTAs per SM with fewer slots
-    static constexpr int NB = MT ? ((M == 4) ? 5 : 4) : ((M == 4) ? 7 : 6);
+    // ring slots; MT (two velocity sets per slot) keeps two CTAs per SM with fewer
+    // slots.  O4 keeps five planes live at a chunk's first layer (k0-2 .. k0+2),
+    // so it needs at least five slots (at M = 2 with MT that leaves one CTA per SM).
+    static constexpr int NB0 = MT ? ((M == 4) ? 5 : 4) : ((M == 4) ? 7 : 6);
+    static constexpr int NB = (O4 && NB0 < 5) ? 5 : NB0;
     // one ring slot (floats): T^n plane, T^{n-1} plane, then the velocity set of
     // one layer k: WY of its upper plane k+1 (its lower plane k is the previous
     // slot's), UO and VR of layer k; with MT the set of the second coarse time
     // level follows at offset DS; then the layer constants
-    static constexpr int oTn = 0, oTm = kPlaneSlot;
-    static constexpr int oWY = 2 * kPlaneSlot;          // [TY][BXC]      plane k+1
+    static constexpr int BYN = O4 ? kTY + 4 : kBY;       // rows of the T^s box
+    static constexpr uint32_t tn_bytes = (uint32_t)(kBX * BYN) * 4;
+    static constexpr int PN = (int)((tn_bytes + 127) / 128) * 128 / 4;
+    static constexpr int LCW = O4 ? 20 : 12;            // floats of one row of layer constants
+    static constexpr int oTn = 0, oTm = PN;
+    static constexpr int oWY = PN + kPlaneSlot;         // [TY][BXC]      plane k+1
     static constexpr int oUO = oWY + kTY * BXC;         // [TY][BXC]
     static constexpr int oVR = oUO + kTY * BXC;         // [TY+1][BXC]
     static constexpr int SET = ((2 * kTY + kTY + 1) * BXC + 31) / 32 * 32;   // one set, 128-B multiple
     static constexpr int DS = MT ? SET : 0;
-    static constexpr int oLC = oWY + (MT ? 2 : 1) * SET;                     // [12] layer constants
-    static constexpr int slot = (((oLC + 16) * 4 + 127) / 128) * 128 / 4;
+    static constexpr int oLC = oWY + (MT ? 2 : 1) * SET;                     // [LCW] layer constants
+    static constexpr int slot = (((oLC + (O4 ? 20 : 16)) * 4 + 127) / 128) * 128 / 4;
     static constexpr int NSET = MT ? 2 : 1;
     static constexpr uint32_t wy_bytes = (uint32_t)(NSET * kTY * BXC) * 4;
-    static constexpr uint32_t bundle_bytes = (uint32_t)(NSET * (kTY * BXC + (kTY + 1) * BXC) + 12) * 4;  // UO, VR, LC
+    static constexpr uint32_t bundle_bytes = (uint32_t)(NSET * (kTY * BXC + (kTY + 1) * BXC) + LCW) * 4;  // UO, VR, LC
     static constexpr int oRed = NB * slot;              // 64 floats
     static constexpr int oBar = ((oRed + 64) * 4 + 7) / 8;
     static constexpr size_t bytes = (size_t)(oBar + 2 * NB) * 8;
@@ -83,6 +92,7 @@ struct XArgs {
                          // segment starts on a coarse cell boundary, so these are the
                          // same for every thread: kept in the constant bank)
     float alpha;         // MT: weight of the second velocity set, i / M_t (Section 3.4)
+    float w4x[4], w4y[4];  // O4: twice the fourth-order face weights of cells f-2..f+1 (uniform, periodic)
 };
 
 // R_x split of three coarse values by one row of R (rows sum to one):
@@ -98,7 +108,10 @@ __device__ __forceinline__ float rsplit(const float (&r)[3], float c0, float c1,
 // interpolating the intermediates interpolates the dense velocity).
 // KIND 0: the step; 1: max |divergence| of the dense velocity; 2: max CFL
 // rate |u|/dx + |v|/dy + |w|/dz (the last two read no scalar).
-template <int M, int KIND, bool LF, bool MT>
+// O4: fourth-order face values of T^s (Section 2.2).  Ring r then carries plane
+// k0-2+r (one more plane below and above the chunk) and the consumers carry the
+// z-face advective flux of plane k+1 to the next layer.
+template <int M, int KIND, bool LF, bool MT, bool O4>
 __global__ void __launch_bounds__(kThreadsAll, 2)
 k_xfused(const __grid_constant__ CUtensorMap tmn, const __grid_constant__ CUtensorMap tmm,
          const __grid_constant__ CUtensorMap twy, const __grid_constant__ CUtensorMap tuo,
@@ -106,9 +119,10 @@ k_xfused(const __grid_constant__ CUtensorMap tmn, const __grid_constant__ CUtens
          const __grid_constant__ CUtensorMap twy1, const __grid_constant__ CUtensorMap tuo1,
          const __grid_constant__ CUtensorMap tvr1, const XArgs A)
 {
-    using L = XT<M, MT>;
+    using L = XT<M, MT, O4>;
     constexpr int NB = L::NB, BXC = L::BXC, NC = 4 / M, NW = kThreads / 32;
     constexpr bool DIVONLY = KIND != 0;
+    constexpr int OFF = O4 ? 2 : 1;                  // ring r carries plane k0 - OFF + r
     extern __shared__ __align__(128) float sm[];
     float* red = sm + L::oRed;
     uint64_t* full = reinterpret_cast<uint64_t*>(sm) + L::oBar;
@@ -121,8 +135,8 @@ k_xfused(const __grid_constant__ CUtensorMap tmn, const __grid_constant__ CUtens
     const int k0 = blockIdx.x * A.kcl;
     const int k1 = min(k0 + A.kcl, g.Nz);
     if (k0 >= k1) return;
-    const int nrings = k1 - k0 + 2;              // ring r: plane k0-1+r and the bundle of layer k0+r-2
-                                                 // (ring 1 carries only WY of plane k0)
+    const int nrings = k1 - k0 + 2 * OFF;        // ring r: plane p = k0-OFF+r, WY of plane p (k0 <= p <= k1)
+                                                 // and the bundle of layer p-1 (k0 <= p-1 < k1)
 
     if (tid == 0) {
         for (int s = 0; s < NB; ++s) {
@@ -143,20 +157,21 @@ k_xfused(const __grid_constant__ CUtensorMap tmn, const __grid_constant__ CUtens
                 break;
             }
             float* slot = sm + s * L::slot;
-            const bool bundle = (r >= 2);
+            const int p = k0 - OFF + r;              // plane of this ring
+            const bool wy = (p >= k0 && p <= k1), bundle = (p - 1 >= k0 && p - 1 < k1);
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-            mbar_expect_tx(&full[s], (DIVONLY ? 0u : 2 * kPlaneBytes) + (r >= 1 ? L::wy_bytes : 0u) +
+            mbar_expect_tx(&full[s], (DIVONLY ? 0u : L::tn_bytes + kPlaneBytes) + (wy ? L::wy_bytes : 0u) +
                                          (bundle ? L::bundle_bytes : 0u));
             if (!DIVONLY) {
-                tma_3d(slot + L::oTn, &tmn, i0 - 4, j0 - 1, k0 - 1 + r, &full[s]);
-                tma_3d(slot + L::oTm, &tmm, i0 - 4, j0 - 1, k0 - 1 + r, &full[s]);
+                tma_3d(slot + L::oTn, &tmn, i0 - 4, j0 - (O4 ? 2 : 1), p, &full[s]);
+                tma_3d(slot + L::oTm, &tmm, i0 - 4, j0 - 1, p, &full[s]);
             }
-            if (r >= 1) {
-                tma_3d(slot + L::oWY, &twy, I0, j0, k0 - 1 + r, &full[s]);   // WY plane k0-1+r
-                if (MT) tma_3d(slot + L::oWY + L::DS, &twy1, I0, j0, k0 - 1 + r, &full[s]);
+            if (wy) {
+                tma_3d(slot + L::oWY, &twy, I0, j0, p, &full[s]);   // WY plane p
+                if (MT) tma_3d(slot + L::oWY + L::DS, &twy1, I0, j0, p, &full[s]);
             }
             if (bundle) {
-                const int kb = k0 + r - 2;
+                const int kb = p - 1;
                 tma_3d(slot + L::oUO, &tuo, I0, j0, kb, &full[s]);
                 tma_3d(slot + L::oVR, &tvr, I0, j0, kb, &full[s]);
                 if (MT) {
@@ -183,17 +198,19 @@ k_xfused(const __grid_constant__ CUtensorMap tmn, const __grid_constant__ CUtens
     float dmax = 0.f;
     const float kx2 = g.kx2, ky2 = g.ky2;
     const float ca = A.a, cbb = A.b, gdt = A.gdt, alpha = A.alpha;
-    // ring bookkeeping without divisions: slots of planes k-1, k, k+1 and the
-    // next (slot, parity) to wait for
-    int sb = 0, sc = 1, st = 2;
+    // ring bookkeeping without divisions: slots of planes k-1, k, k+1 (and, with
+    // O4, k-2 and k+2) and the next (slot, parity) to wait for
+    int sb = O4 ? 1 : 0, sc = sb + 1, st = sc + 1, sm2 = 0, s2 = O4 ? 4 : 0;
     int wslot = 0, wpar = 0, waited = 0;
     const size_t plane = (size_t)g.Nx * g.Ny;
     float* outp = A.Tp1 + (size_t)k0 * plane + (size_t)(j0 + jl) * g.Nx + i0 + il0;
     const int o = (jl + 1) * kBX + il0 + 4;          // this segment's first cell in a plane box
+    const int o4 = (jl + 2) * kBX + il0 + 4;         // the same in the O4 T^s box (two halo rows)
 
     float wcar[4] = {0.f, 0.f, 0.f, 0.f};            // R_x split of W on plane k (from layer k-1)
+    float fcar[4] = {0.f, 0.f, 0.f, 0.f};            // O4: advective flux W T_f through face k (from layer k-1)
     for (int k = k0; k < k1; ++k) {
-        const int need = k - k0 + 2;             // ring of plane k+1 and of this layer's bundle
+        const int need = k - k0 + (O4 ? 4 : 2);  // ring of plane k+1 and this layer's bundle (O4: plane k+2)
         while (!fail && waited <= need) {
             if (!mbar_wait(&full[wslot], wpar)) { fail = true; break; }
             ++waited;
@@ -281,6 +298,99 @@ k_xfused(const __grid_constant__ CUtensorMap tmn, const __grid_constant__ CUtens
                                               : 2.f * ((us[a + 1] - us[a]) + (vn[a] - vs[a])) + (wt[a] - wb[a]) * inv_dz;
                     dmax = fmaxf(dmax, fabsf(d));
                 }
+            } else if constexpr (O4) {
+                const float* Pn_b = sm + sb * L::slot + L::oTn;
+                const float* Pm_b = sm + sb * L::slot + L::oTm;
+                const float* Pn_c = sm + sc * L::slot + L::oTn;
+                const float* Pm_c = sm + sc * L::slot + L::oTm;
+                const float* Pn_t = sm + st * L::slot + L::oTn;
+                const float* Pm_t = sm + st * L::slot + L::oTm;
+                const float* Pn_2 = sm + s2 * L::slot + L::oTn;
+                const float4 tc4 = *reinterpret_cast<const float4*>(Pn_c + o4);
+                float4 ts4 = *reinterpret_cast<const float4*>(Pn_c + o4 - kBX);
+                float4 tn4 = *reinterpret_cast<const float4*>(Pn_c + o4 + kBX);
+                float4 ts24 = *reinterpret_cast<const float4*>(Pn_c + o4 - 2 * kBX);
+                float4 tn24 = *reinterpret_cast<const float4*>(Pn_c + o4 + 2 * kBX);
+                const float4 dc4 = *reinterpret_cast<const float4*>(Pm_c + o);
+                float4 ds4 = *reinterpret_cast<const float4*>(Pm_c + o - kBX);
+                float4 dn4 = *reinterpret_cast<const float4*>(Pm_c + o + kBX);
+                // in-row neighbours: two of T^s, one of T^{s-1} on each side
+                float tw1 = __shfl_up_sync(0xffffffffu, tc4.w, 1), tw2 = __shfl_up_sync(0xffffffffu, tc4.z, 1);
+                float te1 = __shfl_down_sync(0xffffffffu, tc4.x, 1), te2 = __shfl_down_sync(0xffffffffu, tc4.y, 1);
+                float dw = __shfl_up_sync(0xffffffffu, dc4.w, 1), de = __shfl_down_sync(0xffffffffu, dc4.x, 1);
+                if (seg == 0) { tw1 = Pn_c[o4 - 1]; tw2 = Pn_c[o4 - 2]; dw = Pm_c[o - 1]; }
+                if (seg == 15) { te1 = Pn_c[o4 + 4]; te2 = Pn_c[o4 + 5]; de = Pm_c[o + 4]; }
+                const bool ws2 = (j0 == 0 && jl < 2), wn2 = (j0 + kTY == g.Ny && jl >= kTY - 2);
+                if (wrap_w | wrap_e | ws2 | wn2) {
+                    // the box holds zeros beyond the domain: fetch the periodic images
+                    const float* gn = A.Tn + (size_t)k * plane;
+                    const float* gm = A.Tm + (size_t)k * plane;
+                    const size_t row = (size_t)(j0 + jl) * g.Nx, col = (size_t)(i0 + il0);
+                    if (wrap_w) { tw1 = gn[row + g.Nx - 1]; tw2 = gn[row + g.Nx - 2]; dw = gm[row + g.Nx - 1]; }
+                    if (wrap_e) { te1 = gn[row]; te2 = gn[row + 1]; de = gm[row]; }
+                    if (ws2) {                    // rows jl-1 (jl = 0) and jl-2 below row 0
+                        if (jl == 0) {
+                            ts4 = *reinterpret_cast<const float4*>(gn + (size_t)(g.Ny - 1) * g.Nx + col);
+                            ds4 = *reinterpret_cast<const float4*>(gm + (size_t)(g.Ny - 1) * g.Nx + col);
+                        }
+                        ts24 = *reinterpret_cast<const float4*>(gn + (size_t)(g.Ny - 2 + jl) * g.Nx + col);
+                    }
+                    if (wn2) {                    // rows jl+1 (jl = TY-1) and jl+2 above row Ny-1
+                        if (jl == kTY - 1) {
+                            tn4 = *reinterpret_cast<const float4*>(gn + col);
+                            dn4 = *reinterpret_cast<const float4*>(gm + col);
+                        }
+                        tn24 = *reinterpret_cast<const float4*>(gn + (size_t)(jl - (kTY - 2)) * g.Nx + col);
+                    }
+                }
+                const float4 db4 = *reinterpret_cast<const float4*>(Pm_b + o);
+                const float4 dt4 = *reinterpret_cast<const float4*>(Pm_t + o);
+                const float4 tb4 = *reinterpret_cast<const float4*>(Pn_b + o4);
+                const float4 tt4 = *reinterpret_cast<const float4*>(Pn_t + o4);
+                const float4 t24 = *reinterpret_cast<const float4*>(Pn_2 + o4);
+                const float t8[8] = {tw2, tw1, tc4.x, tc4.y, tc4.z, tc4.w, te1, te2};
+                const float dcv[6] = {dw, dc4.x, dc4.y, dc4.z, dc4.w, de};
+                const float tsv[4] = {ts4.x, ts4.y, ts4.z, ts4.w}, tnv[4] = {tn4.x, tn4.y, tn4.z, tn4.w};
+                const float ts2v[4] = {ts24.x, ts24.y, ts24.z, ts24.w}, tn2v[4] = {tn24.x, tn24.y, tn24.z, tn24.w};
+                const float dsv[4] = {ds4.x, ds4.y, ds4.z, ds4.w}, dnv[4] = {dn4.x, dn4.y, dn4.z, dn4.w};
+                const float tbv[4] = {tb4.x, tb4.y, tb4.z, tb4.w}, ttv[4] = {tt4.x, tt4.y, tt4.z, tt4.w};
+                const float t2v[4] = {t24.x, t24.y, t24.z, t24.w};
+                const float dbv[4] = {db4.x, db4.y, db4.z, db4.w}, dtv[4] = {dt4.x, dt4.y, dt4.z, dt4.w};
+                const auto& wx = A.w4x;
+                const auto& wy = A.w4y;
+                // twice the face values of the segment's five x faces (us holds U / (2 dx))
+                float fx[5];
+#pragma unroll
+                for (int a = 0; a < 5; ++a) fx[a] = wx[0] * t8[a] + wx[1] * t8[a + 1] + wx[2] * t8[a + 2] + wx[3] * t8[a + 3];
+                // z-face k+1: weights of planes k-1 .. k+2; face k from the previous layer
+                const float zt0 = bwlo, zt1 = bwhi, zt2 = twlo, zt3 = twhi;
+                if (k == k0) {
+                    // the chunk's first layer: face k from planes k-2 .. k+1
+                    const float* Pn_m2 = sm + sm2 * L::slot + L::oTn;
+                    const float4 tm4 = *reinterpret_cast<const float4*>(Pn_m2 + o4);
+                    const float2 zb01 = *reinterpret_cast<const float2*>(bun + L::oLC + 10);
+                    const float2 zb23 = *reinterpret_cast<const float2*>(bun + L::oLC + 12);
+                    const float tmv[4] = {tm4.x, tm4.y, tm4.z, tm4.w};
+#pragma unroll
+                    for (int a = 0; a < 4; ++a)
+                        fcar[a] = wb[a] * (zb01.x * tmv[a] + zb01.y * tbv[a] + zb23.x * t8[a + 2] + zb23.y * ttv[a]);
+                }
+                float res[4];
+#pragma unroll
+                for (int a = 0; a < 4; ++a) {
+                    const float tc = t8[a + 2], dc = dcv[a + 1];
+                    const float cx = us[a] * fx[a] - us[a + 1] * fx[a + 1];
+                    const float fs = wy[0] * ts2v[a] + wy[1] * tsv[a] + wy[2] * tc + wy[3] * tnv[a];
+                    const float fn = wy[0] * tsv[a] + wy[1] * tc + wy[2] * tnv[a] + wy[3] * tn2v[a];
+                    const float cy = vs[a] * fs - vn[a] * fn;
+                    const float ft = wt[a] * (zt0 * tbv[a] + zt1 * tc + zt2 * ttv[a] + zt3 * t2v[a]);
+                    const float cz = (fcar[a] - ft) * inv_dz;
+                    fcar[a] = ft;
+                    const float D = kx2 * (dcv[a] + dcv[a + 2]) + ky2 * (dsv[a] + dnv[a]) + cdn * dbv[a] + cup * dtv[a] +
+                                    (plate - diag * dc);
+                    res[a] = LF ? dc + gdt * ((cx + cy + cz) + D) : ca * dc + cbb * t8[a + 2] + gdt * ((cx + cy + cz) + D);
+                }
+                *reinterpret_cast<float4*>(outp) = make_float4(res[0], res[1], res[2], res[3]);
             } else {
                 const float* Pn_b = sm + sb * L::slot + L::oTn;
                 const float* Pm_b = sm + sb * L::slot + L::oTm;
@@ -344,10 +454,20 @@ k_xfused(const __grid_constant__ CUtensorMap tmn, const __grid_constant__ CUtens
             }
         }
         // plane k-1 (and the bundle of layer k-2) are no longer needed by this thread
-        mbar_arrive(&empty[sb]);
-        sb = sc;
-        sc = st;
-        st = (st + 1 == NB) ? 0 : st + 1;
+        if constexpr (O4) {
+            if (k == k0) mbar_arrive(&empty[sm2]);   // plane k0-2 served the first layer only
+            mbar_arrive(&empty[sb]);
+            sm2 = sb;
+            sb = sc;
+            sc = st;
+            st = s2;
+            s2 = (s2 + 1 == NB) ? 0 : s2 + 1;
+        } else {
+            mbar_arrive(&empty[sb]);
+            sb = sc;
+            sc = st;
+            st = (st + 1 == NB) ? 0 : st + 1;
+        }
         outp += plane;
     }
     if (consumers_sync_or<kThreads>(fail)) {
@@ -507,15 +627,16 @@ struct XSet {
     const float *wy, *uo, *vr;
 };
 
-template <int M, int KIND, bool LF, bool MT>
-cudaError_t launch_x(const Grid<float>& g, XSet v0, XSet v1, float alpha, int nxg, const float* lc,
-                     const float* rx12, const float* Tm1, const float* T, float* Tp1, StepCoef c, int* err,
-                     unsigned long long* divmax, cudaStream_t st)
+template <int M, int KIND, bool LF, bool MT, bool O4>
+cudaError_t launch_x(const Grid<float>& g, XSet v0, XSet v1, float alpha, int nxg, const float* lc, int lcw,
+                     const float* rx12, const float* w4, const float* Tm1, const float* T, float* Tp1, StepCoef c,
+                     int* err, unsigned long long* divmax, cudaStream_t st)
 {
-    using L = XT<M, MT>;
+    using L = XT<M, MT, O4>;
+    if (lcw < L::LCW) return cudaErrorInvalidValue;
     static unsigned long long attr = 0;                   // one bit per device
     constexpr bool DIVONLY = KIND != 0;
-    cudaError_t e = smem_optin(reinterpret_cast<const void*>(k_xfused<M, KIND, LF, MT>), (int)L::bytes, &attr);
+    cudaError_t e = smem_optin(reinterpret_cast<const void*>(k_xfused<M, KIND, LF, MT, O4>), (int)L::bytes, &attr);
     if (e != cudaSuccess) return e;
     CUtensorMap mn, mm, mwy, muo, mvr, mlc, mwy1, muo1, mvr1;
     memset(&mn, 0, sizeof mn);
@@ -523,7 +644,7 @@ cudaError_t launch_x(const Grid<float>& g, XSet v0, XSet v1, float alpha, int nx
     memset(&mwy1, 0, sizeof mwy1);
     memset(&muo1, 0, sizeof muo1);
     memset(&mvr1, 0, sizeof mvr1);
-    if (!DIVONLY && (!cached_map3(&mn, T, g.Nx, g.Ny, g.Nz, kBX, kBY, 1) ||
+    if (!DIVONLY && (!cached_map3(&mn, T, g.Nx, g.Ny, g.Nz, kBX, L::BYN, 1) ||
                      !cached_map3(&mm, Tm1, g.Nx, g.Ny, g.Nz, kBX, kBY, 1)))
         return cudaErrorInvalidValue;
     auto set_maps = [&](const XSet& v, CUtensorMap* wy, CUtensorMap* uo, CUtensorMap* vr) {
@@ -532,7 +653,7 @@ cudaError_t launch_x(const Grid<float>& g, XSet v0, XSet v1, float alpha, int nx
                cached_map3(vr, v.vr, nxg, g.Ny + 1, g.Nz, L::BXC, kTY + 1, 1);
     };
     if (!set_maps(v0, &mwy, &muo, &mvr) || (MT && !set_maps(v1, &mwy1, &muo1, &mvr1)) ||
-        !cached_map3(&mlc, lc, 12, g.Nz, 1, 12, 1, 1))
+        !cached_map3(&mlc, lc, lcw, g.Nz, 1, L::LCW, 1, 1))
         return cudaErrorInvalidValue;
     const int tiles = (g.Nx / kTX) * (g.Ny / kTY);
     int kcl = kcl_override();
@@ -543,25 +664,29 @@ cudaError_t launch_x(const Grid<float>& g, XSet v0, XSet v1, float alpha, int nx
         kcl = (g.Nz + chunks - 1) / chunks;
     }
     const int chunks = (g.Nz + kcl - 1) / kcl;
-    XArgs A{g, T, Tm1, Tp1, lc, (float)c.a, (float)c.b, (float)c.gdt, kcl, err, divmax, {}, alpha};
+    XArgs A{g, T, Tm1, Tp1, lc, (float)c.a, (float)c.b, (float)c.gdt, kcl, err, divmax, {}, alpha, {}, {}};
     memcpy(A.rx, rx12, sizeof A.rx);
+    if (O4) {
+        memcpy(A.w4x, w4, sizeof A.w4x);
+        memcpy(A.w4y, w4 + 4, sizeof A.w4y);
+    }
     dim3 grid(chunks, g.Nx / kTX, g.Ny / kTY);
-    k_xfused<M, KIND, LF, MT><<<grid, kThreadsAll, L::bytes, st>>>(mn, mm, mwy, muo, mvr, mlc, mwy1, muo1, mvr1, A);
+    k_xfused<M, KIND, LF, MT, O4><<<grid, kThreadsAll, L::bytes, st>>>(mn, mm, mwy, muo, mvr, mlc, mwy1, muo1, mvr1, A);
     return cudaGetLastError();
 }
 
-template <int M>
-cudaError_t launch_step_m(const Grid<float>& g, XSet v0, const XSet* v1, float alpha, int nxg, const float* lc,
-                          const float* rx12, const float* Tm1, const float* T, float* Tp1, StepCoef c, int* err,
-                          cudaStream_t st)
+template <int M, bool O4>
+cudaError_t launch_step_m(const Grid<float>& g, XSet v0, const XSet* v1, float alpha, int nxg, const float* lc, int lcw,
+                          const float* rx12, const float* w4, const float* Tm1, const float* T, float* Tp1, StepCoef c,
+                          int* err, cudaStream_t st)
 {
     const bool lf = (c.a == 1.0 && c.b == 0.0);
     if (v1) {
-        return lf ? launch_x<M, 0, true, true>(g, v0, *v1, alpha, nxg, lc, rx12, Tm1, T, Tp1, c, err, nullptr, st)
-                  : launch_x<M, 0, false, true>(g, v0, *v1, alpha, nxg, lc, rx12, Tm1, T, Tp1, c, err, nullptr, st);
+        return lf ? launch_x<M, 0, true, true, O4>(g, v0, *v1, alpha, nxg, lc, lcw, rx12, w4, Tm1, T, Tp1, c, err, nullptr, st)
+                  : launch_x<M, 0, false, true, O4>(g, v0, *v1, alpha, nxg, lc, lcw, rx12, w4, Tm1, T, Tp1, c, err, nullptr, st);
     }
-    return lf ? launch_x<M, 0, true, false>(g, v0, v0, 0.f, nxg, lc, rx12, Tm1, T, Tp1, c, err, nullptr, st)
-              : launch_x<M, 0, false, false>(g, v0, v0, 0.f, nxg, lc, rx12, Tm1, T, Tp1, c, err, nullptr, st);
+    return lf ? launch_x<M, 0, true, false, O4>(g, v0, v0, 0.f, nxg, lc, lcw, rx12, w4, Tm1, T, Tp1, c, err, nullptr, st)
+              : launch_x<M, 0, false, false, O4>(g, v0, v0, 0.f, nxg, lc, lcw, rx12, w4, Tm1, T, Tp1, c, err, nullptr, st);
 }
 
 }  // namespace
@@ -578,8 +703,8 @@ cudaError_t launch_xfused_prep(const Grid<float>& g, const float* U, const float
 }
 
 cudaError_t launch_step_xfused_f32(const Grid<float>& g, const float* const setA[3], const float* const setB[3],
-                                   double alpha, int nxg, const float* lc, const float* rx12, const float* Tm1,
-                                   const float* T, float* Tp1, StepCoef c, cudaStream_t st)
+                                   double alpha, int nxg, const float* lc, int lcw, const float* rx12, const float* w4,
+                                   const float* Tm1, const float* T, float* Tp1, StepCoef c, cudaStream_t st)
 {
     int* err = fused_error_flag();
     if (!err) return cudaErrorMemoryAllocation;
@@ -590,14 +715,18 @@ cudaError_t launch_step_xfused_f32(const Grid<float>& g, const float* const setA
         v1 = XSet{setB[0], setB[1], setB[2]};
         pv1 = &v1;
     }
-    if (g.mx == 4) return launch_step_m<4>(g, v0, pv1, (float)alpha, nxg, lc, rx12, Tm1, T, Tp1, c, err, st);
-    return launch_step_m<2>(g, v0, pv1, (float)alpha, nxg, lc, rx12, Tm1, T, Tp1, c, err, st);
+    const float a = (float)alpha;
+    if (g.order4)
+        return g.mx == 4 ? launch_step_m<4, true>(g, v0, pv1, a, nxg, lc, lcw, rx12, w4, Tm1, T, Tp1, c, err, st)
+                         : launch_step_m<2, true>(g, v0, pv1, a, nxg, lc, lcw, rx12, w4, Tm1, T, Tp1, c, err, st);
+    return g.mx == 4 ? launch_step_m<4, false>(g, v0, pv1, a, nxg, lc, lcw, rx12, w4, Tm1, T, Tp1, c, err, st)
+                     : launch_step_m<2, false>(g, v0, pv1, a, nxg, lc, lcw, rx12, w4, Tm1, T, Tp1, c, err, st);
 }
 
 // kind 1: max |divergence|, kind 2: max CFL rate, as a double in partials[0]
 // (the other blocks - 1 partials are zeroed).
 cudaError_t launch_xfused_max_f32(const Grid<float>& g, int kind, const float* WY, const float* UO, const float* VR,
-                                  int nxg, const float* lc, const float* rx12, double* partials, int blocks,
+                                  int nxg, const float* lc, int lcw, const float* rx12, double* partials, int blocks,
                                   cudaStream_t st)
 {
     int* err = fused_error_flag();
@@ -608,39 +737,53 @@ cudaError_t launch_xfused_max_f32(const Grid<float>& g, int kind, const float* W
     StepCoef c{0, 0, 0};
     const XSet v{WY, UO, VR};
     if (g.mx == 4)
-        return kind == 2 ? launch_x<4, 2, false, false>(g, v, v, 0.f, nxg, lc, rx12, nullptr, nullptr, nullptr, c, err, dm, st)
-                         : launch_x<4, 1, false, false>(g, v, v, 0.f, nxg, lc, rx12, nullptr, nullptr, nullptr, c, err, dm, st);
-    return kind == 2 ? launch_x<2, 2, false, false>(g, v, v, 0.f, nxg, lc, rx12, nullptr, nullptr, nullptr, c, err, dm, st)
-                     : launch_x<2, 1, false, false>(g, v, v, 0.f, nxg, lc, rx12, nullptr, nullptr, nullptr, c, err, dm, st);
+        return kind == 2 ? launch_x<4, 2, false, false, false>(g, v, v, 0.f, nxg, lc, lcw, rx12, nullptr, nullptr, nullptr,
+                                                               nullptr, c, err, dm, st)
+                         : launch_x<4, 1, false, false, false>(g, v, v, 0.f, nxg, lc, lcw, rx12, nullptr, nullptr, nullptr,
+                                                               nullptr, c, err, dm, st);
+    return kind == 2 ? launch_x<2, 2, false, false, false>(g, v, v, 0.f, nxg, lc, lcw, rx12, nullptr, nullptr, nullptr,
+                                                           nullptr, c, err, dm, st)
+                     : launch_x<2, 1, false, false, false>(g, v, v, 0.f, nxg, lc, lcw, rx12, nullptr, nullptr, nullptr,
+                                                           nullptr, c, err, dm, st);
 }
 
-// Per-layer constants of the split-x kernel, [Nz][12] floats, all folded on
-// the host in FP64: 1/dz; the linear-interpolation weights of T_{k-1}, T_k at
-// face k and of T_k, T_{k+1} at face k+1, each times 1/dz; kappa/(dz d) toward
-// the centre (or plate) below and above; the diagonal 2 kappa/dx^2 +
-// 2 kappa/dy^2 + cdn + cup; the plate term (Dirichlet plates: cdn T_bottom on
-// the first layer, cup T_top on the last); 1/(2 dz).  The kernel reads zeros
-// for the planes beyond the plates, where W is zero.
+// Per-layer constants of the split-x kernel, [Nz][lcw] floats (lcw = 12, or 20
+// with fourth-order faces), all folded on the host in FP64: 1/dz; the
+// linear-interpolation weights of T_{k-1}, T_k at face k and of T_k, T_{k+1}
+// at face k+1, each times 1/dz (fourth order instead: the weights of planes
+// k-1 .. k+2 at face k+1); kappa/(dz d) toward the centre (or plate) below and
+// above; the diagonal 2 kappa/dx^2 + 2 kappa/dy^2 + cdn + cup; the plate term
+// (Dirichlet plates: cdn T_bottom on the first layer, cup T_top on the last);
+// 1/(2 dz); fourth order: the weights of planes k-2 .. k+1 at face k.  The
+// kernel reads zeros for the planes beyond the plates, where W is zero.
 std::vector<float> xfused_layer_constants(int Nz, const double* zf, const double* zc, const double* dz, double kappa,
-                                          double dx, double dy, bool dirichlet)
+                                          double dx, double dy, bool dirichlet, const double* f4z, int* lcw)
 {
-    std::vector<float> lc((size_t)Nz * 12, 0.f);
+    *lcw = f4z ? 20 : 12;
+    std::vector<float> lc((size_t)Nz * *lcw, 0.f);
     const double kx2 = kappa / (dx * dx), ky2 = kappa / (dy * dy);
     for (int k = 0; k < Nz; ++k) {
-        float* q = &lc[(size_t)k * 12];
+        float* q = &lc[(size_t)k * *lcw];
         const double dzk = dz[k], idz = 1.0 / dzk;
         const double below = k > 0 ? zc[k] - zc[k - 1] : zc[0] - zf[0];
         const double above = k < Nz - 1 ? zc[k + 1] - zc[k] : zf[Nz] - zc[Nz - 1];
         const double cdn = (k > 0 || dirichlet) ? kappa / (dzk * below) : 0.0;
         const double cup = (k < Nz - 1 || dirichlet) ? kappa / (dzk * above) : 0.0;
         q[0] = (float)idz;
-        if (k > 0) {
-            q[1] = (float)(dzk / (dz[k - 1] + dzk) * idz);
-            q[2] = (float)(dz[k - 1] / (dz[k - 1] + dzk) * idz);
-        }
-        if (k < Nz - 1) {
-            q[3] = (float)(dz[k + 1] / (dzk + dz[k + 1]) * idz);
-            q[4] = (float)(dzk / (dzk + dz[k + 1]) * idz);
+        if (f4z) {
+            for (int c = 0; c < 4; ++c) {
+                q[1 + c] = (float)f4z[4 * (size_t)(k + 1) + c];    // face k+1: planes k-1 .. k+2
+                q[10 + c] = (float)f4z[4 * (size_t)k + c];         // face k: planes k-2 .. k+1
+            }
+        } else {
+            if (k > 0) {
+                q[1] = (float)(dzk / (dz[k - 1] + dzk) * idz);
+                q[2] = (float)(dz[k - 1] / (dz[k - 1] + dzk) * idz);
+            }
+            if (k < Nz - 1) {
+                q[3] = (float)(dz[k + 1] / (dzk + dz[k + 1]) * idz);
+                q[4] = (float)(dzk / (dzk + dz[k + 1]) * idz);
+            }
         }
         q[5] = (float)cdn;
         q[6] = (float)cup;

@@ -39,6 +39,7 @@ class mr_config(ctypes.Structure):
         ("precision", ctypes.c_int32), ("velocity_mode", ctypes.c_int32),
         ("np_average", ctypes.c_int32), ("bc_plates", ctypes.c_int32),
         ("bc_horizontal", ctypes.c_int32), ("diffz_implicit", ctypes.c_int32),
+        ("face_order", ctypes.c_int32),
     ]
 
 
