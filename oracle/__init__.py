@@ -111,6 +111,7 @@ def _load():
             "or_step": (ctypes.c_int, [cp, dp, dp, dp, dp, dp, i64, dp]),
             "or_rhs": (ctypes.c_int, [cp, dp, dp, dp, dp, dp, dp, dp]),
             "or_run": (ctypes.c_int, [cp, dp, dp, dp, dp, i64, dp, dp]),
+            "or_run_from": (ctypes.c_int, [cp, dp, dp, dp, i64, i64, dp, dp]),
             "or_stats": (ctypes.c_int, [cp, dp, dp, dp, dp, dp]),
             "or_max_divergence": (d, [cp, dp, dp, dp]),
             "or_cfl_dt": (d, [cp, dp, dp, dp, d]),
@@ -238,6 +239,16 @@ def run(cfg: Config, vel, T0, nsteps: int):
     Tp, Tc = np.empty(sh["T"]), np.empty(sh["T"])
     c = cfg._c()
     _check(_load().or_run(ctypes.byref(c), _p(Us), _p(Vs), _p(Ws), _p(T0), nsteps, _p(Tp), _p(Tc)), "run")
+    return Tp, Tc
+
+
+def run_from(cfg: Config, vel, Tm1, T, s0: int, nsteps: int):
+    """Continue nsteps steps from (T^{s0-1}, T^{s0}); returns the new pair."""
+    sh = cfg.shapes()
+    Us, Vs, Ws = (_f64(a, sh[k]) for a, k in zip(vel, ("Us", "Vs", "Ws")))
+    Tp, Tc = np.array(_f64(Tm1, sh["T"]), copy=True), np.array(_f64(T, sh["T"]), copy=True)
+    c = cfg._c()
+    _check(_load().or_run_from(ctypes.byref(c), _p(Us), _p(Vs), _p(Ws), s0, nsteps, _p(Tp), _p(Tc)), "run_from")
     return Tp, Tc
 
 

@@ -812,6 +812,23 @@ int or_run(const or_cfg* c, const double* Us, const double* Vs, const double* Ws
     return 0;
 }
 
+int or_run_from(const or_cfg* c, const double* Us, const double* Vs, const double* Ws, int64_t s0,
+                int64_t nsteps, double* Tprev, double* Tcur)
+{
+    geom G, *g = &G;
+    if (geom_init(c, g)) return -1;
+    size_t n = (size_t)g->Nx * g->Ny * g->Nz;
+    double* w = malloc(4 * n * sizeof(double));
+    double* nxt = w + 3 * n;
+    for (int64_t s = s0; s < s0 + nsteps; ++s) {
+        step_impl(c, g, Us, Vs, Ws, Tprev, Tcur, s, nxt, w, w + n, w + 2 * n);
+        memcpy(Tprev, Tcur, n * sizeof(double));
+        memcpy(Tcur, nxt, n * sizeof(double));
+    }
+    free(w); geom_free(g);
+    return 0;
+}
+
 /* ------------------------------------------------------------------------ */
 /* Statistics, Section 4.1                                                    */
 /* ------------------------------------------------------------------------ */

@@ -65,6 +65,11 @@ int  or_rhs(const or_cfg* c, const double* Us, const double* Vs, const double* W
 int  or_run(const or_cfg* c, const double* Us, const double* Vs, const double* Ws,
             const double* T0, int64_t nsteps, double* Tprev, double* Tcur);
 
+/* Continue from the pair (Tprev, Tcur) = (T^{s0-1}, T^{s0}) for nsteps steps
+ * with global indices s0 .. s0+nsteps-1; the pair is updated in place. */
+int  or_run_from(const or_cfg* c, const double* Us, const double* Vs, const double* Ws, int64_t s0,
+                 int64_t nsteps, double* Tprev, double* Tcur);
+
 /* out[0..5] = Nu_bottom, Nu_top, volume mean, volume variance, integral,
  * max |div u| over dense cells (Section 4.1 and the divergence check, 3.2). */
 int  or_stats(const or_cfg* c, const double* T, const double* Us, const double* Vs,

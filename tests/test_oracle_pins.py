@@ -734,3 +734,15 @@ def test_face4_scalar_integral_conserved(oracle_mod, walls):
         assert abs(float((T * vol).sum()) - I0) < 1e-14
     T2 = O.run(O.Config(**{**cfg.__dict__, "face_order": 2}), vel, T0, 8)[1]
     assert np.abs(T - T2).max() > 1e-6                  # the order changes the result
+
+
+def test_run_from_continues_run(oracle_mod):
+    """Continuing from a state pair with global step indices is the same run:
+    3 + 4 steps (crossing the averaging step) equal 7 steps bit for bit."""
+    O = oracle_mod
+    cfg, T0 = _temporal_case(O)
+    vel = O.refine(cfg, *_velocity(O, cfg))
+    Tp, Tc = O.run(cfg, vel, T0, 3)
+    Tp, Tc = O.run_from(cfg, vel, Tp, Tc, 3, 4)
+    rp, rc = O.run(cfg, vel, T0, 7)
+    assert np.array_equal(Tp, rp) and np.array_equal(Tc, rc)
