@@ -819,12 +819,15 @@ int or_run_from(const or_cfg* c, const double* Us, const double* Vs, const doubl
     if (geom_init(c, g)) return -1;
     size_t n = (size_t)g->Nx * g->Ny * g->Nz;
     double* w = malloc(4 * n * sizeof(double));
-    double* nxt = w + 3 * n;
+    /* the three levels rotate through Tprev, Tcur and one work array */
+    double *a = Tprev, *b = Tcur, *nxt = w + 3 * n;
     for (int64_t s = s0; s < s0 + nsteps; ++s) {
-        step_impl(c, g, Us, Vs, Ws, Tprev, Tcur, s, nxt, w, w + n, w + 2 * n);
-        memcpy(Tprev, Tcur, n * sizeof(double));
-        memcpy(Tcur, nxt, n * sizeof(double));
+        step_impl(c, g, Us, Vs, Ws, a, b, s, nxt, w, w + n, w + 2 * n);
+        double* t = a; a = b; b = nxt; nxt = t;
     }
+    if (a != Tprev) memcpy(w, a, n * sizeof(double));       /* a may alias Tcur: stage it */
+    if (b != Tcur) memcpy(Tcur, b, n * sizeof(double));
+    if (a != Tprev) memcpy(Tprev, w, n * sizeof(double));
     free(w); geom_free(g);
     return 0;
 }

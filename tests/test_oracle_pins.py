@@ -738,11 +738,13 @@ def test_face4_scalar_integral_conserved(oracle_mod, walls):
 
 def test_run_from_continues_run(oracle_mod):
     """Continuing from a state pair with global step indices is the same run:
-    3 + 4 steps (crossing the averaging step) equal 7 steps bit for bit."""
+    a + b steps (crossing the averaging step) equal a + b steps in one run, bit
+    for bit, for every residue of b modulo the three rotating levels."""
     O = oracle_mod
     cfg, T0 = _temporal_case(O)
     vel = O.refine(cfg, *_velocity(O, cfg))
-    Tp, Tc = O.run(cfg, vel, T0, 3)
-    Tp, Tc = O.run_from(cfg, vel, Tp, Tc, 3, 4)
     rp, rc = O.run(cfg, vel, T0, 7)
-    assert np.array_equal(Tp, rp) and np.array_equal(Tc, rc)
+    for a in (1, 2, 3):
+        Tp, Tc = O.run(cfg, vel, T0, a)
+        Tp, Tc = O.run_from(cfg, vel, Tp, Tc, a, 7 - a)
+        assert np.array_equal(Tp, rp) and np.array_equal(Tc, rc), a
