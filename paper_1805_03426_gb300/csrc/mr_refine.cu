@@ -89,7 +89,9 @@ __global__ void k_outer_w(Grid<P> g, const P* __restrict__ W, P* __restrict__ Ws
 }
 
 // Stage Z balance: thread per coarse cell; writes the full-area inner-plane W.
-template <typename P>
+// MZ > 0: the refinement factor in z known at compile time (the loop unrolls
+// and every load is issued before the running balance); 0: any factor.
+template <typename P, int MZ = 0>
 __global__ void k_column_balance(Grid<P> g, const P* __restrict__ U, const P* __restrict__ V,
                                  const P* __restrict__ W, P* __restrict__ scrW)
 {
@@ -102,8 +104,10 @@ __global__ void k_column_balance(Grid<P> g, const P* __restrict__ U, const P* __
     int Ie = g.walls ? I + 1 : (I + 1) % g.nx;
     int Jn = g.walls ? J + 1 : (J + 1) % g.ny;
     P F = W[((size_t)(K + 1) * g.ny + J) * g.nx + I] * g.DX * g.DY;
-    for (int c = g.mz - 1; c >= 1; --c) {
-        int k = K * g.mz + c;
+    const int mz = MZ > 0 ? MZ : g.mz;
+#pragma unroll
+    for (int c = mz - 1; c >= 1; --c) {
+        int k = K * mz + c;
         P uw = 0, ue = 0, vs = 0, vn = 0;
         for (int q = 0; q < 3; ++q) {
             P r = g.Rz[3 * k + q];
@@ -252,7 +256,9 @@ cudaError_t launch_column_balance(const Grid<P>& g, const P* U, const P* V, cons
 {
     if (g.mz > 1) {
         const size_t n = (size_t)g.nz * g.ny * g.nx;
-        k_column_balance<P><<<blocks_for(n), kThreads, 0, st>>>(g, U, V, W, scrW);
+        if (g.mz == 4) k_column_balance<P, 4><<<blocks_for(n), kThreads, 0, st>>>(g, U, V, W, scrW);
+        else if (g.mz == 2) k_column_balance<P, 2><<<blocks_for(n), kThreads, 0, st>>>(g, U, V, W, scrW);
+        else k_column_balance<P><<<blocks_for(n), kThreads, 0, st>>>(g, U, V, W, scrW);
     }
     return cudaGetLastError();
 }

@@ -499,6 +499,7 @@ __device__ __forceinline__ int wrapc(int i, int n) { return i < 0 ? i + n : (i >
 // split first, shared by the M_y dense rows of J) times 1/(2 dx), and WY[k][j][gx], R_y of
 // the full-area W on dense plane k (coarse W on the coarse planes,
 // slab-balanced scrW on the inner ones); the top layer also writes plane Nz.
+template <int MY>
 __global__ void k_xprep_uowy(Grid<float> g, const float* __restrict__ U, const float* __restrict__ W,
                              const float* __restrict__ scrW, float* __restrict__ UO, float* __restrict__ WY, int nxg)
 {
@@ -513,8 +514,9 @@ __global__ void k_xprep_uowy(Grid<float> g, const float* __restrict__ U, const f
         for (int q = 0; q < 3; ++q) s += g.Rz[3 * k + q] * U[((size_t)g.wz[3 * K + q] * g.ny + Jp) * g.nx + I];
         a[p] = s;
     }
-    for (int b = 0; b < g.my; ++b) {
-        const int j = J * g.my + b;
+#pragma unroll
+    for (int b = 0; b < MY; ++b) {
+        const int j = J * MY + b;
         UO[((size_t)k * g.Ny + j) * nxg + gx] =
             (g.Ry[3 * j] * a[0] + g.Ry[3 * j + 1] * a[1] + g.Ry[3 * j + 2] * a[2]) * (0.5f * g.inv_dx);
     }
@@ -523,8 +525,9 @@ __global__ void k_xprep_uowy(Grid<float> g, const float* __restrict__ U, const f
         const float* src = (kp == Kp * g.mz) ? W + (size_t)Kp * g.ny * g.nx : scrW + (size_t)kp * g.ny * g.nx;
         float c[3];
         for (int p = 0; p < 3; ++p) c[p] = src[(size_t)g.wy[3 * J + p] * g.nx + I];
-        for (int b = 0; b < g.my; ++b) {
-            const int j = J * g.my + b;
+#pragma unroll
+        for (int b = 0; b < MY; ++b) {
+            const int j = J * MY + b;
             WY[((size_t)kp * g.Ny + j) * nxg + gx] = g.Ry[3 * j] * c[0] + g.Ry[3 * j + 1] * c[1] + g.Ry[3 * j + 2] * c[2];
         }
     }
@@ -533,6 +536,7 @@ __global__ void k_xprep_uowy(Grid<float> g, const float* __restrict__ U, const f
 // VR[k][j][gx]: full-coarse-width V on every dense y-face times 1/(2 dy), by
 // the row balance (south to north) of stage Y; one thread per coarse row J
 // (0..ny, row ny repeating row 0, periodic) walks its M_y - 1 inner faces.
+template <int MY>
 __global__ void k_xprep_vr(Grid<float> g, const float* __restrict__ V, const float* __restrict__ UO,
                            const float* __restrict__ WY, float* __restrict__ VR, int nxg)
 {
@@ -544,16 +548,25 @@ __global__ void k_xprep_vr(Grid<float> g, const float* __restrict__ V, const flo
     for (int q = 0; q < 3; ++q) vz += g.Rz[3 * k + q] * V[((size_t)g.wz[3 * K + q] * g.ny + Jf) * g.nx + I];
     const size_t vrow = (size_t)g.Ny + 1;
     const float hiy = 0.5f * g.inv_dy, two_dx = 2.f * g.dx;   // UO holds U / (2 dx)
-    VR[((size_t)k * vrow + (size_t)J * g.my) * nxg + gx] = vz * hiy;
+    VR[((size_t)k * vrow + (size_t)J * MY) * nxg + gx] = vz * hiy;
     if (J == g.ny) return;
     const float dzk = g.dz[k];
     const int xi = I + 4, xe = wrapc(I + 1, g.nx) + 4;
+    // the loads of all inner faces first (independent of the running balance)
+    float uw[MY], ue[MY], wb[MY], wt[MY];
+#pragma unroll
+    for (int b = 0; b < MY - 1; ++b) {
+        const size_t r = (size_t)k * g.Ny + J * MY + b;
+        uw[b] = UO[r * nxg + xi] * two_dx;
+        ue[b] = UO[r * nxg + xe] * two_dx;
+        wb[b] = WY[r * nxg + xi];
+        wt[b] = WY[(r + g.Ny) * nxg + xi];
+    }
     float G = vz * g.DX * dzk;
-    for (int b = 0; b < g.my - 1; ++b) {
-        const int j = J * g.my + b;
-        const float uw = UO[((size_t)k * g.Ny + j) * nxg + xi] * two_dx, ue = UO[((size_t)k * g.Ny + j) * nxg + xe] * two_dx;
-        const float wb = WY[((size_t)k * g.Ny + j) * nxg + xi], wt = WY[((size_t)(k + 1) * g.Ny + j) * nxg + xi];
-        G = G - (ue - uw) * g.dy * dzk - (wt - wb) * g.DX * g.dy;
+#pragma unroll
+    for (int b = 0; b < MY - 1; ++b) {
+        const int j = J * MY + b;
+        G = G - (ue[b] - uw[b]) * g.dy * dzk - (wt[b] - wb[b]) * g.DX * g.dy;
         VR[((size_t)k * vrow + j + 1) * nxg + gx] = G / (g.DX * dzk) * hiy;
     }
 }
@@ -697,8 +710,10 @@ cudaError_t launch_xfused_prep(const Grid<float>& g, const float* U, const float
     cudaError_t e = launch_column_balance<float>(g, U, V, W, scrW, st);
     if (e != cudaSuccess) return e;
     const unsigned row = (unsigned)((nxg * g.ny + 127) / 128), rowc = (unsigned)((nxg * (g.ny + 1) + 127) / 128);
-    k_xprep_uowy<<<dim3(row, g.Nz), 128, 0, st>>>(g, U, W, scrW, UO, WY, nxg);
-    k_xprep_vr<<<dim3(rowc, g.Nz), 128, 0, st>>>(g, V, UO, WY, VR, nxg);
+    if (g.my == 4) k_xprep_uowy<4><<<dim3(row, g.Nz), 128, 0, st>>>(g, U, W, scrW, UO, WY, nxg);
+    else k_xprep_uowy<2><<<dim3(row, g.Nz), 128, 0, st>>>(g, U, W, scrW, UO, WY, nxg);
+    if (g.my == 4) k_xprep_vr<4><<<dim3(rowc, g.Nz), 128, 0, st>>>(g, V, UO, WY, VR, nxg);
+    else k_xprep_vr<2><<<dim3(rowc, g.Nz), 128, 0, st>>>(g, V, UO, WY, VR, nxg);
     return cudaGetLastError();
 }
 
