@@ -64,3 +64,52 @@ def test_large_grid_conduction_steady_nu_one(mr):
     T = torch.empty_like(T0)
     mr.mr_get_scalar(h, T)
     assert float((T - T0).abs().max()) <= 1e-6
+
+
+@pytest.mark.parametrize("face_order", [2, 4])
+def test_large_grid_sampled_parity(mr, face_order):
+    """Parity on samples of the full 1536x1536x1024 grid in the benchmarked
+    split-x mode.  The refined faces of a coarse column depend on the coarse
+    velocity within two coarse columns (the balances use the neighbouring
+    columns' balanced faces, whose R windows reach one further), and one step
+    reaches one (two, at fourth order) cells further; so the oracle, run on a
+    periodic block of B x B coarse columns over the full height (same stretched
+    z grid) with the block's coarse velocity and initial scalar, reproduces the
+    full-grid run on the block's interior (checked on the CPU to round-off on a
+    small grid).  Blocks at the periodic seam, mid-domain and a corner are
+    checked after three steps (Euler start, leapfrog, averaging with N_p = 3) at
+    the FP32 bar."""
+    import oracle as O
+    from paper_1805_03426_gb300 import synth
+    h = mr.mr_create(_cfg(mr, face_order=face_order))
+    (Nx, Ny, Nz), zf = mr.mr_grid(h)
+    U, V, W = synth.coarse_velocity(1805, np.arange(385) / 384, np.arange(385) / 384, zf[::4], rms=0.1)
+    mr.mr_refine_velocity(h, torch.from_numpy(U).cuda(), torch.from_numpy(V).cuda(), torch.from_numpy(W).cuda())
+    zc = 0.5 * (zf[1:] + zf[:-1])
+    T0 = synth.initial_scalar_device(1805, zc, Ny, Nx)
+    mr.mr_set_scalar(h, T0)
+    mr.mr_scalar_step(h, 3)
+    assert hi - lo >= 6
+    T3 = torch.empty_like(T0)
+    mr.mr_get_scalar(h, T3)
+    torch.cuda.synchronize()
+    n, M = 384, 4
+    B = 7 if face_order == 2 else 9                   # coarse columns per block side
+    cfg = O.Config(nx=B, ny=B, nz=256, mx=4, my=4, mz=4, lx=B / n, ly=B / n, gamma=1.5,
+                   kappa=(1e10 * 100.0) ** -0.5, dt=2e-4, np_average=3, face_order=face_order)
+    reach = 3 * (2 if face_order == 4 else 1)         # cells the three steps reach
+    lo, hi = 2 * M + reach, (B - 2) * M - reach       # exact columns 2..B-3, less the reach
+    for J0, I0 in ((0, 0), (190, 17), (382, 383)):    # seam, middle, corner (wrapping in x and y)
+        jj = (J0 + np.arange(B)) % n
+        ii = (I0 + np.arange(B)) % n
+        Ub = np.ascontiguousarray(U[:, jj][:, :, ii])
+        Vb = np.ascontiguousarray(V[:, jj][:, :, ii])
+        Wb = np.ascontiguousarray(W[:, jj][:, :, ii])
+        yd = torch.from_numpy((M * J0 + np.arange(B * M)) % Ny).cuda()
+        xd = torch.from_numpy((M * I0 + np.arange(B * M)) % Nx).cuda()
+        T0b = T0[:, yd][:, :, xd].double().cpu().numpy()
+        got = T3[:, yd][:, :, xd].double().cpu().numpy()
+        vel = O.refine(cfg, Ub, Vb, Wb)
+        _, ref = O.run(cfg, vel, T0b, 3)
+        err = np.abs(got[:, lo:hi, lo:hi] - ref[:, lo:hi, lo:hi]).max()
+        assert err <= 1e-5, (J0, I0, err)

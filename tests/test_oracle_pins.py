@@ -748,3 +748,34 @@ def test_run_from_continues_run(oracle_mod):
         Tp, Tc = O.run(cfg, vel, T0, a)
         Tp, Tc = O.run_from(cfg, vel, Tp, Tc, a, 7 - a)
         assert np.array_equal(Tp, rp) and np.array_equal(Tc, rc), a
+
+
+@pytest.mark.parametrize("face_order,B", [(2, 7), (4, 9)])
+def test_block_locality_of_refine_and_steps(oracle_mod, face_order, B):
+    """The locality the full-size sampled GPU check relies on: the oracle on a
+    periodic block of B x B coarse columns (full height) reproduces the
+    full-grid refined faces two coarse columns in from the block edge, and three
+    steps of the scalar one (two) cells per step further in."""
+    O = oracle_mod
+    n, M = 14, 4
+    kw = dict(nz=6, mx=4, my=4, mz=4, gamma=1.5, kappa=1e-3, dt=2e-3, np_average=3, face_order=face_order)
+    full = _cfg(O, nx=n, ny=n, **kw)
+    g = O.grid(full)
+    U, V, W = synth.coarse_velocity(3, g["Xf"], g["Yf"], g["Zf"], 1.0, 1.0, rms=0.1)
+    Nx, Ny, Nz = full.dense
+    T0 = synth.initial_scalar(3, g["zc"], Ny, Nx, noise=0.05)
+    velf = O.refine(full, U, V, W)
+    _, Tf = O.run(full, velf, T0, 3)
+    blk = _cfg(O, nx=B, ny=B, lx=B / n, ly=B / n, **kw)
+    reach = 3 * (2 if face_order == 4 else 1)
+    lo, hi = 2 * M + reach, (B - 2) * M - reach
+    for J0, I0 in ((0, 0), (5, 3), (10, 11)):
+        jj, ii = (J0 + np.arange(B)) % n, (I0 + np.arange(B)) % n
+        cut = lambda a: np.ascontiguousarray(a[:, jj][:, :, ii])
+        yd, xd = (M * J0 + np.arange(B * M)) % Ny, (M * I0 + np.arange(B * M)) % Nx
+        vb = O.refine(blk, cut(U), cut(V), cut(W))
+        _, Tb = O.run(blk, vb, np.ascontiguousarray(T0[:, yd][:, :, xd]), 3)
+        e = slice(2 * M, (B - 2) * M)
+        for full_face, block_face in zip(velf, vb):
+            assert np.abs(full_face[:, yd][:, :, xd][:, e, e] - block_face[:, e, e]).max() < 1e-14
+        assert np.abs(Tf[:, yd][:, :, xd][:, lo:hi, lo:hi] - Tb[:, lo:hi, lo:hi]).max() < 1e-14
