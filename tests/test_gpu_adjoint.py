@@ -142,3 +142,51 @@ def test_adjoint_config_128x128x96_200_steps(mr):
     assert abs(L - Lr) <= 1e-12 * abs(Lr)
     for a, b in zip(g, gr):
         assert np.abs(a - b).max() <= 1e-10 * np.abs(b).max()
+
+
+def test_differentiation_form_16_directions(mr):
+    """The differentiation form at full size (coarse 64x64x48 stretched ->
+    128x128x96, Pr = 7, Ra = 1e7, 200 steps, checkpoints every 20, loss =
+    bottom-plate Nu averaged over the last 50 steps), FP64 and FP32.
+    Along 16 seeded random directions: central differences (eps = 1e-6) of the
+    GPU forward for the initial scalar and the coarse velocity, and the
+    dot-product identity L(T0 + d) - L(T0) = <dL/dT0, d> for unit-size d (the
+    loss is affine in T0 at fixed velocity, so it holds beyond first order).
+    The FP32 gradients agree with the FP64 ones to the FP32 bar."""
+    p = Problem(64, 64, 48, gamma=1.5, ra=1e7, pr=7.0, rms=0.1, dt=1e-3)
+    vel = O.refine(p.cfg, p.U, p.V, p.W)
+    dt = O.cfl_dt(p.cfg, vel, 0.3)
+    p.cfg.dt = dt
+    p.kw["dt"] = dt
+    S, ck = 200, 20
+    wnu = np.zeros(S + 1)
+    wnu[-50:] = 1.0 / 50
+    L64, (gT, gU, gV, gW) = _gpu_grad(mr, p, mr.MR_F64, S, ck, wnu, None)
+    h = mr.mr_create(p.mr_config(mr, mr.MR_F64))
+
+    def loss(T0, U, V, W):
+        mr.mr_refine_velocity(h, dev(U), dev(V), dev(W))
+        mr.mr_set_scalar(h, dev(T0))
+        return mr.mr_adjoint_forward(h, S, ck, wnu, None)
+
+    rng = np.random.default_rng(1605)
+    eps = 1e-6
+    for _ in range(16):
+        d = rng.standard_normal(p.T0.shape)
+        d /= np.linalg.norm(d)
+        an = np.vdot(gT, d)
+        fd = (loss(p.T0 + eps * d, p.U, p.V, p.W) - loss(p.T0 - eps * d, p.U, p.V, p.W)) / (2 * eps)
+        assert abs(fd - an) <= 1e-6 * max(abs(an), 1e-3 * np.linalg.norm(gT))
+        assert abs(loss(p.T0 + d, p.U, p.V, p.W) - L64 - an) <= 1e-10 * max(1.0, abs(L64))
+        du = [rng.standard_normal(a.shape) for a in (p.U, p.V, p.W)]
+        nrm = np.sqrt(sum(np.vdot(b, b) for b in du))
+        du = [b / nrm for b in du]
+        an = sum(np.vdot(a, b) for a, b in zip((gU, gV, gW), du))
+        lp = loss(p.T0, *(a + eps * b for a, b in zip((p.U, p.V, p.W), du)))
+        lm = loss(p.T0, *(a - eps * b for a, b in zip((p.U, p.V, p.W), du)))
+        gnorm = np.sqrt(sum(np.vdot(a, a) for a in (gU, gV, gW)))
+        assert abs((lp - lm) / (2 * eps) - an) <= 1e-5 * max(abs(an), 1e-3 * gnorm)
+    L32, g32 = _gpu_grad(mr, p, mr.MR_F32, S, ck, wnu, None)
+    assert abs(L32 - L64) <= 1e-4 * abs(L64)
+    for a, b in zip(g32, (gT, gU, gV, gW)):
+        assert np.abs(a - b).max() <= 1e-3 * np.abs(b).max()
