@@ -171,21 +171,18 @@ def test_differentiation_form_16_directions(mr):
 
     rng = np.random.default_rng(1605)
     eps = 1e-6
+    floor = 1e-9 * max(1.0, abs(L64))     # rounding of a central difference of O(1) losses at eps = 1e-6
     for _ in range(16):
-        d = rng.standard_normal(p.T0.shape)
-        d /= np.linalg.norm(d)
+        d = rng.standard_normal(p.T0.shape)          # O(1) per cell
         an = np.vdot(gT, d)
         fd = (loss(p.T0 + eps * d, p.U, p.V, p.W) - loss(p.T0 - eps * d, p.U, p.V, p.W)) / (2 * eps)
-        assert abs(fd - an) <= 1e-6 * max(abs(an), 1e-3 * np.linalg.norm(gT))
-        assert abs(loss(p.T0 + d, p.U, p.V, p.W) - L64 - an) <= 1e-10 * max(1.0, abs(L64))
-        du = [rng.standard_normal(a.shape) for a in (p.U, p.V, p.W)]
-        nrm = np.sqrt(sum(np.vdot(b, b) for b in du))
-        du = [b / nrm for b in du]
+        assert abs(fd - an) <= 1e-6 * abs(an) + floor
+        assert abs(loss(p.T0 + d, p.U, p.V, p.W) - L64 - an) <= 1e-10 * max(1.0, abs(L64), abs(an))
+        du = [rng.standard_normal(a.shape) for a in (p.U, p.V, p.W)]   # O(1) per coarse face
         an = sum(np.vdot(a, b) for a, b in zip((gU, gV, gW), du))
         lp = loss(p.T0, *(a + eps * b for a, b in zip((p.U, p.V, p.W), du)))
         lm = loss(p.T0, *(a - eps * b for a, b in zip((p.U, p.V, p.W), du)))
-        gnorm = np.sqrt(sum(np.vdot(a, a) for a in (gU, gV, gW)))
-        assert abs((lp - lm) / (2 * eps) - an) <= 1e-5 * max(abs(an), 1e-3 * gnorm)
+        assert abs((lp - lm) / (2 * eps) - an) <= 1e-5 * abs(an) + floor
     L32, g32 = _gpu_grad(mr, p, mr.MR_F32, S, ck, wnu, None)
     assert abs(L32 - L64) <= 1e-4 * abs(L64)
     for a, b in zip(g32, (gT, gU, gV, gW)):
