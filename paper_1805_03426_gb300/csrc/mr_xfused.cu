@@ -34,45 +34,48 @@ namespace {
 
 using namespace ptx;
 
-constexpr int kTX = 64, kTY = 16;
-constexpr int kBX = kTX + 8, kBY = kTY + 2;            // scalar plane box (floats)
-constexpr int kPlaneFloats = kBX * kBY;
-constexpr int kPlaneSlot = ((kPlaneFloats * 4 + 127) / 128) * 128 / 4;
-constexpr uint32_t kPlaneBytes = kPlaneFloats * 4;
-constexpr int kThreads = 256;                           // consumer threads (8 warps)
-constexpr int kThreadsAll = kThreads + 32;              // + one producer warp
+constexpr int kTX = 64;                                // tile width (cells); the height TY is 16 or 8
+constexpr int kBX = kTX + 8;                            // scalar plane box width (floats)
 constexpr float kTBottom = 0.5f, kTTop = -0.5f;
 
 // O4: fourth-order face values of T^s (Section 2.2): the T^s box has two halo
 // rows each side and the layer constants carry the z-face weights.
-template <int M, bool MT, bool O4 = false>
+// TY: tile height; 16 consumer threads (4-cell segments) per row, one producer
+// warp; 64x16 tiles run two CTAs per SM, 64x8 tiles four (small grids).
+template <int M, bool MT, bool O4 = false, int TY = 16>
 struct XT {
+    static constexpr int CONS = 16 * TY;                // consumer threads
+    static constexpr int THREADS = CONS + 32;           // + one producer warp
+    static constexpr int CTAS = TY == 16 ? 2 : 4;       // resident CTAs per SM the layout is sized for
+    static constexpr int kBY = TY + 2;                  // rows of the T^{s-1} box
+    static constexpr uint32_t tm_bytes = (uint32_t)(kBX * kBY) * 4;
+    static constexpr int PM = (int)((tm_bytes + 127) / 128) * 128 / 4;
     static constexpr int CX = kTX / M;
     static constexpr int BXC = CX + 8;                  // coarse box width: columns I0-4 .. I0+CX+3
     // ring slots; MT (two velocity sets per slot) keeps two CTAs per SM with fewer
     // slots.  O4 keeps five planes live at a chunk's first layer (k0-2 .. k0+2),
     // so it needs at least five slots (at M = 2 with MT that leaves one CTA per SM).
-    static constexpr int NB0 = MT ? ((M == 4) ? 5 : 4) : ((M == 4) ? 7 : 6);
+    static constexpr int NB0 = MT ? ((M == 4) ? 5 : 4) : ((M == 4 && TY == 16) ? 7 : 6);
     static constexpr int NB = (O4 && NB0 < 5) ? 5 : NB0;
     // one ring slot (floats): T^n plane, T^{n-1} plane, then the velocity set of
     // one layer k: WY of its upper plane k+1 (its lower plane k is the previous
     // slot's), UO and VR of layer k; with MT the set of the second coarse time
     // level follows at offset DS; then the layer constants
-    static constexpr int BYN = O4 ? kTY + 4 : kBY;       // rows of the T^s box
+    static constexpr int BYN = O4 ? TY + 4 : kBY;        // rows of the T^s box
     static constexpr uint32_t tn_bytes = (uint32_t)(kBX * BYN) * 4;
     static constexpr int PN = (int)((tn_bytes + 127) / 128) * 128 / 4;
     static constexpr int LCW = O4 ? 20 : 12;            // floats of one row of layer constants
     static constexpr int oTn = 0, oTm = PN;
-    static constexpr int oWY = PN + kPlaneSlot;         // [TY][BXC]      plane k+1
-    static constexpr int oUO = oWY + kTY * BXC;         // [TY][BXC]
-    static constexpr int oVR = oUO + kTY * BXC;         // [TY+1][BXC]
-    static constexpr int SET = ((2 * kTY + kTY + 1) * BXC + 31) / 32 * 32;   // one set, 128-B multiple
+    static constexpr int oWY = PN + PM;                 // [TY][BXC]      plane k+1
+    static constexpr int oUO = oWY + TY * BXC;          // [TY][BXC]
+    static constexpr int oVR = oUO + TY * BXC;          // [TY+1][BXC]
+    static constexpr int SET = ((2 * TY + TY + 1) * BXC + 31) / 32 * 32;     // one set, 128-B multiple
     static constexpr int DS = MT ? SET : 0;
     static constexpr int oLC = oWY + (MT ? 2 : 1) * SET;                     // [LCW] layer constants
     static constexpr int slot = (((oLC + (O4 ? 20 : 16)) * 4 + 127) / 128) * 128 / 4;
     static constexpr int NSET = MT ? 2 : 1;
-    static constexpr uint32_t wy_bytes = (uint32_t)(NSET * kTY * BXC) * 4;
-    static constexpr uint32_t bundle_bytes = (uint32_t)(NSET * (kTY * BXC + (kTY + 1) * BXC) + LCW) * 4;  // UO, VR, LC
+    static constexpr uint32_t wy_bytes = (uint32_t)(NSET * TY * BXC) * 4;
+    static constexpr uint32_t bundle_bytes = (uint32_t)(NSET * (TY * BXC + (TY + 1) * BXC) + LCW) * 4;  // UO, VR, LC
     static constexpr int oRed = NB * slot;              // 64 floats
     static constexpr int oBar = ((oRed + 64) * 4 + 7) / 8;
     static constexpr size_t bytes = (size_t)(oBar + 2 * NB) * 8;
@@ -111,15 +114,16 @@ __device__ __forceinline__ float rsplit(const float (&r)[3], float c0, float c1,
 // O4: fourth-order face values of T^s (Section 2.2).  Ring r then carries plane
 // k0-2+r (one more plane below and above the chunk) and the consumers carry the
 // z-face advective flux of plane k+1 to the next layer.
-template <int M, int KIND, bool LF, bool MT, bool O4>
-__global__ void __launch_bounds__(kThreadsAll, 2)
+template <int M, int KIND, bool LF, bool MT, bool O4, int TY>
+__global__ void __launch_bounds__(XT<M, MT, O4, TY>::THREADS, XT<M, MT, O4, TY>::CTAS)
 k_xfused(const __grid_constant__ CUtensorMap tmn, const __grid_constant__ CUtensorMap tmm,
          const __grid_constant__ CUtensorMap twy, const __grid_constant__ CUtensorMap tuo,
          const __grid_constant__ CUtensorMap tvr, const __grid_constant__ CUtensorMap tlc,
          const __grid_constant__ CUtensorMap twy1, const __grid_constant__ CUtensorMap tuo1,
          const __grid_constant__ CUtensorMap tvr1, const XArgs A)
 {
-    using L = XT<M, MT, O4>;
+    using L = XT<M, MT, O4, TY>;
+    constexpr int kThreads = L::CONS;
     constexpr int NB = L::NB, BXC = L::BXC, NC = 4 / M, NW = kThreads / 32;
     constexpr bool DIVONLY = KIND != 0;
     constexpr int OFF = O4 ? 2 : 1;                  // ring r carries plane k0 - OFF + r
@@ -130,7 +134,7 @@ k_xfused(const __grid_constant__ CUtensorMap tmn, const __grid_constant__ CUtens
 
     const Grid<float>& g = A.g;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int i0 = blockIdx.y * kTX, j0 = blockIdx.z * kTY;
+    const int i0 = blockIdx.y * kTX, j0 = blockIdx.z * TY;
     const int I0 = i0 / M;
     const int k0 = blockIdx.x * A.kcl;
     const int k1 = min(k0 + A.kcl, g.Nz);
@@ -160,7 +164,7 @@ k_xfused(const __grid_constant__ CUtensorMap tmn, const __grid_constant__ CUtens
             const int p = k0 - OFF + r;              // plane of this ring
             const bool wy = (p >= k0 && p <= k1), bundle = (p - 1 >= k0 && p - 1 < k1);
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-            mbar_expect_tx(&full[s], (DIVONLY ? 0u : L::tn_bytes + kPlaneBytes) + (wy ? L::wy_bytes : 0u) +
+            mbar_expect_tx(&full[s], (DIVONLY ? 0u : L::tn_bytes + L::tm_bytes) + (wy ? L::wy_bytes : 0u) +
                                          (bundle ? L::bundle_bytes : 0u));
             if (!DIVONLY) {
                 tma_3d(slot + L::oTn, &tmn, i0 - 4, j0 - (O4 ? 2 : 1), p, &full[s]);
@@ -192,7 +196,7 @@ k_xfused(const __grid_constant__ CUtensorMap tmn, const __grid_constant__ CUtens
     const int il0 = seg * 4, cb0 = il0 / M;      // first coarse column of the segment (tile-local)
     const auto& rx = A.rx;
     const bool wrap_w = (i0 == 0 && seg == 0), wrap_e = (i0 + kTX == g.Nx && seg == 15);
-    const bool wrap_s = (j0 == 0 && jl == 0), wrap_n = (j0 + kTY == g.Ny && jl == kTY - 1);
+    const bool wrap_s = (j0 == 0 && jl == 0), wrap_n = (j0 + TY == g.Ny && jl == TY - 1);
 
     bool fail = false;
     float dmax = 0.f;
@@ -320,7 +324,7 @@ k_xfused(const __grid_constant__ CUtensorMap tmn, const __grid_constant__ CUtens
                 float dw = __shfl_up_sync(0xffffffffu, dc4.w, 1), de = __shfl_down_sync(0xffffffffu, dc4.x, 1);
                 if (seg == 0) { tw1 = Pn_c[o4 - 1]; tw2 = Pn_c[o4 - 2]; dw = Pm_c[o - 1]; }
                 if (seg == 15) { te1 = Pn_c[o4 + 4]; te2 = Pn_c[o4 + 5]; de = Pm_c[o + 4]; }
-                const bool ws2 = (j0 == 0 && jl < 2), wn2 = (j0 + kTY == g.Ny && jl >= kTY - 2);
+                const bool ws2 = (j0 == 0 && jl < 2), wn2 = (j0 + TY == g.Ny && jl >= TY - 2);
                 if (wrap_w | wrap_e | ws2 | wn2) {
                     // the box holds zeros beyond the domain: fetch the periodic images
                     const float* gn = A.Tn + (size_t)k * plane;
@@ -336,11 +340,11 @@ k_xfused(const __grid_constant__ CUtensorMap tmn, const __grid_constant__ CUtens
                         ts24 = *reinterpret_cast<const float4*>(gn + (size_t)(g.Ny - 2 + jl) * g.Nx + col);
                     }
                     if (wn2) {                    // rows jl+1 (jl = TY-1) and jl+2 above row Ny-1
-                        if (jl == kTY - 1) {
+                        if (jl == TY - 1) {
                             tn4 = *reinterpret_cast<const float4*>(gn + col);
                             dn4 = *reinterpret_cast<const float4*>(gm + col);
                         }
-                        tn24 = *reinterpret_cast<const float4*>(gn + (size_t)(jl - (kTY - 2)) * g.Nx + col);
+                        tn24 = *reinterpret_cast<const float4*>(gn + (size_t)(jl - (TY - 2)) * g.Nx + col);
                     }
                 }
                 const float4 db4 = *reinterpret_cast<const float4*>(Pm_b + o);
@@ -640,16 +644,16 @@ struct XSet {
     const float *wy, *uo, *vr;
 };
 
-template <int M, int KIND, bool LF, bool MT, bool O4>
-cudaError_t launch_x(const Grid<float>& g, XSet v0, XSet v1, float alpha, int nxg, const float* lc, int lcw,
-                     const float* rx12, const float* w4, const float* Tm1, const float* T, float* Tp1, StepCoef c,
-                     int* err, unsigned long long* divmax, cudaStream_t st)
+template <int M, int KIND, bool LF, bool MT, bool O4, int TY>
+cudaError_t launch_xt(const Grid<float>& g, XSet v0, XSet v1, float alpha, int nxg, const float* lc, int lcw,
+                      const float* rx12, const float* w4, const float* Tm1, const float* T, float* Tp1, StepCoef c,
+                      int* err, unsigned long long* divmax, cudaStream_t st)
 {
-    using L = XT<M, MT, O4>;
+    using L = XT<M, MT, O4, TY>;
     if (lcw < L::LCW) return cudaErrorInvalidValue;
     static unsigned long long attr = 0;                   // one bit per device
     constexpr bool DIVONLY = KIND != 0;
-    cudaError_t e = smem_optin(reinterpret_cast<const void*>(k_xfused<M, KIND, LF, MT, O4>), (int)L::bytes, &attr);
+    cudaError_t e = smem_optin(reinterpret_cast<const void*>(k_xfused<M, KIND, LF, MT, O4, TY>), (int)L::bytes, &attr);
     if (e != cudaSuccess) return e;
     CUtensorMap mn, mm, mwy, muo, mvr, mlc, mwy1, muo1, mvr1;
     memset(&mn, 0, sizeof mn);
@@ -658,24 +662,24 @@ cudaError_t launch_x(const Grid<float>& g, XSet v0, XSet v1, float alpha, int nx
     memset(&muo1, 0, sizeof muo1);
     memset(&mvr1, 0, sizeof mvr1);
     if (!DIVONLY && (!cached_map3(&mn, T, g.Nx, g.Ny, g.Nz, kBX, L::BYN, 1) ||
-                     !cached_map3(&mm, Tm1, g.Nx, g.Ny, g.Nz, kBX, kBY, 1)))
+                     !cached_map3(&mm, Tm1, g.Nx, g.Ny, g.Nz, kBX, L::kBY, 1)))
         return cudaErrorInvalidValue;
     auto set_maps = [&](const XSet& v, CUtensorMap* wy, CUtensorMap* uo, CUtensorMap* vr) {
-        return cached_map3(wy, v.wy, nxg, g.Ny, g.Nz + 1, L::BXC, kTY, 1) &&
-               cached_map3(uo, v.uo, nxg, g.Ny, g.Nz, L::BXC, kTY, 1) &&
-               cached_map3(vr, v.vr, nxg, g.Ny + 1, g.Nz, L::BXC, kTY + 1, 1);
+        return cached_map3(wy, v.wy, nxg, g.Ny, g.Nz + 1, L::BXC, TY, 1) &&
+               cached_map3(uo, v.uo, nxg, g.Ny, g.Nz, L::BXC, TY, 1) &&
+               cached_map3(vr, v.vr, nxg, g.Ny + 1, g.Nz, L::BXC, TY + 1, 1);
     };
     if (!set_maps(v0, &mwy, &muo, &mvr) || (MT && !set_maps(v1, &mwy1, &muo1, &mvr1)) ||
         !cached_map3(&mlc, lc, lcw, g.Nz, 1, L::LCW, 1, 1))
         return cudaErrorInvalidValue;
-    const int tiles = (g.Nx / kTX) * (g.Ny / kTY);
+    const int tiles = (g.Nx / kTX) * (g.Ny / TY);
     int kcl = kcl_override();
     if (kcl <= 0) {
-        // ~12 waves at 2 CTAs / SM, but no chunk longer than 96 layers: on large
-        // grids long chunks leave the resident CTAs far apart in z (measured on
-        // 1536 x 1536 x 1024: 512 layers 8.8 ms, 64-128 layers 7.0 ms, 96 layers
-        // 6.8 ms per step)
-        const int want = 152 * 2 * 12;
+        // ~12 waves of resident CTAs, but no chunk longer than 96 layers: on
+        // large grids long chunks leave the resident CTAs far apart in z
+        // (measured on 1536 x 1536 x 1024: 512 layers 8.8 ms, 64-128 layers
+        // 7.0 ms, 96 layers 6.8 ms per step)
+        const int want = 152 * L::CTAS * 12;
         int chunks = (want + tiles - 1) / tiles;
         chunks = max(1, min(chunks, g.Nz / 4));
         kcl = min((g.Nz + chunks - 1) / chunks, 96);
@@ -687,9 +691,37 @@ cudaError_t launch_x(const Grid<float>& g, XSet v0, XSet v1, float alpha, int nx
         memcpy(A.w4x, w4, sizeof A.w4x);
         memcpy(A.w4y, w4 + 4, sizeof A.w4y);
     }
-    dim3 grid(chunks, g.Nx / kTX, g.Ny / kTY);
-    k_xfused<M, KIND, LF, MT, O4><<<grid, kThreadsAll, L::bytes, st>>>(mn, mm, mwy, muo, mvr, mlc, mwy1, muo1, mvr1, A);
+    dim3 grid(chunks, g.Nx / kTX, g.Ny / TY);
+    k_xfused<M, KIND, LF, MT, O4, TY><<<grid, L::THREADS, L::bytes, st>>>(mn, mm, mwy, muo, mvr, mlc, mwy1, muo1, mvr1, A);
     return cudaGetLastError();
+}
+
+// Tile height: 64x16 tiles (two CTAs per SM) when the grid offers at least
+// ~8 waves of them in chunks of 96 layers, else 64x8 tiles (four CTAs per SM,
+// so that a small grid still overlaps the chunks' start-up; 512 x 512 x 384:
+// 0.315 -> 0.306 ms per step, while 1536 x 1536 x 1024 prefers 64x16).
+// MR_XFUSED_TY in the environment forces 8 or 16 (used for tuning).
+int tile_rows(const Grid<float>& g)
+{
+    static int forced = -1;
+    if (forced < 0) {
+        const char* e = getenv("MR_XFUSED_TY");
+        forced = e ? atoi(e) : 0;
+    }
+    if (forced == 8 || forced == 16) return forced;
+    const long long tiles16 = (long long)(g.Nx / kTX) * (g.Ny / 16), chunks96 = (g.Nz + 95) / 96;
+    return tiles16 * chunks96 >= 152LL * 2 * 8 ? 16 : 8;
+}
+
+template <int M, int KIND, bool LF, bool MT, bool O4>
+cudaError_t launch_x(const Grid<float>& g, XSet v0, XSet v1, float alpha, int nxg, const float* lc, int lcw,
+                     const float* rx12, const float* w4, const float* Tm1, const float* T, float* Tp1, StepCoef c,
+                     int* err, unsigned long long* divmax, cudaStream_t st)
+{
+    if (tile_rows(g) == 16)
+        return launch_xt<M, KIND, LF, MT, O4, 16>(g, v0, v1, alpha, nxg, lc, lcw, rx12, w4, Tm1, T, Tp1, c, err, divmax,
+                                                  st);
+    return launch_xt<M, KIND, LF, MT, O4, 8>(g, v0, v1, alpha, nxg, lc, lcw, rx12, w4, Tm1, T, Tp1, c, err, divmax, st);
 }
 
 template <int M, bool O4>
