@@ -237,6 +237,24 @@ def run_mr(args):
             "kernel": kname,
             "bytes_per_cell": round(bytes_per_cell, 3), "launch_ms": round(per_launch * 1e3, 4)}
 
+    # the per-call costs around the step: statistics (the call synchronises:
+    # wall clock) and plate Nu (asynchronous: stream-timed)
+    aux = None
+    if rank == 0:
+        nu = torch.zeros(2, dtype=torch.float64, device="cuda")
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(10):
+            mr.mr_scalar_stats(h, stream=stream, allow_nonfinite=True)
+        ts = (time.perf_counter() - t0) / 10
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(50):
+            mr.mr_plate_nu(h, nu, stream=stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        aux = {"mr_scalar_stats_ms": round(ts * 1e3, 4), "mr_plate_nu_ms": round(e0.elapsed_time(e1) / 50, 4)}
+
     # temporal refinement (Section 3.4): coarse steps of mt dense steps each,
     # the next coarse velocity resident on the device
     temporal = None
@@ -311,7 +329,8 @@ def run_mr(args):
                        "velocity_mode": args.mode, "dt": dt, "parallelism": f"replicas{world}",
                        "l2": "inputs larger than L2 (3 scalar levels of %.0f MB)" % (cells * elt / 2**20),
             "bytes_per_cell": round(bytes_per_cell, 3)},
-            "roofline": roof, "fp64_path": fp64, "adjoint": adj, "temporal": temporal, "face_order4": face4, "e2e": e2e,
+            "roofline": roof, "fp64_path": fp64, "adjoint": adj, "temporal": temporal, "face_order4": face4,
+            "per_call": aux, "e2e": e2e,
             "cpu_baseline": cpu,
             "gpu_launches": args.steps, "clocks": clk.summary(),
             "final_stats": {k: st[k] for k in ("nu_bot", "nu_top", "mean", "var")},

@@ -718,10 +718,18 @@ cudaError_t launch_x(const Grid<float>& g, XSet v0, XSet v1, float alpha, int nx
                      const float* rx12, const float* w4, const float* Tm1, const float* T, float* Tp1, StepCoef c,
                      int* err, unsigned long long* divmax, cudaStream_t st)
 {
-    if (tile_rows(g) == 16)
+    // fourth order keeps 64x16 tiles: its five live planes want the deeper ring
+    // (64x8 tiles measured 0.89 ms per step on 512 x 512 x 384)
+    if constexpr (O4) {
         return launch_xt<M, KIND, LF, MT, O4, 16>(g, v0, v1, alpha, nxg, lc, lcw, rx12, w4, Tm1, T, Tp1, c, err, divmax,
                                                   st);
-    return launch_xt<M, KIND, LF, MT, O4, 8>(g, v0, v1, alpha, nxg, lc, lcw, rx12, w4, Tm1, T, Tp1, c, err, divmax, st);
+    } else {
+        if (tile_rows(g) == 16)
+            return launch_xt<M, KIND, LF, MT, O4, 16>(g, v0, v1, alpha, nxg, lc, lcw, rx12, w4, Tm1, T, Tp1, c, err,
+                                                      divmax, st);
+        return launch_xt<M, KIND, LF, MT, O4, 8>(g, v0, v1, alpha, nxg, lc, lcw, rx12, w4, Tm1, T, Tp1, c, err, divmax,
+                                                 st);
+    }
 }
 
 template <int M, bool O4>
