@@ -46,7 +46,7 @@ template <int M, bool MT, bool O4 = false, int TY = 16>
 struct XT {
     static constexpr int CONS = 16 * TY;                // consumer threads
     static constexpr int THREADS = CONS + 32;           // + one producer warp
-    static constexpr int CTAS = TY == 16 ? 2 : 4;       // resident CTAs per SM the layout is sized for
+    static constexpr int CTAS = TY == 16 ? 2 : (O4 ? 3 : 4);   // resident CTAs per SM the layout is sized for
     static constexpr int kBY = TY + 2;                  // rows of the T^{s-1} box
     static constexpr uint32_t tm_bytes = (uint32_t)(kBX * kBY) * 4;
     static constexpr int PM = (int)((tm_bytes + 127) / 128) * 128 / 4;
@@ -56,7 +56,7 @@ struct XT {
     // slots.  O4 keeps five planes live at a chunk's first layer (k0-2 .. k0+2),
     // so it needs at least five slots (at M = 2 with MT that leaves one CTA per SM).
     static constexpr int NB0 = MT ? ((M == 4) ? 5 : 4) : ((M == 4 && TY == 16) ? 7 : 6);
-    static constexpr int NB = (O4 && NB0 < 5) ? 5 : NB0;
+    static constexpr int NB = (O4 && TY == 8 && !MT) ? 7 : ((O4 && NB0 < 5) ? 5 : NB0);
     // one ring slot (floats): T^n plane, T^{n-1} plane, then the velocity set of
     // one layer k: WY of its upper plane k+1 (its lower plane k is the previous
     // slot's), UO and VR of layer k; with MT the set of the second coarse time
@@ -718,9 +718,11 @@ cudaError_t launch_x(const Grid<float>& g, XSet v0, XSet v1, float alpha, int nx
                      const float* rx12, const float* w4, const float* Tm1, const float* T, float* Tp1, StepCoef c,
                      int* err, unsigned long long* divmax, cudaStream_t st)
 {
-    // fourth order keeps 64x16 tiles: its five live planes want the deeper ring
-    // (64x8 tiles measured 0.89 ms per step on 512 x 512 x 384)
-    if constexpr (O4) {
+    // fourth order with two velocity levels keeps 64x16 tiles (its 64x8 ring
+    // would be too shallow for the five live planes); single-level fourth order
+    // on 64x8 tiles runs three CTAs per SM with a 7-slot ring and 128 registers
+    // (512 x 512 x 384: 0.39 ms per step, vs 0.46 on 64x16 tiles)
+    if constexpr (O4 && MT) {
         return launch_xt<M, KIND, LF, MT, O4, 16>(g, v0, v1, alpha, nxg, lc, lcw, rx12, w4, Tm1, T, Tp1, c, err, divmax,
                                                   st);
     } else {
