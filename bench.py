@@ -4,13 +4,16 @@ Workload (default): the FP32 precision form -- coarse 128x128x96 (tanh-stretched
 z, gamma 1.5), refinement 4 -> dense 512x512x384 (100,663,296 cells), Sc = 100,
 Ra = 1e9, dt from CFL 0.3 on the refined synthetic velocity.  One step = one
 pass of the whole hot path over the grid: the divergence-free refinement of
-the coarse velocity and the finite-volume scalar update (fused into one kernel
-in MR_VEL_FUSED mode, the refinement amortised in MR_VEL_STORED mode).
+the coarse velocity and the finite-volume scalar update.  Default mode
+MR_VEL_XFUSED: one kernel launch per step forms the dense velocity in registers
+(x-stage of the refinement) from the z- and y-stage results kept at coarse x
+resolution, and updates the scalar; the dense velocity is never stored.
 
 Prints one JSON line (rank 0).  Metric: dense cell-updates per second.  Beside
-it: the FP64 path on the same grid, the roofline fraction of the dominant
-kernel (CUDA events, algorithmic bytes), the end-to-end rate through the C-ABI
-with host buffers, and the FP64 CPU oracle timed on this host's cores.
+it: the roofline fraction of the dominant kernel (CUDA events, algorithmic
+bytes), the FP64 path on the same grid, the adjoint's cost, temporal
+refinement, fourth-order faces, per-call costs, the end-to-end rate through the
+C-ABI with host buffers, and the FP64 CPU oracle timed on this host's cores.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl mr|reference]
 """
@@ -53,6 +56,14 @@ NCU_TRAFFIC = {
     ("k_xfused", "rb512_stretched_f32"): {"bytes": 1198593000 + 384998400, "sources": "b6249ba9d53f7a08.8945e0b384d6ff21",
                                           "files": ("mr_xfused.cu", "mr_ptx.cuh")},
 }
+
+
+# Floating-point operations of one stored-velocity step per cell in the
+# interior (an FMA counts two): per x or y face 3 for the advective flux and 2
+# for the diffusive difference (20), per z face 5 and 3 (16), and 15 to
+# assemble C, D and the Euler-leapfrog update.
+FP64_FLOPS_PER_CELL = 51
+FP64_NOMINAL_TFLOPS = 1.25   # GB300 FP64 (non-tensor), nominal
 
 
 def _traffic(kernel, workload):
@@ -282,8 +293,16 @@ def run_mr(args):
         k64 = max(10, args.steps // 10)
         t64 = _time_steps(torch, mr, h64, k64, 3, stream)
         v64 = cells * k64 / t64 / 1e9
+        # the FP64 step is bound by GB300's FP64 pipe: report it against the
+        # nominal FP64 rate (no measured FP64 peak) and against HBM
+        flops64 = FP64_FLOPS_PER_CELL * v64 * 1e9 / 1e12
         fp64 = {"value": round(v64, 3), "unit": "Gcell-updates/s", "steps": k64,
-                "ms_per_step": round(t64 / k64 * 1e3, 4), "fp32_over_fp64": round(value / world / v64, 2)}
+                "ms_per_step": round(t64 / k64 * 1e3, 4), "fp32_over_fp64": round(value / world / v64, 2),
+                "fp64_pipe": {"tflops": round(flops64, 3), "flops_per_cell": FP64_FLOPS_PER_CELL,
+                              "peak": FP64_NOMINAL_TFLOPS, "peak_source": "nominal",
+                              "frac": round(flops64 / FP64_NOMINAL_TFLOPS, 4)},
+                "hbm": {"achieved": round(48 * v64, 1), "unit": "GB/s", "bytes_per_cell": 48,
+                        "frac": round(48 * v64 / peak, 4)}}
         h64.close()
 
     # end to end through the C-ABI with host buffers: per step the coarse
