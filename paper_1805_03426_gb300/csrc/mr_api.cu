@@ -457,6 +457,8 @@ int mr_create(const mr_config* cfg, mr_handle* out)
         alloc((void**)&b.xvr, (size_t)h->Nz * (h->Ny + 1) * b.nxg * 4);
         alloc((void**)&b.xlc, (size_t)h->Nz * 20 * 4);
         alloc(&b.scrW, (size_t)(h->Nz + 1) * c.ny * c.nx * h->elt);
+    } else if (c.velocity_mode == MR_VEL_FUSED) {
+        alloc((void**)&b.xlc, (size_t)h->Nz * 12 * 4);   // layer constants of the fused step
     }
     if (e != cudaSuccess) {
         int r = cuda_check(e, "mr_create: device allocation");
@@ -644,7 +646,8 @@ static int one_step(mr_handle h, double alpha, cudaStream_t st)
             U = Lu; V = Lv; W = Lw;
         }
         if (e == cudaSuccess)
-            e = launch_step_fused_f32(h->g32, U, V, W, (const float*)Tm1, (const float*)b.T[h->ic], (float*)b.T[in], c, st);
+            e = launch_step_fused_f32(h->g32, U, V, W, b.xlc, b.xrx, (const float*)Tm1, (const float*)b.T[h->ic],
+                                       (float*)b.T[in], c, st);
     } else {
         const float* A[3] = {(const float*)b.Us, (const float*)b.Vs, (const float*)b.Ws};
         const float* B[3] = {(const float*)nx.Us, (const float*)nx.Vs, (const float*)nx.Ws};
@@ -838,8 +841,8 @@ static int max_divergence(mr_handle h, double* out, cudaStream_t st)
     if (h->cfg.velocity_mode == MR_VEL_XFUSED)
         e = launch_xfused_max_f32(h->g32, 1, b.xwy, b.xuo, b.xvr, b.nxg, b.xlc, b.xlcw, b.xrx, b.red, h->red_blocks, st);
     else if (h->cfg.velocity_mode == MR_VEL_FUSED)
-        e = launch_maxdiv_fused_f32(h->g32, (const float*)b.Uc, (const float*)b.Vc, (const float*)b.Wc, b.red,
-                                    h->red_blocks, st);
+        e = launch_fused_max_f32(h->g32, 1, (const float*)b.Uc, (const float*)b.Vc, (const float*)b.Wc, b.xlc, b.xrx,
+                                  b.red, h->red_blocks, st);
     else if (h->cfg.precision == MR_F64)
         e = launch_maxdiv<double>(h->g64, (const double*)b.Us, (const double*)b.Vs, (const double*)b.Ws, b.red,
                                   h->red_blocks, st);
@@ -911,6 +914,10 @@ int mr_cfl_dt(mr_handle h, double cfl, double* dt_out, mr_stream stream)
     if (h->cfg.velocity_mode == MR_VEL_XFUSED) {
         // the split-x kernel forms the dense faces in registers: one pass, no dense storage
         e = launch_xfused_max_f32(h->g32, 2, b.xwy, b.xuo, b.xvr, b.nxg, b.xlc, b.xlcw, b.xrx, b.red, h->red_blocks, st);
+    } else if (h->cfg.velocity_mode == MR_VEL_FUSED) {
+        // the fused kernel forms the dense faces in registers from the coarse ones
+        e = launch_fused_max_f32(h->g32, 2, (const float*)b.Uc, (const float*)b.Vc, (const float*)b.Wc, b.xlc, b.xrx,
+                                  b.red, h->red_blocks, st);
     } else if (h->cfg.velocity_mode != MR_VEL_STORED) {
         // dense faces are not kept: refine into temporary buffers once
         void *a = nullptr, *bb = nullptr, *c = nullptr;
@@ -926,7 +933,7 @@ int mr_cfl_dt(mr_handle h, double cfl, double* dt_out, mr_stream stream)
         us = a; vs = bb; ws = c;
         tmp = true;
     }
-    if (h->cfg.velocity_mode != MR_VEL_XFUSED)
+    if (h->cfg.velocity_mode == MR_VEL_STORED || tmp)
         e = h->cfg.precision == MR_F64
                 ? launch_cfl<double>(h->g64, (const double*)us, (const double*)vs, (const double*)ws, b.red, h->red_blocks, st)
                 : launch_cfl<float>(h->g32, (const float*)us, (const float*)vs, (const float*)ws, b.red, h->red_blocks, st);
@@ -934,8 +941,8 @@ int mr_cfl_dt(mr_handle h, double cfl, double* dt_out, mr_stream stream)
     int rc = e != cudaSuccess ? cuda_check(e, "mr_cfl_dt: launch") : reduce_partials(h, 1, p, st);
     if (tmp) { cudaFree((void*)us); cudaFree((void*)vs); cudaFree((void*)ws); }
     if (rc) return rc;
-    if (h->cfg.velocity_mode == MR_VEL_XFUSED && fused_take_error(st) == MR_ERR_TIMEOUT)
-        return set_error(MR_ERR_TIMEOUT, "mr_cfl_dt: the split-x kernel gave up a bounded wait");
+    if (h->cfg.velocity_mode != MR_VEL_STORED && fused_take_error(st) == MR_ERR_TIMEOUT)
+        return set_error(MR_ERR_TIMEOUT, "mr_cfl_dt: a fused kernel gave up a bounded wait");
     double m = 0.0;
     for (double v : p) m = std::max(m, v);
     if (!(m > 0)) return set_error(MR_ERR_ARG, "mr_cfl_dt: zero velocity");

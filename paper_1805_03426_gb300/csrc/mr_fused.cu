@@ -1,28 +1,31 @@
-// Fused FP32 refine + scalar-step kernel (MR_VEL_FUSED).
+// MR_VEL_FUSED: the FP32 step kernel with every stage of the refinement
+// (Section 3.2) inside it, from the coarse faces.  The refined velocity, and
+// every intermediate of the refinement, lives in shared memory and registers
+// only; per step the kernel reads the coarse faces, T^s and T^{s-1} and
+// writes T^{s+1}.
 //
-// One CTA owns a 64 x 16 column of dense cells (x by y) and marches up a chunk
-// of coarse layers.  Per coarse layer K it loads the coarse U, V, W it needs
-// (a one-coarse-cell halo, periodic wrap) with cp.async, forms the z-splits
-// and the full-area vertical fluxes of every column by slab balance (stage Z
-// of the refinement, Section 3.2); per dense layer it then builds, entirely
-// in shared memory, the refined W on the layer's top plane (R_y then R_x),
-// the outer U sub-faces, the full-width V of every dense row by row balance
-// (stage Y), the refined V (R_x), and the inner U by cell balance (stage X),
-// and finally applies the second-order finite-volume update (Eq. 5) with the
-// Euler-leapfrog coefficients (Section 2.2).  The refined velocity never
-// touches HBM.
-//
-// The two scalar levels T^n and T^{n-1} stream through a ring of NB dense
-// planes per field, each a (64+8) x (16+2) box fetched by TMA
-// (cp.async.bulk.tensor) onto an mbarrier; the x box starts 4 cells left of
-// the tile so that the copy stays 16-byte aligned.  Where the tile touches the
-// periodic edge, the wrapped halo column / row is patched in with plain loads.
-// Every mbarrier wait is bounded: on time-out the CTA records MR_ERR_TIMEOUT
-// in a device flag and leaves.
+// One CTA owns a 64 x 8 column of dense cells and marches a chunk of coarse
+// slabs.  At the start of each slab K its 128 consumer threads compute, from
+// the coarse U, V, W (global, L1/L2-resident), the slab's refinement stages at
+// coarse resolution in x, for the tile's rows and the bundle columns
+// I0-4 .. I0+CX+3 (periodic images):
+//   - stage Z: the slab balance of every coarse column (full-area W on the
+//     slab's inner dense planes), top-down;
+//   - WY: R_y of the full-area W on the slab's M+1 dense planes;
+//   - UO: the outer U sub-faces (R_y R_z of U) in units of U / (2 dx);
+//   - VR: the full-coarse-width V on every dense y-face of the tile (R_z of V
+//     on the coarse faces, row balance of stage Y on the inner ones) in units
+//     of V / (2 dy);
+// separated by consumer-only barriers.  Each dense layer then runs exactly the
+// split-x step (stage X -- R_x splits and the west-to-east cell balance -- in
+// registers, then the finite-volume update of Eq. 5 with the Euler-leapfrog
+// coefficients of Section 2.2), with T^s, T^{s-1} and the layer constants
+// streamed by one producer warp through a TMA ring on full/empty mbarriers.
+// Every wait is bounded: on time-out the kernel records MR_ERR_TIMEOUT in a
+// device flag.
 //
 // Supported: FP32, periodic x and y, mx = my = mz = M in {2, 4},
-// Nx % 64 == 0, Ny % 16 == 0, explicit diffusion.
-#include <cuda.h>
+// Nx % 64 == 0, Ny % 16 == 0, explicit diffusion, second-order faces.
 #include <stdlib.h>
 #include <string.h>
 
@@ -36,85 +39,220 @@ namespace {
 
 using namespace ptx;
 
-constexpr int kTX = 64, kTY = 16;
-constexpr int kBX = kTX + 8, kBY = kTY + 2;           // TMA box (floats)
-constexpr int kPlaneFloats = kBX * kBY;                // 1296
-constexpr int kSlotFloats = ((kPlaneFloats * 4 + 127) / 128) * 128 / 4;  // 128-byte aligned slot
-constexpr int kThreads = 256;                          // consumer threads (8 warps)
-constexpr int kThreadsAll = kThreads + 32;             // + one producer warp
-constexpr uint32_t kPlaneBytes = kPlaneFloats * 4;
-constexpr float kTBottom = 0.5f, kTTop = -0.5f;
+constexpr int kTX = 64, kTY = 8;                        // tile (cells)
+constexpr int kBX = kTX + 8, kBY = kTY + 2;             // scalar plane box (floats)
+constexpr int kCons = 16 * kTY;                         // consumer threads: 4-cell segments
+constexpr int kThreadsAll = kCons + 32;                 // + one producer warp
+constexpr int kLCW = 12;                                // layer-constant row (floats)
 
 template <int M>
-struct Tile {
-    static constexpr int CX = kTX / M, CY = kTY / M;
-    static constexpr int UX = CX + 3, UY = CY + 2;     // U faces I0-1..I0+CX+1, rows J0-1..J0+CY
-    static constexpr int VX = CX + 2, VY = CY + 3;     // V cells I0-1..I0+CX, faces J0-1..J0+CY+1
-    static constexpr int WX = CX + 2, WY = CY + 2;     // W columns I0-1..I0+CX, J0-1..J0+CY
-    static constexpr int NB = (M == 4) ? 6 : 5;        // dense planes resident per field
-    // shared-memory layout (floats), T ring first (128-byte aligned slots)
-    static constexpr int oT = 0;
-    static constexpr int oCU = oT + NB * 2 * kSlotFloats;
-    static constexpr int oCV = oCU + 2 * 3 * UY * UX;
-    static constexpr int oCW = oCV + 2 * 3 * VY * VX;
-    static constexpr int oUz = oCW + 2 * 2 * WY * WX;
-    static constexpr int oVz = oUz + M * UY * UX;
-    static constexpr int oWc = oVz + M * VY * VX;
-    static constexpr int oWy = oWc + (M + 1) * WY * WX;
-    static constexpr int oUo = oWy + (M + 1) * kTY * WX;
-    static constexpr int oVr = oUo + M * kTY * UX;
-    static constexpr int oRy = oVr + M * (kTY + 1) * VX;
-    static constexpr int oLc = oRy + kTY * 3;          // [M][kLc] per-layer constants of the slab
-    static constexpr int oRed = oLc + M * 12;
-    static constexpr int oBar = ((oRed + 64) * 4 + 7) / 8;  // in uint64 units: full[NB], empty[NB]
+struct FX {
+    static constexpr int CX = kTX / M, CY = kTY / M;    // coarse cells of the tile
+    static constexpr int BXC = CX + 8;                  // bundle columns I0-4 .. I0+CX+3
+    static constexpr int NB = 6;                        // ring slots
+    static constexpr uint32_t plane_bytes = (uint32_t)(kBX * kBY) * 4;
+    static constexpr int PS = (int)((plane_bytes + 127) / 128) * 128 / 4;
+    // ring slot (floats): T^s plane, T^{s-1} plane, the layer constants
+    static constexpr int oTn = 0, oTm = PS, oLC = 2 * PS;
+    static constexpr int slot = (((oLC + 16) * 4 + 127) / 128) * 128 / 4;
+    // the slab's intermediates: WY [M+1][TY][BXC], UO [M][TY][BXC],
+    // VR [M][TY+1][BXC], and the slab balance [M-1][CY+2][BXC]
+    static constexpr int oWY = NB * slot;
+    static constexpr int oUO = oWY + (M + 1) * kTY * BXC;
+    static constexpr int oVR = oUO + M * kTY * BXC;
+    static constexpr int oSW = oVR + M * (kTY + 1) * BXC;
+    // the slab's coarse faces (periodic images), staged by cp.async: U on the
+    // three R_z window planes, coarse rows J0-1 .. J0+CY, columns I0-4 .. I0+CX+4;
+    // V likewise with rows up to J0+CY+1; W on the slab's two coarse planes
+    static constexpr int NUX = BXC + 1, NUY = CY + 2, NVY = CY + 3, NWY = CY + 2;
+    static constexpr int NU = 3 * NUY * NUX, NV = 3 * NVY * BXC, NW = 2 * NWY * BXC;
+    static constexpr int oSU = oSW + (M - 1) * (CY + 2) * BXC;
+    static constexpr int oSV = oSU + NU;
+    static constexpr int oSWc = oSV + NV;
+    // R_y rows of the tile's dense rows [TY][3]; R_z rows and widths of the slab's layers
+    static constexpr int oRy = oSWc + NW;
+    static constexpr int oRz = oRy + 3 * kTY;
+    static constexpr int oDz = oRz + 3 * M;
+    static constexpr int oRed = (oDz + M + 3) / 4 * 4;
+    static constexpr int oBar = ((oRed + 64) * 4 + 7) / 8;
     static constexpr size_t bytes = (size_t)(oBar + 2 * NB) * 8;
 };
 
-struct FusedArgs {
+struct FXArgs {
     Grid<float> g;
-    const float* U;      // coarse faces [nz][ny][nx], [nz+1][ny][nx] for W
-    const float* V;
-    const float* W;
-    const float* Tn;     // T^s (global, for halo patches)
+    const float* U;      // coarse faces, FP32: [nz][ny][nx]
+    const float* V;      // [nz][ny][nx]
+    const float* W;      // [nz+1][ny][nx]
+    const float* Tn;     // T^s (global, for the periodic halo of edge threads)
     const float* Tm;     // T^{s-1}
     float* Tp1;          // T^{s+1}
     float a, b, gdt;
-    int kc;              // coarse layers per chunk
+    int kcs;             // coarse slabs per CTA chunk
     int* err;
-    unsigned long long* divmax;   // DIVONLY: max |div| as FP64 bits
+    unsigned long long* divmax;
+    float rx[4][3];      // R_x rows of the 4 cells of a segment (uniform periodic x)
 };
 
-// Issue the TMA copies of dense plane z (both fields) into ring slot s.
-__device__ __forceinline__ void issue_plane(float* sT, uint64_t* bar, const CUtensorMap* mn, const CUtensorMap* mm,
-                                            int s, int i0, int j0, int z)
+__device__ __forceinline__ int wrapi(int i, int n) { return i < 0 ? i + n : (i >= n ? i - n : i); }
+
+// R_x split of three coarse values by one row of R (rows sum to one).
+__device__ __forceinline__ float rsplit3(const float (&r)[3], float c0, float c1, float c2)
 {
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    mbar_expect_tx(&bar[s], 2 * kPlaneBytes);
-    tma_3d(sT + (2 * s + 0) * kSlotFloats, mn, i0 - 4, j0 - 1, z, &bar[s]);
-    tma_3d(sT + (2 * s + 1) * kSlotFloats, mm, i0 - 4, j0 - 1, z, &bar[s]);
+    return c1 + r[0] * (c0 - c1) + r[2] * (c2 - c1);
 }
 
-template <int M, bool DIVONLY>
-__global__ void __launch_bounds__(kThreadsAll, 2)
-k_fused(const __grid_constant__ CUtensorMap tmn, const __grid_constant__ CUtensorMap tmm, const FusedArgs A)
+// The slab's refinement intermediates (see the file comment), written by the
+// kCons consumer threads from the coarse faces staged in shared memory; ends
+// with every value visible to all of them.
+template <int M>
+__device__ void slab_prep(const FXArgs& A, float* sm, int K, int I0, int J0, int j0, int tid)
 {
-    using L = Tile<M>;
-    constexpr int UX = L::UX, UY = L::UY, VX = L::VX, VY = L::VY, WX = L::WX, WY = L::WY, NB = L::NB;
-    constexpr int NC = 4 / M;                  // coarse cells per 4-cell segment
-    constexpr int NW = kThreads / 32;          // consumer warps
+    using L = FX<M>;
+    constexpr int BXC = L::BXC, CY = L::CY, NUX = L::NUX, NUY = L::NUY, NVY = L::NVY, NWY = L::NWY;
+    const Grid<float>& g = A.g;
+    float* sWY = sm + L::oWY;
+    float* sUO = sm + L::oUO;
+    float* sVR = sm + L::oVR;
+    float* sSW = sm + L::oSW;
+    float* sU = sm + L::oSU;
+    float* sV = sm + L::oSV;
+    float* sW = sm + L::oSWc;
+    const size_t cpl = (size_t)g.ny * g.nx;                 // coarse plane
+    // stage the coarse faces: U, V on the R_z window planes of K, W on K, K+1
+#pragma unroll 4
+    for (int u = 0; u < (L::NU + kCons - 1) / kCons; ++u) {
+        const int t = tid + u * kCons;
+        if (t < L::NU) {
+            const int q = t / (NUY * NUX), r = t - q * NUY * NUX, jr = r / NUX, xc = r - jr * NUX;
+            const int I = wrapi(I0 - 4 + xc, g.nx), J = wrapi(J0 - 1 + jr, g.ny);
+            cp_async4(sU + t, A.U + (size_t)g.wz[3 * K + q] * cpl + (size_t)J * g.nx + I);
+        }
+    }
+#pragma unroll 4
+    for (int u = 0; u < (L::NV + kCons - 1) / kCons; ++u) {
+        const int t = tid + u * kCons;
+        if (t < L::NV) {
+            const int q = t / (NVY * BXC), r = t - q * NVY * BXC, jr = r / BXC, xc = r - jr * BXC;
+            const int I = wrapi(I0 - 4 + xc, g.nx), J = wrapi(J0 - 1 + jr, g.ny);
+            cp_async4(sV + t, A.V + (size_t)g.wz[3 * K + q] * cpl + (size_t)J * g.nx + I);
+        }
+    }
+#pragma unroll 4
+    for (int u = 0; u < (L::NW + kCons - 1) / kCons; ++u) {
+        const int t = tid + u * kCons;
+        if (t < L::NW) {
+            const int q = t / (NWY * BXC), r = t - q * NWY * BXC, jr = r / BXC, xc = r - jr * BXC;
+            const int I = wrapi(I0 - 4 + xc, g.nx), J = wrapi(J0 - 1 + jr, g.ny);
+            cp_async4(sW + t, A.W + (size_t)(K + q) * cpl + (size_t)J * g.nx + I);
+        }
+    }
+    if (tid < 3 * M) sm[L::oRz + tid] = g.Rz[3 * K * M + tid];
+    if (tid < M) sm[L::oDz + tid] = g.dz[K * M + tid];
+    cp_async_commit();
+    cp_async_wait_all();
+    asm volatile("barrier.cta.sync 1, %0;" ::"n"(kCons) : "memory");
+    const float* sRy = sm + L::oRy;
+    const float* sRz = sm + L::oRz;
+    const float* sDz = sm + L::oDz;
+    // stage Z: slab balance of every coarse column, top-down (full-area W on
+    // the inner dense planes K M + c, c = M-1 .. 1), coarse rows J0-1 .. J0+CY
+    for (int t = tid; t < (CY + 2) * BXC; t += kCons) {
+        const int jr = t / BXC, xb = t - jr * BXC;
+        float F = sW[(NWY + jr) * BXC + xb] * g.DX * g.DY;      // W on coarse plane K+1
+#pragma unroll
+        for (int c = M - 1; c >= 1; --c) {
+            float uw = 0.f, ue = 0.f, vs = 0.f, vn = 0.f;
+#pragma unroll
+            for (int q = 0; q < 3; ++q) {
+                const float r = sRz[3 * c + q];
+                uw += r * sU[(q * NUY + jr) * NUX + xb];
+                ue += r * sU[(q * NUY + jr) * NUX + xb + 1];
+                vs += r * sV[(q * NVY + jr) * BXC + xb];
+                vn += r * sV[(q * NVY + jr + 1) * BXC + xb];
+            }
+            F = F + (ue - uw) * g.DY * sDz[c] + (vn - vs) * g.DX * sDz[c];
+            sSW[((c - 1) * (CY + 2) + jr) * BXC + xb] = F / (g.DX * g.DY);
+        }
+    }
+    asm volatile("barrier.cta.sync 1, %0;" ::"n"(kCons) : "memory");
+    // WY on the slab's M + 1 dense planes, per (dense row, bundle column)
+    for (int e = tid; e < kTY * BXC; e += kCons) {
+        const int jl = e / BXC, xb = e - jl * BXC;
+        const int jr = (j0 + jl) / M - J0;                         // coarse row, relative to J0
+        const float r0 = sRy[3 * jl], r1 = sRy[3 * jl + 1], r2 = sRy[3 * jl + 2];
+#pragma unroll
+        for (int i = 0; i <= M; ++i) {
+            const float* src = (i == 0 || i == M) ? sW + (i == M ? NWY : 0) * BXC : sSW + (i - 1) * (CY + 2) * BXC;
+            const float c0 = src[jr * BXC + xb], c1 = src[(jr + 1) * BXC + xb], c2 = src[(jr + 2) * BXC + xb];
+            sWY[(i * kTY + jl) * BXC + xb] = r0 * c0 + r1 * c1 + r2 * c2;
+        }
+    }
+    // UO of the slab's M layers, per (coarse row, bundle column): the z split
+    // of the three window rows is shared by the row's M dense rows
+    const float hix = 0.5f * g.inv_dx;
+    for (int e = tid; e < CY * BXC; e += kCons) {
+        const int Jr = e / BXC, xb = e - Jr * BXC;
+#pragma unroll
+        for (int i = 0; i < M; ++i) {
+            float a[3];
+#pragma unroll
+            for (int p = 0; p < 3; ++p) {
+                float s = 0.f;
+#pragma unroll
+                for (int q = 0; q < 3; ++q) s += sRz[3 * i + q] * sU[(q * NUY + Jr + p) * NUX + xb];
+                a[p] = s;
+            }
+#pragma unroll
+            for (int b = 0; b < M; ++b) {
+                const int jl = Jr * M + b;
+                sUO[(i * kTY + jl) * BXC + xb] =
+                    (sRy[3 * jl] * a[0] + sRy[3 * jl + 1] * a[1] + sRy[3 * jl + 2] * a[2]) * hix;
+            }
+        }
+    }
+    asm volatile("barrier.cta.sync 1, %0;" ::"n"(kCons) : "memory");
+    // VR: per layer and coarse row J0 .. J0+CY, the coarse face from R_z of V,
+    // then (rows inside the tile) the row balance, south to north; the last
+    // bundle column is never read and is skipped (its east neighbour is absent)
+    const float hiy = 0.5f * g.inv_dy, two_dx = 2.f * g.dx;
+    for (int e = tid; e < (CY + 1) * (BXC - 1); e += kCons) {
+        const int Jr = e / (BXC - 1), xb = e - Jr * (BXC - 1);
+#pragma unroll
+        for (int i = 0; i < M; ++i) {
+            float vz = 0.f;
+#pragma unroll
+            for (int q = 0; q < 3; ++q) vz += sRz[3 * i + q] * sV[(q * NVY + Jr + 1) * BXC + xb];
+            float* vr = sVR + (i * (kTY + 1) + Jr * M) * BXC + xb;
+            vr[0] = vz * hiy;
+            if (Jr < CY) {
+                const float dzk = sDz[i];
+                const float* uo = sUO + (i * kTY + Jr * M) * BXC + xb;
+                const float* wyb = sWY + (i * kTY + Jr * M) * BXC + xb;
+                const float* wyt = wyb + kTY * BXC;
+                float G = vz * g.DX * dzk;
+#pragma unroll
+                for (int b = 0; b < M - 1; ++b) {
+                    const float uw = uo[b * BXC] * two_dx, ue = uo[b * BXC + 1] * two_dx;
+                    G = G - (ue - uw) * g.dy * dzk - (wyt[b * BXC] - wyb[b * BXC]) * g.DX * g.dy;
+                    vr[(b + 1) * BXC] = G / (g.DX * dzk) * hiy;
+                }
+            }
+        }
+    }
+    asm volatile("barrier.cta.sync 1, %0;" ::"n"(kCons) : "memory");
+}
+
+// KIND 0: the step; 1: max |divergence| of the dense velocity; 2: max CFL rate.
+// LF: a plain leapfrog step (a = 1, b = 0).
+template <int M, int KIND, bool LF>
+__global__ void __launch_bounds__(kThreadsAll, 4)
+k_fused(const __grid_constant__ CUtensorMap tmn, const __grid_constant__ CUtensorMap tmm,
+         const __grid_constant__ CUtensorMap tlc, const FXArgs A)
+{
+    using L = FX<M>;
+    constexpr int NB = L::NB, BXC = L::BXC, NC = 4 / M, NW = kCons / 32;
+    constexpr bool DIVONLY = KIND != 0;
     extern __shared__ __align__(128) float sm[];
-    float* sT = sm + L::oT;
-    float* cu = sm + L::oCU;   // [2][3][UY][UX]  coarse U of the slab's z-window
-    float* cv = sm + L::oCV;   // [2][3][VY][VX]
-    float* cw = sm + L::oCW;   // [2][2][WY][WX]  coarse W below / above the slab
-    float* Uz = sm + L::oUz;   // [M][UY][UX]     z-split of U per dense layer (R_z)
-    float* Vz = sm + L::oVz;   // [M][VY][VX]
-    float* Wc = sm + L::oWc;   // [M+1][WY][WX]   full-area W per dense plane of the slab
-    float* Wy = sm + L::oWy;   // [M+1][TY][WX]   y-split of Wc
-    float* Uo = sm + L::oUo;   // [M][TY][UX]     outer U sub-faces (R_y of Uz)
-    float* Vr = sm + L::oVr;   // [M][TY+1][VX]   full-coarse-width V of every dense row
-    float* sRy = sm + L::oRy;  // [TY][3]
-    float* Lc = sm + L::oLc;   // [M][12] layer constants: dz, 1/dz, wlo_b, whi_b, wlo_t, whi_t, cdn, cup, dx/dz
     float* red = sm + L::oRed;
     uint64_t* full = reinterpret_cast<uint64_t*>(sm) + L::oBar;
     uint64_t* empty = full + NB;
@@ -123,16 +261,15 @@ k_fused(const __grid_constant__ CUtensorMap tmn, const __grid_constant__ CUtenso
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int i0 = blockIdx.y * kTX, j0 = blockIdx.z * kTY;
     const int I0 = i0 / M, J0 = j0 / M;
-    const int K0 = blockIdx.x * A.kc;
-    const int K1 = min(K0 + A.kc, g.nz);
+    const int K0 = blockIdx.x * A.kcs, K1 = min(K0 + A.kcs, g.nz);
     if (K0 >= K1) return;
-    const int k0 = K0 * M, k1 = K1 * M;          // dense layers [k0, k1)
-    const int nplanes = k1 - k0 + 2;             // ring planes k0-1 .. k1
+    const int k0 = K0 * M, k1 = K1 * M;
+    const int nrings = k1 - k0 + 2;              // ring r: plane k0-1+r and the constants of layer k0+r-2
 
-    if (!DIVONLY && tid == 0) {
+    if (tid == 0) {
         for (int s = 0; s < NB; ++s) {
             mbar_init(&full[s], 1);
-            mbar_init(&empty[s], kThreads);
+            mbar_init(&empty[s], kCons);
         }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -140,297 +277,202 @@ k_fused(const __grid_constant__ CUtensorMap tmn, const __grid_constant__ CUtenso
 
     // ---------------------------------------------------------------- producer warp
     if (warp == NW) {
-        if (DIVONLY || lane != 0) return;
-        for (int r = 0; r < nplanes; ++r) {
+        if (lane != 0) return;
+        for (int r = 0; r < nrings; ++r) {
             const int s = r % NB;
             if (r >= NB && !mbar_wait(&empty[s], ((r / NB) - 1) & 1)) {
-                atomicExch(A.err, MR_ERR_TIMEOUT);    // consumers then time out on full[]
+                atomicExch(A.err, MR_ERR_TIMEOUT);   // consumers then time out on full[]
                 break;
             }
-            issue_plane(sT, full, &tmn, &tmm, s, i0, j0, k0 - 1 + r);
+            float* slot = sm + s * L::slot;
+            const int p = k0 - 1 + r;
+            const bool lc = (r >= 2);
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            mbar_expect_tx(&full[s], (DIVONLY ? 0u : 2 * L::plane_bytes) + (lc ? (uint32_t)kLCW * 4 : 0u));
+            if (!DIVONLY) {
+                tma_3d(slot + L::oTn, &tmn, i0 - 4, j0 - 1, p, &full[s]);
+                tma_3d(slot + L::oTm, &tmm, i0 - 4, j0 - 1, p, &full[s]);
+            }
+            if (lc) tma_3d(slot + L::oLC, &tlc, 0, p - 1, 0, &full[s]);
         }
         return;
     }
 
     // ---------------------------------------------------------------- consumer warps
-    const float DX = g.DX, DY = g.DY, dx = g.dx, dy = g.dy;
-    const int seg = tid & 15, jl = tid >> 4;     // this thread's 4-cell segment of dense row jl
-    const int il0 = seg * 4;
-    float rx[4][3];
-#pragma unroll
-    for (int a = 0; a < 4; ++a)
-#pragma unroll
-        for (int p = 0; p < 3; ++p) rx[a][p] = g.Rx[(size_t)(i0 + il0 + a) * 3 + p];
-    for (int t = tid; t < kTY * 3; t += kThreads) sRy[t] = g.Ry[(size_t)j0 * 3 + t];
-    // periodic wrap of the in-plane halo, for the threads on the domain edge
+    // this thread's 4-cell segment of dense row jl (half-warps on rows two apart)
+    const int seg = tid & 15, jl = ((warp >> 1) << 2) + (warp & 1) + 2 * ((tid >> 4) & 1);
+    const int il0 = seg * 4, cb0 = il0 / M;      // first coarse column of the segment (tile-local)
+    const auto& rx = A.rx;
     const bool wrap_w = (i0 == 0 && seg == 0), wrap_e = (i0 + kTX == g.Nx && seg == 15);
     const bool wrap_s = (j0 == 0 && jl == 0), wrap_n = (j0 + kTY == g.Ny && jl == kTY - 1);
-    const size_t plane = (size_t)g.Nx * g.Ny;
 
-    // coarse tile of layer K into buffer bb (cp.async; one warp per row)
-    auto load_coarse = [&](int K, int bb) {
-        constexpr int RU = 3 * UY, RV = 3 * VY, RW = 2 * WY;
-        for (int row = warp; row < RU + RV + RW; row += NW) {
-            if (row < RU) {
-                const int q = row / UY, uj = row % UY;
-                const float* src = A.U + ((size_t)g.wz[3 * K + q] * g.ny + wrap(J0 - 1 + uj, g.ny)) * g.nx;
-                float* dst = cu + (bb * RU + row) * UX;
-                for (int x = lane; x < UX; x += 32) cp_async4(dst + x, src + wrap(I0 - 1 + x, g.nx));
-            } else if (row < RU + RV) {
-                const int r2 = row - RU, q = r2 / VY, vj = r2 % VY;
-                const float* src = A.V + ((size_t)g.wz[3 * K + q] * g.ny + wrap(J0 - 1 + vj, g.ny)) * g.nx;
-                float* dst = cv + (bb * RV + r2) * VX;
-                for (int x = lane; x < VX; x += 32) cp_async4(dst + x, src + wrap(I0 - 1 + x, g.nx));
-            } else {
-                const int r2 = row - RU - RV, q = r2 / WY, wj = r2 % WY;
-                const float* src = A.W + ((size_t)(K + q) * g.ny + wrap(J0 - 1 + wj, g.ny)) * g.nx;
-                float* dst = cw + (bb * RW + r2) * WX;
-                for (int x = lane; x < WX; x += 32) cp_async4(dst + x, src + wrap(I0 - 1 + x, g.nx));
-            }
-        }
-        cp_async_commit();
-    };
-
-    load_coarse(K0, 0);
-    int waited = 0;            // ring planes this thread has waited for
     bool fail = false;
     float dmax = 0.f;
+    const float kx2 = g.kx2, ky2 = g.ky2;
+    const float ca = A.a, cbb = A.b, gdt = A.gdt;
+    int sb = 0, sc = 1, st = 2;                  // ring slots of planes k-1, k, k+1
+    int wslot = 0, wpar = 0, waited = 0;
+    const size_t plane = (size_t)g.Nx * g.Ny;
+    float* outp = A.Tp1 + (size_t)k0 * plane + (size_t)(j0 + jl) * g.Nx + i0 + il0;
+    const int o = (jl + 1) * kBX + il0 + 4;      // this segment's first cell in a plane box
+    const float* sWY = sm + L::oWY;
+    const float* sUO = sm + L::oUO;
+    const float* sVR = sm + L::oVR;
 
-    for (int K = K0; K < K1; ++K) {
-        const int bb = (K - K0) & 1;
-        cp_async_wait_all();
-        if (consumers_sync_or<kThreads>(fail)) break;       // uniform exit of every consumer
-        if (K + 1 < K1) load_coarse(K + 1, bb ^ 1);
-        const float* ccu = cu + bb * 3 * UY * UX;
-        const float* ccv = cv + bb * 3 * VY * VX;
-        const float* ccw = cw + bb * 2 * WY * WX;
-        // per-layer constants of the slab, read by every thread of every layer
-        if (tid < M) {
-            const int k = K * M + tid;
-            float* lc = Lc + tid * 12;
-            lc[0] = g.dz[k]; lc[1] = g.inv_dz[k];
-            lc[2] = g.wlo[k]; lc[3] = g.whi[k]; lc[4] = g.wlo[k + 1]; lc[5] = g.whi[k + 1];
-            lc[6] = g.cdn[k]; lc[7] = g.cup[k]; lc[8] = dx / g.dz[k];
+    if (tid < 3 * kTY) sm[L::oRy + tid] = g.Ry[3 * j0 + tid];   // the tile's R_y rows (read after a barrier)
+    float wcar[4] = {0.f, 0.f, 0.f, 0.f};        // R_x split of W on plane k (from layer k-1)
+    for (int k = k0; k < k1; ++k) {
+        const int K = k / M, i = k - K * M;
+        if (i == 0) {
+            // the previous slab's intermediates are no longer read: build this slab's
+            asm volatile("barrier.cta.sync 1, %0;" ::"n"(kCons) : "memory");
+            slab_prep<M>(A, sm, K, I0, J0, j0, tid);
         }
-        // A1: z-splits of the U and V faces for the M dense layers (R_z)
-        for (int row = warp; row < M * UY + M * VY; row += NW) {
-            if (row < M * UY) {
-                const int c = row / UY, uj = row % UY;
-                const float* rz = g.Rz + 3 * (K * M + c);
-                const float r0 = rz[0], r1 = rz[1], r2 = rz[2];
-                for (int x = lane; x < UX; x += 32)
-                    Uz[row * UX + x] = r0 * ccu[uj * UX + x] + r1 * ccu[(UY + uj) * UX + x] + r2 * ccu[(2 * UY + uj) * UX + x];
-            } else {
-                const int rr = row - M * UY, c = rr / VY, vj = rr % VY;
-                const float* rz = g.Rz + 3 * (K * M + c);
-                const float r0 = rz[0], r1 = rz[1], r2 = rz[2];
-                for (int x = lane; x < VX; x += 32)
-                    Vz[rr * VX + x] = r0 * ccv[vj * VX + x] + r1 * ccv[(VY + vj) * VX + x] + r2 * ccv[(2 * VY + vj) * VX + x];
-            }
+        const int need = k - k0 + 2;             // ring of plane k+1 and of this layer's constants
+        while (!fail && waited <= need) {
+            if (!mbar_wait(&full[wslot], wpar)) { fail = true; break; }
+            ++waited;
+            if (++wslot == NB) { wslot = 0; wpar ^= 1; }
         }
-        consumers_sync<kThreads>();
-        // A2: stage Z slab balance, top-down, one thread per coarse column
-        for (int t = tid; t < WY * WX; t += kThreads) {
-            const int wj = t / WX, wi = t % WX;
-            const float wtop = ccw[WY * WX + t];
-            Wc[t] = ccw[t];
-            Wc[M * WY * WX + t] = wtop;
-            float F = wtop * DX * DY;
-#pragma unroll
-            for (int c = M - 1; c >= 1; --c) {
-                const float dzk = g.dz[K * M + c];
-                const float* uz = Uz + c * UY * UX + wj * UX + wi;
-                const float* vz = Vz + c * VY * VX + wj * VX + wi;
-                F = F + (uz[1] - uz[0]) * DY * dzk + (vz[VX] - vz[0]) * DX * dzk;
-                Wc[c * WY * WX + t] = F / (DX * DY);
-            }
-        }
-        consumers_sync<kThreads>();
-        // S1: y-split of Wc on the M+1 planes; outer U sub-faces of the M layers (R_y)
-        for (int row = warp; row < (M + 1) * kTY + M * kTY; row += NW) {
-            if (row < (M + 1) * kTY) {
-                const int c = row / kTY, j = row % kTY;
-                const float* ry = sRy + 3 * j;
-                const float* wc = Wc + c * WY * WX + (j / M) * WX;
-                for (int x = lane; x < WX; x += 32)
-                    Wy[row * WX + x] = ry[0] * wc[x] + ry[1] * wc[WX + x] + ry[2] * wc[2 * WX + x];
-            } else {
-                const int rr = row - (M + 1) * kTY, c = rr / kTY, j = rr % kTY;
-                const float* ry = sRy + 3 * j;
-                const float* uz = Uz + c * UY * UX + (j / M) * UX;
-                for (int x = lane; x < UX; x += 32)
-                    Uo[rr * UX + x] = ry[0] * uz[x] + ry[1] * uz[UX + x] + ry[2] * uz[2 * UX + x];
-            }
-        }
-        consumers_sync<kThreads>();
-        // S2: stage Y, full-width V of every dense row by row balance (running
-        // sum from the coarse south face), for the M layers
-        for (int row = warp; row < M * (kTY + 1); row += NW) {
-            const int c = row / (kTY + 1), jr = row % (kTY + 1);
-            const int Jl = jr / M, b = jr % M;
-            const float dzk = g.dz[K * M + c];
-            const float* vz = Vz + (c * VY + Jl + 1) * VX;
-            const float* uo = Uo + c * kTY * UX;
-            const float* wyb = Wy + c * kTY * WX;
-            const float* wyt = Wy + (c + 1) * kTY * WX;
-            for (int x = lane; x < VX; x += 32) {
-                float G = vz[x] * DX * dzk;
-                for (int q = 0; q < b; ++q) {
-                    const int j2 = Jl * M + q;
-                    G = G - (uo[j2 * UX + x + 1] - uo[j2 * UX + x]) * dy * dzk
-                          - (wyt[j2 * WX + x] - wyb[j2 * WX + x]) * DX * dy;
-                }
-                Vr[row * VX + x] = b == 0 ? vz[x] : G / (DX * dzk);
-            }
-        }
-        consumers_sync<kThreads>();
-
-        // the M dense layers of the slab, free-running (no block barrier)
-        for (int c = 0; c < M; ++c) {
-            const int k = K * M + c;
-            if (!DIVONLY && !fail) {
-                const int need = k + 1 - (k0 - 1);             // ring index of plane k+1
-                while (waited <= need) {
-                    if (!mbar_wait(&full[waited % NB], (waited / NB) & 1)) { fail = true; break; }
-                    ++waited;
-                }
-            }
-            if (!fail) {
-            const float* lc = Lc + c * 12;
-            // refined faces of this thread's 4 cells, in registers
+        if (!fail) {
+            const float* lcp = sm + st * L::slot + L::oLC;
+            const float4 c0 = *reinterpret_cast<const float4*>(lcp);
+            const float4 c1 = *reinterpret_cast<const float4*>(lcp + 4);
+            const float2 c2 = *reinterpret_cast<const float2*>(lcp + 8);
+            const float inv_dz = c0.x, bwlo = c0.y, bwhi = c0.z, twlo = c0.w;
+            const float twhi = c1.x, cdn = c1.y, cup = c1.z, diag = c1.w, plate = c2.x, hz = c2.y;
             float wb[4], wt[4], vs[4], vn[4], us[5];
             {
-                const float* yb = Wy + (c * kTY + jl) * WX;
-                const float* yt = Wy + ((c + 1) * kTY + jl) * WX;
-                const float* rs = Vr + (c * (kTY + 1) + jl) * VX;
-                const float* rn = rs + VX;
-                const int cb0 = il0 / M;                      // first coarse column of the window
+                // R_x splits of the full-width W (planes k, k+1) and V (faces jl, jl+1)
+                const float* yb = sWY + (i * kTY + jl) * BXC + cb0 + 3;
+                const float* yt = yb + kTY * BXC;
+                const float* rs = sVR + (i * (kTY + 1) + jl) * BXC + cb0 + 3;
+                const float* rn = rs + BXC;
+                const float* ur = sUO + (i * kTY + jl) * BXC + cb0 + 4;   // outer face of coarse column cb0
+                constexpr int NV = NC + 2;
+                float ytv[NV], rsv[NV], rnv[NV], urv[NC + 1];
+                if (k == k0) {
+#pragma unroll
+                    for (int a = 0; a < 4; ++a) {
+                        const int cb = a / M;
+                        wcar[a] = rsplit3(rx[a], yb[cb], yb[cb + 1], yb[cb + 2]);
+                    }
+                }
+#pragma unroll
+                for (int c = 0; c < NV; ++c) {
+                    ytv[c] = yt[c];
+                    rsv[c] = rs[c];
+                    rnv[c] = rn[c];
+                }
+#pragma unroll
+                for (int q = 0; q <= NC; ++q) urv[q] = ur[q];
 #pragma unroll
                 for (int a = 0; a < 4; ++a) {
-                    const int cb = cb0 + a / M;
-                    wb[a] = rx[a][0] * yb[cb] + rx[a][1] * yb[cb + 1] + rx[a][2] * yb[cb + 2];
-                    wt[a] = rx[a][0] * yt[cb] + rx[a][1] * yt[cb + 1] + rx[a][2] * yt[cb + 2];
-                    vs[a] = rx[a][0] * rs[cb] + rx[a][1] * rs[cb + 1] + rx[a][2] * rs[cb + 2];
-                    vn[a] = rx[a][0] * rn[cb] + rx[a][1] * rn[cb + 1] + rx[a][2] * rn[cb + 2];
+                    const int cb = a / M;
+                    wb[a] = wcar[a];
+                    wt[a] = rsplit3(rx[a], ytv[cb], ytv[cb + 1], ytv[cb + 2]);
+                    vs[a] = rsplit3(rx[a], rsv[cb], rsv[cb + 1], rsv[cb + 2]);
+                    vn[a] = rsplit3(rx[a], rnv[cb], rnv[cb + 1], rnv[cb + 2]);
                 }
-                // stage X: cell balance, west to east (velocity units: h = H / (dy dz))
-                const float* ur = Uo + (c * kTY + jl) * UX;
-                const float fx_y = dx / dy, fx_z = lc[8];
+                // stage X: cell balance, west to east, in units of U / (2 dx)
 #pragma unroll
                 for (int q = 0; q < NC; ++q) {
-                    float h = ur[cb0 + q + 1];                // outer west face of the coarse cell
+                    float h = urv[q];
                     us[q * M] = h;
 #pragma unroll
                     for (int a = 0; a < M - 1; ++a) {
                         const int m = q * M + a;
-                        h = h - (vn[m] - vs[m]) * fx_y - (wt[m] - wb[m]) * fx_z;
+                        h = h - (vn[m] - vs[m]) - (wt[m] - wb[m]) * hz;
                         us[m + 1] = h;
                     }
                 }
-                us[4] = ur[cb0 + NC + 1];                     // outer east face of the segment
+                us[4] = urv[NC];
+#pragma unroll
+                for (int a = 0; a < 4; ++a) wcar[a] = wt[a];
             }
-            const float inv_dz = lc[1];
             if (DIVONLY) {
 #pragma unroll
                 for (int a = 0; a < 4; ++a) {
-                    const float d = (us[a + 1] - us[a]) * g.inv_dx + (vn[a] - vs[a]) * g.inv_dy + (wt[a] - wb[a]) * inv_dz;
+                    const float d = KIND == 2 ? 2.f * (fmaxf(fabsf(us[a]), fabsf(us[a + 1])) + fmaxf(fabsf(vs[a]), fabsf(vn[a]))) +
+                                                    fmaxf(fabsf(wb[a]), fabsf(wt[a])) * inv_dz
+                                              : 2.f * ((us[a + 1] - us[a]) + (vn[a] - vs[a])) + (wt[a] - wb[a]) * inv_dz;
                     dmax = fmaxf(dmax, fabsf(d));
                 }
-                continue;
-            }
-            const int rb = k - k0, rc = rb + 1, rt = rb + 2;   // ring indices of planes k-1, k, k+1
-            const float* Pn_b = sT + (2 * (rb % NB) + 0) * kSlotFloats;
-            const float* Pm_b = sT + (2 * (rb % NB) + 1) * kSlotFloats;
-            const float* Pn_c = sT + (2 * (rc % NB) + 0) * kSlotFloats;
-            const float* Pm_c = sT + (2 * (rc % NB) + 1) * kSlotFloats;
-            const float* Pn_t = sT + (2 * (rt % NB) + 0) * kSlotFloats;
-            const float* Pm_t = sT + (2 * (rt % NB) + 1) * kSlotFloats;
-            const int o = (jl + 1) * kBX + il0 + 4;
-            float4 tc4 = *reinterpret_cast<const float4*>(Pn_c + o);
-            float4 ts4 = *reinterpret_cast<const float4*>(Pn_c + o - kBX);
-            float4 tn4 = *reinterpret_cast<const float4*>(Pn_c + o + kBX);
-            float4 dc4 = *reinterpret_cast<const float4*>(Pm_c + o);
-            float4 ds4 = *reinterpret_cast<const float4*>(Pm_c + o - kBX);
-            float4 dn4 = *reinterpret_cast<const float4*>(Pm_c + o + kBX);
-            float tw = Pn_c[o - 1], te = Pn_c[o + 4], dw = Pm_c[o - 1], de = Pm_c[o + 4];
-            if (wrap_w | wrap_e | wrap_s | wrap_n) {
-                // the box holds zeros beyond the domain: fetch the periodic images
-                const size_t row = (size_t)k * plane + (size_t)(j0 + jl) * g.Nx;
-                if (wrap_w) { tw = A.Tn[row + g.Nx - 1]; dw = A.Tm[row + g.Nx - 1]; }
-                if (wrap_e) { te = A.Tn[row]; de = A.Tm[row]; }
-                if (wrap_s) {
-                    const size_t r2 = (size_t)k * plane + (size_t)(g.Ny - 1) * g.Nx + i0 + il0;
-                    ts4 = *reinterpret_cast<const float4*>(A.Tn + r2);
-                    ds4 = *reinterpret_cast<const float4*>(A.Tm + r2);
+            } else {
+                const float* Pn_b = sm + sb * L::slot + L::oTn;
+                const float* Pm_b = sm + sb * L::slot + L::oTm;
+                const float* Pn_c = sm + sc * L::slot + L::oTn;
+                const float* Pm_c = sm + sc * L::slot + L::oTm;
+                const float* Pn_t = sm + st * L::slot + L::oTn;
+                const float* Pm_t = sm + st * L::slot + L::oTm;
+                const float4 tc4 = *reinterpret_cast<const float4*>(Pn_c + o);
+                float4 ts4 = *reinterpret_cast<const float4*>(Pn_c + o - kBX);
+                float4 tn4 = *reinterpret_cast<const float4*>(Pn_c + o + kBX);
+                const float4 dc4 = *reinterpret_cast<const float4*>(Pm_c + o);
+                float4 ds4 = *reinterpret_cast<const float4*>(Pm_c + o - kBX);
+                float4 dn4 = *reinterpret_cast<const float4*>(Pm_c + o + kBX);
+                float tw = __shfl_up_sync(0xffffffffu, tc4.w, 1), te = __shfl_down_sync(0xffffffffu, tc4.x, 1);
+                float dw = __shfl_up_sync(0xffffffffu, dc4.w, 1), de = __shfl_down_sync(0xffffffffu, dc4.x, 1);
+                if (seg == 0) { tw = Pn_c[o - 1]; dw = Pm_c[o - 1]; }
+                if (seg == 15) { te = Pn_c[o + 4]; de = Pm_c[o + 4]; }
+                if (wrap_w | wrap_e | wrap_s | wrap_n) {
+                    // the box holds zeros beyond the domain: fetch the periodic images
+                    const float* gn = A.Tn + (size_t)k * plane;
+                    const float* gm = A.Tm + (size_t)k * plane;
+                    const size_t row = (size_t)(j0 + jl) * g.Nx;
+                    if (wrap_w) { tw = gn[row + g.Nx - 1]; dw = gm[row + g.Nx - 1]; }
+                    if (wrap_e) { te = gn[row]; de = gm[row]; }
+                    if (wrap_s) {
+                        const size_t r2 = (size_t)(g.Ny - 1) * g.Nx + i0 + il0;
+                        ts4 = *reinterpret_cast<const float4*>(gn + r2);
+                        ds4 = *reinterpret_cast<const float4*>(gm + r2);
+                    }
+                    if (wrap_n) {
+                        tn4 = *reinterpret_cast<const float4*>(gn + i0 + il0);
+                        dn4 = *reinterpret_cast<const float4*>(gm + i0 + il0);
+                    }
                 }
-                if (wrap_n) {
-                    const size_t r2 = (size_t)k * plane + i0 + il0;
-                    tn4 = *reinterpret_cast<const float4*>(A.Tn + r2);
-                    dn4 = *reinterpret_cast<const float4*>(A.Tm + r2);
-                }
-            }
-            const float tcv[6] = {tw, tc4.x, tc4.y, tc4.z, tc4.w, te};
-            const float dcv[6] = {dw, dc4.x, dc4.y, dc4.z, dc4.w, de};
-            const float tsv[4] = {ts4.x, ts4.y, ts4.z, ts4.w}, tnv[4] = {tn4.x, tn4.y, tn4.z, tn4.w};
-            const float dsv[4] = {ds4.x, ds4.y, ds4.z, ds4.w}, dnv[4] = {dn4.x, dn4.y, dn4.z, dn4.w};
-            float tbv[4] = {0.f, 0.f, 0.f, 0.f}, dbv[4] = {0.f, 0.f, 0.f, 0.f};
-            float ttv[4] = {0.f, 0.f, 0.f, 0.f}, dtv[4] = {0.f, 0.f, 0.f, 0.f};
-            const bool bot = (k == 0), top = (k == g.Nz - 1);
-            if (!bot) {
-                const float4 b4 = *reinterpret_cast<const float4*>(Pn_b + o);
-                const float4 e4 = *reinterpret_cast<const float4*>(Pm_b + o);
-                tbv[0] = b4.x; tbv[1] = b4.y; tbv[2] = b4.z; tbv[3] = b4.w;
-                dbv[0] = e4.x; dbv[1] = e4.y; dbv[2] = e4.z; dbv[3] = e4.w;
-            }
-            if (!top) {
-                const float4 b4 = *reinterpret_cast<const float4*>(Pn_t + o);
-                const float4 e4 = *reinterpret_cast<const float4*>(Pm_t + o);
-                ttv[0] = b4.x; ttv[1] = b4.y; ttv[2] = b4.z; ttv[3] = b4.w;
-                dtv[0] = e4.x; dtv[1] = e4.y; dtv[2] = e4.z; dtv[3] = e4.w;
-            }
-            // plane k-1 is no longer needed by this thread: release its ring slot
-            mbar_arrive(&empty[rb % NB]);
-            const float wlo_b = lc[2], whi_b = lc[3], wlo_t = lc[4], whi_t = lc[5];
-            const float cdn = lc[6], cup = lc[7];
-            float res[4];
+                // planes below / above: zero-filled beyond the plates, where W is zero
+                // and the plate value enters D through `plate`
+                const float4 tb4 = *reinterpret_cast<const float4*>(Pn_b + o);
+                const float4 db4 = *reinterpret_cast<const float4*>(Pm_b + o);
+                const float4 tt4 = *reinterpret_cast<const float4*>(Pn_t + o);
+                const float4 dt4 = *reinterpret_cast<const float4*>(Pm_t + o);
+                const float tcv[6] = {tw, tc4.x, tc4.y, tc4.z, tc4.w, te};
+                const float dcv[6] = {dw, dc4.x, dc4.y, dc4.z, dc4.w, de};
+                const float tsv[4] = {ts4.x, ts4.y, ts4.z, ts4.w}, tnv[4] = {tn4.x, tn4.y, tn4.z, tn4.w};
+                const float dsv[4] = {ds4.x, ds4.y, ds4.z, ds4.w}, dnv[4] = {dn4.x, dn4.y, dn4.z, dn4.w};
+                const float tbv[4] = {tb4.x, tb4.y, tb4.z, tb4.w}, ttv[4] = {tt4.x, tt4.y, tt4.z, tt4.w};
+                const float dbv[4] = {db4.x, db4.y, db4.z, db4.w}, dtv[4] = {dt4.x, dt4.y, dt4.z, dt4.w};
+                float res[4];
 #pragma unroll
-            for (int a = 0; a < 4; ++a) {
-                const float tc = tcv[a + 1], dc = dcv[a + 1];
-                float cz = 0.f, dz_ = 0.f;
-                if (!bot) {
-                    cz += wb[a] * (wlo_b * tbv[a] + whi_b * tc);
-                    dz_ -= cdn * (dc - dbv[a]);
-                } else {
-                    dz_ -= cdn * (dc - kTBottom);
+                for (int a = 0; a < 4; ++a) {
+                    const float tc = tcv[a + 1], dc = dcv[a + 1];
+                    const float cx = us[a] * (tcv[a] + tc) - us[a + 1] * (tc + tcv[a + 2]);
+                    const float cy = vs[a] * (tsv[a] + tc) - vn[a] * (tc + tnv[a]);
+                    const float cz = wb[a] * (bwlo * tbv[a] + bwhi * tc) - wt[a] * (twlo * tc + twhi * ttv[a]);
+                    const float D = kx2 * (dcv[a] + dcv[a + 2]) + ky2 * (dsv[a] + dnv[a]) + cdn * dbv[a] + cup * dtv[a] +
+                                    (plate - diag * dc);
+                    res[a] = LF ? dc + gdt * ((cx + cy + cz) + D) : ca * dc + cbb * tc + gdt * ((cx + cy + cz) + D);
                 }
-                if (!top) {
-                    cz -= wt[a] * (wlo_t * tc + whi_t * ttv[a]);
-                    dz_ += cup * (dtv[a] - dc);
-                } else {
-                    dz_ += cup * (kTTop - dc);
-                }
-                const float cx = us[a] * 0.5f * (tcv[a] + tc) - us[a + 1] * 0.5f * (tc + tcv[a + 2]);
-                const float cy = vs[a] * 0.5f * (tsv[a] + tc) - vn[a] * 0.5f * (tc + tnv[a]);
-                const float C = cx * g.inv_dx + cy * g.inv_dy + cz * inv_dz;
-                const float D = g.kx2 * ((dcv[a + 2] - dc) - (dc - dcv[a])) + g.ky2 * ((dnv[a] - dc) - (dc - dsv[a])) + dz_;
-                res[a] = A.a * dc + A.b * tc + A.gdt * (C + D);
-            }
-            *reinterpret_cast<float4*>(A.Tp1 + (size_t)k * plane + (size_t)(j0 + jl) * g.Nx + i0 + il0) =
-                make_float4(res[0], res[1], res[2], res[3]);
-            } else if (!DIVONLY) {
-                mbar_arrive(&empty[(k - k0) % NB]);
+                *reinterpret_cast<float4*>(outp) = make_float4(res[0], res[1], res[2], res[3]);
             }
         }
+        // plane k-1 is no longer needed by this thread
+        mbar_arrive(&empty[sb]);
+        sb = sc;
+        sc = st;
+        st = (st + 1 == NB) ? 0 : st + 1;
+        outp += plane;
     }
-    if (consumers_sync_or<kThreads>(fail)) {
+    if (consumers_sync_or<kCons>(fail)) {
         if (tid == 0) atomicExch(A.err, MR_ERR_TIMEOUT);
         return;
     }
     if (DIVONLY) {
-        // block max -> device max (non-negative doubles order as their bit patterns)
-        for (int o = 16; o > 0; o >>= 1) dmax = fmaxf(dmax, __shfl_down_sync(0xffffffffu, dmax, o));
+        for (int d = 16; d > 0; d >>= 1) dmax = fmaxf(dmax, __shfl_down_sync(0xffffffffu, dmax, d));
         if (lane == 0) red[warp] = dmax;
-        consumers_sync<kThreads>();
+        consumers_sync<kCons>();
         if (tid == 0) {
             float m = 0.f;
             for (int w = 0; w < NW; ++w) m = fmaxf(m, red[w]);
@@ -457,20 +499,100 @@ EncodeTiledFn encode_fn()
     return fn;
 }
 
-bool make_map(CUtensorMap* m, const float* base, const Grid<float>& g)
+// Tensor maps of (buffer, shape, box), encoded once each.
+bool map_fx(CUtensorMap* out, const float* base, int d0, int d1, int d2, int b0, int b1, int b2)
 {
+    struct Entry { const float* p; int d[6]; CUtensorMap m; };
+    static Entry cache[16];
+    static int n = 0, next = 0;
+    static std::mutex mu;
+    const int key[6] = {d0, d1, d2, b0, b1, b2};
+    {
+        std::lock_guard<std::mutex> lock(mu);
+        for (int q = 0; q < n; ++q)
+            if (cache[q].p == base && !memcmp(cache[q].d, key, sizeof key)) {
+                *out = cache[q].m;
+                return true;
+            }
+    }
     EncodeTiledFn fn = encode_fn();
     if (!fn) return false;
-    cuuint64_t dims[3] = {(cuuint64_t)g.Nx, (cuuint64_t)g.Ny, (cuuint64_t)g.Nz};
-    cuuint64_t strides[2] = {(cuuint64_t)g.Nx * 4, (cuuint64_t)g.Nx * g.Ny * 4};
-    cuuint32_t box[3] = {(cuuint32_t)kBX, (cuuint32_t)kBY, 1};
+    cuuint64_t dims[3] = {(cuuint64_t)d0, (cuuint64_t)d1, (cuuint64_t)d2};
+    cuuint64_t strides[2] = {(cuuint64_t)d0 * 4, (cuuint64_t)d0 * d1 * 4};
+    cuuint32_t box[3] = {(cuuint32_t)b0, (cuuint32_t)b1, (cuuint32_t)b2};
     cuuint32_t es[3] = {1, 1, 1};
-    return fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, (void*)base, dims, strides, box, es,
-              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
-              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+    if (fn(out, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, (void*)base, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+           CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) !=
+        CUDA_SUCCESS)
+        return false;
+    std::lock_guard<std::mutex> lock(mu);
+    Entry& e = cache[n < 16 ? n++ : (next = (next + 1) % 16)];
+    e.p = base;
+    memcpy(e.d, key, sizeof key);
+    e.m = *out;
+    return true;
+}
+
+template <int M, int KIND, bool LF>
+cudaError_t launch_fx(const Grid<float>& g, const float* U, const float* V, const float* W, const float* lc,
+                      const float* rx12, const float* Tm1, const float* T, float* Tp1, StepCoef c, int* err,
+                      unsigned long long* divmax, cudaStream_t st)
+{
+    using L = FX<M>;
+    static unsigned long long attr = 0;                   // one bit per device
+    cudaError_t e = smem_optin(reinterpret_cast<const void*>(k_fused<M, KIND, LF>), (int)L::bytes, &attr);
+    if (e != cudaSuccess) return e;
+    CUtensorMap mn, mm, mlc;
+    memset(&mn, 0, sizeof mn);
+    memset(&mm, 0, sizeof mm);
+    if (KIND == 0 && (!map_fx(&mn, T, g.Nx, g.Ny, g.Nz, kBX, kBY, 1) || !map_fx(&mm, Tm1, g.Nx, g.Ny, g.Nz, kBX, kBY, 1)))
+        return cudaErrorInvalidValue;
+    if (!map_fx(&mlc, lc, kLCW, g.Nz, 1, kLCW, 1, 1)) return cudaErrorInvalidValue;
+    // ~12 waves of four CTAs per SM, chunks of at most 96 dense layers
+    const int tiles = (g.Nx / kTX) * (g.Ny / kTY);
+    const int want = 152 * 4 * 12;
+    int chunks = max(1, min((want + tiles - 1) / tiles, g.nz));
+    int kcs = (g.nz + chunks - 1) / chunks;
+    kcs = max(1, min(kcs, 96 / M));
+    chunks = (g.nz + kcs - 1) / kcs;
+    FXArgs A{g, U, V, W, T, Tm1, Tp1, (float)c.a, (float)c.b, (float)c.gdt, kcs, err, divmax, {}};
+    memcpy(A.rx, rx12, sizeof A.rx);
+    dim3 grid(chunks, g.Nx / kTX, g.Ny / kTY);
+    k_fused<M, KIND, LF><<<grid, kThreadsAll, L::bytes, st>>>(mn, mm, mlc, A);
+    return cudaGetLastError();
 }
 
 }  // namespace
+
+cudaError_t launch_step_fused_f32(const Grid<float>& g, const float* U, const float* V, const float* W,
+                                   const float* lc, const float* rx12, const float* Tm1, const float* T, float* Tp1,
+                                   StepCoef c, cudaStream_t st)
+{
+    int* err = fused_error_flag();
+    if (!err) return cudaErrorMemoryAllocation;
+    const bool lf = (c.a == 1.0 && c.b == 0.0);
+    if (g.mx == 4)
+        return lf ? launch_fx<4, 0, true>(g, U, V, W, lc, rx12, Tm1, T, Tp1, c, err, nullptr, st)
+                  : launch_fx<4, 0, false>(g, U, V, W, lc, rx12, Tm1, T, Tp1, c, err, nullptr, st);
+    return lf ? launch_fx<2, 0, true>(g, U, V, W, lc, rx12, Tm1, T, Tp1, c, err, nullptr, st)
+              : launch_fx<2, 0, false>(g, U, V, W, lc, rx12, Tm1, T, Tp1, c, err, nullptr, st);
+}
+
+cudaError_t launch_fused_max_f32(const Grid<float>& g, int kind, const float* U, const float* V, const float* W,
+                                  const float* lc, const float* rx12, double* partials, int blocks, cudaStream_t st)
+{
+    int* err = fused_error_flag();
+    if (!err) return cudaErrorMemoryAllocation;
+    cudaError_t e = cudaMemsetAsync(partials, 0, (size_t)blocks * sizeof(double), st);
+    if (e != cudaSuccess) return e;
+    unsigned long long* dm = reinterpret_cast<unsigned long long*>(partials);
+    const StepCoef c{0, 0, 0};
+    if (g.mx == 4)
+        return kind == 2 ? launch_fx<4, 2, false>(g, U, V, W, lc, rx12, nullptr, nullptr, nullptr, c, err, dm, st)
+                         : launch_fx<4, 1, false>(g, U, V, W, lc, rx12, nullptr, nullptr, nullptr, c, err, dm, st);
+    return kind == 2 ? launch_fx<2, 2, false>(g, U, V, W, lc, rx12, nullptr, nullptr, nullptr, c, err, dm, st)
+                     : launch_fx<2, 1, false>(g, U, V, W, lc, rx12, nullptr, nullptr, nullptr, c, err, dm, st);
+}
 
 // Raise a kernel's dynamic shared-memory limit once per device; *done holds
 // one bit per device index.
@@ -487,74 +609,6 @@ cudaError_t smem_optin(const void* kernel, int bytes, unsigned long long* done)
     if (e == cudaSuccess) *done |= 1ull << dev;
     return e;
 }
-
-namespace {
-
-// Tensor maps of the (few) scalar buffers in use, encoded once each.
-bool cached_map(CUtensorMap* m, const float* base, const Grid<float>& g)
-{
-    struct Entry { const float* p; int nx, ny, nz; CUtensorMap map; };
-    static Entry cache[16];
-    static int n = 0;
-    static std::mutex mu;
-    std::lock_guard<std::mutex> lock(mu);
-    for (int q = 0; q < n; ++q)
-        if (cache[q].p == base && cache[q].nx == g.Nx && cache[q].ny == g.Ny && cache[q].nz == g.Nz) {
-            *m = cache[q].map;
-            return true;
-        }
-    if (!make_map(m, base, g)) return false;
-    Entry& e = cache[n < 16 ? n++ : (n = 1, 0)];
-    e.p = base; e.nx = g.Nx; e.ny = g.Ny; e.nz = g.Nz; e.map = *m;
-    return true;
-}
-
-// Coarse layers per CTA chunk; MR_FUSED_KC in the environment overrides the
-// automatic choice (used for tuning).
-int chunk_override()
-{
-    static int v = -1;
-    if (v < 0) {
-        const char* e = getenv("MR_FUSED_KC");
-        v = e ? atoi(e) : 0;
-    }
-    return v;
-}
-
-template <int M, bool DIVONLY>
-cudaError_t launch_fused(const Grid<float>& g, const float* U, const float* V, const float* W, const float* Tm1,
-                         const float* T, float* Tp1, StepCoef c, int* err, unsigned long long* divmax,
-                         cudaStream_t st)
-{
-    using L = Tile<M>;
-    static unsigned long long attr = 0;                   // one bit per device
-    cudaError_t e = smem_optin(reinterpret_cast<const void*>(k_fused<M, DIVONLY>), (int)L::bytes, &attr);
-    if (e != cudaSuccess) return e;
-    CUtensorMap mn, mm;
-    if (!DIVONLY) {
-        if (!cached_map(&mn, T, g) || !cached_map(&mm, Tm1, g)) return cudaErrorInvalidValue;
-    } else {
-        memset(&mn, 0, sizeof mn);
-        memset(&mm, 0, sizeof mm);
-    }
-    // chunk the z march so that the grid fills the GPU several times over
-    const int tiles = (g.Nx / kTX) * (g.Ny / kTY);
-    int kc = chunk_override();
-    if (kc <= 0) {
-        const int want = 152 * 2 * 8;                     // ~8 waves at 2 CTAs / SM
-        int chunks = (want + tiles - 1) / tiles;
-        chunks = max(1, min(chunks, g.nz));
-        kc = (g.nz + chunks - 1) / chunks;
-        kc = max(kc, 2);
-    }
-    const int chunks = (g.nz + kc - 1) / kc;
-    FusedArgs A{g, U, V, W, T, Tm1, Tp1, (float)c.a, (float)c.b, (float)c.gdt, kc, err, divmax};
-    dim3 grid(chunks, g.Nx / kTX, g.Ny / kTY);
-    k_fused<M, DIVONLY><<<grid, kThreadsAll, L::bytes, st>>>(mn, mm, A);
-    return cudaGetLastError();
-}
-
-}  // namespace
 
 bool fused_supported(const mr_config& cfg, std::string* why)
 {
@@ -614,28 +668,6 @@ int fused_take_error(cudaStream_t st)
     if (cudaStreamSynchronize(st) != cudaSuccess) return MR_ERR_CUDA;
     if (v) cudaMemsetAsync(flag, 0, sizeof(int), st);
     return v;
-}
-
-cudaError_t launch_step_fused_f32(const Grid<float>& g, const float* U, const float* V, const float* W,
-                                  const float* Tm1, const float* T, float* Tp1, StepCoef c, cudaStream_t st)
-{
-    int* err = fused_error_flag();
-    if (!err) return cudaErrorMemoryAllocation;
-    if (g.mx == 4) return launch_fused<4, false>(g, U, V, W, Tm1, T, Tp1, c, err, nullptr, st);
-    return launch_fused<2, false>(g, U, V, W, Tm1, T, Tp1, c, err, nullptr, st);
-}
-
-cudaError_t launch_maxdiv_fused_f32(const Grid<float>& g, const float* U, const float* V, const float* W,
-                                    double* partials, int blocks, cudaStream_t st)
-{
-    int* err = fused_error_flag();
-    if (!err) return cudaErrorMemoryAllocation;
-    cudaError_t e = cudaMemsetAsync(partials, 0, (size_t)blocks * sizeof(double), st);
-    if (e != cudaSuccess) return e;
-    unsigned long long* dm = reinterpret_cast<unsigned long long*>(partials);
-    StepCoef c{0, 0, 0};
-    if (g.mx == 4) return launch_fused<4, true>(g, U, V, W, nullptr, nullptr, nullptr, c, err, dm, st);
-    return launch_fused<2, true>(g, U, V, W, nullptr, nullptr, nullptr, c, err, dm, st);
 }
 
 }  // namespace mr

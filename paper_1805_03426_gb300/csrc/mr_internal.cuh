@@ -171,12 +171,15 @@ cudaError_t launch_nu_profile(const Grid<P>& g, const P* T, const P* Ws, const d
 template <typename P>
 cudaError_t launch_cfl(const Grid<P>& g, const P* Us, const P* Vs, const P* Ws, double* partials,
                        int blocks, cudaStream_t st);
-cudaError_t launch_step_fused_f32(const Grid<float>& g, const float* U, const float* V, const float* W,
-                                  const float* Tm1, const float* T, float* Tp1, StepCoef c,
-                                  cudaStream_t st);
-cudaError_t launch_maxdiv_fused_f32(const Grid<float>& g, const float* U, const float* V,
-                                    const float* W, double* partials, int blocks, cudaStream_t st);
 bool fused_supported(const mr_config& cfg, std::string* why);
+// MR_VEL_FUSED: every refinement stage in the step kernel (lc: the 12-wide layer
+// constants of xfused_layer_constants, rx12: the uniform R_x rows)
+cudaError_t launch_step_fused_f32(const Grid<float>& g, const float* U, const float* V, const float* W,
+                                   const float* lc, const float* rx12, const float* Tm1, const float* T, float* Tp1,
+                                   StepCoef c, cudaStream_t st);
+// kind 1: max |divergence| of the dense velocity, kind 2: max CFL rate (into partials[0])
+cudaError_t launch_fused_max_f32(const Grid<float>& g, int kind, const float* U, const float* V, const float* W,
+                                  const float* lc, const float* rx12, double* partials, int blocks, cudaStream_t st);
 int* fused_error_flag();
 // per-layer constant table [Nz][12] of the split-x kernel (layout owned by mr_xfused.cu)
 std::vector<float> xfused_layer_constants(int Nz, const double* zf, const double* zc, const double* dz, double kappa,
