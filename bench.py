@@ -53,8 +53,10 @@ SEED = 1805
 # DRAM bytes (read + write) per launch of the dominant kernel from one ncu capture of the
 # workload (summarised in profiles/), valid only for the kernel sources they were measured on.
 NCU_TRAFFIC = {
-    ("k_xfused", "rb512_stretched_f32"): {"bytes": 1198593000 + 384998400, "sources": "b6249ba9d53f7a08.8945e0b384d6ff21",
+    ("k_xfused", "rb512_stretched_f32"): {"bytes": 1197496000 + 384963584, "sources": "776ebe25c7dc8ec4.8945e0b384d6ff21",
                                           "files": ("mr_xfused.cu", "mr_ptx.cuh")},
+    ("k_fused", "rb512_stretched_f32"): {"bytes": 874101248 + 379460864, "sources": "f1e51fc86c764f71.8945e0b384d6ff21",
+                                         "files": ("mr_fused.cu", "mr_ptx.cuh")},
 }
 
 
