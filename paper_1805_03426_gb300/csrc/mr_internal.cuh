@@ -181,9 +181,11 @@ cudaError_t launch_step_fused_f32(const Grid<float>& g, const float* U, const fl
 cudaError_t launch_fused_max_f32(const Grid<float>& g, int kind, const float* U, const float* V, const float* W,
                                   const float* lc, const float* rx12, double* partials, int blocks, cudaStream_t st);
 int* fused_error_flag();
-// per-layer constant table [Nz][12] of the split-x kernel (layout owned by mr_xfused.cu)
+// per-layer constant table [Nz][lcw] of the split-x (pairs: 28 wide) and fully
+// fused (12 wide) kernels (layout owned by mr_xfused.cu)
 std::vector<float> xfused_layer_constants(int Nz, const double* zf, const double* zc, const double* dz, double kappa,
-                                          double dx, double dy, bool dirichlet, const double* f4z, int* lcw);
+                                          double dx, double dy, bool dirichlet, const double* f4z, bool pairs,
+                                          int* lcw);
 // Raise a kernel's dynamic shared-memory limit once per device (*done: one bit per device).
 cudaError_t smem_optin(const void* kernel, int bytes, unsigned long long* done);
 template <typename P>

@@ -64,7 +64,7 @@ struct XT {
     static constexpr int BYN = O4 ? TY + 4 : kBY;        // rows of the T^s box
     static constexpr uint32_t tn_bytes = (uint32_t)(kBX * BYN) * 4;
     static constexpr int PN = (int)((tn_bytes + 127) / 128) * 128 / 4;
-    static constexpr int LCW = O4 ? 20 : 12;            // floats of one row of layer constants
+    static constexpr int LCW = 28;                      // floats of one row of layer constants
     static constexpr int oTn = 0, oTm = PN;
     static constexpr int oWY = PN + PM;                 // [TY][BXC]      plane k+1
     static constexpr int oUO = oWY + TY * BXC;          // [TY][BXC]
@@ -72,7 +72,7 @@ struct XT {
     static constexpr int SET = ((2 * TY + TY + 1) * BXC + 31) / 32 * 32;     // one set, 128-B multiple
     static constexpr int DS = MT ? SET : 0;
     static constexpr int oLC = oWY + (MT ? 2 : 1) * SET;                     // [LCW] layer constants
-    static constexpr int slot = (((oLC + (O4 ? 20 : 16)) * 4 + 127) / 128) * 128 / 4;
+    static constexpr int slot = (((oLC + LCW) * 4 + 127) / 128) * 128 / 4;
     static constexpr int NSET = MT ? 2 : 1;
     static constexpr uint32_t wy_bytes = (uint32_t)(NSET * TY * BXC) * 4;
     static constexpr uint32_t bundle_bytes = (uint32_t)(NSET * (TY * BXC + (TY + 1) * BXC) + LCW) * 4;  // UO, VR, LC
@@ -105,6 +105,19 @@ __device__ __forceinline__ float rsplit(const float (&r)[3], float c0, float c1,
     return c1 + r[0] * (c0 - c1) + r[2] * (c2 - c1);
 }
 
+// The same split negated, in as many operations: -c1 + r0 (c1 - c0) + r2 (c1 - c2).
+__device__ __forceinline__ float nrsplit(const float (&r)[3], float c0, float c1, float c2)
+{
+    return -c1 + r[0] * (c1 - c0) + r[2] * (c1 - c2);
+}
+
+// Packed FP32 pairs: one instruction updates two cells (sm_100 and later).
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 lo2(float4 v) { return make_float2(v.x, v.y); }
+__device__ __forceinline__ float2 hi2(float4 v) { return make_float2(v.z, v.w); }
+
 // LF: a plain leapfrog step (a = 1, b = 0), by far the most frequent kind.
 // MT: the velocity is A + alpha (B - A) between the intermediates of two
 // coarse time levels (temporal refinement; the refinement is linear, so
@@ -126,6 +139,9 @@ k_xfused(const __grid_constant__ CUtensorMap tmn, const __grid_constant__ CUtens
     constexpr int kThreads = L::CONS;
     constexpr int NB = L::NB, BXC = L::BXC, NC = 4 / M, NW = kThreads / 32;
     constexpr bool DIVONLY = KIND != 0;
+    // PK: the second-order update runs on packed pairs of cells (0, 1), (2, 3);
+    // vn then holds the negated V split, the sign its flux enters with
+    constexpr bool PK = !DIVONLY && !O4;
     constexpr int OFF = O4 ? 2 : 1;                  // ring r carries plane k0 - OFF + r
     extern __shared__ __align__(128) float sm[];
     float* red = sm + L::oRed;
@@ -202,10 +218,15 @@ k_xfused(const __grid_constant__ CUtensorMap tmn, const __grid_constant__ CUtens
     float dmax = 0.f;
     const float kx2 = g.kx2, ky2 = g.ky2;
     const float ca = A.a, cbb = A.b, gdt = A.gdt, alpha = A.alpha;
+    const float2 kx2p = make_float2(kx2, kx2), ky2p = make_float2(ky2, ky2), gdtp = make_float2(gdt, gdt);
+    const float2 cap = make_float2(ca, ca), cbp = make_float2(cbb, cbb);
     // ring bookkeeping without divisions: slots of planes k-1, k, k+1 (and, with
-    // O4, k-2 and k+2) and the next (slot, parity) to wait for
-    int sb = O4 ? 1 : 0, sc = sb + 1, st = sc + 1, sm2 = 0, s2 = O4 ? 4 : 0;
-    int wslot = 0, wpar = 0, waited = 0;
+    // O4, k-2 and k+2).  Rings 0 .. 2 OFF - 1 (planes k0-OFF .. k0+OFF-1) are
+    // waited for before the layer loop; then layer k waits for one ring, that of
+    // plane k+OFF, in slot st (O4: s2) with parity tpar (2 OFF < NB)
+#pragma unroll
+    for (int r = 0; r < 2 * OFF; ++r)
+        if (!fail && !mbar_wait(&full[r], 0)) fail = true;
     const size_t plane = (size_t)g.Nx * g.Ny;
     float* outp = A.Tp1 + (size_t)k0 * plane + (size_t)(j0 + jl) * g.Nx + i0 + il0;
     const int o = (jl + 1) * kBX + il0 + 4;          // this segment's first cell in a plane box
@@ -213,13 +234,12 @@ k_xfused(const __grid_constant__ CUtensorMap tmn, const __grid_constant__ CUtens
 
     float wcar[4] = {0.f, 0.f, 0.f, 0.f};            // R_x split of W on plane k (from layer k-1)
     float fcar[4] = {0.f, 0.f, 0.f, 0.f};            // O4: advective flux W T_f through face k (from layer k-1)
-    for (int k = k0; k < k1; ++k) {
-        const int need = k - k0 + (O4 ? 4 : 2);  // ring of plane k+1 and this layer's bundle (O4: plane k+2)
-        while (!fail && waited <= need) {
-            if (!mbar_wait(&full[wslot], wpar)) { fail = true; break; }
-            ++waited;
-            if (++wslot == NB) { wslot = 0; wpar ^= 1; }
-        }
+    // one layer; sm2, sb, sc, st, s2: the slots of planes k-2 (O4), k-1, k, k+1
+    // and k+2 (O4); tpar: the parity of the ring of plane k+OFF
+    auto layer = [&](const int k, const int sm2, const int sb, const int sc, const int st, const int s2,
+                     const int tpar) {
+        // the ring of plane k+1 and of this layer's bundle (O4: of plane k+2)
+        if (!fail && !mbar_wait(&full[O4 ? s2 : st], tpar)) fail = true;
         if (!fail) {
             const float* bun = sm + st * L::slot;
             // layer constants (from the bundle, see xfused_layer_constants)
@@ -274,7 +294,8 @@ k_xfused(const __grid_constant__ CUtensorMap tmn, const __grid_constant__ CUtens
                     wb[a] = wcar[a];
                     wt[a] = rsplit(rx[a], ytv[cb], ytv[cb + 1], ytv[cb + 2]);
                     vs[a] = rsplit(rx[a], rsv[cb], rsv[cb + 1], rsv[cb + 2]);
-                    vn[a] = rsplit(rx[a], rnv[cb], rnv[cb + 1], rnv[cb + 2]);
+                    vn[a] = PK ? nrsplit(rx[a], rnv[cb], rnv[cb + 1], rnv[cb + 2])
+                               : rsplit(rx[a], rnv[cb], rnv[cb + 1], rnv[cb + 2]);
                 }
                 // stage X: cell balance, west to east, in units of U / (2 dx) (V is in
                 // units of V / (2 dy): the dx/dy factor of the balance cancels)
@@ -285,7 +306,7 @@ k_xfused(const __grid_constant__ CUtensorMap tmn, const __grid_constant__ CUtens
 #pragma unroll
                     for (int a = 0; a < M - 1; ++a) {
                         const int m = q * M + a;
-                        h = h - (vn[m] - vs[m]) - (wt[m] - wb[m]) * hz;
+                        h = (PK ? h + (vn[m] + vs[m]) : h - (vn[m] - vs[m])) - (wt[m] - wb[m]) * hz;
                         us[m + 1] = h;
                     }
                 }
@@ -438,41 +459,81 @@ k_xfused(const __grid_constant__ CUtensorMap tmn, const __grid_constant__ CUtens
                 const float4 dt4 = *reinterpret_cast<const float4*>(Pm_t + o);
                 const float tcv[6] = {tw, tc4.x, tc4.y, tc4.z, tc4.w, te};
                 const float dcv[6] = {dw, dc4.x, dc4.y, dc4.z, dc4.w, de};
-                const float tsv[4] = {ts4.x, ts4.y, ts4.z, ts4.w}, tnv[4] = {tn4.x, tn4.y, tn4.z, tn4.w};
-                const float dsv[4] = {ds4.x, ds4.y, ds4.z, ds4.w}, dnv[4] = {dn4.x, dn4.y, dn4.z, dn4.w};
-                const float tbv[4] = {tb4.x, tb4.y, tb4.z, tb4.w}, ttv[4] = {tt4.x, tt4.y, tt4.z, tt4.w};
-                const float dbv[4] = {db4.x, db4.y, db4.z, db4.w}, dtv[4] = {dt4.x, dt4.y, dt4.z, dt4.w};
-                // D = kx2 (dw + de) + ky2 (ds + dn) + cdn db + cup dt - diag dc + plate
-                float res[4];
+                // x fluxes in scalar form (adjacent cells share a face), then the rest
+                // of the update on the pairs (0, 1), (2, 3):
+                // D = kx2 (dw + de) + ky2 (ds + dn) + cdn db + cup dt - diag dc + plate,
+                // the pair constants of the row (each value twice) with -diag and the
+                // top-face weights negated, vn negated
+                const float4 q0 = *reinterpret_cast<const float4*>(bun + L::oLC + 12);   // bwlo, bwhi
+                const float4 q1 = *reinterpret_cast<const float4*>(bun + L::oLC + 16);   // -twlo, -twhi
+                const float4 q2 = *reinterpret_cast<const float4*>(bun + L::oLC + 20);   // cdn, cup
+                const float4 q3 = *reinterpret_cast<const float4*>(bun + L::oLC + 24);   // -diag, plate
+                float F[5], cxv[4], sdx[4];
+#pragma unroll
+                for (int a = 0; a < 5; ++a) F[a] = us[a] * (tcv[a] + tcv[a + 1]);
 #pragma unroll
                 for (int a = 0; a < 4; ++a) {
-                    const float tc = tcv[a + 1], dc = dcv[a + 1];
-                    const float cx = us[a] * (tcv[a] + tc) - us[a + 1] * (tc + tcv[a + 2]);
-                    const float cy = vs[a] * (tsv[a] + tc) - vn[a] * (tc + tnv[a]);
-                    const float cz = wb[a] * (bwlo * tbv[a] + bwhi * tc) - wt[a] * (twlo * tc + twhi * ttv[a]);
-                    const float D = kx2 * (dcv[a] + dcv[a + 2]) + ky2 * (dsv[a] + dnv[a]) + cdn * dbv[a] + cup * dtv[a] +
-                                    (plate - diag * dc);
-                    res[a] = LF ? dc + gdt * ((cx + cy + cz) + D) : ca * dc + cbb * tc + gdt * ((cx + cy + cz) + D);
+                    cxv[a] = F[a] - F[a + 1];
+                    sdx[a] = dcv[a] + dcv[a + 2];
                 }
-                *reinterpret_cast<float4*>(outp) = make_float4(res[0], res[1], res[2], res[3]);
+                float2 res[2];
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const float2 tc = h ? hi2(tc4) : lo2(tc4), dc = h ? hi2(dc4) : lo2(dc4);
+                    const float2 ts = h ? hi2(ts4) : lo2(ts4), tn = h ? hi2(tn4) : lo2(tn4);
+                    const float2 ds = h ? hi2(ds4) : lo2(ds4), dn = h ? hi2(dn4) : lo2(dn4);
+                    const float2 tb = h ? hi2(tb4) : lo2(tb4), tt = h ? hi2(tt4) : lo2(tt4);
+                    const float2 db = h ? hi2(db4) : lo2(db4), dt = h ? hi2(dt4) : lo2(dt4);
+                    const int a = 2 * h;
+                    float2 acc = fma2(kx2p, make_float2(sdx[a], sdx[a + 1]), hi2(q3));
+                    acc = fma2(ky2p, add2(ds, dn), acc);
+                    acc = fma2(lo2(q2), db, acc);
+                    acc = fma2(hi2(q2), dt, acc);
+                    acc = fma2(lo2(q3), dc, acc);
+                    acc = add2(acc, make_float2(cxv[a], cxv[a + 1]));
+                    acc = fma2(make_float2(vs[a], vs[a + 1]), add2(ts, tc), acc);
+                    acc = fma2(make_float2(vn[a], vn[a + 1]), add2(tc, tn), acc);
+                    acc = fma2(make_float2(wb[a], wb[a + 1]), fma2(lo2(q0), tb, mul2(hi2(q0), tc)), acc);
+                    acc = fma2(make_float2(wt[a], wt[a + 1]), fma2(lo2(q1), tc, mul2(hi2(q1), tt)), acc);
+                    res[h] = LF ? fma2(gdtp, acc, dc) : fma2(gdtp, acc, fma2(cap, dc, mul2(cbp, tc)));
+                }
+                *reinterpret_cast<float4*>(outp) = make_float4(res[0].x, res[0].y, res[1].x, res[1].y);
             }
         }
         // plane k-1 (and the bundle of layer k-2) are no longer needed by this thread
         if constexpr (O4) {
             if (k == k0) mbar_arrive(&empty[sm2]);   // plane k0-2 served the first layer only
             mbar_arrive(&empty[sb]);
+        } else {
+            mbar_arrive(&empty[sb]);
+        }
+        outp += plane;
+    };
+    if constexpr (!O4) {
+        // unrolled by the ring length: layer k0 + i uses the slots i, i+1, i+2
+        // (mod NB), constants in the inner loop
+        for (int kb = k0, opar = 0; kb < k1; kb += NB, opar ^= 1) {
+#pragma unroll
+            for (int u = 0; u < NB; ++u) {
+                if (kb + u >= k1) break;
+                layer(kb + u, 0, u % NB, (u + 1) % NB, (u + 2) % NB, 0, opar ^ (((u + 2) / NB) & 1));
+            }
+        }
+    } else {
+        // fourth order: the unrolled loop would outgrow the instruction cache, so
+        // the slots rotate
+        int sm2 = 0, sb = 1, sc = 2, st = 3, s2 = 4, tpar = 0;
+        for (int k = k0; k < k1; ++k) {
+            layer(k, sm2, sb, sc, st, s2, tpar);
             sm2 = sb;
             sb = sc;
             sc = st;
             st = s2;
-            s2 = (s2 + 1 == NB) ? 0 : s2 + 1;
-        } else {
-            mbar_arrive(&empty[sb]);
-            sb = sc;
-            sc = st;
-            st = (st + 1 == NB) ? 0 : st + 1;
+            if (++s2 == NB) {
+                s2 = 0;
+                tpar ^= 1;
+            }
         }
-        outp += plane;
     }
     if (consumers_sync_or<kThreads>(fail)) {
         if (tid == 0) atomicExch(A.err, MR_ERR_TIMEOUT);
@@ -808,8 +869,8 @@ cudaError_t launch_xfused_max_f32(const Grid<float>& g, int kind, const float* W
                                                            nullptr, c, err, dm, st);
 }
 
-// Per-layer constants of the split-x kernel, [Nz][lcw] floats (lcw = 12, or 20
-// with fourth-order faces), all folded on the host in FP64: 1/dz; the
+// Per-layer constants of the split-x kernel, [Nz][lcw] floats (lcw = 28 for the
+// split-x step, 12 for the fully fused one), all folded on the host in FP64: 1/dz; the
 // linear-interpolation weights of T_{k-1}, T_k at face k and of T_k, T_{k+1}
 // at face k+1, each times 1/dz (fourth order instead: the weights of planes
 // k-1 .. k+2 at face k+1); kappa/(dz d) toward the centre (or plate) below and
@@ -817,10 +878,14 @@ cudaError_t launch_xfused_max_f32(const Grid<float>& g, int kind, const float* W
 // (Dirichlet plates: cdn T_bottom on the first layer, cup T_top on the last);
 // 1/(2 dz); fourth order: the weights of planes k-2 .. k+1 at face k.  The
 // kernel reads zeros for the planes beyond the plates, where W is zero.
+// `pairs` (split-x, second order) appends at 12..27 each value of the update
+// twice, for the packed pair arithmetic: the face-k weights, the negated
+// face-(k+1) weights, cdn, cup, the negated diagonal and the plate term.
 std::vector<float> xfused_layer_constants(int Nz, const double* zf, const double* zc, const double* dz, double kappa,
-                                          double dx, double dy, bool dirichlet, const double* f4z, int* lcw)
+                                          double dx, double dy, bool dirichlet, const double* f4z, bool pairs,
+                                          int* lcw)
 {
-    *lcw = f4z ? 20 : 12;
+    *lcw = pairs ? 28 : (f4z ? 20 : 12);
     std::vector<float> lc((size_t)Nz * *lcw, 0.f);
     const double kx2 = kappa / (dx * dx), ky2 = kappa / (dy * dy);
     for (int k = 0; k < Nz; ++k) {
@@ -854,6 +919,10 @@ std::vector<float> xfused_layer_constants(int Nz, const double* zf, const double
         if (dirichlet && k == Nz - 1) plate += cup * (double)kTTop;
         q[8] = (float)plate;
         q[9] = (float)(0.5 * idz);
+        if (pairs && !f4z) {
+            const float pv[8] = {q[1], q[2], -q[3], -q[4], q[5], q[6], -q[7], q[8]};
+            for (int c = 0; c < 8; ++c) q[12 + 2 * c] = q[13 + 2 * c] = pv[c];
+        }
     }
     return lc;
 }
