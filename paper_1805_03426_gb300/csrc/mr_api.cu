@@ -458,7 +458,7 @@ int mr_create(const mr_config* cfg, mr_handle* out)
         alloc((void**)&b.xlc, (size_t)h->Nz * 28 * 4);
         alloc(&b.scrW, (size_t)(h->Nz + 1) * c.ny * c.nx * h->elt);
     } else if (c.velocity_mode == MR_VEL_FUSED) {
-        alloc((void**)&b.xlc, (size_t)h->Nz * 12 * 4);   // layer constants of the fused step
+        alloc((void**)&b.xlc, (size_t)h->Nz * 28 * 4);   // layer constants of the fused step
     }
     if (e != cudaSuccess) {
         int r = cuda_check(e, "mr_create: device allocation");
@@ -482,8 +482,7 @@ int mr_create(const mr_config* cfg, mr_handle* out)
         const std::vector<float> lc =
             xfused_layer_constants(h->Nz, h->zf.data(), h->zc.data(), h->dz.data(), h->kappa, c.lx / h->Nx,
                                    c.ly / h->Ny, c.bc_plates == MR_DIRICHLET,
-                                   c.face_order == 4 ? h->f4z.data() : nullptr,
-                                   c.velocity_mode == MR_VEL_XFUSED, &b.xlcw);
+                                   c.face_order == 4 ? h->f4z.data() : nullptr, &b.xlcw);
         // periodic uniform x and y: every face has the same fourth-order weights
         for (int q = 0; q < 4; ++q) {
             b.xw4[q] = (float)(2.0 * h->f4x[q]);

@@ -43,7 +43,7 @@ constexpr int kTX = 64, kTY = 8;                        // tile (cells)
 constexpr int kBX = kTX + 8, kBY = kTY + 2;             // scalar plane box (floats)
 constexpr int kCons = 16 * kTY;                         // consumer threads: 4-cell segments
 constexpr int kThreadsAll = kCons + 32;                 // + one producer warp
-constexpr int kLCW = 12;                                // layer-constant row (floats)
+constexpr int kLCW = 28;                                // layer-constant row (floats)
 
 template <int M>
 struct FX {
@@ -54,7 +54,7 @@ struct FX {
     static constexpr int PS = (int)((plane_bytes + 127) / 128) * 128 / 4;
     // ring slot (floats): T^s plane, T^{s-1} plane, the layer constants
     static constexpr int oTn = 0, oTm = PS, oLC = 2 * PS;
-    static constexpr int slot = (((oLC + 16) * 4 + 127) / 128) * 128 / 4;
+    static constexpr int slot = (((oLC + kLCW) * 4 + 127) / 128) * 128 / 4;
     // the slab's intermediates: WY [M+1][TY][BXC], UO [M][TY][BXC],
     // VR [M][TY+1][BXC], and the slab balance [M-1][CY+2][BXC]
     static constexpr int oWY = NB * slot;
@@ -100,6 +100,17 @@ __device__ __forceinline__ float rsplit3(const float (&r)[3], float c0, float c1
 {
     return c1 + r[0] * (c0 - c1) + r[2] * (c2 - c1);
 }
+// The same split negated, in as many operations.
+__device__ __forceinline__ float nrsplit3(const float (&r)[3], float c0, float c1, float c2)
+{
+    return -c1 + r[0] * (c1 - c0) + r[2] * (c1 - c2);
+}
+// Packed FP32 pairs: one instruction updates two cells (sm_100 and later).
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 lo2(float4 v) { return make_float2(v.x, v.y); }
+__device__ __forceinline__ float2 hi2(float4 v) { return make_float2(v.z, v.w); }
 
 // The slab's refinement intermediates (see the file comment), written by the
 // kCons consumer threads from the coarse faces staged in shared memory; ends
@@ -310,8 +321,11 @@ k_fused(const __grid_constant__ CUtensorMap tmn, const __grid_constant__ CUtenso
     float dmax = 0.f;
     const float kx2 = g.kx2, ky2 = g.ky2;
     const float ca = A.a, cbb = A.b, gdt = A.gdt;
-    int sb = 0, sc = 1, st = 2;                  // ring slots of planes k-1, k, k+1
-    int wslot = 0, wpar = 0, waited = 0;
+    const float2 kx2p = make_float2(kx2, kx2), ky2p = make_float2(ky2, ky2), gdtp = make_float2(gdt, gdt);
+    const float2 cap = make_float2(ca, ca), cbp = make_float2(cbb, cbb);
+    // PK: the update runs on packed pairs of cells (0, 1), (2, 3); vn then holds
+    // the negated V split, the sign its flux enters with
+    constexpr bool PK = !DIVONLY;
     const size_t plane = (size_t)g.Nx * g.Ny;
     float* outp = A.Tp1 + (size_t)k0 * plane + (size_t)(j0 + jl) * g.Nx + i0 + il0;
     const int o = (jl + 1) * kBX + il0 + 4;      // this segment's first cell in a plane box
@@ -321,19 +335,21 @@ k_fused(const __grid_constant__ CUtensorMap tmn, const __grid_constant__ CUtenso
 
     if (tid < 3 * kTY) sm[L::oRy + tid] = g.Ry[3 * j0 + tid];   // the tile's R_y rows (read after a barrier)
     float wcar[4] = {0.f, 0.f, 0.f, 0.f};        // R_x split of W on plane k (from layer k-1)
-    for (int k = k0; k < k1; ++k) {
+    // rings 0 and 1 (planes k0-1, k0) before the layer loop; then layer k waits
+    // for the ring of plane k+1 only
+    for (int r = 0; r < 2; ++r)
+        if (!fail && !mbar_wait(&full[r], 0)) fail = true;
+    // one layer; sb, sc, st: the ring slots of planes k-1, k, k+1, tpar: the
+    // parity of the ring of plane k+1
+    auto layer = [&](const int k, const int sb, const int sc, const int st, const int tpar) {
         const int K = k / M, i = k - K * M;
         if (i == 0) {
             // the previous slab's intermediates are no longer read: build this slab's
             asm volatile("barrier.cta.sync 1, %0;" ::"n"(kCons) : "memory");
             slab_prep<M>(A, sm, K, I0, J0, j0, tid);
         }
-        const int need = k - k0 + 2;             // ring of plane k+1 and of this layer's constants
-        while (!fail && waited <= need) {
-            if (!mbar_wait(&full[wslot], wpar)) { fail = true; break; }
-            ++waited;
-            if (++wslot == NB) { wslot = 0; wpar ^= 1; }
-        }
+        // the ring of plane k+1 and of this layer's constants
+        if (!fail && !mbar_wait(&full[st], tpar)) fail = true;
         if (!fail) {
             const float* lcp = sm + st * L::slot + L::oLC;
             const float4 c0 = *reinterpret_cast<const float4*>(lcp);
@@ -372,7 +388,8 @@ k_fused(const __grid_constant__ CUtensorMap tmn, const __grid_constant__ CUtenso
                     wb[a] = wcar[a];
                     wt[a] = rsplit3(rx[a], ytv[cb], ytv[cb + 1], ytv[cb + 2]);
                     vs[a] = rsplit3(rx[a], rsv[cb], rsv[cb + 1], rsv[cb + 2]);
-                    vn[a] = rsplit3(rx[a], rnv[cb], rnv[cb + 1], rnv[cb + 2]);
+                    vn[a] = PK ? nrsplit3(rx[a], rnv[cb], rnv[cb + 1], rnv[cb + 2])
+                               : rsplit3(rx[a], rnv[cb], rnv[cb + 1], rnv[cb + 2]);
                 }
                 // stage X: cell balance, west to east, in units of U / (2 dx)
 #pragma unroll
@@ -382,7 +399,7 @@ k_fused(const __grid_constant__ CUtensorMap tmn, const __grid_constant__ CUtenso
 #pragma unroll
                     for (int a = 0; a < M - 1; ++a) {
                         const int m = q * M + a;
-                        h = h - (vn[m] - vs[m]) - (wt[m] - wb[m]) * hz;
+                        h = (PK ? h + (vn[m] + vs[m]) : h - (vn[m] - vs[m])) - (wt[m] - wb[m]) * hz;
                         us[m + 1] = h;
                     }
                 }
@@ -440,30 +457,60 @@ k_fused(const __grid_constant__ CUtensorMap tmn, const __grid_constant__ CUtenso
                 const float4 dt4 = *reinterpret_cast<const float4*>(Pm_t + o);
                 const float tcv[6] = {tw, tc4.x, tc4.y, tc4.z, tc4.w, te};
                 const float dcv[6] = {dw, dc4.x, dc4.y, dc4.z, dc4.w, de};
-                const float tsv[4] = {ts4.x, ts4.y, ts4.z, ts4.w}, tnv[4] = {tn4.x, tn4.y, tn4.z, tn4.w};
-                const float dsv[4] = {ds4.x, ds4.y, ds4.z, ds4.w}, dnv[4] = {dn4.x, dn4.y, dn4.z, dn4.w};
-                const float tbv[4] = {tb4.x, tb4.y, tb4.z, tb4.w}, ttv[4] = {tt4.x, tt4.y, tt4.z, tt4.w};
-                const float dbv[4] = {db4.x, db4.y, db4.z, db4.w}, dtv[4] = {dt4.x, dt4.y, dt4.z, dt4.w};
-                float res[4];
+                // x fluxes in scalar form (adjacent cells share a face), then the
+                // rest on the pairs (0, 1), (2, 3) with the pair constants of the row:
+                // D = kx2 (dw + de) + ky2 (ds + dn) + cdn db + cup dt - diag dc + plate
+                const float4 q0 = *reinterpret_cast<const float4*>(lcp + 12);   // bwlo, bwhi
+                const float4 q1 = *reinterpret_cast<const float4*>(lcp + 16);   // -twlo, -twhi
+                const float4 q2 = *reinterpret_cast<const float4*>(lcp + 20);   // cdn, cup
+                const float4 q3 = *reinterpret_cast<const float4*>(lcp + 24);   // -diag, plate
+                float F[5], cxv[4], sdx[4];
+#pragma unroll
+                for (int a = 0; a < 5; ++a) F[a] = us[a] * (tcv[a] + tcv[a + 1]);
 #pragma unroll
                 for (int a = 0; a < 4; ++a) {
-                    const float tc = tcv[a + 1], dc = dcv[a + 1];
-                    const float cx = us[a] * (tcv[a] + tc) - us[a + 1] * (tc + tcv[a + 2]);
-                    const float cy = vs[a] * (tsv[a] + tc) - vn[a] * (tc + tnv[a]);
-                    const float cz = wb[a] * (bwlo * tbv[a] + bwhi * tc) - wt[a] * (twlo * tc + twhi * ttv[a]);
-                    const float D = kx2 * (dcv[a] + dcv[a + 2]) + ky2 * (dsv[a] + dnv[a]) + cdn * dbv[a] + cup * dtv[a] +
-                                    (plate - diag * dc);
-                    res[a] = LF ? dc + gdt * ((cx + cy + cz) + D) : ca * dc + cbb * tc + gdt * ((cx + cy + cz) + D);
+                    cxv[a] = F[a] - F[a + 1];
+                    sdx[a] = dcv[a] + dcv[a + 2];
                 }
-                *reinterpret_cast<float4*>(outp) = make_float4(res[0], res[1], res[2], res[3]);
+                float2 res[2];
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const float2 tc = h ? hi2(tc4) : lo2(tc4), dc = h ? hi2(dc4) : lo2(dc4);
+                    const float2 ts = h ? hi2(ts4) : lo2(ts4), tn = h ? hi2(tn4) : lo2(tn4);
+                    const float2 ds = h ? hi2(ds4) : lo2(ds4), dn = h ? hi2(dn4) : lo2(dn4);
+                    const float2 tb = h ? hi2(tb4) : lo2(tb4), tt = h ? hi2(tt4) : lo2(tt4);
+                    const float2 db = h ? hi2(db4) : lo2(db4), dt = h ? hi2(dt4) : lo2(dt4);
+                    const int a = 2 * h;
+                    float2 acc = fma2(kx2p, make_float2(sdx[a], sdx[a + 1]), hi2(q3));
+                    acc = fma2(ky2p, add2(ds, dn), acc);
+                    acc = fma2(lo2(q2), db, acc);
+                    acc = fma2(hi2(q2), dt, acc);
+                    acc = fma2(lo2(q3), dc, acc);
+                    acc = add2(acc, make_float2(cxv[a], cxv[a + 1]));
+                    acc = fma2(make_float2(vs[a], vs[a + 1]), add2(ts, tc), acc);
+                    acc = fma2(make_float2(vn[a], vn[a + 1]), add2(tc, tn), acc);
+                    acc = fma2(make_float2(wb[a], wb[a + 1]), fma2(lo2(q0), tb, mul2(hi2(q0), tc)), acc);
+                    acc = fma2(make_float2(wt[a], wt[a + 1]), fma2(lo2(q1), tc, mul2(hi2(q1), tt)), acc);
+                    res[h] = LF ? fma2(gdtp, acc, dc) : fma2(gdtp, acc, fma2(cap, dc, mul2(cbp, tc)));
+                }
+                *reinterpret_cast<float4*>(outp) = make_float4(res[0].x, res[0].y, res[1].x, res[1].y);
             }
         }
         // plane k-1 is no longer needed by this thread
         mbar_arrive(&empty[sb]);
+        outp += plane;
+    };
+    // the slots rotate (a loop unrolled by the ring length would copy the slab
+    // build into every layer and outgrow the instruction cache)
+    int sb = 0, sc = 1, st = 2, tpar = 0;
+    for (int k = k0; k < k1; ++k) {
+        layer(k, sb, sc, st, tpar);
         sb = sc;
         sc = st;
-        st = (st + 1 == NB) ? 0 : st + 1;
-        outp += plane;
+        if (++st == NB) {
+            st = 0;
+            tpar ^= 1;
+        }
     }
     if (consumers_sync_or<kCons>(fail)) {
         if (tid == 0) atomicExch(A.err, MR_ERR_TIMEOUT);

@@ -172,7 +172,7 @@ template <typename P>
 cudaError_t launch_cfl(const Grid<P>& g, const P* Us, const P* Vs, const P* Ws, double* partials,
                        int blocks, cudaStream_t st);
 bool fused_supported(const mr_config& cfg, std::string* why);
-// MR_VEL_FUSED: every refinement stage in the step kernel (lc: the 12-wide layer
+// MR_VEL_FUSED: every refinement stage in the step kernel (lc: the layer
 // constants of xfused_layer_constants, rx12: the uniform R_x rows)
 cudaError_t launch_step_fused_f32(const Grid<float>& g, const float* U, const float* V, const float* W,
                                    const float* lc, const float* rx12, const float* Tm1, const float* T, float* Tp1,
@@ -181,11 +181,10 @@ cudaError_t launch_step_fused_f32(const Grid<float>& g, const float* U, const fl
 cudaError_t launch_fused_max_f32(const Grid<float>& g, int kind, const float* U, const float* V, const float* W,
                                   const float* lc, const float* rx12, double* partials, int blocks, cudaStream_t st);
 int* fused_error_flag();
-// per-layer constant table [Nz][lcw] of the split-x (pairs: 28 wide) and fully
-// fused (12 wide) kernels (layout owned by mr_xfused.cu)
+// per-layer constant table [Nz][28] of the split-x and fully fused kernels
+// (layout owned by mr_xfused.cu)
 std::vector<float> xfused_layer_constants(int Nz, const double* zf, const double* zc, const double* dz, double kappa,
-                                          double dx, double dy, bool dirichlet, const double* f4z, bool pairs,
-                                          int* lcw);
+                                          double dx, double dy, bool dirichlet, const double* f4z, int* lcw);
 // Raise a kernel's dynamic shared-memory limit once per device (*done: one bit per device).
 cudaError_t smem_optin(const void* kernel, int bytes, unsigned long long* done);
 template <typename P>

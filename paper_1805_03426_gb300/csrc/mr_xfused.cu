@@ -736,11 +736,12 @@ cudaError_t launch_xt(const Grid<float>& g, XSet v0, XSet v1, float alpha, int n
     const int tiles = (g.Nx / kTX) * (g.Ny / TY);
     int kcl = kcl_override();
     if (kcl <= 0) {
-        // ~12 waves of resident CTAs, but no chunk longer than 96 layers: on
+        // ~20 waves of resident CTAs, but no chunk longer than 96 layers: on
         // large grids long chunks leave the resident CTAs far apart in z
         // (measured on 1536 x 1536 x 1024: 512 layers 8.8 ms, 64-128 layers
-        // 7.0 ms, 96 layers 6.8 ms per step)
-        const int want = 152 * L::CTAS * 12;
+        // 7.0 ms, 96 layers 6.8 ms per step; on 512 x 512 x 384, 64x8 tiles:
+        // 8 layers 0.300 ms, 12: 0.287, 16: 0.284, 26: 0.286, 48: 0.305)
+        const int want = 152 * L::CTAS * 20;
         int chunks = (want + tiles - 1) / tiles;
         chunks = max(1, min(chunks, g.Nz / 4));
         kcl = min((g.Nz + chunks - 1) / chunks, 96);
@@ -869,8 +870,8 @@ cudaError_t launch_xfused_max_f32(const Grid<float>& g, int kind, const float* W
                                                            nullptr, c, err, dm, st);
 }
 
-// Per-layer constants of the split-x kernel, [Nz][lcw] floats (lcw = 28 for the
-// split-x step, 12 for the fully fused one), all folded on the host in FP64: 1/dz; the
+// Per-layer constants of the split-x and fully fused kernels, [Nz][28] floats,
+// all folded on the host in FP64: 1/dz; the
 // linear-interpolation weights of T_{k-1}, T_k at face k and of T_k, T_{k+1}
 // at face k+1, each times 1/dz (fourth order instead: the weights of planes
 // k-1 .. k+2 at face k+1); kappa/(dz d) toward the centre (or plate) below and
@@ -878,14 +879,13 @@ cudaError_t launch_xfused_max_f32(const Grid<float>& g, int kind, const float* W
 // (Dirichlet plates: cdn T_bottom on the first layer, cup T_top on the last);
 // 1/(2 dz); fourth order: the weights of planes k-2 .. k+1 at face k.  The
 // kernel reads zeros for the planes beyond the plates, where W is zero.
-// `pairs` (split-x, second order) appends at 12..27 each value of the update
-// twice, for the packed pair arithmetic: the face-k weights, the negated
-// face-(k+1) weights, cdn, cup, the negated diagonal and the plate term.
+// Second order: entries 12..27 hold each value of the update twice, for the
+// packed pair arithmetic: the face-k weights, the negated face-(k+1) weights,
+// cdn, cup, the negated diagonal and the plate term.
 std::vector<float> xfused_layer_constants(int Nz, const double* zf, const double* zc, const double* dz, double kappa,
-                                          double dx, double dy, bool dirichlet, const double* f4z, bool pairs,
-                                          int* lcw)
+                                          double dx, double dy, bool dirichlet, const double* f4z, int* lcw)
 {
-    *lcw = pairs ? 28 : (f4z ? 20 : 12);
+    *lcw = 28;
     std::vector<float> lc((size_t)Nz * *lcw, 0.f);
     const double kx2 = kappa / (dx * dx), ky2 = kappa / (dy * dy);
     for (int k = 0; k < Nz; ++k) {
@@ -919,7 +919,7 @@ std::vector<float> xfused_layer_constants(int Nz, const double* zf, const double
         if (dirichlet && k == Nz - 1) plate += cup * (double)kTTop;
         q[8] = (float)plate;
         q[9] = (float)(0.5 * idz);
-        if (pairs && !f4z) {
+        if (!f4z) {
             const float pv[8] = {q[1], q[2], -q[3], -q[4], q[5], q[6], -q[7], q[8]};
             for (int c = 0; c < 8; ++c) q[12 + 2 * c] = q[13 + 2 * c] = pv[c];
         }
