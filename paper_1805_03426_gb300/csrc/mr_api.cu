@@ -455,10 +455,10 @@ int mr_create(const mr_config* cfg, mr_handle* out)
         alloc((void**)&b.xwy, (size_t)(h->Nz + 1) * h->Ny * b.nxg * 4);
         alloc((void**)&b.xuo, (size_t)h->Nz * h->Ny * b.nxg * 4);
         alloc((void**)&b.xvr, (size_t)h->Nz * (h->Ny + 1) * b.nxg * 4);
-        alloc((void**)&b.xlc, (size_t)h->Nz * 28 * 4);
+        alloc((void**)&b.xlc, (size_t)h->Nz * 32 * 4);
         alloc(&b.scrW, (size_t)(h->Nz + 1) * c.ny * c.nx * h->elt);
     } else if (c.velocity_mode == MR_VEL_FUSED) {
-        alloc((void**)&b.xlc, (size_t)h->Nz * 28 * 4);   // layer constants of the fused step
+        alloc((void**)&b.xlc, (size_t)h->Nz * 32 * 4);   // layer constants of the fused step
     }
     if (e != cudaSuccess) {
         int r = cuda_check(e, "mr_create: device allocation");

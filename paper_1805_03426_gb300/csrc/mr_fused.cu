@@ -43,7 +43,7 @@ constexpr int kTX = 64, kTY = 8;                        // tile (cells)
 constexpr int kBX = kTX + 8, kBY = kTY + 2;             // scalar plane box (floats)
 constexpr int kCons = 16 * kTY;                         // consumer threads: 4-cell segments
 constexpr int kThreadsAll = kCons + 32;                 // + one producer warp
-constexpr int kLCW = 28;                                // layer-constant row (floats)
+constexpr int kLCW = 32;                                // layer-constant row (floats)
 
 template <int M>
 struct FX {
@@ -352,11 +352,8 @@ k_fused(const __grid_constant__ CUtensorMap tmn, const __grid_constant__ CUtenso
         if (!fail && !mbar_wait(&full[st], tpar)) fail = true;
         if (!fail) {
             const float* lcp = sm + st * L::slot + L::oLC;
-            const float4 c0 = *reinterpret_cast<const float4*>(lcp);
-            const float4 c1 = *reinterpret_cast<const float4*>(lcp + 4);
-            const float2 c2 = *reinterpret_cast<const float2*>(lcp + 8);
-            const float inv_dz = c0.x, bwlo = c0.y, bwhi = c0.z, twlo = c0.w;
-            const float twhi = c1.x, cdn = c1.y, cup = c1.z, diag = c1.w, plate = c2.x, hz = c2.y;
+            const float2 c0 = *reinterpret_cast<const float2*>(lcp);
+            const float inv_dz = c0.x, hz = c0.y;
             float wb[4], wt[4], vs[4], vn[4], us[5];
             {
                 // R_x splits of the full-width W (planes k, k+1) and V (faces jl, jl+1)

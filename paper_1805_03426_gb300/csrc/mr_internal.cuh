@@ -73,7 +73,7 @@ struct DeviceBuffers {
     float* xwy = nullptr;                      // [Nz+1][Ny][nxg]
     float* xuo = nullptr;                      // [Nz][Ny][nxg]
     float* xvr = nullptr;                      // [Nz][Ny+1][nxg]
-    float* xlc = nullptr;                      // [Nz][12]
+    float* xlc = nullptr;                      // [Nz][32] layer constants of the fused steps
     float xrx[12] = {0};                       // R_x rows of the 4 cells of a 4-cell segment
     float xw4[8] = {0};                        // fourth order: twice the x and y face weights (uniform)
     int xlcw = 12;                             // row length of xlc
@@ -181,7 +181,7 @@ cudaError_t launch_step_fused_f32(const Grid<float>& g, const float* U, const fl
 cudaError_t launch_fused_max_f32(const Grid<float>& g, int kind, const float* U, const float* V, const float* W,
                                   const float* lc, const float* rx12, double* partials, int blocks, cudaStream_t st);
 int* fused_error_flag();
-// per-layer constant table [Nz][28] of the split-x and fully fused kernels
+// per-layer constant table [Nz][32] of the split-x and fully fused kernels
 // (layout owned by mr_xfused.cu)
 std::vector<float> xfused_layer_constants(int Nz, const double* zf, const double* zc, const double* dz, double kappa,
                                           double dx, double dy, bool dirichlet, const double* f4z, int* lcw);

@@ -64,7 +64,7 @@ struct XT {
     static constexpr int BYN = O4 ? TY + 4 : kBY;        // rows of the T^s box
     static constexpr uint32_t tn_bytes = (uint32_t)(kBX * BYN) * 4;
     static constexpr int PN = (int)((tn_bytes + 127) / 128) * 128 / 4;
-    static constexpr int LCW = 28;                      // floats of one row of layer constants
+    static constexpr int LCW = 32;                      // floats of one row of layer constants
     static constexpr int oTn = 0, oTm = PN;
     static constexpr int oWY = PN + PM;                 // [TY][BXC]      plane k+1
     static constexpr int oUO = oWY + TY * BXC;          // [TY][BXC]
@@ -86,7 +86,7 @@ struct XArgs {
     const float* Tn;     // T^s (global, for the periodic halo of edge threads)
     const float* Tm;     // T^{s-1}
     float* Tp1;          // T^{s+1}
-    const float* lc;     // [Nz][12] per-layer constants
+    const float* lc;     // [Nz][32] per-layer constants
     float a, b, gdt;
     int kcl;             // dense layers per CTA chunk
     int* err;
@@ -139,9 +139,9 @@ k_xfused(const __grid_constant__ CUtensorMap tmn, const __grid_constant__ CUtens
     constexpr int kThreads = L::CONS;
     constexpr int NB = L::NB, BXC = L::BXC, NC = 4 / M, NW = kThreads / 32;
     constexpr bool DIVONLY = KIND != 0;
-    // PK: the second-order update runs on packed pairs of cells (0, 1), (2, 3);
-    // vn then holds the negated V split, the sign its flux enters with
-    constexpr bool PK = !DIVONLY && !O4;
+    // PK: the update runs on packed pairs of cells (0, 1), (2, 3); vn then
+    // holds the negated V split, the sign its flux enters with
+    constexpr bool PK = !DIVONLY;
     constexpr int OFF = O4 ? 2 : 1;                  // ring r carries plane k0 - OFF + r
     extern __shared__ __align__(128) float sm[];
     float* red = sm + L::oRed;
@@ -220,6 +220,9 @@ k_xfused(const __grid_constant__ CUtensorMap tmn, const __grid_constant__ CUtens
     const float ca = A.a, cbb = A.b, gdt = A.gdt, alpha = A.alpha;
     const float2 kx2p = make_float2(kx2, kx2), ky2p = make_float2(ky2, ky2), gdtp = make_float2(gdt, gdt);
     const float2 cap = make_float2(ca, ca), cbp = make_float2(cbb, cbb);
+    // O4: twice the y-face weights of rows j-2 .. j+1 (uniform), as pairs
+    const float2 wy0p = make_float2(A.w4y[0], A.w4y[0]), wy1p = make_float2(A.w4y[1], A.w4y[1]);
+    const float2 wy2p = make_float2(A.w4y[2], A.w4y[2]), wy3p = make_float2(A.w4y[3], A.w4y[3]);
     // ring bookkeeping without divisions: slots of planes k-1, k, k+1 (and, with
     // O4, k-2 and k+2).  Rings 0 .. 2 OFF - 1 (planes k0-OFF .. k0+OFF-1) are
     // waited for before the layer loop; then layer k waits for one ring, that of
@@ -233,7 +236,7 @@ k_xfused(const __grid_constant__ CUtensorMap tmn, const __grid_constant__ CUtens
     const int o4 = (jl + 2) * kBX + il0 + 4;         // the same in the O4 T^s box (two halo rows)
 
     float wcar[4] = {0.f, 0.f, 0.f, 0.f};            // R_x split of W on plane k (from layer k-1)
-    float fcar[4] = {0.f, 0.f, 0.f, 0.f};            // O4: advective flux W T_f through face k (from layer k-1)
+    float2 fcar[2] = {};                             // O4: advective flux W T_f through face k (from layer k-1)
     // one layer; sm2, sb, sc, st, s2: the slots of planes k-2 (O4), k-1, k, k+1
     // and k+2 (O4); tpar: the parity of the ring of plane k+OFF
     auto layer = [&](const int k, const int sm2, const int sb, const int sc, const int st, const int s2,
@@ -243,11 +246,8 @@ k_xfused(const __grid_constant__ CUtensorMap tmn, const __grid_constant__ CUtens
         if (!fail) {
             const float* bun = sm + st * L::slot;
             // layer constants (from the bundle, see xfused_layer_constants)
-            const float4 c0 = *reinterpret_cast<const float4*>(bun + L::oLC);
-            const float4 c1 = *reinterpret_cast<const float4*>(bun + L::oLC + 4);
-            const float2 c2 = *reinterpret_cast<const float2*>(bun + L::oLC + 8);
-            const float inv_dz = c0.x, bwlo = c0.y, bwhi = c0.z, twlo = c0.w;
-            const float twhi = c1.x, cdn = c1.y, cup = c1.z, diag = c1.w, plate = c2.x, hz = c2.y;
+            const float2 c0 = *reinterpret_cast<const float2*>(bun + L::oLC);
+            const float inv_dz = c0.x, hz = c0.y;
             float wb[4], wt[4], vs[4], vn[4], us[5];
             {
                 // R_x splits of the full-width W (planes k, k+1) and V (faces jl, jl+1);
@@ -375,47 +375,68 @@ k_xfused(const __grid_constant__ CUtensorMap tmn, const __grid_constant__ CUtens
                 const float4 t24 = *reinterpret_cast<const float4*>(Pn_2 + o4);
                 const float t8[8] = {tw2, tw1, tc4.x, tc4.y, tc4.z, tc4.w, te1, te2};
                 const float dcv[6] = {dw, dc4.x, dc4.y, dc4.z, dc4.w, de};
-                const float tsv[4] = {ts4.x, ts4.y, ts4.z, ts4.w}, tnv[4] = {tn4.x, tn4.y, tn4.z, tn4.w};
-                const float ts2v[4] = {ts24.x, ts24.y, ts24.z, ts24.w}, tn2v[4] = {tn24.x, tn24.y, tn24.z, tn24.w};
-                const float dsv[4] = {ds4.x, ds4.y, ds4.z, ds4.w}, dnv[4] = {dn4.x, dn4.y, dn4.z, dn4.w};
-                const float tbv[4] = {tb4.x, tb4.y, tb4.z, tb4.w}, ttv[4] = {tt4.x, tt4.y, tt4.z, tt4.w};
-                const float t2v[4] = {t24.x, t24.y, t24.z, t24.w};
-                const float dbv[4] = {db4.x, db4.y, db4.z, db4.w}, dtv[4] = {dt4.x, dt4.y, dt4.z, dt4.w};
                 const auto& wx = A.w4x;
-                const auto& wy = A.w4y;
-                // twice the face values of the segment's five x faces (us holds U / (2 dx))
-                float fx[5];
+                // twice the face values of the segment's five x faces (us holds U / (2 dx)),
+                // and the x fluxes in scalar form (adjacent cells share a face)
+                float F[5], cxv[4], sdx[4];
 #pragma unroll
-                for (int a = 0; a < 5; ++a) fx[a] = wx[0] * t8[a] + wx[1] * t8[a + 1] + wx[2] * t8[a + 2] + wx[3] * t8[a + 3];
-                // z-face k+1: weights of planes k-1 .. k+2; face k from the previous layer
-                const float zt0 = bwlo, zt1 = bwhi, zt2 = twlo, zt3 = twhi;
+                for (int a = 0; a < 5; ++a)
+                    F[a] = us[a] * (wx[0] * t8[a] + wx[1] * t8[a + 1] + wx[2] * t8[a + 2] + wx[3] * t8[a + 3]);
+#pragma unroll
+                for (int a = 0; a < 4; ++a) {
+                    cxv[a] = F[a] - F[a + 1];
+                    sdx[a] = dcv[a] + dcv[a + 2];
+                }
                 if (k == k0) {
                     // the chunk's first layer: face k from planes k-2 .. k+1
                     const float* Pn_m2 = sm + sm2 * L::slot + L::oTn;
                     const float4 tm4 = *reinterpret_cast<const float4*>(Pn_m2 + o4);
-                    const float2 zb01 = *reinterpret_cast<const float2*>(bun + L::oLC + 10);
-                    const float2 zb23 = *reinterpret_cast<const float2*>(bun + L::oLC + 12);
-                    const float tmv[4] = {tm4.x, tm4.y, tm4.z, tm4.w};
+                    const float4 zb = *reinterpret_cast<const float4*>(bun + L::oLC + 4);
+                    const float tmv[4] = {tm4.x, tm4.y, tm4.z, tm4.w}, tbv[4] = {tb4.x, tb4.y, tb4.z, tb4.w};
+                    const float ttv[4] = {tt4.x, tt4.y, tt4.z, tt4.w};
+                    float f[4];
 #pragma unroll
                     for (int a = 0; a < 4; ++a)
-                        fcar[a] = wb[a] * (zb01.x * tmv[a] + zb01.y * tbv[a] + zb23.x * t8[a + 2] + zb23.y * ttv[a]);
+                        f[a] = wb[a] * (zb.x * tmv[a] + zb.y * tbv[a] + zb.z * t8[a + 2] + zb.w * ttv[a]);
+                    fcar[0] = make_float2(f[0], f[1]);
+                    fcar[1] = make_float2(f[2], f[3]);
                 }
-                float res[4];
+                // the rest on the pairs (0, 1), (2, 3) with the pair constants of the row:
+                // face-(k+1) weights of planes k-1 .. k+2, cdn, cup, -diag, plate, 1/dz, -1/dz
+                const float4 q0 = *reinterpret_cast<const float4*>(bun + L::oLC + 12);
+                const float4 q1 = *reinterpret_cast<const float4*>(bun + L::oLC + 16);
+                const float4 q2 = *reinterpret_cast<const float4*>(bun + L::oLC + 20);
+                const float4 q3 = *reinterpret_cast<const float4*>(bun + L::oLC + 24);
+                const float4 q4 = *reinterpret_cast<const float4*>(bun + L::oLC + 28);
+                float2 res[2];
 #pragma unroll
-                for (int a = 0; a < 4; ++a) {
-                    const float tc = t8[a + 2], dc = dcv[a + 1];
-                    const float cx = us[a] * fx[a] - us[a + 1] * fx[a + 1];
-                    const float fs = wy[0] * ts2v[a] + wy[1] * tsv[a] + wy[2] * tc + wy[3] * tnv[a];
-                    const float fn = wy[0] * tsv[a] + wy[1] * tc + wy[2] * tnv[a] + wy[3] * tn2v[a];
-                    const float cy = vs[a] * fs - vn[a] * fn;
-                    const float ft = wt[a] * (zt0 * tbv[a] + zt1 * tc + zt2 * ttv[a] + zt3 * t2v[a]);
-                    const float cz = (fcar[a] - ft) * inv_dz;
-                    fcar[a] = ft;
-                    const float D = kx2 * (dcv[a] + dcv[a + 2]) + ky2 * (dsv[a] + dnv[a]) + cdn * dbv[a] + cup * dtv[a] +
-                                    (plate - diag * dc);
-                    res[a] = LF ? dc + gdt * ((cx + cy + cz) + D) : ca * dc + cbb * t8[a + 2] + gdt * ((cx + cy + cz) + D);
+                for (int h = 0; h < 2; ++h) {
+                    const float2 tc = h ? hi2(tc4) : lo2(tc4), dc = h ? hi2(dc4) : lo2(dc4);
+                    const float2 ts = h ? hi2(ts4) : lo2(ts4), tn = h ? hi2(tn4) : lo2(tn4);
+                    const float2 ts2 = h ? hi2(ts24) : lo2(ts24), tn2 = h ? hi2(tn24) : lo2(tn24);
+                    const float2 ds = h ? hi2(ds4) : lo2(ds4), dn = h ? hi2(dn4) : lo2(dn4);
+                    const float2 tb = h ? hi2(tb4) : lo2(tb4), tt = h ? hi2(tt4) : lo2(tt4);
+                    const float2 t2 = h ? hi2(t24) : lo2(t24);
+                    const float2 db = h ? hi2(db4) : lo2(db4), dt = h ? hi2(dt4) : lo2(dt4);
+                    const int a = 2 * h;
+                    float2 acc = fma2(kx2p, make_float2(sdx[a], sdx[a + 1]), hi2(q3));
+                    acc = fma2(ky2p, add2(ds, dn), acc);
+                    acc = fma2(lo2(q2), db, acc);
+                    acc = fma2(hi2(q2), dt, acc);
+                    acc = fma2(lo2(q3), dc, acc);
+                    acc = add2(acc, make_float2(cxv[a], cxv[a + 1]));
+                    const float2 fs = fma2(wy0p, ts2, fma2(wy1p, ts, fma2(wy2p, tc, mul2(wy3p, tn))));
+                    const float2 fn = fma2(wy0p, ts, fma2(wy1p, tc, fma2(wy2p, tn, mul2(wy3p, tn2))));
+                    acc = fma2(make_float2(vs[a], vs[a + 1]), fs, acc);
+                    acc = fma2(make_float2(vn[a], vn[a + 1]), fn, acc);
+                    const float2 ft = mul2(make_float2(wt[a], wt[a + 1]),
+                                           fma2(lo2(q0), tb, fma2(hi2(q0), tc, fma2(lo2(q1), tt, mul2(hi2(q1), t2)))));
+                    acc = fma2(lo2(q4), fcar[h], acc);
+                    acc = fma2(hi2(q4), ft, acc);
+                    fcar[h] = ft;
+                    res[h] = LF ? fma2(gdtp, acc, dc) : fma2(gdtp, acc, fma2(cap, dc, mul2(cbp, tc)));
                 }
-                *reinterpret_cast<float4*>(outp) = make_float4(res[0], res[1], res[2], res[3]);
+                *reinterpret_cast<float4*>(outp) = make_float4(res[0].x, res[0].y, res[1].x, res[1].y);
             } else {
                 const float* Pn_b = sm + sb * L::slot + L::oTn;
                 const float* Pm_b = sm + sb * L::slot + L::oTm;
@@ -870,22 +891,23 @@ cudaError_t launch_xfused_max_f32(const Grid<float>& g, int kind, const float* W
                                                            nullptr, c, err, dm, st);
 }
 
-// Per-layer constants of the split-x and fully fused kernels, [Nz][28] floats,
-// all folded on the host in FP64: 1/dz; the
-// linear-interpolation weights of T_{k-1}, T_k at face k and of T_k, T_{k+1}
-// at face k+1, each times 1/dz (fourth order instead: the weights of planes
-// k-1 .. k+2 at face k+1); kappa/(dz d) toward the centre (or plate) below and
-// above; the diagonal 2 kappa/dx^2 + 2 kappa/dy^2 + cdn + cup; the plate term
-// (Dirichlet plates: cdn T_bottom on the first layer, cup T_top on the last);
-// 1/(2 dz); fourth order: the weights of planes k-2 .. k+1 at face k.  The
-// kernel reads zeros for the planes beyond the plates, where W is zero.
-// Second order: entries 12..27 hold each value of the update twice, for the
-// packed pair arithmetic: the face-k weights, the negated face-(k+1) weights,
-// cdn, cup, the negated diagonal and the plate term.
+// Per-layer constants of the split-x and fully fused kernels, [Nz][32] floats,
+// all folded on the host in FP64.  The pair entries hold each value twice, for
+// the packed pair arithmetic of the update:
+//   0: 1/dz, 1: 1/(2 dz), 4..7: fourth order only, the weights of planes
+//   k-2 .. k+1 at face k (the first layer of a chunk);
+//   12..19 (pairs): second order, the linear-interpolation weights of T_{k-1},
+//   T_k at face k and the negated weights of T_k, T_{k+1} at face k+1, each
+//   times 1/dz; fourth order, the weights of planes k-1 .. k+2 at face k+1;
+//   20..27 (pairs): kappa/(dz d) toward the centre (or plate) below and above,
+//   the negated diagonal 2 kappa/dx^2 + 2 kappa/dy^2 + cdn + cup, the plate term
+//   (Dirichlet plates: cdn T_bottom on the first layer, cup T_top on the last);
+//   28..31: fourth order only, the pairs 1/dz and -1/dz.
+// The kernels read zeros for the planes beyond the plates, where W is zero.
 std::vector<float> xfused_layer_constants(int Nz, const double* zf, const double* zc, const double* dz, double kappa,
                                           double dx, double dy, bool dirichlet, const double* f4z, int* lcw)
 {
-    *lcw = 28;
+    *lcw = 32;
     std::vector<float> lc((size_t)Nz * *lcw, 0.f);
     const double kx2 = kappa / (dx * dx), ky2 = kappa / (dy * dy);
     for (int k = 0; k < Nz; ++k) {
@@ -895,34 +917,31 @@ std::vector<float> xfused_layer_constants(int Nz, const double* zf, const double
         const double above = k < Nz - 1 ? zc[k + 1] - zc[k] : zf[Nz] - zc[Nz - 1];
         const double cdn = (k > 0 || dirichlet) ? kappa / (dzk * below) : 0.0;
         const double cup = (k < Nz - 1 || dirichlet) ? kappa / (dzk * above) : 0.0;
-        q[0] = (float)idz;
+        double zw[4] = {0.0, 0.0, 0.0, 0.0};
         if (f4z) {
             for (int c = 0; c < 4; ++c) {
-                q[1 + c] = (float)f4z[4 * (size_t)(k + 1) + c];    // face k+1: planes k-1 .. k+2
-                q[10 + c] = (float)f4z[4 * (size_t)k + c];         // face k: planes k-2 .. k+1
+                zw[c] = f4z[4 * (size_t)(k + 1) + c];             // face k+1: planes k-1 .. k+2
+                q[4 + c] = (float)f4z[4 * (size_t)k + c];       // face k: planes k-2 .. k+1
             }
+            q[28] = q[29] = (float)idz;
+            q[30] = q[31] = (float)-idz;
         } else {
             if (k > 0) {
-                q[1] = (float)(dzk / (dz[k - 1] + dzk) * idz);
-                q[2] = (float)(dz[k - 1] / (dz[k - 1] + dzk) * idz);
+                zw[0] = dzk / (dz[k - 1] + dzk) * idz;
+                zw[1] = dz[k - 1] / (dz[k - 1] + dzk) * idz;
             }
             if (k < Nz - 1) {
-                q[3] = (float)(dz[k + 1] / (dzk + dz[k + 1]) * idz);
-                q[4] = (float)(dzk / (dzk + dz[k + 1]) * idz);
+                zw[2] = -(dz[k + 1] / (dzk + dz[k + 1]) * idz);
+                zw[3] = -(dzk / (dzk + dz[k + 1]) * idz);
             }
         }
-        q[5] = (float)cdn;
-        q[6] = (float)cup;
-        q[7] = (float)(2.0 * kx2 + 2.0 * ky2 + cdn + cup);
         double plate = 0.0;
         if (dirichlet && k == 0) plate += cdn * (double)kTBottom;
         if (dirichlet && k == Nz - 1) plate += cup * (double)kTTop;
-        q[8] = (float)plate;
-        q[9] = (float)(0.5 * idz);
-        if (!f4z) {
-            const float pv[8] = {q[1], q[2], -q[3], -q[4], q[5], q[6], -q[7], q[8]};
-            for (int c = 0; c < 8; ++c) q[12 + 2 * c] = q[13 + 2 * c] = pv[c];
-        }
+        q[0] = (float)idz;
+        q[1] = (float)(0.5 * idz);
+        const double pv[8] = {zw[0], zw[1], zw[2], zw[3], cdn, cup, -(2.0 * kx2 + 2.0 * ky2 + cdn + cup), plate};
+        for (int c = 0; c < 8; ++c) q[12 + 2 * c] = q[13 + 2 * c] = (float)pv[c];
     }
     return lc;
 }
