@@ -657,6 +657,120 @@ __global__ void k_xprep_vr(Grid<float> g, const float* __restrict__ V, const flo
     }
 }
 
+// All three intermediates of one coarse slab K (dense layers K M .. K M + M - 1)
+// and one coarse row J (dense rows J M .. J M + M - 1): one block, M = mx = my = mz.
+// Phase 1 forms UO and WY of the slab at the interior coarse columns in shared
+// memory, the 3 x 3 coarse U values of a column (R_z x R_y windows) loaded once
+// for the M layers, WY also on the next slab's first plane; phase 2 stores them
+// for every bundle column (periodic ghosts included) and runs the row balance
+// of VR from shared memory, so that UO and WY are not read back from HBM.  The
+// arithmetic is that of k_xprep_uowy and k_xprep_vr, operation for operation.
+template <int M>
+__global__ void __launch_bounds__(128) k_xprep_slab(Grid<float> g, const float* __restrict__ U,
+                                                     const float* __restrict__ V, const float* __restrict__ W,
+                                                     const float* __restrict__ scrW, float* __restrict__ UO,
+                                                     float* __restrict__ WY, float* __restrict__ VR, int nxg)
+{
+    extern __shared__ float s[];
+    const int nx = g.nx, J = blockIdx.x, K = blockIdx.y, k0 = K * M;
+    float* suo = s;                       // [M layers][M rows][nx]  U / (2 dx)
+    float* swy = s + M * M * nx;          // [M + 1 planes][M rows][nx]
+    int wz[3], wy[3];
+    float rz[M][3], ry[M][3];
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+        wz[q] = g.wz[3 * K + q];
+        wy[q] = g.wy[3 * J + q];
+#pragma unroll
+        for (int m = 0; m < M; ++m) {
+            rz[m][q] = g.Rz[3 * (k0 + m) + q];
+            ry[m][q] = g.Ry[3 * (J * M + m) + q];
+        }
+    }
+    const float hx = 0.5f * g.inv_dx;
+    const size_t cplane = (size_t)g.ny * nx;
+    for (int I = threadIdx.x; I < nx; I += blockDim.x) {
+        float u[3][3];
+#pragma unroll
+        for (int q = 0; q < 3; ++q)
+#pragma unroll
+            for (int p = 0; p < 3; ++p) u[q][p] = U[((size_t)wz[q] * g.ny + wy[p]) * nx + I];
+#pragma unroll
+        for (int m = 0; m < M; ++m) {
+            float a[3];
+#pragma unroll
+            for (int p = 0; p < 3; ++p) {
+                float t = 0.f;
+#pragma unroll
+                for (int q = 0; q < 3; ++q) t += rz[m][q] * u[q][p];
+                a[p] = t;
+            }
+#pragma unroll
+            for (int b = 0; b < M; ++b)
+                suo[(m * M + b) * nx + I] = (ry[b][0] * a[0] + ry[b][1] * a[1] + ry[b][2] * a[2]) * hx;
+        }
+#pragma unroll
+        for (int mp = 0; mp <= M; ++mp) {
+            // coarse W on the coarse planes, the slab-balanced scrW on the inner ones
+            const float* src = (mp == 0 || mp == M) ? W + (size_t)(K + mp / M) * cplane : scrW + (size_t)(k0 + mp) * cplane;
+            float c[3];
+#pragma unroll
+            for (int p = 0; p < 3; ++p) c[p] = src[(size_t)wy[p] * nx + I];
+#pragma unroll
+            for (int b = 0; b < M; ++b)
+                swy[(mp * M + b) * nx + I] = ry[b][0] * c[0] + ry[b][1] * c[1] + ry[b][2] * c[2];
+        }
+    }
+    __syncthreads();
+    const size_t vrow = (size_t)g.Ny + 1;
+    const float hiy = 0.5f * g.inv_dy, two_dx = 2.f * g.dx;
+    const bool last_row = (J == g.ny - 1), top = (K == g.nz - 1);
+    for (int gx = threadIdx.x; gx < nxg; gx += blockDim.x) {
+        const int I = wrapc(gx - 4, nx), Ie = wrapc(I + 1, nx);
+#pragma unroll
+        for (int m = 0; m < M; ++m)
+#pragma unroll
+            for (int b = 0; b < M; ++b) {
+                const size_t r = (size_t)(k0 + m) * g.Ny + J * M + b;
+                UO[r * nxg + gx] = suo[(m * M + b) * nx + I];
+                WY[r * nxg + gx] = swy[(m * M + b) * nx + I];
+            }
+        if (top)
+#pragma unroll
+            for (int b = 0; b < M; ++b)
+                WY[((size_t)g.Nz * g.Ny + J * M + b) * nxg + gx] = swy[(M * M + b) * nx + I];
+        float v[3], v0[3];
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+            v[q] = V[((size_t)wz[q] * g.ny + J) * nx + I];
+            v0[q] = last_row ? V[(size_t)wz[q] * g.ny * nx + I] : 0.f;   // row ny repeats row 0
+        }
+#pragma unroll
+        for (int m = 0; m < M; ++m) {
+            const int k = k0 + m;
+            float vz = 0.f;
+#pragma unroll
+            for (int q = 0; q < 3; ++q) vz += rz[m][q] * v[q];
+            VR[((size_t)k * vrow + (size_t)J * M) * nxg + gx] = vz * hiy;
+            if (last_row) {
+                float vz0 = 0.f;
+#pragma unroll
+                for (int q = 0; q < 3; ++q) vz0 += rz[m][q] * v0[q];
+                VR[((size_t)k * vrow + (size_t)g.Ny) * nxg + gx] = vz0 * hiy;
+            }
+            const float dzk = g.dz[k];
+            float G = vz * g.DX * dzk;
+#pragma unroll
+            for (int b = 0; b < M - 1; ++b) {
+                const float uw = suo[(m * M + b) * nx + I] * two_dx, ue = suo[(m * M + b) * nx + Ie] * two_dx;
+                const float wb = swy[(m * M + b) * nx + I], wt = swy[((m + 1) * M + b) * nx + I];
+                G = G - (ue - uw) * g.dy * dzk - (wt - wb) * g.DX * g.dy;
+                VR[((size_t)k * vrow + J * M + b + 1) * nxg + gx] = G / (g.DX * dzk) * hiy;
+            }
+        }
+    }
+}
+
 typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
@@ -838,6 +952,22 @@ cudaError_t launch_xfused_prep(const Grid<float>& g, const float* U, const float
 {
     cudaError_t e = launch_column_balance<float>(g, U, V, W, scrW, st);
     if (e != cudaSuccess) return e;
+    // one block per (coarse row, coarse slab) while the slab's UO and WY fit in
+    // shared memory; else the two per-layer kernels
+    const int M = g.mz;
+    const size_t smem = (size_t)(2 * M + 1) * M * g.nx * sizeof(float);
+    if (g.mx == M && g.my == M && smem <= 200 * 1024) {
+        static unsigned long long attr[2] = {0, 0};
+        const void* kern = M == 4 ? reinterpret_cast<const void*>(k_xprep_slab<4>)
+                                  : reinterpret_cast<const void*>(k_xprep_slab<2>);
+        e = smem_optin(kern, 200 * 1024, &attr[M == 4]);   // the cap, once per device
+        if (e != cudaSuccess) return e;
+        if (M == 4)
+            k_xprep_slab<4><<<dim3(g.ny, g.nz), 128, smem, st>>>(g, U, V, W, scrW, UO, WY, VR, nxg);
+        else
+            k_xprep_slab<2><<<dim3(g.ny, g.nz), 128, smem, st>>>(g, U, V, W, scrW, UO, WY, VR, nxg);
+        return cudaGetLastError();
+    }
     const unsigned row = (unsigned)((nxg * g.ny + 127) / 128), rowc = (unsigned)((nxg * (g.ny + 1) + 127) / 128);
     if (g.my == 4) k_xprep_uowy<4><<<dim3(row, g.Nz), 128, 0, st>>>(g, U, W, scrW, UO, WY, nxg);
     else k_xprep_uowy<2><<<dim3(row, g.Nz), 128, 0, st>>>(g, U, W, scrW, UO, WY, nxg);
