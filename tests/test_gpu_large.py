@@ -113,3 +113,42 @@ def test_large_grid_sampled_parity(mr, face_order):
         _, ref = O.run(cfg, vel, T0b, 3)
         err = np.abs(got[:, lo:hi, lo:hi] - ref[:, lo:hi, lo:hi]).max()
         assert err <= 1e-5, (J0, I0, err)
+
+
+def test_large_grid_nu_drift_vs_fp64_gpu(mr, capsys):
+    """The large precision form's Nusselt check: the FP32 split-x run against
+    the FP64 GPU path (stored dense velocity) on the same seed, the same time
+    step (CFL 0.3 on the refined FP64 velocity) and the same 200 steps (the
+    shorter FP64 reference the configuration names cannot be shorter than a
+    200-step run; it is read as a same-length run).  The plate Nusselt numbers,
+    reduced in FP64 on both paths, agree to 1e-4 relative."""
+    from paper_1805_03426_gb300 import synth
+    if torch.cuda.get_device_properties(0).total_memory < 200e9:
+        pytest.skip("needs ~140 GB of device memory")
+    steps = 200
+    h64 = mr.mr_create(_cfg(mr, precision=mr.MR_F64, velocity_mode=mr.MR_VEL_STORED, np_average=50))
+    (Nx, Ny, Nz), zf = mr.mr_grid(h64)
+    U, V, W = synth.coarse_velocity(1805, np.arange(385) / 384, np.arange(385) / 384, zf[::4], rms=0.1)
+    dU, dV, dW = (torch.from_numpy(a).cuda() for a in (U, V, W))
+    mr.mr_refine_velocity(h64, dU, dV, dW)
+    dt = mr.mr_cfl_dt(h64, 0.3)
+    mr.mr_set_dt(h64, dt)
+    zc = 0.5 * (zf[1:] + zf[:-1])
+    T0 = synth.initial_scalar_device(1805, zc, Ny, Nx)
+    mr.mr_set_scalar(h64, T0)
+    mr.mr_scalar_step(h64, steps)
+    nu64 = mr.mr_plate_nu(h64)
+    h64.close()
+    torch.cuda.empty_cache()
+
+    h32 = mr.mr_create(_cfg(mr, dt=dt, np_average=50))
+    mr.mr_refine_velocity(h32, dU, dV, dW)
+    mr.mr_set_scalar(h32, T0)
+    mr.mr_scalar_step(h32, steps)
+    nu32 = mr.mr_plate_nu(h32)
+    h32.close()
+    drift = [abs(a - b) / abs(b) for a, b in zip(nu32, nu64)]
+    with capsys.disabled():
+        print(f"\n1536x1536x1024, {steps} steps, dt {dt:.4e}: Nu FP32 {nu32}, FP64 {nu64}, relative drift {drift}")
+    assert all(np.isfinite(nu32)) and all(np.isfinite(nu64))
+    assert max(drift) <= 1e-4
