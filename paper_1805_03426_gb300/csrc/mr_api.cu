@@ -446,7 +446,8 @@ int mr_create(const mr_config* cfg, mr_handle* out)
     alloc(&b.metric, mb64 + mb32 + nwin * sizeof(int));
     h->red_blocks = 152 * 8;
     alloc((void**)&b.red, (size_t)h->red_blocks * 2 * sizeof(double));
-    alloc((void**)&b.nu2, (2 + 2 * kPlateBlocks) * sizeof(double));
+    alloc((void**)&b.nu2, (3 + 2 * kPlateBlocks) * sizeof(double));
+    if (e == cudaSuccess) e = cudaMemset(b.nu2, 0, (3 + 2 * kPlateBlocks) * sizeof(double));   // the block count
     h->stage_bytes = std::min<size_t>((size_t)64 << 20, std::max<size_t>(h->ncell * 8, 1 << 16));
     alloc(&b.stage, h->stage_bytes);
     if (c.diffz_implicit) alloc(&b.tri, h->ncell * h->elt);

@@ -12,7 +12,7 @@
 
 namespace mr {
 
-constexpr int kPlateBlocks = 64;   // blocks of the plate Nusselt reduction
+constexpr int kPlateBlocks = 304;  // blocks of the plate Nusselt reduction
 
 // Device view of the grid and of the per-layer coefficients, in precision P.
 // Built once per handle from the FP64 host grid (Sections 3.1, 3.2).

@@ -100,31 +100,41 @@ __global__ void __launch_bounds__(kRedThreads) k_moments(Grid<P> g, const P* __r
     block_reduce_store<2, false>(v, partials + 2 * blockIdx.x);
 }
 
-// Plate Nusselt numbers, stage 1: every block sums a fixed slice of both
-// plates into two FP64 partials (deterministic order).
+// Plate Nusselt numbers: every block sums a fixed slice of both plates,
+// sum (T_bottom - T) and sum (T - T_top), into two FP64 partials; the block
+// that finishes last (an atomic count, nothing waits) adds the partials in
+// block order -- deterministic -- divides by the centre distance and the cell
+// count, and resets the count for the next launch.
 template <typename P>
-__global__ void __launch_bounds__(256) k_plate_partials(Grid<P> g, const P* __restrict__ T, double zb, double zt,
-                                                        double* __restrict__ partials)
+__global__ void __launch_bounds__(256) k_plate_nu(Grid<P> g, const P* __restrict__ T, double zb, double zt,
+                                                  double inv_plane, double* __restrict__ partials,
+                                                  unsigned* __restrict__ count, double* __restrict__ out2)
 {
     const size_t plane = (size_t)g.Nx * g.Ny;
     const P* top = T + (size_t)(g.Nz - 1) * plane;
     double v[2] = {0.0, 0.0};
     for (size_t m = (size_t)blockIdx.x * blockDim.x + threadIdx.x; m < plane; m += (size_t)gridDim.x * blockDim.x) {
-        v[0] += (0.5 - (double)T[m]) / zb;
-        v[1] += ((double)top[m] + 0.5) / zt;
+        v[0] += 0.5 - (double)T[m];
+        v[1] += (double)top[m] + 0.5;
     }
     block_reduce_store<2, false>(v, partials + 2 * blockIdx.x);
-}
-
-// Stage 2: one block adds the partials in block order and writes the means.
-__global__ void __launch_bounds__(32) k_plate_final(const double* __restrict__ partials, int blocks, double inv_plane,
-                                                    double* __restrict__ out2)
-{
-    if (threadIdx.x != 0) return;
-    double b = 0.0, t = 0.0;
-    for (int q = 0; q < blocks; ++q) { b += partials[2 * q]; t += partials[2 * q + 1]; }
-    out2[0] = b * inv_plane;
-    out2[1] = t * inv_plane;
+    __shared__ bool last;
+    if (threadIdx.x == 0) {
+        __threadfence();                     // this block's partials before its count
+        last = atomicAdd(count, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (last && threadIdx.x == 0) {
+        __threadfence();
+        double b = 0.0, t = 0.0;
+        for (unsigned q = 0; q < gridDim.x; ++q) {
+            b += __ldcg(partials + 2 * q);
+            t += __ldcg(partials + 2 * q + 1);
+        }
+        out2[0] = b / zb * inv_plane;
+        out2[1] = t / zt * inv_plane;
+        *count = 0u;
+    }
 }
 
 // Max |divergence| of the dense refined faces (outward flux sum / volume).
@@ -292,9 +302,10 @@ cudaError_t launch_moments(const Grid<P>& g, const P* T, double mean, int pass, 
 template <typename P>
 cudaError_t launch_plate_nu(const Grid<P>& g, const P* T, const double* zb_zt, double* out2, cudaStream_t st)
 {
-    // the partials live in out2[2..]: the caller's buffer holds 2 + 2 * kPlateBlocks doubles
-    k_plate_partials<P><<<kPlateBlocks, 256, 0, st>>>(g, T, zb_zt[0], zb_zt[1], out2 + 2);
-    k_plate_final<<<1, 32, 0, st>>>(out2 + 2, kPlateBlocks, 1.0 / ((double)g.Nx * g.Ny), out2);
+    // out2 holds 3 + 2 * kPlateBlocks doubles: the two means, the block count
+    // (zero between launches) and the partials
+    k_plate_nu<P><<<kPlateBlocks, 256, 0, st>>>(g, T, zb_zt[0], zb_zt[1], 1.0 / ((double)g.Nx * g.Ny), out2 + 3,
+                                                reinterpret_cast<unsigned*>(out2 + 2), out2);
     return cudaGetLastError();
 }
 
