@@ -60,11 +60,12 @@ NCU_TRAFFIC = {
 }
 
 
-# Floating-point operations of one stored-velocity step per cell in the
-# interior (an FMA counts two): per x or y face 3 for the advective flux and 2
-# for the diffusive difference (20), per z face 5 and 3 (16), and 15 to
-# assemble C, D and the Euler-leapfrog update.
-FP64_FLOPS_PER_CELL = 51
+# Floating-point operations of one periodic stored-velocity leapfrog step per
+# cell (an FMA counts two), as the folded kernel forms it: x and y advective
+# flux differences 5 each, the z one 9 (weights carrying 1/dz), diffusion 12
+# (opposite neighbours summed, diagonal and plate terms per layer), 4 to
+# scale and add the advective parts, 3 for the update.
+FP64_FLOPS_PER_CELL = 38
 FP64_NOMINAL_TFLOPS = 1.25   # GB300 FP64 (non-tensor), nominal
 
 

@@ -206,7 +206,7 @@ template <typename P>
 static size_t metric_bytes(const mr_handle_s* h)
 {
     const size_t nP = (size_t)h->Nz * 4 + 2 * ((size_t)h->Nz + 1) + 3 * ((size_t)h->Nx + h->Ny + h->Nz) +
-                      4 * ((size_t)h->Nx + h->Ny + h->Nz + 3);
+                      4 * ((size_t)h->Nx + h->Ny + h->Nz + 3) + 8 * (size_t)h->Nz;
     return ((nP * sizeof(P) + 255) / 256) * 256;
 }
 
@@ -236,9 +236,25 @@ static int upload_metric(mr_handle_s* h, char* dst, const int* dwin, Grid<P>& g)
         cdn[k] = (k > 0 || dir) ? h->kappa / (h->dz[k] * below) : 0.0;
         cup[k] = (k < Nz - 1 || dir) ? h->kappa / (h->dz[k] * above) : 0.0;
     }
+    const double dx = c.lx / h->Nx, dy = c.ly / h->Ny;
+    const double kx2 = h->kappa / (dx * dx), ky2 = h->kappa / (dy * dy);
+    std::vector<double> lz(8 * (size_t)Nz);
+    for (int k = 0; k < Nz; ++k) {
+        double* q = &lz[8 * (size_t)k];
+        q[0] = wlo[k] * inv_dz[k];
+        q[1] = whi[k] * inv_dz[k];
+        q[2] = -(wlo[k + 1] * inv_dz[k]);
+        q[3] = -(whi[k + 1] * inv_dz[k]);
+        q[4] = cdn[k];
+        q[5] = cup[k];
+        q[6] = -(2.0 * kx2 + 2.0 * ky2 + cdn[k] + cup[k]);
+        // plates at T = +0.5 (bottom) and -0.5 (top); cdn[0] = cup[Nz-1] = 0 when adiabatic
+        q[7] = (k == 0 ? cdn[0] * 0.5 : 0.0) + (k == Nz - 1 ? cup[Nz - 1] * -0.5 : 0.0);
+    }
     push(h->dz); push(inv_dz); push(wlo); push(whi); push(cdn); push(cup);
     push(h->Rx); push(h->Ry); push(h->Rz);
     push(h->f4x); push(h->f4y); push(h->f4z);
+    push(lz);
     cudaError_t e = cudaMemcpy(dst, host.data(), host.size() * sizeof(P), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) return cuda_check(e, "upload metric");
     const P* base = (const P*)dst;
@@ -246,13 +262,14 @@ static int upload_metric(mr_handle_s* h, char* dst, const int* dwin, Grid<P>& g)
     g.Nx = h->Nx; g.Ny = h->Ny; g.Nz = h->Nz; g.walls = h->w;
     g.ufx = h->Nx + h->w; g.vfy = h->Ny + h->w; g.cux = c.nx + h->w; g.cvy = c.ny + h->w;
     g.dirichlet = dir ? 1 : 0;
-    const double dx = c.lx / h->Nx, dy = c.ly / h->Ny;
     g.dx = (P)dx; g.dy = (P)dy; g.DX = (P)(c.lx / c.nx); g.DY = (P)(c.ly / c.ny);
     g.inv_dx = (P)(1.0 / dx); g.inv_dy = (P)(1.0 / dy);
-    g.kx2 = (P)(h->kappa / (dx * dx)); g.ky2 = (P)(h->kappa / (dy * dy));
+    g.kx2 = (P)kx2; g.ky2 = (P)ky2;
+    g.hx = (P)(0.5 / dx); g.hy = (P)(0.5 / dy);
     g.dz = base + off[0]; g.inv_dz = base + off[1]; g.wlo = base + off[2]; g.whi = base + off[3];
     g.cdn = base + off[4]; g.cup = base + off[5]; g.Rx = base + off[6]; g.Ry = base + off[7]; g.Rz = base + off[8];
     g.f4x = base + off[9]; g.f4y = base + off[10]; g.f4z = base + off[11];
+    g.lz = base + off[12];
     g.order4 = c.face_order == 4 ? 1 : 0;
     g.wx = dwin; g.wy = dwin + 3 * c.nx; g.wz = dwin + 3 * (c.nx + c.ny);
     return MR_OK;

@@ -43,6 +43,13 @@ struct Grid {
     const P* f4y;                // [Ny+1][4]
     const P* f4z;                // [Nz+1][4]
     int order4;                  // 1: fourth-order face values of the advected scalar
+    P hx, hy;                    // 1 / (2 dx), 1 / (2 dy)
+    // [Nz][8] per-layer constants of the periodic second-order step: the
+    // weights of T_{k-1}, T_k at z-face k times 1/dz_k, the negated weights of
+    // T_k, T_{k+1} at z-face k+1 times 1/dz_k, cdn, cup, the negated diagonal
+    // 2 kx2 + 2 ky2 + cdn + cup, and the plate term (cdn T_bottom on the first
+    // layer, cup T_top on the last, Dirichlet plates)
+    const P* lz;
 };
 
 // Coefficients of one step: T^{s+1} = a T^{s-1} + b T^s + gdt [C(T^s) + D(T^{s-1})].

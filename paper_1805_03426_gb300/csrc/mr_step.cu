@@ -125,6 +125,44 @@ __global__ void __launch_bounds__(256) k_step_stored(Grid<P> g, const FaceVel<P,
     Tp1[m] = a * Dc + b * Tc + gdt * (C + D);
 }
 
+// The same step (Eq. 5) for the common case -- periodic x and y, explicit
+// diffusion, second-order faces, one velocity level -- with the arithmetic
+// folded for the FP64 pipe (25 FP operations per cell instead of 39):
+// 1/(2 dx), 1/(2 dy) scale the summed x and y flux differences, the z-face
+// weights carry 1/dz_k (the top face's negated), the opposite diffusion
+// neighbours are summed before kx2, ky2, and the diagonal and the plate
+// terms come from the per-layer table g.lz.  LF: a plain leapfrog step.
+template <typename P, bool LF>
+__global__ void __launch_bounds__(256) k_step_periodic(Grid<P> g, const P* __restrict__ Us,
+                                                       const P* __restrict__ Vs, const P* __restrict__ Ws,
+                                                       const P* __restrict__ Tm1, const P* __restrict__ T,
+                                                       P* __restrict__ Tp1, P a, P b, P gdt)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y * blockDim.y + threadIdx.y;
+    const int k = blockIdx.z;
+    if (i >= g.Nx || j >= g.Ny) return;
+    const size_t plane = (size_t)g.Nx * g.Ny;
+    const size_t row = (size_t)j * g.Nx, m = (size_t)k * plane + row + i;
+    const P* L = g.lz + 8 * k;
+    const int iw = i == 0 ? g.Nx - 1 : i - 1, ie = i == g.Nx - 1 ? 0 : i + 1;
+    const int js = j == 0 ? g.Ny - 1 : j - 1, jn = j == g.Ny - 1 ? 0 : j + 1;
+    const size_t mw = m - i + iw, me = m - i + ie;
+    const size_t ms = m - row + (size_t)js * g.Nx, mn = m - row + (size_t)jn * g.Nx;
+    const P Tc = T[m], Dc = Tm1[m];
+    // beyond the plates: zero (W is zero there; the plate values enter through L[7])
+    const bool lo = k > 0, hi = k < g.Nz - 1;
+    const P Tb = lo ? T[m - plane] : P(0), Db = lo ? Tm1[m - plane] : P(0);
+    const P Tt = hi ? T[m + plane] : P(0), Dt = hi ? Tm1[m + plane] : P(0);
+    const size_t urow = ((size_t)k * g.Ny + j) * g.Nx, vrow = (size_t)k * g.Ny * g.Nx;
+    const P ax = Us[urow + i] * (T[mw] + Tc) - Us[urow + ie] * (Tc + T[me]);
+    const P ay = Vs[vrow + row + i] * (T[ms] + Tc) - Vs[vrow + (size_t)jn * g.Nx + i] * (Tc + T[mn]);
+    const P az = Ws[m] * (L[0] * Tb + L[1] * Tc) + Ws[m + plane] * (L[2] * Tc + L[3] * Tt);
+    const P D = L[7] + g.kx2 * (Tm1[mw] + Tm1[me]) + g.ky2 * (Tm1[ms] + Tm1[mn]) + L[4] * Db + L[5] * Dt + L[6] * Dc;
+    const P C = g.hx * ax + g.hy * ay + az;
+    Tp1[m] = LF ? Dc + gdt * (C + D) : a * Dc + b * Tc + gdt * (C + D);
+}
+
 // Opt-in implicit vertical diffusion: per (x, y) column solve
 //   (1 + h (cup + cdn)) x_k - h cdn_k x_{k-1} - h cup_k x_{k+1} = r_k,
 // h = gdt / 2, by the Thomas algorithm; work holds the eliminated
@@ -165,6 +203,13 @@ cudaError_t step_stored(const Grid<P>& g, const FaceVel<P, LERP>& u, const FaceV
     dim3 blk(64, 4);
     dim3 grd((g.Nx + blk.x - 1) / blk.x, (g.Ny + blk.y - 1) / blk.y, g.Nz);
     const P a = (P)c.a, b = (P)c.b, gdt = (P)c.gdt;
+    if (!LERP && !implz && !g.order4 && !g.walls) {
+        if (c.a == 1.0 && c.b == 0.0)
+            k_step_periodic<P, true><<<grd, blk, 0, st>>>(g, u.A, v.A, w.A, Tm1, T, Tp1, a, b, gdt);
+        else
+            k_step_periodic<P, false><<<grd, blk, 0, st>>>(g, u.A, v.A, w.A, Tm1, T, Tp1, a, b, gdt);
+        return cudaGetLastError();
+    }
     if (g.order4) {
         if (implz) k_step_stored<P, true, LERP, true><<<grd, blk, 0, st>>>(g, u, v, w, Tm1, T, Tp1, a, b, gdt);
         else k_step_stored<P, false, LERP, true><<<grd, blk, 0, st>>>(g, u, v, w, Tm1, T, Tp1, a, b, gdt);
