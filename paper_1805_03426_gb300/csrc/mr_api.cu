@@ -35,6 +35,18 @@ int cuda_check(cudaError_t e, const char* what)
     return set_error(MR_ERR_CUDA, m);
 }
 
+// The device address of mapped pinned host memory (page-locked by the CUDA
+// runtime, so addressable from kernels), else NULL.
+static const double* host_mapped(const double* p)
+{
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return a.type == cudaMemoryTypeHost ? (const double*)a.devicePointer : nullptr;
+}
+
 bool is_device_pointer(const void* p)
 {
     cudaPointerAttributes a;
@@ -606,10 +618,25 @@ static int load_velocity(mr_handle h, const double* U, const double* V, const do
 {
     DeviceBuffers& b = h->buf;
     int rc;
-    if ((rc = copy_in(h, U, MR_F64, b.U64, MR_F64, h->ncU, st))) return rc;
-    if ((rc = copy_in(h, V, MR_F64, b.V64, MR_F64, h->ncV, st))) return rc;
-    if ((rc = copy_in(h, W, MR_F64, b.W64, MR_F64, h->ncW, st))) return rc;
-    if (h->cfg.precision == MR_F32) {
+    const bool f32 = h->cfg.precision == MR_F32;
+    bool fetched = false;
+    const double *mU = host_mapped(U), *mV = host_mapped(V), *mW = host_mapped(W);
+    if (mU && mV && mW) {
+        // pinned host faces: the SMs read them over the host link, writing the
+        // FP64 copy and the FP32 faces in the same pass
+        cudaError_t e = launch_fetch_f64(mU, b.U64, f32 ? (float*)b.Uc : nullptr, h->ncU, st);
+        if (e == cudaSuccess) e = launch_fetch_f64(mV, b.V64, f32 ? (float*)b.Vc : nullptr, h->ncV, st);
+        if (e == cudaSuccess) e = launch_fetch_f64(mW, b.W64, f32 ? (float*)b.Wc : nullptr, h->ncW, st);
+        if (e == cudaErrorInvalidValue) cudaGetLastError();   // unaligned: the copy path below
+        else if (e != cudaSuccess) return cuda_check(e, "fetch coarse faces");
+        else fetched = true;
+    }
+    if (!fetched) {
+        if ((rc = copy_in(h, U, MR_F64, b.U64, MR_F64, h->ncU, st))) return rc;
+        if ((rc = copy_in(h, V, MR_F64, b.V64, MR_F64, h->ncV, st))) return rc;
+        if ((rc = copy_in(h, W, MR_F64, b.W64, MR_F64, h->ncW, st))) return rc;
+    }
+    if (f32 && !fetched) {
         if ((rc = copy_in(h, b.U64, MR_F64, b.Uc, MR_F32, h->ncU, st))) return rc;
         if ((rc = copy_in(h, b.V64, MR_F64, b.Vc, MR_F32, h->ncV, st))) return rc;
         if ((rc = copy_in(h, b.W64, MR_F64, b.Wc, MR_F32, h->ncW, st))) return rc;

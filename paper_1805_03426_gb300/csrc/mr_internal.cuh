@@ -179,6 +179,9 @@ template <typename P>
 cudaError_t launch_cfl(const Grid<P>& g, const P* Us, const P* Vs, const P* Ws, double* partials,
                        int blocks, cudaStream_t st);
 bool fused_supported(const mr_config& cfg, std::string* why);
+// FP64 values from mapped pinned host memory into an FP64 device array and,
+// where d32 is given, an FP32 one (16-byte aligned src and d64, 8-byte d32).
+cudaError_t launch_fetch_f64(const double* src, double* d64, float* d32, size_t n, cudaStream_t st);
 // MR_VEL_FUSED: every refinement stage in the step kernel (lc: the layer
 // constants of xfused_layer_constants, rx12: the uniform R_x rows)
 cudaError_t launch_step_fused_f32(const Grid<float>& g, const float* U, const float* V, const float* W,

@@ -102,9 +102,10 @@ __global__ void __launch_bounds__(kRedThreads) k_moments(Grid<P> g, const P* __r
 
 // Plate Nusselt numbers: every block sums a fixed slice of both plates,
 // sum (T_bottom - T) and sum (T - T_top), into two FP64 partials; the block
-// that finishes last (an atomic count, nothing waits) adds the partials in
-// block order -- deterministic -- divides by the centre distance and the cell
-// count, and resets the count for the next launch.
+// that finishes last (an atomic count, nothing waits) adds the partials --
+// thread t the partials t, t + 256, ..., then the block's fixed reduction tree,
+// so the order of the additions never changes -- divides by the centre
+// distance and the cell count, and resets the count for the next launch.
 template <typename P>
 __global__ void __launch_bounds__(256) k_plate_nu(Grid<P> g, const P* __restrict__ T, double zb, double zt,
                                                   double inv_plane, double* __restrict__ partials,
@@ -124,16 +125,39 @@ __global__ void __launch_bounds__(256) k_plate_nu(Grid<P> g, const P* __restrict
         last = atomicAdd(count, 1u) == gridDim.x - 1;
     }
     __syncthreads();
-    if (last && threadIdx.x == 0) {
-        __threadfence();
-        double b = 0.0, t = 0.0;
-        for (unsigned q = 0; q < gridDim.x; ++q) {
-            b += __ldcg(partials + 2 * q);
-            t += __ldcg(partials + 2 * q + 1);
-        }
-        out2[0] = b / zb * inv_plane;
-        out2[1] = t / zt * inv_plane;
+    if (!last) return;
+    __threadfence();
+    double s2[2] = {0.0, 0.0};
+    for (unsigned q = threadIdx.x; q < gridDim.x; q += blockDim.x) {
+        s2[0] += __ldcg(partials + 2 * q);
+        s2[1] += __ldcg(partials + 2 * q + 1);
+    }
+    __shared__ double tot[2];
+    block_reduce_store<2, false>(s2, tot);
+    if (threadIdx.x == 0) {                  // the thread that wrote tot
+        out2[0] = tot[0] / zb * inv_plane;
+        out2[1] = tot[1] / zt * inv_plane;
         *count = 0u;
+    }
+}
+
+// FP64 values from mapped pinned host memory (read by the SMs over the host
+// link) into the FP64 device copy and, where d32 is given, its FP32 rounding.
+__global__ void k_fetch_f64(const double* __restrict__ src, double* __restrict__ d64, float* __restrict__ d32,
+                            size_t n)
+{
+    const size_t stride = (size_t)gridDim.x * blockDim.x;
+    const size_t n2 = n / 2;
+    const double2* s2 = reinterpret_cast<const double2*>(src);
+    double2* o2 = reinterpret_cast<double2*>(d64);
+    for (size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x; t < n2; t += stride) {
+        const double2 v = s2[t];
+        o2[t] = v;
+        if (d32) reinterpret_cast<float2*>(d32)[t] = make_float2((float)v.x, (float)v.y);
+    }
+    if ((n & 1) && blockIdx.x == 0 && threadIdx.x == 0) {
+        d64[n - 1] = src[n - 1];
+        if (d32) d32[n - 1] = (float)src[n - 1];
     }
 }
 
@@ -373,5 +397,16 @@ MR_INST(double)
 MR_INST(float)
 #undef MR_INST
 template cudaError_t launch_convert<double>(const void*, int, void*, int, size_t, cudaStream_t);
+
+cudaError_t launch_fetch_f64(const double* src, double* d64, float* d32, size_t n, cudaStream_t st)
+{
+    if (n == 0) return cudaSuccess;
+    // 16-byte alignment for the pair loads and stores
+    if ((reinterpret_cast<uintptr_t>(src) | reinterpret_cast<uintptr_t>(d64)) & 15 ||
+        reinterpret_cast<uintptr_t>(d32) & 7)
+        return cudaErrorInvalidValue;
+    k_fetch_f64<<<152 * 8, 256, 0, st>>>(src, d64, d32, n);
+    return cudaGetLastError();
+}
 
 }  // namespace mr

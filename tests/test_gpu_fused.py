@@ -124,3 +124,26 @@ def test_fused_diagnostics_fp32(mr, prob, mode):
     nz_ref, nT_ref = O.nusselt_profile(prob.cfg, T_ref, vel[2])
     assert np.abs(nu_z - nz_ref).max() <= F32_NU_TOL * np.abs(nz_ref).max() * 10
     assert abs(nu_T - nT_ref) <= F32_NU_TOL * abs(nT_ref)
+
+
+@pytest.mark.parametrize("kind", ["f32_xfused", "f32_fused", "f64_stored"])
+def test_refine_from_pinned_host_faces(mr, prob, kind):
+    """Coarse faces in pinned host memory are read by the kernels over the host
+    link (with the FP32 rounding in the same pass); the run is bit-identical to
+    one from device copies of the same faces."""
+    prec, mode = {"f32_xfused": (mr.MR_F32, mr.MR_VEL_XFUSED), "f32_fused": (mr.MR_F32, mr.MR_VEL_FUSED),
+                  "f64_stored": (mr.MR_F64, mr.MR_VEL_STORED)}[kind]
+    out = []
+    for pinned in (False, True):
+        faces = [torch.from_numpy(np.ascontiguousarray(a)) for a in (prob.U, prob.V, prob.W)]
+        faces = [f.pin_memory() for f in faces] if pinned else [f.cuda() for f in faces]
+        h = mr.mr_create(prob.mr_config(mr, prec, mode))
+        mr.mr_refine_velocity(h, *faces)
+        mr.mr_set_scalar(h, dev(prob.T0))
+        mr.mr_scalar_step(h, 5)
+        T = torch.empty(prob.T0.shape, dtype=torch.float64, device="cuda")
+        mr.mr_get_scalar(h, T)
+        torch.cuda.synchronize()
+        out.append(T.cpu().numpy())
+        h.close()
+    assert np.array_equal(out[0], out[1])
