@@ -141,6 +141,23 @@ int mr_grid(mr_handle h, int32_t* dims3, double* zf_host);
 int mr_refine_velocity(mr_handle h, const double* U, const double* V, const double* W,
                        void* Us, void* Vs, void* Ws, mr_stream stream);
 
+/* The refinement of mr_refine_velocity split in two, so that the hand-over of
+ * the next coarse velocity overlaps the current steps (the paper has no such
+ * call: it is the pipelining of the host-to-device copy).
+ * mr_stage_velocity copies U, V, W (FP64, host or device, the layout of
+ * mr_refine_velocity) into one of two device slots owned by the handle, on
+ * copy_stream, and returns at once; the caller must not change U, V, W until
+ * copy_stream has passed the copy (pinned host memory keeps it asynchronous).
+ * A second call before a refinement replaces the staged faces.
+ * mr_refine_velocity_staged refines the last staged faces on stream (which
+ * waits for their copy): the same result as mr_refine_velocity with them.
+ * A slot is reused only after the work queued on the refining stream before
+ * its release has run.  Errors: MR_ERR_ARG (NULL), MR_ERR_STATE (nothing
+ * staged), MR_ERR_CUDA, MR_ERR_OOM (slots are allocated at the first call). */
+int mr_stage_velocity(mr_handle h, const double* U, const double* V, const double* W,
+                      mr_stream copy_stream);
+int mr_refine_velocity_staged(mr_handle h, mr_stream stream);
+
 /* Copy the scalar in (dtype MR_F64 or MR_F32, host or device) and restart the
  * time integration: the next step is the forward-Euler start. */
 int mr_set_scalar(mr_handle h, const void* T0, int32_t dtype, mr_stream stream);

@@ -386,6 +386,13 @@ void mr_destroy(mr_handle h)
     void* xptrs[] = {b.xwy, b.xuo, b.xvr, b.xlc, b.diag};
     for (void* p : xptrs)
         if (p) cudaFree(p);
+    for (int q = 0; q < 2; ++q) {
+        void* sptrs[] = {b.sU[q], b.sV[q], b.sW[q]};
+        for (void* p : sptrs)
+            if (p) cudaFree(p);
+        if (b.stg_copied[q]) cudaEventDestroy(b.stg_copied[q]);
+        if (b.stg_free[q]) cudaEventDestroy(b.stg_free[q]);
+    }
     void* aptrs[] = {h->adj.cp, h->adj.seg, h->adj.mu, h->adj.face, h->adj.scr, h->adj.out};
     for (void* p : aptrs)
         if (p) cudaFree(p);
@@ -614,6 +621,8 @@ static int refine_into(mr_handle h, void* dUs, void* dVs, void* dWs, cudaStream_
 // Load a coarse velocity into the handle's current level: FP64 copy, the
 // precision-P coarse faces, and what the velocity mode steps from (dense faces
 // for MR_VEL_STORED, the split-x intermediates for MR_VEL_XFUSED).
+static int derive_velocity(mr_handle h, bool convert, cudaStream_t st);
+
 static int load_velocity(mr_handle h, const double* U, const double* V, const double* W, cudaStream_t st)
 {
     DeviceBuffers& b = h->buf;
@@ -636,7 +645,16 @@ static int load_velocity(mr_handle h, const double* U, const double* V, const do
         if ((rc = copy_in(h, V, MR_F64, b.V64, MR_F64, h->ncV, st))) return rc;
         if ((rc = copy_in(h, W, MR_F64, b.W64, MR_F64, h->ncW, st))) return rc;
     }
-    if (f32 && !fetched) {
+    return derive_velocity(h, !fetched, st);
+}
+
+// What the velocity mode steps from, given the FP64 coarse faces in U64/V64/W64
+// (and, unless convert, their FP32 rounding already in Uc/Vc/Wc).
+static int derive_velocity(mr_handle h, bool convert, cudaStream_t st)
+{
+    DeviceBuffers& b = h->buf;
+    int rc;
+    if (h->cfg.precision == MR_F32 && convert) {
         if ((rc = copy_in(h, b.U64, MR_F64, b.Uc, MR_F32, h->ncU, st))) return rc;
         if ((rc = copy_in(h, b.V64, MR_F64, b.Vc, MR_F32, h->ncV, st))) return rc;
         if ((rc = copy_in(h, b.W64, MR_F64, b.Wc, MR_F32, h->ncW, st))) return rc;
@@ -790,6 +808,64 @@ int mr_refine_velocity(mr_handle h, const double* U, const double* V, const doub
     if ((rc = copy_out(h, b.Us, P, Us, P, h->nU, st))) return rc;
     if ((rc = copy_out(h, b.Vs, P, Vs, P, h->nV, st))) return rc;
     return copy_out(h, b.Ws, P, Ws, P, h->nW, st);
+}
+
+int mr_stage_velocity(mr_handle h, const double* U, const double* V, const double* W, mr_stream copy_stream)
+{
+    if (!h || !U || !V || !W) return set_error(MR_ERR_ARG, "mr_stage_velocity: NULL argument");
+    DeviceBuffers& b = h->buf;
+    cudaStream_t cs = (cudaStream_t)copy_stream;
+    cudaError_t e = cudaSuccess;
+    if (!b.sU[0]) {
+        for (int q = 0; q < 2 && e == cudaSuccess; ++q) {
+            e = cudaMalloc((void**)&b.sU[q], h->ncU * 8);
+            if (e == cudaSuccess) e = cudaMalloc((void**)&b.sV[q], h->ncV * 8);
+            if (e == cudaSuccess) e = cudaMalloc((void**)&b.sW[q], h->ncW * 8);
+            if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b.stg_copied[q], cudaEventDisableTiming);
+            if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b.stg_free[q], cudaEventDisableTiming);
+        }
+        if (e != cudaSuccess) return cuda_check(e, "mr_stage_velocity: staging slots");
+    }
+    const int q = b.stg_next;
+    // the slot's memory may still be read by work queued before the refinement
+    // that released it (a wait on a never-recorded event passes at once)
+    e = cudaStreamWaitEvent(cs, b.stg_free[q], 0);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(b.sU[q], U, h->ncU * 8, cudaMemcpyDefault, cs);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(b.sV[q], V, h->ncV * 8, cudaMemcpyDefault, cs);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(b.sW[q], W, h->ncW * 8, cudaMemcpyDefault, cs);
+    if (e == cudaSuccess) e = cudaEventRecord(b.stg_copied[q], cs);
+    if (e != cudaSuccess) return cuda_check(e, "mr_stage_velocity: copy");
+    b.stg_ready = q;
+    b.stg_next = q ^ 1;
+    return MR_OK;
+}
+
+int mr_refine_velocity_staged(mr_handle h, mr_stream stream)
+{
+    if (!h) return set_error(MR_ERR_ARG, "mr_refine_velocity_staged: NULL argument");
+    DeviceBuffers& b = h->buf;
+    if (b.stg_ready < 0) return set_error(MR_ERR_STATE, "mr_refine_velocity_staged: call mr_stage_velocity first");
+    cudaStream_t st = (cudaStream_t)stream;
+    const int q = b.stg_ready;
+    cudaError_t e = cudaStreamWaitEvent(st, b.stg_copied[q], 0);
+    if (e != cudaSuccess) return cuda_check(e, "mr_refine_velocity_staged: wait");
+    // the staged slot becomes the handle's FP64 faces; the old faces' memory
+    // becomes the slot, free once the work queued so far has run
+    std::swap(b.U64, b.sU[q]);
+    std::swap(b.V64, b.sV[q]);
+    std::swap(b.W64, b.sW[q]);
+    if (h->elt == 8) {
+        b.Uc = b.U64;
+        b.Vc = b.V64;
+        b.Wc = b.W64;
+    }
+    b.stg_ready = -1;
+    int rc = derive_velocity(h, true, st);
+    e = cudaEventRecord(b.stg_free[q], st);
+    if (rc) return rc;
+    if (e != cudaSuccess) return cuda_check(e, "mr_refine_velocity_staged: record");
+    h->have_velocity = true;
+    return MR_OK;
 }
 
 int mr_scalar_coarse_step(mr_handle h, const double* U, const double* V, const double* W, int32_t mt,

@@ -96,6 +96,13 @@ struct DeviceBuffers {
         float *xwy = nullptr, *xuo = nullptr, *xvr = nullptr;
     } next;
     float* lerpc = nullptr;                    // MR_VEL_FUSED: interpolated coarse faces (U, V, W)
+    // staged coarse faces (mr_stage_velocity): two FP64 slots; a refinement
+    // swaps the slot with U64/V64/W64 instead of copying it
+    double *sU[2] = {nullptr, nullptr}, *sV[2] = {nullptr, nullptr}, *sW[2] = {nullptr, nullptr};
+    cudaEvent_t stg_copied[2] = {nullptr, nullptr};   // on the copy stream: the slot's copy is done
+    cudaEvent_t stg_free[2] = {nullptr, nullptr};     // on the compute stream: the slot's memory is free
+    int stg_next = 0;                                 // slot the next mr_stage_velocity fills
+    int stg_ready = -1;                               // slot holding staged faces not yet refined
 };
 
 }  // namespace mr

@@ -59,6 +59,8 @@ _SIGS = {
     "mr_last_error": (ctypes.c_char_p, []),
     "mr_grid": (ctypes.c_int, [_VP, _VP, _VP]),
     "mr_refine_velocity": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP]),
+    "mr_stage_velocity": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP]),
+    "mr_refine_velocity_staged": (ctypes.c_int, [_VP, _VP]),
     "mr_set_scalar": (ctypes.c_int, [_VP, _VP, _I32, _VP]),
     "mr_get_scalar": (ctypes.c_int, [_VP, _VP, _VP, _I32, _VP]),
     "mr_scalar_step": (ctypes.c_int, [_VP, _I64, _VP]),
@@ -217,6 +219,21 @@ def mr_refine_velocity(h: Handle, U, V, W, Us=None, Vs=None, Ws=None, stream=Non
     qv = _ptr(Vs, _n(s["Vs"]), h.np_dtype, "Vs")
     qw = _ptr(Ws, _n(s["Ws"]), h.np_dtype, "Ws")
     _check(lib().mr_refine_velocity(h.ptr, pu, pv, pw, qu, qv, qw, _stream(stream)))
+
+
+def mr_stage_velocity(h: Handle, U, V, W, copy_stream=None):
+    """Copy the next coarse faces into a staging slot on ``copy_stream``
+    (asynchronous; keep U, V, W unchanged until the stream has passed it)."""
+    s = h.shapes
+    pu = _ptr(U, _n(s["U"]), np.float64, "U")
+    pv = _ptr(V, _n(s["V"]), np.float64, "V")
+    pw = _ptr(W, _n(s["W"]), np.float64, "W")
+    _check(lib().mr_stage_velocity(h.ptr, pu, pv, pw, _stream(copy_stream)))
+
+
+def mr_refine_velocity_staged(h: Handle, stream=None):
+    """Refine the last staged faces on ``stream`` (which waits for their copy)."""
+    _check(lib().mr_refine_velocity_staged(h.ptr, _stream(stream)))
 
 
 def _dtype_code(a):

@@ -147,3 +147,39 @@ def test_refine_from_pinned_host_faces(mr, prob, kind):
         out.append(T.cpu().numpy())
         h.close()
     assert np.array_equal(out[0], out[1])
+
+
+@pytest.mark.parametrize("kind", ["f32_xfused", "f32_fused", "f64_stored"])
+def test_staged_refinement_matches_direct(mr, prob, kind):
+    """mr_stage_velocity on a second stream, overlapping the steps, then
+    mr_refine_velocity_staged, over three coarse velocities (both staging slots
+    reused): bit-identical to mr_refine_velocity with the same faces."""
+    prec, mode = {"f32_xfused": (mr.MR_F32, mr.MR_VEL_XFUSED), "f32_fused": (mr.MR_F32, mr.MR_VEL_FUSED),
+                  "f64_stored": (mr.MR_F64, mr.MR_VEL_STORED)}[kind]
+    vels = [[torch.from_numpy(np.ascontiguousarray(a * (1.0 - 0.3 * q))).pin_memory() for a in (prob.U, prob.V, prob.W)]
+            for q in range(3)]
+    out = []
+    for staged in (False, True):
+        h = mr.mr_create(prob.mr_config(mr, prec, mode))
+        cs = torch.cuda.Stream()
+        if staged:
+            with pytest.raises(mr.MRError) as e:
+                mr.mr_refine_velocity_staged(h)
+            assert e.value.code == mr.MR_ERR_STATE
+            mr.mr_stage_velocity(h, *vels[0], copy_stream=cs)
+        for q in range(3):
+            if staged:
+                mr.mr_refine_velocity_staged(h)
+                if q + 1 < 3:
+                    mr.mr_stage_velocity(h, *vels[q + 1], copy_stream=cs)
+            else:
+                mr.mr_refine_velocity(h, *vels[q])
+            if q == 0:
+                mr.mr_set_scalar(h, dev(prob.T0))
+            mr.mr_scalar_step(h, 3)
+        T = torch.empty(prob.T0.shape, dtype=torch.float64, device="cuda")
+        mr.mr_get_scalar(h, T)
+        torch.cuda.synchronize()
+        out.append(T.cpu().numpy())
+        h.close()
+    assert np.array_equal(out[0], out[1])
