@@ -816,15 +816,27 @@ int mr_stage_velocity(mr_handle h, const double* U, const double* V, const doubl
     DeviceBuffers& b = h->buf;
     cudaStream_t cs = (cudaStream_t)copy_stream;
     cudaError_t e = cudaSuccess;
-    if (!b.sU[0]) {
-        for (int q = 0; q < 2 && e == cudaSuccess; ++q) {
-            e = cudaMalloc((void**)&b.sU[q], h->ncU * 8);
-            if (e == cudaSuccess) e = cudaMalloc((void**)&b.sV[q], h->ncV * 8);
-            if (e == cudaSuccess) e = cudaMalloc((void**)&b.sW[q], h->ncW * 8);
-            if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b.stg_copied[q], cudaEventDisableTiming);
-            if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b.stg_free[q], cudaEventDisableTiming);
+    if (!b.stg_free[1]) {
+        // both slots and their events, or nothing (a failed call leaves no half state)
+        double* p[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+        cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+        const size_t n[3] = {h->ncU, h->ncV, h->ncW};
+        for (int k = 0; k < 6 && e == cudaSuccess; ++k) e = cudaMalloc((void**)&p[k], n[k % 3] * 8);
+        for (int k = 0; k < 4 && e == cudaSuccess; ++k) e = cudaEventCreateWithFlags(&ev[k], cudaEventDisableTiming);
+        if (e != cudaSuccess) {
+            for (double* x : p)
+                if (x) cudaFree(x);
+            for (cudaEvent_t x : ev)
+                if (x) cudaEventDestroy(x);
+            return cuda_check(e, "mr_stage_velocity: staging slots");
         }
-        if (e != cudaSuccess) return cuda_check(e, "mr_stage_velocity: staging slots");
+        for (int q = 0; q < 2; ++q) {
+            b.sU[q] = p[3 * q];
+            b.sV[q] = p[3 * q + 1];
+            b.sW[q] = p[3 * q + 2];
+            b.stg_copied[q] = ev[2 * q];
+            b.stg_free[q] = ev[2 * q + 1];
+        }
     }
     const int q = b.stg_next;
     // the slot's memory may still be read by work queued before the refinement
