@@ -42,28 +42,31 @@ constexpr float kTBottom = 0.5f, kTTop = -0.5f;
 // rows each side and the layer constants carry the z-face weights.
 // TY: tile height; 16 consumer threads (4-cell segments) per row, one producer
 // warp; 64x16 tiles run two CTAs per SM, 64x8 tiles four (small grids).
-template <int M, bool MT, bool O4 = false, int TY = 16>
+// DIV: the layout of the reductions (divergence, CFL), which stream only the
+// velocity sets: no scalar boxes, 16 slots, so that about four times the bytes
+// are in flight per CTA.
+template <int M, bool MT, bool O4 = false, int TY = 16, bool DIV = false>
 struct XT {
     static constexpr int CONS = 16 * TY;                // consumer threads
     static constexpr int THREADS = CONS + 32;           // + one producer warp
     static constexpr int CTAS = TY == 16 ? 2 : (O4 ? 3 : 4);   // resident CTAs per SM the layout is sized for
     static constexpr int kBY = TY + 2;                  // rows of the T^{s-1} box
     static constexpr uint32_t tm_bytes = (uint32_t)(kBX * kBY) * 4;
-    static constexpr int PM = (int)((tm_bytes + 127) / 128) * 128 / 4;
+    static constexpr int PM = DIV ? 0 : (int)((tm_bytes + 127) / 128) * 128 / 4;
     static constexpr int CX = kTX / M;
     static constexpr int BXC = CX + 8;                  // coarse box width: columns I0-4 .. I0+CX+3
     // ring slots; MT (two velocity sets per slot) keeps two CTAs per SM with fewer
     // slots.  O4 keeps five planes live at a chunk's first layer (k0-2 .. k0+2),
     // so it needs at least five slots (at M = 2 with MT that leaves one CTA per SM).
     static constexpr int NB0 = MT ? ((M == 4) ? 5 : 4) : ((M == 4 && TY == 16) ? 7 : 6);
-    static constexpr int NB = (O4 && TY == 8 && !MT) ? 7 : ((O4 && NB0 < 5) ? 5 : NB0);
+    static constexpr int NB = DIV ? 16 : ((O4 && TY == 8 && !MT) ? 7 : ((O4 && NB0 < 5) ? 5 : NB0));
     // one ring slot (floats): T^n plane, T^{n-1} plane, then the velocity set of
     // one layer k: WY of its upper plane k+1 (its lower plane k is the previous
     // slot's), UO and VR of layer k; with MT the set of the second coarse time
     // level follows at offset DS; then the layer constants
     static constexpr int BYN = O4 ? TY + 4 : kBY;        // rows of the T^s box
     static constexpr uint32_t tn_bytes = (uint32_t)(kBX * BYN) * 4;
-    static constexpr int PN = (int)((tn_bytes + 127) / 128) * 128 / 4;
+    static constexpr int PN = DIV ? 0 : (int)((tn_bytes + 127) / 128) * 128 / 4;
     static constexpr int LCW = 32;                      // floats of one row of layer constants
     static constexpr int oTn = 0, oTm = PN;
     static constexpr int oWY = PN + PM;                 // [TY][BXC]      plane k+1
@@ -128,14 +131,14 @@ __device__ __forceinline__ float2 hi2(float4 v) { return make_float2(v.z, v.w); 
 // k0-2+r (one more plane below and above the chunk) and the consumers carry the
 // z-face advective flux of plane k+1 to the next layer.
 template <int M, int KIND, bool LF, bool MT, bool O4, int TY>
-__global__ void __launch_bounds__(XT<M, MT, O4, TY>::THREADS, XT<M, MT, O4, TY>::CTAS)
+__global__ void __launch_bounds__(XT<M, MT, O4, TY, (KIND != 0)>::THREADS, XT<M, MT, O4, TY, (KIND != 0)>::CTAS)
 k_xfused(const __grid_constant__ CUtensorMap tmn, const __grid_constant__ CUtensorMap tmm,
          const __grid_constant__ CUtensorMap twy, const __grid_constant__ CUtensorMap tuo,
          const __grid_constant__ CUtensorMap tvr, const __grid_constant__ CUtensorMap tlc,
          const __grid_constant__ CUtensorMap twy1, const __grid_constant__ CUtensorMap tuo1,
          const __grid_constant__ CUtensorMap tvr1, const XArgs A)
 {
-    using L = XT<M, MT, O4, TY>;
+    using L = XT<M, MT, O4, TY, (KIND != 0)>;
     constexpr int kThreads = L::CONS;
     constexpr int NB = L::NB, BXC = L::BXC, NC = 4 / M, NW = kThreads / 32;
     constexpr bool DIVONLY = KIND != 0;
@@ -530,7 +533,7 @@ k_xfused(const __grid_constant__ CUtensorMap tmn, const __grid_constant__ CUtens
         }
         outp += plane;
     };
-    if constexpr (!O4) {
+    if constexpr (!O4 && !DIVONLY) {
         // unrolled by the ring length: layer k0 + i uses the slots i, i+1, i+2
         // (mod NB), constants in the inner loop
         for (int kb = k0, opar = 0; kb < k1; kb += NB, opar ^= 1) {
@@ -541,18 +544,26 @@ k_xfused(const __grid_constant__ CUtensorMap tmn, const __grid_constant__ CUtens
             }
         }
     } else {
-        // fourth order: the unrolled loop would outgrow the instruction cache, so
-        // the slots rotate
-        int sm2 = 0, sb = 1, sc = 2, st = 3, s2 = 4, tpar = 0;
+        // fourth order (an unrolled loop would outgrow the instruction cache) and
+        // the reductions (16 slots): the slots rotate; the waited slot is s2
+        // (O4) or st, its parity flips when it wraps
+        int sm2 = 0, sb = OFF - 1, sc = OFF, st = OFF + 1, s2 = OFF + 2, tpar = 0;
         for (int k = k0; k < k1; ++k) {
             layer(k, sm2, sb, sc, st, s2, tpar);
             sm2 = sb;
             sb = sc;
             sc = st;
-            st = s2;
-            if (++s2 == NB) {
-                s2 = 0;
-                tpar ^= 1;
+            if constexpr (O4) {
+                st = s2;
+                if (++s2 == NB) {
+                    s2 = 0;
+                    tpar ^= 1;
+                }
+            } else {
+                if (++st == NB) {
+                    st = 0;
+                    tpar ^= 1;
+                }
             }
         }
     }
@@ -845,7 +856,7 @@ cudaError_t launch_xt(const Grid<float>& g, XSet v0, XSet v1, float alpha, int n
                       const float* rx12, const float* w4, const float* Tm1, const float* T, float* Tp1, StepCoef c,
                       int* err, unsigned long long* divmax, cudaStream_t st)
 {
-    using L = XT<M, MT, O4, TY>;
+    using L = XT<M, MT, O4, TY, (KIND != 0)>;
     if (lcw < L::LCW) return cudaErrorInvalidValue;
     static unsigned long long attr = 0;                   // one bit per device
     constexpr bool DIVONLY = KIND != 0;
