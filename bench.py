@@ -53,7 +53,7 @@ SEED = 1805
 # DRAM bytes (read + write) per launch of the dominant kernel from one ncu capture of the
 # workload (summarised in profiles/), valid only for the kernel sources they were measured on.
 NCU_TRAFFIC = {
-    ("k_xfused", "rb512_stretched_f32"): {"bytes": 1153919744 + 384205568, "sources": "175ef27ec588b793.8945e0b384d6ff21",
+    ("k_xfused", "rb512_stretched_f32"): {"bytes": 1153799936 + 384546048, "sources": "f3cacf946487e655.8945e0b384d6ff21",
                                           "files": ("mr_xfused.cu", "mr_ptx.cuh")},
     ("k_fused", "rb512_stretched_f32"): {"bytes": 874555904 + 379363328, "sources": "d08bd9598cfdcca9.8945e0b384d6ff21",
                                          "files": ("mr_fused.cu", "mr_ptx.cuh")},

@@ -964,10 +964,13 @@ cudaError_t launch_xfused_prep(const Grid<float>& g, const float* U, const float
     cudaError_t e = launch_column_balance<float>(g, U, V, W, scrW, st);
     if (e != cudaSuccess) return e;
     // one block per (coarse row, coarse slab) while the slab's UO and WY fit in
-    // shared memory; else the two per-layer kernels
+    // shared memory; else the two per-layer kernels (MR_XFUSED_PREP_LAYERS=1 in
+    // the environment, read at every call, selects them on any grid so that
+    // they stay tested)
     const int M = g.mz;
     const size_t smem = (size_t)(2 * M + 1) * M * g.nx * sizeof(float);
-    if (g.mx == M && g.my == M && smem <= 200 * 1024) {
+    const char* force = getenv("MR_XFUSED_PREP_LAYERS");
+    if (g.mx == M && g.my == M && smem <= 200 * 1024 && !(force && force[0] == '1')) {
         static unsigned long long attr[2] = {0, 0};
         const void* kern = M == 4 ? reinterpret_cast<const void*>(k_xprep_slab<4>)
                                   : reinterpret_cast<const void*>(k_xprep_slab<2>);

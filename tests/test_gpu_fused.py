@@ -183,3 +183,18 @@ def test_staged_refinement_matches_direct(mr, prob, kind):
         out.append(T.cpu().numpy())
         h.close()
     assert np.array_equal(out[0], out[1])
+
+
+def test_xfused_per_layer_intermediates(mr, prob, monkeypatch):
+    """The per-layer kernels of the split-x intermediates, which serve grids
+    whose slab arrays exceed shared memory, forced here through
+    MR_XFUSED_PREP_LAYERS: the same run as the one-block-per-slab kernel (to a
+    few FP32 ulps), and the oracle's."""
+    n = 17
+    _, Ta, Tpa = _run(mr, prob, mr.MR_VEL_XFUSED, n)
+    monkeypatch.setenv("MR_XFUSED_PREP_LAYERS", "1")
+    _, Tb, Tpb = _run(mr, prob, mr.MR_VEL_XFUSED, n)
+    assert np.abs(Ta - Tb).max() <= 1e-6 and np.abs(Tpa - Tpb).max() <= 1e-6
+    vel = O.refine(prob.cfg, prob.U, prob.V, prob.W)
+    _, T_ref = O.run(prob.cfg, vel, prob.T0, n)
+    assert np.abs(Tb - T_ref).max() <= F32_T_TOL
