@@ -399,6 +399,24 @@ def test_cfl_dt_uniform_flow(oracle_mod):
     assert abs(dt - 0.3 / (0.5 * Nx + 0.25 * Ny)) < 1e-15
 
 
+def test_cfl_dt_single_faces_stretched(oracle_mod):
+    """CFL of dense faces that are zero but for one or two (stretched z): one W
+    face on plane p gives dt = CFL min(dz_{p-1}, dz_p) / |w| (the rate uses the
+    cell's own dz); a U face and a W face of the same cell add their rates."""
+    O = oracle_mod
+    cfg = _cfg(O, nx=4, ny=4, nz=4, mx=2, my=2, mz=2, gamma=1.5)
+    sh = cfg.shapes()
+    dz = np.diff(O.grid(cfg)["zf"])
+    Nx = cfg.dense[0]
+    dx = 1.0 / Nx
+    Us, Vs, Ws = np.zeros(sh["Us"]), np.zeros(sh["Vs"]), np.zeros(sh["Ws"])
+    Ws[3, 5, 2] = -0.7
+    assert abs(O.cfl_dt(cfg, (Us, Vs, Ws), 0.3) - 0.3 * min(dz[2], dz[3]) / 0.7) < 1e-15
+    Us[2, 5, 2] = 0.2                    # west face of cell (2, 5, 2), whose top face carries the W
+    expect = 0.3 / (0.2 / dx + 0.7 / dz[2])
+    assert abs(O.cfl_dt(cfg, (Us, Vs, Ws), 0.3) / expect - 1.0) < 1e-14
+
+
 # ----------------------------------------------------------------------------- adjoint
 
 @pytest.mark.parametrize("walls", [0, 1])
