@@ -399,6 +399,23 @@ def test_cfl_dt_uniform_flow(oracle_mod):
     assert abs(dt - 0.3 / (0.5 * Nx + 0.25 * Ny)) < 1e-15
 
 
+def test_max_divergence_single_faces_stretched(oracle_mod):
+    """Max |divergence| of dense faces that are zero but for one (stretched z):
+    a U face u changes the net flux of its two cells by u dy dz_k, so
+    max |div| = |u| / dx; a W face w on plane p gives |w| / min(dz_{p-1}, dz_p)."""
+    O = oracle_mod
+    cfg = _cfg(O, nx=4, ny=4, nz=4, mx=2, my=2, mz=2, gamma=1.5)
+    sh = cfg.shapes()
+    dz = np.diff(O.grid(cfg)["zf"])
+    dx = 1.0 / cfg.dense[0]
+    Us, Vs, Ws = np.zeros(sh["Us"]), np.zeros(sh["Vs"]), np.zeros(sh["Ws"])
+    Us[6, 1, 3] = 0.4
+    assert abs(O.max_divergence(cfg, (Us, Vs, Ws)) / (0.4 / dx) - 1.0) < 1e-14
+    Us[6, 1, 3] = 0.0
+    Ws[5, 2, 7] = -0.9
+    assert abs(O.max_divergence(cfg, (Us, Vs, Ws)) / (0.9 / min(dz[4], dz[5])) - 1.0) < 1e-14
+
+
 def test_cfl_dt_single_faces_stretched(oracle_mod):
     """CFL of dense faces that are zero but for one or two (stretched z): one W
     face on plane p gives dt = CFL min(dz_{p-1}, dz_p) / |w| (the rate uses the
