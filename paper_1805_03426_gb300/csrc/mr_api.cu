@@ -840,8 +840,10 @@ int mr_stage_velocity(mr_handle h, const double* U, const double* V, const doubl
     }
     const int q = b.stg_next;
     // the slot's memory may still be read by work queued before the refinement
-    // that released it (a wait on a never-recorded event passes at once)
+    // that released it, or written by an earlier copy on another stream (a wait
+    // on a never-recorded event passes at once)
     e = cudaStreamWaitEvent(cs, b.stg_free[q], 0);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, b.stg_copied[q], 0);
     if (e == cudaSuccess) e = cudaMemcpyAsync(b.sU[q], U, h->ncU * 8, cudaMemcpyDefault, cs);
     if (e == cudaSuccess) e = cudaMemcpyAsync(b.sV[q], V, h->ncV * 8, cudaMemcpyDefault, cs);
     if (e == cudaSuccess) e = cudaMemcpyAsync(b.sW[q], W, h->ncW * 8, cudaMemcpyDefault, cs);
