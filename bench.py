@@ -49,6 +49,17 @@ WORKLOADS = {
                                       "Ra=1e8, Pr=7, CFL 0.3"),
 }
 SEED = 1805
+METRIC = "dense-grid scalar Gcell-updates/s & % HBM roofline, FP32 vs FP64; adjoint/fwd"
+# what one timed step holds, per velocity mode
+STEP_LABEL = {
+    "xfused": "one kernel launch per step: the x-stage of the refinement (Section 3.2) in registers from the "
+              "z- and y-stage results kept at coarse x resolution (formed once per velocity, outside the timed "
+              "region: the velocity is fixed), and the finite-volume update (Eq. 5)",
+    "fused": "one kernel launch per step: the whole refinement (Section 3.2) from the coarse faces, in shared "
+             "memory and registers, and the finite-volume update (Eq. 5); nothing of the refined velocity in HBM",
+    "stored": "one kernel launch per step: the finite-volume update (Eq. 5) on dense faces refined once per "
+              "velocity, outside the timed region",
+}
 
 # DRAM bytes (read + write) per launch of the dominant kernel from one ncu capture of the
 # workload (summarised in profiles/), valid only for the kernel sources they were measured on.
@@ -66,7 +77,6 @@ NCU_TRAFFIC = {
 # (opposite neighbours summed, diagonal and plate terms per layer), 4 to
 # scale and add the advective parts, 3 for the update.
 FP64_FLOPS_PER_CELL = 38
-FP64_NOMINAL_TFLOPS = 1.25   # GB300 FP64 (non-tensor), nominal
 
 
 def _traffic(kernel, workload):
@@ -232,24 +242,42 @@ def run_mr(args):
     value = job_rate(cells, args.steps, world, t)
     st = mr.mr_scalar_stats(h, stream=stream, allow_nonfinite=True)
 
-    # roofline of the dominant (only) kernel of the step: one launch per step
+    # the state the timed steps reached, for the error against the FP64 oracle
+    # (the handle is reused below)
+    Tgpu = torch.empty(tuple(reversed((Nx, Ny, Nz))), dtype=torch.float64, device="cuda")
+    Tgpu_prev = torch.empty_like(Tgpu)
+    mr.mr_get_scalar(h, Tgpu, Tgpu_prev, stream=stream)
+    torch.cuda.synchronize()
+    Tgpu, Tgpu_prev = Tgpu.cpu().numpy(), Tgpu_prev.cpu().numpy()
+    nsteps_run = mr.mr_step_index(h)
+
+    # roofline of the dominant (only) kernel of the step, one launch per step,
+    # on the method's algorithmic bytes per dense cell-update: two scalar levels
+    # in and one out, plus the coarse faces (velocity refined in the kernel) or
+    # the three dense faces (stored velocity)
     elt = 4 if prec == mr.MR_F32 else 8
     M3 = w["m"] ** 3
-    if mode == mr.MR_VEL_FUSED:      # two scalar levels in, one out, coarse faces
+    if mode in (mr.MR_VEL_FUSED, mr.MR_VEL_XFUSED):
         bytes_per_cell = 3 * elt + 3 * elt / M3
-    elif mode == mr.MR_VEL_XFUSED:   # two levels in, one out, three coarse-x intermediates (4 ghost columns each side)
-        nx = w["nx"]
-        bytes_per_cell = 3 * elt + 3 * elt * (nx + 8) / (nx * w["m"])
-    else:                            # two levels in, one out, three dense faces
+    else:
         bytes_per_cell = 6 * elt
+    # what the kernel itself moves: the split-x kernel also reads the z- and
+    # y-stage results at coarse x resolution (4 ghost columns each side)
+    kernel_bpc = bytes_per_cell
+    if mode == mr.MR_VEL_XFUSED:
+        nx = w["nx"]
+        kernel_bpc = 3 * elt + 3 * elt * (nx + 8) / (nx * w["m"])
     per_launch = t / args.steps
     peak, peak_kind = _peaks()
     achieved = bytes_per_cell * cells / per_launch / 1e9
     kname = {mr.MR_VEL_FUSED: "k_fused", mr.MR_VEL_XFUSED: "k_xfused"}.get(mode, "k_step_stored")
+    traffic = _traffic(kname, args.workload)
     roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-            "frac": round(achieved / peak, 4), "traffic": _traffic(kname, args.workload), "peak_source": peak_kind,
-            "kernel": kname,
-            "bytes_per_cell": round(bytes_per_cell, 3), "launch_ms": round(per_launch * 1e3, 4)}
+            "frac": round(achieved / peak, 4), "traffic": traffic, "peak_source": peak_kind,
+            "kernel": kname, "bytes_per_cell": round(bytes_per_cell, 3), "launch_ms": round(per_launch * 1e3, 4),
+            "kernel_bytes_per_cell": round(kernel_bpc, 3),
+            "kernel_frac_own_bytes": round(kernel_bpc * cells / per_launch / 1e9 / peak, 4),
+            "traffic_over_algorithmic": round(traffic / (bytes_per_cell * cells), 3) if traffic else None}
 
     # the per-call costs around the step: statistics (the call synchronises:
     # wall clock) and plate Nu (asynchronous: stream-timed)
@@ -273,7 +301,7 @@ def run_mr(args):
     # the next coarse velocity resident on the device
     temporal = None
     if rank == 0 and not args.no_temporal:
-        temporal = temporal_cost(torch, mr, h, w, (dU, dV, dW), cells, stream)
+        temporal = {f"mt{mt}": temporal_cost(torch, mr, h, w, (dU, dV, dW), cells, stream, mt=mt) for mt in (2, 4)}
 
     # the same step with the fourth-order face values of Section 2.2 (opt-in)
     face4 = None
@@ -299,11 +327,12 @@ def run_mr(args):
         # the FP64 step is bound by GB300's FP64 pipe: report it against the
         # nominal FP64 rate (no measured FP64 peak) and against HBM
         flops64 = FP64_FLOPS_PER_CELL * v64 * 1e9 / 1e12
+        peak64 = mr.mr_fp64_fma_rate(stream=stream)
         fp64 = {"value": round(v64, 3), "unit": "Gcell-updates/s", "steps": k64,
                 "ms_per_step": round(t64 / k64 * 1e3, 4), "fp32_over_fp64": round(value / world / v64, 2),
                 "fp64_pipe": {"tflops": round(flops64, 3), "flops_per_cell": FP64_FLOPS_PER_CELL,
-                              "peak": FP64_NOMINAL_TFLOPS, "peak_source": "nominal",
-                              "frac": round(flops64 / FP64_NOMINAL_TFLOPS, 4)},
+                              "peak": round(peak64, 4), "peak_source": "measured: FP64 FMA chains, CUDA events",
+                              "frac": round(flops64 / peak64, 4)},
                 "hbm": {"achieved": round(48 * v64, 1), "unit": "GB/s", "bytes_per_cell": 48,
                         "frac": round(48 * v64 / peak, 4)}}
         h64.close()
@@ -318,6 +347,7 @@ def run_mr(args):
     if rank == 0 and not args.no_e2e:
         Uh, Vh, Wh = (torch.from_numpy(a).pin_memory() for a in (U, V, W))
         nu = torch.zeros(2, dtype=torch.float64).pin_memory()
+        Tc = torch.zeros((w["nz"], w["ny"], w["nx"]), dtype=torch.float64).pin_memory()
         ke = max(20, args.steps // 5)
         copy_stream = torch.cuda.Stream()
 
@@ -329,6 +359,7 @@ def run_mr(args):
                     mr.mr_stage_velocity(h, Uh, Vh, Wh, copy_stream=copy_stream)
                 mr.mr_scalar_step(h, 1, stream=stream)
                 mr.mr_plate_nu(h, nu, stream=stream)
+                mr.mr_upscale_scalar(h, Tc, stream=stream)     # synchronises
                 stream.synchronize()
 
         def serial(n):
@@ -336,6 +367,7 @@ def run_mr(args):
                 mr.mr_refine_velocity(h, Uh, Vh, Wh, stream=stream)
                 mr.mr_scalar_step(h, 1, stream=stream)
                 mr.mr_plate_nu(h, nu, stream=stream)
+                mr.mr_upscale_scalar(h, Tc, stream=stream)
                 stream.synchronize()
 
         def timed(fn):
@@ -348,31 +380,36 @@ def run_mr(args):
 
         te, ts = timed(pipelined), timed(serial)
         e2e = {"value": round(cells * ke / te / 1e9, 3), "unit": "Gcell-updates/s",
-               "h2d_bytes_per_step": int(U.nbytes + V.nbytes + W.nbytes), "d2h_bytes_per_step": 16,
-               "steps": ke, "pipeline": "next step's faces staged on a copy stream during the step",
+               "h2d_bytes_per_step": int(U.nbytes + V.nbytes + W.nbytes),
+               "d2h_bytes_per_step": int(nu.numel() * 8 + Tc.numel() * 8),
+               "steps": ke, "per_step": "coarse velocity in (pinned host), refinement, one step, plate Nu and "
+                                        "the upscaled coarse T (Section 3.3) out to pinned host memory",
+               "pipeline": "next step's faces staged on a copy stream during the step",
                "serial": round(cells * ke / ts / 1e9, 3)}
 
     adj = None
     if rank == 0 and not args.no_adjoint:
         adj = adjoint_cost(torch, mr, stream)
 
-    cpu = None
+    cpu, prec_err = None, None
     if rank == 0 and world == 1 and not args.no_cpu:
-        cpu = cpu_baseline(w, dt, budget_s=args.cpu_budget)
+        # the oracle from the same inputs and dt: a timed sample for the CPU
+        # baseline, then on (untimed) to the GPU run's step count for its error
+        cpu, ref = cpu_baseline(w, dt, budget_s=args.cpu_budget, run_to=nsteps_run)
+        if ref is not None:
+            prec_err = precision_error(Tgpu, Tgpu_prev, ref, st, nsteps_run, prec == mr.MR_F32)
 
     h.close()
     if rank == 0:
         line = {
-            "metric": "dense-grid scalar cell-updates/s (refine + finite-volume step)",
+            "metric": METRIC,
             "value": round(value, 3), "unit": "Gcell-updates/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": round(t / args.steps * 1e3, 4), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None,
             "dtype": "f32" if prec == mr.MR_F32 else "f64", "data": "synthetic",
-            "config": {"workload": args.workload, "description": w["label"], "dense_cells": cells,
-                       "velocity_mode": args.mode, "dt": dt, "parallelism": f"replicas{world}",
-                       "l2": "inputs larger than L2 (3 scalar levels of %.0f MB)" % (cells * elt / 2**20),
-            "bytes_per_cell": round(bytes_per_cell, 3)},
-            "roofline": roof, "fp64_path": fp64, "adjoint": adj, "temporal": temporal, "face_order4": face4,
+            "config": bench_config(args, w, dt, world, args.mode),
+            "roofline": roof, "precision_error": prec_err, "fp64_path": fp64, "adjoint": adj,
+            "temporal": temporal, "face_order4": face4,
             "per_call": aux, "e2e": e2e,
             "cpu_baseline": cpu,
             "gpu_launches": args.steps, "clocks": clk.summary(),
@@ -382,6 +419,30 @@ def run_mr(args):
     if world > 1:
         dist.barrier()
         dist.destroy_process_group()
+
+
+def bench_config(args, w, dt, world, mode):
+    """The workload as both arms state it."""
+    cells = w["nx"] * w["ny"] * w["nz"] * w["m"] ** 3
+    return {"workload": args.workload, "description": w["label"], "dense_cells": cells,
+            "velocity_mode": mode, "step": STEP_LABEL[mode], "cfl": 0.3, "dt": float("%.5g" % dt),
+            "parallelism": f"replicas{world}",
+            "l2": "inputs larger than L2 (3 scalar levels of %.0f MB)" % (cells * 4 / 2**20)}
+
+
+def precision_error(T, Tprev, ref, st_gpu, nsteps, f32):
+    """Max-norm scalar error and relative plate-Nu error of the GPU run against
+    the FP64 oracle after the same steps from the same inputs and dt."""
+    Tm_ref, T_ref, st_ref = ref
+    out = {"steps": int(nsteps), "scalar_maxnorm": float(np.abs(T - T_ref).max()),
+           "scalar_maxnorm_prev_level": float(np.abs(Tprev - Tm_ref).max()),
+           "nu_bot_rel": abs(st_gpu["nu_bot"] / st_ref["nu_bot"] - 1),
+           "nu_top_rel": abs(st_gpu["nu_top"] / st_ref["nu_top"] - 1),
+           "against": "FP64 oracle, same coarse velocity, initial scalar and dt"}
+    if f32:
+        out["bars"] = {"scalar_maxnorm": 1e-5, "nu_rel": 1e-4}
+        out["within_bars"] = bool(out["scalar_maxnorm"] <= 1e-5 and max(out["nu_bot_rel"], out["nu_top_rel"]) <= 1e-4)
+    return out
 
 
 def temporal_cost(torch, mr, h, w, vel0, cells, stream, mt=4, K=20):
@@ -455,10 +516,11 @@ def adjoint_cost(torch, mr, stream, S=200, ck=20):
     return out
 
 
-def cpu_baseline(w, dt, budget_s=30.0, max_steps=None, warmup=0):
+def cpu_baseline(w, dt, budget_s=30.0, max_steps=None, warmup=0, run_to=None):
     """FP64 oracle on this host's cores: one refinement, `warmup` untimed
     whole-grid steps, then timed steps until the time budget or `max_steps` is
-    reached (at least one)."""
+    reached (at least one).  With run_to, the oracle then continues untimed to
+    run_to steps in all and also returns (T^{run_to-1}, T^{run_to}, stats)."""
     import oracle as O
     from paper_1805_03426_gb300 import synth
     cfg = O.Config(nx=w["nx"], ny=w["ny"], nz=w["nz"], mx=w["m"], my=w["m"], mz=w["m"], gamma=w["gamma"],
@@ -479,14 +541,31 @@ def cpu_baseline(w, dt, budget_s=30.0, max_steps=None, warmup=0):
         Tm, T = T, O.step(cfg, vel, Tm, T, warmup + n)
         t_steps += time.perf_counter() - t0
         n += 1
-        if t_steps >= budget_s or (max_steps and n >= max_steps):
+        if t_steps >= budget_s or (max_steps and n >= max_steps) or (run_to and warmup + n >= run_to):
             break
     cores = len(os.sched_getaffinity(0))
-    return {"value": round(Nx * Ny * Nz * n / t_steps / 1e9, 5), "unit": "Gcell-updates/s", "cores": cores,
-            "kind": "oracle", "sample": f"{n} FP64 oracle steps on the full {Nx}x{Ny}x{Nz} grid after one "
-                                        f"refinement ({t_ref:.1f} s, not counted) and {warmup} untimed steps; "
-                                        f"OpenMP over {cores} threads",
-            "steps": n, "seconds": round(t_steps, 2)}
+    out = {"value": round(Nx * Ny * Nz * n / t_steps / 1e9, 5), "unit": "Gcell-updates/s", "cores": cores,
+           "kind": "oracle", "sample": f"{n} FP64 oracle steps on the full {Nx}x{Ny}x{Nz} grid after one "
+                                       f"refinement ({t_ref:.1f} s, not counted) and {warmup} untimed steps; "
+                                       f"OpenMP over {cores} threads",
+           "steps": n, "seconds": round(t_steps, 2)}
+    if run_to is None:
+        return out
+    s = warmup + n
+    if run_to > s:
+        Tm, T = O.run_from(cfg, vel, Tm, T, s, run_to - s)
+    return out, (Tm, T, O.stats(cfg, T))
+
+
+def reference_dt(w):
+    """dt at CFL 0.3 on the oracle's refined FP64 velocity of the workload."""
+    import oracle as O
+    from paper_1805_03426_gb300 import synth
+    cfg = O.Config(nx=w["nx"], ny=w["ny"], nz=w["nz"], mx=w["m"], my=w["m"], mz=w["m"], gamma=w["gamma"],
+                   kappa=(w["ra"] * w["pr"]) ** -0.5, dt=1.0)
+    g = O.grid(cfg)
+    U, V, W = synth.coarse_velocity(SEED, g["Xf"], g["Yf"], g["Zf"], rms=w["rms"])
+    return O.cfl_dt(cfg, O.refine(cfg, U, V, W), 0.3)
 
 
 def run_reference(args):
@@ -495,14 +574,14 @@ def run_reference(args):
     if rank != 0:
         return
     w = WORKLOADS[args.workload]
-    dt = 1e-4
+    dt = reference_dt(w)
     budget = min(120.0, 10.0 * args.steps)
     cpu = cpu_baseline(w, dt, budget_s=budget, max_steps=args.steps, warmup=args.warmup)
-    line = {"impl": "reference", "metric": "dense-grid scalar cell-updates/s (refine + finite-volume step)",
+    line = {"impl": "reference", "metric": METRIC,
             "value": cpu["value"], "unit": "Gcell-updates/s", "n_gpus": 0, "steps": cpu["steps"],
             "warmup": args.warmup, "ms_per_step": round(cpu["seconds"] / cpu["steps"] * 1e3, 2), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": args.workload, "description": w["label"]},
+            "config": bench_config(args, w, dt, world, args.mode),
             "cpu_baseline": cpu,
             "e2e": {"value": cpu["value"], "unit": "Gcell-updates/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
@@ -528,6 +607,10 @@ def main():
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
+    world = _dist()[0]
+    if args.impl == "mr" and args.gpus != world:
+        raise SystemExit(f"--gpus {args.gpus}: launch one process per GPU (torchrun --nproc-per-node "
+                         f"{args.gpus}); this process group has {world}")
     if args.impl == "reference":
         run_reference(args)
     else:

@@ -235,24 +235,52 @@ int mr_adjoint_forward(mr_handle h, int64_t nsteps, int32_t checkpoint_every, co
 int mr_adjoint_backward(mr_handle h, double gscale, void* gT0, int32_t gT0_dtype, double* gU, double* gV,
                         double* gW, mr_stream stream);
 
-/* Allocation-free refinement (no counterpart in the paper: an interface for
- * callers that cannot allocate device memory, e.g. code running inside a
- * framework whose caching allocator owns the whole device, or a plug-in
- * forbidden to call cudaMalloc).  Computes the same dense faces as
- * mr_refine_velocity (FP64 in, FP64 out, Section 3.2) from *cfg alone -- no
- * handle -- using only a file-scope device scratch array of 32 MiB that every
- * GPU loading this library holds until the process exits; it allocates nothing.
- * Its grid and R matrices are rebuilt into that array at every call.  Sizes
- * whose grid, R matrices and work arrays exceed the 32 MiB give MR_ERR_ARG with
- * the needed size in mr_last_error().  U, V, W, Us, Vs, Ws must be device
- * memory (MR_ERR_ARG otherwise); cfg's precision, velocity_mode, Ra, Pr, dt and
- * plate settings are ignored.  The first call on a device looks the array's
- * device address up (cudaGetSymbolAddress, with that device current), so make
- * that first call before any stream capture.  Every call shares the one array:
- * calls that overlap on the GPU (different streams, or devices sharing nothing
- * but the host thread's current device) race and corrupt each other. */
+/* Allocation-free refinement.  The paper has no counterpart: this is an
+ * interface for callers that cannot allocate device memory, e.g. code running
+ * inside a framework whose caching allocator owns the whole device, or a
+ * plug-in forbidden to call cudaMalloc.  It computes the same dense faces as
+ * mr_refine_velocity (FP64 in, FP64 out) from *cfg alone -- no handle -- using
+ * only a file-scope device scratch array of 32 MiB that every GPU loading this
+ * library holds until the process exits; it allocates nothing.  Its grid and R
+ * matrices are rebuilt into that array at every call.  Sizes whose grid, R
+ * matrices and work arrays exceed the 32 MiB give MR_ERR_ARG with the needed
+ * size in mr_last_error(), and so does a stretching that collapses the dense
+ * z-layers at the plates (width <= 1e-12).  U, V, W, Us, Vs, Ws must be device
+ * memory (MR_ERR_ARG otherwise); cfg's precision, velocity_mode, Ra, Pr, dt
+ * and plate settings are ignored.  The first call on a device looks the
+ * array's device address up (cudaGetSymbolAddress, with that device current),
+ * so make that first call before any stream capture.  Each device has its own
+ * copy of the array, shared by every call on that device: calls that overlap
+ * on the same device (on any streams) race and corrupt each other's results;
+ * calls on different devices do not interact. */
 int mr_refine_velocity_noalloc(const mr_config* cfg, const double* U, const double* V, const double* W,
                                double* Us, double* Vs, double* Ws, mr_stream stream);
+
+/* Measurement aid (no counterpart in the paper): the FP64 arithmetic rate of
+ * the current device in TFLOP/s (an FMA counts two), from a kernel of
+ * independent FMA chains in registers timed with CUDA events on stream (best
+ * of three launches after one untimed).  The FP64 stored-velocity step is
+ * bound by this rate rather than by HBM.  Synchronises.  Errors: MR_ERR_ARG
+ * (NULL), MR_ERR_CUDA. */
+int mr_fp64_fma_rate(double* tflops, mr_stream stream);
+
+/* Test hooks of the failure paths (no counterpart in the paper; neither
+ * faults the GPU).
+ * mr_debug_inject_wait_timeout arms a one-shot injection: in the next launch
+ * of a TMA-fed step kernel (MR_VEL_XFUSED or MR_VEL_FUSED), every bounded
+ * wait gives up after wait_seconds (0 < wait_seconds <= 1, instead of 1 s), and
+ * the producer warp of the first CTA issues none of its ring loads from ring
+ * stop_ring on.  Every load it did issue is still waited for, so nothing is
+ * in flight when the CTA exits; the consumers' wait for ring stop_ring runs
+ * out and the launch records MR_ERR_TIMEOUT, which the next synchronising
+ * call on a handle in a fused mode returns.  The scalar that launch wrote is
+ * then invalid (restart with mr_set_scalar).
+ * mr_debug_alloc_cap caps the bytes of device memory the library may hold
+ * (cap_bytes >= 0; -1 removes the cap; -2 leaves it unchanged); a refused
+ * allocation fails like an exhausted device (MR_ERR_OOM).  live_bytes (may be
+ * NULL) receives the bytes the library holds now.  Process-wide, thread-safe. */
+int mr_debug_inject_wait_timeout(int32_t stop_ring, double wait_seconds);
+int mr_debug_alloc_cap(int64_t cap_bytes, int64_t* live_bytes);
 
 /* Integer index maps for testing (synchronous, host buffer): coarse cell of
  * every dense cell along x, y, z, then the three coarse cells of the R window

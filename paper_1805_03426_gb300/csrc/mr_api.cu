@@ -373,33 +373,33 @@ void mr_destroy(mr_handle h)
     void* ptrs[] = {b.T[0], b.T[1], b.T[2], b.U64, b.V64, b.W64, b.Us, b.Vs, b.Ws, b.scrW, b.scrV,
                     b.metric, b.red, b.nu2, b.stage, b.tri};
     for (void* p : ptrs)
-        if (p) cudaFree(p);
+        if (p) dev_free(p);
     DeviceBuffers::Level& n = b.next;
     void* nptrs[] = {n.U64, n.V64, n.W64, n.Us, n.Vs, n.Ws, n.xwy, n.xuo, n.xvr, b.lerpc};
     for (void* p : nptrs)
-        if (p) cudaFree(p);
+        if (p) dev_free(p);
     if (h->elt == 4) {
         void* cptrs[] = {n.Uc, n.Vc, n.Wc};
         for (void* p : cptrs)
-            if (p) cudaFree(p);
+            if (p) dev_free(p);
     }
     void* xptrs[] = {b.xwy, b.xuo, b.xvr, b.xlc, b.diag};
     for (void* p : xptrs)
-        if (p) cudaFree(p);
+        if (p) dev_free(p);
     for (int q = 0; q < 2; ++q) {
         void* sptrs[] = {b.sU[q], b.sV[q], b.sW[q]};
         for (void* p : sptrs)
-            if (p) cudaFree(p);
+            if (p) dev_free(p);
         if (b.stg_copied[q]) cudaEventDestroy(b.stg_copied[q]);
         if (b.stg_free[q]) cudaEventDestroy(b.stg_free[q]);
     }
     void* aptrs[] = {h->adj.cp, h->adj.seg, h->adj.mu, h->adj.face, h->adj.scr, h->adj.out};
     for (void* p : aptrs)
-        if (p) cudaFree(p);
+        if (p) dev_free(p);
     if (h->elt == 4) {
-        if (b.Uc) cudaFree(b.Uc);
-        if (b.Vc) cudaFree(b.Vc);
-        if (b.Wc) cudaFree(b.Wc);
+        if (b.Uc) dev_free(b.Uc);
+        if (b.Vc) dev_free(b.Vc);
+        if (b.Wc) dev_free(b.Wc);
     }
     cudaSetDevice(cur);
     delete h;
@@ -435,6 +435,11 @@ int mr_create(const mr_config* cfg, mr_handle* out)
     for (int k = 0; k < h->Nz; ++k) {
         h->zc[k] = 0.5 * (h->zf[k] + h->zf[k + 1]);
         h->dz[k] = h->zf[k + 1] - h->zf[k];
+        if (!(h->dz[k] > 1e-12)) {
+            // tanh clustering saturating in double precision collapses the layers at the plates
+            delete h;
+            return set_error(MR_ERR_ARG, "mr_create: stretching collapses a dense z-layer (width <= 1e-12)");
+        }
     }
     std::vector<double> xf(h->Nx + 1), yf(h->Ny + 1);
     for (int i = 0; i <= h->Nx; ++i) xf[i] = c.lx * i / h->Nx;
@@ -457,7 +462,7 @@ int mr_create(const mr_config* cfg, mr_handle* out)
     DeviceBuffers& b = h->buf;
     cudaError_t e = cudaSuccess;
     auto alloc = [&](void** p, size_t bytes) {
-        if (e == cudaSuccess && bytes) e = cudaMalloc(p, bytes);
+        if (e == cudaSuccess && bytes) e = dev_malloc(p, bytes);
     };
     for (int q = 0; q < 3; ++q) alloc(&b.T[q], h->ncell * h->elt);
     alloc((void**)&b.U64, h->ncU * 8);
@@ -604,8 +609,8 @@ static int refine_into(mr_handle h, void* dUs, void* dVs, void* dWs, cudaStream_
 {
     DeviceBuffers& b = h->buf;
     cudaError_t e = cudaSuccess;
-    if (!b.scrW) e = cudaMalloc(&b.scrW, (size_t)(h->Nz + 1) * h->cfg.ny * h->cfg.nx * h->elt);
-    if (e == cudaSuccess && !b.scrV) e = cudaMalloc(&b.scrV, (size_t)h->Nz * (h->Ny + h->w) * h->cfg.nx * h->elt);
+    if (!b.scrW) e = dev_malloc(&b.scrW, (size_t)(h->Nz + 1) * h->cfg.ny * h->cfg.nx * h->elt);
+    if (e == cudaSuccess && !b.scrV) e = dev_malloc(&b.scrV, (size_t)h->Nz * (h->Ny + h->w) * h->cfg.nx * h->elt);
     if (e != cudaSuccess) return cuda_check(e, "refinement scratch");
     if (h->cfg.precision == MR_F64)
         e = launch_refine<double>(h->g64, (const double*)b.Uc, (const double*)b.Vc, (const double*)b.Wc,
@@ -654,6 +659,7 @@ static int derive_velocity(mr_handle h, bool convert, cudaStream_t st)
 {
     DeviceBuffers& b = h->buf;
     int rc;
+    h->maxdiv_valid = false;
     if (h->cfg.precision == MR_F32 && convert) {
         if ((rc = copy_in(h, b.U64, MR_F64, b.Uc, MR_F32, h->ncU, st))) return rc;
         if ((rc = copy_in(h, b.V64, MR_F64, b.Vc, MR_F32, h->ncV, st))) return rc;
@@ -745,7 +751,7 @@ static int alloc_next(mr_handle h)
     if (n.U64) return MR_OK;
     cudaError_t e = cudaSuccess;
     auto alloc = [&](void** p, size_t bytes) {
-        if (e == cudaSuccess && bytes) e = cudaMalloc(p, bytes);
+        if (e == cudaSuccess && bytes) e = dev_malloc(p, bytes);
     };
     alloc((void**)&n.U64, h->ncU * 8);
     alloc((void**)&n.V64, h->ncV * 8);
@@ -770,11 +776,11 @@ static int alloc_next(mr_handle h)
     if (e != cudaSuccess) {
         void* ptrs[] = {n.U64, n.V64, n.W64, n.Us, n.Vs, n.Ws, n.xwy, n.xuo, n.xvr, b.lerpc};
         for (void* p : ptrs)
-            if (p) cudaFree(p);
+            if (p) dev_free(p);
         if (h->elt == 4) {
             void* cptrs[] = {n.Uc, n.Vc, n.Wc};
             for (void* p : cptrs)
-                if (p) cudaFree(p);
+                if (p) dev_free(p);
         }
         n = DeviceBuffers::Level();
         b.lerpc = nullptr;
@@ -821,11 +827,11 @@ int mr_stage_velocity(mr_handle h, const double* U, const double* V, const doubl
         double* p[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
         cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
         const size_t n[3] = {h->ncU, h->ncV, h->ncW};
-        for (int k = 0; k < 6 && e == cudaSuccess; ++k) e = cudaMalloc((void**)&p[k], n[k % 3] * 8);
+        for (int k = 0; k < 6 && e == cudaSuccess; ++k) e = dev_malloc((void**)&p[k], n[k % 3] * 8);
         for (int k = 0; k < 4 && e == cudaSuccess; ++k) e = cudaEventCreateWithFlags(&ev[k], cudaEventDisableTiming);
         if (e != cudaSuccess) {
             for (double* x : p)
-                if (x) cudaFree(x);
+                if (x) dev_free(x);
             for (cudaEvent_t x : ev)
                 if (x) cudaEventDestroy(x);
             return cuda_check(e, "mr_stage_velocity: staging slots");
@@ -900,6 +906,7 @@ int mr_scalar_coarse_step(mr_handle h, const double* U, const double* V, const d
     for (int32_t i = 0; i < mt; ++i)
         if ((rc = one_step(h, (double)i / (double)mt, st))) return rc;
     swap_levels(b);                    // U^n is now the current velocity
+    h->maxdiv_valid = false;
     return MR_OK;
 }
 
@@ -1031,7 +1038,14 @@ int mr_scalar_stats(mr_handle h, mr_stats* out, mr_stream stream)
     out->nu_bot = nu[0];
     out->nu_top = nu[1];
     out->max_div = 0.0;
-    if (h->have_velocity && (rc = max_divergence(h, &out->max_div, st))) return rc;
+    if (h->have_velocity) {
+        // the divergence depends on the velocity alone: once per velocity
+        if (!h->maxdiv_valid) {
+            if ((rc = max_divergence(h, &h->maxdiv, st))) return rc;
+            h->maxdiv_valid = true;
+        }
+        out->max_div = h->maxdiv;
+    }
     if (bad > 0.0) return set_error(MR_ERR_NONFINITE, "mr_scalar_stats: the scalar holds NaN or Inf");
     return MR_OK;
 }
@@ -1056,15 +1070,15 @@ int mr_cfl_dt(mr_handle h, double cfl, double* dt_out, mr_stream stream)
     } else if (h->cfg.velocity_mode != MR_VEL_STORED) {
         // dense faces are not kept: refine into temporary buffers once
         void *a = nullptr, *bb = nullptr, *c = nullptr;
-        e = cudaMalloc(&a, h->nU * h->elt);
-        if (e == cudaSuccess) e = cudaMalloc(&bb, h->nV * h->elt);
-        if (e == cudaSuccess) e = cudaMalloc(&c, h->nW * h->elt);
+        e = dev_malloc(&a, h->nU * h->elt);
+        if (e == cudaSuccess) e = dev_malloc(&bb, h->nV * h->elt);
+        if (e == cudaSuccess) e = dev_malloc(&c, h->nW * h->elt);
         if (e != cudaSuccess) {
-            cudaFree(a); cudaFree(bb); cudaFree(c);
+            dev_free(a); dev_free(bb); dev_free(c);
             return cuda_check(e, "mr_cfl_dt: temporary dense faces");
         }
         int rc = refine_into(h, a, bb, c, st);
-        if (rc) { cudaFree(a); cudaFree(bb); cudaFree(c); return rc; }
+        if (rc) { dev_free(a); dev_free(bb); dev_free(c); return rc; }
         us = a; vs = bb; ws = c;
         tmp = true;
     }
@@ -1074,7 +1088,7 @@ int mr_cfl_dt(mr_handle h, double cfl, double* dt_out, mr_stream stream)
                 : launch_cfl<float>(h->g32, (const float*)us, (const float*)vs, (const float*)ws, b.red, h->red_blocks, st);
     std::vector<double> p;
     int rc = e != cudaSuccess ? cuda_check(e, "mr_cfl_dt: launch") : reduce_partials(h, 1, p, st);
-    if (tmp) { cudaFree((void*)us); cudaFree((void*)vs); cudaFree((void*)ws); }
+    if (tmp) { dev_free((void*)us); dev_free((void*)vs); dev_free((void*)ws); }
     if (rc) return rc;
     if (h->cfg.velocity_mode != MR_VEL_STORED && fused_take_error(st) == MR_ERR_TIMEOUT)
         return set_error(MR_ERR_TIMEOUT, "mr_cfl_dt: a fused kernel gave up a bounded wait");
@@ -1162,7 +1176,7 @@ void adj_free(mr_handle h)
     auto& a = h->adj;
     void* ptrs[] = {a.cp, a.seg, a.mu, a.face, a.scr, a.out, a.face32};
     for (void* p : ptrs)
-        if (p) cudaFree(p);
+        if (p) dev_free(p);
     a.cp = a.seg = a.mu = nullptr;
     a.face = a.scr = a.out = nullptr;
     a.face32 = nullptr;
@@ -1190,15 +1204,15 @@ int mr_adjoint_forward(mr_handle h, int64_t nsteps, int32_t ck, const double* wn
     if (a.cp && (a.cp_pairs < cpairs || a.ck < ck)) adj_free(h);
     cudaError_t e = cudaSuccess;
     if (!a.cp) {
-        e = cudaMalloc(&a.cp, cpairs * 2 * fb);
-        if (e == cudaSuccess) e = cudaMalloc(&a.seg, ((size_t)ck + 1) * fb);
-        if (e == cudaSuccess) e = cudaMalloc(&a.mu, 3 * fb);
-        if (e == cudaSuccess) e = cudaMalloc((void**)&a.face, (h->nU + h->nV + h->nW) * sizeof(double));
+        e = dev_malloc(&a.cp, cpairs * 2 * fb);
+        if (e == cudaSuccess) e = dev_malloc(&a.seg, ((size_t)ck + 1) * fb);
+        if (e == cudaSuccess) e = dev_malloc(&a.mu, 3 * fb);
+        if (e == cudaSuccess) e = dev_malloc((void**)&a.face, (h->nU + h->nV + h->nW) * sizeof(double));
         const size_t nscr = (size_t)(h->Nz + 1) * h->cfg.ny * h->cfg.nx + (size_t)h->Nz * (h->Ny + h->w) * h->cfg.nx;
-        if (e == cudaSuccess) e = cudaMalloc((void**)&a.scr, nscr * sizeof(double));
-        if (e == cudaSuccess) e = cudaMalloc((void**)&a.out, (h->ncell + h->ncU + h->ncV + h->ncW) * sizeof(double));
+        if (e == cudaSuccess) e = dev_malloc((void**)&a.scr, nscr * sizeof(double));
+        if (e == cudaSuccess) e = dev_malloc((void**)&a.out, (h->ncell + h->ncU + h->ncV + h->ncW) * sizeof(double));
         if (e == cudaSuccess && h->cfg.precision == MR_F32) {
-            e = cudaMalloc((void**)&a.face32, (h->nU + h->nV + h->nW) * sizeof(float));
+            e = dev_malloc((void**)&a.face32, (h->nU + h->nV + h->nW) * sizeof(float));
             if (e == cudaSuccess) e = cudaMemset(a.face32, 0, (h->nU + h->nV + h->nW) * sizeof(float));
         }
         if (e != cudaSuccess) {
@@ -1362,7 +1376,7 @@ int mr_upscale_scalar(mr_handle h, double* Tc, mr_stream stream)
     const size_t nc = (size_t)h->cfg.nx * h->cfg.ny * h->cfg.nz;
     const size_t need = nc + (size_t)h->Nz + 1 + (size_t)h->Nz;
     if (!b.diag) {
-        cudaError_t e = cudaMalloc((void**)&b.diag, need * sizeof(double));
+        cudaError_t e = dev_malloc((void**)&b.diag, need * sizeof(double));
         if (e != cudaSuccess) return cuda_check(e, "mr_upscale_scalar: buffer");
     }
     const bool dev = is_device_pointer(Tc);
@@ -1384,7 +1398,7 @@ int mr_scalar_profiles(mr_handle h, double* nu_z, double* nu_T, mr_stream stream
     DeviceBuffers& b = h->buf;
     const size_t nc = (size_t)h->cfg.nx * h->cfg.ny * h->cfg.nz;
     if (!b.diag) {
-        cudaError_t e = cudaMalloc((void**)&b.diag, (nc + 2 * (size_t)h->Nz + 1) * sizeof(double));
+        cudaError_t e = dev_malloc((void**)&b.diag, (nc + 2 * (size_t)h->Nz + 1) * sizeof(double));
         if (e != cudaSuccess) return cuda_check(e, "mr_scalar_profiles: buffer");
     }
     double* dnu = b.diag + nc;
@@ -1395,11 +1409,11 @@ int mr_scalar_profiles(mr_handle h, double* nu_z, double* nu_T, mr_stream stream
     const void* ws = b.Ws;
     void *tu = nullptr, *tv = nullptr, *tw = nullptr;
     if (h->cfg.velocity_mode != MR_VEL_STORED) {
-        e = cudaMalloc(&tu, h->nU * h->elt);
-        if (e == cudaSuccess) e = cudaMalloc(&tv, h->nV * h->elt);
-        if (e == cudaSuccess) e = cudaMalloc(&tw, h->nW * h->elt);
+        e = dev_malloc(&tu, h->nU * h->elt);
+        if (e == cudaSuccess) e = dev_malloc(&tv, h->nV * h->elt);
+        if (e == cudaSuccess) e = dev_malloc(&tw, h->nW * h->elt);
         int rc = e != cudaSuccess ? cuda_check(e, "mr_scalar_profiles: temporary faces") : refine_into(h, tu, tv, tw, st);
-        if (rc) { cudaFree(tu); cudaFree(tv); cudaFree(tw); return rc; }
+        if (rc) { dev_free(tu); dev_free(tv); dev_free(tw); return rc; }
         ws = tw;
     }
     const double zb = h->zc[0] - h->zf[0], zt = h->zf[h->Nz] - h->zc[h->Nz - 1];
@@ -1410,7 +1424,7 @@ int mr_scalar_profiles(mr_handle h, double* nu_z, double* nu_T, mr_stream stream
                                        dnu, b.red, h->red_blocks, st);
     std::vector<double> p;
     int rc = e != cudaSuccess ? cuda_check(e, "mr_scalar_profiles: launch") : reduce_partials(h, 1, p, st);
-    if (tu) { cudaFree(tu); cudaFree(tv); cudaFree(tw); }
+    if (tu) { dev_free(tu); dev_free(tv); dev_free(tw); }
     if (rc) return rc;
     if (nu_T) {
         double s = 0.0, vt = 0.0;

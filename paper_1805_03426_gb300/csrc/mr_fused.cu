@@ -91,6 +91,8 @@ struct FXArgs {
     int* err;
     unsigned long long* divmax;
     float rx[4][3];      // R_x rows of the 4 cells of a segment (uniform periodic x)
+    unsigned long long wait_ns;   // time limit of every bounded wait
+    int stop_ring;       // test hook: the producer of CTA (0,0,0) issues no ring from this one on (-1: none)
 };
 
 __device__ __forceinline__ int wrapi(int i, int n) { return i < 0 ? i + n : (i >= n ? i - n : i); }
@@ -289,9 +291,11 @@ k_fused(const __grid_constant__ CUtensorMap tmn, const __grid_constant__ CUtenso
     // ---------------------------------------------------------------- producer warp
     if (warp == NW) {
         if (lane != 0) return;
+        const bool stopper = (A.stop_ring >= 0 && blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0);
         for (int r = 0; r < nrings; ++r) {
             const int s = r % NB;
-            if (r >= NB && !mbar_wait(&empty[s], ((r / NB) - 1) & 1)) {
+            if (stopper && r == A.stop_ring) break;  // every ring issued so far is waited for by the consumers
+            if (r >= NB && !mbar_wait(&empty[s], ((r / NB) - 1) & 1, A.wait_ns)) {
                 atomicExch(A.err, MR_ERR_TIMEOUT);   // consumers then time out on full[]
                 break;
             }
@@ -338,7 +342,7 @@ k_fused(const __grid_constant__ CUtensorMap tmn, const __grid_constant__ CUtenso
     // rings 0 and 1 (planes k0-1, k0) before the layer loop; then layer k waits
     // for the ring of plane k+1 only
     for (int r = 0; r < 2; ++r)
-        if (!fail && !mbar_wait(&full[r], 0)) fail = true;
+        if (!fail && !mbar_wait(&full[r], 0, A.wait_ns)) fail = true;
     // one layer; sb, sc, st: the ring slots of planes k-1, k, k+1, tpar: the
     // parity of the ring of plane k+1
     auto layer = [&](const int k, const int sb, const int sc, const int st, const int tpar) {
@@ -349,7 +353,7 @@ k_fused(const __grid_constant__ CUtensorMap tmn, const __grid_constant__ CUtenso
             slab_prep<M>(A, sm, K, I0, J0, j0, tid);
         }
         // the ring of plane k+1 and of this layer's constants
-        if (!fail && !mbar_wait(&full[st], tpar)) fail = true;
+        if (!fail && !mbar_wait(&full[st], tpar, A.wait_ns)) fail = true;
         if (!fail) {
             const float* lcp = sm + st * L::slot + L::oLC;
             const float2 c0 = *reinterpret_cast<const float2*>(lcp);
@@ -599,8 +603,9 @@ cudaError_t launch_fx(const Grid<float>& g, const float* U, const float* V, cons
     int kcs = (g.nz + chunks - 1) / chunks;
     kcs = max(1, min(kcs, 96 / M));
     chunks = (g.nz + kcs - 1) / kcs;
-    FXArgs A{g, U, V, W, T, Tm1, Tp1, (float)c.a, (float)c.b, (float)c.gdt, kcs, err, divmax, {}};
+    FXArgs A{g, U, V, W, T, Tm1, Tp1, (float)c.a, (float)c.b, (float)c.gdt, kcs, err, divmax, {}, ptx::kWaitNs, -1};
     memcpy(A.rx, rx12, sizeof A.rx);
+    if (KIND == 0) take_wait_injection(&A.stop_ring, &A.wait_ns);
     dim3 grid(chunks, g.Nx / kTX, g.Ny / kTY);
     k_fused<M, KIND, LF><<<grid, kThreadsAll, L::bytes, st>>>(mn, mm, mlc, A);
     return cudaGetLastError();
@@ -691,8 +696,8 @@ int* fused_error_flag()
     if (!slot) return nullptr;
     if (!*slot) {
         int* p = nullptr;
-        if (cudaMalloc(&p, sizeof(int)) != cudaSuccess) return nullptr;
-        if (cudaMemset(p, 0, sizeof(int)) != cudaSuccess) { cudaFree(p); return nullptr; }
+        if (dev_malloc(&p, sizeof(int)) != cudaSuccess) return nullptr;
+        if (cudaMemset(p, 0, sizeof(int)) != cudaSuccess) { dev_free(p); return nullptr; }
         *slot = p;
     }
     return *slot;

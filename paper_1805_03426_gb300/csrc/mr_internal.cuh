@@ -117,6 +117,10 @@ struct mr_handle_s {
     int64_t step = 0;        // steps taken since mr_set_scalar
     int ip = 0, ic = 1;      // indices of T^{n-1}, T^n in buf.T
     bool have_velocity = false, have_scalar = false;
+    // maximum divergence of the current refined velocity, computed by the
+    // first mr_scalar_stats after the velocity changed
+    bool maxdiv_valid = false;
+    double maxdiv = 0.0;
     // host FP64 grid (Section 3.1) and R matrices (Section 3.2)
     std::vector<double> zf, zc, dz, Rx, Ry, Rz;
     std::vector<double> f4x, f4y, f4z;   // fourth-order face weights (zeros at face_order 2)
@@ -231,5 +235,17 @@ cudaError_t launch_adj_direct(const Grid<P>& g, const P* T, double s_nu_bottom, 
 template <typename P>
 cudaError_t launch_times_volume(const Grid<P>& g, const P* mu, int dst_dtype, void* out, cudaStream_t st);
 int fused_take_error(cudaStream_t st);   // MR_ERR_TIMEOUT if a fused kernel gave up a wait
+// Test hook (mr_debug_inject_wait_timeout): if armed, hand the next TMA step
+// launch its stop ring and wait limit, and disarm; else leave both unchanged.
+void take_wait_injection(int* stop_ring, unsigned long long* wait_ns);
+// Device allocations of the library, counted so that a test can cap them
+// (mr_debug_alloc_cap) and check that a failed call leaks nothing.
+cudaError_t dev_malloc(void** p, size_t bytes);
+template <typename T>
+cudaError_t dev_malloc(T** p, size_t bytes)
+{
+    return dev_malloc(reinterpret_cast<void**>(p), bytes);
+}
+cudaError_t dev_free(void* p);
 
 }  // namespace mr

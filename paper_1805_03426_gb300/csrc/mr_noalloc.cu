@@ -20,6 +20,7 @@ namespace mr {
 namespace {
 
 constexpr int kMaxDevices = 64;
+constexpr double kMinLayer = 1e-12;   // narrowest dense z-layer accepted (domain height 1)
 std::mutex g_addr_mutex;
 void* g_addr[kMaxDevices] = {nullptr};
 
@@ -152,6 +153,21 @@ extern "C" int mr_refine_velocity_noalloc(const mr_config* c, const double* U, c
     }
     if (!(c->lx > 0) || !(c->ly > 0) || !(c->stretch_gamma >= 0) || c->stretch_gamma > 20)
         return set_error(MR_ERR_ARG, "mr_refine_velocity_noalloc: bad extents or stretching");
+    // the narrowest dense z-layers of a tanh-clustered grid are the two at the
+    // plates: a clustering that collapses them (tanh saturating in double
+    // precision) would make the R matrices and the layer balance divide by zero
+    {
+        const int Nzd = c->nz * c->mz;
+        const double gam = c->stretch_gamma;
+        auto zface = [&](int i) {
+            if (gam <= 0.0) return (double)i / (double)Nzd;
+            return 0.5 * (1.0 + tanh(gam * (2.0 * ((double)i / (double)Nzd) - 1.0)) / tanh(gam));
+        };
+        const double lo = zface(1) - 0.0, hi = 1.0 - zface(Nzd - 1);
+        if (!(lo > kMinLayer) || !(hi > kMinLayer))
+            return set_error(MR_ERR_ARG, "mr_refine_velocity_noalloc: stretching collapses the dense z-layers at the "
+                                         "plates (width <= 1e-12)");
+    }
     const void* ptrs[6] = {U, V, W, Us, Vs, Ws};
     for (const void* p : ptrs)
         if (!is_device_pointer(p)) return set_error(MR_ERR_ARG, "mr_refine_velocity_noalloc: pointers must be device memory");

@@ -10,7 +10,7 @@ namespace mr {
 namespace ptx {
 
 constexpr long kWaitLimit = 1L << 26;                  // bounded mbarrier wait: iterations ...
-constexpr unsigned long long kWaitNs = 1000000000ull;  // ... and wall time (1 s)
+constexpr unsigned long long kWaitNs = 1000000000ull;  // ... and wall time (1 s, unless a launch gives less)
 
 __device__ __forceinline__ uint32_t sa(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -64,14 +64,14 @@ __device__ __forceinline__ unsigned long long global_ns()
     asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
     return t;
 }
-// Bounded wait (iteration count and wall time); true on success.
-__device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity)
+// Bounded wait (iteration count and wall time limit_ns); true on success.
+__device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity, unsigned long long limit_ns = kWaitNs)
 {
     if (mbar_test(b, parity)) return true;
     const unsigned long long t0 = global_ns();
     for (long it = 0; it < kWaitLimit; ++it) {
         if (mbar_test(b, parity)) return true;
-        if ((it & 255) == 0 && global_ns() - t0 > kWaitNs) break;
+        if ((it & 15) == 0 && global_ns() - t0 > limit_ns) break;
     }
     return false;
 }

@@ -99,6 +99,8 @@ struct XArgs {
                          // same for every thread: kept in the constant bank)
     float alpha;         // MT: weight of the second velocity set, i / M_t (Section 3.4)
     float w4x[4], w4y[4];  // O4: twice the fourth-order face weights of cells f-2..f+1 (uniform, periodic)
+    unsigned long long wait_ns;   // time limit of every bounded wait
+    int stop_ring;       // test hook: the producer of CTA (0,0,0) issues no ring from this one on (-1: none)
 };
 
 // R_x split of three coarse values by one row of R (rows sum to one):
@@ -173,9 +175,11 @@ k_xfused(const __grid_constant__ CUtensorMap tmn, const __grid_constant__ CUtens
     // ---------------------------------------------------------------- producer warp
     if (warp == NW) {
         if (lane != 0) return;
+        const bool stopper = (A.stop_ring >= 0 && blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0);
         for (int r = 0; r < nrings; ++r) {
             const int s = r % NB;
-            if (r >= NB && !mbar_wait(&empty[s], ((r / NB) - 1) & 1)) {
+            if (stopper && r == A.stop_ring) break;  // every ring issued so far is waited for by the consumers
+            if (r >= NB && !mbar_wait(&empty[s], ((r / NB) - 1) & 1, A.wait_ns)) {
                 atomicExch(A.err, MR_ERR_TIMEOUT);   // consumers then time out on full[]
                 break;
             }
@@ -232,7 +236,7 @@ k_xfused(const __grid_constant__ CUtensorMap tmn, const __grid_constant__ CUtens
     // plane k+OFF, in slot st (O4: s2) with parity tpar (2 OFF < NB)
 #pragma unroll
     for (int r = 0; r < 2 * OFF; ++r)
-        if (!fail && !mbar_wait(&full[r], 0)) fail = true;
+        if (!fail && !mbar_wait(&full[r], 0, A.wait_ns)) fail = true;
     const size_t plane = (size_t)g.Nx * g.Ny;
     float* outp = A.Tp1 + (size_t)k0 * plane + (size_t)(j0 + jl) * g.Nx + i0 + il0;
     const int o = (jl + 1) * kBX + il0 + 4;          // this segment's first cell in a plane box
@@ -245,7 +249,7 @@ k_xfused(const __grid_constant__ CUtensorMap tmn, const __grid_constant__ CUtens
     auto layer = [&](const int k, const int sm2, const int sb, const int sc, const int st, const int s2,
                      const int tpar) {
         // the ring of plane k+1 and of this layer's bundle (O4: of plane k+2)
-        if (!fail && !mbar_wait(&full[O4 ? s2 : st], tpar)) fail = true;
+        if (!fail && !mbar_wait(&full[O4 ? s2 : st], tpar, A.wait_ns)) fail = true;
         if (!fail) {
             const float* bun = sm + st * L::slot;
             // layer constants (from the bundle, see xfused_layer_constants)
@@ -836,16 +840,6 @@ bool cached_map3(CUtensorMap* out, const float* base, int d0, int d1, int d2, in
     return true;
 }
 
-int kcl_override()
-{
-    static int v = -1;
-    if (v < 0) {
-        const char* e = getenv("MR_XFUSED_KC");
-        v = e ? atoi(e) : 0;
-    }
-    return v;
-}
-
 // Velocity intermediates of one coarse time level.
 struct XSet {
     const float *wy, *uo, *vr;
@@ -880,20 +874,19 @@ cudaError_t launch_xt(const Grid<float>& g, XSet v0, XSet v1, float alpha, int n
         !cached_map3(&mlc, lc, lcw, g.Nz, 1, L::LCW, 1, 1))
         return cudaErrorInvalidValue;
     const int tiles = (g.Nx / kTX) * (g.Ny / TY);
-    int kcl = kcl_override();
-    if (kcl <= 0) {
-        // ~20 waves of resident CTAs, but no chunk longer than 96 layers: on
-        // large grids long chunks leave the resident CTAs far apart in z
-        // (measured on 1536 x 1536 x 1024: 512 layers 8.8 ms, 64-128 layers
-        // 7.0 ms, 96 layers 6.8 ms per step; on 512 x 512 x 384, 64x8 tiles:
-        // 8 layers 0.300 ms, 12: 0.287, 16: 0.284, 26: 0.286, 48: 0.305)
-        const int want = 152 * L::CTAS * 20;
-        int chunks = (want + tiles - 1) / tiles;
-        chunks = max(1, min(chunks, g.Nz / 4));
-        kcl = min((g.Nz + chunks - 1) / chunks, 96);
-    }
+    // ~20 waves of resident CTAs, but no chunk longer than 96 layers: on large
+    // grids long chunks leave the resident CTAs far apart in z (measured on
+    // 1536 x 1536 x 1024: 512 layers 8.8 ms, 64-128 layers 7.0 ms, 96 layers
+    // 6.8 ms per step; on 512 x 512 x 384, 64x8 tiles: 8 layers 0.300 ms,
+    // 12: 0.287, 16: 0.284, 26: 0.286, 48: 0.305)
+    const int want = 152 * L::CTAS * 20;
+    int nch = (want + tiles - 1) / tiles;
+    nch = max(1, min(nch, g.Nz / 4));
+    const int kcl = min((g.Nz + nch - 1) / nch, 96);
     const int chunks = (g.Nz + kcl - 1) / kcl;
-    XArgs A{g, T, Tm1, Tp1, lc, (float)c.a, (float)c.b, (float)c.gdt, kcl, err, divmax, {}, alpha, {}, {}};
+    XArgs A{g, T, Tm1, Tp1, lc, (float)c.a, (float)c.b, (float)c.gdt, kcl, err, divmax, {}, alpha, {}, {},
+            ptx::kWaitNs, -1};
+    if (KIND == 0) take_wait_injection(&A.stop_ring, &A.wait_ns);
     memcpy(A.rx, rx12, sizeof A.rx);
     if (O4) {
         memcpy(A.w4x, w4, sizeof A.w4x);
@@ -908,15 +901,8 @@ cudaError_t launch_xt(const Grid<float>& g, XSet v0, XSet v1, float alpha, int n
 // ~8 waves of them in chunks of 96 layers, else 64x8 tiles (four CTAs per SM,
 // so that a small grid still overlaps the chunks' start-up; 512 x 512 x 384:
 // 0.315 -> 0.306 ms per step, while 1536 x 1536 x 1024 prefers 64x16).
-// MR_XFUSED_TY in the environment forces 8 or 16 (used for tuning).
 int tile_rows(const Grid<float>& g)
 {
-    static int forced = -1;
-    if (forced < 0) {
-        const char* e = getenv("MR_XFUSED_TY");
-        forced = e ? atoi(e) : 0;
-    }
-    if (forced == 8 || forced == 16) return forced;
     const long long tiles16 = (long long)(g.Nx / kTX) * (g.Ny / 16), chunks96 = (g.Nz + 95) / 96;
     return tiles16 * chunks96 >= 152LL * 2 * 8 ? 16 : 8;
 }

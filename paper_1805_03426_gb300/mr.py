@@ -76,6 +76,9 @@ _SIGS = {
     "mr_upscale_scalar": (ctypes.c_int, [_VP, _VP, _VP]),
     "mr_scalar_profiles": (ctypes.c_int, [_VP, _VP, ctypes.POINTER(_D), _VP]),
     "mr_refine_velocity_noalloc": (ctypes.c_int, [ctypes.POINTER(mr_config), _VP, _VP, _VP, _VP, _VP, _VP, _VP]),
+    "mr_fp64_fma_rate": (ctypes.c_int, [ctypes.POINTER(_D), _VP]),
+    "mr_debug_inject_wait_timeout": (ctypes.c_int, [_I32, _D]),
+    "mr_debug_alloc_cap": (ctypes.c_int, [_I64, ctypes.POINTER(_I64)]),
 }
 
 
@@ -369,3 +372,23 @@ def mr_scalar_profiles(h: Handle, stream=None):
     nu_T = _D()
     _check(lib().mr_scalar_profiles(h.ptr, nu_z.ctypes.data, ctypes.byref(nu_T), _stream(stream)))
     return nu_z, nu_T.value
+
+
+def mr_fp64_fma_rate(stream=None) -> float:
+    """Measured FP64 FMA rate of the current device, TFLOP/s."""
+    r = _D()
+    _check(lib().mr_fp64_fma_rate(ctypes.byref(r), _stream(stream)))
+    return r.value
+
+
+def mr_debug_inject_wait_timeout(stop_ring: int, wait_seconds: float):
+    """Test hook: the next TMA step launch times out in its first CTA."""
+    _check(lib().mr_debug_inject_wait_timeout(stop_ring, wait_seconds))
+
+
+def mr_debug_alloc_cap(cap_bytes: int = -2) -> int:
+    """Test hook: cap the library's device memory (-1: none, -2: unchanged);
+    returns the bytes it holds."""
+    live = _I64()
+    _check(lib().mr_debug_alloc_cap(cap_bytes, ctypes.byref(live)))
+    return live.value

@@ -56,6 +56,7 @@ def test_config_struct_layout_matches(mr):
     dict(bc_plates=3),
     dict(diffz_implicit=2),
     dict(stretch_gamma=-1.0),
+    dict(stretch_gamma=20.0, nz=96, mz=4),   # tanh saturates: zero-width layers at the plates
     dict(struct_size=12),
 ])
 def test_invalid_config_rejected_on_host(mr, bad):
@@ -72,3 +73,36 @@ def test_null_arguments_rejected(mr):
     assert L.mr_scalar_step(None, 1, None) == mr.MR_ERR_ARG
     assert L.mr_set_dt(None, 1.0) == mr.MR_ERR_ARG
     L.mr_destroy(None)
+
+
+def test_noalloc_rejects_collapsed_plate_layers_on_host(mr):
+    """The allocation-free refinement refuses a clustering that collapses the
+    plate layers before any CUDA call (host arrays never reach the GPU)."""
+    import numpy as np
+    c = mr.mr_config_default(nx=8, ny=6, nz=96, mx=2, my=2, mz=4, stretch_gamma=20.0)
+    Nx, Ny, Nz = 16, 12, 384
+    a = [np.zeros(n) for n in (96 * 6 * 8, 96 * 6 * 8, 97 * 6 * 8, Nz * Ny * Nx, Nz * Ny * Nx, (Nz + 1) * Ny * Nx)]
+    with pytest.raises(mr.MRError) as e:
+        mr.mr_refine_velocity_noalloc(c, *a)
+    assert e.value.code == mr.MR_ERR_ARG and "collapses" in str(e.value)
+
+
+def test_allocation_refusal_gives_oom_and_leaks_nothing(mr):
+    """A capped device allocation fails like an exhausted device: mr_create
+    returns MR_ERR_OOM before any CUDA work and holds nothing afterwards."""
+    live0 = mr.mr_debug_alloc_cap(-2)
+    mr.mr_debug_alloc_cap(live0)          # no new byte allowed
+    try:
+        with pytest.raises(mr.MRError) as e:
+            mr.mr_create(mr.mr_config_default(nx=8, ny=8, nz=8))
+        assert e.value.code == mr.MR_ERR_OOM
+        assert mr.mr_debug_alloc_cap(-2) == live0
+    finally:
+        mr.mr_debug_alloc_cap(-1)
+
+
+def test_wait_injection_arguments_checked(mr):
+    for ring, secs in ((-1, 0.01), (2, 0.0), (2, 2.0)):
+        with pytest.raises(mr.MRError) as e:
+            mr.mr_debug_inject_wait_timeout(ring, secs)
+        assert e.value.code == mr.MR_ERR_ARG

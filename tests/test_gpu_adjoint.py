@@ -68,7 +68,9 @@ def test_adjoint_fp64_matches_oracle(mr, name, ck):
     Lr, gr = _oracle_grad(p, S, wnu, wvar)
     assert abs(L - Lr) <= 1e-12 * abs(Lr)
     for a, b in zip(g, gr):
-        assert np.abs(a - b).max() <= 1e-11 * np.abs(b).max()
+        err = np.abs(a - b).max() / np.abs(b).max()
+        print(f"adjoint FP64 {name} ck={ck}: relative gradient error {err:.2e}")
+        assert err <= 1e-12
 
 
 def test_adjoint_fp32_close_to_oracle(mr):
@@ -141,7 +143,9 @@ def test_adjoint_config_128x128x96_200_steps(mr):
     Lr, gr = _oracle_grad(p, S, wnu, None)
     assert abs(L - Lr) <= 1e-12 * abs(Lr)
     for a, b in zip(g, gr):
-        assert np.abs(a - b).max() <= 1e-10 * np.abs(b).max()
+        err = np.abs(a - b).max() / np.abs(b).max()
+        print(f"adjoint FP64 128x128x96, 200 steps: relative gradient error {err:.2e}")
+        assert err <= 1e-12
 
 
 def test_differentiation_form_16_directions(mr):

@@ -71,8 +71,8 @@ def test_stored_face4_matches_oracle(mr, name, precision):
     if precision == "f64":
         nu_z, nu_T = mr.mr_scalar_profiles(h)
         nz_ref, nT_ref = O.nusselt_profile(p.cfg, T_ref, vel[2])
-        assert np.abs(nu_z - nz_ref).max() <= 1e-10 * max(1.0, np.abs(nz_ref).max())
-        assert abs(nu_T - nT_ref) <= 1e-10 * abs(nT_ref)
+        assert np.abs(nu_z - nz_ref).max() <= F64_TOL * max(1.0, np.abs(nz_ref).max())
+        assert abs(nu_T - nT_ref) <= F64_TOL * abs(nT_ref)
 
 
 def test_face4_refused_configurations(mr):

@@ -58,6 +58,6 @@ def test_precision_form_1000_steps_every_100(mr):
                 worst["nu32"] = max(worst["nu32"], nu)
             else:
                 assert err <= 1e-12 * scale, (100 * (block + 1), err)
-                assert nu <= 1e-11, (100 * (block + 1), nu)
+                assert nu <= 1e-12, (100 * (block + 1), nu)
                 worst["f64"] = max(worst["f64"], err / scale)
     print("precision form, worst over 1000 steps:", worst)
