@@ -156,7 +156,7 @@ def _dist():
 
 
 def max_over_ranks(t, device):
-    """The slowest rank's time: the job ends when every replica has."""
+    """The slowest rank's time: the job ends when every rank has."""
     import torch
     import torch.distributed as dist
     if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
@@ -167,7 +167,7 @@ def max_over_ranks(t, device):
 
 
 def job_rate(cells, steps, world, t):
-    """Whole-job rate: every replica advances its own grid (weak scaling)."""
+    """Whole-job rate: every rank advances a slab of `cells` cells (weak scaling)."""
     return world * cells * steps / t / 1e9
 
 
@@ -208,15 +208,93 @@ def _time_steps(torch, mr, h, steps, warmup, stream):
     return e0.elapsed_time(e1) / 1e3
 
 
-def run_mr(args):
+def run_slabs(args):
+    """N GPUs: the y-slab decomposition (paper_1805_03426_gb300.slabs), weak
+    scaling: N slabs of the workload's coarse rows stacked in y into one
+    periodic domain of ny * N coarse rows (ly = N), one slab per rank, the
+    fused FP32 step with the NCCL halo exchange of one dense row each side
+    after every step inside the timed region."""
     import torch
     import torch.distributed as dist
     import paper_1805_03426_gb300.mr as mr
+    from paper_1805_03426_gb300 import slabs, synth
 
     world, rank, local = _dist()
     torch.cuda.set_device(local)
+    dist.init_process_group("nccl")
+    w = WORKLOADS[args.workload]
+    Nx, Ny, Nz = w["nx"] * w["m"], w["ny"] * w["m"], w["nz"] * w["m"]
+    cells = Nx * Ny * Nz                      # per rank
+    nyg = w["ny"] * world
+    j0, rows = slabs.partition(nyg, w["m"], world)[rank]
+    c = mr.mr_config_default(nx=w["nx"], ny=nyg, nz=w["nz"], mx=w["m"], my=w["m"], mz=w["m"], ly=float(world),
+                             stretch_gamma=w["gamma"], ra=w["ra"], pr_or_sc=w["pr"], dt=1e-3, precision=mr.MR_F32,
+                             velocity_mode=mr.MR_VEL_FUSED, slab_j0=j0, slab_ny=rows)
+    h = mr.mr_create(c)
+    _, zf = mr.mr_grid(h)
+    Xf = np.arange(w["nx"] + 1) / w["nx"]
+    Yf = np.arange(nyg + 1) / w["ny"]
+    U, V, W = synth.coarse_velocity(SEED, Xf, Yf, zf[::w["m"]].copy(), 1.0, float(world), rms=w["rms"])
+    zc = 0.5 * (zf[1:] + zf[:-1])
+    T0 = torch.from_numpy(synth.initial_scalar(SEED + 7 * rank, zc, rows * w["m"], Nx)).cuda()
+    mr.mr_refine_velocity(h, *(torch.from_numpy(a).cuda() for a in (U, V, W)))
+    # the whole domain's CFL step: the largest rate over the slabs
+    rate = torch.tensor([0.3 / mr.mr_cfl_dt(h, 0.3)], dtype=torch.float64, device="cuda")
+    dist.all_reduce(rate, op=dist.ReduceOp.MAX)
+    dt = 0.3 / float(rate.item())
+    mr.mr_set_dt(h, dt)
+    stepper = slabs.SlabStepper(slabs.HandleEngine(mr, h), slabs.HaloExchange(rank, world), (Nz, Nx),
+                                torch.float32, "cuda")
+    stepper.set_scalar(T0)
+    for _ in range(args.warmup):
+        stepper.step()
+    torch.cuda.synchronize()
+    dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(args.steps):
+            stepper.step()
+        e1.record()
+        torch.cuda.synchronize()
+        t = e0.elapsed_time(e1) / 1e3
+    dist.barrier()
+    t = max_over_ranks(t, "cuda")
+    value = job_rate(cells, args.steps, world, t)
+    vol, area = slabs.slab_geometry(h.cfg, zf)
+    part = slabs.slab_stats(mr.mr_scalar_stats(h, allow_nonfinite=True), vol, area)
+    parts = [None] * world
+    dist.all_gather_object(parts, part)
+    st = slabs.combine_stats(parts)
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": round(value, 3), "unit": "Gcell-updates/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(t / args.steps * 1e3, 4),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": args.workload, "description": f"{world} y-slabs of: " + w["label"],
+                       "dense_cells": cells * world, "velocity_mode": "fused", "step": STEP_LABEL["fused"] +
+                       "; then the halo exchange of one dense row each side with the neighbouring slabs (NCCL)",
+                       "cfl": 0.3, "dt": float("%.5g" % dt), "parallelism": f"y-slabs{world}",
+                       "l2": "inputs larger than L2 (3 scalar levels of %.0f MB per GPU)" % (cells * 4 / 2**20)},
+            "gpu_launches": args.steps, "clocks": clk.summary(),
+            "final_stats": {k: st[k] for k in ("nu_bot", "nu_top", "mean", "var")},
+        }
+        print(json.dumps(line), flush=True)
+    h.close()
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def run_mr(args):
+    """One GPU: the workload on the whole domain, then the figures beside it."""
+    import torch
+    import paper_1805_03426_gb300.mr as mr
+
+    world, rank, local = _dist()
     if world > 1:
-        dist.init_process_group("nccl")
+        return run_slabs(args)
+    torch.cuda.set_device(local)
     w = WORKLOADS[args.workload]
     Nx, Ny, Nz = w["nx"] * w["m"], w["ny"] * w["m"], w["nz"] * w["m"]
     cells = Nx * Ny * Nz
@@ -234,11 +312,8 @@ def run_mr(args):
     mr.mr_set_scalar(h, dT0, stream=stream)
     torch.cuda.synchronize()
 
-    if world > 1:
-        dist.barrier()
     with ClockSampler(local) as clk:
         t = _time_steps(torch, mr, h, args.steps, args.warmup, stream)
-    t = max_over_ranks(t, "cuda")
     value = job_rate(cells, args.steps, world, t)
     st = mr.mr_scalar_stats(h, stream=stream, allow_nonfinite=True)
 
@@ -416,9 +491,6 @@ def run_mr(args):
             "final_stats": {k: st[k] for k in ("nu_bot", "nu_top", "mean", "var")},
         }
         print(json.dumps(line), flush=True)
-    if world > 1:
-        dist.barrier()
-        dist.destroy_process_group()
 
 
 def bench_config(args, w, dt, world, mode):

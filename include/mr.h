@@ -99,6 +99,22 @@ typedef struct {
                                  supported by MR_VEL_STORED and MR_VEL_XFUSED,
                                  not by the adjoint; it needs >= 4 dense cells
                                  on periodic axes and >= 3 between walls.     */
+    int32_t slab_j0, slab_ny; /* y-slab decomposition over GPUs (the data
+                                 partition of the paper's parallel solver,
+                                 Section 2.4, in slabs of whole coarse rows):
+                                 slab_ny = 0 (default) gives the whole domain;
+                                 otherwise the handle owns coarse rows
+                                 slab_j0 .. slab_j0 + slab_ny - 1 of the
+                                 periodic domain of ny coarse rows (ly is the
+                                 whole domain's): its scalar arrays hold the
+                                 slab's slab_ny * my dense rows, the coarse
+                                 velocity it takes is the whole domain's, and
+                                 the dense rows just outside the slab come
+                                 from mr_set_halo_rows instead of the periodic
+                                 wrap.  MR_VEL_FUSED only; slab_ny * my % 16
+                                 == 0; one step per mr_scalar_step call; the
+                                 reductions cover the slab (the caller sums
+                                 over slabs).                                 */
 } mr_config;
 
 typedef struct {
@@ -255,6 +271,23 @@ int mr_adjoint_backward(mr_handle h, double gscale, void* gT0, int32_t gT0_dtype
  * calls on different devices do not interact. */
 int mr_refine_velocity_noalloc(const mr_config* cfg, const double* U, const double* V, const double* W,
                                double* Us, double* Vs, double* Ws, mr_stream stream);
+
+/* Halo exchange of a y-slab handle (mr_config.slab_ny > 0): the paper's
+ * parallel solver swaps ghost layers between subdomains every step (Section
+ * 2.4); here a slab needs one dense row of T^n and of T^{n-1} beyond each of
+ * its two y edges.  mr_get_boundary_rows copies the slab's first (south) and
+ * last (north) dense rows of T^n, each as [Nz][Nx] values in the handle's
+ * precision (host or device pointers, either may be NULL); they are the
+ * north halo of the southern neighbour and the south halo of the northern
+ * one.  mr_set_halo_rows gives T^n its halo rows: below (the row south of row
+ * 0, i.e. the southern neighbour's last row) and above (the row north of the
+ * last row, the northern neighbour's first), [Nz][Nx] each, copied in.  The
+ * halo rows of T^n become those of T^{n-1} at the next step, so after
+ * mr_set_scalar and after every step the caller exchanges and sets them once;
+ * mr_scalar_step returns MR_ERR_STATE if they are missing.  Asynchronous on
+ * stream.  MR_ERR_ARG on a whole-domain handle or NULL arguments. */
+int mr_get_boundary_rows(mr_handle h, void* south, void* north, mr_stream stream);
+int mr_set_halo_rows(mr_handle h, const void* below, const void* above, mr_stream stream);
 
 /* Measurement aid (no counterpart in the paper): the FP64 arithmetic rate of
  * the current device in TFLOP/s (an FMA counts two), from a kernel of

@@ -270,8 +270,9 @@ static int upload_metric(mr_handle_s* h, char* dst, const int* dwin, Grid<P>& g)
     cudaError_t e = cudaMemcpy(dst, host.data(), host.size() * sizeof(P), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) return cuda_check(e, "upload metric");
     const P* base = (const P*)dst;
-    g.nx = c.nx; g.ny = c.ny; g.nz = c.nz; g.mx = c.mx; g.my = c.my; g.mz = c.mz;
-    g.Nx = h->Nx; g.Ny = h->Ny; g.Nz = h->Nz; g.walls = h->w;
+    // the kernels see the rows the handle stores (a y-slab's, or the whole domain's)
+    g.nx = c.nx; g.ny = h->nys; g.nz = c.nz; g.mx = c.mx; g.my = c.my; g.mz = c.mz;
+    g.Nx = h->Nx; g.Ny = h->Nys; g.Nz = h->Nz; g.walls = h->w;
     g.ufx = h->Nx + h->w; g.vfy = h->Ny + h->w; g.cux = c.nx + h->w; g.cvy = c.ny + h->w;
     g.dirichlet = dir ? 1 : 0;
     g.dx = (P)dx; g.dy = (P)dy; g.DX = (P)(c.lx / c.nx); g.DY = (P)(c.ly / c.ny);
@@ -327,6 +328,17 @@ static int validate(const mr_config* c, std::string* why)
         if (c->velocity_mode == MR_VEL_FUSED) { *why = "MR_VEL_FUSED supports face_order 2 only"; return MR_ERR_ARG; }
     }
     if (c->velocity_mode != MR_VEL_STORED && !fused_supported(*c, why)) return MR_ERR_ARG;
+    if (c->slab_ny != 0) {
+        if (c->velocity_mode != MR_VEL_FUSED) { *why = "a y-slab handle needs MR_VEL_FUSED"; return MR_ERR_ARG; }
+        if (c->slab_ny < 0 || c->slab_j0 < 0 || c->slab_j0 + c->slab_ny > c->ny) {
+            *why = "y-slab rows out of range (0 <= slab_j0, slab_j0 + slab_ny <= ny)";
+            return MR_ERR_ARG;
+        }
+        if ((c->slab_ny * c->my) % 16) { *why = "a y-slab needs slab_ny * my % 16 == 0"; return MR_ERR_ARG; }
+    } else if (c->slab_j0 != 0) {
+        *why = "slab_j0 without slab_ny";
+        return MR_ERR_ARG;
+    }
     return MR_OK;
 }
 
@@ -383,7 +395,7 @@ void mr_destroy(mr_handle h)
         for (void* p : cptrs)
             if (p) dev_free(p);
     }
-    void* xptrs[] = {b.xwy, b.xuo, b.xvr, b.xlc, b.diag};
+    void* xptrs[] = {b.xwy, b.xuo, b.xvr, b.xlc, b.diag, b.cpad, b.fsc, n.cpad, b.halo};
     for (void* p : xptrs)
         if (p) dev_free(p);
     for (int q = 0; q < 2; ++q) {
@@ -418,7 +430,10 @@ int mr_create(const mr_config* cfg, mr_handle* out)
     const mr_config& c = h->cfg;
     h->w = c.bc_horizontal == MR_WALLS ? 1 : 0;
     h->Nx = c.nx * c.mx; h->Ny = c.ny * c.my; h->Nz = c.nz * c.mz;
-    h->ncell = (size_t)h->Nx * h->Ny * h->Nz;
+    h->slab = c.slab_ny > 0;
+    h->nys = h->slab ? c.slab_ny : c.ny;
+    h->Nys = h->nys * c.my;
+    h->ncell = (size_t)h->Nx * h->Nys * h->Nz;
     h->nU = (size_t)h->Nz * h->Ny * (h->Nx + h->w);
     h->nV = (size_t)h->Nz * (h->Ny + h->w) * h->Nx;
     h->nW = (size_t)(h->Nz + 1) * h->Ny * h->Nx;
@@ -501,6 +516,9 @@ int mr_create(const mr_config* cfg, mr_handle* out)
         alloc(&b.scrW, (size_t)(h->Nz + 1) * c.ny * c.nx * h->elt);
     } else if (c.velocity_mode == MR_VEL_FUSED) {
         alloc((void**)&b.xlc, (size_t)h->Nz * 32 * 4);   // layer constants of the fused step
+        alloc((void**)&b.fsc, (size_t)c.nz * 32 * 4);    // slab constants
+        alloc((void**)&b.cpad, fused_pad_floats(c.nx, h->nys, c.nz) * 4);
+        if (h->slab) alloc((void**)&b.halo, (size_t)6 * h->Nz * h->Nx * 4);
     }
     if (e != cudaSuccess) {
         int r = cuda_check(e, "mr_create: device allocation");
@@ -533,6 +551,11 @@ int mr_create(const mr_config* cfg, mr_handle* out)
         rc = cuda_check(cudaMemcpy(b.xlc, lc.data(), lc.size() * 4, cudaMemcpyHostToDevice), "mr_create: layer constants");
         // x is uniform and periodic: every coarse cell has the same R_x rows
         for (int q = 0; q < 12; ++q) b.xrx[q] = (float)h->Rx[(size_t)(q / 3) * 3 + q % 3];
+        for (int q = 0; q < 12 && (size_t)q < h->Ry.size(); ++q) b.xry[q] = (float)h->Ry[(size_t)(q / 3) * 3 + q % 3];
+    }
+    if (!rc && b.fsc) {
+        const std::vector<float> sc = fused_slab_constants(c.nz, c.mz, h->Rz.data(), h->dz.data());
+        rc = cuda_check(cudaMemcpy(b.fsc, sc.data(), sc.size() * 4, cudaMemcpyHostToDevice), "mr_create: slab constants");
     }
     if (rc) {
         mr_destroy(h);
@@ -545,7 +568,7 @@ int mr_create(const mr_config* cfg, mr_handle* out)
 int mr_grid(mr_handle h, int32_t* dims3, double* zf_host)
 {
     if (!h) return set_error(MR_ERR_ARG, "mr_grid: NULL handle");
-    if (dims3) { dims3[0] = h->Nx; dims3[1] = h->Ny; dims3[2] = h->Nz; }
+    if (dims3) { dims3[0] = h->Nx; dims3[1] = h->Nys; dims3[2] = h->Nz; }
     if (zf_host) memcpy(zf_host, h->zf.data(), h->zf.size() * sizeof(double));
     return MR_OK;
 }
@@ -670,6 +693,11 @@ static int derive_velocity(mr_handle h, bool convert, cudaStream_t st)
                                            (float*)b.scrW, b.xwy, b.xuo, b.xvr, b.nxg, st);
         if (e != cudaSuccess) return cuda_check(e, "split-x intermediates");
     }
+    if (h->cfg.velocity_mode == MR_VEL_FUSED) {
+        cudaError_t e = launch_fused_pad((const float*)b.Uc, (const float*)b.Vc, (const float*)b.Wc, b.cpad,
+                                         h->cfg.nx, h->cfg.ny, h->cfg.nz, h->slab ? h->cfg.slab_j0 : 0, h->nys, st);
+        if (e != cudaSuccess) return cuda_check(e, "padded coarse faces");
+    }
     if (h->cfg.velocity_mode == MR_VEL_STORED) return refine_into(h, b.Us, b.Vs, b.Ws, st);
     return MR_OK;
 }
@@ -701,22 +729,33 @@ static int one_step(mr_handle h, double alpha, cudaStream_t st)
                                    (const float*)Tm1,
                                    (const float*)b.T[h->ic], (float*)b.T[in], c, st);
     } else if (h->cfg.velocity_mode == MR_VEL_FUSED) {
-        const float *U = (const float*)b.Uc, *V = (const float*)b.Vc, *W = (const float*)b.Wc;
+        FusedInputs fin{b.cpad, {}, {}, 0, b.fsc, b.xlc, b.xrx, b.xry};
+        // the rows beyond the y edges of T^s and T^{s-1}
+        const int lm = h->step == 0 ? h->ic : h->ip;
+        if (h->slab) {
+            const size_t hp = (size_t)h->Nz * h->Nx;
+            fin.hs[0] = b.halo + (2 * h->ic) * hp;
+            fin.hn[0] = b.halo + (2 * h->ic + 1) * hp;
+            fin.hs[1] = b.halo + (2 * lm) * hp;
+            fin.hn[1] = b.halo + (2 * lm + 1) * hp;
+            fin.hstride = h->Nx;
+        } else {
+            const size_t row = (size_t)(h->Nys - 1) * h->Nx;
+            fin.hs[0] = (const float*)b.T[h->ic] + row;
+            fin.hn[0] = (const float*)b.T[h->ic];
+            fin.hs[1] = (const float*)b.T[lm] + row;
+            fin.hn[1] = (const float*)b.T[lm];
+            fin.hstride = (size_t)h->Nx * h->Nys;
+        }
         e = cudaSuccess;
         if (lerp) {
             // the refinement is linear: refining the interpolated coarse faces
-            // interpolates the refined ones
-            float* Lu = b.lerpc;
-            float* Lv = Lu + h->ncU;
-            float* Lw = Lv + h->ncV;
-            e = launch_lerp_f32(U, (const float*)nx.Uc, alpha, Lu, h->ncU, st);
-            if (e == cudaSuccess) e = launch_lerp_f32(V, (const float*)nx.Vc, alpha, Lv, h->ncV, st);
-            if (e == cudaSuccess) e = launch_lerp_f32(W, (const float*)nx.Wc, alpha, Lw, h->ncW, st);
-            U = Lu; V = Lv; W = Lw;
+            // interpolates the refined ones (the periodic images interpolate too)
+            e = launch_lerp_f32(b.cpad, nx.cpad, alpha, b.lerpc, fused_pad_floats(h->cfg.nx, h->nys, h->cfg.nz), st);
+            fin.pad = b.lerpc;
         }
         if (e == cudaSuccess)
-            e = launch_step_fused_f32(h->g32, U, V, W, b.xlc, b.xrx, (const float*)Tm1, (const float*)b.T[h->ic],
-                                       (float*)b.T[in], c, st);
+            e = launch_step_fused_f32(h->g32, fin, (const float*)Tm1, (const float*)b.T[h->ic], (float*)b.T[in], c, st);
     } else {
         const float* A[3] = {(const float*)b.Us, (const float*)b.Vs, (const float*)b.Ws};
         const float* B[3] = {(const float*)nx.Us, (const float*)nx.Vs, (const float*)nx.Ws};
@@ -729,6 +768,7 @@ static int one_step(mr_handle h, double alpha, cudaStream_t st)
     if (e != cudaSuccess) return cuda_check(e, "scalar step launch");
     h->ip = h->ic;
     h->ic = in;
+    h->halo_set[in] = false;       // a y-slab's new level has no halo rows yet
     ++h->step;
     return MR_OK;
 }
@@ -741,6 +781,7 @@ static void swap_levels(DeviceBuffers& b)
     std::swap(b.Uc, n.Uc); std::swap(b.Vc, n.Vc); std::swap(b.Wc, n.Wc);
     std::swap(b.Us, n.Us); std::swap(b.Vs, n.Vs); std::swap(b.Ws, n.Ws);
     std::swap(b.xwy, n.xwy); std::swap(b.xuo, n.xuo); std::swap(b.xvr, n.xvr);
+    std::swap(b.cpad, n.cpad);
 }
 
 // Allocate the next velocity level (once per handle).
@@ -771,10 +812,12 @@ static int alloc_next(mr_handle h)
         alloc((void**)&n.xuo, (size_t)h->Nz * h->Ny * b.nxg * 4);
         alloc((void**)&n.xvr, (size_t)h->Nz * (h->Ny + 1) * b.nxg * 4);
     } else {
-        alloc((void**)&b.lerpc, (h->ncU + h->ncV + h->ncW) * 4);
+        const size_t np = fused_pad_floats(h->cfg.nx, h->nys, h->cfg.nz);
+        alloc((void**)&n.cpad, np * 4);
+        alloc((void**)&b.lerpc, np * 4);
     }
     if (e != cudaSuccess) {
-        void* ptrs[] = {n.U64, n.V64, n.W64, n.Us, n.Vs, n.Ws, n.xwy, n.xuo, n.xvr, b.lerpc};
+        void* ptrs[] = {n.U64, n.V64, n.W64, n.Us, n.Vs, n.Ws, n.xwy, n.xuo, n.xvr, n.cpad, b.lerpc};
         for (void* p : ptrs)
             if (p) dev_free(p);
         if (h->elt == 4) {
@@ -803,6 +846,7 @@ int mr_refine_velocity(mr_handle h, const double* U, const double* V, const doub
     if (Us && h->cfg.velocity_mode != MR_VEL_STORED &&
         (!is_device_pointer(Us) || !is_device_pointer(Vs) || !is_device_pointer(Ws)))
         return set_error(MR_ERR_ARG, "mr_refine_velocity: in fused mode Us, Vs, Ws must be device memory");
+    if (Us && h->slab) return set_error(MR_ERR_ARG, "mr_refine_velocity: no dense faces from a y-slab handle");
     cudaStream_t st = (cudaStream_t)stream;
     DeviceBuffers& b = h->buf;
     int rc = load_velocity(h, U, V, W, st);
@@ -893,6 +937,10 @@ int mr_scalar_coarse_step(mr_handle h, const double* U, const double* V, const d
 {
     if (!h || !U || !V || !W) return set_error(MR_ERR_ARG, "mr_scalar_coarse_step: NULL argument");
     if (mt < 1) return set_error(MR_ERR_ARG, "mr_scalar_coarse_step: mt must be >= 1");
+    if (h->slab && mt > 1)
+        return set_error(MR_ERR_ARG, "mr_scalar_coarse_step: a y-slab handle takes one step per call (mt = 1)");
+    if (h->slab && !(h->halo_set[h->ic] && (h->step == 0 || h->halo_set[h->ip])))
+        return set_error(MR_ERR_STATE, "mr_scalar_coarse_step: set the y-slab's halo rows first");
     if (!h->have_velocity || !h->have_scalar)
         return set_error(MR_ERR_STATE, "mr_scalar_coarse_step: call mr_refine_velocity and mr_set_scalar first");
     cudaStream_t st = (cudaStream_t)stream;
@@ -924,6 +972,7 @@ int mr_set_scalar(mr_handle h, const void* T0, int32_t dtype, mr_stream stream)
     if (rc) return rc;
     h->step = 0;
     h->have_scalar = true;
+    for (bool& f : h->halo_set) f = false;
     return MR_OK;
 }
 
@@ -948,10 +997,44 @@ int mr_scalar_step(mr_handle h, int64_t nsteps, mr_stream stream)
     if (!h->have_velocity || !h->have_scalar)
         return set_error(MR_ERR_STATE, "mr_scalar_step: call mr_refine_velocity and mr_set_scalar first");
     cudaStream_t st = (cudaStream_t)stream;
+    if (h->slab && nsteps > 1)
+        return set_error(MR_ERR_ARG, "mr_scalar_step: a y-slab handle takes one step per call (halo rows between)");
+    if (h->slab && nsteps == 1 && !(h->halo_set[h->ic] && (h->step == 0 || h->halo_set[h->ip])))
+        return set_error(MR_ERR_STATE, "mr_scalar_step: set the y-slab's halo rows (mr_set_halo_rows) first");
     for (int64_t q = 0; q < nsteps; ++q) {
         const int rc = one_step(h, 0.0, st);
         if (rc) return rc;
     }
+    return MR_OK;
+}
+
+int mr_get_boundary_rows(mr_handle h, void* south, void* north, mr_stream stream)
+{
+    if (!h || (!south && !north)) return set_error(MR_ERR_ARG, "mr_get_boundary_rows: NULL argument");
+    if (!h->slab) return set_error(MR_ERR_ARG, "mr_get_boundary_rows: not a y-slab handle");
+    if (!h->have_scalar) return set_error(MR_ERR_STATE, "mr_get_boundary_rows: no scalar set");
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t row = (size_t)h->Nx * h->elt, plane = row * h->Nys;
+    const char* T = (const char*)h->buf.T[h->ic];
+    cudaError_t e = cudaSuccess;
+    if (south) e = cudaMemcpy2DAsync(south, row, T, plane, row, h->Nz, cudaMemcpyDefault, st);
+    if (e == cudaSuccess && north)
+        e = cudaMemcpy2DAsync(north, row, T + (size_t)(h->Nys - 1) * row, plane, row, h->Nz, cudaMemcpyDefault, st);
+    return cuda_check(e, "mr_get_boundary_rows");
+}
+
+int mr_set_halo_rows(mr_handle h, const void* below, const void* above, mr_stream stream)
+{
+    if (!h || !below || !above) return set_error(MR_ERR_ARG, "mr_set_halo_rows: NULL argument");
+    if (!h->slab) return set_error(MR_ERR_ARG, "mr_set_halo_rows: not a y-slab handle");
+    if (!h->have_scalar) return set_error(MR_ERR_STATE, "mr_set_halo_rows: no scalar set");
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t n = (size_t)h->Nz * h->Nx;
+    float* dst = h->buf.halo + 2 * (size_t)h->ic * n;
+    cudaError_t e = cudaMemcpyAsync(dst, below, n * h->elt, cudaMemcpyDefault, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(dst + n, above, n * h->elt, cudaMemcpyDefault, st);
+    if (e != cudaSuccess) return cuda_check(e, "mr_set_halo_rows");
+    h->halo_set[h->ic] = true;
     return MR_OK;
 }
 
@@ -983,8 +1066,8 @@ static int max_divergence(mr_handle h, double* out, cudaStream_t st)
     if (h->cfg.velocity_mode == MR_VEL_XFUSED)
         e = launch_xfused_max_f32(h->g32, 1, b.xwy, b.xuo, b.xvr, b.nxg, b.xlc, b.xlcw, b.xrx, b.red, h->red_blocks, st);
     else if (h->cfg.velocity_mode == MR_VEL_FUSED)
-        e = launch_fused_max_f32(h->g32, 1, (const float*)b.Uc, (const float*)b.Vc, (const float*)b.Wc, b.xlc, b.xrx,
-                                  b.red, h->red_blocks, st);
+        e = launch_fused_max_f32(h->g32, 1, FusedInputs{b.cpad, {}, {}, 0, b.fsc, b.xlc, b.xrx, b.xry}, b.red,
+                                 h->red_blocks, st);
     else if (h->cfg.precision == MR_F64)
         e = launch_maxdiv<double>(h->g64, (const double*)b.Us, (const double*)b.Vs, (const double*)b.Ws, b.red,
                                   h->red_blocks, st);
@@ -1012,7 +1095,7 @@ int mr_scalar_stats(mr_handle h, mr_stats* out, mr_stream stream)
     const double dxdy = (h->cfg.lx / h->Nx) * (h->cfg.ly / h->Ny);
     double vtot = 0.0;
     for (int k = 0; k < h->Nz; ++k) vtot += h->dz[k];
-    vtot *= dxdy * (double)h->Nx * (double)h->Ny;
+    vtot *= dxdy * (double)h->Nx * (double)h->Nys;
     std::vector<double> p;
     cudaError_t e;
     e = h->cfg.precision == MR_F64 ? launch_moments<double>(h->g64, (const double*)T, 0.0, 0, h->buf.red, h->red_blocks, st)
@@ -1065,8 +1148,8 @@ int mr_cfl_dt(mr_handle h, double cfl, double* dt_out, mr_stream stream)
         e = launch_xfused_max_f32(h->g32, 2, b.xwy, b.xuo, b.xvr, b.nxg, b.xlc, b.xlcw, b.xrx, b.red, h->red_blocks, st);
     } else if (h->cfg.velocity_mode == MR_VEL_FUSED) {
         // the fused kernel forms the dense faces in registers from the coarse ones
-        e = launch_fused_max_f32(h->g32, 2, (const float*)b.Uc, (const float*)b.Vc, (const float*)b.Wc, b.xlc, b.xrx,
-                                  b.red, h->red_blocks, st);
+        e = launch_fused_max_f32(h->g32, 2, FusedInputs{b.cpad, {}, {}, 0, b.fsc, b.xlc, b.xrx, b.xry}, b.red,
+                                 h->red_blocks, st);
     } else if (h->cfg.velocity_mode != MR_VEL_STORED) {
         // dense faces are not kept: refine into temporary buffers once
         void *a = nullptr, *bb = nullptr, *c = nullptr;
@@ -1132,7 +1215,7 @@ int field_moments(mr_handle h, const void* T, double* mean, double* var, cudaStr
     const double dxdy = (h->cfg.lx / h->Nx) * (h->cfg.ly / h->Ny);
     double vtot = 0.0;
     for (int k = 0; k < h->Nz; ++k) vtot += h->dz[k];
-    vtot *= dxdy * (double)h->Nx * (double)h->Ny;
+    vtot *= dxdy * (double)h->Nx * (double)h->Nys;
     std::vector<double> p;
     for (int pass = 0; pass < 2; ++pass) {
         cudaError_t e = h->cfg.precision == MR_F64
@@ -1273,7 +1356,7 @@ int mr_adjoint_backward(mr_handle h, double gscale, void* gT0, int32_t gT0_dtype
     const double dxdy = (h->cfg.lx / h->Nx) * (h->cfg.ly / h->Ny);
     double vtot = 0.0;
     for (int k = 0; k < h->Nz; ++k) vtot += h->dz[k];
-    vtot *= dxdy * (double)h->Nx * (double)h->Ny;
+    vtot *= dxdy * (double)h->Nx * (double)h->Nys;
     const double zb = h->zc[0] - h->zf[0];
     // direct terms in adjoint-density units (per unit volume)
     auto s_nu = [&](int64_t s) { return -gscale * a.wnu[s] / ((double)h->Nx * h->Ny * zb * dxdy * h->dz[0]); };
@@ -1373,7 +1456,7 @@ int mr_upscale_scalar(mr_handle h, double* Tc, mr_stream stream)
     if (!h->have_scalar) return set_error(MR_ERR_STATE, "mr_upscale_scalar: no scalar set");
     cudaStream_t st = (cudaStream_t)stream;
     DeviceBuffers& b = h->buf;
-    const size_t nc = (size_t)h->cfg.nx * h->cfg.ny * h->cfg.nz;
+    const size_t nc = (size_t)h->cfg.nx * h->nys * h->cfg.nz;
     const size_t need = nc + (size_t)h->Nz + 1 + (size_t)h->Nz;
     if (!b.diag) {
         cudaError_t e = dev_malloc((void**)&b.diag, need * sizeof(double));
@@ -1396,7 +1479,8 @@ int mr_scalar_profiles(mr_handle h, double* nu_z, double* nu_T, mr_stream stream
         return set_error(MR_ERR_STATE, "mr_scalar_profiles: call mr_refine_velocity and mr_set_scalar first");
     cudaStream_t st = (cudaStream_t)stream;
     DeviceBuffers& b = h->buf;
-    const size_t nc = (size_t)h->cfg.nx * h->cfg.ny * h->cfg.nz;
+    const size_t nc = (size_t)h->cfg.nx * h->nys * h->cfg.nz;
+    if (h->slab) return set_error(MR_ERR_ARG, "mr_scalar_profiles: not on a y-slab handle");
     if (!b.diag) {
         cudaError_t e = dev_malloc((void**)&b.diag, (nc + 2 * (size_t)h->Nz + 1) * sizeof(double));
         if (e != cudaSuccess) return cuda_check(e, "mr_scalar_profiles: buffer");

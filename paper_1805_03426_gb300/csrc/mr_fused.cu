@@ -4,25 +4,36 @@
 // only; per step the kernel reads the coarse faces, T^s and T^{s-1} and
 // writes T^{s+1}.
 //
-// One CTA owns a 64 x 8 column of dense cells and marches a chunk of coarse
-// slabs.  At the start of each slab K its 128 consumer threads compute, from
-// the coarse U, V, W (global, L1/L2-resident), the slab's refinement stages at
-// coarse resolution in x, for the tile's rows and the bundle columns
-// I0-4 .. I0+CX+3 (periodic images):
-//   - stage Z: the slab balance of every coarse column (full-area W on the
-//     slab's inner dense planes), top-down;
-//   - WY: R_y of the full-area W on the slab's M+1 dense planes;
-//   - UO: the outer U sub-faces (R_y R_z of U) in units of U / (2 dx);
-//   - VR: the full-coarse-width V on every dense y-face of the tile (R_z of V
-//     on the coarse faces, row balance of stage Y on the inner ones) in units
-//     of V / (2 dy);
-// separated by consumer-only barriers.  Each dense layer then runs exactly the
-// split-x step (stage X -- R_x splits and the west-to-east cell balance -- in
-// registers, then the finite-volume update of Eq. 5 with the Euler-leapfrog
-// coefficients of Section 2.2), with T^s, T^{s-1} and the layer constants
-// streamed by one producer warp through a TMA ring on full/empty mbarriers.
-// Every wait is bounded: on time-out the kernel records MR_ERR_TIMEOUT in a
-// device flag.
+// One CTA owns a 64 x TY column of dense cells (TY = 8 or 16) and marches a
+// chunk of coarse slabs with three kinds of warps:
+//   - a producer warp streams, through TMA onto mbarriers, the two scalar
+//     planes of every dense layer with the layer's constants (a ring of NB
+//     slots), and the coarse faces of every coarse slab (two buffers: the R_z
+//     window planes of U and V and the slab's two W planes, for the tile's
+//     coarse rows and columns with their neighbours, from a copy of the coarse
+//     faces padded with their periodic images so that every box is in bounds);
+//   - two builder warps form, from those coarse faces, the slab's refinement
+//     stages at coarse resolution in x (two buffers: slab K+1 while slab K is
+//     stepped; the first slab of a chunk is built by every consumer and
+//     builder thread together):
+//       stage Z  the full-area W on the slab's inner dense planes by the slab
+//                balance, top-down, written as W(K+1) + sum_q Z[c][q] D_q with
+//                D_q the horizontal divergence of coarse plane q of the R_z
+//                window and Z[c][q] = sum_{c' >= c} dz_c' R_z[c'][q] (the same
+//                linear map as the layer-by-layer balance, reassociated);
+//       WY       R_y of the full-area W on the slab's M + 1 dense planes;
+//       UO       the outer U sub-faces (R_y R_z of U), in units of U / (2 dx);
+//       VR       the full-coarse-width V on every dense y-face of the tile: R_z
+//                of V on the coarse faces, the row balance of stage Y (south
+//                to north) on the inner ones, in units of V / (2 dy);
+//   - the consumer warps run every dense layer: stage X (R_x splits of W and
+//     V, the west-to-east cell balance for U) in registers, then the
+//     finite-volume update of Eq. 5 with the Euler-leapfrog coefficients of
+//     Section 2.2, on packed FP32 pairs.
+// The hand-overs are full/empty mbarrier pairs (ring slots, coarse buffers,
+// slab buffers); every wait is bounded, and a time-out records MR_ERR_TIMEOUT
+// in a device flag.  Before the CTA exits, the producer waits for every copy
+// it issued, so that none is in flight even after a time-out.
 //
 // Supported: FP32, periodic x and y, mx = my = mz = M in {2, 4},
 // Nx % 64 == 0, Ny % 16 == 0, explicit diffusion, second-order faces.
@@ -39,63 +50,71 @@ namespace {
 
 using namespace ptx;
 
-constexpr int kTX = 64, kTY = 8;                        // tile (cells)
-constexpr int kBX = kTX + 8, kBY = kTY + 2;             // scalar plane box (floats)
-constexpr int kCons = 16 * kTY;                         // consumer threads: 4-cell segments
-constexpr int kThreadsAll = kCons + 32;                 // + one producer warp
-constexpr int kLCW = 32;                                // layer-constant row (floats)
+constexpr int kTX = 64;                 // tile width (cells)
+constexpr int kBX = kTX + 8;            // scalar plane box width (floats)
+constexpr int kLCW = 32;                // layer-constant row (floats)
+constexpr int kSCW = 32;                // slab-constant row (floats)
 
-template <int M>
-struct FX {
-    static constexpr int CX = kTX / M, CY = kTY / M;    // coarse cells of the tile
-    static constexpr int BXC = CX + 8;                  // bundle columns I0-4 .. I0+CX+3
-    static constexpr int NB = 6;                        // ring slots
+__host__ __device__ constexpr int up32(int n) { return (n + 31) / 32 * 32; }
+
+// Shared-memory layout (offsets in floats; every TMA destination on a
+// 128-byte boundary).  DIV: the reductions, which stream no scalar planes.
+template <int M, int TY, bool DIV>
+struct FL {
+    static constexpr int CONS = 16 * TY;                    // consumer threads: 4-cell segments
+    static constexpr int NCW = CONS / 32;                   // consumer warps
+    static constexpr int NBT = 64;                          // builder threads (two warps)
+    static constexpr int THREADS = CONS + 32 + NBT;         // + producer warp + builder warps
+    static constexpr int CTAS = TY == 16 ? 2 : 3;           // resident CTAs per SM the layout is sized for
+    static constexpr int NB = DIV ? 8 : (TY == 16 ? 6 : (M == 4 ? 7 : 6));   // ring slots
+    static constexpr int CX = kTX / M, CY = TY / M;         // coarse cells of the tile
+    static constexpr int BXC = CX + 8;                      // coarse box columns I0-4 .. I0+CX+3
+    static constexpr int SXC = CX + 4;                      // slab buffer columns I0-1 .. I0+CX+2
+    static constexpr int kBY = TY + 2;                      // rows of a scalar plane box
     static constexpr uint32_t plane_bytes = (uint32_t)(kBX * kBY) * 4;
-    static constexpr int PS = (int)((plane_bytes + 127) / 128) * 128 / 4;
-    // ring slot (floats): T^s plane, T^{s-1} plane, the layer constants
+    static constexpr int PS = DIV ? 0 : up32(kBX * kBY);
+    // ring slot: T^s plane, T^{s-1} plane, the layer constants
     static constexpr int oTn = 0, oTm = PS, oLC = 2 * PS;
-    static constexpr int slot = (((oLC + kLCW) * 4 + 127) / 128) * 128 / 4;
-    // the slab's intermediates: WY [M+1][TY][BXC], UO [M][TY][BXC],
-    // VR [M][TY+1][BXC], and the slab balance [M-1][CY+2][BXC]
-    static constexpr int oWY = NB * slot;
-    static constexpr int oUO = oWY + (M + 1) * kTY * BXC;
-    static constexpr int oVR = oUO + M * kTY * BXC;
-    static constexpr int oSW = oVR + M * (kTY + 1) * BXC;
-    // the slab's coarse faces (periodic images), staged by cp.async: U on the
-    // three R_z window planes, coarse rows J0-1 .. J0+CY, columns I0-4 .. I0+CX+4;
-    // V likewise with rows up to J0+CY+1; W on the slab's two coarse planes
-    static constexpr int NUX = BXC + 1, NUY = CY + 2, NVY = CY + 3, NWY = CY + 2;
-    static constexpr int NU = 3 * NUY * NUX, NV = 3 * NVY * BXC, NW = 2 * NWY * BXC;
-    static constexpr int oSU = oSW + (M - 1) * (CY + 2) * BXC;
-    static constexpr int oSV = oSU + NU;
-    static constexpr int oSWc = oSV + NV;
-    // R_y rows of the tile's dense rows [TY][3]; R_z rows and widths of the slab's layers
-    static constexpr int oRy = oSWc + NW;
-    static constexpr int oRz = oRy + 3 * kTY;
-    static constexpr int oDz = oRz + 3 * M;
-    static constexpr int oRed = (oDz + M + 3) / 4 * 4;
-    static constexpr int oBar = ((oRed + 64) * 4 + 7) / 8;
-    static constexpr size_t bytes = (size_t)(oBar + 2 * NB) * 8;
+    static constexpr int slot = up32(oLC + kLCW);
+    // slab buffer: WY [M+1][TY][SXC], UO [M][TY][SXC], VR [M][TY+1][SXC]
+    static constexpr int bWY = 0, bUO = (M + 1) * TY * SXC, bVR = bUO + M * TY * SXC;
+    static constexpr int SLAB = up32(bVR + M * (TY + 1) * SXC);
+    static constexpr int oSlab = NB * slot;
+    // coarse buffer: U [3][NUR][BXC] (R_z window planes, coarse rows J0-1 .. J0+CY),
+    // V [3][NVR][BXC] (rows J0-1 .. J0+CY+1), W [2][NUR][BXC] (planes K, K+1)
+    static constexpr int NUR = CY + 2, NVR = CY + 3;
+    static constexpr int cU = 0, cV = up32(3 * NUR * BXC), cW = cV + up32(3 * NVR * BXC);
+    static constexpr int CBOX = cW + up32(2 * NUR * BXC);
+    static constexpr uint32_t cu_bytes = 3 * NUR * BXC * 4, cv_bytes = 3 * NVR * BXC * 4,
+                              cw_bytes = 2 * NUR * BXC * 4;
+    static constexpr int oCoarse = oSlab + 2 * SLAB;
+    static constexpr int oZ = oCoarse + 2 * CBOX;           // stage Z: [M-1][NUR][BXC]
+    static constexpr int oRed = oZ + up32((M - 1) * NUR * BXC);   // 64 floats: reduction, failure flag
+    static constexpr int oBar = (oRed + 64) / 2;            // in uint64
+    // full[NB], empty[NB], cfull[2], cempty[2], built[2], freed[2]
+    static constexpr size_t bytes = (size_t)(oBar + 2 * NB + 8) * 8;
 };
 
-struct FXArgs {
+struct FLArgs {
     Grid<float> g;
-    const float* U;      // coarse faces, FP32: [nz][ny][nx]
-    const float* V;      // [nz][ny][nx]
-    const float* W;      // [nz+1][ny][nx]
     const float* Tn;     // T^s (global, for the periodic halo of edge threads)
     const float* Tm;     // T^{s-1}
     float* Tp1;          // T^{s+1}
+    const float* sc;     // [nz][32] slab constants (fused_slab_constants)
     float a, b, gdt;
     int kcs;             // coarse slabs per CTA chunk
     int* err;
     unsigned long long* divmax;
     float rx[4][3];      // R_x rows of the 4 cells of a segment (uniform periodic x)
+    float ry[4][3];      // R_y rows of the sub-rows of a coarse row (uniform periodic y)
+    float iDX, iDY;      // 1 / DX, 1 / DY (coarse)
+    float hx, hy;        // 1 / (2 dx), 1 / (2 dy)
     unsigned long long wait_ns;   // time limit of every bounded wait
-    int stop_ring;       // test hook: the producer of CTA (0,0,0) issues no ring from this one on (-1: none)
+    int stop_ring;       // test hook: the producer of CTA (0,0,0) issues nothing from this ring on (-1: none)
+    const float* hs[2];  // rows south of row 0 of T^s, T^{s-1} (periodic images or y-slab halo)
+    const float* hn[2];  // rows north of row Ny-1
+    size_t hstride;      // layer stride of those rows
 };
-
-__device__ __forceinline__ int wrapi(int i, int n) { return i < 0 ? i + n : (i >= n ? i - n : i); }
 
 // R_x split of three coarse values by one row of R (rows sum to one).
 __device__ __forceinline__ float rsplit3(const float (&r)[3], float c0, float c1, float c2)
@@ -114,165 +133,174 @@ __device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a
 __device__ __forceinline__ float2 lo2(float4 v) { return make_float2(v.x, v.y); }
 __device__ __forceinline__ float2 hi2(float4 v) { return make_float2(v.z, v.w); }
 
-// The slab's refinement intermediates (see the file comment), written by the
-// kCons consumer threads from the coarse faces staged in shared memory; ends
-// with every value visible to all of them.
-template <int M>
-__device__ void slab_prep(const FXArgs& A, float* sm, int K, int I0, int J0, int j0, int tid)
+// Named barriers of the builder group (id 2, the builder warps) and of the
+// first slab's build (id 3, consumers and builders); each agrees on failure
+// first, so that either every participant builds or none does.
+template <int N>
+__device__ __forceinline__ void named_sync(int id)
 {
-    using L = FX<M>;
-    constexpr int BXC = L::BXC, CY = L::CY, NUX = L::NUX, NUY = L::NUY, NVY = L::NVY, NWY = L::NWY;
-    const Grid<float>& g = A.g;
-    float* sWY = sm + L::oWY;
-    float* sUO = sm + L::oUO;
-    float* sVR = sm + L::oVR;
-    float* sSW = sm + L::oSW;
-    float* sU = sm + L::oSU;
-    float* sV = sm + L::oSV;
-    float* sW = sm + L::oSWc;
-    const size_t cpl = (size_t)g.ny * g.nx;                 // coarse plane
-    // stage the coarse faces: U, V on the R_z window planes of K, W on K, K+1
-#pragma unroll 4
-    for (int u = 0; u < (L::NU + kCons - 1) / kCons; ++u) {
-        const int t = tid + u * kCons;
-        if (t < L::NU) {
-            const int q = t / (NUY * NUX), r = t - q * NUY * NUX, jr = r / NUX, xc = r - jr * NUX;
-            const int I = wrapi(I0 - 4 + xc, g.nx), J = wrapi(J0 - 1 + jr, g.ny);
-            cp_async4(sU + t, A.U + (size_t)g.wz[3 * K + q] * cpl + (size_t)J * g.nx + I);
-        }
-    }
-#pragma unroll 4
-    for (int u = 0; u < (L::NV + kCons - 1) / kCons; ++u) {
-        const int t = tid + u * kCons;
-        if (t < L::NV) {
-            const int q = t / (NVY * BXC), r = t - q * NVY * BXC, jr = r / BXC, xc = r - jr * BXC;
-            const int I = wrapi(I0 - 4 + xc, g.nx), J = wrapi(J0 - 1 + jr, g.ny);
-            cp_async4(sV + t, A.V + (size_t)g.wz[3 * K + q] * cpl + (size_t)J * g.nx + I);
-        }
-    }
-#pragma unroll 4
-    for (int u = 0; u < (L::NW + kCons - 1) / kCons; ++u) {
-        const int t = tid + u * kCons;
-        if (t < L::NW) {
-            const int q = t / (NWY * BXC), r = t - q * NWY * BXC, jr = r / BXC, xc = r - jr * BXC;
-            const int I = wrapi(I0 - 4 + xc, g.nx), J = wrapi(J0 - 1 + jr, g.ny);
-            cp_async4(sW + t, A.W + (size_t)(K + q) * cpl + (size_t)J * g.nx + I);
-        }
-    }
-    if (tid < 3 * M) sm[L::oRz + tid] = g.Rz[3 * K * M + tid];
-    if (tid < M) sm[L::oDz + tid] = g.dz[K * M + tid];
-    cp_async_commit();
-    cp_async_wait_all();
-    asm volatile("barrier.cta.sync 1, %0;" ::"n"(kCons) : "memory");
-    const float* sRy = sm + L::oRy;
-    const float* sRz = sm + L::oRz;
-    const float* sDz = sm + L::oDz;
-    // stage Z: slab balance of every coarse column, top-down (full-area W on
-    // the inner dense planes K M + c, c = M-1 .. 1), coarse rows J0-1 .. J0+CY
-    for (int t = tid; t < (CY + 2) * BXC; t += kCons) {
-        const int jr = t / BXC, xb = t - jr * BXC;
-        float F = sW[(NWY + jr) * BXC + xb] * g.DX * g.DY;      // W on coarse plane K+1
-#pragma unroll
-        for (int c = M - 1; c >= 1; --c) {
-            float uw = 0.f, ue = 0.f, vs = 0.f, vn = 0.f;
-#pragma unroll
-            for (int q = 0; q < 3; ++q) {
-                const float r = sRz[3 * c + q];
-                uw += r * sU[(q * NUY + jr) * NUX + xb];
-                ue += r * sU[(q * NUY + jr) * NUX + xb + 1];
-                vs += r * sV[(q * NVY + jr) * BXC + xb];
-                vn += r * sV[(q * NVY + jr + 1) * BXC + xb];
-            }
-            F = F + (ue - uw) * g.DY * sDz[c] + (vn - vs) * g.DX * sDz[c];
-            sSW[((c - 1) * (CY + 2) + jr) * BXC + xb] = F / (g.DX * g.DY);
-        }
-    }
-    asm volatile("barrier.cta.sync 1, %0;" ::"n"(kCons) : "memory");
-    // WY on the slab's M + 1 dense planes, per (dense row, bundle column)
-    for (int e = tid; e < kTY * BXC; e += kCons) {
-        const int jl = e / BXC, xb = e - jl * BXC;
-        const int jr = (j0 + jl) / M - J0;                         // coarse row, relative to J0
-        const float r0 = sRy[3 * jl], r1 = sRy[3 * jl + 1], r2 = sRy[3 * jl + 2];
-#pragma unroll
-        for (int i = 0; i <= M; ++i) {
-            const float* src = (i == 0 || i == M) ? sW + (i == M ? NWY : 0) * BXC : sSW + (i - 1) * (CY + 2) * BXC;
-            const float c0 = src[jr * BXC + xb], c1 = src[(jr + 1) * BXC + xb], c2 = src[(jr + 2) * BXC + xb];
-            sWY[(i * kTY + jl) * BXC + xb] = r0 * c0 + r1 * c1 + r2 * c2;
-        }
-    }
-    // UO of the slab's M layers, per (coarse row, bundle column): the z split
-    // of the three window rows is shared by the row's M dense rows
-    const float hix = 0.5f * g.inv_dx;
-    for (int e = tid; e < CY * BXC; e += kCons) {
-        const int Jr = e / BXC, xb = e - Jr * BXC;
+    asm volatile("barrier.cta.sync %0, %1;" ::"r"(id), "n"(N) : "memory");
+}
+template <int N>
+__device__ __forceinline__ bool named_or(int id, bool v)
+{
+    uint32_t r;
+    asm volatile(
+        "{\n\t.reg .pred p, q;\n\t"
+        "setp.ne.u32 q, %1, 0;\n\t"
+        "barrier.cta.red.or.pred p, %2, %3, q;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(r)
+        : "r"((uint32_t)v), "r"(id), "n"(N)
+        : "memory");
+    return r != 0;
+}
+
+// VR of the slab on the columns I0-1 .. I0+CX: the coarse face of rows
+// J0 .. J0+CY from R_z of V, then, inside the tile, the row balance of stage Y
+// south to north.  The UO and WY it reads and the VR it writes are disjoint
+// regions of the slab buffer (separate restrict pointers, so that every load
+// of an item can be issued ahead of its running balance).
+template <int M, int TY, int NT>
+__device__ __forceinline__ void build_vr(const float* __restrict__ cv, const float* __restrict__ uo_all,
+                                         const float* __restrict__ wy_all, float* __restrict__ vr_all,
+                                         const float (&rz)[M][3], const float (&hz)[M], float hy, int t0)
+{
+    using L = FL<M, TY, false>;
+    constexpr int BXC = L::BXC, SXC = L::SXC, NVR = L::NVR, CX = L::CX, CY = L::CY, NZC = CX + 2;
+    constexpr float iM = 1.f / (float)M;
+    for (int t = t0; t < NZC * (CY + 1); t += NT) {
+        const int Jr = t / NZC, xs = t - Jr * NZC, x = xs + 3;     // slab column xs, coarse box column x
+        const float v0 = cv[(0 * NVR + Jr + 1) * BXC + x], v1 = cv[(1 * NVR + Jr + 1) * BXC + x],
+                    v2 = cv[(2 * NVR + Jr + 1) * BXC + x];
 #pragma unroll
         for (int i = 0; i < M; ++i) {
-            float a[3];
-#pragma unroll
-            for (int p = 0; p < 3; ++p) {
-                float s = 0.f;
-#pragma unroll
-                for (int q = 0; q < 3; ++q) s += sRz[3 * i + q] * sU[(q * NUY + Jr + p) * NUX + xb];
-                a[p] = s;
-            }
-#pragma unroll
-            for (int b = 0; b < M; ++b) {
-                const int jl = Jr * M + b;
-                sUO[(i * kTY + jl) * BXC + xb] =
-                    (sRy[3 * jl] * a[0] + sRy[3 * jl + 1] * a[1] + sRy[3 * jl + 2] * a[2]) * hix;
-            }
-        }
-    }
-    asm volatile("barrier.cta.sync 1, %0;" ::"n"(kCons) : "memory");
-    // VR: per layer and coarse row J0 .. J0+CY, the coarse face from R_z of V,
-    // then (rows inside the tile) the row balance, south to north; the last
-    // bundle column is never read and is skipped (its east neighbour is absent)
-    const float hiy = 0.5f * g.inv_dy, two_dx = 2.f * g.dx;
-    for (int e = tid; e < (CY + 1) * (BXC - 1); e += kCons) {
-        const int Jr = e / (BXC - 1), xb = e - Jr * (BXC - 1);
-#pragma unroll
-        for (int i = 0; i < M; ++i) {
-            float vz = 0.f;
-#pragma unroll
-            for (int q = 0; q < 3; ++q) vz += sRz[3 * i + q] * sV[(q * NVY + Jr + 1) * BXC + xb];
-            float* vr = sVR + (i * (kTY + 1) + Jr * M) * BXC + xb;
-            vr[0] = vz * hiy;
+            float du[M - 1], dw[M - 1];
             if (Jr < CY) {
-                const float dzk = sDz[i];
-                const float* uo = sUO + (i * kTY + Jr * M) * BXC + xb;
-                const float* wyb = sWY + (i * kTY + Jr * M) * BXC + xb;
-                const float* wyt = wyb + kTY * BXC;
-                float G = vz * g.DX * dzk;
+                const float* uo = uo_all + (i * TY + Jr * M) * SXC + xs;
+                const float* wb = wy_all + (i * TY + Jr * M) * SXC + xs;
 #pragma unroll
                 for (int b = 0; b < M - 1; ++b) {
-                    const float uw = uo[b * BXC] * two_dx, ue = uo[b * BXC + 1] * two_dx;
-                    G = G - (ue - uw) * g.dy * dzk - (wyt[b * BXC] - wyb[b * BXC]) * g.DX * g.dy;
-                    vr[(b + 1) * BXC] = G / (g.DX * dzk) * hiy;
+                    du[b] = uo[b * SXC + 1] - uo[b * SXC];
+                    dw[b] = wb[(TY + b) * SXC] - wb[b * SXC];
+                }
+            }
+            float vr = (rz[i][0] * v0 + rz[i][1] * v1 + rz[i][2] * v2) * hy;
+            float* dst = vr_all + (i * (TY + 1) + Jr * M) * SXC + xs;
+            dst[0] = vr;
+            if (Jr < CY) {
+#pragma unroll
+                for (int b = 0; b < M - 1; ++b) {
+                    vr = vr - du[b] * iM - dw[b] * hz[i];
+                    dst[(b + 1) * SXC] = vr;
                 }
             }
         }
     }
-    asm volatile("barrier.cta.sync 1, %0;" ::"n"(kCons) : "memory");
+}
+
+// One coarse slab's refinement stages (see the file comment) from the coarse
+// buffer cb into the slab buffer sb (sz: stage-Z scratch), by NT threads
+// (this one t0) that meet at named barrier bar between the stages.  scg: the
+// slab's constants in global memory (R_z rows of its M layers, 1/(2 dz) of
+// each, the stage-Z weights Z[c][q]).
+template <int M, int TY, int NT>
+__device__ void build_slab(const FLArgs& A, const float* __restrict__ cb, float* __restrict__ sb,
+                           float* __restrict__ sz, const float* __restrict__ scg, int t0, int bar)
+{
+    using L = FL<M, TY, false>;
+    constexpr int BXC = L::BXC, SXC = L::SXC, NUR = L::NUR, NVR = L::NVR, CX = L::CX, CY = L::CY;
+    const float* cu = cb + L::cU;
+    const float* cv = cb + L::cV;
+    const float* cw = cb + L::cW;
+    float rz[M][3], hz[M], zc[M - 1][3];
+#pragma unroll
+    for (int i = 0; i < M; ++i) {
+#pragma unroll
+        for (int q = 0; q < 3; ++q) rz[i][q] = scg[3 * i + q];
+        hz[i] = scg[3 * M + i];
+    }
+#pragma unroll
+    for (int c = 0; c < M - 1; ++c)
+#pragma unroll
+        for (int q = 0; q < 3; ++q) zc[c][q] = scg[4 * M + 3 * c + q];
+    const float iDX = A.iDX, iDY = A.iDY, hx = A.hx;
+    // stage Z on the columns I0-1 .. I0+CX of coarse rows J0-1 .. J0+CY
+    constexpr int NZC = CX + 2;
+    for (int t = t0; t < NUR * NZC; t += NT) {
+        const int r = t / NZC, x = 3 + t - r * NZC;
+        float D[3];
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+            const float uw = cu[(q * NUR + r) * BXC + x], ue = cu[(q * NUR + r) * BXC + x + 1];
+            const float vs = cv[(q * NVR + r) * BXC + x], vn = cv[(q * NVR + r + 1) * BXC + x];
+            D[q] = (ue - uw) * iDX + (vn - vs) * iDY;
+        }
+        const float wtop = cw[(NUR + r) * BXC + x];
+#pragma unroll
+        for (int c = 0; c < M - 1; ++c)
+            sz[(c * NUR + r) * BXC + x] = wtop + zc[c][0] * D[0] + zc[c][1] * D[1] + zc[c][2] * D[2];
+    }
+    // UO of the slab's M layers on the columns I0-1 .. I0+CX+1 (from the coarse
+    // faces alone, so before the barrier): the z split of the three window rows
+    // is shared by the coarse row's M dense rows
+    constexpr int NUC = CX + 3;
+    for (int t = t0; t < NUC * CY; t += NT) {
+        const int Jc = t / NUC, x = 3 + t - Jc * NUC;
+        float u[3][3];
+#pragma unroll
+        for (int q = 0; q < 3; ++q)
+#pragma unroll
+            for (int p = 0; p < 3; ++p) u[q][p] = cu[(q * NUR + Jc + p) * BXC + x];
+#pragma unroll
+        for (int i = 0; i < M; ++i) {
+            float a[3];
+#pragma unroll
+            for (int p = 0; p < 3; ++p) a[p] = (rz[i][0] * u[0][p] + rz[i][1] * u[1][p] + rz[i][2] * u[2][p]) * hx;
+            float* dst = sb + L::bUO + (i * TY + Jc * M) * SXC + x - 3;
+#pragma unroll
+            for (int b = 0; b < M; ++b) dst[b * SXC] = A.ry[b][0] * a[0] + A.ry[b][1] * a[1] + A.ry[b][2] * a[2];
+        }
+    }
+    named_sync<NT>(bar);
+    // WY on the slab's M + 1 dense planes: per (plane, coarse row, column)
+    for (int t = t0; t < NZC * CY * (M + 1); t += NT) {
+        const int i = t / (NZC * CY), rem = t - i * (NZC * CY), Jc = rem / NZC, x = 3 + rem - Jc * NZC;
+        const float* src = (i == 0) ? cw : (i == M ? cw + NUR * BXC : sz + (i - 1) * NUR * BXC);
+        const float c0 = src[Jc * BXC + x], c1 = src[(Jc + 1) * BXC + x], c2 = src[(Jc + 2) * BXC + x];
+        float* dst = sb + L::bWY + (i * TY + Jc * M) * SXC + x - 3;
+#pragma unroll
+        for (int b = 0; b < M; ++b) dst[b * SXC] = A.ry[b][0] * c0 + A.ry[b][1] * c1 + A.ry[b][2] * c2;
+    }
+    named_sync<NT>(bar);
+    build_vr<M, TY, NT>(cv, sb + L::bUO, sb + L::bWY, sb + L::bVR, rz, hz, A.hy, t0);
+    named_sync<NT>(bar);
 }
 
 // KIND 0: the step; 1: max |divergence| of the dense velocity; 2: max CFL rate.
 // LF: a plain leapfrog step (a = 1, b = 0).
-template <int M, int KIND, bool LF>
-__global__ void __launch_bounds__(kThreadsAll, 4)
+template <int M, int TY, int KIND, bool LF>
+__global__ void __launch_bounds__(FL<M, TY, (KIND != 0)>::THREADS, FL<M, TY, (KIND != 0)>::CTAS)
 k_fused(const __grid_constant__ CUtensorMap tmn, const __grid_constant__ CUtensorMap tmm,
-         const __grid_constant__ CUtensorMap tlc, const FXArgs A)
+        const __grid_constant__ CUtensorMap tlc, const __grid_constant__ CUtensorMap tcu,
+        const __grid_constant__ CUtensorMap tcv, const __grid_constant__ CUtensorMap tcw, const FLArgs A)
 {
-    using L = FX<M>;
-    constexpr int NB = L::NB, BXC = L::BXC, NC = 4 / M, NW = kCons / 32;
     constexpr bool DIVONLY = KIND != 0;
+    using L = FL<M, TY, DIVONLY>;
+    constexpr int NB = L::NB, SXC = L::SXC, NC = 4 / M, NCW = L::NCW, CONS = L::CONS;
     extern __shared__ __align__(128) float sm[];
     float* red = sm + L::oRed;
+    volatile int* s_fail = reinterpret_cast<volatile int*>(sm + L::oRed + 32);
     uint64_t* full = reinterpret_cast<uint64_t*>(sm) + L::oBar;
     uint64_t* empty = full + NB;
+    uint64_t* cfull = empty + NB;
+    uint64_t* cempty = cfull + 2;
+    uint64_t* built = cempty + 2;
+    uint64_t* freed = built + 2;
 
     const Grid<float>& g = A.g;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int i0 = blockIdx.y * kTX, j0 = blockIdx.z * kTY;
+    const int i0 = blockIdx.y * kTX, j0 = blockIdx.z * TY;
     const int I0 = i0 / M, J0 = j0 / M;
     const int K0 = blockIdx.x * A.kcs, K1 = min(K0 + A.kcs, g.nz);
     if (K0 >= K1) return;
@@ -282,250 +310,358 @@ k_fused(const __grid_constant__ CUtensorMap tmn, const __grid_constant__ CUtenso
     if (tid == 0) {
         for (int s = 0; s < NB; ++s) {
             mbar_init(&full[s], 1);
-            mbar_init(&empty[s], kCons);
+            mbar_init(&empty[s], CONS);
         }
+        for (int s = 0; s < 2; ++s) {
+            mbar_init(&cfull[s], 1);
+            mbar_init(&cempty[s], L::NBT);
+            mbar_init(&built[s], L::NBT);
+            mbar_init(&freed[s], CONS);
+        }
+        *s_fail = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     __syncthreads();
 
-    // ---------------------------------------------------------------- producer warp
-    if (warp == NW) {
-        if (lane != 0) return;
-        const bool stopper = (A.stop_ring >= 0 && blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0);
-        for (int r = 0; r < nrings; ++r) {
-            const int s = r % NB;
-            if (stopper && r == A.stop_ring) break;  // every ring issued so far is waited for by the consumers
-            if (r >= NB && !mbar_wait(&empty[s], ((r / NB) - 1) & 1, A.wait_ns)) {
-                atomicExch(A.err, MR_ERR_TIMEOUT);   // consumers then time out on full[]
-                break;
+    int rings_issued = 0, slabs_issued = 0;       // producer lane 0: for the final drain
+    if (warp == NCW) {
+        // ------------------------------------------------------------ producer warp
+        if (lane == 0) {
+            const bool stopper = (A.stop_ring >= 0 && blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0);
+            // the coarse faces of slab K into buffer (K - K0) & 1
+            auto issue_coarse = [&](int K) {
+                const int bb = (K - K0) & 1, use = (K - K0) >> 1;
+                if (use > 0 && !mbar_wait(&cempty[bb], (use - 1) & 1, A.wait_ns)) return false;
+                float* dst = sm + L::oCoarse + bb * L::CBOX;
+                const int wz0 = min(max(K - 1, 0), g.nz - 3);     // first plane of the R_z window
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                mbar_expect_tx(&cfull[bb], L::cu_bytes + L::cv_bytes + L::cw_bytes);
+                tma_3d(dst + L::cU, &tcu, I0, J0, wz0, &cfull[bb]);
+                tma_3d(dst + L::cV, &tcv, I0, J0, wz0, &cfull[bb]);
+                tma_3d(dst + L::cW, &tcw, I0, J0, K, &cfull[bb]);
+                ++slabs_issued;
+                return true;
+            };
+            bool ok = true, stopped = stopper && A.stop_ring == 0;
+            if (!stopped) {
+                ok = issue_coarse(K0);
+                if (ok && K0 + 1 < K1) ok = issue_coarse(K0 + 1);
             }
-            float* slot = sm + s * L::slot;
-            const int p = k0 - 1 + r;
-            const bool lc = (r >= 2);
-            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-            mbar_expect_tx(&full[s], (DIVONLY ? 0u : 2 * L::plane_bytes) + (lc ? (uint32_t)kLCW * 4 : 0u));
-            if (!DIVONLY) {
-                tma_3d(slot + L::oTn, &tmn, i0 - 4, j0 - 1, p, &full[s]);
-                tma_3d(slot + L::oTm, &tmm, i0 - 4, j0 - 1, p, &full[s]);
+            for (int r = 0; ok && !stopped && r < nrings; ++r) {
+                const int s = r % NB;
+                if (stopper && r == A.stop_ring) break;    // every copy issued so far is waited for
+                if (r >= NB && !mbar_wait(&empty[s], ((r / NB) - 1) & 1, A.wait_ns)) {
+                    ok = false;
+                    break;
+                }
+                float* slot = sm + s * L::slot;
+                const int p = k0 - 1 + r;
+                const bool lc = (r >= 2);
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                mbar_expect_tx(&full[s], (DIVONLY ? 0u : 2 * L::plane_bytes) + (lc ? (uint32_t)kLCW * 4 : 0u));
+                if (!DIVONLY) {
+                    tma_3d(slot + L::oTn, &tmn, i0 - 4, j0 - 1, p, &full[s]);
+                    tma_3d(slot + L::oTm, &tmm, i0 - 4, j0 - 1, p, &full[s]);
+                }
+                if (lc) tma_3d(slot + L::oLC, &tlc, 0, p - 1, 0, &full[s]);
+                rings_issued = r + 1;
+                // the first plane of slab K (K > K0) goes out with the coarse faces of slab K + 1
+                if (p > k0 && p < k1 && (p - k0) % M == 0 && p / M + 1 < K1) ok = issue_coarse(p / M + 1);
             }
-            if (lc) tma_3d(slot + L::oLC, &tlc, 0, p - 1, 0, &full[s]);
+            if (!ok) *s_fail = 1;
         }
-        return;
-    }
-
-    // ---------------------------------------------------------------- consumer warps
-    // this thread's 4-cell segment of dense row jl (half-warps on rows two apart)
-    const int seg = tid & 15, jl = ((warp >> 1) << 2) + (warp & 1) + 2 * ((tid >> 4) & 1);
-    const int il0 = seg * 4, cb0 = il0 / M;      // first coarse column of the segment (tile-local)
-    const auto& rx = A.rx;
-    const bool wrap_w = (i0 == 0 && seg == 0), wrap_e = (i0 + kTX == g.Nx && seg == 15);
-    const bool wrap_s = (j0 == 0 && jl == 0), wrap_n = (j0 + kTY == g.Ny && jl == kTY - 1);
-
-    bool fail = false;
-    float dmax = 0.f;
-    const float kx2 = g.kx2, ky2 = g.ky2;
-    const float ca = A.a, cbb = A.b, gdt = A.gdt;
-    const float2 kx2p = make_float2(kx2, kx2), ky2p = make_float2(ky2, ky2), gdtp = make_float2(gdt, gdt);
-    const float2 cap = make_float2(ca, ca), cbp = make_float2(cbb, cbb);
-    // PK: the update runs on packed pairs of cells (0, 1), (2, 3); vn then holds
-    // the negated V split, the sign its flux enters with
-    constexpr bool PK = !DIVONLY;
-    const size_t plane = (size_t)g.Nx * g.Ny;
-    float* outp = A.Tp1 + (size_t)k0 * plane + (size_t)(j0 + jl) * g.Nx + i0 + il0;
-    const int o = (jl + 1) * kBX + il0 + 4;      // this segment's first cell in a plane box
-    const float* sWY = sm + L::oWY;
-    const float* sUO = sm + L::oUO;
-    const float* sVR = sm + L::oVR;
-
-    if (tid < 3 * kTY) sm[L::oRy + tid] = g.Ry[3 * j0 + tid];   // the tile's R_y rows (read after a barrier)
-    float wcar[4] = {0.f, 0.f, 0.f, 0.f};        // R_x split of W on plane k (from layer k-1)
-    // rings 0 and 1 (planes k0-1, k0) before the layer loop; then layer k waits
-    // for the ring of plane k+1 only
-    for (int r = 0; r < 2; ++r)
-        if (!fail && !mbar_wait(&full[r], 0, A.wait_ns)) fail = true;
-    // one layer; sb, sc, st: the ring slots of planes k-1, k, k+1, tpar: the
-    // parity of the ring of plane k+1
-    auto layer = [&](const int k, const int sb, const int sc, const int st, const int tpar) {
-        const int K = k / M, i = k - K * M;
-        if (i == 0) {
-            // the previous slab's intermediates are no longer read: build this slab's
-            asm volatile("barrier.cta.sync 1, %0;" ::"n"(kCons) : "memory");
-            slab_prep<M>(A, sm, K, I0, J0, j0, tid);
-        }
-        // the ring of plane k+1 and of this layer's constants
-        if (!fail && !mbar_wait(&full[st], tpar, A.wait_ns)) fail = true;
+    } else if (warp > NCW) {
+        // ------------------------------------------------------------ builder warps
+        const int bt = tid - CONS - 32;              // 0 .. NBT-1
+        // the chunk's first slab, with the consumers
+        bool fail = !mbar_wait(&cfull[0], 0, A.wait_ns);
+        fail = named_or<CONS + L::NBT>(3, fail);
+        if (!fail)
+            build_slab<M, TY, CONS + L::NBT>(A, sm + L::oCoarse, sm + L::oSlab, sm + L::oZ, A.sc + (size_t)K0 * kSCW,
+                                             CONS + bt, 3);
         if (!fail) {
-            const float* lcp = sm + st * L::slot + L::oLC;
-            const float2 c0 = *reinterpret_cast<const float2*>(lcp);
-            const float inv_dz = c0.x, hz = c0.y;
-            float wb[4], wt[4], vs[4], vn[4], us[5];
-            {
-                // R_x splits of the full-width W (planes k, k+1) and V (faces jl, jl+1)
-                const float* yb = sWY + (i * kTY + jl) * BXC + cb0 + 3;
-                const float* yt = yb + kTY * BXC;
-                const float* rs = sVR + (i * (kTY + 1) + jl) * BXC + cb0 + 3;
-                const float* rn = rs + BXC;
-                const float* ur = sUO + (i * kTY + jl) * BXC + cb0 + 4;   // outer face of coarse column cb0
-                constexpr int NV = NC + 2;
-                float ytv[NV], rsv[NV], rnv[NV], urv[NC + 1];
-                if (k == k0) {
+            mbar_arrive(&cempty[0]);
+            mbar_arrive(&built[0]);
+        }
+        for (int K = K0 + 1; K < K1 && !fail; ++K) {
+            const int bb = (K - K0) & 1, use = (K - K0) >> 1;
+            bool f = !mbar_wait(&cfull[bb], use & 1, A.wait_ns);
+            if (!f && use > 0) f = !mbar_wait(&freed[bb], (use - 1) & 1, A.wait_ns);
+            fail = named_or<L::NBT>(2, f);
+            if (fail) break;
+            build_slab<M, TY, L::NBT>(A, sm + L::oCoarse + bb * L::CBOX, sm + L::oSlab + bb * L::SLAB, sm + L::oZ,
+                                      A.sc + (size_t)K * kSCW, bt, 2);
+            mbar_arrive(&cempty[bb]);
+            mbar_arrive(&built[bb]);
+        }
+        if (fail && bt == 0) *s_fail = 1;
+    } else {
+        // ------------------------------------------------------------ consumer warps
+        // this thread's 4-cell segment of dense row jl; the half-warps take rows
+        // four apart (slab rows 4 SXC floats apart fall 16 banks apart, so the
+        // half-warps' coarse-column reads do not conflict)
+        const int seg = tid & 15, jl = ((warp >> 2) << 3) + (warp & 3) + 4 * ((tid >> 4) & 1);
+        const int il0 = seg * 4, cb0 = il0 / M;      // first coarse column of the segment (tile-local)
+        const auto& rx = A.rx;
+        const bool wrap_w = (i0 == 0 && seg == 0), wrap_e = (i0 + kTX == g.Nx && seg == 15);
+        const bool wrap_s = (j0 == 0 && jl == 0), wrap_n = (j0 + TY == g.Ny && jl == TY - 1);
+        bool fail = false;
+        float dmax = 0.f;
+        const float kx2 = g.kx2, ky2 = g.ky2;
+        const float ca = A.a, cbb = A.b, gdt = A.gdt;
+        const float2 kx2p = make_float2(kx2, kx2), ky2p = make_float2(ky2, ky2), gdtp = make_float2(gdt, gdt);
+        const float2 cap = make_float2(ca, ca), cbp = make_float2(cbb, cbb);
+        // PK: the update runs on packed pairs of cells (0, 1), (2, 3); vn then
+        // holds the negated V split, the sign its flux enters with
+        constexpr bool PK = !DIVONLY;
+        const size_t plane = (size_t)g.Nx * g.Ny;
+        float* outp = A.Tp1 + (size_t)k0 * plane + (size_t)(j0 + jl) * g.Nx + i0 + il0;
+        const int o = (jl + 1) * kBX + il0 + 4;      // this segment's first cell in a plane box
+        float wcar[4] = {0.f, 0.f, 0.f, 0.f};        // R_x split of W on plane k (from layer k-1)
+        // the chunk's first slab, with the builder warps
+        fail = !mbar_wait(&cfull[0], 0, A.wait_ns);
+        fail = named_or<CONS + L::NBT>(3, fail);
+        if (!fail)
+            build_slab<M, TY, CONS + L::NBT>(A, sm + L::oCoarse, sm + L::oSlab, sm + L::oZ, A.sc + (size_t)K0 * kSCW,
+                                             tid, 3);
+        for (int r = 0; r < 2; ++r)
+            if (!fail && !mbar_wait(&full[r], 0, A.wait_ns)) fail = true;
+        // one layer; sb, sc, st: the ring slots of planes k-1, k, k+1; tpar: the
+        // parity of the ring of plane k+1
+        auto layer = [&](const int k, const int sb, const int sc, const int st, const int tpar) {
+            const int i = k & (M - 1), Kr = (k - k0) / M, bb = Kr & 1;
+            if (i == 0 && Kr > 0 && !fail && !mbar_wait(&built[bb], (Kr >> 1) & 1, A.wait_ns)) fail = true;
+            if (!fail && !mbar_wait(&full[st], tpar, A.wait_ns)) fail = true;
+            if (!fail) {
+                const float* slab = sm + L::oSlab + bb * L::SLAB;
+                const float* lcp = sm + st * L::slot + L::oLC;
+                const float2 c0 = *reinterpret_cast<const float2*>(lcp);
+                const float inv_dz = c0.x, hz = c0.y;
+                float wb[4], wt[4], vs[4], vn[4], us[5];
+                {
+                    // R_x splits of the full-width W (planes k, k+1) and V (faces jl, jl+1)
+                    // slab column c holds coarse column I0 - 1 + c
+                    const float* yt = slab + L::bWY + ((i + 1) * TY + jl) * SXC + cb0;
+                    const float* rs = slab + L::bVR + (i * (TY + 1) + jl) * SXC + cb0;
+                    const float* rn = rs + SXC;
+                    const float* ur = slab + L::bUO + (i * TY + jl) * SXC + cb0 + 1;   // outer face of column cb0
+                    constexpr int NV = NC + 2;
+                    float ytv[NV], rsv[NV], rnv[NV], urv[NC + 1];
+                    if (k == k0) {
+                        const float* yb = slab + L::bWY + jl * SXC + cb0;            // plane k0 (i = 0)
+#pragma unroll
+                        for (int a = 0; a < 4; ++a) {
+                            const int cb = a / M;
+                            wcar[a] = rsplit3(rx[a], yb[cb], yb[cb + 1], yb[cb + 2]);
+                        }
+                    }
+#pragma unroll
+                    for (int c = 0; c < NV; ++c) {
+                        ytv[c] = yt[c];
+                        rsv[c] = rs[c];
+                        rnv[c] = rn[c];
+                    }
+#pragma unroll
+                    for (int q = 0; q <= NC; ++q) urv[q] = ur[q];
 #pragma unroll
                     for (int a = 0; a < 4; ++a) {
                         const int cb = a / M;
-                        wcar[a] = rsplit3(rx[a], yb[cb], yb[cb + 1], yb[cb + 2]);
+                        wb[a] = wcar[a];
+                        wt[a] = rsplit3(rx[a], ytv[cb], ytv[cb + 1], ytv[cb + 2]);
+                        vs[a] = rsplit3(rx[a], rsv[cb], rsv[cb + 1], rsv[cb + 2]);
+                        vn[a] = PK ? nrsplit3(rx[a], rnv[cb], rnv[cb + 1], rnv[cb + 2])
+                                   : rsplit3(rx[a], rnv[cb], rnv[cb + 1], rnv[cb + 2]);
                     }
-                }
+                    // stage X: cell balance, west to east, in units of U / (2 dx)
 #pragma unroll
-                for (int c = 0; c < NV; ++c) {
-                    ytv[c] = yt[c];
-                    rsv[c] = rs[c];
-                    rnv[c] = rn[c];
-                }
+                    for (int q = 0; q < NC; ++q) {
+                        float h = urv[q];
+                        us[q * M] = h;
 #pragma unroll
-                for (int q = 0; q <= NC; ++q) urv[q] = ur[q];
-#pragma unroll
-                for (int a = 0; a < 4; ++a) {
-                    const int cb = a / M;
-                    wb[a] = wcar[a];
-                    wt[a] = rsplit3(rx[a], ytv[cb], ytv[cb + 1], ytv[cb + 2]);
-                    vs[a] = rsplit3(rx[a], rsv[cb], rsv[cb + 1], rsv[cb + 2]);
-                    vn[a] = PK ? nrsplit3(rx[a], rnv[cb], rnv[cb + 1], rnv[cb + 2])
-                               : rsplit3(rx[a], rnv[cb], rnv[cb + 1], rnv[cb + 2]);
-                }
-                // stage X: cell balance, west to east, in units of U / (2 dx)
-#pragma unroll
-                for (int q = 0; q < NC; ++q) {
-                    float h = urv[q];
-                    us[q * M] = h;
-#pragma unroll
-                    for (int a = 0; a < M - 1; ++a) {
-                        const int m = q * M + a;
-                        h = (PK ? h + (vn[m] + vs[m]) : h - (vn[m] - vs[m])) - (wt[m] - wb[m]) * hz;
-                        us[m + 1] = h;
+                        for (int a = 0; a < M - 1; ++a) {
+                            const int m = q * M + a;
+                            h = (PK ? h + (vn[m] + vs[m]) : h - (vn[m] - vs[m])) - (wt[m] - wb[m]) * hz;
+                            us[m + 1] = h;
+                        }
                     }
-                }
-                us[4] = urv[NC];
+                    us[4] = urv[NC];
 #pragma unroll
-                for (int a = 0; a < 4; ++a) wcar[a] = wt[a];
+                    for (int a = 0; a < 4; ++a) wcar[a] = wt[a];
+                }
+                if (DIVONLY) {
+#pragma unroll
+                    for (int a = 0; a < 4; ++a) {
+                        const float d = KIND == 2 ? 2.f * (fmaxf(fabsf(us[a]), fabsf(us[a + 1])) +
+                                                           fmaxf(fabsf(vs[a]), fabsf(vn[a]))) +
+                                                        fmaxf(fabsf(wb[a]), fabsf(wt[a])) * inv_dz
+                                                  : 2.f * ((us[a + 1] - us[a]) + (vn[a] - vs[a])) +
+                                                        (wt[a] - wb[a]) * inv_dz;
+                        dmax = fmaxf(dmax, fabsf(d));
+                    }
+                } else {
+                    const float* Pn_b = sm + sb * L::slot + L::oTn;
+                    const float* Pm_b = sm + sb * L::slot + L::oTm;
+                    const float* Pn_c = sm + sc * L::slot + L::oTn;
+                    const float* Pm_c = sm + sc * L::slot + L::oTm;
+                    const float* Pn_t = sm + st * L::slot + L::oTn;
+                    const float* Pm_t = sm + st * L::slot + L::oTm;
+                    const float4 tc4 = *reinterpret_cast<const float4*>(Pn_c + o);
+                    float4 ts4 = *reinterpret_cast<const float4*>(Pn_c + o - kBX);
+                    float4 tn4 = *reinterpret_cast<const float4*>(Pn_c + o + kBX);
+                    const float4 dc4 = *reinterpret_cast<const float4*>(Pm_c + o);
+                    float4 ds4 = *reinterpret_cast<const float4*>(Pm_c + o - kBX);
+                    float4 dn4 = *reinterpret_cast<const float4*>(Pm_c + o + kBX);
+                    float tw = __shfl_up_sync(0xffffffffu, tc4.w, 1), te = __shfl_down_sync(0xffffffffu, tc4.x, 1);
+                    float dw = __shfl_up_sync(0xffffffffu, dc4.w, 1), de = __shfl_down_sync(0xffffffffu, dc4.x, 1);
+                    if (seg == 0) { tw = Pn_c[o - 1]; dw = Pm_c[o - 1]; }
+                    if (seg == 15) { te = Pn_c[o + 4]; de = Pm_c[o + 4]; }
+                    if (wrap_w | wrap_e | wrap_s | wrap_n) {
+                        // the box holds zeros beyond the domain: fetch the periodic images
+                        const float* gn = A.Tn + (size_t)k * plane;
+                        const float* gm = A.Tm + (size_t)k * plane;
+                        const size_t row = (size_t)(j0 + jl) * g.Nx;
+                        if (wrap_w) { tw = gn[row + g.Nx - 1]; dw = gm[row + g.Nx - 1]; }
+                        if (wrap_e) { te = gn[row]; de = gm[row]; }
+                        // rows beyond the y edges: periodic images, or a y-slab's halo rows
+                        const size_t hrow = (size_t)k * A.hstride + i0 + il0;
+                        if (wrap_s) {
+                            ts4 = *reinterpret_cast<const float4*>(A.hs[0] + hrow);
+                            ds4 = *reinterpret_cast<const float4*>(A.hs[1] + hrow);
+                        }
+                        if (wrap_n) {
+                            tn4 = *reinterpret_cast<const float4*>(A.hn[0] + hrow);
+                            dn4 = *reinterpret_cast<const float4*>(A.hn[1] + hrow);
+                        }
+                    }
+                    // planes below / above: zero-filled beyond the plates, where W is zero
+                    // and the plate value enters D through `plate`
+                    const float4 tb4 = *reinterpret_cast<const float4*>(Pn_b + o);
+                    const float4 db4 = *reinterpret_cast<const float4*>(Pm_b + o);
+                    const float4 tt4 = *reinterpret_cast<const float4*>(Pn_t + o);
+                    const float4 dt4 = *reinterpret_cast<const float4*>(Pm_t + o);
+                    const float tcv[6] = {tw, tc4.x, tc4.y, tc4.z, tc4.w, te};
+                    const float dcv[6] = {dw, dc4.x, dc4.y, dc4.z, dc4.w, de};
+                    // x fluxes in scalar form (adjacent cells share a face), then the
+                    // rest on the pairs (0, 1), (2, 3) with the pair constants of the row:
+                    // D = kx2 (dw + de) + ky2 (ds + dn) + cdn db + cup dt - diag dc + plate
+                    const float4 q0 = *reinterpret_cast<const float4*>(lcp + 12);   // bwlo, bwhi
+                    const float4 q1 = *reinterpret_cast<const float4*>(lcp + 16);   // -twlo, -twhi
+                    const float4 q2 = *reinterpret_cast<const float4*>(lcp + 20);   // cdn, cup
+                    const float4 q3 = *reinterpret_cast<const float4*>(lcp + 24);   // -diag, plate
+                    float F[5], cxv[4], sdx[4];
+#pragma unroll
+                    for (int a = 0; a < 5; ++a) F[a] = us[a] * (tcv[a] + tcv[a + 1]);
+#pragma unroll
+                    for (int a = 0; a < 4; ++a) {
+                        cxv[a] = F[a] - F[a + 1];
+                        sdx[a] = dcv[a] + dcv[a + 2];
+                    }
+                    float2 res[2];
+#pragma unroll
+                    for (int h = 0; h < 2; ++h) {
+                        const float2 tc = h ? hi2(tc4) : lo2(tc4), dc = h ? hi2(dc4) : lo2(dc4);
+                        const float2 ts = h ? hi2(ts4) : lo2(ts4), tn = h ? hi2(tn4) : lo2(tn4);
+                        const float2 ds = h ? hi2(ds4) : lo2(ds4), dn = h ? hi2(dn4) : lo2(dn4);
+                        const float2 tb = h ? hi2(tb4) : lo2(tb4), tt = h ? hi2(tt4) : lo2(tt4);
+                        const float2 db = h ? hi2(db4) : lo2(db4), dt = h ? hi2(dt4) : lo2(dt4);
+                        const int a = 2 * h;
+                        float2 acc = fma2(kx2p, make_float2(sdx[a], sdx[a + 1]), hi2(q3));
+                        acc = fma2(ky2p, add2(ds, dn), acc);
+                        acc = fma2(lo2(q2), db, acc);
+                        acc = fma2(hi2(q2), dt, acc);
+                        acc = fma2(lo2(q3), dc, acc);
+                        acc = add2(acc, make_float2(cxv[a], cxv[a + 1]));
+                        acc = fma2(make_float2(vs[a], vs[a + 1]), add2(ts, tc), acc);
+                        acc = fma2(make_float2(vn[a], vn[a + 1]), add2(tc, tn), acc);
+                        acc = fma2(make_float2(wb[a], wb[a + 1]), fma2(lo2(q0), tb, mul2(hi2(q0), tc)), acc);
+                        acc = fma2(make_float2(wt[a], wt[a + 1]), fma2(lo2(q1), tc, mul2(hi2(q1), tt)), acc);
+                        res[h] = LF ? fma2(gdtp, acc, dc) : fma2(gdtp, acc, fma2(cap, dc, mul2(cbp, tc)));
+                    }
+                    *reinterpret_cast<float4*>(outp) = make_float4(res[0].x, res[0].y, res[1].x, res[1].y);
+                }
             }
-            if (DIVONLY) {
+            // plane k-1 is no longer needed by this thread; nor, after the
+            // slab's last layer, the slab's intermediates
+            mbar_arrive(&empty[sb]);
+            if (i == M - 1) mbar_arrive(&freed[bb]);
+            outp += plane;
+        };
+        if constexpr (!DIVONLY) {
+            // unrolled by the ring length: layer k0 + u uses the slots u, u+1, u+2 (mod NB)
+            for (int kb = k0, opar = 0; kb < k1; kb += NB, opar ^= 1) {
 #pragma unroll
-                for (int a = 0; a < 4; ++a) {
-                    const float d = KIND == 2 ? 2.f * (fmaxf(fabsf(us[a]), fabsf(us[a + 1])) + fmaxf(fabsf(vs[a]), fabsf(vn[a]))) +
-                                                    fmaxf(fabsf(wb[a]), fabsf(wt[a])) * inv_dz
-                                              : 2.f * ((us[a + 1] - us[a]) + (vn[a] - vs[a])) + (wt[a] - wb[a]) * inv_dz;
-                    dmax = fmaxf(dmax, fabsf(d));
+                for (int u = 0; u < NB; ++u) {
+                    if (kb + u >= k1) break;
+                    layer(kb + u, u % NB, (u + 1) % NB, (u + 2) % NB, opar ^ (((u + 2) / NB) & 1));
                 }
-            } else {
-                const float* Pn_b = sm + sb * L::slot + L::oTn;
-                const float* Pm_b = sm + sb * L::slot + L::oTm;
-                const float* Pn_c = sm + sc * L::slot + L::oTn;
-                const float* Pm_c = sm + sc * L::slot + L::oTm;
-                const float* Pn_t = sm + st * L::slot + L::oTn;
-                const float* Pm_t = sm + st * L::slot + L::oTm;
-                const float4 tc4 = *reinterpret_cast<const float4*>(Pn_c + o);
-                float4 ts4 = *reinterpret_cast<const float4*>(Pn_c + o - kBX);
-                float4 tn4 = *reinterpret_cast<const float4*>(Pn_c + o + kBX);
-                const float4 dc4 = *reinterpret_cast<const float4*>(Pm_c + o);
-                float4 ds4 = *reinterpret_cast<const float4*>(Pm_c + o - kBX);
-                float4 dn4 = *reinterpret_cast<const float4*>(Pm_c + o + kBX);
-                float tw = __shfl_up_sync(0xffffffffu, tc4.w, 1), te = __shfl_down_sync(0xffffffffu, tc4.x, 1);
-                float dw = __shfl_up_sync(0xffffffffu, dc4.w, 1), de = __shfl_down_sync(0xffffffffu, dc4.x, 1);
-                if (seg == 0) { tw = Pn_c[o - 1]; dw = Pm_c[o - 1]; }
-                if (seg == 15) { te = Pn_c[o + 4]; de = Pm_c[o + 4]; }
-                if (wrap_w | wrap_e | wrap_s | wrap_n) {
-                    // the box holds zeros beyond the domain: fetch the periodic images
-                    const float* gn = A.Tn + (size_t)k * plane;
-                    const float* gm = A.Tm + (size_t)k * plane;
-                    const size_t row = (size_t)(j0 + jl) * g.Nx;
-                    if (wrap_w) { tw = gn[row + g.Nx - 1]; dw = gm[row + g.Nx - 1]; }
-                    if (wrap_e) { te = gn[row]; de = gm[row]; }
-                    if (wrap_s) {
-                        const size_t r2 = (size_t)(g.Ny - 1) * g.Nx + i0 + il0;
-                        ts4 = *reinterpret_cast<const float4*>(gn + r2);
-                        ds4 = *reinterpret_cast<const float4*>(gm + r2);
-                    }
-                    if (wrap_n) {
-                        tn4 = *reinterpret_cast<const float4*>(gn + i0 + il0);
-                        dn4 = *reinterpret_cast<const float4*>(gm + i0 + il0);
-                    }
+            }
+        } else {
+            int sb = 0, sc = 1, st = 2, tpar = 0;
+            for (int k = k0; k < k1; ++k) {
+                layer(k, sb, sc, st, tpar);
+                sb = sc;
+                sc = st;
+                if (++st == NB) {
+                    st = 0;
+                    tpar ^= 1;
                 }
-                // planes below / above: zero-filled beyond the plates, where W is zero
-                // and the plate value enters D through `plate`
-                const float4 tb4 = *reinterpret_cast<const float4*>(Pn_b + o);
-                const float4 db4 = *reinterpret_cast<const float4*>(Pm_b + o);
-                const float4 tt4 = *reinterpret_cast<const float4*>(Pn_t + o);
-                const float4 dt4 = *reinterpret_cast<const float4*>(Pm_t + o);
-                const float tcv[6] = {tw, tc4.x, tc4.y, tc4.z, tc4.w, te};
-                const float dcv[6] = {dw, dc4.x, dc4.y, dc4.z, dc4.w, de};
-                // x fluxes in scalar form (adjacent cells share a face), then the
-                // rest on the pairs (0, 1), (2, 3) with the pair constants of the row:
-                // D = kx2 (dw + de) + ky2 (ds + dn) + cdn db + cup dt - diag dc + plate
-                const float4 q0 = *reinterpret_cast<const float4*>(lcp + 12);   // bwlo, bwhi
-                const float4 q1 = *reinterpret_cast<const float4*>(lcp + 16);   // -twlo, -twhi
-                const float4 q2 = *reinterpret_cast<const float4*>(lcp + 20);   // cdn, cup
-                const float4 q3 = *reinterpret_cast<const float4*>(lcp + 24);   // -diag, plate
-                float F[5], cxv[4], sdx[4];
-#pragma unroll
-                for (int a = 0; a < 5; ++a) F[a] = us[a] * (tcv[a] + tcv[a + 1]);
-#pragma unroll
-                for (int a = 0; a < 4; ++a) {
-                    cxv[a] = F[a] - F[a + 1];
-                    sdx[a] = dcv[a] + dcv[a + 2];
-                }
-                float2 res[2];
-#pragma unroll
-                for (int h = 0; h < 2; ++h) {
-                    const float2 tc = h ? hi2(tc4) : lo2(tc4), dc = h ? hi2(dc4) : lo2(dc4);
-                    const float2 ts = h ? hi2(ts4) : lo2(ts4), tn = h ? hi2(tn4) : lo2(tn4);
-                    const float2 ds = h ? hi2(ds4) : lo2(ds4), dn = h ? hi2(dn4) : lo2(dn4);
-                    const float2 tb = h ? hi2(tb4) : lo2(tb4), tt = h ? hi2(tt4) : lo2(tt4);
-                    const float2 db = h ? hi2(db4) : lo2(db4), dt = h ? hi2(dt4) : lo2(dt4);
-                    const int a = 2 * h;
-                    float2 acc = fma2(kx2p, make_float2(sdx[a], sdx[a + 1]), hi2(q3));
-                    acc = fma2(ky2p, add2(ds, dn), acc);
-                    acc = fma2(lo2(q2), db, acc);
-                    acc = fma2(hi2(q2), dt, acc);
-                    acc = fma2(lo2(q3), dc, acc);
-                    acc = add2(acc, make_float2(cxv[a], cxv[a + 1]));
-                    acc = fma2(make_float2(vs[a], vs[a + 1]), add2(ts, tc), acc);
-                    acc = fma2(make_float2(vn[a], vn[a + 1]), add2(tc, tn), acc);
-                    acc = fma2(make_float2(wb[a], wb[a + 1]), fma2(lo2(q0), tb, mul2(hi2(q0), tc)), acc);
-                    acc = fma2(make_float2(wt[a], wt[a + 1]), fma2(lo2(q1), tc, mul2(hi2(q1), tt)), acc);
-                    res[h] = LF ? fma2(gdtp, acc, dc) : fma2(gdtp, acc, fma2(cap, dc, mul2(cbp, tc)));
-                }
-                *reinterpret_cast<float4*>(outp) = make_float4(res[0].x, res[0].y, res[1].x, res[1].y);
             }
         }
-        // plane k-1 is no longer needed by this thread
-        mbar_arrive(&empty[sb]);
-        outp += plane;
-    };
-    // the slots rotate (a loop unrolled by the ring length would copy the slab
-    // build into every layer and outgrow the instruction cache)
-    int sb = 0, sc = 1, st = 2, tpar = 0;
-    for (int k = k0; k < k1; ++k) {
-        layer(k, sb, sc, st, tpar);
-        sb = sc;
-        sc = st;
-        if (++st == NB) {
-            st = 0;
-            tpar ^= 1;
+        if (fail) *s_fail = 1;
+        if (DIVONLY) {
+            for (int d = 16; d > 0; d >>= 1) dmax = fmaxf(dmax, __shfl_down_sync(0xffffffffu, dmax, d));
+            if (lane == 0) red[warp] = dmax;
         }
     }
-    if (consumers_sync_or<kCons>(fail)) {
-        if (tid == 0) atomicExch(A.err, MR_ERR_TIMEOUT);
-        return;
-    }
-    if (DIVONLY) {
-        for (int d = 16; d > 0; d >>= 1) dmax = fmaxf(dmax, __shfl_down_sync(0xffffffffu, dmax, d));
-        if (lane == 0) red[warp] = dmax;
-        consumers_sync<kCons>();
-        if (tid == 0) {
-            float m = 0.f;
-            for (int w = 0; w < NW; ++w) m = fmaxf(m, red[w]);
-            atomicMax(A.divmax, (unsigned long long)__double_as_longlong((double)m));
+    __syncthreads();
+    if (warp == NCW && lane == 0) {
+        // no copy may still be in flight when the CTA exits: wait for the last
+        // phase issued on every ring slot and coarse buffer (already complete
+        // unless a wait gave up)
+        bool ok = true;
+        for (int s = 0; s < NB && s < rings_issued; ++s) {
+            const int last = s + NB * ((rings_issued - 1 - s) / NB);
+            ok &= mbar_wait(&full[s], (last / NB) & 1, A.wait_ns);
         }
+        for (int bb = 0; bb < 2 && bb < slabs_issued; ++bb) {
+            const int last = bb + 2 * ((slabs_issued - 1 - bb) / 2);
+            ok &= mbar_wait(&cfull[bb], (last >> 1) & 1, A.wait_ns);
+        }
+        if (!ok || *s_fail) atomicExch(A.err, MR_ERR_TIMEOUT);
+    }
+    if (DIVONLY && tid == 0 && !*s_fail) {
+        float m = 0.f;
+        for (int w = 0; w < NCW; ++w) m = fmaxf(m, red[w]);
+        atomicMax(A.divmax, (unsigned long long)__double_as_longlong((double)m));
+    }
+}
+
+// The coarse faces padded with their periodic images: U and W with one ghost
+// row each side in y, V with one below and two above, all with four ghost
+// columns each side in x, so that every coarse box of k_fused is in bounds and
+// starts on a 16-byte boundary.  out: padded U, V, W one after the other, for
+// the ny coarse rows from j0 of a domain of nyg rows (a y-slab: its padded
+// rows come from the neighbouring slabs' rows).
+__global__ void k_pad_coarse(const float* __restrict__ U, const float* __restrict__ V, const float* __restrict__ W,
+                             float* __restrict__ out, int nx, int nyg, int nz, int j0, int ny)
+{
+    const int px = nx + 8;
+    const size_t nU = (size_t)nz * (ny + 2) * px, nV = (size_t)nz * (ny + 3) * px, nW = (size_t)(nz + 1) * (ny + 2) * px;
+    for (size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x; t < nU + nV + nW;
+         t += (size_t)gridDim.x * blockDim.x) {
+        const float* src;
+        size_t e;
+        int rows;
+        if (t < nU) { src = U; e = t; rows = ny + 2; }
+        else if (t < nU + nV) { src = V; e = t - nU; rows = ny + 3; }
+        else { src = W; e = t - nU - nV; rows = ny + 2; }
+        const int x = (int)(e % px);
+        const size_t zr = e / px;
+        const int r = (int)(zr % rows), z = (int)(zr / rows);
+        int I = x - 4, J = j0 + r - 1;
+        I = I < 0 ? I + nx : (I >= nx ? I - nx : I);
+        J = J < 0 ? J + nyg : (J >= nyg ? J - nyg : J);
+        out[t] = src[((size_t)z * nyg + J) * nx + I];
     }
 }
 
@@ -551,7 +687,7 @@ EncodeTiledFn encode_fn()
 bool map_fx(CUtensorMap* out, const float* base, int d0, int d1, int d2, int b0, int b1, int b2)
 {
     struct Entry { const float* p; int d[6]; CUtensorMap m; };
-    static Entry cache[16];
+    static Entry cache[32];
     static int n = 0, next = 0;
     static std::mutex mu;
     const int key[6] = {d0, d1, d2, b0, b1, b2};
@@ -574,61 +710,154 @@ bool map_fx(CUtensorMap* out, const float* base, int d0, int d1, int d2, int b0,
         CUDA_SUCCESS)
         return false;
     std::lock_guard<std::mutex> lock(mu);
-    Entry& e = cache[n < 16 ? n++ : (next = (next + 1) % 16)];
+    Entry& e = cache[n < 32 ? n++ : (next = (next + 1) % 32)];
     e.p = base;
     memcpy(e.d, key, sizeof key);
     e.m = *out;
     return true;
 }
 
-template <int M, int KIND, bool LF>
-cudaError_t launch_fx(const Grid<float>& g, const float* U, const float* V, const float* W, const float* lc,
-                      const float* rx12, const float* Tm1, const float* T, float* Tp1, StepCoef c, int* err,
-                      unsigned long long* divmax, cudaStream_t st)
+// Tile height: 64x16 tiles (two CTAs per SM) at M = 4 (measured on 512 x 512 x
+// 384: 0.432 ms per step against 0.491 on 64x8 tiles; 1536 x 1536 x 1024: 8.77
+// against 10.2 ms), 64x8 at M = 2 (its 64x16 layout would not fit two CTAs per
+// SM).
+int fused_tile_rows(const Grid<float>& g)
 {
-    using L = FX<M>;
+#ifdef MR_FUSED_TY
+    if (g.mx == 4) return MR_FUSED_TY;    // compile-time override for tuning sweeps
+#endif
+    return g.mx == 4 ? 16 : 8;
+}
+
+template <int M, int TY, int KIND, bool LF>
+cudaError_t launch_fl(const Grid<float>& g, const FusedInputs& in, const float* Tm1, const float* T, float* Tp1,
+                      StepCoef c, int* err, unsigned long long* divmax, cudaStream_t st)
+{
+    using L = FL<M, TY, (KIND != 0)>;
     static unsigned long long attr = 0;                   // one bit per device
-    cudaError_t e = smem_optin(reinterpret_cast<const void*>(k_fused<M, KIND, LF>), (int)L::bytes, &attr);
+    cudaError_t e = smem_optin(reinterpret_cast<const void*>(k_fused<M, TY, KIND, LF>), (int)L::bytes, &attr);
     if (e != cudaSuccess) return e;
-    CUtensorMap mn, mm, mlc;
+    CUtensorMap mn, mm, mlc, mu, mv, mw;
     memset(&mn, 0, sizeof mn);
     memset(&mm, 0, sizeof mm);
-    if (KIND == 0 && (!map_fx(&mn, T, g.Nx, g.Ny, g.Nz, kBX, kBY, 1) || !map_fx(&mm, Tm1, g.Nx, g.Ny, g.Nz, kBX, kBY, 1)))
+    if (KIND == 0 && (!map_fx(&mn, T, g.Nx, g.Ny, g.Nz, kBX, L::kBY, 1) ||
+                      !map_fx(&mm, Tm1, g.Nx, g.Ny, g.Nz, kBX, L::kBY, 1)))
         return cudaErrorInvalidValue;
-    if (!map_fx(&mlc, lc, kLCW, g.Nz, 1, kLCW, 1, 1)) return cudaErrorInvalidValue;
-    // ~12 waves of four CTAs per SM, chunks of at most 96 dense layers
-    const int tiles = (g.Nx / kTX) * (g.Ny / kTY);
-    const int want = 152 * 4 * 12;
+    const int px = g.nx + 8;
+    const float* pU = in.pad;
+    const float* pV = pU + (size_t)g.nz * (g.ny + 2) * px;
+    const float* pW = pV + (size_t)g.nz * (g.ny + 3) * px;
+    if (!map_fx(&mlc, in.lc, kLCW, g.Nz, 1, kLCW, 1, 1) || !map_fx(&mu, pU, px, g.ny + 2, g.nz, L::BXC, L::NUR, 3) ||
+        !map_fx(&mv, pV, px, g.ny + 3, g.nz, L::BXC, L::NVR, 3) ||
+        !map_fx(&mw, pW, px, g.ny + 2, g.nz + 1, L::BXC, L::NUR, 2))
+        return cudaErrorInvalidValue;
+    // ~12 waves of resident CTAs, chunks of at most 96 dense layers
+#ifndef MR_FUSED_WAVES
+#define MR_FUSED_WAVES 12                 // compile-time override for tuning sweeps
+#endif
+    const int tiles = (g.Nx / kTX) * (g.Ny / TY);
+    const int want = 152 * L::CTAS * MR_FUSED_WAVES;
     int chunks = max(1, min((want + tiles - 1) / tiles, g.nz));
     int kcs = (g.nz + chunks - 1) / chunks;
     kcs = max(1, min(kcs, 96 / M));
     chunks = (g.nz + kcs - 1) / kcs;
-    FXArgs A{g, U, V, W, T, Tm1, Tp1, (float)c.a, (float)c.b, (float)c.gdt, kcs, err, divmax, {}, ptx::kWaitNs, -1};
-    memcpy(A.rx, rx12, sizeof A.rx);
-    if (KIND == 0) take_wait_injection(&A.stop_ring, &A.wait_ns);
-    dim3 grid(chunks, g.Nx / kTX, g.Ny / kTY);
-    k_fused<M, KIND, LF><<<grid, kThreadsAll, L::bytes, st>>>(mn, mm, mlc, A);
+    FLArgs A;
+    memset(&A, 0, sizeof A);
+    A.g = g;
+    A.Tn = T;
+    A.Tm = Tm1;
+    A.Tp1 = Tp1;
+    A.sc = in.sc;
+    A.a = (float)c.a;
+    A.b = (float)c.b;
+    A.gdt = (float)c.gdt;
+    A.kcs = kcs;
+    A.err = err;
+    A.divmax = divmax;
+    memcpy(A.rx, in.rx12, sizeof A.rx);
+    memcpy(A.ry, in.ry12, sizeof A.ry);
+    A.iDX = (float)(1.0 / (double)g.DX);
+    A.iDY = (float)(1.0 / (double)g.DY);
+    A.hx = g.hx;
+    A.hy = g.hy;
+    A.wait_ns = ptx::kWaitNs;
+    A.stop_ring = -1;
+    if (KIND == 0) {
+        take_wait_injection(&A.stop_ring, &A.wait_ns);
+        for (int q = 0; q < 2; ++q) {
+            A.hs[q] = in.hs[q];
+            A.hn[q] = in.hn[q];
+        }
+        A.hstride = in.hstride;
+    }
+    k_fused<M, TY, KIND, LF><<<dim3(chunks, g.Nx / kTX, g.Ny / TY), L::THREADS, L::bytes, st>>>(mn, mm, mlc, mu, mv,
+                                                                                               mw, A);
     return cudaGetLastError();
+}
+
+template <int KIND, bool LF>
+cudaError_t launch_fl_any(const Grid<float>& g, const FusedInputs& in, const float* Tm1, const float* T, float* Tp1,
+                          StepCoef c, int* err, unsigned long long* divmax, cudaStream_t st)
+{
+    if (g.mx == 2) return launch_fl<2, 8, KIND, LF>(g, in, Tm1, T, Tp1, c, err, divmax, st);
+    if constexpr (KIND == 0)
+        if (fused_tile_rows(g) == 16) return launch_fl<4, 16, KIND, LF>(g, in, Tm1, T, Tp1, c, err, divmax, st);
+    return launch_fl<4, 8, KIND, LF>(g, in, Tm1, T, Tp1, c, err, divmax, st);
 }
 
 }  // namespace
 
-cudaError_t launch_step_fused_f32(const Grid<float>& g, const float* U, const float* V, const float* W,
-                                   const float* lc, const float* rx12, const float* Tm1, const float* T, float* Tp1,
-                                   StepCoef c, cudaStream_t st)
+size_t fused_pad_floats(int nx, int ny, int nz)
+{
+    const size_t px = (size_t)nx + 8;
+    return (size_t)nz * (ny + 2) * px + (size_t)nz * (ny + 3) * px + (size_t)(nz + 1) * (ny + 2) * px;
+}
+
+cudaError_t launch_fused_pad(const float* U, const float* V, const float* W, float* out, int nx, int nyg, int nz,
+                             int j0, int ny, cudaStream_t st)
+{
+    const size_t n = fused_pad_floats(nx, ny, nz);
+    const size_t want = (n + 255) / 256;
+    const unsigned blocks = (unsigned)(want < 152 * 16 ? want : 152 * 16);
+    k_pad_coarse<<<blocks, 256, 0, st>>>(U, V, W, out, nx, nyg, nz, j0, ny);
+    return cudaGetLastError();
+}
+
+// Per coarse slab K, 32 floats (FP64 on the host, rounded once): the R_z rows
+// of its M dense layers (3M), 1/(2 dz) of each (M), and the stage-Z weights
+// Z[c][q] = sum_{c' = c}^{M-1} dz_{KM+c'} R_z[KM+c'][q], c = 1 .. M-1 (3(M-1)).
+std::vector<float> fused_slab_constants(int nz, int M, const double* Rz, const double* dz)
+{
+    std::vector<float> t((size_t)nz * kSCW, 0.f);
+    for (int K = 0; K < nz; ++K) {
+        float* q = &t[(size_t)K * kSCW];
+        for (int i = 0; i < M; ++i) {
+            const int k = K * M + i;
+            for (int c = 0; c < 3; ++c) q[3 * i + c] = (float)Rz[3 * (size_t)k + c];
+            q[3 * M + i] = (float)(0.5 / dz[k]);
+        }
+        for (int c = 1; c < M; ++c)
+            for (int r = 0; r < 3; ++r) {
+                double s = 0.0;
+                for (int cc = c; cc < M; ++cc) s += dz[K * M + cc] * Rz[3 * (size_t)(K * M + cc) + r];
+                q[4 * M + 3 * (c - 1) + r] = (float)s;
+            }
+    }
+    return t;
+}
+
+cudaError_t launch_step_fused_f32(const Grid<float>& g, const FusedInputs& in, const float* Tm1, const float* T,
+                                  float* Tp1, StepCoef c, cudaStream_t st)
 {
     int* err = fused_error_flag();
     if (!err) return cudaErrorMemoryAllocation;
     const bool lf = (c.a == 1.0 && c.b == 0.0);
-    if (g.mx == 4)
-        return lf ? launch_fx<4, 0, true>(g, U, V, W, lc, rx12, Tm1, T, Tp1, c, err, nullptr, st)
-                  : launch_fx<4, 0, false>(g, U, V, W, lc, rx12, Tm1, T, Tp1, c, err, nullptr, st);
-    return lf ? launch_fx<2, 0, true>(g, U, V, W, lc, rx12, Tm1, T, Tp1, c, err, nullptr, st)
-              : launch_fx<2, 0, false>(g, U, V, W, lc, rx12, Tm1, T, Tp1, c, err, nullptr, st);
+    return lf ? launch_fl_any<0, true>(g, in, Tm1, T, Tp1, c, err, nullptr, st)
+              : launch_fl_any<0, false>(g, in, Tm1, T, Tp1, c, err, nullptr, st);
 }
 
-cudaError_t launch_fused_max_f32(const Grid<float>& g, int kind, const float* U, const float* V, const float* W,
-                                  const float* lc, const float* rx12, double* partials, int blocks, cudaStream_t st)
+cudaError_t launch_fused_max_f32(const Grid<float>& g, int kind, const FusedInputs& in, double* partials, int blocks,
+                                 cudaStream_t st)
 {
     int* err = fused_error_flag();
     if (!err) return cudaErrorMemoryAllocation;
@@ -636,11 +865,8 @@ cudaError_t launch_fused_max_f32(const Grid<float>& g, int kind, const float* U,
     if (e != cudaSuccess) return e;
     unsigned long long* dm = reinterpret_cast<unsigned long long*>(partials);
     const StepCoef c{0, 0, 0};
-    if (g.mx == 4)
-        return kind == 2 ? launch_fx<4, 2, false>(g, U, V, W, lc, rx12, nullptr, nullptr, nullptr, c, err, dm, st)
-                         : launch_fx<4, 1, false>(g, U, V, W, lc, rx12, nullptr, nullptr, nullptr, c, err, dm, st);
-    return kind == 2 ? launch_fx<2, 2, false>(g, U, V, W, lc, rx12, nullptr, nullptr, nullptr, c, err, dm, st)
-                     : launch_fx<2, 1, false>(g, U, V, W, lc, rx12, nullptr, nullptr, nullptr, c, err, dm, st);
+    return kind == 2 ? launch_fl_any<2, false>(g, in, nullptr, nullptr, nullptr, c, err, dm, st)
+                     : launch_fl_any<1, false>(g, in, nullptr, nullptr, nullptr, c, err, dm, st);
 }
 
 // Raise a kernel's dynamic shared-memory limit once per device; *done holds
@@ -667,7 +893,7 @@ bool fused_supported(const mr_config& cfg, std::string* why)
         *why = "MR_VEL_FUSED needs mx = my = mz in {2, 4}";
         return false;
     }
-    if ((cfg.nx * cfg.mx) % kTX || (cfg.ny * cfg.my) % kTY) {
+    if ((cfg.nx * cfg.mx) % kTX || (cfg.ny * cfg.my) % 16) {
         *why = "MR_VEL_FUSED needs Nx % 64 == 0 and Ny % 16 == 0";
         return false;
     }

@@ -82,6 +82,10 @@ struct DeviceBuffers {
     float* xvr = nullptr;                      // [Nz][Ny+1][nxg]
     float* xlc = nullptr;                      // [Nz][32] layer constants of the fused steps
     float xrx[12] = {0};                       // R_x rows of the 4 cells of a 4-cell segment
+    float xry[12] = {0};                       // R_y rows of dense rows 0..3 (MR_VEL_FUSED)
+    float* cpad = nullptr;                     // MR_VEL_FUSED: padded FP32 coarse faces
+    float* fsc = nullptr;                      // MR_VEL_FUSED: [nz][32] slab constants
+    float* halo = nullptr;                     // y-slab: [3 levels][below, above][Nz][Nx] halo rows
     float xw4[8] = {0};                        // fourth order: twice the x and y face weights (uniform)
     int xlcw = 12;                             // row length of xlc
     double* diag = nullptr;                    // diagnostics: coarse T, Nu(z), dense z centres (lazy)
@@ -94,8 +98,9 @@ struct DeviceBuffers {
         void *Uc = nullptr, *Vc = nullptr, *Wc = nullptr;
         void *Us = nullptr, *Vs = nullptr, *Ws = nullptr;
         float *xwy = nullptr, *xuo = nullptr, *xvr = nullptr;
+        float* cpad = nullptr;
     } next;
-    float* lerpc = nullptr;                    // MR_VEL_FUSED: interpolated coarse faces (U, V, W)
+    float* lerpc = nullptr;                    // MR_VEL_FUSED: interpolated padded coarse faces
     // staged coarse faces (mr_stage_velocity): two FP64 slots; a refinement
     // swaps the slot with U64/V64/W64 instead of copying it
     double *sU[2] = {nullptr, nullptr}, *sV[2] = {nullptr, nullptr}, *sW[2] = {nullptr, nullptr};
@@ -111,6 +116,10 @@ struct mr_handle_s {
     mr_config cfg;
     int device = 0;
     int Nx = 0, Ny = 0, Nz = 0, w = 0;
+    // stored dense and coarse rows: the whole domain's Ny, ny, or a y-slab's
+    int Nys = 0, nys = 0;
+    bool slab = false;
+    bool halo_set[3] = {false, false, false};   // y-slab: halo rows given for each scalar level
     size_t ncell = 0, nU = 0, nV = 0, nW = 0, ncU = 0, ncV = 0, ncW = 0;
     size_t elt = 8;          // bytes per element of precision P
     double kappa = 0.0;
@@ -193,14 +202,33 @@ bool fused_supported(const mr_config& cfg, std::string* why);
 // FP64 values from mapped pinned host memory into an FP64 device array and,
 // where d32 is given, an FP32 one (16-byte aligned src and d64, 8-byte d32).
 cudaError_t launch_fetch_f64(const double* src, double* d64, float* d32, size_t n, cudaStream_t st);
-// MR_VEL_FUSED: every refinement stage in the step kernel (lc: the layer
-// constants of xfused_layer_constants, rx12: the uniform R_x rows)
-cudaError_t launch_step_fused_f32(const Grid<float>& g, const float* U, const float* V, const float* W,
-                                   const float* lc, const float* rx12, const float* Tm1, const float* T, float* Tp1,
-                                   StepCoef c, cudaStream_t st);
+// MR_VEL_FUSED: what the fused step kernel reads besides the scalar levels
+struct FusedInputs {
+    const float* pad;    // coarse U, V, W padded with their periodic images (launch_fused_pad)
+    // the dense rows south of row 0 and north of row Ny-1 of T^s and T^{s-1}
+    // (hs, hn), element (k, i) at k * hstride + i: the periodic images on a
+    // whole-domain grid, the halo rows of a y-slab
+    const float* hs[2];
+    const float* hn[2];
+    size_t hstride;
+    const float* sc;     // [nz][32] slab constants (fused_slab_constants)
+    const float* lc;     // [Nz][32] layer constants (xfused_layer_constants)
+    const float* rx12;   // R_x rows of the 4 cells of a 4-cell segment (uniform, periodic x)
+    const float* ry12;   // R_y rows of dense rows 0..3 (uniform, periodic y)
+};
+// every refinement stage in the step kernel
+cudaError_t launch_step_fused_f32(const Grid<float>& g, const FusedInputs& in, const float* Tm1, const float* T,
+                                  float* Tp1, StepCoef c, cudaStream_t st);
 // kind 1: max |divergence| of the dense velocity, kind 2: max CFL rate (into partials[0])
-cudaError_t launch_fused_max_f32(const Grid<float>& g, int kind, const float* U, const float* V, const float* W,
-                                  const float* lc, const float* rx12, double* partials, int blocks, cudaStream_t st);
+cudaError_t launch_fused_max_f32(const Grid<float>& g, int kind, const FusedInputs& in, double* partials, int blocks,
+                                 cudaStream_t st);
+// floats of the padded coarse faces, and the kernel that forms them from the FP32 coarse faces
+size_t fused_pad_floats(int nx, int ny, int nz);
+// (the coarse rows j0-1 .. j0+ny+1 of a domain of nyg rows, periodic)
+cudaError_t launch_fused_pad(const float* U, const float* V, const float* W, float* out, int nx, int nyg, int nz,
+                             int j0, int ny, cudaStream_t st);
+// per coarse slab: R_z rows, 1/(2 dz) and the stage-Z weights, [nz][32]
+std::vector<float> fused_slab_constants(int nz, int M, const double* Rz, const double* dz);
 int* fused_error_flag();
 // per-layer constant table [Nz][32] of the split-x and fully fused kernels
 // (layout owned by mr_xfused.cu)

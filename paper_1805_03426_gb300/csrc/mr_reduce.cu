@@ -228,12 +228,16 @@ __global__ void k_upscale(Grid<P> g, const P* __restrict__ T, double* __restrict
     const size_t n = (size_t)g.nz * g.ny * g.nx;
     for (size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (size_t)gridDim.x * blockDim.x) {
         const int I = (int)(t % g.nx), J = (int)((t / g.nx) % g.ny), K = (int)(t / ((size_t)g.nx * g.ny));
+        // the sum over each dense layer in the working precision (GB300's FP64
+        // pipe is 1/64 of its FP32 rate), the volume weighting in FP64
         double s = 0.0, h = 0.0;
         for (int k = K * g.mz; k < (K + 1) * g.mz; ++k) {
-            double r = 0.0;
-            for (int j = J * g.my; j < (J + 1) * g.my; ++j)
-                for (int i = I * g.mx; i < (I + 1) * g.mx; ++i) r += (double)T[((size_t)k * g.Ny + j) * g.Nx + i];
-            s += r * (double)g.dz[k];
+            P r = P(0);
+            for (int j = J * g.my; j < (J + 1) * g.my; ++j) {
+                const P* row = T + ((size_t)k * g.Ny + j) * g.Nx + (size_t)I * g.mx;
+                for (int i = 0; i < g.mx; ++i) r += row[i];
+            }
+            s += (double)r * (double)g.dz[k];
             h += (double)g.dz[k];
         }
         Tc[t] = s / (h * g.mx * g.my);

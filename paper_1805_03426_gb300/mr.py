@@ -40,6 +40,7 @@ class mr_config(ctypes.Structure):
         ("np_average", ctypes.c_int32), ("bc_plates", ctypes.c_int32),
         ("bc_horizontal", ctypes.c_int32), ("diffz_implicit", ctypes.c_int32),
         ("face_order", ctypes.c_int32),
+        ("slab_j0", ctypes.c_int32), ("slab_ny", ctypes.c_int32),
     ]
 
 
@@ -77,6 +78,8 @@ _SIGS = {
     "mr_scalar_profiles": (ctypes.c_int, [_VP, _VP, ctypes.POINTER(_D), _VP]),
     "mr_refine_velocity_noalloc": (ctypes.c_int, [ctypes.POINTER(mr_config), _VP, _VP, _VP, _VP, _VP, _VP, _VP]),
     "mr_fp64_fma_rate": (ctypes.c_int, [ctypes.POINTER(_D), _VP]),
+    "mr_get_boundary_rows": (ctypes.c_int, [_VP, _VP, _VP, _VP]),
+    "mr_set_halo_rows": (ctypes.c_int, [_VP, _VP, _VP, _VP]),
     "mr_debug_inject_wait_timeout": (ctypes.c_int, [_I32, _D]),
     "mr_debug_alloc_cap": (ctypes.c_int, [_I64, ctypes.POINTER(_I64)]),
 }
@@ -162,8 +165,11 @@ class Handle:
         _check(lib().mr_create(ctypes.byref(cfg), ctypes.byref(h)))
         self._h = h
         w = 1 if cfg.bc_horizontal == MR_WALLS else 0
-        self.dense = (cfg.nx * cfg.mx, cfg.ny * cfg.my, cfg.nz * cfg.mz)
+        # dense cells the handle stores (a y-slab handle: its slab's rows)
+        rows = cfg.slab_ny if cfg.slab_ny > 0 else cfg.ny
+        self.dense = (cfg.nx * cfg.mx, rows * cfg.my, cfg.nz * cfg.mz)
         Nx, Ny, Nz = self.dense
+        self.coarse_rows = rows
         self.shapes = {
             "U": (cfg.nz, cfg.ny, cfg.nx + w), "V": (cfg.nz, cfg.ny + w, cfg.nx),
             "W": (cfg.nz + 1, cfg.ny, cfg.nx),
@@ -360,9 +366,10 @@ def mr_refine_velocity_noalloc(cfg: mr_config, U, V, W, Us, Vs, Ws, stream=None)
 def mr_upscale_scalar(h: Handle, Tc=None, stream=None):
     """Volume-weighted coarse-cell averages of T^n (Section 3.3), FP64."""
     c = h.cfg
+    rows = h.coarse_rows
     if Tc is None:
-        Tc = np.empty((c.nz, c.ny, c.nx))
-    _check(lib().mr_upscale_scalar(h.ptr, _ptr(Tc, c.nz * c.ny * c.nx, np.float64, "Tc"), _stream(stream)))
+        Tc = np.empty((c.nz, rows, c.nx))
+    _check(lib().mr_upscale_scalar(h.ptr, _ptr(Tc, c.nz * rows * c.nx, np.float64, "Tc"), _stream(stream)))
     return Tc
 
 
@@ -392,3 +399,17 @@ def mr_debug_alloc_cap(cap_bytes: int = -2) -> int:
     live = _I64()
     _check(lib().mr_debug_alloc_cap(cap_bytes, ctypes.byref(live)))
     return live.value
+
+
+def mr_get_boundary_rows(h: Handle, south, north, stream=None):
+    """First and last dense rows of T^n of a y-slab handle, [Nz][Nx] each."""
+    Nx, _, Nz = h.dense
+    _check(lib().mr_get_boundary_rows(h.ptr, _ptr(south, Nx * Nz, h.np_dtype, "south"),
+                                      _ptr(north, Nx * Nz, h.np_dtype, "north"), _stream(stream)))
+
+
+def mr_set_halo_rows(h: Handle, below, above, stream=None):
+    """Halo rows of T^n of a y-slab handle (south of row 0, north of the last row)."""
+    Nx, _, Nz = h.dense
+    _check(lib().mr_set_halo_rows(h.ptr, _ptr(below, Nx * Nz, h.np_dtype, "below"),
+                                  _ptr(above, Nx * Nz, h.np_dtype, "above"), _stream(stream)))

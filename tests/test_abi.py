@@ -106,3 +106,16 @@ def test_wait_injection_arguments_checked(mr):
         with pytest.raises(mr.MRError) as e:
             mr.mr_debug_inject_wait_timeout(ring, secs)
         assert e.value.code == mr.MR_ERR_ARG
+
+
+@pytest.mark.parametrize("bad", [
+    dict(slab_j0=0, slab_ny=4),                                   # a y-slab needs MR_VEL_FUSED
+    dict(velocity_mode=1, precision=1, nx=16, ny=8, mx=4, my=4, mz=4, slab_j0=6, slab_ny=4),  # past the last row
+    dict(velocity_mode=1, precision=1, nx=16, ny=8, mx=4, my=4, mz=4, slab_j0=0, slab_ny=3),  # 12 dense rows
+    dict(slab_j0=2, slab_ny=0),                                   # slab_j0 without slab_ny
+])
+def test_invalid_slab_config_rejected(mr, bad):
+    c = mr.mr_config_default(**bad)
+    with pytest.raises(mr.MRError) as e:
+        mr.mr_create(c)
+    assert e.value.code == mr.MR_ERR_ARG

@@ -1,5 +1,5 @@
-"""The multi-rank path of bench.py on CPU: two gloo ranks take the maximum of
-their times and report the whole-job rate over both replicas."""
+"""The multi-rank timing of bench.py on CPU: two gloo ranks take the maximum
+of their times and report the whole-job rate over both ranks' slabs."""
 import os
 import socket
 
