@@ -185,6 +185,16 @@ int mr_get_scalar(mr_handle h, void* T, void* Tprev, int32_t dtype, mr_stream st
  * step.  Needs mr_refine_velocity and mr_set_scalar first (MR_ERR_STATE). */
 int mr_scalar_step(mr_handle h, int64_t nsteps, mr_stream stream);
 
+/* One time step (as mr_scalar_step) followed by what a coupled coarse solver
+ * takes back every step: the plate Nusselt numbers of the new T^n into nu2
+ * (2 doubles, bottom then top, Section 4.1) and the volume-weighted average of
+ * T^n over every coarse cell into Tc (nz x ny x nx doubles, [z][y][x]; a
+ * y-slab handle: its slab's coarse rows), the upscale integration of Section
+ * 3.3.  Either may be NULL.  Each must be device memory or pinned host memory,
+ * which the kernels write directly (MR_ERR_ARG for pageable host memory).
+ * Asynchronous on stream; the other rules are mr_scalar_step's. */
+int mr_scalar_step_coupled(mr_handle h, double* nu2, double* Tc, mr_stream stream);
+
 /* One coarse time step with temporal refinement (Section 3.4, Eq. 18): the
  * velocity set by mr_refine_velocity (or by the previous call) is U^{n-1};
  * U, V, W (FP64, host or device, coarse layout as in mr_refine_velocity) are

@@ -395,7 +395,7 @@ void mr_destroy(mr_handle h)
         for (void* p : cptrs)
             if (p) dev_free(p);
     }
-    void* xptrs[] = {b.xwy, b.xuo, b.xvr, b.xlc, b.diag, b.cpad, b.fsc, n.cpad, b.halo};
+    void* xptrs[] = {b.xwy, b.xuo, b.xvr, b.xlc, b.diag, b.cpad, b.fsc, n.cpad, b.halo, b.tcp, b.tcinv};
     for (void* p : xptrs)
         if (p) dev_free(p);
     for (int q = 0; q < 2; ++q) {
@@ -705,7 +705,7 @@ static int derive_velocity(mr_handle h, bool convert, cudaStream_t st)
 // One time step of the scalar.  alpha = 0: the current velocity; otherwise the
 // velocity (1 - alpha) U^{n-1} + alpha U^n between the current level and the
 // next one (temporal refinement, Section 3.4).
-static int one_step(mr_handle h, double alpha, cudaStream_t st)
+static int one_step(mr_handle h, double alpha, cudaStream_t st, float* tcp = nullptr)
 {
     DeviceBuffers& b = h->buf;
     const DeviceBuffers::Level& nx = b.next;
@@ -729,7 +729,7 @@ static int one_step(mr_handle h, double alpha, cudaStream_t st)
                                    (const float*)Tm1,
                                    (const float*)b.T[h->ic], (float*)b.T[in], c, st);
     } else if (h->cfg.velocity_mode == MR_VEL_FUSED) {
-        FusedInputs fin{b.cpad, {}, {}, 0, b.fsc, b.xlc, b.xrx, b.xry};
+        FusedInputs fin{b.cpad, {}, {}, 0, b.fsc, b.xlc, b.xrx, b.xry, tcp};
         // the rows beyond the y edges of T^s and T^{s-1}
         const int lm = h->step == 0 ? h->ic : h->ip;
         if (h->slab) {
@@ -1008,6 +1008,80 @@ int mr_scalar_step(mr_handle h, int64_t nsteps, mr_stream stream)
     return MR_OK;
 }
 
+// The device address of a device pointer, or of pinned host memory; NULL for
+// pageable host memory.
+static void* device_alias(void* p)
+{
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    if (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged) return p;
+    if (a.type == cudaMemoryTypeHost) return a.devicePointer;
+    return nullptr;
+}
+
+int mr_scalar_step_coupled(mr_handle h, double* nu2, double* Tc, mr_stream stream)
+{
+    if (!h) return set_error(MR_ERR_ARG, "mr_scalar_step_coupled: NULL handle");
+    double* dnu = nullptr;
+    double* dtc = nullptr;
+    if (nu2 && !(dnu = (double*)device_alias(nu2)))
+        return set_error(MR_ERR_ARG, "mr_scalar_step_coupled: nu2 must be device or pinned host memory");
+    if (Tc && !(dtc = (double*)device_alias(Tc)))
+        return set_error(MR_ERR_ARG, "mr_scalar_step_coupled: Tc must be device or pinned host memory");
+    cudaStream_t st = (cudaStream_t)stream;
+    DeviceBuffers& b = h->buf;
+    const bool fused = h->cfg.velocity_mode == MR_VEL_FUSED;
+    int rc;
+    if (fused && dtc && !b.tcp) {
+        // the fused step leaves the upscale partials; the FP64 factors per slab
+        const mr_config& c = h->cfg;
+        cudaError_t e = dev_malloc(&b.tcp, (size_t)c.nz * h->Nys * c.nx * sizeof(float));
+        if (e == cudaSuccess) e = dev_malloc(&b.tcinv, (size_t)c.nz * sizeof(double));
+        std::vector<double> inv(c.nz);
+        for (int K = 0; K < c.nz; ++K) {
+            double z = 0.0;
+            for (int k = K * c.mz; k < (K + 1) * c.mz; ++k) z += h->dz[k];
+            inv[K] = 1.0 / (z * c.mx * c.my);
+        }
+        if (e == cudaSuccess) e = cudaMemcpy(b.tcinv, inv.data(), inv.size() * sizeof(double), cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) {
+            dev_free(b.tcp);
+            dev_free(b.tcinv);
+            b.tcp = nullptr;
+            b.tcinv = nullptr;
+            return cuda_check(e, "mr_scalar_step_coupled: upscale partials");
+        }
+    }
+    if (fused && dtc) {
+        // the step kernel forms the upscale partials of the new level itself
+        if (h->slab && !(h->halo_set[h->ic] && (h->step == 0 || h->halo_set[h->ip])))
+            return set_error(MR_ERR_STATE, "mr_scalar_step_coupled: set the y-slab's halo rows first");
+        if (!h->have_velocity || !h->have_scalar)
+            return set_error(MR_ERR_STATE, "mr_scalar_step_coupled: call mr_refine_velocity and mr_set_scalar first");
+        rc = one_step(h, 0.0, st, b.tcp);
+    } else {
+        rc = mr_scalar_step(h, 1, stream);
+    }
+    if (rc) return rc;
+    cudaError_t e = cudaSuccess;
+    if (dnu) {
+        const double zz[2] = {h->zc[0] - h->zf[0], h->zf[h->Nz] - h->zc[h->Nz - 1]};
+        e = h->cfg.precision == MR_F64
+                ? launch_plate_nu<double>(h->g64, (const double*)h->buf.T[h->ic], zz, h->buf.nu2, st)
+                : launch_plate_nu<float>(h->g32, (const float*)h->buf.T[h->ic], zz, h->buf.nu2, st);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(dnu, h->buf.nu2, 2 * sizeof(double), cudaMemcpyDefault, st);
+    }
+    if (e == cudaSuccess && dtc)
+        e = fused ? launch_fused_tc_reduce(h->g32, b.tcp, b.tcinv, dtc, st)
+                  : h->cfg.precision == MR_F64
+                        ? launch_upscale<double>(h->g64, (const double*)h->buf.T[h->ic], dtc, st)
+                        : launch_upscale<float>(h->g32, (const float*)h->buf.T[h->ic], dtc, st);
+    return cuda_check(e, "mr_scalar_step_coupled");
+}
+
 int mr_get_boundary_rows(mr_handle h, void* south, void* north, mr_stream stream)
 {
     if (!h || (!south && !north)) return set_error(MR_ERR_ARG, "mr_get_boundary_rows: NULL argument");
@@ -1066,7 +1140,7 @@ static int max_divergence(mr_handle h, double* out, cudaStream_t st)
     if (h->cfg.velocity_mode == MR_VEL_XFUSED)
         e = launch_xfused_max_f32(h->g32, 1, b.xwy, b.xuo, b.xvr, b.nxg, b.xlc, b.xlcw, b.xrx, b.red, h->red_blocks, st);
     else if (h->cfg.velocity_mode == MR_VEL_FUSED)
-        e = launch_fused_max_f32(h->g32, 1, FusedInputs{b.cpad, {}, {}, 0, b.fsc, b.xlc, b.xrx, b.xry}, b.red,
+        e = launch_fused_max_f32(h->g32, 1, FusedInputs{b.cpad, {}, {}, 0, b.fsc, b.xlc, b.xrx, b.xry, nullptr}, b.red,
                                  h->red_blocks, st);
     else if (h->cfg.precision == MR_F64)
         e = launch_maxdiv<double>(h->g64, (const double*)b.Us, (const double*)b.Vs, (const double*)b.Ws, b.red,
@@ -1148,7 +1222,7 @@ int mr_cfl_dt(mr_handle h, double cfl, double* dt_out, mr_stream stream)
         e = launch_xfused_max_f32(h->g32, 2, b.xwy, b.xuo, b.xvr, b.nxg, b.xlc, b.xlcw, b.xrx, b.red, h->red_blocks, st);
     } else if (h->cfg.velocity_mode == MR_VEL_FUSED) {
         // the fused kernel forms the dense faces in registers from the coarse ones
-        e = launch_fused_max_f32(h->g32, 2, FusedInputs{b.cpad, {}, {}, 0, b.fsc, b.xlc, b.xrx, b.xry}, b.red,
+        e = launch_fused_max_f32(h->g32, 2, FusedInputs{b.cpad, {}, {}, 0, b.fsc, b.xlc, b.xrx, b.xry, nullptr}, b.red,
                                  h->red_blocks, st);
     } else if (h->cfg.velocity_mode != MR_VEL_STORED) {
         // dense faces are not kept: refine into temporary buffers once

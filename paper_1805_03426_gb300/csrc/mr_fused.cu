@@ -54,6 +54,14 @@ constexpr int kTX = 64;                 // tile width (cells)
 constexpr int kBX = kTX + 8;            // scalar plane box width (floats)
 constexpr int kLCW = 32;                // layer-constant row (floats)
 constexpr int kSCW = 32;                // slab-constant row (floats)
+#ifndef MR_FUSED_IDLE_NS
+#define MR_FUSED_IDLE_NS 256
+#endif
+constexpr unsigned kIdleNs = MR_FUSED_IDLE_NS;   // sleep between the polls of the producer and builder warps
+#ifndef MR_FUSED_PREFETCH
+#define MR_FUSED_PREFETCH 6
+#endif
+constexpr int kPrefetch = MR_FUSED_PREFETCH;      // planes of L2 prefetch ahead of the ring's loads
 
 __host__ __device__ constexpr int up32(int n) { return (n + 31) / 32 * 32; }
 
@@ -114,6 +122,8 @@ struct FLArgs {
     const float* hs[2];  // rows south of row 0 of T^s, T^{s-1} (periodic images or y-slab halo)
     const float* hn[2];  // rows north of row Ny-1
     size_t hstride;      // layer stride of those rows
+    float* tcp;          // NULL, or [nz][Ny][nx]: per coarse slab, dense row and coarse column,
+                         // sum over the slab's layers of dz times the column's new values
 };
 
 // R_x split of three coarse values by one row of R (rows sum to one).
@@ -278,8 +288,9 @@ __device__ void build_slab(const FLArgs& A, const float* __restrict__ cb, float*
 }
 
 // KIND 0: the step; 1: max |divergence| of the dense velocity; 2: max CFL rate.
-// LF: a plain leapfrog step (a = 1, b = 0).
-template <int M, int TY, int KIND, bool LF>
+// LF: a plain leapfrog step (a = 1, b = 0).  TC: the step also leaves the
+// upscale partials of the new level (A.tcp).
+template <int M, int TY, int KIND, bool LF, bool TC = false>
 __global__ void __launch_bounds__(FL<M, TY, (KIND != 0)>::THREADS, FL<M, TY, (KIND != 0)>::CTAS)
 k_fused(const __grid_constant__ CUtensorMap tmn, const __grid_constant__ CUtensorMap tmm,
         const __grid_constant__ CUtensorMap tlc, const __grid_constant__ CUtensorMap tcu,
@@ -331,7 +342,7 @@ k_fused(const __grid_constant__ CUtensorMap tmn, const __grid_constant__ CUtenso
             // the coarse faces of slab K into buffer (K - K0) & 1
             auto issue_coarse = [&](int K) {
                 const int bb = (K - K0) & 1, use = (K - K0) >> 1;
-                if (use > 0 && !mbar_wait(&cempty[bb], (use - 1) & 1, A.wait_ns)) return false;
+                if (use > 0 && !mbar_wait_idle(&cempty[bb], (use - 1) & 1, A.wait_ns, kIdleNs)) return false;
                 float* dst = sm + L::oCoarse + bb * L::CBOX;
                 const int wz0 = min(max(K - 1, 0), g.nz - 3);     // first plane of the R_z window
                 asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -350,7 +361,7 @@ k_fused(const __grid_constant__ CUtensorMap tmn, const __grid_constant__ CUtenso
             for (int r = 0; ok && !stopped && r < nrings; ++r) {
                 const int s = r % NB;
                 if (stopper && r == A.stop_ring) break;    // every copy issued so far is waited for
-                if (r >= NB && !mbar_wait(&empty[s], ((r / NB) - 1) & 1, A.wait_ns)) {
+                if (r >= NB && !mbar_wait_idle(&empty[s], ((r / NB) - 1) & 1, A.wait_ns, kIdleNs)) {
                     ok = false;
                     break;
                 }
@@ -362,6 +373,11 @@ k_fused(const __grid_constant__ CUtensorMap tmn, const __grid_constant__ CUtenso
                 if (!DIVONLY) {
                     tma_3d(slot + L::oTn, &tmn, i0 - 4, j0 - 1, p, &full[s]);
                     tma_3d(slot + L::oTm, &tmm, i0 - 4, j0 - 1, p, &full[s]);
+                    if (kPrefetch > 0 && p + kPrefetch <= k1) {
+                        // the planes a few rings ahead into L2: deeper in flight than the ring
+                        tma_prefetch_3d(&tmn, i0 - 4, j0 - 1, p + kPrefetch);
+                        tma_prefetch_3d(&tmm, i0 - 4, j0 - 1, p + kPrefetch);
+                    }
                 }
                 if (lc) tma_3d(slot + L::oLC, &tlc, 0, p - 1, 0, &full[s]);
                 rings_issued = r + 1;
@@ -385,8 +401,8 @@ k_fused(const __grid_constant__ CUtensorMap tmn, const __grid_constant__ CUtenso
         }
         for (int K = K0 + 1; K < K1 && !fail; ++K) {
             const int bb = (K - K0) & 1, use = (K - K0) >> 1;
-            bool f = !mbar_wait(&cfull[bb], use & 1, A.wait_ns);
-            if (!f && use > 0) f = !mbar_wait(&freed[bb], (use - 1) & 1, A.wait_ns);
+            bool f = !mbar_wait_idle(&cfull[bb], use & 1, A.wait_ns, kIdleNs);
+            if (!f && use > 0) f = !mbar_wait_idle(&freed[bb], (use - 1) & 1, A.wait_ns, kIdleNs);
             fail = named_or<L::NBT>(2, f);
             if (fail) break;
             build_slab<M, TY, L::NBT>(A, sm + L::oCoarse + bb * L::CBOX, sm + L::oSlab + bb * L::SLAB, sm + L::oZ,
@@ -418,7 +434,9 @@ k_fused(const __grid_constant__ CUtensorMap tmn, const __grid_constant__ CUtenso
         float* outp = A.Tp1 + (size_t)k0 * plane + (size_t)(j0 + jl) * g.Nx + i0 + il0;
         const int o = (jl + 1) * kBX + il0 + 4;      // this segment's first cell in a plane box
         float wcar[4] = {0.f, 0.f, 0.f, 0.f};        // R_x split of W on plane k (from layer k-1)
-        // the chunk's first slab, with the builder warps
+        float tcs[NC] = {};                          // upscale partials of the segment's coarse columns
+        // the chunk's first slab, with the builder warps (measured faster than
+        // waiting for the builders alone)
         fail = !mbar_wait(&cfull[0], 0, A.wait_ns);
         fail = named_or<CONS + L::NBT>(3, fail);
         if (!fail)
@@ -578,6 +596,25 @@ k_fused(const __grid_constant__ CUtensorMap tmn, const __grid_constant__ CUtenso
                         res[h] = LF ? fma2(gdtp, acc, dc) : fma2(gdtp, acc, fma2(cap, dc, mul2(cbp, tc)));
                     }
                     *reinterpret_cast<float4*>(outp) = make_float4(res[0].x, res[0].y, res[1].x, res[1].y);
+                    if constexpr (TC) {
+                        // the upscale integration (Section 3.3): dz-weighted sums over the
+                        // slab's layers of each coarse column's cells in this row
+                        const float dzk = lcp[2];
+                        if (NC == 1) {
+                            tcs[0] += dzk * ((res[0].x + res[0].y) + (res[1].x + res[1].y));
+                        } else {
+                            tcs[0] += dzk * (res[0].x + res[0].y);
+                            tcs[NC - 1] += dzk * (res[1].x + res[1].y);
+                        }
+                        if (i == M - 1) {
+                            float* tp = A.tcp + ((size_t)(k / M) * g.Ny + j0 + jl) * g.nx + I0 + cb0;
+#pragma unroll
+                            for (int q = 0; q < NC; ++q) {
+                                tp[q] = tcs[q];
+                                tcs[q] = 0.f;
+                            }
+                        }
+                    }
                 }
             }
             // plane k-1 is no longer needed by this thread; nor, after the
@@ -586,16 +623,9 @@ k_fused(const __grid_constant__ CUtensorMap tmn, const __grid_constant__ CUtenso
             if (i == M - 1) mbar_arrive(&freed[bb]);
             outp += plane;
         };
-        if constexpr (!DIVONLY) {
-            // unrolled by the ring length: layer k0 + u uses the slots u, u+1, u+2 (mod NB)
-            for (int kb = k0, opar = 0; kb < k1; kb += NB, opar ^= 1) {
-#pragma unroll
-                for (int u = 0; u < NB; ++u) {
-                    if (kb + u >= k1) break;
-                    layer(kb + u, u % NB, (u + 1) % NB, (u + 2) % NB, opar ^ (((u + 2) / NB) & 1));
-                }
-            }
-        } else {
+        // the slots rotate (a loop unrolled by the ring length ran 8 % slower on
+        // 512 x 512 x 384: its copies of the layer body miss the instruction cache)
+        {
             int sb = 0, sc = 1, st = 2, tpar = 0;
             for (int k = k0; k < k1; ++k) {
                 layer(k, sb, sc, st, tpar);
@@ -717,25 +747,13 @@ bool map_fx(CUtensorMap* out, const float* base, int d0, int d1, int d2, int b0,
     return true;
 }
 
-// Tile height: 64x16 tiles (two CTAs per SM) at M = 4 (measured on 512 x 512 x
-// 384: 0.432 ms per step against 0.491 on 64x8 tiles; 1536 x 1536 x 1024: 8.77
-// against 10.2 ms), 64x8 at M = 2 (its 64x16 layout would not fit two CTAs per
-// SM).
-int fused_tile_rows(const Grid<float>& g)
-{
-#ifdef MR_FUSED_TY
-    if (g.mx == 4) return MR_FUSED_TY;    // compile-time override for tuning sweeps
-#endif
-    return g.mx == 4 ? 16 : 8;
-}
-
-template <int M, int TY, int KIND, bool LF>
+template <int M, int TY, int KIND, bool LF, bool TC = false>
 cudaError_t launch_fl(const Grid<float>& g, const FusedInputs& in, const float* Tm1, const float* T, float* Tp1,
                       StepCoef c, int* err, unsigned long long* divmax, cudaStream_t st)
 {
     using L = FL<M, TY, (KIND != 0)>;
     static unsigned long long attr = 0;                   // one bit per device
-    cudaError_t e = smem_optin(reinterpret_cast<const void*>(k_fused<M, TY, KIND, LF>), (int)L::bytes, &attr);
+    cudaError_t e = smem_optin(reinterpret_cast<const void*>(k_fused<M, TY, KIND, LF, TC>), (int)L::bytes, &attr);
     if (e != cudaSuccess) return e;
     CUtensorMap mn, mm, mlc, mu, mv, mw;
     memset(&mn, 0, sizeof mn);
@@ -789,23 +807,54 @@ cudaError_t launch_fl(const Grid<float>& g, const FusedInputs& in, const float* 
             A.hn[q] = in.hn[q];
         }
         A.hstride = in.hstride;
+        A.tcp = in.tcp;
     }
-    k_fused<M, TY, KIND, LF><<<dim3(chunks, g.Nx / kTX, g.Ny / TY), L::THREADS, L::bytes, st>>>(mn, mm, mlc, mu, mv,
-                                                                                               mw, A);
+    k_fused<M, TY, KIND, LF, TC><<<dim3(chunks, g.Nx / kTX, g.Ny / TY), L::THREADS, L::bytes, st>>>(mn, mm, mlc, mu,
+                                                                                                   mv, mw, A);
     return cudaGetLastError();
 }
 
-template <int KIND, bool LF>
+// The step on 64x16 tiles at M = 4 (two CTAs per SM; measured on 512 x 512 x
+// 384: 0.432 ms per step against 0.491 on 64x8 tiles, on 1536 x 1536 x 1024
+// 8.77 against 10.2 ms), on 64x8 tiles at M = 2 (its 64x16 layout would not
+// fit two CTAs per SM); the reductions, which stream no scalar, on 64x8 tiles.
+template <int KIND, bool LF, bool TC>
 cudaError_t launch_fl_any(const Grid<float>& g, const FusedInputs& in, const float* Tm1, const float* T, float* Tp1,
                           StepCoef c, int* err, unsigned long long* divmax, cudaStream_t st)
 {
-    if (g.mx == 2) return launch_fl<2, 8, KIND, LF>(g, in, Tm1, T, Tp1, c, err, divmax, st);
-    if constexpr (KIND == 0)
-        if (fused_tile_rows(g) == 16) return launch_fl<4, 16, KIND, LF>(g, in, Tm1, T, Tp1, c, err, divmax, st);
-    return launch_fl<4, 8, KIND, LF>(g, in, Tm1, T, Tp1, c, err, divmax, st);
+    if (g.mx == 2) return launch_fl<2, 8, KIND, LF, TC>(g, in, Tm1, T, Tp1, c, err, divmax, st);
+    if constexpr (KIND == 0) return launch_fl<4, 16, KIND, LF, TC>(g, in, Tm1, T, Tp1, c, err, divmax, st);
+    else return launch_fl<4, 8, KIND, LF, TC>(g, in, Tm1, T, Tp1, c, err, divmax, st);
+}
+
+// Tc[K][J][I] from the step's upscale partials: the sum over the coarse row's
+// my dense rows, times 1 / (mx my sum of the slab's dz) (FP64).
+__global__ void k_tc_reduce(const float* __restrict__ tcp, const double* __restrict__ inv, double* __restrict__ Tc,
+                            int nx, int ny, int nz, int my)
+{
+    const size_t n = (size_t)nz * ny * nx;
+    for (size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (size_t)gridDim.x * blockDim.x) {
+        const int I = (int)(t % nx);
+        const size_t KJ = t / nx;
+        const int J = (int)(KJ % ny), K = (int)(KJ / ny);
+        const float* p = tcp + ((size_t)K * ny * my + (size_t)J * my) * nx + I;
+        float s = 0.f;
+        for (int b = 0; b < my; ++b) s += p[(size_t)b * nx];
+        Tc[t] = (double)s * inv[K];
+    }
 }
 
 }  // namespace
+
+cudaError_t launch_fused_tc_reduce(const Grid<float>& g, const float* tcp, const double* inv, double* Tc,
+                                   cudaStream_t st)
+{
+    const size_t n = (size_t)g.nz * g.ny * g.nx;
+    const size_t want = (n + 255) / 256;
+    const unsigned blocks = (unsigned)(want < 152 * 16 ? want : 152 * 16);
+    k_tc_reduce<<<blocks, 256, 0, st>>>(tcp, inv, Tc, g.nx, g.ny, g.nz, g.my);
+    return cudaGetLastError();
+}
 
 size_t fused_pad_floats(int nx, int ny, int nz)
 {
@@ -852,8 +901,11 @@ cudaError_t launch_step_fused_f32(const Grid<float>& g, const FusedInputs& in, c
     int* err = fused_error_flag();
     if (!err) return cudaErrorMemoryAllocation;
     const bool lf = (c.a == 1.0 && c.b == 0.0);
-    return lf ? launch_fl_any<0, true>(g, in, Tm1, T, Tp1, c, err, nullptr, st)
-              : launch_fl_any<0, false>(g, in, Tm1, T, Tp1, c, err, nullptr, st);
+    if (in.tcp)
+        return lf ? launch_fl_any<0, true, true>(g, in, Tm1, T, Tp1, c, err, nullptr, st)
+                  : launch_fl_any<0, false, true>(g, in, Tm1, T, Tp1, c, err, nullptr, st);
+    return lf ? launch_fl_any<0, true, false>(g, in, Tm1, T, Tp1, c, err, nullptr, st)
+              : launch_fl_any<0, false, false>(g, in, Tm1, T, Tp1, c, err, nullptr, st);
 }
 
 cudaError_t launch_fused_max_f32(const Grid<float>& g, int kind, const FusedInputs& in, double* partials, int blocks,
@@ -865,8 +917,8 @@ cudaError_t launch_fused_max_f32(const Grid<float>& g, int kind, const FusedInpu
     if (e != cudaSuccess) return e;
     unsigned long long* dm = reinterpret_cast<unsigned long long*>(partials);
     const StepCoef c{0, 0, 0};
-    return kind == 2 ? launch_fl_any<2, false>(g, in, nullptr, nullptr, nullptr, c, err, dm, st)
-                     : launch_fl_any<1, false>(g, in, nullptr, nullptr, nullptr, c, err, dm, st);
+    return kind == 2 ? launch_fl_any<2, false, false>(g, in, nullptr, nullptr, nullptr, c, err, dm, st)
+                     : launch_fl_any<1, false, false>(g, in, nullptr, nullptr, nullptr, c, err, dm, st);
 }
 
 // Raise a kernel's dynamic shared-memory limit once per device; *done holds

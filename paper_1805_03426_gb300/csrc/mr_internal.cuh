@@ -86,6 +86,8 @@ struct DeviceBuffers {
     float* cpad = nullptr;                     // MR_VEL_FUSED: padded FP32 coarse faces
     float* fsc = nullptr;                      // MR_VEL_FUSED: [nz][32] slab constants
     float* halo = nullptr;                     // y-slab: [3 levels][below, above][Nz][Nx] halo rows
+    float* tcp = nullptr;                      // MR_VEL_FUSED: upscale partials of the step (lazy)
+    double* tcinv = nullptr;                   // MR_VEL_FUSED: 1 / (mx my sum of each slab's dz) (lazy)
     float xw4[8] = {0};                        // fourth order: twice the x and y face weights (uniform)
     int xlcw = 12;                             // row length of xlc
     double* diag = nullptr;                    // diagnostics: coarse T, Nu(z), dense z centres (lazy)
@@ -215,6 +217,8 @@ struct FusedInputs {
     const float* lc;     // [Nz][32] layer constants (xfused_layer_constants)
     const float* rx12;   // R_x rows of the 4 cells of a 4-cell segment (uniform, periodic x)
     const float* ry12;   // R_y rows of dense rows 0..3 (uniform, periodic y)
+    // NULL, or the step's upscale partials [nz][Ny][nx] (launch_fused_tc_reduce)
+    float* tcp;
 };
 // every refinement stage in the step kernel
 cudaError_t launch_step_fused_f32(const Grid<float>& g, const FusedInputs& in, const float* Tm1, const float* T,
@@ -222,6 +226,9 @@ cudaError_t launch_step_fused_f32(const Grid<float>& g, const FusedInputs& in, c
 // kind 1: max |divergence| of the dense velocity, kind 2: max CFL rate (into partials[0])
 cudaError_t launch_fused_max_f32(const Grid<float>& g, int kind, const FusedInputs& in, double* partials, int blocks,
                                  cudaStream_t st);
+// Tc (nz x ny x nx, FP64) from the fused step's upscale partials; inv[K] = 1 / (mx my sum of slab K's dz)
+cudaError_t launch_fused_tc_reduce(const Grid<float>& g, const float* tcp, const double* inv, double* Tc,
+                                   cudaStream_t st);
 // floats of the padded coarse faces, and the kernel that forms them from the FP32 coarse faces
 size_t fused_pad_floats(int nx, int ny, int nz);
 // (the coarse rows j0-1 .. j0+ny+1 of a domain of nyg rows, periodic)

@@ -75,12 +75,36 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity, unsigned
     }
     return false;
 }
+// Bounded wait for a warp with slack (a producer that runs ahead of its
+// consumers, a builder a slab ahead): between polls it sleeps sleep_ns, so
+// that its polling does not take issue slots from the warps on the critical
+// path.  true on success.
+__device__ __forceinline__ bool mbar_wait_idle(uint64_t* b, uint32_t parity, unsigned long long limit_ns,
+                                               unsigned sleep_ns)
+{
+    if (mbar_test(b, parity)) return true;
+    const unsigned long long t0 = global_ns();
+    for (long it = 0; it < kWaitLimit; ++it) {
+        __nanosleep(sleep_ns);
+        if (mbar_test(b, parity)) return true;
+        if (global_ns() - t0 > limit_ns) break;
+    }
+    return false;
+}
 __device__ __forceinline__ void tma_3d(void* dst, const CUtensorMap* map, int x, int y, int z, uint64_t* bar)
 {
     asm volatile(
         "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];"
         ::"r"(sa(dst)), "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(sa(bar))
         : "memory");
+}
+// L2 prefetch of a 3-D TMA tile (nothing lands in shared memory, nothing to
+// wait for); coordinates outside the tensor fetch nothing.
+__device__ __forceinline__ void tma_prefetch_3d(const CUtensorMap* map, int x, int y, int z)
+{
+    asm volatile("cp.async.bulk.prefetch.tensor.3d.L2.global.tile [%0, {%1, %2, %3}];"
+                 ::"l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z)
+                 : "memory");
 }
 __device__ __forceinline__ void cp_async4(float* dst, const float* src)
 {

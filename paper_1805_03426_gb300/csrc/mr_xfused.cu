@@ -37,6 +37,14 @@ using namespace ptx;
 constexpr int kTX = 64;                                // tile width (cells); the height TY is 16 or 8
 constexpr int kBX = kTX + 8;                            // scalar plane box width (floats)
 constexpr float kTBottom = 0.5f, kTTop = -0.5f;
+#ifndef MR_XFUSED_IDLE_NS
+#define MR_XFUSED_IDLE_NS 256
+#endif
+constexpr unsigned kIdleNs = MR_XFUSED_IDLE_NS;  // sleep between the producer warp's polls
+#ifndef MR_XFUSED_PREFETCH
+#define MR_XFUSED_PREFETCH 0
+#endif
+constexpr int kPrefetch = MR_XFUSED_PREFETCH;     // planes of L2 prefetch ahead of the ring's loads
 
 // O4: fourth-order face values of T^s (Section 2.2): the T^s box has two halo
 // rows each side and the layer constants carry the z-face weights.
@@ -179,7 +187,7 @@ k_xfused(const __grid_constant__ CUtensorMap tmn, const __grid_constant__ CUtens
         for (int r = 0; r < nrings; ++r) {
             const int s = r % NB;
             if (stopper && r == A.stop_ring) break;  // every ring issued so far is waited for by the consumers
-            if (r >= NB && !mbar_wait(&empty[s], ((r / NB) - 1) & 1, A.wait_ns)) {
+            if (r >= NB && !mbar_wait_idle(&empty[s], ((r / NB) - 1) & 1, A.wait_ns, kIdleNs)) {
                 atomicExch(A.err, MR_ERR_TIMEOUT);   // consumers then time out on full[]
                 break;
             }
@@ -192,6 +200,11 @@ k_xfused(const __grid_constant__ CUtensorMap tmn, const __grid_constant__ CUtens
             if (!DIVONLY) {
                 tma_3d(slot + L::oTn, &tmn, i0 - 4, j0 - (O4 ? 2 : 1), p, &full[s]);
                 tma_3d(slot + L::oTm, &tmm, i0 - 4, j0 - 1, p, &full[s]);
+                if (kPrefetch > 0 && p + kPrefetch <= k1) {
+                    // the planes a few rings ahead into L2: deeper in flight than the ring
+                    tma_prefetch_3d(&tmn, i0 - 4, j0 - (O4 ? 2 : 1), p + kPrefetch);
+                    tma_prefetch_3d(&tmm, i0 - 4, j0 - 1, p + kPrefetch);
+                }
             }
             if (wy) {
                 tma_3d(slot + L::oWY, &twy, I0, j0, p, &full[s]);   // WY plane p
@@ -1024,7 +1037,7 @@ cudaError_t launch_xfused_max_f32(const Grid<float>& g, int kind, const float* W
 // Per-layer constants of the split-x and fully fused kernels, [Nz][32] floats,
 // all folded on the host in FP64.  The pair entries hold each value twice, for
 // the packed pair arithmetic of the update:
-//   0: 1/dz, 1: 1/(2 dz), 4..7: fourth order only, the weights of planes
+//   0: 1/dz, 1: 1/(2 dz), 2: dz, 4..7: fourth order only, the weights of planes
 //   k-2 .. k+1 at face k (the first layer of a chunk);
 //   12..19 (pairs): second order, the linear-interpolation weights of T_{k-1},
 //   T_k at face k and the negated weights of T_k, T_{k+1} at face k+1, each
@@ -1070,6 +1083,7 @@ std::vector<float> xfused_layer_constants(int Nz, const double* zf, const double
         if (dirichlet && k == Nz - 1) plate += cup * (double)kTTop;
         q[0] = (float)idz;
         q[1] = (float)(0.5 * idz);
+        q[2] = (float)dzk;
         const double pv[8] = {zw[0], zw[1], zw[2], zw[3], cdn, cup, -(2.0 * kx2 + 2.0 * ky2 + cdn + cup), plate};
         for (int c = 0; c < 8; ++c) q[12 + 2 * c] = q[13 + 2 * c] = (float)pv[c];
     }

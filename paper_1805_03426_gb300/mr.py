@@ -79,6 +79,7 @@ _SIGS = {
     "mr_refine_velocity_noalloc": (ctypes.c_int, [ctypes.POINTER(mr_config), _VP, _VP, _VP, _VP, _VP, _VP, _VP]),
     "mr_fp64_fma_rate": (ctypes.c_int, [ctypes.POINTER(_D), _VP]),
     "mr_get_boundary_rows": (ctypes.c_int, [_VP, _VP, _VP, _VP]),
+    "mr_scalar_step_coupled": (ctypes.c_int, [_VP, _VP, _VP, _VP]),
     "mr_set_halo_rows": (ctypes.c_int, [_VP, _VP, _VP, _VP]),
     "mr_debug_inject_wait_timeout": (ctypes.c_int, [_I32, _D]),
     "mr_debug_alloc_cap": (ctypes.c_int, [_I64, ctypes.POINTER(_I64)]),
@@ -413,3 +414,11 @@ def mr_set_halo_rows(h: Handle, below, above, stream=None):
     Nx, _, Nz = h.dense
     _check(lib().mr_set_halo_rows(h.ptr, _ptr(below, Nx * Nz, h.np_dtype, "below"),
                                   _ptr(above, Nx * Nz, h.np_dtype, "above"), _stream(stream)))
+
+
+def mr_scalar_step_coupled(h: Handle, nu2=None, Tc=None, stream=None):
+    """One step, then the plate Nusselt numbers (2 doubles) and the upscaled
+    coarse T (Section 3.3) of the new level into device or pinned host tensors."""
+    c = h.cfg
+    _check(lib().mr_scalar_step_coupled(h.ptr, _ptr(nu2, 2, np.float64, "nu2"),
+                                        _ptr(Tc, c.nz * h.coarse_rows * c.nx, np.float64, "Tc"), _stream(stream)))

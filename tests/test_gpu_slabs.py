@@ -93,10 +93,15 @@ def test_slab_handles_reproduce_whole_domain(mr, name):
     assert torch.equal(torch.cat(Ts, dim=1), Tw)
     assert torch.equal(torch.cat(Tps, dim=1), Tpw)
     comb = slabs.combine_stats(stats)
-    for k in ("integral", "mean", "nu_bot", "nu_top"):
-        assert abs(comb[k] - stw[k]) <= 1e-12 * max(1.0, abs(stw[k])), k
-    # the FP32 path's moment kernel sums groups of 16 squared deviations in FP32
-    # before its FP64 accumulation: a variance good to ~1e-9 relative either way
+    for k in ("nu_bot", "nu_top"):
+        assert abs(comb[k] - stw[k]) <= 1e-12 * abs(stw[k]), k
+    # the FP32 path's moment kernel sums groups of 16 values in FP32 before its
+    # FP64 accumulation, so its integral and mean are good to ~1e-9 of the
+    # integral of |T| (|T| <= 0.5 here, and the signed sum nearly cancels) and
+    # its variance to ~1e-9 relative, however the domain is split
+    V = sum(s.volume for s in stats)
+    assert abs(comb["integral"] - stw["integral"]) <= 1e-9 * 0.5 * V
+    assert abs(comb["mean"] - stw["mean"]) <= 1e-9 * 0.5
     assert abs(comb["var"] - stw["var"]) <= 1e-8 * stw["var"]
     # the refined velocity of the slabs is the whole domain's, row for row
     assert comb["max_div"] == pytest.approx(stw["max_div"], rel=1e-6)
