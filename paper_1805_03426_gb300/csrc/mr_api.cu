@@ -395,7 +395,7 @@ void mr_destroy(mr_handle h)
         for (void* p : cptrs)
             if (p) dev_free(p);
     }
-    void* xptrs[] = {b.xwy, b.xuo, b.xvr, b.xlc, b.diag, b.cpad, b.fsc, n.cpad, b.halo, b.tcp, b.tcinv};
+    void* xptrs[] = {b.xwy, b.xuo, b.xvr, b.xlc, b.diag, b.cpad, b.fsc, n.cpad, b.halo, b.tcp, b.tcinv, b.nup};
     for (void* p : xptrs)
         if (p) dev_free(p);
     for (int q = 0; q < 2; ++q) {
@@ -729,7 +729,8 @@ static int one_step(mr_handle h, double alpha, cudaStream_t st, float* tcp = nul
                                    (const float*)Tm1,
                                    (const float*)b.T[h->ic], (float*)b.T[in], c, st);
     } else if (h->cfg.velocity_mode == MR_VEL_FUSED) {
-        FusedInputs fin{b.cpad, {}, {}, 0, b.fsc, b.xlc, b.xrx, b.xry, tcp};
+        FusedInputs fin{b.cpad, {}, {}, 0, b.fsc, b.xlc, b.xrx, b.xry, tcp, b.nup,
+                        1.0 / (h->zc[0] - h->zf[0]), 1.0 / (h->zf[h->Nz] - h->zc[h->Nz - 1])};
         // the rows beyond the y edges of T^s and T^{s-1}
         const int lm = h->step == 0 ? h->ic : h->ip;
         if (h->slab) {
@@ -1035,11 +1036,13 @@ int mr_scalar_step_coupled(mr_handle h, double* nu2, double* Tc, mr_stream strea
     DeviceBuffers& b = h->buf;
     const bool fused = h->cfg.velocity_mode == MR_VEL_FUSED;
     int rc;
-    if (fused && dtc && !b.tcp) {
-        // the fused step leaves the upscale partials; the FP64 factors per slab
+    if (fused && (dtc || dnu) && !b.tcp) {
+        // the fused step leaves the upscale partials and the plate-flux sums;
+        // the FP64 factors per slab
         const mr_config& c = h->cfg;
         cudaError_t e = dev_malloc(&b.tcp, (size_t)c.nz * h->Nys * c.nx * sizeof(float));
         if (e == cudaSuccess) e = dev_malloc(&b.tcinv, (size_t)c.nz * sizeof(double));
+        if (e == cudaSuccess) e = dev_malloc(&b.nup, fused_nu_partials(h->g32) * sizeof(double));
         std::vector<double> inv(c.nz);
         for (int K = 0; K < c.nz; ++K) {
             double z = 0.0;
@@ -1050,12 +1053,14 @@ int mr_scalar_step_coupled(mr_handle h, double* nu2, double* Tc, mr_stream strea
         if (e != cudaSuccess) {
             dev_free(b.tcp);
             dev_free(b.tcinv);
+            dev_free(b.nup);
             b.tcp = nullptr;
             b.tcinv = nullptr;
+            b.nup = nullptr;
             return cuda_check(e, "mr_scalar_step_coupled: upscale partials");
         }
     }
-    if (fused && dtc) {
+    if (fused && (dtc || dnu)) {
         // the step kernel forms the upscale partials of the new level itself
         if (h->slab && !(h->halo_set[h->ic] && (h->step == 0 || h->halo_set[h->ip])))
             return set_error(MR_ERR_STATE, "mr_scalar_step_coupled: set the y-slab's halo rows first");
@@ -1067,7 +1072,9 @@ int mr_scalar_step_coupled(mr_handle h, double* nu2, double* Tc, mr_stream strea
     }
     if (rc) return rc;
     cudaError_t e = cudaSuccess;
-    if (dnu) {
+    if (dnu && fused) {
+        e = launch_fused_nu_finish(h->g32, b.nup, dnu, st);
+    } else if (dnu) {
         const double zz[2] = {h->zc[0] - h->zf[0], h->zf[h->Nz] - h->zc[h->Nz - 1]};
         e = h->cfg.precision == MR_F64
                 ? launch_plate_nu<double>(h->g64, (const double*)h->buf.T[h->ic], zz, h->buf.nu2, st)
@@ -1140,7 +1147,7 @@ static int max_divergence(mr_handle h, double* out, cudaStream_t st)
     if (h->cfg.velocity_mode == MR_VEL_XFUSED)
         e = launch_xfused_max_f32(h->g32, 1, b.xwy, b.xuo, b.xvr, b.nxg, b.xlc, b.xlcw, b.xrx, b.red, h->red_blocks, st);
     else if (h->cfg.velocity_mode == MR_VEL_FUSED)
-        e = launch_fused_max_f32(h->g32, 1, FusedInputs{b.cpad, {}, {}, 0, b.fsc, b.xlc, b.xrx, b.xry, nullptr}, b.red,
+        e = launch_fused_max_f32(h->g32, 1, FusedInputs{b.cpad, {}, {}, 0, b.fsc, b.xlc, b.xrx, b.xry, nullptr, nullptr, 0.0, 0.0}, b.red,
                                  h->red_blocks, st);
     else if (h->cfg.precision == MR_F64)
         e = launch_maxdiv<double>(h->g64, (const double*)b.Us, (const double*)b.Vs, (const double*)b.Ws, b.red,
@@ -1222,7 +1229,7 @@ int mr_cfl_dt(mr_handle h, double cfl, double* dt_out, mr_stream stream)
         e = launch_xfused_max_f32(h->g32, 2, b.xwy, b.xuo, b.xvr, b.nxg, b.xlc, b.xlcw, b.xrx, b.red, h->red_blocks, st);
     } else if (h->cfg.velocity_mode == MR_VEL_FUSED) {
         // the fused kernel forms the dense faces in registers from the coarse ones
-        e = launch_fused_max_f32(h->g32, 2, FusedInputs{b.cpad, {}, {}, 0, b.fsc, b.xlc, b.xrx, b.xry, nullptr}, b.red,
+        e = launch_fused_max_f32(h->g32, 2, FusedInputs{b.cpad, {}, {}, 0, b.fsc, b.xlc, b.xrx, b.xry, nullptr, nullptr, 0.0, 0.0}, b.red,
                                  h->red_blocks, st);
     } else if (h->cfg.velocity_mode != MR_VEL_STORED) {
         // dense faces are not kept: refine into temporary buffers once

@@ -58,10 +58,6 @@ constexpr int kSCW = 32;                // slab-constant row (floats)
 #define MR_FUSED_IDLE_NS 256
 #endif
 constexpr unsigned kIdleNs = MR_FUSED_IDLE_NS;   // sleep between the polls of the producer and builder warps
-#ifndef MR_FUSED_PREFETCH
-#define MR_FUSED_PREFETCH 6
-#endif
-constexpr int kPrefetch = MR_FUSED_PREFETCH;      // planes of L2 prefetch ahead of the ring's loads
 
 __host__ __device__ constexpr int up32(int n) { return (n + 31) / 32 * 32; }
 
@@ -124,6 +120,9 @@ struct FLArgs {
     size_t hstride;      // layer stride of those rows
     float* tcp;          // NULL, or [nz][Ny][nx]: per coarse slab, dense row and coarse column,
                          // sum over the slab's layers of dz times the column's new values
+    double* nup;         // with tcp: [2][tiles][NCW] per-warp sums of the plate fluxes of the new
+                         // level, (0.5 - T) / zb on the bottom layer, (T + 0.5) / zt on the top one
+    double izb, izt;     // 1 / zb, 1 / zt (the plate-to-centre distances)
 };
 
 // R_x split of three coarse values by one row of R (rows sum to one).
@@ -289,7 +288,8 @@ __device__ void build_slab(const FLArgs& A, const float* __restrict__ cb, float*
 
 // KIND 0: the step; 1: max |divergence| of the dense velocity; 2: max CFL rate.
 // LF: a plain leapfrog step (a = 1, b = 0).  TC: the step also leaves the
-// upscale partials of the new level (A.tcp).
+// upscale partials (A.tcp) and the per-warp plate-flux sums (A.nup) of the
+// new level, which a coupled coarse solver takes back every step.
 template <int M, int TY, int KIND, bool LF, bool TC = false>
 __global__ void __launch_bounds__(FL<M, TY, (KIND != 0)>::THREADS, FL<M, TY, (KIND != 0)>::CTAS)
 k_fused(const __grid_constant__ CUtensorMap tmn, const __grid_constant__ CUtensorMap tmm,
@@ -373,11 +373,6 @@ k_fused(const __grid_constant__ CUtensorMap tmn, const __grid_constant__ CUtenso
                 if (!DIVONLY) {
                     tma_3d(slot + L::oTn, &tmn, i0 - 4, j0 - 1, p, &full[s]);
                     tma_3d(slot + L::oTm, &tmm, i0 - 4, j0 - 1, p, &full[s]);
-                    if (kPrefetch > 0 && p + kPrefetch <= k1) {
-                        // the planes a few rings ahead into L2: deeper in flight than the ring
-                        tma_prefetch_3d(&tmn, i0 - 4, j0 - 1, p + kPrefetch);
-                        tma_prefetch_3d(&tmm, i0 - 4, j0 - 1, p + kPrefetch);
-                    }
                 }
                 if (lc) tma_3d(slot + L::oLC, &tlc, 0, p - 1, 0, &full[s]);
                 rings_issued = r + 1;
@@ -614,6 +609,21 @@ k_fused(const __grid_constant__ CUtensorMap tmn, const __grid_constant__ CUtenso
                                 tcs[q] = 0.f;
                             }
                         }
+                        if (k == 0 || k == g.Nz - 1) {
+                            // the plate Nusselt numbers (Section 4.1): FP64 sums of the
+                            // conductive plate fluxes, one per warp
+                            const bool bot = (k == 0);
+                            const double v[4] = {res[0].x, res[0].y, res[1].x, res[1].y};
+                            double f = 0.0;
+#pragma unroll
+                            for (int a = 0; a < 4; ++a) f += bot ? (0.5 - v[a]) * A.izb : (v[a] + 0.5) * A.izt;
+#pragma unroll
+                            for (int d = 16; d > 0; d >>= 1) f += __shfl_down_sync(0xffffffffu, f, d);
+                            if (lane == 0) {
+                                const int tile = blockIdx.y + gridDim.y * blockIdx.z;
+                                A.nup[((size_t)(bot ? 0 : 1) * gridDim.y * gridDim.z + tile) * NCW + warp] = f;
+                            }
+                        }
                     }
                 }
             }
@@ -808,6 +818,9 @@ cudaError_t launch_fl(const Grid<float>& g, const FusedInputs& in, const float* 
         }
         A.hstride = in.hstride;
         A.tcp = in.tcp;
+        A.nup = in.nup;
+        A.izb = in.izb;
+        A.izt = in.izt;
     }
     k_fused<M, TY, KIND, LF, TC><<<dim3(chunks, g.Nx / kTX, g.Ny / TY), L::THREADS, L::bytes, st>>>(mn, mm, mlc, mu,
                                                                                                    mv, mw, A);
@@ -844,7 +857,40 @@ __global__ void k_tc_reduce(const float* __restrict__ tcp, const double* __restr
     }
 }
 
+// The plate Nusselt numbers from the step's per-warp sums: one block per
+// plate, a fixed order of additions (deterministic), divided by the plate's
+// cell count.
+__global__ void __launch_bounds__(1024) k_nu_finish(const double* __restrict__ nup, size_t per_plate, double inv_n,
+                                                    double* __restrict__ nu2)
+{
+    __shared__ double red[1024];
+    const double* p = nup + (size_t)blockIdx.x * per_plate;
+    double s = 0.0;
+    for (size_t m = threadIdx.x; m < per_plate; m += 1024) s += p[m];
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int w = 512; w > 0; w >>= 1) {
+        if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) nu2[blockIdx.x] = red[0] * inv_n;
+}
+
 }  // namespace
+
+cudaError_t launch_fused_nu_finish(const Grid<float>& g, const double* nup, double* nu2, cudaStream_t st)
+{
+    const size_t tiles = (size_t)(g.Nx / kTX) * (g.Ny / (g.mx == 4 ? 16 : 8));
+    const size_t warps = (g.mx == 4 ? 16 : 8) / 2;
+    k_nu_finish<<<2, 1024, 0, st>>>(nup, tiles * warps, 1.0 / ((double)g.Nx * g.Ny), nu2);
+    return cudaGetLastError();
+}
+
+size_t fused_nu_partials(const Grid<float>& g)
+{
+    const int ty = g.mx == 4 ? 16 : 8;
+    return 2 * (size_t)(g.Nx / kTX) * (g.Ny / ty) * (ty / 2);
+}
 
 cudaError_t launch_fused_tc_reduce(const Grid<float>& g, const float* tcp, const double* inv, double* Tc,
                                    cudaStream_t st)

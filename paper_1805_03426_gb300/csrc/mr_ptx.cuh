@@ -98,14 +98,6 @@ __device__ __forceinline__ void tma_3d(void* dst, const CUtensorMap* map, int x,
         ::"r"(sa(dst)), "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(sa(bar))
         : "memory");
 }
-// L2 prefetch of a 3-D TMA tile (nothing lands in shared memory, nothing to
-// wait for); coordinates outside the tensor fetch nothing.
-__device__ __forceinline__ void tma_prefetch_3d(const CUtensorMap* map, int x, int y, int z)
-{
-    asm volatile("cp.async.bulk.prefetch.tensor.3d.L2.global.tile [%0, {%1, %2, %3}];"
-                 ::"l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z)
-                 : "memory");
-}
 __device__ __forceinline__ void cp_async4(float* dst, const float* src)
 {
     asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(sa(dst)), "l"(src) : "memory");

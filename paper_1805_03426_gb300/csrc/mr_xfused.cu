@@ -41,10 +41,6 @@ constexpr float kTBottom = 0.5f, kTTop = -0.5f;
 #define MR_XFUSED_IDLE_NS 256
 #endif
 constexpr unsigned kIdleNs = MR_XFUSED_IDLE_NS;  // sleep between the producer warp's polls
-#ifndef MR_XFUSED_PREFETCH
-#define MR_XFUSED_PREFETCH 0
-#endif
-constexpr int kPrefetch = MR_XFUSED_PREFETCH;     // planes of L2 prefetch ahead of the ring's loads
 
 // O4: fourth-order face values of T^s (Section 2.2): the T^s box has two halo
 // rows each side and the layer constants carry the z-face weights.
@@ -200,11 +196,6 @@ k_xfused(const __grid_constant__ CUtensorMap tmn, const __grid_constant__ CUtens
             if (!DIVONLY) {
                 tma_3d(slot + L::oTn, &tmn, i0 - 4, j0 - (O4 ? 2 : 1), p, &full[s]);
                 tma_3d(slot + L::oTm, &tmm, i0 - 4, j0 - 1, p, &full[s]);
-                if (kPrefetch > 0 && p + kPrefetch <= k1) {
-                    // the planes a few rings ahead into L2: deeper in flight than the ring
-                    tma_prefetch_3d(&tmn, i0 - 4, j0 - (O4 ? 2 : 1), p + kPrefetch);
-                    tma_prefetch_3d(&tmm, i0 - 4, j0 - 1, p + kPrefetch);
-                }
             }
             if (wy) {
                 tma_3d(slot + L::oWY, &twy, I0, j0, p, &full[s]);   // WY plane p

@@ -57,11 +57,13 @@ def test_coupled_step_outputs(mr, kind, where):
     nu_ref = np.zeros(2)
     mr.mr_plate_nu(h, nu_ref)
     torch.cuda.synchronize()
-    assert np.array_equal(nu, nu_ref)
     if mode == 1:
-        # the fused step sums each coarse column's cells in its own order (FP32)
+        # the fused step sums the plate fluxes (FP64) and each coarse column's
+        # cells (FP32) itself, in its own order
+        assert np.abs(nu / nu_ref - 1).max() <= 1e-13
         assert np.abs(Tc - mr.mr_upscale_scalar(h)).max() <= 1e-6
     else:
+        assert np.array_equal(nu, nu_ref)
         assert np.array_equal(Tc, mr.mr_upscale_scalar(h))
     vel = O.refine(p.cfg, p.U, p.V, p.W)
     _, T_ref = O.run(p.cfg, vel, p.T0, n)
@@ -86,3 +88,57 @@ def test_coupled_step_refuses_pageable_host_memory(mr):
     assert e.value.code == mr.MR_ERR_ARG
     assert mr.mr_step_index(h) == 0           # refused before stepping
     h.close()
+
+
+def test_coupled_step_on_y_slabs_matches_whole_domain(mr):
+    """The coupled outputs of two y-slab handles, put together, are the whole
+    domain's: the slabs' coarse rows of Tc, and the plate Nusselt numbers as
+    the area-weighted mean of the slabs'."""
+    from paper_1805_03426_gb300 import slabs
+    p = Problem(nx=16, ny=8, nz=6, mx=4, my=4, mz=4, gamma=1.5, np_average=4, ra=1e6, pr=7.0, dt=2e-3)
+    U, V, W = dev(p.U), dev(p.V), dev(p.W)
+    T0 = dev(p.T0).float()
+    n = 5
+    hw = mr.mr_create(p.mr_config(mr, mr.MR_F32, mr.MR_VEL_FUSED))
+    mr.mr_refine_velocity(hw, U, V, W)
+    mr.mr_set_scalar(hw, T0)
+    mr.mr_scalar_step(hw, n - 1)
+    nuw = torch.zeros(2, dtype=torch.float64, device="cuda")
+    Tcw = torch.zeros((6, 8, 16), dtype=torch.float64, device="cuda")
+    mr.mr_scalar_step_coupled(hw, nuw, Tcw)
+    hub = slabs.LocalExchange(2)
+    parts = slabs.partition(8, 4, 2)
+    hs, steppers = [], []
+    for r, (j0, rows) in enumerate(parts):
+        cfg = p.mr_config(mr, mr.MR_F32, mr.MR_VEL_FUSED)
+        cfg.slab_j0, cfg.slab_ny = j0, rows
+        h = mr.mr_create(cfg)
+        mr.mr_refine_velocity(h, U, V, W)
+        hs.append(h)
+        steppers.append(slabs.SlabStepper(slabs.HandleEngine(mr, h), hub.endpoint(r), (24, 64), torch.float32, "cuda"))
+
+    def deliver():
+        hub.run()
+        for s in steppers:
+            s.finish_exchange()
+
+    for s, (j0, rows) in zip(steppers, parts):
+        s.set_scalar(T0[:, j0 * 4:(j0 + rows) * 4, :].contiguous())
+    deliver()
+    for _ in range(n - 1):
+        for s in steppers:
+            s.step()
+        deliver()
+    nus, Tcs = [], []
+    for h, (j0, rows) in zip(hs, parts):
+        nu = torch.zeros(2, dtype=torch.float64, device="cuda")
+        Tc = torch.zeros((6, rows, 16), dtype=torch.float64, device="cuda")
+        mr.mr_scalar_step_coupled(h, nu, Tc)
+        nus.append(nu)
+        Tcs.append(Tc)
+    torch.cuda.synchronize()
+    assert torch.equal(torch.cat(Tcs, dim=1), Tcw)
+    nu = (nus[0] + nus[1]) / 2          # equal slab areas
+    assert float((nu / nuw - 1).abs().max()) <= 1e-13
+    for h in hs + [hw]:
+        h.close()
