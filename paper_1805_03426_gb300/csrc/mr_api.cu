@@ -681,12 +681,19 @@ static int load_velocity(mr_handle h, const double* U, const double* V, const do
 static int derive_velocity(mr_handle h, bool convert, cudaStream_t st)
 {
     DeviceBuffers& b = h->buf;
-    int rc;
     h->maxdiv_valid = false;
+    if (h->cfg.velocity_mode == MR_VEL_FUSED && convert) {
+        // the FP64 faces straight to the padded FP32 copy (and the FP32 faces)
+        cudaError_t e = launch_fused_pad64(b.U64, b.V64, b.W64, b.cpad, (float*)b.Uc, (float*)b.Vc, (float*)b.Wc,
+                                           h->cfg.nx, h->cfg.ny, h->cfg.nz, h->slab ? h->cfg.slab_j0 : 0, h->nys, st);
+        return cuda_check(e, "padded coarse faces");
+    }
     if (h->cfg.precision == MR_F32 && convert) {
-        if ((rc = copy_in(h, b.U64, MR_F64, b.Uc, MR_F32, h->ncU, st))) return rc;
-        if ((rc = copy_in(h, b.V64, MR_F64, b.Vc, MR_F32, h->ncV, st))) return rc;
-        if ((rc = copy_in(h, b.W64, MR_F64, b.Wc, MR_F32, h->ncW, st))) return rc;
+        // the handle's own FP64 device faces: no pointer queries
+        cudaError_t e = launch_convert<double>(b.U64, MR_F64, b.Uc, MR_F32, h->ncU, st);
+        if (e == cudaSuccess) e = launch_convert<double>(b.V64, MR_F64, b.Vc, MR_F32, h->ncV, st);
+        if (e == cudaSuccess) e = launch_convert<double>(b.W64, MR_F64, b.Wc, MR_F32, h->ncW, st);
+        if (e != cudaSuccess) return cuda_check(e, "coarse faces to FP32");
     }
     if (h->cfg.velocity_mode == MR_VEL_XFUSED) {
         cudaError_t e = launch_xfused_prep(h->g32, (const float*)b.Uc, (const float*)b.Vc, (const float*)b.Wc,

@@ -840,6 +840,41 @@ cudaError_t launch_fl_any(const Grid<float>& g, const FusedInputs& in, const flo
     else return launch_fl<4, 8, KIND, LF, TC>(g, in, Tm1, T, Tp1, c, err, divmax, st);
 }
 
+// The same padding from the FP64 coarse faces, rounding them to FP32 once;
+// on a whole-domain grid (j0 = 0, ny = nyg) the interior of the padded copy
+// also goes to the unpadded FP32 faces U32, V32, W32 (one pass instead of a
+// conversion and a padding).
+__global__ void k_pad_coarse64(const double* __restrict__ U, const double* __restrict__ V,
+                               const double* __restrict__ W, float* __restrict__ out, float* __restrict__ U32,
+                               float* __restrict__ V32, float* __restrict__ W32, int nx, int nyg, int nz, int j0,
+                               int ny)
+{
+    const int px = nx + 8;
+    const size_t nU = (size_t)nz * (ny + 2) * px, nV = (size_t)nz * (ny + 3) * px, nW = (size_t)(nz + 1) * (ny + 2) * px;
+    const bool whole = (j0 == 0 && ny == nyg);
+    for (size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x; t < nU + nV + nW;
+         t += (size_t)gridDim.x * blockDim.x) {
+        const double* src;
+        float* dst;
+        size_t e;
+        int rows;
+        if (t < nU) { src = U; dst = U32; e = t; rows = ny + 2; }
+        else if (t < nU + nV) { src = V; dst = V32; e = t - nU; rows = ny + 3; }
+        else { src = W; dst = W32; e = t - nU - nV; rows = ny + 2; }
+        const int x = (int)(e % px);
+        const size_t zr = e / px;
+        const int r = (int)(zr % rows), z = (int)(zr / rows);
+        int I = x - 4, J = j0 + r - 1;
+        const bool interior = (I >= 0 && I < nx && J >= 0 && J < nyg && r >= 1 && r <= ny);
+        I = I < 0 ? I + nx : (I >= nx ? I - nx : I);
+        J = J < 0 ? J + nyg : (J >= nyg ? J - nyg : J);
+        const size_t m = ((size_t)z * nyg + J) * nx + I;
+        const float v = (float)src[m];
+        out[t] = v;
+        if (whole && interior) dst[m] = v;
+    }
+}
+
 // Tc[K][J][I] from the step's upscale partials: the sum over the coarse row's
 // my dense rows, times 1 / (mx my sum of the slab's dz) (FP64).
 __global__ void k_tc_reduce(const float* __restrict__ tcp, const double* __restrict__ inv, double* __restrict__ Tc,
@@ -890,6 +925,16 @@ size_t fused_nu_partials(const Grid<float>& g)
 {
     const int ty = g.mx == 4 ? 16 : 8;
     return 2 * (size_t)(g.Nx / kTX) * (g.Ny / ty) * (ty / 2);
+}
+
+cudaError_t launch_fused_pad64(const double* U, const double* V, const double* W, float* out, float* U32, float* V32,
+                               float* W32, int nx, int nyg, int nz, int j0, int ny, cudaStream_t st)
+{
+    const size_t n = fused_pad_floats(nx, ny, nz);
+    const size_t want = (n + 255) / 256;
+    const unsigned blocks = (unsigned)(want < 152 * 16 ? want : 152 * 16);
+    k_pad_coarse64<<<blocks, 256, 0, st>>>(U, V, W, out, U32, V32, W32, nx, nyg, nz, j0, ny);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_fused_tc_reduce(const Grid<float>& g, const float* tcp, const double* inv, double* Tc,

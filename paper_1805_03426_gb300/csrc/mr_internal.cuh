@@ -241,6 +241,9 @@ size_t fused_pad_floats(int nx, int ny, int nz);
 // (the coarse rows j0-1 .. j0+ny+1 of a domain of nyg rows, periodic)
 cudaError_t launch_fused_pad(const float* U, const float* V, const float* W, float* out, int nx, int nyg, int nz,
                              int j0, int ny, cudaStream_t st);
+// the same from the FP64 coarse faces, also writing the FP32 faces on a whole-domain grid
+cudaError_t launch_fused_pad64(const double* U, const double* V, const double* W, float* out, float* U32, float* V32,
+                               float* W32, int nx, int nyg, int nz, int j0, int ny, cudaStream_t st);
 // per coarse slab: R_z rows, 1/(2 dz) and the stage-Z weights, [nz][32]
 std::vector<float> fused_slab_constants(int nz, int M, const double* Rz, const double* dz);
 int* fused_error_flag();
