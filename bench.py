@@ -64,9 +64,10 @@ STEP_LABEL = {
 # DRAM bytes (read + write) per launch of the dominant kernel from one ncu capture of the
 # workload (summarised in profiles/), valid only for the kernel sources they were measured on.
 NCU_TRAFFIC = {
-    ("k_xfused", "rb512_stretched_f32"): {"bytes": 1153799936 + 384546048, "sources": "f3cacf946487e655.8945e0b384d6ff21",
+    # ncu printed the split-x read bytes to three digits
+    ("k_xfused", "rb512_stretched_f32"): {"bytes": int(1.150e9) + 384230000, "sources": "a0d17f174842153e.c41e21757bf0efe9",
                                           "files": ("mr_xfused.cu", "mr_ptx.cuh")},
-    ("k_fused", "rb512_stretched_f32"): {"bytes": 874555904 + 379363328, "sources": "d08bd9598cfdcca9.8945e0b384d6ff21",
+    ("k_fused", "rb512_stretched_f32"): {"bytes": 879000576 + 379811072, "sources": "1b47ade26da71535.c41e21757bf0efe9",
                                          "files": ("mr_fused.cu", "mr_ptx.cuh")},
 }
 
@@ -354,6 +355,25 @@ def run_mr(args):
             "kernel_frac_own_bytes": round(kernel_bpc * cells / per_launch / 1e9 / peak, 4),
             "traffic_over_algorithmic": round(traffic / (bytes_per_cell * cells), 3) if traffic else None}
 
+    # the fully fused mode beside the split-x one: every stage of the
+    # refinement inside the step kernel, nothing of it in HBM (the kernel
+    # moves the algorithmic bytes themselves)
+    fused = None
+    if rank == 0 and mode == mr.MR_VEL_XFUSED and not args.no_fused:
+        hf = _make(mr, w, prec, mr.MR_VEL_FUSED, dt=dt)
+        mr.mr_refine_velocity(hf, dU, dV, dW, stream=stream)
+        mr.mr_set_scalar(hf, dT0, stream=stream)
+        tf = _time_steps(torch, mr, hf, args.steps, args.warmup, stream)
+        hf.close()
+        pf = tf / args.steps
+        af = bytes_per_cell * cells / pf / 1e9
+        trf = _traffic("k_fused", args.workload)
+        fused = {"value": round(cells * args.steps / tf / 1e9, 3), "unit": "Gcell-updates/s", "steps": args.steps,
+                 "ms_per_step": round(pf * 1e3, 4), "kernel": "k_fused",
+                 "roofline": {"bound": "hbm", "achieved": round(af, 1), "peak": peak, "unit": "GB/s",
+                              "frac": round(af / peak, 4), "traffic": trf, "bytes_per_cell": round(bytes_per_cell, 3),
+                              "traffic_over_algorithmic": round(trf / (bytes_per_cell * cells), 3) if trf else None}}
+
     # the per-call costs around the step: statistics (the call synchronises:
     # wall clock) and plate Nu (asynchronous: stream-timed)
     aux = None
@@ -491,7 +511,7 @@ def run_mr(args):
             "dtype": "f32" if prec == mr.MR_F32 else "f64", "data": "synthetic",
             "config": bench_config(args, w, dt, world, args.mode),
             "roofline": roof, "precision_error": prec_err, "fp64_path": fp64, "adjoint": adj,
-            "temporal": temporal, "face_order4": face4,
+            "fused_mode": fused, "temporal": temporal, "face_order4": face4,
             "per_call": aux, "e2e": e2e,
             "cpu_baseline": cpu,
             "gpu_launches": args.steps, "clocks": clk.summary(),
@@ -683,6 +703,7 @@ def main():
     ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--no-temporal", action="store_true")
     ap.add_argument("--no-face4", action="store_true")
+    ap.add_argument("--no-fused", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
