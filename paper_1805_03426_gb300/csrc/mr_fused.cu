@@ -12,7 +12,7 @@
 //     window planes of U and V and the slab's two W planes, for the tile's
 //     coarse rows and columns with their neighbours, from a copy of the coarse
 //     faces padded with their periodic images so that every box is in bounds);
-//   - two builder warps form, from those coarse faces, the slab's refinement
+//   - three builder warps form, from those coarse faces, the slab's refinement
 //     stages at coarse resolution in x (two buffers: slab K+1 while slab K is
 //     stepped; the first slab of a chunk is built by every consumer and
 //     builder thread together):
@@ -58,6 +58,11 @@ constexpr int kSCW = 32;                // slab-constant row (floats)
 #define MR_FUSED_IDLE_NS 256
 #endif
 constexpr unsigned kIdleNs = MR_FUSED_IDLE_NS;   // sleep between the polls of the producer and builder warps
+// builder warps: three measured 0.379 ms per step on 512 x 512 x 384 (7.66 on
+// 1536 x 1536 x 1024) against 0.397 (8.19) with two and 0.392 (7.87) with four
+#ifndef MR_FUSED_BUILDER_WARPS
+#define MR_FUSED_BUILDER_WARPS 3
+#endif
 
 __host__ __device__ constexpr int up32(int n) { return (n + 31) / 32 * 32; }
 
@@ -67,7 +72,7 @@ template <int M, int TY, bool DIV>
 struct FL {
     static constexpr int CONS = 16 * TY;                    // consumer threads: 4-cell segments
     static constexpr int NCW = CONS / 32;                   // consumer warps
-    static constexpr int NBT = 64;                          // builder threads (two warps)
+    static constexpr int NBT = 32 * MR_FUSED_BUILDER_WARPS;  // builder threads
     static constexpr int THREADS = CONS + 32 + NBT;         // + producer warp + builder warps
     static constexpr int CTAS = TY == 16 ? 2 : 3;           // resident CTAs per SM the layout is sized for
     static constexpr int NB = DIV ? 8 : (TY == 16 ? 6 : (M == 4 ? 7 : 6));   // ring slots
@@ -234,41 +239,43 @@ __device__ void build_slab(const FLArgs& A, const float* __restrict__ cb, float*
 #pragma unroll
         for (int q = 0; q < 3; ++q) zc[c][q] = scg[4 * M + 3 * c + q];
     const float iDX = A.iDX, iDY = A.iDY, hx = A.hx;
-    // stage Z on the columns I0-1 .. I0+CX of coarse rows J0-1 .. J0+CY
-    constexpr int NZC = CX + 2;
-    for (int t = t0; t < NUR * NZC; t += NT) {
-        const int r = t / NZC, x = 3 + t - r * NZC;
-        float D[3];
+    // one pass over two kinds of items (so that the builder lanes stay busy):
+    // stage Z on the columns I0-1 .. I0+CX of coarse rows J0-1 .. J0+CY, and
+    // UO of the slab's M layers on the columns I0-1 .. I0+CX+1 (from the
+    // coarse faces alone, so before the barrier): the z split of the three
+    // window rows is shared by the coarse row's M dense rows
+    constexpr int NZC = CX + 2, NUC = CX + 3, NZI = NUR * NZC;
+    for (int t = t0; t < NZI + NUC * CY; t += NT) {
+        if (t < NZI) {
+            const int r = t / NZC, x = 3 + t - r * NZC;
+            float D[3];
 #pragma unroll
-        for (int q = 0; q < 3; ++q) {
-            const float uw = cu[(q * NUR + r) * BXC + x], ue = cu[(q * NUR + r) * BXC + x + 1];
-            const float vs = cv[(q * NVR + r) * BXC + x], vn = cv[(q * NVR + r + 1) * BXC + x];
-            D[q] = (ue - uw) * iDX + (vn - vs) * iDY;
-        }
-        const float wtop = cw[(NUR + r) * BXC + x];
+            for (int q = 0; q < 3; ++q) {
+                const float uw = cu[(q * NUR + r) * BXC + x], ue = cu[(q * NUR + r) * BXC + x + 1];
+                const float vs = cv[(q * NVR + r) * BXC + x], vn = cv[(q * NVR + r + 1) * BXC + x];
+                D[q] = (ue - uw) * iDX + (vn - vs) * iDY;
+            }
+            const float wtop = cw[(NUR + r) * BXC + x];
 #pragma unroll
-        for (int c = 0; c < M - 1; ++c)
-            sz[(c * NUR + r) * BXC + x] = wtop + zc[c][0] * D[0] + zc[c][1] * D[1] + zc[c][2] * D[2];
-    }
-    // UO of the slab's M layers on the columns I0-1 .. I0+CX+1 (from the coarse
-    // faces alone, so before the barrier): the z split of the three window rows
-    // is shared by the coarse row's M dense rows
-    constexpr int NUC = CX + 3;
-    for (int t = t0; t < NUC * CY; t += NT) {
-        const int Jc = t / NUC, x = 3 + t - Jc * NUC;
-        float u[3][3];
+            for (int c = 0; c < M - 1; ++c)
+                sz[(c * NUR + r) * BXC + x] = wtop + zc[c][0] * D[0] + zc[c][1] * D[1] + zc[c][2] * D[2];
+        } else {
+            const int u0 = t - NZI, Jc = u0 / NUC, x = 3 + u0 - Jc * NUC;
+            float u[3][3];
 #pragma unroll
-        for (int q = 0; q < 3; ++q)
+            for (int q = 0; q < 3; ++q)
 #pragma unroll
-            for (int p = 0; p < 3; ++p) u[q][p] = cu[(q * NUR + Jc + p) * BXC + x];
+                for (int p = 0; p < 3; ++p) u[q][p] = cu[(q * NUR + Jc + p) * BXC + x];
 #pragma unroll
-        for (int i = 0; i < M; ++i) {
-            float a[3];
+            for (int i = 0; i < M; ++i) {
+                float a[3];
 #pragma unroll
-            for (int p = 0; p < 3; ++p) a[p] = (rz[i][0] * u[0][p] + rz[i][1] * u[1][p] + rz[i][2] * u[2][p]) * hx;
-            float* dst = sb + L::bUO + (i * TY + Jc * M) * SXC + x - 3;
+                for (int p = 0; p < 3; ++p)
+                    a[p] = (rz[i][0] * u[0][p] + rz[i][1] * u[1][p] + rz[i][2] * u[2][p]) * hx;
+                float* dst = sb + L::bUO + (i * TY + Jc * M) * SXC + x - 3;
 #pragma unroll
-            for (int b = 0; b < M; ++b) dst[b * SXC] = A.ry[b][0] * a[0] + A.ry[b][1] * a[1] + A.ry[b][2] * a[2];
+                for (int b = 0; b < M; ++b) dst[b * SXC] = A.ry[b][0] * a[0] + A.ry[b][1] * a[1] + A.ry[b][2] * a[2];
+            }
         }
     }
     named_sync<NT>(bar);
@@ -441,8 +448,9 @@ k_fused(const __grid_constant__ CUtensorMap tmn, const __grid_constant__ CUtenso
             if (!fail && !mbar_wait(&full[r], 0, A.wait_ns)) fail = true;
         // one layer; sb, sc, st: the ring slots of planes k-1, k, k+1; tpar: the
         // parity of the ring of plane k+1
-        auto layer = [&](const int k, const int sb, const int sc, const int st, const int tpar) {
-            const int i = k & (M - 1), Kr = (k - k0) / M, bb = Kr & 1;
+        auto layer = [&](const int k, const int i, const int Kr, const int sb, const int sc, const int st,
+                         const int tpar) {
+            const int bb = Kr & 1;
             if (i == 0 && Kr > 0 && !fail && !mbar_wait(&built[bb], (Kr >> 1) & 1, A.wait_ns)) fail = true;
             if (!fail && !mbar_wait(&full[st], tpar, A.wait_ns)) fail = true;
             if (!fail) {
@@ -634,11 +642,13 @@ k_fused(const __grid_constant__ CUtensorMap tmn, const __grid_constant__ CUtenso
             outp += plane;
         };
         // the slots rotate (a loop unrolled by the ring length ran 8 % slower on
-        // 512 x 512 x 384: its copies of the layer body miss the instruction cache)
+        // 512 x 512 x 384: its copies of the layer body miss the instruction
+        // cache; unrolled by M, so that the slab offsets are constants, it was
+        // no faster)
         {
             int sb = 0, sc = 1, st = 2, tpar = 0;
             for (int k = k0; k < k1; ++k) {
-                layer(k, sb, sc, st, tpar);
+                layer(k, k & (M - 1), (k - k0) / M, sb, sc, st, tpar);
                 sb = sc;
                 sc = st;
                 if (++st == NB) {
