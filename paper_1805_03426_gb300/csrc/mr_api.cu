@@ -736,8 +736,7 @@ static int one_step(mr_handle h, double alpha, cudaStream_t st, float* tcp = nul
                                    (const float*)Tm1,
                                    (const float*)b.T[h->ic], (float*)b.T[in], c, st);
     } else if (h->cfg.velocity_mode == MR_VEL_FUSED) {
-        FusedInputs fin{b.cpad, {}, {}, 0, b.fsc, b.xlc, b.xrx, b.xry, tcp, b.nup,
-                        1.0 / (h->zc[0] - h->zf[0]), 1.0 / (h->zf[h->Nz] - h->zc[h->Nz - 1])};
+        FusedInputs fin{b.cpad, {}, {}, 0, b.fsc, b.xlc, b.xrx, b.xry, tcp};
         // the rows beyond the y edges of T^s and T^{s-1}
         const int lm = h->step == 0 ? h->ic : h->ip;
         if (h->slab) {
@@ -1043,13 +1042,13 @@ int mr_scalar_step_coupled(mr_handle h, double* nu2, double* Tc, mr_stream strea
     DeviceBuffers& b = h->buf;
     const bool fused = h->cfg.velocity_mode == MR_VEL_FUSED;
     int rc;
-    if (fused && (dtc || dnu) && !b.tcp) {
-        // the fused step leaves the upscale partials and the plate-flux sums;
-        // the FP64 factors per slab
+    if (fused && (dtc || dnu) && !b.nup) {
+        // the fused step leaves the upscale partials; one reduction forms Tc
+        // from them and the plate Nusselt numbers from the new level
         const mr_config& c = h->cfg;
         cudaError_t e = dev_malloc(&b.tcp, (size_t)c.nz * h->Nys * c.nx * sizeof(float));
         if (e == cudaSuccess) e = dev_malloc(&b.tcinv, (size_t)c.nz * sizeof(double));
-        if (e == cudaSuccess) e = dev_malloc(&b.nup, fused_nu_partials(h->g32) * sizeof(double));
+        if (e == cudaSuccess) e = dev_malloc(&b.nup, fused_coupled_work(h->g32) * sizeof(double));
         std::vector<double> inv(c.nz);
         for (int K = 0; K < c.nz; ++K) {
             double z = 0.0;
@@ -1057,6 +1056,7 @@ int mr_scalar_step_coupled(mr_handle h, double* nu2, double* Tc, mr_stream strea
             inv[K] = 1.0 / (z * c.mx * c.my);
         }
         if (e == cudaSuccess) e = cudaMemcpy(b.tcinv, inv.data(), inv.size() * sizeof(double), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemset(b.nup, 0, sizeof(double));      // the reduction's block count
         if (e != cudaSuccess) {
             dev_free(b.tcp);
             dev_free(b.tcinv);
@@ -1067,7 +1067,7 @@ int mr_scalar_step_coupled(mr_handle h, double* nu2, double* Tc, mr_stream strea
             return cuda_check(e, "mr_scalar_step_coupled: upscale partials");
         }
     }
-    if (fused && (dtc || dnu)) {
+    if (fused && dtc) {
         // the step kernel forms the upscale partials of the new level itself
         if (h->slab && !(h->halo_set[h->ic] && (h->step == 0 || h->halo_set[h->ip])))
             return set_error(MR_ERR_STATE, "mr_scalar_step_coupled: set the y-slab's halo rows first");
@@ -1079,20 +1079,22 @@ int mr_scalar_step_coupled(mr_handle h, double* nu2, double* Tc, mr_stream strea
     }
     if (rc) return rc;
     cudaError_t e = cudaSuccess;
-    if (dnu && fused) {
-        e = launch_fused_nu_finish(h->g32, b.nup, dnu, st);
-    } else if (dnu) {
-        const double zz[2] = {h->zc[0] - h->zf[0], h->zf[h->Nz] - h->zc[h->Nz - 1]};
-        e = h->cfg.precision == MR_F64
-                ? launch_plate_nu<double>(h->g64, (const double*)h->buf.T[h->ic], zz, h->buf.nu2, st)
-                : launch_plate_nu<float>(h->g32, (const float*)h->buf.T[h->ic], zz, h->buf.nu2, st);
-        if (e == cudaSuccess) e = cudaMemcpyAsync(dnu, h->buf.nu2, 2 * sizeof(double), cudaMemcpyDefault, st);
+    if (fused && (dtc || dnu)) {
+        e = launch_fused_coupled_reduce(h->g32, b.tcp, b.tcinv, dtc, (const float*)h->buf.T[h->ic],
+                                        1.0 / (h->zc[0] - h->zf[0]), 1.0 / (h->zf[h->Nz] - h->zc[h->Nz - 1]), b.nup,
+                                        dnu, st);
+    } else {
+        if (dnu) {
+            const double zz[2] = {h->zc[0] - h->zf[0], h->zf[h->Nz] - h->zc[h->Nz - 1]};
+            e = h->cfg.precision == MR_F64
+                    ? launch_plate_nu<double>(h->g64, (const double*)h->buf.T[h->ic], zz, h->buf.nu2, st)
+                    : launch_plate_nu<float>(h->g32, (const float*)h->buf.T[h->ic], zz, h->buf.nu2, st);
+            if (e == cudaSuccess) e = cudaMemcpyAsync(dnu, h->buf.nu2, 2 * sizeof(double), cudaMemcpyDefault, st);
+        }
+        if (e == cudaSuccess && dtc)
+            e = h->cfg.precision == MR_F64 ? launch_upscale<double>(h->g64, (const double*)h->buf.T[h->ic], dtc, st)
+                                           : launch_upscale<float>(h->g32, (const float*)h->buf.T[h->ic], dtc, st);
     }
-    if (e == cudaSuccess && dtc)
-        e = fused ? launch_fused_tc_reduce(h->g32, b.tcp, b.tcinv, dtc, st)
-                  : h->cfg.precision == MR_F64
-                        ? launch_upscale<double>(h->g64, (const double*)h->buf.T[h->ic], dtc, st)
-                        : launch_upscale<float>(h->g32, (const float*)h->buf.T[h->ic], dtc, st);
     return cuda_check(e, "mr_scalar_step_coupled");
 }
 
@@ -1154,7 +1156,7 @@ static int max_divergence(mr_handle h, double* out, cudaStream_t st)
     if (h->cfg.velocity_mode == MR_VEL_XFUSED)
         e = launch_xfused_max_f32(h->g32, 1, b.xwy, b.xuo, b.xvr, b.nxg, b.xlc, b.xlcw, b.xrx, b.red, h->red_blocks, st);
     else if (h->cfg.velocity_mode == MR_VEL_FUSED)
-        e = launch_fused_max_f32(h->g32, 1, FusedInputs{b.cpad, {}, {}, 0, b.fsc, b.xlc, b.xrx, b.xry, nullptr, nullptr, 0.0, 0.0}, b.red,
+        e = launch_fused_max_f32(h->g32, 1, FusedInputs{b.cpad, {}, {}, 0, b.fsc, b.xlc, b.xrx, b.xry, nullptr}, b.red,
                                  h->red_blocks, st);
     else if (h->cfg.precision == MR_F64)
         e = launch_maxdiv<double>(h->g64, (const double*)b.Us, (const double*)b.Vs, (const double*)b.Ws, b.red,
@@ -1236,7 +1238,7 @@ int mr_cfl_dt(mr_handle h, double cfl, double* dt_out, mr_stream stream)
         e = launch_xfused_max_f32(h->g32, 2, b.xwy, b.xuo, b.xvr, b.nxg, b.xlc, b.xlcw, b.xrx, b.red, h->red_blocks, st);
     } else if (h->cfg.velocity_mode == MR_VEL_FUSED) {
         // the fused kernel forms the dense faces in registers from the coarse ones
-        e = launch_fused_max_f32(h->g32, 2, FusedInputs{b.cpad, {}, {}, 0, b.fsc, b.xlc, b.xrx, b.xry, nullptr, nullptr, 0.0, 0.0}, b.red,
+        e = launch_fused_max_f32(h->g32, 2, FusedInputs{b.cpad, {}, {}, 0, b.fsc, b.xlc, b.xrx, b.xry, nullptr}, b.red,
                                  h->red_blocks, st);
     } else if (h->cfg.velocity_mode != MR_VEL_STORED) {
         // dense faces are not kept: refine into temporary buffers once

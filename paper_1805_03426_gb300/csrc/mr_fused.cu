@@ -40,6 +40,7 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <algorithm>
 #include <mutex>
 
 #include "mr_internal.cuh"
@@ -125,9 +126,6 @@ struct FLArgs {
     size_t hstride;      // layer stride of those rows
     float* tcp;          // NULL, or [nz][Ny][nx]: per coarse slab, dense row and coarse column,
                          // sum over the slab's layers of dz times the column's new values
-    double* nup;         // with tcp: [2][tiles][NCW] per-warp sums of the plate fluxes of the new
-                         // level, (0.5 - T) / zb on the bottom layer, (T + 0.5) / zt on the top one
-    double izb, izt;     // 1 / zb, 1 / zt (the plate-to-centre distances)
 };
 
 // R_x split of three coarse values by one row of R (rows sum to one).
@@ -295,8 +293,8 @@ __device__ void build_slab(const FLArgs& A, const float* __restrict__ cb, float*
 
 // KIND 0: the step; 1: max |divergence| of the dense velocity; 2: max CFL rate.
 // LF: a plain leapfrog step (a = 1, b = 0).  TC: the step also leaves the
-// upscale partials (A.tcp) and the per-warp plate-flux sums (A.nup) of the
-// new level, which a coupled coarse solver takes back every step.
+// upscale partials of the new level (A.tcp), from which k_coupled_reduce forms
+// the coarse scalar a coupled coarse solver takes back every step.
 template <int M, int TY, int KIND, bool LF, bool TC = false>
 __global__ void __launch_bounds__(FL<M, TY, (KIND != 0)>::THREADS, FL<M, TY, (KIND != 0)>::CTAS)
 k_fused(const __grid_constant__ CUtensorMap tmn, const __grid_constant__ CUtensorMap tmm,
@@ -617,21 +615,6 @@ k_fused(const __grid_constant__ CUtensorMap tmn, const __grid_constant__ CUtenso
                                 tcs[q] = 0.f;
                             }
                         }
-                        if (k == 0 || k == g.Nz - 1) {
-                            // the plate Nusselt numbers (Section 4.1): FP64 sums of the
-                            // conductive plate fluxes, one per warp
-                            const bool bot = (k == 0);
-                            const double v[4] = {res[0].x, res[0].y, res[1].x, res[1].y};
-                            double f = 0.0;
-#pragma unroll
-                            for (int a = 0; a < 4; ++a) f += bot ? (0.5 - v[a]) * A.izb : (v[a] + 0.5) * A.izt;
-#pragma unroll
-                            for (int d = 16; d > 0; d >>= 1) f += __shfl_down_sync(0xffffffffu, f, d);
-                            if (lane == 0) {
-                                const int tile = blockIdx.y + gridDim.y * blockIdx.z;
-                                A.nup[((size_t)(bot ? 0 : 1) * gridDim.y * gridDim.z + tile) * NCW + warp] = f;
-                            }
-                        }
                     }
                 }
             }
@@ -828,9 +811,6 @@ cudaError_t launch_fl(const Grid<float>& g, const FusedInputs& in, const float* 
         }
         A.hstride = in.hstride;
         A.tcp = in.tcp;
-        A.nup = in.nup;
-        A.izb = in.izb;
-        A.izt = in.izt;
     }
     k_fused<M, TY, KIND, LF, TC><<<dim3(chunks, g.Nx / kTX, g.Ny / TY), L::THREADS, L::bytes, st>>>(mn, mm, mlc, mu,
                                                                                                    mv, mw, A);
@@ -885,57 +865,104 @@ __global__ void k_pad_coarse64(const double* __restrict__ U, const double* __res
     }
 }
 
-// Tc[K][J][I] from the step's upscale partials: the sum over the coarse row's
-// my dense rows, times 1 / (mx my sum of the slab's dz) (FP64).
-__global__ void k_tc_reduce(const float* __restrict__ tcp, const double* __restrict__ inv, double* __restrict__ Tc,
-                            int nx, int ny, int nz, int my)
+// After a coupled fused step, in one launch: the upscaled coarse scalar
+// (Section 3.3) from the step's partials, Tc = inv[K] * (sum over the coarse
+// cell's M dense rows of the partials), and the plate Nusselt numbers of the
+// new level (Section 4.1).  For these each of the first kCRNu blocks adds the
+// conductive fluxes of a fixed set of plate cells in FP64 and stores its two
+// sums; the last of them to finish (an atomic count) adds them in a fixed
+// order -- so the result never changes from run to run -- and resets the
+// count.
+constexpr int kCRThreads = 256, kCRNu = 304;
+__device__ __forceinline__ void cr_block_sum(double& a, double& b, double (*s)[kCRThreads / 32])
 {
-    const size_t n = (size_t)nz * ny * nx;
-    for (size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (size_t)gridDim.x * blockDim.x) {
-        const int I = (int)(t % nx);
-        const size_t KJ = t / nx;
-        const int J = (int)(KJ % ny), K = (int)(KJ / ny);
-        const float* p = tcp + ((size_t)K * ny * my + (size_t)J * my) * nx + I;
-        float s = 0.f;
-        for (int b = 0; b < my; ++b) s += p[(size_t)b * nx];
-        Tc[t] = (double)s * inv[K];
+    for (int d = 16; d > 0; d >>= 1) {
+        a += __shfl_down_sync(0xffffffffu, a, d);
+        b += __shfl_down_sync(0xffffffffu, b, d);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        s[0][threadIdx.x >> 5] = a;
+        s[1][threadIdx.x >> 5] = b;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        a = 0.0;
+        b = 0.0;
+        for (int w = 0; w < kCRThreads / 32; ++w) {
+            a += s[0][w];
+            b += s[1][w];
+        }
+    }
+}
+__device__ __forceinline__ void cr_plate_nu(const float* __restrict__ T, size_t plane, size_t top, double izb,
+                                            double izt, double inv_plane, double* __restrict__ work,
+                                            double* __restrict__ nu2, unsigned nb)
+{
+    double a = 0.0, b = 0.0;
+    for (size_t m = (size_t)blockIdx.x * blockDim.x + threadIdx.x; m < plane; m += (size_t)nb * blockDim.x) {
+        a += 0.5 - (double)T[m];
+        b += (double)T[top + m] + 0.5;
+    }
+    __shared__ double s[2][kCRThreads / 32];
+    __shared__ bool last;
+    unsigned* count = reinterpret_cast<unsigned*>(work);
+    double* part = work + 1;
+    cr_block_sum(a, b, s);
+    if (threadIdx.x == 0) {
+        part[2 * blockIdx.x] = a;
+        part[2 * blockIdx.x + 1] = b;
+        __threadfence();                     // this block's sums before its count
+        last = atomicAdd(count, 1u) == nb - 1;
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    a = 0.0;
+    b = 0.0;
+    for (unsigned q = threadIdx.x; q < nb; q += blockDim.x) {
+        a += __ldcg(part + 2 * q);
+        b += __ldcg(part + 2 * q + 1);
+    }
+    __syncthreads();                         // s is reused
+    cr_block_sum(a, b, s);
+    if (threadIdx.x == 0) {
+        nu2[0] = a * izb * inv_plane;
+        nu2[1] = b * izt * inv_plane;
+        *count = 0u;
+    }
+}
+__global__ void __launch_bounds__(kCRThreads)
+k_coupled_reduce(const float* __restrict__ tcp, const double* __restrict__ inv, double* __restrict__ Tc, int nx, int ny,
+                 int nz, int my, const float* __restrict__ T, size_t plane, size_t top, double izb, double izt,
+                 double inv_plane, double* __restrict__ work, double* __restrict__ nu2)
+{
+    // the plate sums first, so that their last block's total is not behind the Tc work
+    const unsigned nb = min(gridDim.x, (unsigned)kCRNu);
+    if (nu2 && blockIdx.x < nb) cr_plate_nu(T, plane, top, izb, izt, inv_plane, work, nu2, nb);
+    if (Tc) {
+        const size_t n = (size_t)nz * ny * nx, stride = (size_t)gridDim.x * blockDim.x;
+        for (size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += stride) {
+            const int I = (int)(t % nx);
+            const size_t KJ = t / nx;
+            const int J = (int)(KJ % ny), K = (int)(KJ / ny);
+            const float* p = tcp + ((size_t)K * ny * my + (size_t)J * my) * nx + I;
+            float s = 0.f;
+            for (int b = 0; b < my; ++b) s += p[(size_t)b * nx];
+            Tc[t] = (double)s * inv[K];
+        }
     }
 }
 
-// The plate Nusselt numbers from the step's per-warp sums: one block per
-// plate, a fixed order of additions (deterministic), divided by the plate's
-// cell count.
-__global__ void __launch_bounds__(1024) k_nu_finish(const double* __restrict__ nup, size_t per_plate, double inv_n,
-                                                    double* __restrict__ nu2)
+// blocks of k_coupled_reduce: a function of the grid alone, so that the plate
+// sums are formed the same way whatever a call asks for
+unsigned coupled_blocks(const Grid<float>& g)
 {
-    __shared__ double red[1024];
-    const double* p = nup + (size_t)blockIdx.x * per_plate;
-    double s = 0.0;
-    for (size_t m = threadIdx.x; m < per_plate; m += 1024) s += p[m];
-    red[threadIdx.x] = s;
-    __syncthreads();
-    for (int w = 512; w > 0; w >>= 1) {
-        if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
-        __syncthreads();
-    }
-    if (threadIdx.x == 0) nu2[blockIdx.x] = red[0] * inv_n;
+    const size_t n = std::max((size_t)g.nz * g.ny * g.nx, (size_t)g.Nx * g.Ny);
+    const size_t want = (n + kCRThreads - 1) / kCRThreads;
+    return (unsigned)std::min(want, (size_t)152 * 16);
 }
 
 }  // namespace
-
-cudaError_t launch_fused_nu_finish(const Grid<float>& g, const double* nup, double* nu2, cudaStream_t st)
-{
-    const size_t tiles = (size_t)(g.Nx / kTX) * (g.Ny / (g.mx == 4 ? 16 : 8));
-    const size_t warps = (g.mx == 4 ? 16 : 8) / 2;
-    k_nu_finish<<<2, 1024, 0, st>>>(nup, tiles * warps, 1.0 / ((double)g.Nx * g.Ny), nu2);
-    return cudaGetLastError();
-}
-
-size_t fused_nu_partials(const Grid<float>& g)
-{
-    const int ty = g.mx == 4 ? 16 : 8;
-    return 2 * (size_t)(g.Nx / kTX) * (g.Ny / ty) * (ty / 2);
-}
 
 cudaError_t launch_fused_pad64(const double* U, const double* V, const double* W, float* out, float* U32, float* V32,
                                float* W32, int nx, int nyg, int nz, int j0, int ny, cudaStream_t st)
@@ -947,15 +974,18 @@ cudaError_t launch_fused_pad64(const double* U, const double* V, const double* W
     return cudaGetLastError();
 }
 
-cudaError_t launch_fused_tc_reduce(const Grid<float>& g, const float* tcp, const double* inv, double* Tc,
-                                   cudaStream_t st)
+cudaError_t launch_fused_coupled_reduce(const Grid<float>& g, const float* tcp, const double* inv, double* Tc,
+                                       const float* T, double izb, double izt, double* work, double* nu2,
+                                       cudaStream_t st)
 {
-    const size_t n = (size_t)g.nz * g.ny * g.nx;
-    const size_t want = (n + 255) / 256;
-    const unsigned blocks = (unsigned)(want < 152 * 16 ? want : 152 * 16);
-    k_tc_reduce<<<blocks, 256, 0, st>>>(tcp, inv, Tc, g.nx, g.ny, g.nz, g.my);
+    const size_t plane = (size_t)g.Nx * g.Ny;
+    k_coupled_reduce<<<coupled_blocks(g), kCRThreads, 0, st>>>(tcp, inv, Tc, g.nx, g.ny, g.nz, g.my, T, plane,
+                                                                (size_t)(g.Nz - 1) * plane, izb, izt,
+                                                                1.0 / (double)plane, work, nu2);
     return cudaGetLastError();
 }
+
+size_t fused_coupled_work(const Grid<float>& g) { return 1 + 2 * (size_t)coupled_blocks(g); }
 
 size_t fused_pad_floats(int nx, int ny, int nz)
 {

@@ -88,7 +88,7 @@ struct DeviceBuffers {
     float* halo = nullptr;                     // y-slab: [3 levels][below, above][Nz][Nx] halo rows
     float* tcp = nullptr;                      // MR_VEL_FUSED: upscale partials of the step (lazy)
     double* tcinv = nullptr;                   // MR_VEL_FUSED: 1 / (mx my sum of each slab's dz) (lazy)
-    double* nup = nullptr;                     // MR_VEL_FUSED: per-warp plate-flux sums of the step (lazy)
+    double* nup = nullptr;                     // MR_VEL_FUSED: work of the coupled reduction (lazy)
     float xw4[8] = {0};                        // fourth order: twice the x and y face weights (uniform)
     int xlcw = 12;                             // row length of xlc
     double* diag = nullptr;                    // diagnostics: coarse T, Nu(z), dense z centres (lazy)
@@ -218,11 +218,8 @@ struct FusedInputs {
     const float* lc;     // [Nz][32] layer constants (xfused_layer_constants)
     const float* rx12;   // R_x rows of the 4 cells of a 4-cell segment (uniform, periodic x)
     const float* ry12;   // R_y rows of dense rows 0..3 (uniform, periodic y)
-    // NULL, or the step's upscale partials [nz][Ny][nx] (launch_fused_tc_reduce);
-    // then also its per-warp plate-flux sums (launch_fused_nu_finish) and 1/zb, 1/zt
+    // NULL, or the step's upscale partials [nz][Ny][nx] (launch_fused_coupled_reduce)
     float* tcp;
-    double* nup;
-    double izb, izt;
 };
 // every refinement stage in the step kernel
 cudaError_t launch_step_fused_f32(const Grid<float>& g, const FusedInputs& in, const float* Tm1, const float* T,
@@ -230,12 +227,15 @@ cudaError_t launch_step_fused_f32(const Grid<float>& g, const FusedInputs& in, c
 // kind 1: max |divergence| of the dense velocity, kind 2: max CFL rate (into partials[0])
 cudaError_t launch_fused_max_f32(const Grid<float>& g, int kind, const FusedInputs& in, double* partials, int blocks,
                                  cudaStream_t st);
-// Tc (nz x ny x nx, FP64) from the fused step's upscale partials; inv[K] = 1 / (mx my sum of slab K's dz)
-cudaError_t launch_fused_tc_reduce(const Grid<float>& g, const float* tcp, const double* inv, double* Tc,
-                                   cudaStream_t st);
-// the plate Nusselt numbers (nu2[0] bottom, nu2[1] top) from the step's per-warp sums
-cudaError_t launch_fused_nu_finish(const Grid<float>& g, const double* nup, double* nu2, cudaStream_t st);
-size_t fused_nu_partials(const Grid<float>& g);   // doubles of those sums
+// After a coupled fused step, one launch: Tc (nz x ny x nx, FP64; NULL: none) from the
+// step's upscale partials, inv[K] = 1 / (mx my sum of slab K's dz), and the plate
+// Nusselt numbers of the new level T (nu2[0] bottom, nu2[1] top; NULL: none), izb and
+// izt the inverse plate-to-centre distances.  work: fused_coupled_work(g) doubles, the
+// first one zero before the first launch (each launch leaves it zero).
+cudaError_t launch_fused_coupled_reduce(const Grid<float>& g, const float* tcp, const double* inv, double* Tc,
+                                       const float* T, double izb, double izt, double* work, double* nu2,
+                                       cudaStream_t st);
+size_t fused_coupled_work(const Grid<float>& g);
 // floats of the padded coarse faces, and the kernel that forms them from the FP32 coarse faces
 size_t fused_pad_floats(int nx, int ny, int nz);
 // (the coarse rows j0-1 .. j0+ny+1 of a domain of nyg rows, periodic)
