@@ -395,7 +395,7 @@ void mr_destroy(mr_handle h)
         for (void* p : cptrs)
             if (p) dev_free(p);
     }
-    void* xptrs[] = {b.xwy, b.xuo, b.xvr, b.xlc, b.diag, b.cpad, b.fsc, n.cpad, b.halo, b.tcp, b.tcinv, b.nup};
+    void* xptrs[] = {b.xwy, b.xuo, b.xvr, b.xlc, b.diag, b.cpad, b.fsc, n.cpad, b.halo, b.tcinv, b.nup};
     for (void* p : xptrs)
         if (p) dev_free(p);
     for (int q = 0; q < 2; ++q) {
@@ -712,7 +712,7 @@ static int derive_velocity(mr_handle h, bool convert, cudaStream_t st)
 // One time step of the scalar.  alpha = 0: the current velocity; otherwise the
 // velocity (1 - alpha) U^{n-1} + alpha U^n between the current level and the
 // next one (temporal refinement, Section 3.4).
-static int one_step(mr_handle h, double alpha, cudaStream_t st, float* tcp = nullptr)
+static int one_step(mr_handle h, double alpha, cudaStream_t st, double* Tc = nullptr)
 {
     DeviceBuffers& b = h->buf;
     const DeviceBuffers::Level& nx = b.next;
@@ -736,7 +736,7 @@ static int one_step(mr_handle h, double alpha, cudaStream_t st, float* tcp = nul
                                    (const float*)Tm1,
                                    (const float*)b.T[h->ic], (float*)b.T[in], c, st);
     } else if (h->cfg.velocity_mode == MR_VEL_FUSED) {
-        FusedInputs fin{b.cpad, {}, {}, 0, b.fsc, b.xlc, b.xrx, b.xry, tcp};
+        FusedInputs fin{b.cpad, {}, {}, 0, b.fsc, b.xlc, b.xrx, b.xry, Tc, b.tcinv};
         // the rows beyond the y edges of T^s and T^{s-1}
         const int lm = h->step == 0 ? h->ic : h->ip;
         if (h->slab) {
@@ -1043,12 +1043,11 @@ int mr_scalar_step_coupled(mr_handle h, double* nu2, double* Tc, mr_stream strea
     const bool fused = h->cfg.velocity_mode == MR_VEL_FUSED;
     int rc;
     if (fused && (dtc || dnu) && !b.nup) {
-        // the fused step leaves the upscale partials; one reduction forms Tc
-        // from them and the plate Nusselt numbers from the new level
+        // the fused step writes Tc itself (per coarse slab, 1 / (mx my sum of its
+        // dz) in FP64); one launch forms the plate Nusselt numbers of the new level
         const mr_config& c = h->cfg;
-        cudaError_t e = dev_malloc(&b.tcp, (size_t)c.nz * h->Nys * c.nx * sizeof(float));
-        if (e == cudaSuccess) e = dev_malloc(&b.tcinv, (size_t)c.nz * sizeof(double));
-        if (e == cudaSuccess) e = dev_malloc(&b.nup, fused_coupled_work(h->g32) * sizeof(double));
+        cudaError_t e = dev_malloc(&b.tcinv, (size_t)c.nz * sizeof(double));
+        if (e == cudaSuccess) e = dev_malloc(&b.nup, fused_plate_nu_work() * sizeof(double));
         std::vector<double> inv(c.nz);
         for (int K = 0; K < c.nz; ++K) {
             double z = 0.0;
@@ -1056,33 +1055,31 @@ int mr_scalar_step_coupled(mr_handle h, double* nu2, double* Tc, mr_stream strea
             inv[K] = 1.0 / (z * c.mx * c.my);
         }
         if (e == cudaSuccess) e = cudaMemcpy(b.tcinv, inv.data(), inv.size() * sizeof(double), cudaMemcpyHostToDevice);
-        if (e == cudaSuccess) e = cudaMemset(b.nup, 0, sizeof(double));      // the reduction's block count
+        if (e == cudaSuccess) e = cudaMemset(b.nup, 0, sizeof(double));      // the launch's block count
         if (e != cudaSuccess) {
-            dev_free(b.tcp);
             dev_free(b.tcinv);
             dev_free(b.nup);
-            b.tcp = nullptr;
             b.tcinv = nullptr;
             b.nup = nullptr;
-            return cuda_check(e, "mr_scalar_step_coupled: upscale partials");
+            return cuda_check(e, "mr_scalar_step_coupled: coupled outputs");
         }
     }
     if (fused && dtc) {
-        // the step kernel forms the upscale partials of the new level itself
+        // the step kernel writes the upscaled coarse scalar of the new level itself
         if (h->slab && !(h->halo_set[h->ic] && (h->step == 0 || h->halo_set[h->ip])))
             return set_error(MR_ERR_STATE, "mr_scalar_step_coupled: set the y-slab's halo rows first");
         if (!h->have_velocity || !h->have_scalar)
             return set_error(MR_ERR_STATE, "mr_scalar_step_coupled: call mr_refine_velocity and mr_set_scalar first");
-        rc = one_step(h, 0.0, st, b.tcp);
+        rc = one_step(h, 0.0, st, dtc);
     } else {
         rc = mr_scalar_step(h, 1, stream);
     }
     if (rc) return rc;
     cudaError_t e = cudaSuccess;
-    if (fused && (dtc || dnu)) {
-        e = launch_fused_coupled_reduce(h->g32, b.tcp, b.tcinv, dtc, (const float*)h->buf.T[h->ic],
-                                        1.0 / (h->zc[0] - h->zf[0]), 1.0 / (h->zf[h->Nz] - h->zc[h->Nz - 1]), b.nup,
-                                        dnu, st);
+    if (fused) {
+        if (dnu)
+            e = launch_fused_plate_nu(h->g32, (const float*)h->buf.T[h->ic], 1.0 / (h->zc[0] - h->zf[0]),
+                                      1.0 / (h->zf[h->Nz] - h->zc[h->Nz - 1]), b.nup, dnu, st);
     } else {
         if (dnu) {
             const double zz[2] = {h->zc[0] - h->zf[0], h->zf[h->Nz] - h->zc[h->Nz - 1]};
@@ -1156,7 +1153,7 @@ static int max_divergence(mr_handle h, double* out, cudaStream_t st)
     if (h->cfg.velocity_mode == MR_VEL_XFUSED)
         e = launch_xfused_max_f32(h->g32, 1, b.xwy, b.xuo, b.xvr, b.nxg, b.xlc, b.xlcw, b.xrx, b.red, h->red_blocks, st);
     else if (h->cfg.velocity_mode == MR_VEL_FUSED)
-        e = launch_fused_max_f32(h->g32, 1, FusedInputs{b.cpad, {}, {}, 0, b.fsc, b.xlc, b.xrx, b.xry, nullptr}, b.red,
+        e = launch_fused_max_f32(h->g32, 1, FusedInputs{b.cpad, {}, {}, 0, b.fsc, b.xlc, b.xrx, b.xry, nullptr, nullptr}, b.red,
                                  h->red_blocks, st);
     else if (h->cfg.precision == MR_F64)
         e = launch_maxdiv<double>(h->g64, (const double*)b.Us, (const double*)b.Vs, (const double*)b.Ws, b.red,
@@ -1238,7 +1235,7 @@ int mr_cfl_dt(mr_handle h, double cfl, double* dt_out, mr_stream stream)
         e = launch_xfused_max_f32(h->g32, 2, b.xwy, b.xuo, b.xvr, b.nxg, b.xlc, b.xlcw, b.xrx, b.red, h->red_blocks, st);
     } else if (h->cfg.velocity_mode == MR_VEL_FUSED) {
         // the fused kernel forms the dense faces in registers from the coarse ones
-        e = launch_fused_max_f32(h->g32, 2, FusedInputs{b.cpad, {}, {}, 0, b.fsc, b.xlc, b.xrx, b.xry, nullptr}, b.red,
+        e = launch_fused_max_f32(h->g32, 2, FusedInputs{b.cpad, {}, {}, 0, b.fsc, b.xlc, b.xrx, b.xry, nullptr, nullptr}, b.red,
                                  h->red_blocks, st);
     } else if (h->cfg.velocity_mode != MR_VEL_STORED) {
         // dense faces are not kept: refine into temporary buffers once

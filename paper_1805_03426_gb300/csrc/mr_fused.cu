@@ -99,7 +99,8 @@ struct FL {
                               cw_bytes = 2 * NUR * BXC * 4;
     static constexpr int oCoarse = oSlab + 2 * SLAB;
     static constexpr int oZ = oCoarse + 2 * CBOX;           // stage Z: [M-1][NUR][BXC]
-    static constexpr int oRed = oZ + up32((M - 1) * NUR * BXC);   // 64 floats: reduction, failure flag
+    static constexpr int oTcb = oZ + up32((M - 1) * NUR * BXC);   // upscale sums: [2][TY][CX]
+    static constexpr int oRed = oTcb + (DIV ? 0 : up32(2 * TY * CX));   // 64 floats: reduction, failure flag
     static constexpr int oBar = (oRed + 64) / 2;            // in uint64
     // full[NB], empty[NB], cfull[2], cempty[2], built[2], freed[2]
     static constexpr size_t bytes = (size_t)(oBar + 2 * NB + 8) * 8;
@@ -124,8 +125,8 @@ struct FLArgs {
     const float* hs[2];  // rows south of row 0 of T^s, T^{s-1} (periodic images or y-slab halo)
     const float* hn[2];  // rows north of row Ny-1
     size_t hstride;      // layer stride of those rows
-    float* tcp;          // NULL, or [nz][Ny][nx]: per coarse slab, dense row and coarse column,
-                         // sum over the slab's layers of dz times the column's new values
+    double* Tc;          // NULL, or the upscaled coarse scalar of the new level [nz][ny][nx]
+    const double* tcinv; // with Tc: per coarse slab, 1 / (mx my sum of its dz)
 };
 
 // R_x split of three coarse values by one row of R (rows sum to one).
@@ -292,9 +293,11 @@ __device__ void build_slab(const FLArgs& A, const float* __restrict__ cb, float*
 }
 
 // KIND 0: the step; 1: max |divergence| of the dense velocity; 2: max CFL rate.
-// LF: a plain leapfrog step (a = 1, b = 0).  TC: the step also leaves the
-// upscale partials of the new level (A.tcp), from which k_coupled_reduce forms
-// the coarse scalar a coupled coarse solver takes back every step.
+// LF: a plain leapfrog step (a = 1, b = 0).  TC: the step also writes the
+// upscaled coarse scalar of the new level (A.Tc), which a coupled coarse solver
+// takes back every step: the consumers leave each row's dz-weighted sums of a
+// slab in shared memory, and once the slab is freed the builder warps add the
+// M rows of each coarse cell and scale them (Section 3.3).
 template <int M, int TY, int KIND, bool LF, bool TC = false>
 __global__ void __launch_bounds__(FL<M, TY, (KIND != 0)>::THREADS, FL<M, TY, (KIND != 0)>::CTAS)
 k_fused(const __grid_constant__ CUtensorMap tmn, const __grid_constant__ CUtensorMap tmm,
@@ -399,16 +402,41 @@ k_fused(const __grid_constant__ CUtensorMap tmn, const __grid_constant__ CUtenso
             mbar_arrive(&cempty[0]);
             mbar_arrive(&built[0]);
         }
+        // TC: the coarse cells of a freed slab K (sums over its M dense rows, in
+        // the rows' order, in FP32; the scaling in FP64)
+        auto upscale = [&](int K) {
+            constexpr int CX = L::CX, CY = L::CY;
+            const float* tb = sm + L::oTcb + ((K - K0) & 1) * TY * CX;
+            const double inv = A.tcinv[K];
+            for (int t = bt; t < CY * CX; t += L::NBT) {
+                const int Jc = t / CX, I = t - Jc * CX;
+                float v = 0.f;
+#pragma unroll
+                for (int b = 0; b < M; ++b) v += tb[(Jc * M + b) * CX + I];
+                A.Tc[((size_t)K * g.ny + J0 + Jc) * g.nx + I0 + I] = (double)v * inv;
+            }
+        };
         for (int K = K0 + 1; K < K1 && !fail; ++K) {
             const int bb = (K - K0) & 1, use = (K - K0) >> 1;
             bool f = !mbar_wait_idle(&cfull[bb], use & 1, A.wait_ns, kIdleNs);
             if (!f && use > 0) f = !mbar_wait_idle(&freed[bb], (use - 1) & 1, A.wait_ns, kIdleNs);
             fail = named_or<L::NBT>(2, f);
             if (fail) break;
+            if constexpr (TC) {
+                if (use > 0) upscale(K - 2);
+            }
             build_slab<M, TY, L::NBT>(A, sm + L::oCoarse + bb * L::CBOX, sm + L::oSlab + bb * L::SLAB, sm + L::oZ,
                                       A.sc + (size_t)K * kSCW, bt, 2);
             mbar_arrive(&cempty[bb]);
             mbar_arrive(&built[bb]);
+        }
+        if constexpr (TC) {
+            // the chunk's last two slabs, once the consumers have freed them
+            for (int K = max(K0, K1 - 2); K < K1 && !fail; ++K) {
+                const int bb = (K - K0) & 1, use = (K - K0) >> 1;
+                fail = named_or<L::NBT>(2, !mbar_wait_idle(&freed[bb], use & 1, A.wait_ns, kIdleNs));
+                if (!fail) upscale(K);
+            }
         }
         if (fail && bt == 0) *s_fail = 1;
     } else {
@@ -608,7 +636,7 @@ k_fused(const __grid_constant__ CUtensorMap tmn, const __grid_constant__ CUtenso
                             tcs[NC - 1] += dzk * (res[1].x + res[1].y);
                         }
                         if (i == M - 1) {
-                            float* tp = A.tcp + ((size_t)(k / M) * g.Ny + j0 + jl) * g.nx + I0 + cb0;
+                            float* tp = sm + L::oTcb + (bb * TY + jl) * L::CX + cb0;
 #pragma unroll
                             for (int q = 0; q < NC; ++q) {
                                 tp[q] = tcs[q];
@@ -810,7 +838,8 @@ cudaError_t launch_fl(const Grid<float>& g, const FusedInputs& in, const float* 
             A.hn[q] = in.hn[q];
         }
         A.hstride = in.hstride;
-        A.tcp = in.tcp;
+        A.Tc = in.Tc;
+        A.tcinv = in.tcinv;
     }
     k_fused<M, TY, KIND, LF, TC><<<dim3(chunks, g.Nx / kTX, g.Ny / TY), L::THREADS, L::bytes, st>>>(mn, mm, mlc, mu,
                                                                                                    mv, mw, A);
@@ -865,14 +894,11 @@ __global__ void k_pad_coarse64(const double* __restrict__ U, const double* __res
     }
 }
 
-// After a coupled fused step, in one launch: the upscaled coarse scalar
-// (Section 3.3) from the step's partials, Tc = inv[K] * (sum over the coarse
-// cell's M dense rows of the partials), and the plate Nusselt numbers of the
-// new level (Section 4.1).  For these each of the first kCRNu blocks adds the
-// conductive fluxes of a fixed set of plate cells in FP64 and stores its two
-// sums; the last of them to finish (an atomic count) adds them in a fixed
-// order -- so the result never changes from run to run -- and resets the
-// count.
+// The plate Nusselt numbers of a new level (Section 4.1) in one launch: each
+// of kCRNu blocks adds the conductive fluxes of a fixed set of plate cells in
+// FP64 and stores its two sums; the last to finish (an atomic count) adds them
+// in a fixed order -- so the result never changes from run to run -- and
+// resets the count.
 constexpr int kCRThreads = 256, kCRNu = 304;
 __device__ __forceinline__ void cr_block_sum(double& a, double& b, double (*s)[kCRThreads / 32])
 {
@@ -932,34 +958,10 @@ __device__ __forceinline__ void cr_plate_nu(const float* __restrict__ T, size_t 
     }
 }
 __global__ void __launch_bounds__(kCRThreads)
-k_coupled_reduce(const float* __restrict__ tcp, const double* __restrict__ inv, double* __restrict__ Tc, int nx, int ny,
-                 int nz, int my, const float* __restrict__ T, size_t plane, size_t top, double izb, double izt,
-                 double inv_plane, double* __restrict__ work, double* __restrict__ nu2)
+k_coupled_nu(const float* __restrict__ T, size_t plane, size_t top, double izb, double izt, double inv_plane,
+             double* __restrict__ work, double* __restrict__ nu2)
 {
-    // the plate sums first, so that their last block's total is not behind the Tc work
-    const unsigned nb = min(gridDim.x, (unsigned)kCRNu);
-    if (nu2 && blockIdx.x < nb) cr_plate_nu(T, plane, top, izb, izt, inv_plane, work, nu2, nb);
-    if (Tc) {
-        const size_t n = (size_t)nz * ny * nx, stride = (size_t)gridDim.x * blockDim.x;
-        for (size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += stride) {
-            const int I = (int)(t % nx);
-            const size_t KJ = t / nx;
-            const int J = (int)(KJ % ny), K = (int)(KJ / ny);
-            const float* p = tcp + ((size_t)K * ny * my + (size_t)J * my) * nx + I;
-            float s = 0.f;
-            for (int b = 0; b < my; ++b) s += p[(size_t)b * nx];
-            Tc[t] = (double)s * inv[K];
-        }
-    }
-}
-
-// blocks of k_coupled_reduce: a function of the grid alone, so that the plate
-// sums are formed the same way whatever a call asks for
-unsigned coupled_blocks(const Grid<float>& g)
-{
-    const size_t n = std::max((size_t)g.nz * g.ny * g.nx, (size_t)g.Nx * g.Ny);
-    const size_t want = (n + kCRThreads - 1) / kCRThreads;
-    return (unsigned)std::min(want, (size_t)152 * 16);
+    cr_plate_nu(T, plane, top, izb, izt, inv_plane, work, nu2, gridDim.x);
 }
 
 }  // namespace
@@ -974,18 +976,17 @@ cudaError_t launch_fused_pad64(const double* U, const double* V, const double* W
     return cudaGetLastError();
 }
 
-cudaError_t launch_fused_coupled_reduce(const Grid<float>& g, const float* tcp, const double* inv, double* Tc,
-                                       const float* T, double izb, double izt, double* work, double* nu2,
-                                       cudaStream_t st)
+cudaError_t launch_fused_plate_nu(const Grid<float>& g, const float* T, double izb, double izt, double* work,
+                                  double* nu2, cudaStream_t st)
 {
     const size_t plane = (size_t)g.Nx * g.Ny;
-    k_coupled_reduce<<<coupled_blocks(g), kCRThreads, 0, st>>>(tcp, inv, Tc, g.nx, g.ny, g.nz, g.my, T, plane,
-                                                                (size_t)(g.Nz - 1) * plane, izb, izt,
-                                                                1.0 / (double)plane, work, nu2);
+    const unsigned blocks = (unsigned)std::min((plane + kCRThreads - 1) / kCRThreads, (size_t)kCRNu);
+    k_coupled_nu<<<blocks, kCRThreads, 0, st>>>(T, plane, (size_t)(g.Nz - 1) * plane, izb, izt, 1.0 / (double)plane,
+                                               work, nu2);
     return cudaGetLastError();
 }
 
-size_t fused_coupled_work(const Grid<float>& g) { return 1 + 2 * (size_t)coupled_blocks(g); }
+size_t fused_plate_nu_work() { return 1 + 2 * (size_t)kCRNu; }
 
 size_t fused_pad_floats(int nx, int ny, int nz)
 {
@@ -1032,7 +1033,7 @@ cudaError_t launch_step_fused_f32(const Grid<float>& g, const FusedInputs& in, c
     int* err = fused_error_flag();
     if (!err) return cudaErrorMemoryAllocation;
     const bool lf = (c.a == 1.0 && c.b == 0.0);
-    if (in.tcp)
+    if (in.Tc)
         return lf ? launch_fl_any<0, true, true>(g, in, Tm1, T, Tp1, c, err, nullptr, st)
                   : launch_fl_any<0, false, true>(g, in, Tm1, T, Tp1, c, err, nullptr, st);
     return lf ? launch_fl_any<0, true, false>(g, in, Tm1, T, Tp1, c, err, nullptr, st)

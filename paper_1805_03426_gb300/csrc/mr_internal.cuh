@@ -86,9 +86,8 @@ struct DeviceBuffers {
     float* cpad = nullptr;                     // MR_VEL_FUSED: padded FP32 coarse faces
     float* fsc = nullptr;                      // MR_VEL_FUSED: [nz][32] slab constants
     float* halo = nullptr;                     // y-slab: [3 levels][below, above][Nz][Nx] halo rows
-    float* tcp = nullptr;                      // MR_VEL_FUSED: upscale partials of the step (lazy)
     double* tcinv = nullptr;                   // MR_VEL_FUSED: 1 / (mx my sum of each slab's dz) (lazy)
-    double* nup = nullptr;                     // MR_VEL_FUSED: work of the coupled reduction (lazy)
+    double* nup = nullptr;                     // MR_VEL_FUSED: work of the plate-Nu launch (lazy)
     float xw4[8] = {0};                        // fourth order: twice the x and y face weights (uniform)
     int xlcw = 12;                             // row length of xlc
     double* diag = nullptr;                    // diagnostics: coarse T, Nu(z), dense z centres (lazy)
@@ -218,8 +217,11 @@ struct FusedInputs {
     const float* lc;     // [Nz][32] layer constants (xfused_layer_constants)
     const float* rx12;   // R_x rows of the 4 cells of a 4-cell segment (uniform, periodic x)
     const float* ry12;   // R_y rows of dense rows 0..3 (uniform, periodic y)
-    // NULL, or the step's upscale partials [nz][Ny][nx] (launch_fused_coupled_reduce)
-    float* tcp;
+    // NULL, or where the step writes the upscaled coarse scalar of the new level
+    // ([nz][ny][nx], FP64, device or mapped host memory); then tcinv[K] = 1 / (mx my
+    // sum of slab K's dz)
+    double* Tc;
+    const double* tcinv;
 };
 // every refinement stage in the step kernel
 cudaError_t launch_step_fused_f32(const Grid<float>& g, const FusedInputs& in, const float* Tm1, const float* T,
@@ -227,15 +229,12 @@ cudaError_t launch_step_fused_f32(const Grid<float>& g, const FusedInputs& in, c
 // kind 1: max |divergence| of the dense velocity, kind 2: max CFL rate (into partials[0])
 cudaError_t launch_fused_max_f32(const Grid<float>& g, int kind, const FusedInputs& in, double* partials, int blocks,
                                  cudaStream_t st);
-// After a coupled fused step, one launch: Tc (nz x ny x nx, FP64; NULL: none) from the
-// step's upscale partials, inv[K] = 1 / (mx my sum of slab K's dz), and the plate
-// Nusselt numbers of the new level T (nu2[0] bottom, nu2[1] top; NULL: none), izb and
-// izt the inverse plate-to-centre distances.  work: fused_coupled_work(g) doubles, the
-// first one zero before the first launch (each launch leaves it zero).
-cudaError_t launch_fused_coupled_reduce(const Grid<float>& g, const float* tcp, const double* inv, double* Tc,
-                                       const float* T, double izb, double izt, double* work, double* nu2,
-                                       cudaStream_t st);
-size_t fused_coupled_work(const Grid<float>& g);
+// The plate Nusselt numbers of the level T (nu2[0] bottom, nu2[1] top) in one launch;
+// izb, izt the inverse plate-to-centre distances; work: fused_plate_nu_work() doubles,
+// the first one zero before the first launch (each launch leaves it zero).
+cudaError_t launch_fused_plate_nu(const Grid<float>& g, const float* T, double izb, double izt, double* work,
+                                  double* nu2, cudaStream_t st);
+size_t fused_plate_nu_work();
 // floats of the padded coarse faces, and the kernel that forms them from the FP32 coarse faces
 size_t fused_pad_floats(int nx, int ny, int nz);
 // (the coarse rows j0-1 .. j0+ny+1 of a domain of nyg rows, periodic)
