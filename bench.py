@@ -67,7 +67,7 @@ NCU_TRAFFIC = {
     # ncu printed the split-x read bytes to three digits
     ("k_xfused", "rb512_stretched_f32"): {"bytes": int(1.150e9) + 384230000, "sources": "a0d17f174842153e.c41e21757bf0efe9",
                                           "files": ("mr_xfused.cu", "mr_ptx.cuh")},
-    ("k_fused", "rb512_stretched_f32"): {"bytes": 879000576 + 379811072, "sources": "1b47ade26da71535.c41e21757bf0efe9",
+    ("k_fused", "rb512_stretched_f32"): {"bytes": 879469824 + 379962624, "sources": "cc58c2c9153c487a.c41e21757bf0efe9",
                                          "files": ("mr_fused.cu", "mr_ptx.cuh")},
 }
 
@@ -293,7 +293,7 @@ def run_mr(args):
     import paper_1805_03426_gb300.mr as mr
 
     world, rank, local = _dist()
-    if world > 1:
+    if world > 1 or args.slabs:
         return run_slabs(args)
     torch.cuda.set_device(local)
     w = WORKLOADS[args.workload]
@@ -704,6 +704,8 @@ def main():
     ap.add_argument("--no-temporal", action="store_true")
     ap.add_argument("--no-face4", action="store_true")
     ap.add_argument("--no-fused", action="store_true")
+    ap.add_argument("--slabs", action="store_true",
+                    help="the y-slab path (under torchrun) even on one GPU: one slab, its own halo rows")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

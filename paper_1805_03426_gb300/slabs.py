@@ -168,14 +168,17 @@ class HandleEngine:
         self.mr.mr_scalar_step(self.h, 1, stream=self.stream)
 
     def boundary_rows(self, first, last):
+        import torch
         self.mr.mr_get_boundary_rows(self.h, first, last, stream=self.stream)
-        if self.stream is not None:
-            self.stream.synchronize()      # the rows are read by the exchange's own stream
+        if self.stream is not None and first.is_cuda:
+            # the exchange runs on the current stream: it waits for the copies
+            # on the device, the host does not
+            torch.cuda.current_stream().wait_stream(self.stream)
 
     def set_halo(self, below, above):
         import torch
-        if below.is_cuda:
-            torch.cuda.current_stream().synchronize()   # the exchange's receives have landed
+        if self.stream is not None and below.is_cuda:
+            self.stream.wait_stream(torch.cuda.current_stream())   # the receives have landed
         self.mr.mr_set_halo_rows(self.h, below, above, stream=self.stream)
 
 
