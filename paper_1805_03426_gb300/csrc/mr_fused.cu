@@ -52,7 +52,6 @@ namespace {
 using namespace ptx;
 
 constexpr int kTX = 64;                 // tile width (cells)
-constexpr int kBX = kTX + 8;            // scalar plane box width (floats)
 constexpr int kLCW = 32;                // layer-constant row (floats)
 constexpr int kSCW = 32;                // slab-constant row (floats)
 #ifndef MR_FUSED_IDLE_NS
@@ -67,24 +66,47 @@ constexpr unsigned kIdleNs = MR_FUSED_IDLE_NS;   // sleep between the polls of t
 
 __host__ __device__ constexpr int up32(int n) { return (n + 31) / 32 * 32; }
 
+// Registers per thread of the step on 64 x 16 tiles (256 threads, two CTAs per
+// SM): at launch, and after the split between the consumer warpgroup and the
+// producer / builder warpgroup (128 kRegCons + 128 kRegOther = 256 kRegLaunch).
+#ifndef MR_FUSED_REG_CONS
+#define MR_FUSED_REG_CONS 168     // compile-time override for tuning sweeps
+#endif
+constexpr int kRegLaunch = 128, kRegCons = MR_FUSED_REG_CONS, kRegOther = 2 * kRegLaunch - kRegCons;
+static_assert(kRegCons + kRegOther == 2 * kRegLaunch, "register split exceeds the launch");
+
 // Shared-memory layout (offsets in floats; every TMA destination on a
 // 128-byte boundary).  DIV: the reductions, which stream no scalar planes.
 template <int M, int TY, bool DIV>
 struct FL {
-    static constexpr int CONS = 16 * TY;                    // consumer threads: 4-cell segments
+    // consumer threads: 4-cell segments of one dense row (the reductions) or
+    // of two rows (the step)
+    static constexpr int CONS = DIV ? 16 * TY : 8 * TY;
     static constexpr int NCW = CONS / 32;                   // consumer warps
     static constexpr int NBT = 32 * MR_FUSED_BUILDER_WARPS;  // builder threads
     static constexpr int THREADS = CONS + 32 + NBT;         // + producer warp + builder warps
-    static constexpr int CTAS = TY == 16 ? 2 : 3;           // resident CTAs per SM the layout is sized for
-    static constexpr int NB = DIV ? 8 : (TY == 16 ? 6 : (M == 4 ? 7 : 6));   // ring slots
+    // resident CTAs per SM the layout is sized for (the step at M = 2, two rows
+    // per consumer thread, runs two so that its registers need not spill)
+    static constexpr int CTAS = (TY == 16 || (!DIV && M == 2)) ? 2 : 3;
+    // registers move from warpgroup 1 (producer, builders) to warpgroup 0 (consumers)
+    static constexpr bool RS = !DIV && CONS == 128 && NBT == 96;
+#ifndef MR_FUSED_NB16
+#define MR_FUSED_NB16 6           // ring slots of the step on 64 x 16 tiles (tuning override)
+#endif
+    static constexpr int NB = DIV ? 8 : (TY == 16 ? MR_FUSED_NB16 : (M == 4 ? 7 : 6));   // ring slots
     static constexpr int CX = kTX / M, CY = TY / M;         // coarse cells of the tile
     static constexpr int BXC = CX + 8;                      // coarse box columns I0-4 .. I0+CX+3
     static constexpr int SXC = CX + 4;                      // slab buffer columns I0-1 .. I0+CX+2
-    static constexpr int kBY = TY + 2;                      // rows of a scalar plane box
-    static constexpr uint32_t plane_bytes = (uint32_t)(kBX * kBY) * 4;
-    static constexpr int PS = DIV ? 0 : up32(kBX * kBY);
-    // ring slot: T^s plane, T^{s-1} plane, the layer constants
-    static constexpr int oTn = 0, oTm = PS, oLC = 2 * PS;
+    // one scalar level (T^s or T^{s-1}) of one plane in a ring slot, each part a
+    // TMA box on a 128-byte boundary: the tile's TY rows (64 wide), the row
+    // south and the row north of them, the 4 columns west and east of them (the
+    // periodic images at the domain's x edges, the periodic images or a
+    // y-slab's halo rows at its y edges)
+    static constexpr int fYS = kTX * TY, fYN = fYS + kTX, fXW = fYN + kTX, fXE = fXW + 4 * TY;
+    static constexpr int FW = DIV ? 0 : fXE + 4 * TY;
+    static_assert(FW % 32 == 0 && fXE % 32 == 0, "TMA boxes of a slot start on 128-byte boundaries");
+    // ring slot: T^s, T^{s-1}, the layer constants
+    static constexpr int oTn = 0, oTm = FW, oLC = 2 * FW;
     static constexpr int slot = up32(oLC + kLCW);
     // slab buffer: WY [M+1][TY][SXC], UO [M][TY][SXC], VR [M][TY+1][SXC]
     static constexpr int bWY = 0, bUO = (M + 1) * TY * SXC, bVR = bUO + M * TY * SXC;
@@ -106,10 +128,16 @@ struct FL {
     static constexpr size_t bytes = (size_t)(oBar + 2 * NB + 8) * 8;
 };
 
+// Tensor maps of the step: per scalar level (n: T^s, m: T^{s-1}) the tile's
+// rows (64 x TY boxes), single rows (64 x 1), four columns (4 x TY), and single
+// rows of the arrays holding the rows south of row 0 (s) and north of row Ny-1
+// (h); then the layer constants and the padded coarse faces.
+struct FLMaps {
+    CUtensorMap tn, tm, rn, rm, xn, xm, sn, smp, hn, hm, lc, cu, cv, cw;
+};
+
 struct FLArgs {
     Grid<float> g;
-    const float* Tn;     // T^s (global, for the periodic halo of edge threads)
-    const float* Tm;     // T^{s-1}
     float* Tp1;          // T^{s+1}
     const float* sc;     // [nz][32] slab constants (fused_slab_constants)
     float a, b, gdt;
@@ -122,9 +150,6 @@ struct FLArgs {
     float hx, hy;        // 1 / (2 dx), 1 / (2 dy)
     unsigned long long wait_ns;   // time limit of every bounded wait
     int stop_ring;       // test hook: the producer of CTA (0,0,0) issues nothing from this ring on (-1: none)
-    const float* hs[2];  // rows south of row 0 of T^s, T^{s-1} (periodic images or y-slab halo)
-    const float* hn[2];  // rows north of row Ny-1
-    size_t hstride;      // layer stride of those rows
     double* Tc;          // NULL, or the upscaled coarse scalar of the new level [nz][ny][nx]
     const double* tcinv; // with Tc: per coarse slab, 1 / (mx my sum of its dz)
 };
@@ -300,9 +325,7 @@ __device__ void build_slab(const FLArgs& A, const float* __restrict__ cb, float*
 // M rows of each coarse cell and scale them (Section 3.3).
 template <int M, int TY, int KIND, bool LF, bool TC = false>
 __global__ void __launch_bounds__(FL<M, TY, (KIND != 0)>::THREADS, FL<M, TY, (KIND != 0)>::CTAS)
-k_fused(const __grid_constant__ CUtensorMap tmn, const __grid_constant__ CUtensorMap tmm,
-        const __grid_constant__ CUtensorMap tlc, const __grid_constant__ CUtensorMap tcu,
-        const __grid_constant__ CUtensorMap tcv, const __grid_constant__ CUtensorMap tcw, const FLArgs A)
+k_fused(const __grid_constant__ FLMaps T, const FLArgs A)
 {
     constexpr bool DIVONLY = KIND != 0;
     using L = FL<M, TY, DIVONLY>;
@@ -343,150 +366,161 @@ k_fused(const __grid_constant__ CUtensorMap tmn, const __grid_constant__ CUtenso
     __syncthreads();
 
     int rings_issued = 0, slabs_issued = 0;       // producer lane 0: for the final drain
-    if (warp == NCW) {
-        // ------------------------------------------------------------ producer warp
-        if (lane == 0) {
-            const bool stopper = (A.stop_ring >= 0 && blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0);
-            // the coarse faces of slab K into buffer (K - K0) & 1
-            auto issue_coarse = [&](int K) {
-                const int bb = (K - K0) & 1, use = (K - K0) >> 1;
-                if (use > 0 && !mbar_wait_idle(&cempty[bb], (use - 1) & 1, A.wait_ns, kIdleNs)) return false;
-                float* dst = sm + L::oCoarse + bb * L::CBOX;
-                const int wz0 = min(max(K - 1, 0), g.nz - 3);     // first plane of the R_z window
-                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                mbar_expect_tx(&cfull[bb], L::cu_bytes + L::cv_bytes + L::cw_bytes);
-                tma_3d(dst + L::cU, &tcu, I0, J0, wz0, &cfull[bb]);
-                tma_3d(dst + L::cV, &tcv, I0, J0, wz0, &cfull[bb]);
-                tma_3d(dst + L::cW, &tcw, I0, J0, K, &cfull[bb]);
-                ++slabs_issued;
-                return true;
-            };
-            bool ok = true, stopped = stopper && A.stop_ring == 0;
-            if (!stopped) {
-                ok = issue_coarse(K0);
-                if (ok && K0 + 1 < K1) ok = issue_coarse(K0 + 1);
-            }
-            for (int r = 0; ok && !stopped && r < nrings; ++r) {
-                const int s = r % NB;
-                if (stopper && r == A.stop_ring) break;    // every copy issued so far is waited for
-                if (r >= NB && !mbar_wait_idle(&empty[s], ((r / NB) - 1) & 1, A.wait_ns, kIdleNs)) {
-                    ok = false;
-                    break;
+    // the step on 64 x 16 tiles: the consumer warps (warpgroup 0) take
+    // registers from the producer and builder warps (warpgroup 1); the launch
+    // gives every thread kRegLaunch (checked on the host before the launch)
+    if (warp >= NCW) {
+        if constexpr (L::RS) asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(kRegOther));
+        if (warp == NCW) {
+            // ------------------------------------------------------------ producer warp
+            if (lane == 0) {
+                const bool stopper = (A.stop_ring >= 0 && blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0);
+                // the coarse faces of slab K into buffer (K - K0) & 1
+                auto issue_coarse = [&](int K) {
+                    const int bb = (K - K0) & 1, use = (K - K0) >> 1;
+                    if (use > 0 && !mbar_wait_idle(&cempty[bb], (use - 1) & 1, A.wait_ns, kIdleNs)) return false;
+                    float* dst = sm + L::oCoarse + bb * L::CBOX;
+                    const int wz0 = min(max(K - 1, 0), g.nz - 3);     // first plane of the R_z window
+                    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                    mbar_expect_tx(&cfull[bb], L::cu_bytes + L::cv_bytes + L::cw_bytes);
+                    tma_3d(dst + L::cU, &T.cu, I0, J0, wz0, &cfull[bb]);
+                    tma_3d(dst + L::cV, &T.cv, I0, J0, wz0, &cfull[bb]);
+                    tma_3d(dst + L::cW, &T.cw, I0, J0, K, &cfull[bb]);
+                    ++slabs_issued;
+                    return true;
+                };
+                // the rows south / north of the tile: inside the domain from the
+                // level itself, beyond its y edges from the arrays of those rows;
+                // the columns west / east: periodic in x
+                const bool s_edge = (j0 == 0), n_edge = (j0 + TY == g.Ny);
+                const CUtensorMap* ys_n = s_edge ? &T.sn : &T.rn;
+                const CUtensorMap* ys_m = s_edge ? &T.smp : &T.rm;
+                const CUtensorMap* yn_n = n_edge ? &T.hn : &T.rn;
+                const CUtensorMap* yn_m = n_edge ? &T.hm : &T.rm;
+                const int ys_y = s_edge ? 0 : j0 - 1, yn_y = n_edge ? 0 : j0 + TY;
+                const int xw_x = (i0 == 0) ? g.Nx - 4 : i0 - 4, xe_x = (i0 + kTX == g.Nx) ? 0 : i0 + kTX;
+                bool ok = true, stopped = stopper && A.stop_ring == 0;
+                if (!stopped) {
+                    ok = issue_coarse(K0);
+                    if (ok && K0 + 1 < K1) ok = issue_coarse(K0 + 1);
                 }
-                float* slot = sm + s * L::slot;
-                const int p = k0 - 1 + r;
-                const bool lc = (r >= 2);
-                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                mbar_expect_tx(&full[s], (DIVONLY ? 0u : 2 * L::plane_bytes) + (lc ? (uint32_t)kLCW * 4 : 0u));
-                if (!DIVONLY) {
-                    tma_3d(slot + L::oTn, &tmn, i0 - 4, j0 - 1, p, &full[s]);
-                    tma_3d(slot + L::oTm, &tmm, i0 - 4, j0 - 1, p, &full[s]);
+                for (int r = 0; ok && !stopped && r < nrings; ++r) {
+                    const int s = r % NB;
+                    if (stopper && r == A.stop_ring) break;    // every copy issued so far is waited for
+                    if (r >= NB && !mbar_wait_idle(&empty[s], ((r / NB) - 1) & 1, A.wait_ns, kIdleNs)) {
+                        ok = false;
+                        break;
+                    }
+                    float* slot = sm + s * L::slot;
+                    const int p = k0 - 1 + r;
+                    const bool lc = (r >= 2);
+                    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                    mbar_expect_tx(&full[s], (uint32_t)(2 * L::FW + (lc ? kLCW : 0)) * 4u);
+                    if (!DIVONLY) {
+                        // per level: the tile's rows, the rows beyond its y edges, the
+                        // columns beyond its x edges (wrapped at the domain's edges,
+                        // so that every box is in bounds in x and y)
+                        tma_3d(slot + L::oTn, &T.tn, i0, j0, p, &full[s]);
+                        tma_3d(slot + L::oTm, &T.tm, i0, j0, p, &full[s]);
+                        tma_3d(slot + L::oTn + L::fYS, ys_n, i0, ys_y, p, &full[s]);
+                        tma_3d(slot + L::oTm + L::fYS, ys_m, i0, ys_y, p, &full[s]);
+                        tma_3d(slot + L::oTn + L::fYN, yn_n, i0, yn_y, p, &full[s]);
+                        tma_3d(slot + L::oTm + L::fYN, yn_m, i0, yn_y, p, &full[s]);
+                        tma_3d(slot + L::oTn + L::fXW, &T.xn, xw_x, j0, p, &full[s]);
+                        tma_3d(slot + L::oTm + L::fXW, &T.xm, xw_x, j0, p, &full[s]);
+                        tma_3d(slot + L::oTn + L::fXE, &T.xn, xe_x, j0, p, &full[s]);
+                        tma_3d(slot + L::oTm + L::fXE, &T.xm, xe_x, j0, p, &full[s]);
+                    }
+                    if (lc) tma_3d(slot + L::oLC, &T.lc, 0, p - 1, 0, &full[s]);
+                    rings_issued = r + 1;
+                    // the first plane of slab K (K > K0) goes out with the coarse faces of slab K + 1
+                    if (p > k0 && p < k1 && (p - k0) % M == 0 && p / M + 1 < K1) ok = issue_coarse(p / M + 1);
                 }
-                if (lc) tma_3d(slot + L::oLC, &tlc, 0, p - 1, 0, &full[s]);
-                rings_issued = r + 1;
-                // the first plane of slab K (K > K0) goes out with the coarse faces of slab K + 1
-                if (p > k0 && p < k1 && (p - k0) % M == 0 && p / M + 1 < K1) ok = issue_coarse(p / M + 1);
+                if (!ok) *s_fail = 1;
             }
-            if (!ok) *s_fail = 1;
-        }
-    } else if (warp > NCW) {
-        // ------------------------------------------------------------ builder warps
-        const int bt = tid - CONS - 32;              // 0 .. NBT-1
-        // the chunk's first slab, with the consumers
-        bool fail = !mbar_wait(&cfull[0], 0, A.wait_ns);
-        fail = named_or<CONS + L::NBT>(3, fail);
-        if (!fail)
-            build_slab<M, TY, CONS + L::NBT>(A, sm + L::oCoarse, sm + L::oSlab, sm + L::oZ, A.sc + (size_t)K0 * kSCW,
-                                             CONS + bt, 3);
-        if (!fail) {
-            mbar_arrive(&cempty[0]);
-            mbar_arrive(&built[0]);
-        }
-        // TC: the coarse cells of a freed slab K (sums over its M dense rows, in
-        // the rows' order, in FP32; the scaling in FP64)
-        auto upscale = [&](int K) {
-            constexpr int CX = L::CX, CY = L::CY;
-            const float* tb = sm + L::oTcb + ((K - K0) & 1) * TY * CX;
-            const double inv = A.tcinv[K];
-            for (int t = bt; t < CY * CX; t += L::NBT) {
-                const int Jc = t / CX, I = t - Jc * CX;
-                float v = 0.f;
-#pragma unroll
-                for (int b = 0; b < M; ++b) v += tb[(Jc * M + b) * CX + I];
-                A.Tc[((size_t)K * g.ny + J0 + Jc) * g.nx + I0 + I] = (double)v * inv;
-            }
-        };
-        for (int K = K0 + 1; K < K1 && !fail; ++K) {
-            const int bb = (K - K0) & 1, use = (K - K0) >> 1;
-            bool f = !mbar_wait_idle(&cfull[bb], use & 1, A.wait_ns, kIdleNs);
-            if (!f && use > 0) f = !mbar_wait_idle(&freed[bb], (use - 1) & 1, A.wait_ns, kIdleNs);
-            fail = named_or<L::NBT>(2, f);
-            if (fail) break;
-            if constexpr (TC) {
-                if (use > 0) upscale(K - 2);
-            }
-            build_slab<M, TY, L::NBT>(A, sm + L::oCoarse + bb * L::CBOX, sm + L::oSlab + bb * L::SLAB, sm + L::oZ,
-                                      A.sc + (size_t)K * kSCW, bt, 2);
-            mbar_arrive(&cempty[bb]);
-            mbar_arrive(&built[bb]);
-        }
-        if constexpr (TC) {
-            // the chunk's last two slabs, once the consumers have freed them
-            for (int K = max(K0, K1 - 2); K < K1 && !fail; ++K) {
-                const int bb = (K - K0) & 1, use = (K - K0) >> 1;
-                fail = named_or<L::NBT>(2, !mbar_wait_idle(&freed[bb], use & 1, A.wait_ns, kIdleNs));
-                if (!fail) upscale(K);
-            }
-        }
-        if (fail && bt == 0) *s_fail = 1;
-    } else {
-        // ------------------------------------------------------------ consumer warps
-        // this thread's 4-cell segment of dense row jl; the half-warps take rows
-        // four apart (slab rows 4 SXC floats apart fall 16 banks apart, so the
-        // half-warps' coarse-column reads do not conflict)
-        const int seg = tid & 15, jl = ((warp >> 2) << 3) + (warp & 3) + 4 * ((tid >> 4) & 1);
-        const int il0 = seg * 4, cb0 = il0 / M;      // first coarse column of the segment (tile-local)
-        const auto& rx = A.rx;
-        const bool wrap_w = (i0 == 0 && seg == 0), wrap_e = (i0 + kTX == g.Nx && seg == 15);
-        const bool wrap_s = (j0 == 0 && jl == 0), wrap_n = (j0 + TY == g.Ny && jl == TY - 1);
-        bool fail = false;
-        float dmax = 0.f;
-        const float kx2 = g.kx2, ky2 = g.ky2;
-        const float ca = A.a, cbb = A.b, gdt = A.gdt;
-        const float2 kx2p = make_float2(kx2, kx2), ky2p = make_float2(ky2, ky2), gdtp = make_float2(gdt, gdt);
-        const float2 cap = make_float2(ca, ca), cbp = make_float2(cbb, cbb);
-        // PK: the update runs on packed pairs of cells (0, 1), (2, 3); vn then
-        // holds the negated V split, the sign its flux enters with
-        constexpr bool PK = !DIVONLY;
-        const size_t plane = (size_t)g.Nx * g.Ny;
-        float* outp = A.Tp1 + (size_t)k0 * plane + (size_t)(j0 + jl) * g.Nx + i0 + il0;
-        const int o = (jl + 1) * kBX + il0 + 4;      // this segment's first cell in a plane box
-        float wcar[4] = {0.f, 0.f, 0.f, 0.f};        // R_x split of W on plane k (from layer k-1)
-        float tcs[NC] = {};                          // upscale partials of the segment's coarse columns
-        // the chunk's first slab, with the builder warps (measured faster than
-        // waiting for the builders alone)
-        fail = !mbar_wait(&cfull[0], 0, A.wait_ns);
-        fail = named_or<CONS + L::NBT>(3, fail);
-        if (!fail)
-            build_slab<M, TY, CONS + L::NBT>(A, sm + L::oCoarse, sm + L::oSlab, sm + L::oZ, A.sc + (size_t)K0 * kSCW,
-                                             tid, 3);
-        for (int r = 0; r < 2; ++r)
-            if (!fail && !mbar_wait(&full[r], 0, A.wait_ns)) fail = true;
-        // one layer; sb, sc, st: the ring slots of planes k-1, k, k+1; tpar: the
-        // parity of the ring of plane k+1
-        auto layer = [&](const int k, const int i, const int Kr, const int sb, const int sc, const int st,
-                         const int tpar) {
-            const int bb = Kr & 1;
-            if (i == 0 && Kr > 0 && !fail && !mbar_wait(&built[bb], (Kr >> 1) & 1, A.wait_ns)) fail = true;
-            if (!fail && !mbar_wait(&full[st], tpar, A.wait_ns)) fail = true;
+        } else {
+            // ------------------------------------------------------------ builder warps
+            const int bt = tid - CONS - 32;              // 0 .. NBT-1
+            // the chunk's first slab, with the consumers
+            bool fail = !mbar_wait(&cfull[0], 0, A.wait_ns);
+            fail = named_or<CONS + L::NBT>(3, fail);
+            if (!fail)
+                build_slab<M, TY, CONS + L::NBT>(A, sm + L::oCoarse, sm + L::oSlab, sm + L::oZ, A.sc + (size_t)K0 * kSCW,
+                                                 CONS + bt, 3);
             if (!fail) {
-                const float* slab = sm + L::oSlab + bb * L::SLAB;
-                const float* lcp = sm + st * L::slot + L::oLC;
-                const float2 c0 = *reinterpret_cast<const float2*>(lcp);
-                const float inv_dz = c0.x, hz = c0.y;
-                float wb[4], wt[4], vs[4], vn[4], us[5];
-                {
-                    // R_x splits of the full-width W (planes k, k+1) and V (faces jl, jl+1)
+                mbar_arrive(&cempty[0]);
+                mbar_arrive(&built[0]);
+            }
+            // TC: the coarse cells of a freed slab K (sums over its M dense rows, in
+            // the rows' order, in FP32; the scaling in FP64)
+            auto upscale = [&](int K) {
+                constexpr int CX = L::CX, CY = L::CY;
+                const float* tb = sm + L::oTcb + ((K - K0) & 1) * TY * CX;
+                const double inv = A.tcinv[K];
+                for (int t = bt; t < CY * CX; t += L::NBT) {
+                    const int Jc = t / CX, I = t - Jc * CX;
+                    float v = 0.f;
+    #pragma unroll
+                    for (int b = 0; b < M; ++b) v += tb[(Jc * M + b) * CX + I];
+                    A.Tc[((size_t)K * g.ny + J0 + Jc) * g.nx + I0 + I] = (double)v * inv;
+                }
+            };
+            for (int K = K0 + 1; K < K1 && !fail; ++K) {
+                const int bb = (K - K0) & 1, use = (K - K0) >> 1;
+                bool f = !mbar_wait_idle(&cfull[bb], use & 1, A.wait_ns, kIdleNs);
+                if (!f && use > 0) f = !mbar_wait_idle(&freed[bb], (use - 1) & 1, A.wait_ns, kIdleNs);
+                fail = named_or<L::NBT>(2, f);
+                if (fail) break;
+                if constexpr (TC) {
+                    if (use > 0) upscale(K - 2);
+                }
+                build_slab<M, TY, L::NBT>(A, sm + L::oCoarse + bb * L::CBOX, sm + L::oSlab + bb * L::SLAB, sm + L::oZ,
+                                          A.sc + (size_t)K * kSCW, bt, 2);
+                mbar_arrive(&cempty[bb]);
+                mbar_arrive(&built[bb]);
+            }
+            if constexpr (TC) {
+                // the chunk's last two slabs, once the consumers have freed them
+                for (int K = max(K0, K1 - 2); K < K1 && !fail; ++K) {
+                    const int bb = (K - K0) & 1, use = (K - K0) >> 1;
+                    fail = named_or<L::NBT>(2, !mbar_wait_idle(&freed[bb], use & 1, A.wait_ns, kIdleNs));
+                    if (!fail) upscale(K);
+                }
+            }
+            if (fail && bt == 0) *s_fail = 1;
+        }
+    } else {
+        if constexpr (L::RS) asm volatile("setmaxnreg.inc.sync.aligned.u32 %0;" ::"n"(kRegCons));
+        if constexpr (DIVONLY) {
+            // ------------------------------------------------------------ consumer warps (the reductions)
+            // this thread's 4-cell segment of dense row jl; the half-warps take rows
+            // four apart (slab rows 4 SXC floats apart fall 16 banks apart, so the
+            // half-warps' coarse-column reads do not conflict)
+            const int seg = tid & 15, jl = ((warp >> 2) << 3) + (warp & 3) + 4 * ((tid >> 4) & 1);
+            const int cb0 = seg * 4 / M;                 // first coarse column of the segment (tile-local)
+            const auto& rx = A.rx;
+            bool fail = false;
+            float dmax = 0.f;
+            float wcar[4] = {0.f, 0.f, 0.f, 0.f};        // R_x split of W on plane k (from layer k-1)
+            // the chunk's first slab, with the builder warps
+            fail = !mbar_wait(&cfull[0], 0, A.wait_ns);
+            fail = named_or<CONS + L::NBT>(3, fail);
+            if (!fail)
+                build_slab<M, TY, CONS + L::NBT>(A, sm + L::oCoarse, sm + L::oSlab, sm + L::oZ, A.sc + (size_t)K0 * kSCW,
+                                                 tid, 3);
+            for (int r = 0; r < 2; ++r)
+                if (!fail && !mbar_wait(&full[r], 0, A.wait_ns)) fail = true;
+            auto layer = [&](const int k, const int i, const int Kr, const int sb, const int st, const int tpar) {
+                const int bb = Kr & 1;
+                if (i == 0 && Kr > 0 && !fail && !mbar_wait(&built[bb], (Kr >> 1) & 1, A.wait_ns)) fail = true;
+                if (!fail && !mbar_wait(&full[st], tpar, A.wait_ns)) fail = true;
+                if (!fail) {
+                    const float* slab = sm + L::oSlab + bb * L::SLAB;
+                    const float* lcp = sm + st * L::slot + L::oLC;
+                    const float2 c0 = *reinterpret_cast<const float2*>(lcp);
+                    const float inv_dz = c0.x, hz = c0.y;
+                    float wb[4], wt[4], vs[4], vn[4], us[5];
+                    // R_x splits of the full-width W (planes k, k+1) and V (faces jl, jl+1);
                     // slab column c holds coarse column I0 - 1 + c
                     const float* yt = slab + L::bWY + ((i + 1) * TY + jl) * SXC + cb0;
                     const float* rs = slab + L::bVR + (i * (TY + 1) + jl) * SXC + cb0;
@@ -496,48 +530,44 @@ k_fused(const __grid_constant__ CUtensorMap tmn, const __grid_constant__ CUtenso
                     float ytv[NV], rsv[NV], rnv[NV], urv[NC + 1];
                     if (k == k0) {
                         const float* yb = slab + L::bWY + jl * SXC + cb0;            // plane k0 (i = 0)
-#pragma unroll
+    #pragma unroll
                         for (int a = 0; a < 4; ++a) {
                             const int cb = a / M;
                             wcar[a] = rsplit3(rx[a], yb[cb], yb[cb + 1], yb[cb + 2]);
                         }
                     }
-#pragma unroll
+    #pragma unroll
                     for (int c = 0; c < NV; ++c) {
                         ytv[c] = yt[c];
                         rsv[c] = rs[c];
                         rnv[c] = rn[c];
                     }
-#pragma unroll
+    #pragma unroll
                     for (int q = 0; q <= NC; ++q) urv[q] = ur[q];
-#pragma unroll
+    #pragma unroll
                     for (int a = 0; a < 4; ++a) {
                         const int cb = a / M;
                         wb[a] = wcar[a];
                         wt[a] = rsplit3(rx[a], ytv[cb], ytv[cb + 1], ytv[cb + 2]);
                         vs[a] = rsplit3(rx[a], rsv[cb], rsv[cb + 1], rsv[cb + 2]);
-                        vn[a] = PK ? nrsplit3(rx[a], rnv[cb], rnv[cb + 1], rnv[cb + 2])
-                                   : rsplit3(rx[a], rnv[cb], rnv[cb + 1], rnv[cb + 2]);
+                        vn[a] = rsplit3(rx[a], rnv[cb], rnv[cb + 1], rnv[cb + 2]);
                     }
                     // stage X: cell balance, west to east, in units of U / (2 dx)
-#pragma unroll
+    #pragma unroll
                     for (int q = 0; q < NC; ++q) {
                         float h = urv[q];
                         us[q * M] = h;
-#pragma unroll
+    #pragma unroll
                         for (int a = 0; a < M - 1; ++a) {
                             const int m = q * M + a;
-                            h = (PK ? h + (vn[m] + vs[m]) : h - (vn[m] - vs[m])) - (wt[m] - wb[m]) * hz;
+                            h = h - (vn[m] - vs[m]) - (wt[m] - wb[m]) * hz;
                             us[m + 1] = h;
                         }
                     }
                     us[4] = urv[NC];
-#pragma unroll
-                    for (int a = 0; a < 4; ++a) wcar[a] = wt[a];
-                }
-                if (DIVONLY) {
-#pragma unroll
+    #pragma unroll
                     for (int a = 0; a < 4; ++a) {
+                        wcar[a] = wt[a];
                         const float d = KIND == 2 ? 2.f * (fmaxf(fabsf(us[a]), fabsf(us[a + 1])) +
                                                            fmaxf(fabsf(vs[a]), fabsf(vn[a]))) +
                                                         fmaxf(fabsf(wb[a]), fabsf(wt[a])) * inv_dz
@@ -545,59 +575,208 @@ k_fused(const __grid_constant__ CUtensorMap tmn, const __grid_constant__ CUtenso
                                                         (wt[a] - wb[a]) * inv_dz;
                         dmax = fmaxf(dmax, fabsf(d));
                     }
-                } else {
-                    const float* Pn_b = sm + sb * L::slot + L::oTn;
-                    const float* Pm_b = sm + sb * L::slot + L::oTm;
-                    const float* Pn_c = sm + sc * L::slot + L::oTn;
-                    const float* Pm_c = sm + sc * L::slot + L::oTm;
-                    const float* Pn_t = sm + st * L::slot + L::oTn;
-                    const float* Pm_t = sm + st * L::slot + L::oTm;
-                    const float4 tc4 = *reinterpret_cast<const float4*>(Pn_c + o);
-                    float4 ts4 = *reinterpret_cast<const float4*>(Pn_c + o - kBX);
-                    float4 tn4 = *reinterpret_cast<const float4*>(Pn_c + o + kBX);
-                    const float4 dc4 = *reinterpret_cast<const float4*>(Pm_c + o);
-                    float4 ds4 = *reinterpret_cast<const float4*>(Pm_c + o - kBX);
-                    float4 dn4 = *reinterpret_cast<const float4*>(Pm_c + o + kBX);
-                    float tw = __shfl_up_sync(0xffffffffu, tc4.w, 1), te = __shfl_down_sync(0xffffffffu, tc4.x, 1);
-                    float dw = __shfl_up_sync(0xffffffffu, dc4.w, 1), de = __shfl_down_sync(0xffffffffu, dc4.x, 1);
-                    if (seg == 0) { tw = Pn_c[o - 1]; dw = Pm_c[o - 1]; }
-                    if (seg == 15) { te = Pn_c[o + 4]; de = Pm_c[o + 4]; }
-                    if (wrap_w | wrap_e | wrap_s | wrap_n) {
-                        // the box holds zeros beyond the domain: fetch the periodic images
-                        const float* gn = A.Tn + (size_t)k * plane;
-                        const float* gm = A.Tm + (size_t)k * plane;
-                        const size_t row = (size_t)(j0 + jl) * g.Nx;
-                        if (wrap_w) { tw = gn[row + g.Nx - 1]; dw = gm[row + g.Nx - 1]; }
-                        if (wrap_e) { te = gn[row]; de = gm[row]; }
-                        // rows beyond the y edges: periodic images, or a y-slab's halo rows
-                        const size_t hrow = (size_t)k * A.hstride + i0 + il0;
-                        if (wrap_s) {
-                            ts4 = *reinterpret_cast<const float4*>(A.hs[0] + hrow);
-                            ds4 = *reinterpret_cast<const float4*>(A.hs[1] + hrow);
-                        }
-                        if (wrap_n) {
-                            tn4 = *reinterpret_cast<const float4*>(A.hn[0] + hrow);
-                            dn4 = *reinterpret_cast<const float4*>(A.hn[1] + hrow);
-                        }
+                }
+                // ring slot sb (plane k-1) and, after the slab's last layer, the
+                // slab's intermediates are no longer needed by this thread
+                mbar_arrive(&empty[sb]);
+                if (i == M - 1) mbar_arrive(&freed[bb]);
+            };
+            {
+                int sb = 0, st = 2, tpar = 0;
+                for (int k = k0; k < k1; ++k) {
+                    layer(k, k & (M - 1), (k - k0) / M, sb, st, tpar);
+                    sb = (sb + 1 == NB) ? 0 : sb + 1;
+                    if (++st == NB) {
+                        st = 0;
+                        tpar ^= 1;
                     }
-                    // planes below / above: zero-filled beyond the plates, where W is zero
-                    // and the plate value enters D through `plate`
-                    const float4 tb4 = *reinterpret_cast<const float4*>(Pn_b + o);
-                    const float4 db4 = *reinterpret_cast<const float4*>(Pm_b + o);
-                    const float4 tt4 = *reinterpret_cast<const float4*>(Pn_t + o);
-                    const float4 dt4 = *reinterpret_cast<const float4*>(Pm_t + o);
-                    const float tcv[6] = {tw, tc4.x, tc4.y, tc4.z, tc4.w, te};
-                    const float dcv[6] = {dw, dc4.x, dc4.y, dc4.z, dc4.w, de};
-                    // x fluxes in scalar form (adjacent cells share a face), then the
-                    // rest on the pairs (0, 1), (2, 3) with the pair constants of the row:
-                    // D = kx2 (dw + de) + ky2 (ds + dn) + cdn db + cup dt - diag dc + plate
-                    const float4 q0 = *reinterpret_cast<const float4*>(lcp + 12);   // bwlo, bwhi
-                    const float4 q1 = *reinterpret_cast<const float4*>(lcp + 16);   // -twlo, -twhi
-                    const float4 q2 = *reinterpret_cast<const float4*>(lcp + 20);   // cdn, cup
-                    const float4 q3 = *reinterpret_cast<const float4*>(lcp + 24);   // -diag, plate
+                }
+            }
+            if (fail) *s_fail = 1;
+            for (int d = 16; d > 0; d >>= 1) dmax = fmaxf(dmax, __shfl_down_sync(0xffffffffu, dmax, d));
+            if (lane == 0) red[warp] = dmax;
+        } else {
+            // ------------------------------------------------------------ consumer warps (the step)
+            // this thread's 4-cell segment of the dense rows jl and jl + 1; the
+            // half-warps take row pairs four rows apart (slab rows 4 SXC floats
+            // apart fall 16 banks apart, so the half-warps' coarse-column reads do
+            // not conflict).  Per layer a thread loads from the ring its two rows
+            // of plane k + 1 and the rows jl - 1 and jl + 2 of plane k, and splits
+            // the V face between its rows once.  Carried from layer to layer
+            // (Carry): the rows of T^s and T^{s-1} on plane k, the advective flux
+            // through the layer's bottom face (w T_f), the diffusive term of the
+            // plane below (cdn T^{s-1}_{k-1}) and the R_x split of W on plane k.
+            // Layers run in pairs with both rings waited for first, so that the
+            // pair's body has no branch: the two Carry sets alternate and no
+            // register is copied between layers.
+            const int seg = tid & 15, jl = ((warp >> 1) << 3) + ((warp & 1) << 1) + 4 * ((tid >> 4) & 1);
+            const int il0 = seg * 4, cb0 = il0 / M;      // first coarse column of the segment (tile-local)
+            const auto& rx = A.rx;
+            bool fail = false;
+            const float2 kx2p = make_float2(g.kx2, g.kx2), ky2p = make_float2(g.ky2, g.ky2);
+            const float2 gdtp = make_float2(A.gdt, A.gdt), cap = make_float2(A.a, A.a), cbp = make_float2(A.b, A.b);
+            const size_t plane = (size_t)g.Nx * g.Ny;
+            float* outp = A.Tp1 + (size_t)k0 * plane + (size_t)(j0 + jl) * g.Nx + i0 + il0;
+            // offsets in a level of a ring slot: the segment's first cell of row jl
+            // (row jl + 1 follows kTX floats on), of rows jl - 1 and jl + 2, and the
+            // west / east neighbours of row jl (row jl + 1: 4 floats on)
+            const int om = jl * kTX + il0;
+            const int osr = (jl == 0) ? L::fYS + il0 : om - kTX;
+            const int onr = (jl + 2 == TY) ? L::fYN + il0 : om + 2 * kTX;
+            const int oxw = L::fXW + jl * 4 + 3, oxe = L::fXE + jl * 4;
+            float tcs[2][NC] = {};                       // upscale partials of the segment's coarse columns
+            struct Carry {
+                float4 t[2], d[2];     // T^s, T^{s-1} of rows jl, jl + 1 on plane k
+                float2 ab[2][2];       // advective flux w T_f through the bottom face of layer k (pairs)
+                float2 pd[2][2];       // cdn_k T^{s-1} on plane k - 1 (pairs)
+                float w[2][4];         // R_x split of W on plane k
+            };
+            Carry S0, S1;
+            // the chunk's first slab, with the builder warps (measured faster than
+            // waiting for the builders alone)
+            fail = !mbar_wait(&cfull[0], 0, A.wait_ns);
+            fail = named_or<CONS + L::NBT>(3, fail);
+            if (!fail)
+                build_slab<M, TY, CONS + L::NBT>(A, sm + L::oCoarse, sm + L::oSlab, sm + L::oZ,
+                                                 A.sc + (size_t)K0 * kSCW, tid, 3);
+            // planes k0 - 1, k0, k0 + 1 (rings 0, 1, 2; ring 2 holds the
+            // constants of layer k0): the state at the chunk's first layer
+            for (int r = 0; r < 3; ++r)
+                if (!fail && !mbar_wait(&full[r], 0, A.wait_ns)) fail = true;
+            if (!fail) {
+                const float* lc0 = sm + 2 * L::slot + L::oLC;
+                const float dzk = lc0[2], bwlo = lc0[12], bwhi = lc0[14], cdn = lc0[20];
+                const float* yb = sm + L::oSlab + L::bWY + jl * SXC + cb0;          // plane k0 (slab 0, i = 0)
+#pragma unroll
+                for (int r = 0; r < 2; ++r) {
+                    const float4 tb = *reinterpret_cast<const float4*>(sm + L::oTn + om + r * kTX);
+                    const float4 db = *reinterpret_cast<const float4*>(sm + L::oTm + om + r * kTX);
+                    S0.t[r] = *reinterpret_cast<const float4*>(sm + L::slot + L::oTn + om + r * kTX);
+                    S0.d[r] = *reinterpret_cast<const float4*>(sm + L::slot + L::oTm + om + r * kTX);
+                    const float tbv[4] = {tb.x, tb.y, tb.z, tb.w}, tcv[4] = {S0.t[r].x, S0.t[r].y, S0.t[r].z, S0.t[r].w};
+                    const float dbv[4] = {db.x, db.y, db.z, db.w};
+                    float ab[4], pd[4];
+#pragma unroll
+                    for (int a = 0; a < 4; ++a) {
+                        const int cb = r * SXC + a / M;
+                        S0.w[r][a] = rsplit3(rx[a], yb[cb], yb[cb + 1], yb[cb + 2]);
+                        ab[a] = S0.w[r][a] * (dzk * (bwlo * tbv[a] + bwhi * tcv[a]));
+                        pd[a] = cdn * dbv[a];
+                    }
+                    S0.ab[r][0] = make_float2(ab[0], ab[1]);
+                    S0.ab[r][1] = make_float2(ab[2], ab[3]);
+                    S0.pd[r][0] = make_float2(pd[0], pd[1]);
+                    S0.pd[r][1] = make_float2(pd[2], pd[3]);
+                }
+            }
+            mbar_arrive(&empty[0]);
+            // one layer, no waits: sc, st the ring slots of planes k, k + 1; bb the
+            // slab buffer; in the state at layer k, out the state at layer k + 1
+            auto layer = [&](const int k, const int i, const int bb, const int sc, const int st, const Carry& in,
+                             Carry& out) {
+                const float* slab = sm + L::oSlab + bb * L::SLAB;
+                const float* lcp = sm + st * L::slot + L::oLC;
+                const float hz = lcp[1];
+                float vf[3][4], us[2][5];
+                {
+                    // R_x splits of the full-width W (plane k+1, rows jl, jl+1) and V
+                    // (faces jl, jl+1, jl+2); slab column c holds coarse column I0 - 1 + c
+                    constexpr int NV = NC + 2;
+                    const float* yt = slab + L::bWY + ((i + 1) * TY + jl) * SXC + cb0;
+                    const float* rs = slab + L::bVR + (i * (TY + 1) + jl) * SXC + cb0;
+                    const float* ur = slab + L::bUO + (i * TY + jl) * SXC + cb0 + 1;   // outer face of column cb0
+                    float ytv[2][NV], vv[3][NV], urv[2][NC + 1];
+#pragma unroll
+                    for (int c = 0; c < NV; ++c) {
+                        ytv[0][c] = yt[c];
+                        ytv[1][c] = yt[SXC + c];
+                        vv[0][c] = rs[c];
+                        vv[1][c] = rs[SXC + c];
+                        vv[2][c] = rs[2 * SXC + c];
+                    }
+#pragma unroll
+                    for (int q = 0; q <= NC; ++q) {
+                        urv[0][q] = ur[q];
+                        urv[1][q] = ur[SXC + q];
+                    }
+#pragma unroll
+                    for (int a = 0; a < 4; ++a) {
+                        const int cb = a / M;
+#pragma unroll
+                        for (int r = 0; r < 2; ++r)
+                            out.w[r][a] = rsplit3(rx[a], ytv[r][cb], ytv[r][cb + 1], ytv[r][cb + 2]);
+#pragma unroll
+                        for (int f = 0; f < 3; ++f) vf[f][a] = rsplit3(rx[a], vv[f][cb], vv[f][cb + 1], vv[f][cb + 2]);
+                    }
+                    // stage X: cell balance, west to east, in units of U / (2 dx)
+#pragma unroll
+                    for (int r = 0; r < 2; ++r) {
+#pragma unroll
+                        for (int q = 0; q < NC; ++q) {
+                            float h = urv[r][q];
+                            us[r][q * M] = h;
+#pragma unroll
+                            for (int a = 0; a < M - 1; ++a) {
+                                const int m = q * M + a;
+                                h = h - (vf[r + 1][m] - vf[r][m]) - (out.w[r][m] - in.w[r][m]) * hz;
+                                us[r][m + 1] = h;
+                            }
+                        }
+                        us[r][4] = urv[r][NC];
+                    }
+                }
+                const float* Pn_c = sm + sc * L::slot + L::oTn;
+                const float* Pm_c = sm + sc * L::slot + L::oTm;
+                const float* Pn_t = sm + st * L::slot + L::oTn;
+                const float* Pm_t = sm + st * L::slot + L::oTm;
+#pragma unroll
+                for (int r = 0; r < 2; ++r) {
+                    out.t[r] = *reinterpret_cast<const float4*>(Pn_t + om + r * kTX);
+                    out.d[r] = *reinterpret_cast<const float4*>(Pm_t + om + r * kTX);
+                }
+                // rows jl - 1 and jl + 2 of plane k
+                const float4 ts4 = *reinterpret_cast<const float4*>(Pn_c + osr);
+                const float4 ds4 = *reinterpret_cast<const float4*>(Pm_c + osr);
+                const float4 tn4 = *reinterpret_cast<const float4*>(Pn_c + onr);
+                const float4 dn4 = *reinterpret_cast<const float4*>(Pm_c + onr);
+                // x neighbours: shuffles inside the tile, the slot's edge columns at its edges
+                float tw[2], te[2], dw[2], de[2];
+#pragma unroll
+                for (int r = 0; r < 2; ++r) {
+                    tw[r] = __shfl_up_sync(0xffffffffu, in.t[r].w, 1);
+                    te[r] = __shfl_down_sync(0xffffffffu, in.t[r].x, 1);
+                    dw[r] = __shfl_up_sync(0xffffffffu, in.d[r].w, 1);
+                    de[r] = __shfl_down_sync(0xffffffffu, in.d[r].x, 1);
+                    if (seg == 0) {
+                        tw[r] = Pn_c[oxw + 4 * r];
+                        dw[r] = Pm_c[oxw + 4 * r];
+                    }
+                    if (seg == 15) {
+                        te[r] = Pn_c[oxe + 4 * r];
+                        de[r] = Pm_c[oxe + 4 * r];
+                    }
+                }
+                // x fluxes in scalar form (adjacent cells share a face), then the
+                // rest on the pairs (0, 1), (2, 3) with the pair constants of the layer:
+                // D = kx2 (dw + de) + ky2 (ds + dn) + cdn db + cup dt - diag dc + plate,
+                // the z advective terms as (w T_f)(bottom) - (w T_f)(top) over dz; the
+                // planes beyond the plates are zero-filled, where W is zero and the plate
+                // value enters D through `plate`
+                const float4 qf = *reinterpret_cast<const float4*>(lcp + 4);    // f_lo, f_hi (top face)
+                const float4 qn = *reinterpret_cast<const float4*>(lcp + 8);    // 1/dz, cdn of layer k+1
+                const float4 q2 = *reinterpret_cast<const float4*>(lcp + 20);   // cdn, cup
+                const float4 q3 = *reinterpret_cast<const float4*>(lcp + 24);   // -diag, plate
+                float4 out4[2];
+#pragma unroll
+                for (int r = 0; r < 2; ++r) {
+                    const float4 tc4 = in.t[r], dc4 = in.d[r];
+                    const float4 tsr = r ? in.t[0] : ts4, tnr = r ? tn4 : in.t[1];
+                    const float4 dsr = r ? in.d[0] : ds4, dnr = r ? dn4 : in.d[1];
+                    const float tcv[6] = {tw[r], tc4.x, tc4.y, tc4.z, tc4.w, te[r]};
+                    const float dcv[6] = {dw[r], dc4.x, dc4.y, dc4.z, dc4.w, de[r]};
                     float F[5], cxv[4], sdx[4];
 #pragma unroll
-                    for (int a = 0; a < 5; ++a) F[a] = us[a] * (tcv[a] + tcv[a + 1]);
+                    for (int a = 0; a < 5; ++a) F[a] = us[r][a] * (tcv[a] + tcv[a + 1]);
 #pragma unroll
                     for (int a = 0; a < 4; ++a) {
                         cxv[a] = F[a] - F[a + 1];
@@ -606,72 +785,96 @@ k_fused(const __grid_constant__ CUtensorMap tmn, const __grid_constant__ CUtenso
                     float2 res[2];
 #pragma unroll
                     for (int h = 0; h < 2; ++h) {
-                        const float2 tc = h ? hi2(tc4) : lo2(tc4), dc = h ? hi2(dc4) : lo2(dc4);
-                        const float2 ts = h ? hi2(ts4) : lo2(ts4), tn = h ? hi2(tn4) : lo2(tn4);
-                        const float2 ds = h ? hi2(ds4) : lo2(ds4), dn = h ? hi2(dn4) : lo2(dn4);
-                        const float2 tb = h ? hi2(tb4) : lo2(tb4), tt = h ? hi2(tt4) : lo2(tt4);
-                        const float2 db = h ? hi2(db4) : lo2(db4), dt = h ? hi2(dt4) : lo2(dt4);
+                        const float2 tcp = h ? hi2(tc4) : lo2(tc4), dcp = h ? hi2(dc4) : lo2(dc4);
+                        const float2 tsp = h ? hi2(tsr) : lo2(tsr), tnp = h ? hi2(tnr) : lo2(tnr);
+                        const float2 dsp = h ? hi2(dsr) : lo2(dsr), dnp = h ? hi2(dnr) : lo2(dnr);
+                        const float2 ttp = h ? hi2(out.t[r]) : lo2(out.t[r]), dtp = h ? hi2(out.d[r]) : lo2(out.d[r]);
                         const int a = 2 * h;
+                        // the top face: T_f = f_lo T_k + f_hi T_{k+1}, its advective flux
+                        const float2 atop = mul2(make_float2(out.w[r][a], out.w[r][a + 1]),
+                                                 fma2(lo2(qf), tcp, mul2(hi2(qf), ttp)));
                         float2 acc = fma2(kx2p, make_float2(sdx[a], sdx[a + 1]), hi2(q3));
-                        acc = fma2(ky2p, add2(ds, dn), acc);
-                        acc = fma2(lo2(q2), db, acc);
-                        acc = fma2(hi2(q2), dt, acc);
-                        acc = fma2(lo2(q3), dc, acc);
+                        acc = fma2(ky2p, add2(dsp, dnp), acc);
+                        acc = add2(acc, in.pd[r][h]);
+                        acc = fma2(hi2(q2), dtp, acc);
+                        acc = fma2(lo2(q3), dcp, acc);
                         acc = add2(acc, make_float2(cxv[a], cxv[a + 1]));
-                        acc = fma2(make_float2(vs[a], vs[a + 1]), add2(ts, tc), acc);
-                        acc = fma2(make_float2(vn[a], vn[a + 1]), add2(tc, tn), acc);
-                        acc = fma2(make_float2(wb[a], wb[a + 1]), fma2(lo2(q0), tb, mul2(hi2(q0), tc)), acc);
-                        acc = fma2(make_float2(wt[a], wt[a + 1]), fma2(lo2(q1), tc, mul2(hi2(q1), tt)), acc);
-                        res[h] = LF ? fma2(gdtp, acc, dc) : fma2(gdtp, acc, fma2(cap, dc, mul2(cbp, tc)));
+                        acc = fma2(make_float2(vf[r][a], vf[r][a + 1]), add2(tsp, tcp), acc);
+                        acc = fma2(make_float2(-vf[r + 1][a], -vf[r + 1][a + 1]), add2(tcp, tnp), acc);
+                        acc = fma2(lo2(qn), add2(in.ab[r][h], make_float2(-atop.x, -atop.y)), acc);
+                        res[h] = LF ? fma2(gdtp, acc, dcp) : fma2(gdtp, acc, fma2(cap, dcp, mul2(cbp, tcp)));
+                        out.ab[r][h] = atop;
+                        out.pd[r][h] = mul2(hi2(qn), dcp);
                     }
-                    *reinterpret_cast<float4*>(outp) = make_float4(res[0].x, res[0].y, res[1].x, res[1].y);
-                    if constexpr (TC) {
-                        // the upscale integration (Section 3.3): dz-weighted sums over the
-                        // slab's layers of each coarse column's cells in this row
-                        const float dzk = lcp[2];
-                        if (NC == 1) {
-                            tcs[0] += dzk * ((res[0].x + res[0].y) + (res[1].x + res[1].y));
-                        } else {
-                            tcs[0] += dzk * (res[0].x + res[0].y);
-                            tcs[NC - 1] += dzk * (res[1].x + res[1].y);
-                        }
-                        if (i == M - 1) {
-                            float* tp = sm + L::oTcb + (bb * TY + jl) * L::CX + cb0;
+                    out4[r] = make_float4(res[0].x, res[0].y, res[1].x, res[1].y);
+                }
+                float* op = outp + (size_t)(k - k0) * plane;
+                *reinterpret_cast<float4*>(op) = out4[0];
+                *reinterpret_cast<float4*>(op + g.Nx) = out4[1];
+                if constexpr (TC) {
+                    // the upscale integration (Section 3.3): dz-weighted sums over the
+                    // slab's layers of each coarse column's cells in these rows
+                    const float dzk = lcp[2];
 #pragma unroll
-                            for (int q = 0; q < NC; ++q) {
-                                tp[q] = tcs[q];
-                                tcs[q] = 0.f;
+                    for (int r = 0; r < 2; ++r) {
+                        const float4 v = out4[r];
+                        if (NC == 1) {
+                            tcs[r][0] += dzk * ((v.x + v.y) + (v.z + v.w));
+                        } else {
+                            tcs[r][0] += dzk * (v.x + v.y);
+                            tcs[r][NC - 1] += dzk * (v.z + v.w);
+                        }
+                    }
+                }
+            };
+            // the layers in pairs (chunks hold whole coarse slabs of M = 2 or 4
+            // layers); ring r holds plane k0 - 1 + r in slot r % NB with parity
+            // (r / NB) & 1
+            {
+                int sc = 1, st = 2, su = 3 % NB, pt = 0, pu = (3 / NB) & 1;   // slots of planes k, k+1, k+2
+                for (int k = k0; k < k1; k += 2) {
+                    const int i = k & (M - 1), Kr = (k - k0) / M, bb = Kr & 1;
+                    if (i == 0 && Kr > 0 && !fail && !mbar_wait(&built[bb], (Kr >> 1) & 1, A.wait_ns)) fail = true;
+                    if (!fail && !mbar_wait(&full[st], pt, A.wait_ns)) fail = true;
+                    if (!fail && !mbar_wait(&full[su], pu, A.wait_ns)) fail = true;
+                    if (!fail) {
+                        layer(k, i, bb, sc, st, S0, S1);
+                        layer(k + 1, i + 1, bb, st, su, S1, S0);
+                    }
+                    // planes k and k + 1 are no longer needed by this thread; nor,
+                    // after the slab's last layer, the slab's intermediates
+                    mbar_arrive(&empty[sc]);
+                    mbar_arrive(&empty[st]);
+                    if (i + 1 == M - 1) {
+                        if constexpr (TC) {
+#pragma unroll
+                            for (int r = 0; r < 2; ++r) {
+                                float* tp = sm + L::oTcb + (bb * TY + jl + r) * L::CX + cb0;
+#pragma unroll
+                                for (int q = 0; q < NC; ++q) {
+                                    tp[q] = tcs[r][q];
+                                    tcs[r][q] = 0.f;
+                                }
                             }
                         }
+                        mbar_arrive(&freed[bb]);
+                    }
+                    sc = su;
+                    st = su + 1;
+                    pt = pu;
+                    if (st == NB) {
+                        st = 0;
+                        pt ^= 1;
+                    }
+                    su = st + 1;
+                    pu = pt;
+                    if (su == NB) {
+                        su = 0;
+                        pu ^= 1;
                     }
                 }
             }
-            // plane k-1 is no longer needed by this thread; nor, after the
-            // slab's last layer, the slab's intermediates
-            mbar_arrive(&empty[sb]);
-            if (i == M - 1) mbar_arrive(&freed[bb]);
-            outp += plane;
-        };
-        // the slots rotate (a loop unrolled by the ring length ran 8 % slower on
-        // 512 x 512 x 384: its copies of the layer body miss the instruction
-        // cache; unrolled by M, so that the slab offsets are constants, it was
-        // no faster)
-        {
-            int sb = 0, sc = 1, st = 2, tpar = 0;
-            for (int k = k0; k < k1; ++k) {
-                layer(k, k & (M - 1), (k - k0) / M, sb, sc, st, tpar);
-                sb = sc;
-                sc = st;
-                if (++st == NB) {
-                    st = 0;
-                    tpar ^= 1;
-                }
-            }
-        }
-        if (fail) *s_fail = 1;
-        if (DIVONLY) {
-            for (int d = 16; d > 0; d >>= 1) dmax = fmaxf(dmax, __shfl_down_sync(0xffffffffu, dmax, d));
-            if (lane == 0) red[warp] = dmax;
+            if (fail) *s_fail = 1;
         }
     }
     __syncthreads();
@@ -744,14 +947,17 @@ EncodeTiledFn encode_fn()
     return fn;
 }
 
-// Tensor maps of (buffer, shape, box), encoded once each.
-bool map_fx(CUtensorMap* out, const float* base, int d0, int d1, int d2, int b0, int b1, int b2)
+// Tensor maps of (buffer, shape, row and layer strides in floats, box),
+// encoded once each.
+bool map_fx3(CUtensorMap* out, const float* base, int d0, int d1, int d2, size_t s1, size_t s2, int b0, int b1,
+             int b2)
 {
-    struct Entry { const float* p; int d[6]; CUtensorMap m; };
-    static Entry cache[32];
+    struct Entry { const float* p; long long d[8]; CUtensorMap m; };
+    constexpr int kCache = 128;
+    static Entry cache[kCache];
     static int n = 0, next = 0;
     static std::mutex mu;
-    const int key[6] = {d0, d1, d2, b0, b1, b2};
+    const long long key[8] = {d0, d1, d2, (long long)s1, (long long)s2, b0, b1, b2};
     {
         std::lock_guard<std::mutex> lock(mu);
         for (int q = 0; q < n; ++q)
@@ -763,7 +969,7 @@ bool map_fx(CUtensorMap* out, const float* base, int d0, int d1, int d2, int b0,
     EncodeTiledFn fn = encode_fn();
     if (!fn) return false;
     cuuint64_t dims[3] = {(cuuint64_t)d0, (cuuint64_t)d1, (cuuint64_t)d2};
-    cuuint64_t strides[2] = {(cuuint64_t)d0 * 4, (cuuint64_t)d0 * d1 * 4};
+    cuuint64_t strides[2] = {(cuuint64_t)s1 * 4, (cuuint64_t)s2 * 4};
     cuuint32_t box[3] = {(cuuint32_t)b0, (cuuint32_t)b1, (cuuint32_t)b2};
     cuuint32_t es[3] = {1, 1, 1};
     if (fn(out, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, (void*)base, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
@@ -771,11 +977,16 @@ bool map_fx(CUtensorMap* out, const float* base, int d0, int d1, int d2, int b0,
         CUDA_SUCCESS)
         return false;
     std::lock_guard<std::mutex> lock(mu);
-    Entry& e = cache[n < 32 ? n++ : (next = (next + 1) % 32)];
+    Entry& e = cache[n < kCache ? n++ : (next = (next + 1) % kCache)];
     e.p = base;
     memcpy(e.d, key, sizeof key);
     e.m = *out;
     return true;
+}
+// A contiguous [d2][d1][d0] array.
+bool map_fx(CUtensorMap* out, const float* base, int d0, int d1, int d2, int b0, int b1, int b2)
+{
+    return map_fx3(out, base, d0, d1, d2, (size_t)d0, (size_t)d0 * d1, b0, b1, b2);
 }
 
 template <int M, int TY, int KIND, bool LF, bool TC = false>
@@ -786,19 +997,44 @@ cudaError_t launch_fl(const Grid<float>& g, const FusedInputs& in, const float* 
     static unsigned long long attr = 0;                   // one bit per device
     cudaError_t e = smem_optin(reinterpret_cast<const void*>(k_fused<M, TY, KIND, LF, TC>), (int)L::bytes, &attr);
     if (e != cudaSuccess) return e;
-    CUtensorMap mn, mm, mlc, mu, mv, mw;
-    memset(&mn, 0, sizeof mn);
-    memset(&mm, 0, sizeof mm);
-    if (KIND == 0 && (!map_fx(&mn, T, g.Nx, g.Ny, g.Nz, kBX, L::kBY, 1) ||
-                      !map_fx(&mm, Tm1, g.Nx, g.Ny, g.Nz, kBX, L::kBY, 1)))
-        return cudaErrorInvalidValue;
+    if constexpr (L::RS) {
+        // the register split inside the kernel adds up only to a launch of
+        // exactly kRegLaunch registers per thread: refuse any other build
+        static int regs = -1;
+        if (regs < 0) {
+            cudaFuncAttributes fa;
+            e = cudaFuncGetAttributes(&fa, reinterpret_cast<const void*>(k_fused<M, TY, KIND, LF, TC>));
+            if (e != cudaSuccess) return e;
+            regs = fa.numRegs;
+        }
+        if (regs != kRegLaunch) return cudaErrorInvalidConfiguration;
+    }
+    FLMaps maps;
+    memset(&maps, 0, sizeof maps);
+    if (KIND == 0) {
+        // per level: the tile's rows, single rows, four columns; the rows beyond
+        // the y edges: [Nz][Nx] at layer stride hstride
+        const float* lv[2] = {T, Tm1};
+        CUtensorMap* mt[2] = {&maps.tn, &maps.tm};
+        CUtensorMap* mr1[2] = {&maps.rn, &maps.rm};
+        CUtensorMap* mx4[2] = {&maps.xn, &maps.xm};
+        CUtensorMap* ms[2] = {&maps.sn, &maps.smp};
+        CUtensorMap* mh[2] = {&maps.hn, &maps.hm};
+        for (int q = 0; q < 2; ++q)
+            if (!map_fx(mt[q], lv[q], g.Nx, g.Ny, g.Nz, kTX, TY, 1) || !map_fx(mr1[q], lv[q], g.Nx, g.Ny, g.Nz, kTX, 1, 1) ||
+                !map_fx(mx4[q], lv[q], g.Nx, g.Ny, g.Nz, 4, TY, 1) ||
+                !map_fx3(ms[q], in.hs[q], g.Nx, 1, g.Nz, (size_t)g.Nx, in.hstride, kTX, 1, 1) ||
+                !map_fx3(mh[q], in.hn[q], g.Nx, 1, g.Nz, (size_t)g.Nx, in.hstride, kTX, 1, 1))
+                return cudaErrorInvalidValue;
+    }
     const int px = g.nx + 8;
     const float* pU = in.pad;
     const float* pV = pU + (size_t)g.nz * (g.ny + 2) * px;
     const float* pW = pV + (size_t)g.nz * (g.ny + 3) * px;
-    if (!map_fx(&mlc, in.lc, kLCW, g.Nz, 1, kLCW, 1, 1) || !map_fx(&mu, pU, px, g.ny + 2, g.nz, L::BXC, L::NUR, 3) ||
-        !map_fx(&mv, pV, px, g.ny + 3, g.nz, L::BXC, L::NVR, 3) ||
-        !map_fx(&mw, pW, px, g.ny + 2, g.nz + 1, L::BXC, L::NUR, 2))
+    if (!map_fx(&maps.lc, in.lc, kLCW, g.Nz, 1, kLCW, 1, 1) ||
+        !map_fx(&maps.cu, pU, px, g.ny + 2, g.nz, L::BXC, L::NUR, 3) ||
+        !map_fx(&maps.cv, pV, px, g.ny + 3, g.nz, L::BXC, L::NVR, 3) ||
+        !map_fx(&maps.cw, pW, px, g.ny + 2, g.nz + 1, L::BXC, L::NUR, 2))
         return cudaErrorInvalidValue;
     // ~12 waves of resident CTAs, chunks of at most 96 dense layers
 #ifndef MR_FUSED_WAVES
@@ -813,8 +1049,6 @@ cudaError_t launch_fl(const Grid<float>& g, const FusedInputs& in, const float* 
     FLArgs A;
     memset(&A, 0, sizeof A);
     A.g = g;
-    A.Tn = T;
-    A.Tm = Tm1;
     A.Tp1 = Tp1;
     A.sc = in.sc;
     A.a = (float)c.a;
@@ -833,16 +1067,10 @@ cudaError_t launch_fl(const Grid<float>& g, const FusedInputs& in, const float* 
     A.stop_ring = -1;
     if (KIND == 0) {
         take_wait_injection(&A.stop_ring, &A.wait_ns);
-        for (int q = 0; q < 2; ++q) {
-            A.hs[q] = in.hs[q];
-            A.hn[q] = in.hn[q];
-        }
-        A.hstride = in.hstride;
         A.Tc = in.Tc;
         A.tcinv = in.tcinv;
     }
-    k_fused<M, TY, KIND, LF, TC><<<dim3(chunks, g.Nx / kTX, g.Ny / TY), L::THREADS, L::bytes, st>>>(mn, mm, mlc, mu,
-                                                                                                   mv, mw, A);
+    k_fused<M, TY, KIND, LF, TC><<<dim3(chunks, g.Nx / kTX, g.Ny / TY), L::THREADS, L::bytes, st>>>(maps, A);
     return cudaGetLastError();
 }
 

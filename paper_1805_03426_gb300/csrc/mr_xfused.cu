@@ -1029,7 +1029,9 @@ cudaError_t launch_xfused_max_f32(const Grid<float>& g, int kind, const float* W
 // all folded on the host in FP64.  The pair entries hold each value twice, for
 // the packed pair arithmetic of the update:
 //   0: 1/dz, 1: 1/(2 dz), 2: dz, 4..7: fourth order only, the weights of planes
-//   k-2 .. k+1 at face k (the first layer of a chunk);
+//   k-2 .. k+1 at face k (the first layer of a chunk); second order (read by the
+//   fully fused kernel, pairs): 4..7 the linear-interpolation weights of T_k and
+//   T_{k+1} at face k+1, 8..11 1/dz and cdn of layer k+1 (zero on the last layer);
 //   12..19 (pairs): second order, the linear-interpolation weights of T_{k-1},
 //   T_k at face k and the negated weights of T_k, T_{k+1} at face k+1, each
 //   times 1/dz; fourth order, the weights of planes k-1 .. k+2 at face k+1;
@@ -1060,6 +1062,13 @@ std::vector<float> xfused_layer_constants(int Nz, const double* zf, const double
             q[28] = q[29] = (float)idz;
             q[30] = q[31] = (float)-idz;
         } else {
+            if (k < Nz - 1) {
+                const double dn = dz[k + 1], cnext = kappa / (dn * (zc[k + 1] - zc[k]));
+                q[4] = q[5] = (float)(dn / (dzk + dn));
+                q[6] = q[7] = (float)(dzk / (dzk + dn));
+                q[10] = q[11] = (float)cnext;
+            }
+            q[8] = q[9] = (float)idz;
             if (k > 0) {
                 zw[0] = dzk / (dz[k - 1] + dzk) * idz;
                 zw[1] = dz[k - 1] / (dz[k - 1] + dzk) * idz;
