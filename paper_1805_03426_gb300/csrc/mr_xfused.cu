@@ -35,15 +35,14 @@ namespace {
 using namespace ptx;
 
 constexpr int kTX = 64;                                // tile width (cells); the height TY is 16 or 8
-constexpr int kBX = kTX + 8;                            // scalar plane box width (floats)
 constexpr float kTBottom = 0.5f, kTTop = -0.5f;
 #ifndef MR_XFUSED_IDLE_NS
 #define MR_XFUSED_IDLE_NS 256
 #endif
 constexpr unsigned kIdleNs = MR_XFUSED_IDLE_NS;  // sleep between the producer warp's polls
 
-// O4: fourth-order face values of T^s (Section 2.2): the T^s box has two halo
-// rows each side and the layer constants carry the z-face weights.
+// O4: fourth-order face values of T^s (Section 2.2): T^s has two halo rows
+// each side and the layer constants carry the z-face weights.
 // TY: tile height; 16 consumer threads (4-cell segments) per row, one producer
 // warp; 64x16 tiles run two CTAs per SM, 64x8 tiles four (small grids).
 // DIV: the layout of the reductions (divergence, CFL), which stream only the
@@ -54,9 +53,16 @@ struct XT {
     static constexpr int CONS = 16 * TY;                // consumer threads
     static constexpr int THREADS = CONS + 32;           // + one producer warp
     static constexpr int CTAS = TY == 16 ? 2 : (O4 ? 3 : 4);   // resident CTAs per SM the layout is sized for
-    static constexpr int kBY = TY + 2;                  // rows of the T^{s-1} box
-    static constexpr uint32_t tm_bytes = (uint32_t)(kBX * kBY) * 4;
-    static constexpr int PM = DIV ? 0 : (int)((tm_bytes + 127) / 128) * 128 / 4;
+    // one scalar level of one plane in a ring slot, each part a TMA box on a
+    // 128-byte boundary: the tile's TY rows (64 wide), H rows south and H rows
+    // north of them, the 4 columns west and east of them (periodic images at
+    // the domain's edges); T^s has H = HN (two rows with O4), T^{s-1} H = 1
+    static constexpr int HN = O4 ? 2 : 1;
+    static constexpr int nYS = kTX * TY, nYN = nYS + kTX * HN, nXW = nYN + kTX * HN, nXE = nXW + 4 * TY;
+    static constexpr int mYS = kTX * TY, mYN = mYS + kTX, mXW = mYN + kTX, mXE = mXW + 4 * TY;
+    static constexpr int PN = DIV ? 0 : nXE + 4 * TY, PM = DIV ? 0 : mXE + 4 * TY;
+    static_assert(PN % 32 == 0 && PM % 32 == 0 && nXE % 32 == 0 && mXE % 32 == 0, "128-byte TMA boxes");
+    static constexpr uint32_t tn_bytes = (uint32_t)PN * 4, tm_bytes = (uint32_t)PM * 4;
     static constexpr int CX = kTX / M;
     static constexpr int BXC = CX + 8;                  // coarse box width: columns I0-4 .. I0+CX+3
     // ring slots; MT (two velocity sets per slot) keeps two CTAs per SM with fewer
@@ -68,9 +74,6 @@ struct XT {
     // one layer k: WY of its upper plane k+1 (its lower plane k is the previous
     // slot's), UO and VR of layer k; with MT the set of the second coarse time
     // level follows at offset DS; then the layer constants
-    static constexpr int BYN = O4 ? TY + 4 : kBY;        // rows of the T^s box
-    static constexpr uint32_t tn_bytes = (uint32_t)(kBX * BYN) * 4;
-    static constexpr int PN = DIV ? 0 : (int)((tn_bytes + 127) / 128) * 128 / 4;
     static constexpr int LCW = 32;                      // floats of one row of layer constants
     static constexpr int oTn = 0, oTm = PN;
     static constexpr int oWY = PN + PM;                 // [TY][BXC]      plane k+1
@@ -88,10 +91,16 @@ struct XT {
     static constexpr size_t bytes = (size_t)(oBar + 2 * NB) * 8;
 };
 
+// Tensor maps of the step: per scalar level (n: T^s, m: T^{s-1}) the tile's
+// rows (64 x TY boxes), the rows beyond its y edges (64 x H), the columns beyond
+// its x edges (4 x TY); the intermediates of one or two coarse time levels and
+// the layer constants.
+struct XMaps {
+    CUtensorMap tn, tm, rn, rm, xn, xm, wy, uo, vr, lc, wy1, uo1, vr1;
+};
+
 struct XArgs {
     Grid<float> g;
-    const float* Tn;     // T^s (global, for the periodic halo of edge threads)
-    const float* Tm;     // T^{s-1}
     float* Tp1;          // T^{s+1}
     const float* lc;     // [Nz][32] per-layer constants
     float a, b, gdt;
@@ -138,11 +147,7 @@ __device__ __forceinline__ float2 hi2(float4 v) { return make_float2(v.z, v.w); 
 // z-face advective flux of plane k+1 to the next layer.
 template <int M, int KIND, bool LF, bool MT, bool O4, int TY>
 __global__ void __launch_bounds__(XT<M, MT, O4, TY, (KIND != 0)>::THREADS, XT<M, MT, O4, TY, (KIND != 0)>::CTAS)
-k_xfused(const __grid_constant__ CUtensorMap tmn, const __grid_constant__ CUtensorMap tmm,
-         const __grid_constant__ CUtensorMap twy, const __grid_constant__ CUtensorMap tuo,
-         const __grid_constant__ CUtensorMap tvr, const __grid_constant__ CUtensorMap tlc,
-         const __grid_constant__ CUtensorMap twy1, const __grid_constant__ CUtensorMap tuo1,
-         const __grid_constant__ CUtensorMap tvr1, const XArgs A)
+k_xfused(const __grid_constant__ XMaps T, const XArgs A)
 {
     using L = XT<M, MT, O4, TY, (KIND != 0)>;
     constexpr int kThreads = L::CONS;
@@ -180,6 +185,10 @@ k_xfused(const __grid_constant__ CUtensorMap tmn, const __grid_constant__ CUtens
     if (warp == NW) {
         if (lane != 0) return;
         const bool stopper = (A.stop_ring >= 0 && blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0);
+        // the rows and columns beyond the tile's edges, periodic in x and y
+        const int ysn = (j0 == 0) ? g.Ny - L::HN : j0 - L::HN, ysm = (j0 == 0) ? g.Ny - 1 : j0 - 1;
+        const int yn = (j0 + TY == g.Ny) ? 0 : j0 + TY;
+        const int xw = (i0 == 0) ? g.Nx - 4 : i0 - 4, xe = (i0 + kTX == g.Nx) ? 0 : i0 + kTX;
         for (int r = 0; r < nrings; ++r) {
             const int s = r % NB;
             if (stopper && r == A.stop_ring) break;  // every ring issued so far is waited for by the consumers
@@ -194,22 +203,32 @@ k_xfused(const __grid_constant__ CUtensorMap tmn, const __grid_constant__ CUtens
             mbar_expect_tx(&full[s], (DIVONLY ? 0u : L::tn_bytes + L::tm_bytes) + (wy ? L::wy_bytes : 0u) +
                                          (bundle ? L::bundle_bytes : 0u));
             if (!DIVONLY) {
-                tma_3d(slot + L::oTn, &tmn, i0 - 4, j0 - (O4 ? 2 : 1), p, &full[s]);
-                tma_3d(slot + L::oTm, &tmm, i0 - 4, j0 - 1, p, &full[s]);
+                float* sn = slot + L::oTn;
+                float* smm = slot + L::oTm;
+                tma_3d(sn, &T.tn, i0, j0, p, &full[s]);
+                tma_3d(sn + L::nYS, &T.rn, i0, ysn, p, &full[s]);
+                tma_3d(sn + L::nYN, &T.rn, i0, yn, p, &full[s]);
+                tma_3d(sn + L::nXW, &T.xn, xw, j0, p, &full[s]);
+                tma_3d(sn + L::nXE, &T.xn, xe, j0, p, &full[s]);
+                tma_3d(smm, &T.tm, i0, j0, p, &full[s]);
+                tma_3d(smm + L::mYS, &T.rm, i0, ysm, p, &full[s]);
+                tma_3d(smm + L::mYN, &T.rm, i0, yn, p, &full[s]);
+                tma_3d(smm + L::mXW, &T.xm, xw, j0, p, &full[s]);
+                tma_3d(smm + L::mXE, &T.xm, xe, j0, p, &full[s]);
             }
             if (wy) {
-                tma_3d(slot + L::oWY, &twy, I0, j0, p, &full[s]);   // WY plane p
-                if (MT) tma_3d(slot + L::oWY + L::DS, &twy1, I0, j0, p, &full[s]);
+                tma_3d(slot + L::oWY, &T.wy, I0, j0, p, &full[s]);   // WY plane p
+                if (MT) tma_3d(slot + L::oWY + L::DS, &T.wy1, I0, j0, p, &full[s]);
             }
             if (bundle) {
                 const int kb = p - 1;
-                tma_3d(slot + L::oUO, &tuo, I0, j0, kb, &full[s]);
-                tma_3d(slot + L::oVR, &tvr, I0, j0, kb, &full[s]);
+                tma_3d(slot + L::oUO, &T.uo, I0, j0, kb, &full[s]);
+                tma_3d(slot + L::oVR, &T.vr, I0, j0, kb, &full[s]);
                 if (MT) {
-                    tma_3d(slot + L::oUO + L::DS, &tuo1, I0, j0, kb, &full[s]);
-                    tma_3d(slot + L::oVR + L::DS, &tvr1, I0, j0, kb, &full[s]);
+                    tma_3d(slot + L::oUO + L::DS, &T.uo1, I0, j0, kb, &full[s]);
+                    tma_3d(slot + L::oVR + L::DS, &T.vr1, I0, j0, kb, &full[s]);
                 }
-                tma_3d(slot + L::oLC, &tlc, 0, kb, 0, &full[s]);
+                tma_3d(slot + L::oLC, &T.lc, 0, kb, 0, &full[s]);
             }
         }
         return;
@@ -222,8 +241,6 @@ k_xfused(const __grid_constant__ CUtensorMap tmn, const __grid_constant__ CUtens
     const int seg = tid & 15, jl = ((warp >> 1) << 2) + (warp & 1) + 2 * ((tid >> 4) & 1);
     const int il0 = seg * 4, cb0 = il0 / M;      // first coarse column of the segment (tile-local)
     const auto& rx = A.rx;
-    const bool wrap_w = (i0 == 0 && seg == 0), wrap_e = (i0 + kTX == g.Nx && seg == 15);
-    const bool wrap_s = (j0 == 0 && jl == 0), wrap_n = (j0 + TY == g.Ny && jl == TY - 1);
 
     bool fail = false;
     float dmax = 0.f;
@@ -243,8 +260,18 @@ k_xfused(const __grid_constant__ CUtensorMap tmn, const __grid_constant__ CUtens
         if (!fail && !mbar_wait(&full[r], 0, A.wait_ns)) fail = true;
     const size_t plane = (size_t)g.Nx * g.Ny;
     float* outp = A.Tp1 + (size_t)k0 * plane + (size_t)(j0 + jl) * g.Nx + i0 + il0;
-    const int o = (jl + 1) * kBX + il0 + 4;          // this segment's first cell in a plane box
-    const int o4 = (jl + 2) * kBX + il0 + 4;         // the same in the O4 T^s box (two halo rows)
+    // offsets in a scalar level of a ring slot: the segment's first cell (both
+    // levels), rows jl - 1 and jl + 1 of T^s (n) and T^{s-1} (m), rows jl - 2 and
+    // jl + 2 of T^s (O4), the west and east neighbours of the row
+    const int om = jl * kTX + il0;
+    const int osn = jl >= 1 ? om - kTX : L::nYS + (L::HN - 1) * kTX + il0;
+    const int onn = jl + 1 < TY ? om + kTX : L::nYN + il0;
+    const int osn2 = jl >= 2 ? om - 2 * kTX : L::nYS + jl * kTX + il0;
+    const int onn2 = jl + 2 < TY ? om + 2 * kTX : L::nYN + (jl + 2 - TY) * kTX + il0;
+    const int osm = jl >= 1 ? om - kTX : L::mYS + il0;
+    const int onm = jl + 1 < TY ? om + kTX : L::mYN + il0;
+    const int oxwn = L::nXW + jl * 4 + 3, oxen = L::nXE + jl * 4;
+    const int oxwm = L::mXW + jl * 4 + 3, oxem = L::mXE + jl * 4;
 
     float wcar[4] = {0.f, 0.f, 0.f, 0.f};            // R_x split of W on plane k (from layer k-1)
     float2 fcar[2] = {};                             // O4: advective flux W T_f through face k (from layer k-1)
@@ -342,48 +369,25 @@ k_xfused(const __grid_constant__ CUtensorMap tmn, const __grid_constant__ CUtens
                 const float* Pn_t = sm + st * L::slot + L::oTn;
                 const float* Pm_t = sm + st * L::slot + L::oTm;
                 const float* Pn_2 = sm + s2 * L::slot + L::oTn;
-                const float4 tc4 = *reinterpret_cast<const float4*>(Pn_c + o4);
-                float4 ts4 = *reinterpret_cast<const float4*>(Pn_c + o4 - kBX);
-                float4 tn4 = *reinterpret_cast<const float4*>(Pn_c + o4 + kBX);
-                float4 ts24 = *reinterpret_cast<const float4*>(Pn_c + o4 - 2 * kBX);
-                float4 tn24 = *reinterpret_cast<const float4*>(Pn_c + o4 + 2 * kBX);
-                const float4 dc4 = *reinterpret_cast<const float4*>(Pm_c + o);
-                float4 ds4 = *reinterpret_cast<const float4*>(Pm_c + o - kBX);
-                float4 dn4 = *reinterpret_cast<const float4*>(Pm_c + o + kBX);
+                const float4 tc4 = *reinterpret_cast<const float4*>(Pn_c + om);
+                const float4 ts4 = *reinterpret_cast<const float4*>(Pn_c + osn);
+                const float4 tn4 = *reinterpret_cast<const float4*>(Pn_c + onn);
+                const float4 ts24 = *reinterpret_cast<const float4*>(Pn_c + osn2);
+                const float4 tn24 = *reinterpret_cast<const float4*>(Pn_c + onn2);
+                const float4 dc4 = *reinterpret_cast<const float4*>(Pm_c + om);
+                const float4 ds4 = *reinterpret_cast<const float4*>(Pm_c + osm);
+                const float4 dn4 = *reinterpret_cast<const float4*>(Pm_c + onm);
                 // in-row neighbours: two of T^s, one of T^{s-1} on each side
                 float tw1 = __shfl_up_sync(0xffffffffu, tc4.w, 1), tw2 = __shfl_up_sync(0xffffffffu, tc4.z, 1);
                 float te1 = __shfl_down_sync(0xffffffffu, tc4.x, 1), te2 = __shfl_down_sync(0xffffffffu, tc4.y, 1);
                 float dw = __shfl_up_sync(0xffffffffu, dc4.w, 1), de = __shfl_down_sync(0xffffffffu, dc4.x, 1);
-                if (seg == 0) { tw1 = Pn_c[o4 - 1]; tw2 = Pn_c[o4 - 2]; dw = Pm_c[o - 1]; }
-                if (seg == 15) { te1 = Pn_c[o4 + 4]; te2 = Pn_c[o4 + 5]; de = Pm_c[o + 4]; }
-                const bool ws2 = (j0 == 0 && jl < 2), wn2 = (j0 + TY == g.Ny && jl >= TY - 2);
-                if (wrap_w | wrap_e | ws2 | wn2) {
-                    // the box holds zeros beyond the domain: fetch the periodic images
-                    const float* gn = A.Tn + (size_t)k * plane;
-                    const float* gm = A.Tm + (size_t)k * plane;
-                    const size_t row = (size_t)(j0 + jl) * g.Nx, col = (size_t)(i0 + il0);
-                    if (wrap_w) { tw1 = gn[row + g.Nx - 1]; tw2 = gn[row + g.Nx - 2]; dw = gm[row + g.Nx - 1]; }
-                    if (wrap_e) { te1 = gn[row]; te2 = gn[row + 1]; de = gm[row]; }
-                    if (ws2) {                    // rows jl-1 (jl = 0) and jl-2 below row 0
-                        if (jl == 0) {
-                            ts4 = *reinterpret_cast<const float4*>(gn + (size_t)(g.Ny - 1) * g.Nx + col);
-                            ds4 = *reinterpret_cast<const float4*>(gm + (size_t)(g.Ny - 1) * g.Nx + col);
-                        }
-                        ts24 = *reinterpret_cast<const float4*>(gn + (size_t)(g.Ny - 2 + jl) * g.Nx + col);
-                    }
-                    if (wn2) {                    // rows jl+1 (jl = TY-1) and jl+2 above row Ny-1
-                        if (jl == TY - 1) {
-                            tn4 = *reinterpret_cast<const float4*>(gn + col);
-                            dn4 = *reinterpret_cast<const float4*>(gm + col);
-                        }
-                        tn24 = *reinterpret_cast<const float4*>(gn + (size_t)(jl - (TY - 2)) * g.Nx + col);
-                    }
-                }
-                const float4 db4 = *reinterpret_cast<const float4*>(Pm_b + o);
-                const float4 dt4 = *reinterpret_cast<const float4*>(Pm_t + o);
-                const float4 tb4 = *reinterpret_cast<const float4*>(Pn_b + o4);
-                const float4 tt4 = *reinterpret_cast<const float4*>(Pn_t + o4);
-                const float4 t24 = *reinterpret_cast<const float4*>(Pn_2 + o4);
+                if (seg == 0) { tw1 = Pn_c[oxwn]; tw2 = Pn_c[oxwn - 1]; dw = Pm_c[oxwm]; }
+                if (seg == 15) { te1 = Pn_c[oxen]; te2 = Pn_c[oxen + 1]; de = Pm_c[oxem]; }
+                const float4 db4 = *reinterpret_cast<const float4*>(Pm_b + om);
+                const float4 dt4 = *reinterpret_cast<const float4*>(Pm_t + om);
+                const float4 tb4 = *reinterpret_cast<const float4*>(Pn_b + om);
+                const float4 tt4 = *reinterpret_cast<const float4*>(Pn_t + om);
+                const float4 t24 = *reinterpret_cast<const float4*>(Pn_2 + om);
                 const float t8[8] = {tw2, tw1, tc4.x, tc4.y, tc4.z, tc4.w, te1, te2};
                 const float dcv[6] = {dw, dc4.x, dc4.y, dc4.z, dc4.w, de};
                 const auto& wx = A.w4x;
@@ -401,7 +405,7 @@ k_xfused(const __grid_constant__ CUtensorMap tmn, const __grid_constant__ CUtens
                 if (k == k0) {
                     // the chunk's first layer: face k from planes k-2 .. k+1
                     const float* Pn_m2 = sm + sm2 * L::slot + L::oTn;
-                    const float4 tm4 = *reinterpret_cast<const float4*>(Pn_m2 + o4);
+                    const float4 tm4 = *reinterpret_cast<const float4*>(Pn_m2 + om);
                     const float4 zb = *reinterpret_cast<const float4*>(bun + L::oLC + 4);
                     const float tmv[4] = {tm4.x, tm4.y, tm4.z, tm4.w}, tbv[4] = {tb4.x, tb4.y, tb4.z, tb4.w};
                     const float ttv[4] = {tt4.x, tt4.y, tt4.z, tt4.w};
@@ -455,40 +459,23 @@ k_xfused(const __grid_constant__ CUtensorMap tmn, const __grid_constant__ CUtens
                 const float* Pm_c = sm + sc * L::slot + L::oTm;
                 const float* Pn_t = sm + st * L::slot + L::oTn;
                 const float* Pm_t = sm + st * L::slot + L::oTm;
-                const float4 tc4 = *reinterpret_cast<const float4*>(Pn_c + o);
-                float4 ts4 = *reinterpret_cast<const float4*>(Pn_c + o - kBX);
-                float4 tn4 = *reinterpret_cast<const float4*>(Pn_c + o + kBX);
-                const float4 dc4 = *reinterpret_cast<const float4*>(Pm_c + o);
-                float4 ds4 = *reinterpret_cast<const float4*>(Pm_c + o - kBX);
-                float4 dn4 = *reinterpret_cast<const float4*>(Pm_c + o + kBX);
+                const float4 tc4 = *reinterpret_cast<const float4*>(Pn_c + om);
+                const float4 ts4 = *reinterpret_cast<const float4*>(Pn_c + osn);
+                const float4 tn4 = *reinterpret_cast<const float4*>(Pn_c + onn);
+                const float4 dc4 = *reinterpret_cast<const float4*>(Pm_c + om);
+                const float4 ds4 = *reinterpret_cast<const float4*>(Pm_c + osm);
+                const float4 dn4 = *reinterpret_cast<const float4*>(Pm_c + onm);
                 // in-row neighbours from the adjacent segments (16 lanes per row)
                 float tw = __shfl_up_sync(0xffffffffu, tc4.w, 1), te = __shfl_down_sync(0xffffffffu, tc4.x, 1);
                 float dw = __shfl_up_sync(0xffffffffu, dc4.w, 1), de = __shfl_down_sync(0xffffffffu, dc4.x, 1);
-                if (seg == 0) { tw = Pn_c[o - 1]; dw = Pm_c[o - 1]; }
-                if (seg == 15) { te = Pn_c[o + 4]; de = Pm_c[o + 4]; }
-                if (wrap_w | wrap_e | wrap_s | wrap_n) {
-                    // the box holds zeros beyond the domain: fetch the periodic images
-                    const float* gn = A.Tn + (size_t)k * plane;
-                    const float* gm = A.Tm + (size_t)k * plane;
-                    const size_t row = (size_t)(j0 + jl) * g.Nx;
-                    if (wrap_w) { tw = gn[row + g.Nx - 1]; dw = gm[row + g.Nx - 1]; }
-                    if (wrap_e) { te = gn[row]; de = gm[row]; }
-                    if (wrap_s) {
-                        const size_t r2 = (size_t)(g.Ny - 1) * g.Nx + i0 + il0;
-                        ts4 = *reinterpret_cast<const float4*>(gn + r2);
-                        ds4 = *reinterpret_cast<const float4*>(gm + r2);
-                    }
-                    if (wrap_n) {
-                        tn4 = *reinterpret_cast<const float4*>(gn + i0 + il0);
-                        dn4 = *reinterpret_cast<const float4*>(gm + i0 + il0);
-                    }
-                }
+                if (seg == 0) { tw = Pn_c[oxwn]; dw = Pm_c[oxwm]; }
+                if (seg == 15) { te = Pn_c[oxen]; de = Pm_c[oxem]; }
                 // planes below / above: zero-filled beyond the plates, where the plate
                 // W is exactly zero and the plate value enters D through `plate`
-                const float4 tb4 = *reinterpret_cast<const float4*>(Pn_b + o);
-                const float4 db4 = *reinterpret_cast<const float4*>(Pm_b + o);
-                const float4 tt4 = *reinterpret_cast<const float4*>(Pn_t + o);
-                const float4 dt4 = *reinterpret_cast<const float4*>(Pm_t + o);
+                const float4 tb4 = *reinterpret_cast<const float4*>(Pn_b + om);
+                const float4 db4 = *reinterpret_cast<const float4*>(Pm_b + om);
+                const float4 tt4 = *reinterpret_cast<const float4*>(Pn_t + om);
+                const float4 dt4 = *reinterpret_cast<const float4*>(Pm_t + om);
                 const float tcv[6] = {tw, tc4.x, tc4.y, tc4.z, tc4.w, te};
                 const float dcv[6] = {dw, dc4.x, dc4.y, dc4.z, dc4.w, de};
                 // x fluxes in scalar form (adjacent cells share a face), then the rest
@@ -826,7 +813,8 @@ bool map3(CUtensorMap* m, const float* base, int d0, int d1, int d2, int b0, int
 bool cached_map3(CUtensorMap* out, const float* base, int d0, int d1, int d2, int b0, int b1, int b2)
 {
     struct Entry { const float* p; int d[6]; CUtensorMap m; };
-    static Entry cache[32];
+    constexpr int kCache = 128;
+    static Entry cache[kCache];
     static int n = 0, next = 0;
     static std::mutex mu;
     std::lock_guard<std::mutex> lock(mu);
@@ -837,7 +825,7 @@ bool cached_map3(CUtensorMap* out, const float* base, int d0, int d1, int d2, in
             return true;
         }
     if (!map3(out, base, d0, d1, d2, b0, b1, b2)) return false;
-    Entry& e = cache[n < 32 ? n++ : (next = (next + 1) % 32)];
+    Entry& e = cache[n < kCache ? n++ : (next = (next + 1) % kCache)];
     e.p = base;
     memcpy(e.d, key, sizeof key);
     e.m = *out;
@@ -860,22 +848,22 @@ cudaError_t launch_xt(const Grid<float>& g, XSet v0, XSet v1, float alpha, int n
     constexpr bool DIVONLY = KIND != 0;
     cudaError_t e = smem_optin(reinterpret_cast<const void*>(k_xfused<M, KIND, LF, MT, O4, TY>), (int)L::bytes, &attr);
     if (e != cudaSuccess) return e;
-    CUtensorMap mn, mm, mwy, muo, mvr, mlc, mwy1, muo1, mvr1;
-    memset(&mn, 0, sizeof mn);
-    memset(&mm, 0, sizeof mm);
-    memset(&mwy1, 0, sizeof mwy1);
-    memset(&muo1, 0, sizeof muo1);
-    memset(&mvr1, 0, sizeof mvr1);
-    if (!DIVONLY && (!cached_map3(&mn, T, g.Nx, g.Ny, g.Nz, kBX, L::BYN, 1) ||
-                     !cached_map3(&mm, Tm1, g.Nx, g.Ny, g.Nz, kBX, L::kBY, 1)))
+    XMaps maps;
+    memset(&maps, 0, sizeof maps);
+    if (!DIVONLY && (!cached_map3(&maps.tn, T, g.Nx, g.Ny, g.Nz, kTX, TY, 1) ||
+                     !cached_map3(&maps.rn, T, g.Nx, g.Ny, g.Nz, kTX, L::HN, 1) ||
+                     !cached_map3(&maps.xn, T, g.Nx, g.Ny, g.Nz, 4, TY, 1) ||
+                     !cached_map3(&maps.tm, Tm1, g.Nx, g.Ny, g.Nz, kTX, TY, 1) ||
+                     !cached_map3(&maps.rm, Tm1, g.Nx, g.Ny, g.Nz, kTX, 1, 1) ||
+                     !cached_map3(&maps.xm, Tm1, g.Nx, g.Ny, g.Nz, 4, TY, 1)))
         return cudaErrorInvalidValue;
     auto set_maps = [&](const XSet& v, CUtensorMap* wy, CUtensorMap* uo, CUtensorMap* vr) {
         return cached_map3(wy, v.wy, nxg, g.Ny, g.Nz + 1, L::BXC, TY, 1) &&
                cached_map3(uo, v.uo, nxg, g.Ny, g.Nz, L::BXC, TY, 1) &&
                cached_map3(vr, v.vr, nxg, g.Ny + 1, g.Nz, L::BXC, TY + 1, 1);
     };
-    if (!set_maps(v0, &mwy, &muo, &mvr) || (MT && !set_maps(v1, &mwy1, &muo1, &mvr1)) ||
-        !cached_map3(&mlc, lc, lcw, g.Nz, 1, L::LCW, 1, 1))
+    if (!set_maps(v0, &maps.wy, &maps.uo, &maps.vr) || (MT && !set_maps(v1, &maps.wy1, &maps.uo1, &maps.vr1)) ||
+        !cached_map3(&maps.lc, lc, lcw, g.Nz, 1, L::LCW, 1, 1))
         return cudaErrorInvalidValue;
     const int tiles = (g.Nx / kTX) * (g.Ny / TY);
     // ~20 waves of resident CTAs, but no chunk longer than 96 layers: on large
@@ -888,7 +876,7 @@ cudaError_t launch_xt(const Grid<float>& g, XSet v0, XSet v1, float alpha, int n
     nch = max(1, min(nch, g.Nz / 4));
     const int kcl = min((g.Nz + nch - 1) / nch, 96);
     const int chunks = (g.Nz + kcl - 1) / kcl;
-    XArgs A{g, T, Tm1, Tp1, lc, (float)c.a, (float)c.b, (float)c.gdt, kcl, err, divmax, {}, alpha, {}, {},
+    XArgs A{g, Tp1, lc, (float)c.a, (float)c.b, (float)c.gdt, kcl, err, divmax, {}, alpha, {}, {},
             ptx::kWaitNs, -1};
     if (KIND == 0) take_wait_injection(&A.stop_ring, &A.wait_ns);
     memcpy(A.rx, rx12, sizeof A.rx);
@@ -897,7 +885,7 @@ cudaError_t launch_xt(const Grid<float>& g, XSet v0, XSet v1, float alpha, int n
         memcpy(A.w4y, w4 + 4, sizeof A.w4y);
     }
     dim3 grid(chunks, g.Nx / kTX, g.Ny / TY);
-    k_xfused<M, KIND, LF, MT, O4, TY><<<grid, L::THREADS, L::bytes, st>>>(mn, mm, mwy, muo, mvr, mlc, mwy1, muo1, mvr1, A);
+    k_xfused<M, KIND, LF, MT, O4, TY><<<grid, L::THREADS, L::bytes, st>>>(maps, A);
     return cudaGetLastError();
 }
 
