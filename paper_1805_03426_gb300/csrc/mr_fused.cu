@@ -70,7 +70,7 @@ __host__ __device__ constexpr int up32(int n) { return (n + 31) / 32 * 32; }
 // SM): at launch, and after the split between the consumer warpgroup and the
 // producer / builder warpgroup (128 kRegCons + 128 kRegOther = 256 kRegLaunch).
 #ifndef MR_FUSED_REG_CONS
-#define MR_FUSED_REG_CONS 168     // compile-time override for tuning sweeps
+#define MR_FUSED_REG_CONS 184     // compile-time override for tuning sweeps
 #endif
 constexpr int kRegLaunch = 128, kRegCons = MR_FUSED_REG_CONS, kRegOther = 2 * kRegLaunch - kRegCons;
 static_assert(kRegCons + kRegOther == 2 * kRegLaunch, "register split exceeds the launch");
@@ -116,7 +116,9 @@ struct FL {
     // V [3][NVR][BXC] (rows J0-1 .. J0+CY+1), W [2][NUR][BXC] (planes K, K+1)
     static constexpr int NUR = CY + 2, NVR = CY + 3;
     static constexpr int cU = 0, cV = up32(3 * NUR * BXC), cW = cV + up32(3 * NVR * BXC);
-    static constexpr int CBOX = cW + up32(2 * NUR * BXC);
+    // then the slab's constants (fused_slab_constants)
+    static constexpr int cSC = cW + up32(2 * NUR * BXC);
+    static constexpr int CBOX = cSC + kSCW;
     static constexpr uint32_t cu_bytes = 3 * NUR * BXC * 4, cv_bytes = 3 * NVR * BXC * 4,
                               cw_bytes = 2 * NUR * BXC * 4;
     static constexpr int oCoarse = oSlab + 2 * SLAB;
@@ -131,15 +133,14 @@ struct FL {
 // Tensor maps of the step: per scalar level (n: T^s, m: T^{s-1}) the tile's
 // rows (64 x TY boxes), single rows (64 x 1), four columns (4 x TY), and single
 // rows of the arrays holding the rows south of row 0 (s) and north of row Ny-1
-// (h); then the layer constants and the padded coarse faces.
+// (h); then the layer constants, the padded coarse faces and the slab constants.
 struct FLMaps {
-    CUtensorMap tn, tm, rn, rm, xn, xm, sn, smp, hn, hm, lc, cu, cv, cw;
+    CUtensorMap tn, tm, rn, rm, xn, xm, sn, smp, hn, hm, lc, cu, cv, cw, sc;
 };
 
 struct FLArgs {
     Grid<float> g;
     float* Tp1;          // T^{s+1}
-    const float* sc;     // [nz][32] slab constants (fused_slab_constants)
     float a, b, gdt;
     int kcs;             // coarse slabs per CTA chunk
     int* err;
@@ -240,8 +241,8 @@ __device__ __forceinline__ void build_vr(const float* __restrict__ cv, const flo
 // One coarse slab's refinement stages (see the file comment) from the coarse
 // buffer cb into the slab buffer sb (sz: stage-Z scratch), by NT threads
 // (this one t0) that meet at named barrier bar between the stages.  scg: the
-// slab's constants in global memory (R_z rows of its M layers, 1/(2 dz) of
-// each, the stage-Z weights Z[c][q]).
+// slab's constants, which come with its coarse faces (R_z rows of its M
+// layers, 1/(2 dz) of each, the stage-Z weights Z[c][q]).
 template <int M, int TY, int NT>
 __device__ void build_slab(const FLArgs& A, const float* __restrict__ cb, float* __restrict__ sb,
                            float* __restrict__ sz, const float* __restrict__ scg, int t0, int bar)
@@ -382,10 +383,11 @@ k_fused(const __grid_constant__ FLMaps T, const FLArgs A)
                     float* dst = sm + L::oCoarse + bb * L::CBOX;
                     const int wz0 = min(max(K - 1, 0), g.nz - 3);     // first plane of the R_z window
                     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                    mbar_expect_tx(&cfull[bb], L::cu_bytes + L::cv_bytes + L::cw_bytes);
+                    mbar_expect_tx(&cfull[bb], L::cu_bytes + L::cv_bytes + L::cw_bytes + kSCW * 4);
                     tma_3d(dst + L::cU, &T.cu, I0, J0, wz0, &cfull[bb]);
                     tma_3d(dst + L::cV, &T.cv, I0, J0, wz0, &cfull[bb]);
                     tma_3d(dst + L::cW, &T.cw, I0, J0, K, &cfull[bb]);
+                    tma_3d(dst + L::cSC, &T.sc, 0, K, 0, &cfull[bb]);
                     ++slabs_issued;
                     return true;
                 };
@@ -445,7 +447,7 @@ k_fused(const __grid_constant__ FLMaps T, const FLArgs A)
             bool fail = !mbar_wait(&cfull[0], 0, A.wait_ns);
             fail = named_or<CONS + L::NBT>(3, fail);
             if (!fail)
-                build_slab<M, TY, CONS + L::NBT>(A, sm + L::oCoarse, sm + L::oSlab, sm + L::oZ, A.sc + (size_t)K0 * kSCW,
+                build_slab<M, TY, CONS + L::NBT>(A, sm + L::oCoarse, sm + L::oSlab, sm + L::oZ, sm + L::oCoarse + L::cSC,
                                                  CONS + bt, 3);
             if (!fail) {
                 mbar_arrive(&cempty[0]);
@@ -475,7 +477,7 @@ k_fused(const __grid_constant__ FLMaps T, const FLArgs A)
                     if (use > 0) upscale(K - 2);
                 }
                 build_slab<M, TY, L::NBT>(A, sm + L::oCoarse + bb * L::CBOX, sm + L::oSlab + bb * L::SLAB, sm + L::oZ,
-                                          A.sc + (size_t)K * kSCW, bt, 2);
+                                          sm + L::oCoarse + bb * L::CBOX + L::cSC, bt, 2);
                 mbar_arrive(&cempty[bb]);
                 mbar_arrive(&built[bb]);
             }
@@ -506,7 +508,7 @@ k_fused(const __grid_constant__ FLMaps T, const FLArgs A)
             fail = !mbar_wait(&cfull[0], 0, A.wait_ns);
             fail = named_or<CONS + L::NBT>(3, fail);
             if (!fail)
-                build_slab<M, TY, CONS + L::NBT>(A, sm + L::oCoarse, sm + L::oSlab, sm + L::oZ, A.sc + (size_t)K0 * kSCW,
+                build_slab<M, TY, CONS + L::NBT>(A, sm + L::oCoarse, sm + L::oSlab, sm + L::oZ, sm + L::oCoarse + L::cSC,
                                                  tid, 3);
             for (int r = 0; r < 2; ++r)
                 if (!fail && !mbar_wait(&full[r], 0, A.wait_ns)) fail = true;
@@ -638,7 +640,7 @@ k_fused(const __grid_constant__ FLMaps T, const FLArgs A)
             fail = named_or<CONS + L::NBT>(3, fail);
             if (!fail)
                 build_slab<M, TY, CONS + L::NBT>(A, sm + L::oCoarse, sm + L::oSlab, sm + L::oZ,
-                                                 A.sc + (size_t)K0 * kSCW, tid, 3);
+                                                 sm + L::oCoarse + L::cSC, tid, 3);
             // planes k0 - 1, k0, k0 + 1 (rings 0, 1, 2; ring 2 holds the
             // constants of layer k0): the state at the chunk's first layer
             for (int r = 0; r < 3; ++r)
@@ -1034,11 +1036,12 @@ cudaError_t launch_fl(const Grid<float>& g, const FusedInputs& in, const float* 
     if (!map_fx(&maps.lc, in.lc, kLCW, g.Nz, 1, kLCW, 1, 1) ||
         !map_fx(&maps.cu, pU, px, g.ny + 2, g.nz, L::BXC, L::NUR, 3) ||
         !map_fx(&maps.cv, pV, px, g.ny + 3, g.nz, L::BXC, L::NVR, 3) ||
-        !map_fx(&maps.cw, pW, px, g.ny + 2, g.nz + 1, L::BXC, L::NUR, 2))
+        !map_fx(&maps.cw, pW, px, g.ny + 2, g.nz + 1, L::BXC, L::NUR, 2) ||
+        !map_fx(&maps.sc, in.sc, kSCW, g.nz, 1, kSCW, 1, 1))
         return cudaErrorInvalidValue;
-    // ~12 waves of resident CTAs, chunks of at most 96 dense layers
+    // ~6 waves of resident CTAs, chunks of at most 96 dense layers
 #ifndef MR_FUSED_WAVES
-#define MR_FUSED_WAVES 12                 // compile-time override for tuning sweeps
+#define MR_FUSED_WAVES 6                  // compile-time override for tuning sweeps
 #endif
     const int tiles = (g.Nx / kTX) * (g.Ny / TY);
     const int want = 152 * L::CTAS * MR_FUSED_WAVES;
@@ -1050,7 +1053,6 @@ cudaError_t launch_fl(const Grid<float>& g, const FusedInputs& in, const float* 
     memset(&A, 0, sizeof A);
     A.g = g;
     A.Tp1 = Tp1;
-    A.sc = in.sc;
     A.a = (float)c.a;
     A.b = (float)c.b;
     A.gdt = (float)c.gdt;
