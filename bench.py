@@ -5,9 +5,11 @@ z, gamma 1.5), refinement 4 -> dense 512x512x384 (100,663,296 cells), Sc = 100,
 Ra = 1e9, dt from CFL 0.3 on the refined synthetic velocity.  One step = one
 pass of the whole hot path over the grid: the divergence-free refinement of
 the coarse velocity and the finite-volume scalar update.  Default mode
-MR_VEL_XFUSED: one kernel launch per step forms the dense velocity in registers
-(x-stage of the refinement) from the z- and y-stage results kept at coarse x
-resolution, and updates the scalar; the dense velocity is never stored.
+MR_VEL_FUSED: one kernel launch per step forms the dense velocity from the
+coarse faces (every stage of the refinement in shared memory and registers)
+and updates the scalar; nothing of the refined velocity touches HBM.  The
+split-x mode (MR_VEL_XFUSED: z- and y-stage results kept at coarse x
+resolution in HBM, the x-stage in the step kernel) is timed beside it.
 
 Prints one JSON line (rank 0).  Metric: dense cell-updates per second.  Beside
 it: the roofline fraction of the dominant kernel (CUDA events, algorithmic
@@ -355,24 +357,31 @@ def run_mr(args):
             "kernel_frac_own_bytes": round(kernel_bpc * cells / per_launch / 1e9 / peak, 4),
             "traffic_over_algorithmic": round(traffic / (bytes_per_cell * cells), 3) if traffic else None}
 
-    # the fully fused mode beside the split-x one: every stage of the
-    # refinement inside the step kernel, nothing of it in HBM (the kernel
-    # moves the algorithmic bytes themselves)
-    fused = None
-    if rank == 0 and mode == mr.MR_VEL_XFUSED and not args.no_fused:
-        hf = _make(mr, w, prec, mr.MR_VEL_FUSED, dt=dt)
+    # the other fused mode beside the headline one, timed the same way: the
+    # fully fused kernel (every stage of the refinement inside the step, the
+    # method's bytes) or the split-x kernel (z- and y-stage results re-read from
+    # HBM every step: 12 (nx + 8) / (nx M) more bytes per cell)
+    beside, beside_key = None, None
+    if rank == 0 and mode in (mr.MR_VEL_FUSED, mr.MR_VEL_XFUSED) and not args.no_fused:
+        omode = mr.MR_VEL_XFUSED if mode == mr.MR_VEL_FUSED else mr.MR_VEL_FUSED
+        oname = "k_xfused" if omode == mr.MR_VEL_XFUSED else "k_fused"
+        beside_key = "split_x_mode" if omode == mr.MR_VEL_XFUSED else "fused_mode"
+        obpc = (3 * elt + 3 * elt * (w["nx"] + 8) / (w["nx"] * w["m"])) if omode == mr.MR_VEL_XFUSED else bytes_per_cell
+        hf = _make(mr, w, prec, omode, dt=dt)
         mr.mr_refine_velocity(hf, dU, dV, dW, stream=stream)
         mr.mr_set_scalar(hf, dT0, stream=stream)
         tf = _time_steps(torch, mr, hf, args.steps, args.warmup, stream)
         hf.close()
         pf = tf / args.steps
         af = bytes_per_cell * cells / pf / 1e9
-        trf = _traffic("k_fused", args.workload)
-        fused = {"value": round(cells * args.steps / tf / 1e9, 3), "unit": "Gcell-updates/s", "steps": args.steps,
-                 "ms_per_step": round(pf * 1e3, 4), "kernel": "k_fused",
-                 "roofline": {"bound": "hbm", "achieved": round(af, 1), "peak": peak, "unit": "GB/s",
-                              "frac": round(af / peak, 4), "traffic": trf, "bytes_per_cell": round(bytes_per_cell, 3),
-                              "traffic_over_algorithmic": round(trf / (bytes_per_cell * cells), 3) if trf else None}}
+        trf = _traffic(oname, args.workload)
+        beside = {"value": round(cells * args.steps / tf / 1e9, 3), "unit": "Gcell-updates/s", "steps": args.steps,
+                  "ms_per_step": round(pf * 1e3, 4), "kernel": oname,
+                  "roofline": {"bound": "hbm", "achieved": round(af, 1), "peak": peak, "unit": "GB/s",
+                               "frac": round(af / peak, 4), "traffic": trf, "bytes_per_cell": round(bytes_per_cell, 3),
+                               "kernel_bytes_per_cell": round(obpc, 3),
+                               "kernel_frac_own_bytes": round(obpc * cells / pf / 1e9 / peak, 4),
+                               "traffic_over_algorithmic": round(trf / (bytes_per_cell * cells), 3) if trf else None}}
 
     # the per-call costs around the step: statistics (the call synchronises:
     # wall clock) and plate Nu (asynchronous: stream-timed)
@@ -400,13 +409,17 @@ def run_mr(args):
 
     # the same step with the fourth-order face values of Section 2.2 (opt-in)
     face4 = None
-    if rank == 0 and not args.no_face4 and mode != mr.MR_VEL_FUSED:
-        h4 = _make(mr, w, prec, mode, dt=dt, face_order=4)
+    if rank == 0 and not args.no_face4:
+        # fourth-order faces run in the split-x mode (the fully fused kernel is
+        # second order only)
+        m4 = mr.MR_VEL_XFUSED if mode == mr.MR_VEL_FUSED else mode
+        h4 = _make(mr, w, prec, m4, dt=dt, face_order=4)
         mr.mr_refine_velocity(h4, dU, dV, dW, stream=stream)
         mr.mr_set_scalar(h4, dT0, stream=stream)
         k4 = max(20, args.steps // 5)
         t4 = _time_steps(torch, mr, h4, k4, 3, stream)
         face4 = {"value": round(cells * k4 / t4 / 1e9, 3), "unit": "Gcell-updates/s", "steps": k4,
+                 "velocity_mode": "xfused" if m4 == mr.MR_VEL_XFUSED else "stored",
                  "ms_per_step": round(t4 / k4 * 1e3, 4)}
         h4.close()
 
@@ -511,7 +524,7 @@ def run_mr(args):
             "dtype": "f32" if prec == mr.MR_F32 else "f64", "data": "synthetic",
             "config": bench_config(args, w, dt, world, args.mode),
             "roofline": roof, "precision_error": prec_err, "fp64_path": fp64, "adjoint": adj,
-            "fused_mode": fused, "temporal": temporal, "face_order4": face4,
+            beside_key or "fused_mode": beside, "temporal": temporal, "face_order4": face4,
             "per_call": aux, "e2e": e2e,
             "cpu_baseline": cpu,
             "gpu_launches": args.steps, "clocks": clk.summary(),
@@ -695,7 +708,7 @@ def main():
     ap.add_argument("--impl", default="mr", choices=["mr", "reference"])
     ap.add_argument("--workload", default="rb512_stretched_f32", choices=sorted(WORKLOADS))
     ap.add_argument("--precision", default="f32", choices=["f32", "f64"])
-    ap.add_argument("--mode", default="xfused", choices=["stored", "fused", "xfused"])
+    ap.add_argument("--mode", default="fused", choices=["stored", "fused", "xfused"])
     ap.add_argument("--cpu-budget", type=float, default=20.0)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
