@@ -4,8 +4,12 @@
 // only; per step the kernel reads the coarse faces, T^s and T^{s-1} and
 // writes T^{s+1}.
 //
-// One CTA owns a 64 x TY column of dense cells (TY = 8 or 16) and marches a
-// chunk of coarse slabs with three kinds of warps:
+// The work is cut into chunks: a run of coarse slabs of a 64 x TY column of
+// dense cells (TY = 8 or 16).  The step launches one CTA per resident slot,
+// and each CTA marches its chunks one after the other without a break in its
+// pipelines (the next chunk's coarse faces, first slab and first planes
+// arrive while the current chunk's last layers are stepped); the reductions
+// launch one CTA per chunk.  A CTA has three kinds of warps:
 //   - a producer warp streams, through TMA onto mbarriers, the two scalar
 //     planes of every dense layer with the layer's constants (a ring of NB
 //     slots), and the coarse faces of every coarse slab (two buffers: the R_z
@@ -142,7 +146,9 @@ struct FLArgs {
     Grid<float> g;
     float* Tp1;          // T^{s+1}
     float a, b, gdt;
-    int kcs;             // coarse slabs per CTA chunk
+    int kcs;             // coarse slabs per chunk
+    int nch, zch, tpx;   // chunks in all, chunks per 64 x TY column, columns in x
+    int nfull, sp, ps;   // chunks below nfull are whole; each later one is a part of ps slabs, sp per whole chunk
     int* err;
     unsigned long long* divmax;
     float rx[4][3];      // R_x rows of the 4 cells of a segment (uniform periodic x)
@@ -343,12 +349,36 @@ k_fused(const __grid_constant__ FLMaps T, const FLArgs A)
 
     const Grid<float>& g = A.g;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int i0 = blockIdx.y * kTX, j0 = blockIdx.z * TY;
-    const int I0 = i0 / M, J0 = j0 / M;
-    const int K0 = blockIdx.x * A.kcs, K1 = min(K0 + A.kcs, g.nz);
-    if (K0 >= K1) return;
-    const int k0 = K0 * M, k1 = K1 * M;
-    const int nrings = k1 - k0 + 2;              // ring r: plane k0-1+r and the constants of layer k0+r-2
+    // Chunk c: the coarse slabs K0 .. K1-1 of the 64 x TY column at (i0, j0).
+    // A CTA steps the chunks blockIdx.x, blockIdx.x + gridDim.x, ... (the
+    // step launches one CTA per resident slot, the reductions one per chunk);
+    // the chunks of a column are consecutive, so that the CTAs resident at one
+    // time cover neighbouring columns at the same heights.  Every counter of
+    // ring slots, coarse buffers and slab buffers runs on across the chunks of
+    // a CTA, so that the next chunk's coarse faces, first slab and first planes
+    // are fetched and built while the current chunk's last layers are stepped.
+    // The chunks from A.nfull on are parts of the last whole chunks, sp parts
+    // of ps slabs each (some may be empty: K0 >= K1, skipped by every warp),
+    // so that the CTAs' shares of the last round differ by one part at most.
+    struct Chunk { int K0, K1, i0, j0; };
+    auto chunk = [&](int c) {
+        int cw = c, q = -1;
+        if (c >= A.nfull) {
+            cw = A.nfull + (c - A.nfull) / A.sp;
+            q = (c - A.nfull) % A.sp;
+        }
+        const int cz = cw % A.zch, t = cw / A.zch;
+        Chunk h;
+        h.K0 = cz * A.kcs;
+        h.K1 = min(h.K0 + A.kcs, g.nz);
+        if (q >= 0) {
+            h.K0 += q * A.ps;
+            h.K1 = min(h.K0 + A.ps, h.K1);
+        }
+        h.i0 = (t % A.tpx) * kTX;
+        h.j0 = (t / A.tpx) * TY;
+        return h;
+    };
 
     if (tid == 0) {
         for (int s = 0; s < NB; ++s) {
@@ -375,89 +405,97 @@ k_fused(const __grid_constant__ FLMaps T, const FLArgs A)
         if (warp == NCW) {
             // ------------------------------------------------------------ producer warp
             if (lane == 0) {
-                const bool stopper = (A.stop_ring >= 0 && blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0);
-                // the coarse faces of slab K into buffer (K - K0) & 1
-                auto issue_coarse = [&](int K) {
-                    const int bb = (K - K0) & 1, use = (K - K0) >> 1;
-                    if (use > 0 && !mbar_wait_idle(&cempty[bb], (use - 1) & 1, A.wait_ns, kIdleNs)) return false;
-                    float* dst = sm + L::oCoarse + bb * L::CBOX;
-                    const int wz0 = min(max(K - 1, 0), g.nz - 3);     // first plane of the R_z window
-                    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                    mbar_expect_tx(&cfull[bb], L::cu_bytes + L::cv_bytes + L::cw_bytes + kSCW * 4);
-                    tma_3d(dst + L::cU, &T.cu, I0, J0, wz0, &cfull[bb]);
-                    tma_3d(dst + L::cV, &T.cv, I0, J0, wz0, &cfull[bb]);
-                    tma_3d(dst + L::cW, &T.cw, I0, J0, K, &cfull[bb]);
-                    tma_3d(dst + L::cSC, &T.sc, 0, K, 0, &cfull[bb]);
-                    ++slabs_issued;
-                    return true;
-                };
-                // the rows south / north of the tile: inside the domain from the
-                // level itself, beyond its y edges from the arrays of those rows;
-                // the columns west / east: periodic in x
-                const bool s_edge = (j0 == 0), n_edge = (j0 + TY == g.Ny);
-                const CUtensorMap* ys_n = s_edge ? &T.sn : &T.rn;
-                const CUtensorMap* ys_m = s_edge ? &T.smp : &T.rm;
-                const CUtensorMap* yn_n = n_edge ? &T.hn : &T.rn;
-                const CUtensorMap* yn_m = n_edge ? &T.hm : &T.rm;
-                const int ys_y = s_edge ? 0 : j0 - 1, yn_y = n_edge ? 0 : j0 + TY;
-                const int xw_x = (i0 == 0) ? g.Nx - 4 : i0 - 4, xe_x = (i0 + kTX == g.Nx) ? 0 : i0 + kTX;
+                const bool stopper = (A.stop_ring >= 0 && blockIdx.x == 0);
+                int R = 0;                                // rings of the CTA's earlier chunks
                 bool ok = true, stopped = stopper && A.stop_ring == 0;
-                if (!stopped) {
+                for (int c = blockIdx.x; ok && !stopped && c < A.nch; c += gridDim.x) {
+                    const Chunk h = chunk(c);
+                    if (h.K0 >= h.K1) continue;
+                    const int K0 = h.K0, K1 = h.K1, i0 = h.i0, j0 = h.j0, I0 = i0 / M, J0 = j0 / M;
+                    const int k0 = K0 * M, k1 = K1 * M;
+                    const int nrings = k1 - k0 + 2;      // ring R + r: plane k0-1+r and the constants of layer k0+r-2
+                    // the coarse faces of slab K into buffer S & 1, S counting the
+                    // slabs of every chunk of the CTA
+                    auto issue_coarse = [&](int K) {
+                        const int S = slabs_issued, bb = S & 1, use = S >> 1;
+                        if (use > 0 && !mbar_wait_idle(&cempty[bb], (use - 1) & 1, A.wait_ns, kIdleNs)) return false;
+                        float* dst = sm + L::oCoarse + bb * L::CBOX;
+                        const int wz0 = min(max(K - 1, 0), g.nz - 3);     // first plane of the R_z window
+                        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                        mbar_expect_tx(&cfull[bb], L::cu_bytes + L::cv_bytes + L::cw_bytes + kSCW * 4);
+                        tma_3d(dst + L::cU, &T.cu, I0, J0, wz0, &cfull[bb]);
+                        tma_3d(dst + L::cV, &T.cv, I0, J0, wz0, &cfull[bb]);
+                        tma_3d(dst + L::cW, &T.cw, I0, J0, K, &cfull[bb]);
+                        tma_3d(dst + L::cSC, &T.sc, 0, K, 0, &cfull[bb]);
+                        ++slabs_issued;
+                        return true;
+                    };
+                    // the rows south / north of the tile: inside the domain from the
+                    // level itself, beyond its y edges from the arrays of those rows;
+                    // the columns west / east: periodic in x
+                    const bool s_edge = (j0 == 0), n_edge = (j0 + TY == g.Ny);
+                    const CUtensorMap* ys_n = s_edge ? &T.sn : &T.rn;
+                    const CUtensorMap* ys_m = s_edge ? &T.smp : &T.rm;
+                    const CUtensorMap* yn_n = n_edge ? &T.hn : &T.rn;
+                    const CUtensorMap* yn_m = n_edge ? &T.hm : &T.rm;
+                    const int ys_y = s_edge ? 0 : j0 - 1, yn_y = n_edge ? 0 : j0 + TY;
+                    const int xw_x = (i0 == 0) ? g.Nx - 4 : i0 - 4, xe_x = (i0 + kTX == g.Nx) ? 0 : i0 + kTX;
                     ok = issue_coarse(K0);
                     if (ok && K0 + 1 < K1) ok = issue_coarse(K0 + 1);
-                }
-                for (int r = 0; ok && !stopped && r < nrings; ++r) {
-                    const int s = r % NB;
-                    if (stopper && r == A.stop_ring) break;    // every copy issued so far is waited for
-                    if (r >= NB && !mbar_wait_idle(&empty[s], ((r / NB) - 1) & 1, A.wait_ns, kIdleNs)) {
-                        ok = false;
-                        break;
+                    for (int r = 0; ok && r < nrings; ++r) {
+                        const int G = R + r, s = G % NB;  // the CTA's ring G: slot G % NB, phase G / NB
+                        if (stopper && G == A.stop_ring) {   // every copy issued so far is waited for
+                            stopped = true;
+                            break;
+                        }
+                        if (G >= NB && !mbar_wait_idle(&empty[s], ((G / NB) - 1) & 1, A.wait_ns, kIdleNs)) {
+                            ok = false;
+                            break;
+                        }
+                        float* slot = sm + s * L::slot;
+                        const int p = k0 - 1 + r;
+                        const bool lc = (r >= 2);
+                        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                        mbar_expect_tx(&full[s], (uint32_t)(2 * L::FW + (lc ? kLCW : 0)) * 4u);
+                        if (!DIVONLY) {
+                            // per level: the tile's rows, the rows beyond its y edges, the
+                            // columns beyond its x edges (wrapped at the domain's edges,
+                            // so that every box is in bounds in x and y)
+                            tma_3d(slot + L::oTn, &T.tn, i0, j0, p, &full[s]);
+                            tma_3d(slot + L::oTm, &T.tm, i0, j0, p, &full[s]);
+                            tma_3d(slot + L::oTn + L::fYS, ys_n, i0, ys_y, p, &full[s]);
+                            tma_3d(slot + L::oTm + L::fYS, ys_m, i0, ys_y, p, &full[s]);
+                            tma_3d(slot + L::oTn + L::fYN, yn_n, i0, yn_y, p, &full[s]);
+                            tma_3d(slot + L::oTm + L::fYN, yn_m, i0, yn_y, p, &full[s]);
+                            tma_3d(slot + L::oTn + L::fXW, &T.xn, xw_x, j0, p, &full[s]);
+                            tma_3d(slot + L::oTm + L::fXW, &T.xm, xw_x, j0, p, &full[s]);
+                            tma_3d(slot + L::oTn + L::fXE, &T.xn, xe_x, j0, p, &full[s]);
+                            tma_3d(slot + L::oTm + L::fXE, &T.xm, xe_x, j0, p, &full[s]);
+                        }
+                        if (lc) tma_3d(slot + L::oLC, &T.lc, 0, p - 1, 0, &full[s]);
+                        rings_issued = G + 1;
+                        // the first plane of slab K (K > K0) goes out with the coarse faces of slab K + 1
+                        if (p > k0 && p < k1 && (p - k0) % M == 0 && p / M + 1 < K1) ok = issue_coarse(p / M + 1);
                     }
-                    float* slot = sm + s * L::slot;
-                    const int p = k0 - 1 + r;
-                    const bool lc = (r >= 2);
-                    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                    mbar_expect_tx(&full[s], (uint32_t)(2 * L::FW + (lc ? kLCW : 0)) * 4u);
-                    if (!DIVONLY) {
-                        // per level: the tile's rows, the rows beyond its y edges, the
-                        // columns beyond its x edges (wrapped at the domain's edges,
-                        // so that every box is in bounds in x and y)
-                        tma_3d(slot + L::oTn, &T.tn, i0, j0, p, &full[s]);
-                        tma_3d(slot + L::oTm, &T.tm, i0, j0, p, &full[s]);
-                        tma_3d(slot + L::oTn + L::fYS, ys_n, i0, ys_y, p, &full[s]);
-                        tma_3d(slot + L::oTm + L::fYS, ys_m, i0, ys_y, p, &full[s]);
-                        tma_3d(slot + L::oTn + L::fYN, yn_n, i0, yn_y, p, &full[s]);
-                        tma_3d(slot + L::oTm + L::fYN, yn_m, i0, yn_y, p, &full[s]);
-                        tma_3d(slot + L::oTn + L::fXW, &T.xn, xw_x, j0, p, &full[s]);
-                        tma_3d(slot + L::oTm + L::fXW, &T.xm, xw_x, j0, p, &full[s]);
-                        tma_3d(slot + L::oTn + L::fXE, &T.xn, xe_x, j0, p, &full[s]);
-                        tma_3d(slot + L::oTm + L::fXE, &T.xm, xe_x, j0, p, &full[s]);
-                    }
-                    if (lc) tma_3d(slot + L::oLC, &T.lc, 0, p - 1, 0, &full[s]);
-                    rings_issued = r + 1;
-                    // the first plane of slab K (K > K0) goes out with the coarse faces of slab K + 1
-                    if (p > k0 && p < k1 && (p - k0) % M == 0 && p / M + 1 < K1) ok = issue_coarse(p / M + 1);
+                    R += nrings;
                 }
                 if (!ok) *s_fail = 1;
             }
         } else {
             // ------------------------------------------------------------ builder warps
             const int bt = tid - CONS - 32;              // 0 .. NBT-1
-            // the chunk's first slab, with the consumers
-            bool fail = !mbar_wait(&cfull[0], 0, A.wait_ns);
-            fail = named_or<CONS + L::NBT>(3, fail);
-            if (!fail)
-                build_slab<M, TY, CONS + L::NBT>(A, sm + L::oCoarse, sm + L::oSlab, sm + L::oZ, sm + L::oCoarse + L::cSC,
-                                                 CONS + bt, 3);
-            if (!fail) {
-                mbar_arrive(&cempty[0]);
-                mbar_arrive(&built[0]);
-            }
-            // TC: the coarse cells of a freed slab K (sums over its M dense rows, in
+            bool fail = false;
+            int S = 0;                                   // slabs of the CTA built so far (every chunk)
+            // TC: coarse slab and chunk of the slabs in buffers 0 and 1
+            int hK0 = 0, hc0 = 0, hK1 = 0, hc1 = 0;
+            // TC: the coarse cells of a freed slab Sx (sums over its M dense rows, in
             // the rows' order, in FP32; the scaling in FP64)
-            auto upscale = [&](int K) {
+            auto upscale = [&](int Sx) {
                 constexpr int CX = L::CX, CY = L::CY;
-                const float* tb = sm + L::oTcb + ((K - K0) & 1) * TY * CX;
+                const int bb = Sx & 1, K = bb ? hK1 : hK0;
+                const Chunk h = chunk(bb ? hc1 : hc0);
+                const int I0 = h.i0 / M, J0 = h.j0 / M;
+                const float* tb = sm + L::oTcb + bb * TY * CX;
                 const double inv = A.tcinv[K];
                 for (int t = bt; t < CY * CX; t += L::NBT) {
                     const int Jc = t / CX, I = t - Jc * CX;
@@ -467,26 +505,46 @@ k_fused(const __grid_constant__ FLMaps T, const FLArgs A)
                     A.Tc[((size_t)K * g.ny + J0 + Jc) * g.nx + I0 + I] = (double)v * inv;
                 }
             };
-            for (int K = K0 + 1; K < K1 && !fail; ++K) {
-                const int bb = (K - K0) & 1, use = (K - K0) >> 1;
-                bool f = !mbar_wait_idle(&cfull[bb], use & 1, A.wait_ns, kIdleNs);
-                if (!f && use > 0) f = !mbar_wait_idle(&freed[bb], (use - 1) & 1, A.wait_ns, kIdleNs);
-                fail = named_or<L::NBT>(2, f);
-                if (fail) break;
-                if constexpr (TC) {
-                    if (use > 0) upscale(K - 2);
+            for (int c = blockIdx.x; !fail && c < A.nch; c += gridDim.x) {
+                const Chunk h = chunk(c);
+                for (int K = h.K0; K < h.K1; ++K, ++S) {
+                    const int bb = S & 1, use = S >> 1;
+                    if (S == 0) {
+                        // the CTA's first slab, with the consumers
+                        fail = !mbar_wait(&cfull[0], 0, A.wait_ns);
+                        fail = named_or<CONS + L::NBT>(3, fail);
+                        if (!fail)
+                            build_slab<M, TY, CONS + L::NBT>(A, sm + L::oCoarse, sm + L::oSlab, sm + L::oZ,
+                                                             sm + L::oCoarse + L::cSC, CONS + bt, 3);
+                    } else {
+                        bool f = !mbar_wait_idle(&cfull[bb], use & 1, A.wait_ns, kIdleNs);
+                        if (!f && use > 0) f = !mbar_wait_idle(&freed[bb], (use - 1) & 1, A.wait_ns, kIdleNs);
+                        fail = named_or<L::NBT>(2, f);
+                        if (!fail) {
+                            if constexpr (TC) {
+                                if (use > 0) upscale(S - 2);
+                            }
+                            build_slab<M, TY, L::NBT>(A, sm + L::oCoarse + bb * L::CBOX, sm + L::oSlab + bb * L::SLAB,
+                                                      sm + L::oZ, sm + L::oCoarse + bb * L::CBOX + L::cSC, bt, 2);
+                        }
+                    }
+                    if (fail) break;
+                    mbar_arrive(&cempty[bb]);
+                    mbar_arrive(&built[bb]);
+                    if (bb) {
+                        hK1 = K;
+                        hc1 = c;
+                    } else {
+                        hK0 = K;
+                        hc0 = c;
+                    }
                 }
-                build_slab<M, TY, L::NBT>(A, sm + L::oCoarse + bb * L::CBOX, sm + L::oSlab + bb * L::SLAB, sm + L::oZ,
-                                          sm + L::oCoarse + bb * L::CBOX + L::cSC, bt, 2);
-                mbar_arrive(&cempty[bb]);
-                mbar_arrive(&built[bb]);
             }
             if constexpr (TC) {
-                // the chunk's last two slabs, once the consumers have freed them
-                for (int K = max(K0, K1 - 2); K < K1 && !fail; ++K) {
-                    const int bb = (K - K0) & 1, use = (K - K0) >> 1;
-                    fail = named_or<L::NBT>(2, !mbar_wait_idle(&freed[bb], use & 1, A.wait_ns, kIdleNs));
-                    if (!fail) upscale(K);
+                // the last two slabs, once the consumers have freed them
+                for (int Sx = max(0, S - 2); Sx < S && !fail; ++Sx) {
+                    fail = named_or<L::NBT>(2, !mbar_wait_idle(&freed[Sx & 1], (Sx >> 1) & 1, A.wait_ns, kIdleNs));
+                    if (!fail) upscale(Sx);
                 }
             }
             if (fail && bt == 0) *s_fail = 1;
@@ -501,6 +559,9 @@ k_fused(const __grid_constant__ FLMaps T, const FLArgs A)
             const int seg = tid & 15, jl = ((warp >> 2) << 3) + (warp & 3) + 4 * ((tid >> 4) & 1);
             const int cb0 = seg * 4 / M;                 // first coarse column of the segment (tile-local)
             const auto& rx = A.rx;
+            // one chunk per CTA (the reductions launch one CTA per chunk)
+            const Chunk h = chunk(blockIdx.x);
+            const int k0 = h.K0 * M, k1 = h.K1 * M;
             bool fail = false;
             float dmax = 0.f;
             float wcar[4] = {0.f, 0.f, 0.f, 0.f};        // R_x split of W on plane k (from layer k-1)
@@ -618,7 +679,6 @@ k_fused(const __grid_constant__ FLMaps T, const FLArgs A)
             const float2 kx2p = make_float2(g.kx2, g.kx2), ky2p = make_float2(g.ky2, g.ky2);
             const float2 gdtp = make_float2(A.gdt, A.gdt), cap = make_float2(A.a, A.a), cbp = make_float2(A.b, A.b);
             const size_t plane = (size_t)g.Nx * g.Ny;
-            float* outp = A.Tp1 + (size_t)k0 * plane + (size_t)(j0 + jl) * g.Nx + i0 + il0;
             // offsets in a level of a ring slot: the segment's first cell of row jl
             // (row jl + 1 follows kTX floats on), of rows jl - 1 and jl + 2, and the
             // west / east neighbours of row jl (row jl + 1: 4 floats on)
@@ -626,7 +686,6 @@ k_fused(const __grid_constant__ FLMaps T, const FLArgs A)
             const int osr = (jl == 0) ? L::fYS + il0 : om - kTX;
             const int onr = (jl + 2 == TY) ? L::fYN + il0 : om + 2 * kTX;
             const int oxw = L::fXW + jl * 4 + 3, oxe = L::fXE + jl * 4;
-            float tcs[2][NC] = {};                       // upscale partials of the segment's coarse columns
             struct Carry {
                 float4 t[2], d[2];     // T^s, T^{s-1} of rows jl, jl + 1 on plane k
                 float2 ab[2][2];       // advective flux w T_f through the bottom face of layer k (pairs)
@@ -634,247 +693,268 @@ k_fused(const __grid_constant__ FLMaps T, const FLArgs A)
                 float w[2][4];         // R_x split of W on plane k
             };
             Carry S0, S1;
-            // the chunk's first slab, with the builder warps (measured faster than
-            // waiting for the builders alone)
-            fail = !mbar_wait(&cfull[0], 0, A.wait_ns);
-            fail = named_or<CONS + L::NBT>(3, fail);
-            if (!fail)
-                build_slab<M, TY, CONS + L::NBT>(A, sm + L::oCoarse, sm + L::oSlab, sm + L::oZ,
-                                                 sm + L::oCoarse + L::cSC, tid, 3);
-            // planes k0 - 1, k0, k0 + 1 (rings 0, 1, 2; ring 2 holds the
-            // constants of layer k0): the state at the chunk's first layer
-            for (int r = 0; r < 3; ++r)
-                if (!fail && !mbar_wait(&full[r], 0, A.wait_ns)) fail = true;
-            if (!fail) {
-                const float* lc0 = sm + 2 * L::slot + L::oLC;
-                const float dzk = lc0[2], bwlo = lc0[12], bwhi = lc0[14], cdn = lc0[20];
-                const float* yb = sm + L::oSlab + L::bWY + jl * SXC + cb0;          // plane k0 (slab 0, i = 0)
-#pragma unroll
-                for (int r = 0; r < 2; ++r) {
-                    const float4 tb = *reinterpret_cast<const float4*>(sm + L::oTn + om + r * kTX);
-                    const float4 db = *reinterpret_cast<const float4*>(sm + L::oTm + om + r * kTX);
-                    S0.t[r] = *reinterpret_cast<const float4*>(sm + L::slot + L::oTn + om + r * kTX);
-                    S0.d[r] = *reinterpret_cast<const float4*>(sm + L::slot + L::oTm + om + r * kTX);
-                    const float tbv[4] = {tb.x, tb.y, tb.z, tb.w}, tcv[4] = {S0.t[r].x, S0.t[r].y, S0.t[r].z, S0.t[r].w};
-                    const float dbv[4] = {db.x, db.y, db.z, db.w};
-                    float ab[4], pd[4];
-#pragma unroll
-                    for (int a = 0; a < 4; ++a) {
-                        const int cb = r * SXC + a / M;
-                        S0.w[r][a] = rsplit3(rx[a], yb[cb], yb[cb + 1], yb[cb + 2]);
-                        ab[a] = S0.w[r][a] * (dzk * (bwlo * tbv[a] + bwhi * tcv[a]));
-                        pd[a] = cdn * dbv[a];
-                    }
-                    S0.ab[r][0] = make_float2(ab[0], ab[1]);
-                    S0.ab[r][1] = make_float2(ab[2], ab[3]);
-                    S0.pd[r][0] = make_float2(pd[0], pd[1]);
-                    S0.pd[r][1] = make_float2(pd[2], pd[3]);
+            int R = 0, S = 0;                            // rings and slabs of the CTA's earlier chunks
+            for (int c = blockIdx.x; !fail && c < A.nch; c += gridDim.x) {
+                const Chunk h = chunk(c);
+                if (h.K0 >= h.K1) continue;
+                const int k0 = h.K0 * M, k1 = h.K1 * M, nrings = k1 - k0 + 2;
+                float* outp = A.Tp1 + (size_t)k0 * plane + (size_t)(h.j0 + jl) * g.Nx + h.i0 + il0;
+                float tcs[2][NC] = {};                       // upscale partials of the segment's coarse columns
+                if (S == 0) {
+                    // the CTA's first slab, with the builder warps (measured faster than
+                    // waiting for the builders alone)
+                    fail = !mbar_wait(&cfull[0], 0, A.wait_ns);
+                    fail = named_or<CONS + L::NBT>(3, fail);
+                    if (!fail)
+                        build_slab<M, TY, CONS + L::NBT>(A, sm + L::oCoarse, sm + L::oSlab, sm + L::oZ,
+                                                         sm + L::oCoarse + L::cSC, tid, 3);
+                } else if (!mbar_wait(&built[S & 1], (S >> 1) & 1, A.wait_ns)) {
+                    fail = true;                             // a later chunk's first slab, from the builder warps
                 }
-            }
-            mbar_arrive(&empty[0]);
-            // one layer, no waits: sc, st the ring slots of planes k, k + 1; bb the
-            // slab buffer; in the state at layer k, out the state at layer k + 1
-            auto layer = [&](const int k, const int i, const int bb, const int sc, const int st, const Carry& in,
-                             Carry& out) {
-                const float* slab = sm + L::oSlab + bb * L::SLAB;
-                const float* lcp = sm + st * L::slot + L::oLC;
-                const float hz = lcp[1];
-                float vf[3][4], us[2][5];
-                {
-                    // R_x splits of the full-width W (plane k+1, rows jl, jl+1) and V
-                    // (faces jl, jl+1, jl+2); slab column c holds coarse column I0 - 1 + c
-                    constexpr int NV = NC + 2;
-                    const float* yt = slab + L::bWY + ((i + 1) * TY + jl) * SXC + cb0;
-                    const float* rs = slab + L::bVR + (i * (TY + 1) + jl) * SXC + cb0;
-                    const float* ur = slab + L::bUO + (i * TY + jl) * SXC + cb0 + 1;   // outer face of column cb0
-                    float ytv[2][NV], vv[3][NV], urv[2][NC + 1];
-#pragma unroll
-                    for (int c = 0; c < NV; ++c) {
-                        ytv[0][c] = yt[c];
-                        ytv[1][c] = yt[SXC + c];
-                        vv[0][c] = rs[c];
-                        vv[1][c] = rs[SXC + c];
-                        vv[2][c] = rs[2 * SXC + c];
-                    }
-#pragma unroll
-                    for (int q = 0; q <= NC; ++q) {
-                        urv[0][q] = ur[q];
-                        urv[1][q] = ur[SXC + q];
-                    }
-#pragma unroll
-                    for (int a = 0; a < 4; ++a) {
-                        const int cb = a / M;
-#pragma unroll
-                        for (int r = 0; r < 2; ++r)
-                            out.w[r][a] = rsplit3(rx[a], ytv[r][cb], ytv[r][cb + 1], ytv[r][cb + 2]);
-#pragma unroll
-                        for (int f = 0; f < 3; ++f) vf[f][a] = rsplit3(rx[a], vv[f][cb], vv[f][cb + 1], vv[f][cb + 2]);
-                    }
-                    // stage X: cell balance, west to east, in units of U / (2 dx)
+                // planes k0 - 1, k0, k0 + 1 (rings R, R + 1, R + 2; ring R + 2 holds
+                // the constants of layer k0): the state at the chunk's first layer
+                const int s0 = R % NB, s1 = (R + 1) % NB, s2 = (R + 2) % NB;
+                for (int r = 0; r < 3; ++r)
+                    if (!fail && !mbar_wait(&full[(R + r) % NB], ((R + r) / NB) & 1, A.wait_ns)) fail = true;
+                if (!fail) {
+                    const float* lc0 = sm + s2 * L::slot + L::oLC;
+                    const float dzk = lc0[2], bwlo = lc0[12], bwhi = lc0[14], cdn = lc0[20];
+                    const float* yb = sm + L::oSlab + (S & 1) * L::SLAB + L::bWY + jl * SXC + cb0;   // plane k0 (i = 0)
 #pragma unroll
                     for (int r = 0; r < 2; ++r) {
+                        const float4 tb = *reinterpret_cast<const float4*>(sm + s0 * L::slot + L::oTn + om + r * kTX);
+                        const float4 db = *reinterpret_cast<const float4*>(sm + s0 * L::slot + L::oTm + om + r * kTX);
+                        S0.t[r] = *reinterpret_cast<const float4*>(sm + s1 * L::slot + L::oTn + om + r * kTX);
+                        S0.d[r] = *reinterpret_cast<const float4*>(sm + s1 * L::slot + L::oTm + om + r * kTX);
+                        const float tbv[4] = {tb.x, tb.y, tb.z, tb.w};
+                        const float tcv[4] = {S0.t[r].x, S0.t[r].y, S0.t[r].z, S0.t[r].w};
+                        const float dbv[4] = {db.x, db.y, db.z, db.w};
+                        float ab[4], pd[4];
 #pragma unroll
-                        for (int q = 0; q < NC; ++q) {
-                            float h = urv[r][q];
-                            us[r][q * M] = h;
-#pragma unroll
-                            for (int a = 0; a < M - 1; ++a) {
-                                const int m = q * M + a;
-                                h = h - (vf[r + 1][m] - vf[r][m]) - (out.w[r][m] - in.w[r][m]) * hz;
-                                us[r][m + 1] = h;
-                            }
+                        for (int a = 0; a < 4; ++a) {
+                            const int cb = r * SXC + a / M;
+                            S0.w[r][a] = rsplit3(rx[a], yb[cb], yb[cb + 1], yb[cb + 2]);
+                            ab[a] = S0.w[r][a] * (dzk * (bwlo * tbv[a] + bwhi * tcv[a]));
+                            pd[a] = cdn * dbv[a];
                         }
-                        us[r][4] = urv[r][NC];
+                        S0.ab[r][0] = make_float2(ab[0], ab[1]);
+                        S0.ab[r][1] = make_float2(ab[2], ab[3]);
+                        S0.pd[r][0] = make_float2(pd[0], pd[1]);
+                        S0.pd[r][1] = make_float2(pd[2], pd[3]);
                     }
                 }
-                const float* Pn_c = sm + sc * L::slot + L::oTn;
-                const float* Pm_c = sm + sc * L::slot + L::oTm;
-                const float* Pn_t = sm + st * L::slot + L::oTn;
-                const float* Pm_t = sm + st * L::slot + L::oTm;
+                mbar_arrive(&empty[s0]);
+                // one layer, no waits: sc, st the ring slots of planes k, k + 1; bb the
+                // slab buffer; in the state at layer k, out the state at layer k + 1
+                auto layer = [&](const int k, const int i, const int bb, const int sc, const int st, const Carry& in,
+                                 Carry& out) {
+                    const float* slab = sm + L::oSlab + bb * L::SLAB;
+                    const float* lcp = sm + st * L::slot + L::oLC;
+                    const float hz = lcp[1];
+                    float vf[3][4], us[2][5];
+                    {
+                        // R_x splits of the full-width W (plane k+1, rows jl, jl+1) and V
+                        // (faces jl, jl+1, jl+2); slab column c holds coarse column I0 - 1 + c
+                        constexpr int NV = NC + 2;
+                        const float* yt = slab + L::bWY + ((i + 1) * TY + jl) * SXC + cb0;
+                        const float* rs = slab + L::bVR + (i * (TY + 1) + jl) * SXC + cb0;
+                        const float* ur = slab + L::bUO + (i * TY + jl) * SXC + cb0 + 1;   // outer face of column cb0
+                        float ytv[2][NV], vv[3][NV], urv[2][NC + 1];
 #pragma unroll
-                for (int r = 0; r < 2; ++r) {
-                    out.t[r] = *reinterpret_cast<const float4*>(Pn_t + om + r * kTX);
-                    out.d[r] = *reinterpret_cast<const float4*>(Pm_t + om + r * kTX);
-                }
-                // rows jl - 1 and jl + 2 of plane k
-                const float4 ts4 = *reinterpret_cast<const float4*>(Pn_c + osr);
-                const float4 ds4 = *reinterpret_cast<const float4*>(Pm_c + osr);
-                const float4 tn4 = *reinterpret_cast<const float4*>(Pn_c + onr);
-                const float4 dn4 = *reinterpret_cast<const float4*>(Pm_c + onr);
-                // x neighbours: shuffles inside the tile, the slot's edge columns at its edges
-                float tw[2], te[2], dw[2], de[2];
-#pragma unroll
-                for (int r = 0; r < 2; ++r) {
-                    tw[r] = __shfl_up_sync(0xffffffffu, in.t[r].w, 1);
-                    te[r] = __shfl_down_sync(0xffffffffu, in.t[r].x, 1);
-                    dw[r] = __shfl_up_sync(0xffffffffu, in.d[r].w, 1);
-                    de[r] = __shfl_down_sync(0xffffffffu, in.d[r].x, 1);
-                    if (seg == 0) {
-                        tw[r] = Pn_c[oxw + 4 * r];
-                        dw[r] = Pm_c[oxw + 4 * r];
-                    }
-                    if (seg == 15) {
-                        te[r] = Pn_c[oxe + 4 * r];
-                        de[r] = Pm_c[oxe + 4 * r];
-                    }
-                }
-                // x fluxes in scalar form (adjacent cells share a face), then the
-                // rest on the pairs (0, 1), (2, 3) with the pair constants of the layer:
-                // D = kx2 (dw + de) + ky2 (ds + dn) + cdn db + cup dt - diag dc + plate,
-                // the z advective terms as (w T_f)(bottom) - (w T_f)(top) over dz; the
-                // planes beyond the plates are zero-filled, where W is zero and the plate
-                // value enters D through `plate`
-                const float4 qf = *reinterpret_cast<const float4*>(lcp + 4);    // f_lo, f_hi (top face)
-                const float4 qn = *reinterpret_cast<const float4*>(lcp + 8);    // 1/dz, cdn of layer k+1
-                const float4 q2 = *reinterpret_cast<const float4*>(lcp + 20);   // cdn, cup
-                const float4 q3 = *reinterpret_cast<const float4*>(lcp + 24);   // -diag, plate
-                float4 out4[2];
-#pragma unroll
-                for (int r = 0; r < 2; ++r) {
-                    const float4 tc4 = in.t[r], dc4 = in.d[r];
-                    const float4 tsr = r ? in.t[0] : ts4, tnr = r ? tn4 : in.t[1];
-                    const float4 dsr = r ? in.d[0] : ds4, dnr = r ? dn4 : in.d[1];
-                    const float tcv[6] = {tw[r], tc4.x, tc4.y, tc4.z, tc4.w, te[r]};
-                    const float dcv[6] = {dw[r], dc4.x, dc4.y, dc4.z, dc4.w, de[r]};
-                    float F[5], cxv[4], sdx[4];
-#pragma unroll
-                    for (int a = 0; a < 5; ++a) F[a] = us[r][a] * (tcv[a] + tcv[a + 1]);
-#pragma unroll
-                    for (int a = 0; a < 4; ++a) {
-                        cxv[a] = F[a] - F[a + 1];
-                        sdx[a] = dcv[a] + dcv[a + 2];
-                    }
-                    float2 res[2];
-#pragma unroll
-                    for (int h = 0; h < 2; ++h) {
-                        const float2 tcp = h ? hi2(tc4) : lo2(tc4), dcp = h ? hi2(dc4) : lo2(dc4);
-                        const float2 tsp = h ? hi2(tsr) : lo2(tsr), tnp = h ? hi2(tnr) : lo2(tnr);
-                        const float2 dsp = h ? hi2(dsr) : lo2(dsr), dnp = h ? hi2(dnr) : lo2(dnr);
-                        const float2 ttp = h ? hi2(out.t[r]) : lo2(out.t[r]), dtp = h ? hi2(out.d[r]) : lo2(out.d[r]);
-                        const int a = 2 * h;
-                        // the top face: T_f = f_lo T_k + f_hi T_{k+1}, its advective flux
-                        const float2 atop = mul2(make_float2(out.w[r][a], out.w[r][a + 1]),
-                                                 fma2(lo2(qf), tcp, mul2(hi2(qf), ttp)));
-                        float2 acc = fma2(kx2p, make_float2(sdx[a], sdx[a + 1]), hi2(q3));
-                        acc = fma2(ky2p, add2(dsp, dnp), acc);
-                        acc = add2(acc, in.pd[r][h]);
-                        acc = fma2(hi2(q2), dtp, acc);
-                        acc = fma2(lo2(q3), dcp, acc);
-                        acc = add2(acc, make_float2(cxv[a], cxv[a + 1]));
-                        acc = fma2(make_float2(vf[r][a], vf[r][a + 1]), add2(tsp, tcp), acc);
-                        acc = fma2(make_float2(-vf[r + 1][a], -vf[r + 1][a + 1]), add2(tcp, tnp), acc);
-                        acc = fma2(lo2(qn), add2(in.ab[r][h], make_float2(-atop.x, -atop.y)), acc);
-                        res[h] = LF ? fma2(gdtp, acc, dcp) : fma2(gdtp, acc, fma2(cap, dcp, mul2(cbp, tcp)));
-                        out.ab[r][h] = atop;
-                        out.pd[r][h] = mul2(hi2(qn), dcp);
-                    }
-                    out4[r] = make_float4(res[0].x, res[0].y, res[1].x, res[1].y);
-                }
-                float* op = outp + (size_t)(k - k0) * plane;
-                *reinterpret_cast<float4*>(op) = out4[0];
-                *reinterpret_cast<float4*>(op + g.Nx) = out4[1];
-                if constexpr (TC) {
-                    // the upscale integration (Section 3.3): dz-weighted sums over the
-                    // slab's layers of each coarse column's cells in these rows
-                    const float dzk = lcp[2];
-#pragma unroll
-                    for (int r = 0; r < 2; ++r) {
-                        const float4 v = out4[r];
-                        if (NC == 1) {
-                            tcs[r][0] += dzk * ((v.x + v.y) + (v.z + v.w));
-                        } else {
-                            tcs[r][0] += dzk * (v.x + v.y);
-                            tcs[r][NC - 1] += dzk * (v.z + v.w);
+                        for (int c = 0; c < NV; ++c) {
+                            ytv[0][c] = yt[c];
+                            ytv[1][c] = yt[SXC + c];
+                            vv[0][c] = rs[c];
+                            vv[1][c] = rs[SXC + c];
+                            vv[2][c] = rs[2 * SXC + c];
                         }
-                    }
-                }
-            };
-            // the layers in pairs (chunks hold whole coarse slabs of M = 2 or 4
-            // layers); ring r holds plane k0 - 1 + r in slot r % NB with parity
-            // (r / NB) & 1
-            {
-                int sc = 1, st = 2, su = 3 % NB, pt = 0, pu = (3 / NB) & 1;   // slots of planes k, k+1, k+2
-                for (int k = k0; k < k1; k += 2) {
-                    const int i = k & (M - 1), Kr = (k - k0) / M, bb = Kr & 1;
-                    if (i == 0 && Kr > 0 && !fail && !mbar_wait(&built[bb], (Kr >> 1) & 1, A.wait_ns)) fail = true;
-                    if (!fail && !mbar_wait(&full[st], pt, A.wait_ns)) fail = true;
-                    if (!fail && !mbar_wait(&full[su], pu, A.wait_ns)) fail = true;
-                    if (!fail) {
-                        layer(k, i, bb, sc, st, S0, S1);
-                        layer(k + 1, i + 1, bb, st, su, S1, S0);
-                    }
-                    // planes k and k + 1 are no longer needed by this thread; nor,
-                    // after the slab's last layer, the slab's intermediates
-                    mbar_arrive(&empty[sc]);
-                    mbar_arrive(&empty[st]);
-                    if (i + 1 == M - 1) {
-                        if constexpr (TC) {
 #pragma unroll
-                            for (int r = 0; r < 2; ++r) {
-                                float* tp = sm + L::oTcb + (bb * TY + jl + r) * L::CX + cb0;
+                        for (int q = 0; q <= NC; ++q) {
+                            urv[0][q] = ur[q];
+                            urv[1][q] = ur[SXC + q];
+                        }
 #pragma unroll
-                                for (int q = 0; q < NC; ++q) {
-                                    tp[q] = tcs[r][q];
-                                    tcs[r][q] = 0.f;
+                        for (int a = 0; a < 4; ++a) {
+                            const int cb = a / M;
+#pragma unroll
+                            for (int r = 0; r < 2; ++r)
+                                out.w[r][a] = rsplit3(rx[a], ytv[r][cb], ytv[r][cb + 1], ytv[r][cb + 2]);
+#pragma unroll
+                            for (int f = 0; f < 3; ++f)
+                                vf[f][a] = rsplit3(rx[a], vv[f][cb], vv[f][cb + 1], vv[f][cb + 2]);
+                        }
+                        // stage X: cell balance, west to east, in units of U / (2 dx)
+#pragma unroll
+                        for (int r = 0; r < 2; ++r) {
+#pragma unroll
+                            for (int q = 0; q < NC; ++q) {
+                                float h = urv[r][q];
+                                us[r][q * M] = h;
+#pragma unroll
+                                for (int a = 0; a < M - 1; ++a) {
+                                    const int m = q * M + a;
+                                    h = h - (vf[r + 1][m] - vf[r][m]) - (out.w[r][m] - in.w[r][m]) * hz;
+                                    us[r][m + 1] = h;
                                 }
                             }
+                            us[r][4] = urv[r][NC];
                         }
-                        mbar_arrive(&freed[bb]);
                     }
-                    sc = su;
-                    st = su + 1;
-                    pt = pu;
-                    if (st == NB) {
-                        st = 0;
-                        pt ^= 1;
+                    const float* Pn_c = sm + sc * L::slot + L::oTn;
+                    const float* Pm_c = sm + sc * L::slot + L::oTm;
+                    const float* Pn_t = sm + st * L::slot + L::oTn;
+                    const float* Pm_t = sm + st * L::slot + L::oTm;
+#pragma unroll
+                    for (int r = 0; r < 2; ++r) {
+                        out.t[r] = *reinterpret_cast<const float4*>(Pn_t + om + r * kTX);
+                        out.d[r] = *reinterpret_cast<const float4*>(Pm_t + om + r * kTX);
                     }
-                    su = st + 1;
-                    pu = pt;
-                    if (su == NB) {
-                        su = 0;
-                        pu ^= 1;
+                    // rows jl - 1 and jl + 2 of plane k
+                    const float4 ts4 = *reinterpret_cast<const float4*>(Pn_c + osr);
+                    const float4 ds4 = *reinterpret_cast<const float4*>(Pm_c + osr);
+                    const float4 tn4 = *reinterpret_cast<const float4*>(Pn_c + onr);
+                    const float4 dn4 = *reinterpret_cast<const float4*>(Pm_c + onr);
+                    // x neighbours: shuffles inside the tile, the slot's edge columns at its edges
+                    float tw[2], te[2], dw[2], de[2];
+#pragma unroll
+                    for (int r = 0; r < 2; ++r) {
+                        tw[r] = __shfl_up_sync(0xffffffffu, in.t[r].w, 1);
+                        te[r] = __shfl_down_sync(0xffffffffu, in.t[r].x, 1);
+                        dw[r] = __shfl_up_sync(0xffffffffu, in.d[r].w, 1);
+                        de[r] = __shfl_down_sync(0xffffffffu, in.d[r].x, 1);
+                        if (seg == 0) {
+                            tw[r] = Pn_c[oxw + 4 * r];
+                            dw[r] = Pm_c[oxw + 4 * r];
+                        }
+                        if (seg == 15) {
+                            te[r] = Pn_c[oxe + 4 * r];
+                            de[r] = Pm_c[oxe + 4 * r];
+                        }
                     }
+                    // x fluxes in scalar form (adjacent cells share a face), then the
+                    // rest on the pairs (0, 1), (2, 3) with the pair constants of the layer:
+                    // D = kx2 (dw + de) + ky2 (ds + dn) + cdn db + cup dt - diag dc + plate,
+                    // the z advective terms as (w T_f)(bottom) - (w T_f)(top) over dz; the
+                    // planes beyond the plates are zero-filled, where W is zero and the plate
+                    // value enters D through `plate`
+                    const float4 qf = *reinterpret_cast<const float4*>(lcp + 4);    // f_lo, f_hi (top face)
+                    const float4 qn = *reinterpret_cast<const float4*>(lcp + 8);    // 1/dz, cdn of layer k+1
+                    const float4 q2 = *reinterpret_cast<const float4*>(lcp + 20);   // cdn, cup
+                    const float4 q3 = *reinterpret_cast<const float4*>(lcp + 24);   // -diag, plate
+                    float4 out4[2];
+#pragma unroll
+                    for (int r = 0; r < 2; ++r) {
+                        const float4 tc4 = in.t[r], dc4 = in.d[r];
+                        const float4 tsr = r ? in.t[0] : ts4, tnr = r ? tn4 : in.t[1];
+                        const float4 dsr = r ? in.d[0] : ds4, dnr = r ? dn4 : in.d[1];
+                        const float tcv[6] = {tw[r], tc4.x, tc4.y, tc4.z, tc4.w, te[r]};
+                        const float dcv[6] = {dw[r], dc4.x, dc4.y, dc4.z, dc4.w, de[r]};
+                        float F[5], cxv[4], sdx[4];
+#pragma unroll
+                        for (int a = 0; a < 5; ++a) F[a] = us[r][a] * (tcv[a] + tcv[a + 1]);
+#pragma unroll
+                        for (int a = 0; a < 4; ++a) {
+                            cxv[a] = F[a] - F[a + 1];
+                            sdx[a] = dcv[a] + dcv[a + 2];
+                        }
+                        float2 res[2];
+#pragma unroll
+                        for (int h = 0; h < 2; ++h) {
+                            const float2 tcp = h ? hi2(tc4) : lo2(tc4), dcp = h ? hi2(dc4) : lo2(dc4);
+                            const float2 tsp = h ? hi2(tsr) : lo2(tsr), tnp = h ? hi2(tnr) : lo2(tnr);
+                            const float2 dsp = h ? hi2(dsr) : lo2(dsr), dnp = h ? hi2(dnr) : lo2(dnr);
+                            const float2 ttp = h ? hi2(out.t[r]) : lo2(out.t[r]);
+                            const float2 dtp = h ? hi2(out.d[r]) : lo2(out.d[r]);
+                            const int a = 2 * h;
+                            // the top face: T_f = f_lo T_k + f_hi T_{k+1}, its advective flux
+                            const float2 atop = mul2(make_float2(out.w[r][a], out.w[r][a + 1]),
+                                                     fma2(lo2(qf), tcp, mul2(hi2(qf), ttp)));
+                            float2 acc = fma2(kx2p, make_float2(sdx[a], sdx[a + 1]), hi2(q3));
+                            acc = fma2(ky2p, add2(dsp, dnp), acc);
+                            acc = add2(acc, in.pd[r][h]);
+                            acc = fma2(hi2(q2), dtp, acc);
+                            acc = fma2(lo2(q3), dcp, acc);
+                            acc = add2(acc, make_float2(cxv[a], cxv[a + 1]));
+                            acc = fma2(make_float2(vf[r][a], vf[r][a + 1]), add2(tsp, tcp), acc);
+                            acc = fma2(make_float2(-vf[r + 1][a], -vf[r + 1][a + 1]), add2(tcp, tnp), acc);
+                            acc = fma2(lo2(qn), add2(in.ab[r][h], make_float2(-atop.x, -atop.y)), acc);
+                            res[h] = LF ? fma2(gdtp, acc, dcp) : fma2(gdtp, acc, fma2(cap, dcp, mul2(cbp, tcp)));
+                            out.ab[r][h] = atop;
+                            out.pd[r][h] = mul2(hi2(qn), dcp);
+                        }
+                        out4[r] = make_float4(res[0].x, res[0].y, res[1].x, res[1].y);
+                    }
+                    float* op = outp + (size_t)(k - k0) * plane;
+                    *reinterpret_cast<float4*>(op) = out4[0];
+                    *reinterpret_cast<float4*>(op + g.Nx) = out4[1];
+                    if constexpr (TC) {
+                        // the upscale integration (Section 3.3): dz-weighted sums over the
+                        // slab's layers of each coarse column's cells in these rows
+                        const float dzk = lcp[2];
+#pragma unroll
+                        for (int r = 0; r < 2; ++r) {
+                            const float4 v = out4[r];
+                            if (NC == 1) {
+                                tcs[r][0] += dzk * ((v.x + v.y) + (v.z + v.w));
+                            } else {
+                                tcs[r][0] += dzk * (v.x + v.y);
+                                tcs[r][NC - 1] += dzk * (v.z + v.w);
+                            }
+                        }
+                    }
+                };
+                // the layers in pairs (chunks hold whole coarse slabs of M = 2 or 4
+                // layers); ring R + r holds plane k0 - 1 + r in slot (R + r) % NB with
+                // parity ((R + r) / NB) & 1, the chunk's coarse slab Kr is the CTA's
+                // slab S + Kr, in buffer (S + Kr) & 1
+                {
+                    int sc = s1, st = s2, su = (R + 3) % NB, pt = ((R + 2) / NB) & 1, pu = ((R + 3) / NB) & 1;
+                    for (int k = k0; k < k1; k += 2) {
+                        const int i = k & (M - 1), Sg = S + (k - k0) / M, bb = Sg & 1;
+                        if (i == 0 && k > k0 && !fail && !mbar_wait(&built[bb], (Sg >> 1) & 1, A.wait_ns)) fail = true;
+                        if (!fail && !mbar_wait(&full[st], pt, A.wait_ns)) fail = true;
+                        if (!fail && !mbar_wait(&full[su], pu, A.wait_ns)) fail = true;
+                        if (!fail) {
+                            layer(k, i, bb, sc, st, S0, S1);
+                            layer(k + 1, i + 1, bb, st, su, S1, S0);
+                        }
+                        // planes k and k + 1 are no longer needed by this thread; nor,
+                        // after the slab's last layer, the slab's intermediates
+                        mbar_arrive(&empty[sc]);
+                        mbar_arrive(&empty[st]);
+                        if (i + 1 == M - 1) {
+                            if constexpr (TC) {
+#pragma unroll
+                                for (int r = 0; r < 2; ++r) {
+                                    float* tp = sm + L::oTcb + (bb * TY + jl + r) * L::CX + cb0;
+#pragma unroll
+                                    for (int q = 0; q < NC; ++q) {
+                                        tp[q] = tcs[r][q];
+                                        tcs[r][q] = 0.f;
+                                    }
+                                }
+                            }
+                            mbar_arrive(&freed[bb]);
+                        }
+                        sc = su;
+                        st = su + 1;
+                        pt = pu;
+                        if (st == NB) {
+                            st = 0;
+                            pt ^= 1;
+                        }
+                        su = st + 1;
+                        pu = pt;
+                        if (su == NB) {
+                            su = 0;
+                            pu ^= 1;
+                        }
+                    }
+                    // the chunk's last ring (plane k1), which no layer releases
+                    mbar_arrive(&empty[(R + nrings - 1) % NB]);
                 }
+                R += nrings;
+                S += h.K1 - h.K0;
             }
             if (fail) *s_fail = 1;
         }
@@ -1039,16 +1119,56 @@ cudaError_t launch_fl(const Grid<float>& g, const FusedInputs& in, const float* 
         !map_fx(&maps.cw, pW, px, g.ny + 2, g.nz + 1, L::BXC, L::NUR, 2) ||
         !map_fx(&maps.sc, in.sc, kSCW, g.nz, 1, kSCW, 1, 1))
         return cudaErrorInvalidValue;
-    // ~6 waves of resident CTAs, chunks of at most 96 dense layers
+    // ~6 chunks per resident CTA, chunks of at most 96 dense layers
 #ifndef MR_FUSED_WAVES
 #define MR_FUSED_WAVES 6                  // compile-time override for tuning sweeps
 #endif
-    const int tiles = (g.Nx / kTX) * (g.Ny / TY);
+    const int tpx = g.Nx / kTX, tiles = tpx * (g.Ny / TY);
     const int want = 152 * L::CTAS * MR_FUSED_WAVES;
     int chunks = max(1, min((want + tiles - 1) / tiles, g.nz));
     int kcs = (g.nz + chunks - 1) / chunks;
     kcs = max(1, min(kcs, 96 / M));
-    chunks = (g.nz + kcs - 1) / kcs;
+    chunks = (g.nz + kcs - 1) / kcs;      // every chunk holds at least one coarse slab
+    const int nch = chunks * tiles;
+    // the step: one CTA per resident slot, each stepping every gridDim.x-th
+    // chunk; the reductions: one CTA per chunk
+    int grid = nch;
+    if (KIND == 0) {
+        static int slots[64] = {};        // resident CTAs of this kernel on all SMs, per device
+        int dev = 0;
+        e = cudaGetDevice(&dev);
+        if (e != cudaSuccess) return e;
+        if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+        if (!slots[dev]) {
+            int sms = 0, per = 0;
+            e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+            if (e != cudaSuccess) return e;
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_fused<M, TY, KIND, LF, TC>, L::THREADS,
+                                                              L::bytes);
+            if (e != cudaSuccess) return e;
+            if (per < 1) return cudaErrorInvalidConfiguration;
+            slots[dev] = sms * per;
+        }
+        grid = min(nch, slots[dev]);
+    }
+    // the last round of chunks, which not every CTA gets, in sp parts of ps
+    // slabs: sp minimises the slabs of the busiest CTA, counting each part's two
+    // extra planes as half a slab
+    int nfull = nch, sp = 1, ps = kcs;
+    if (KIND == 0 && nch > grid && nch % grid) {
+        const int F = nch / grid, rem = nch - F * grid;
+        double best = 1e30;
+        for (int q = 1; q <= kcs; ++q) {
+            const int p = (kcs + q - 1) / q;
+            const double cost = (double)((rem * q + grid - 1) / grid) * (p + 0.5);
+            if (cost < best - 1e-9) {
+                best = cost;
+                sp = q;
+                ps = p;
+            }
+        }
+        nfull = F * grid;
+    }
     FLArgs A;
     memset(&A, 0, sizeof A);
     A.g = g;
@@ -1057,6 +1177,12 @@ cudaError_t launch_fl(const Grid<float>& g, const FusedInputs& in, const float* 
     A.b = (float)c.b;
     A.gdt = (float)c.gdt;
     A.kcs = kcs;
+    A.nch = nfull + (nch - nfull) * sp;
+    A.zch = chunks;
+    A.tpx = tpx;
+    A.nfull = nfull;
+    A.sp = sp;
+    A.ps = ps;
     A.err = err;
     A.divmax = divmax;
     memcpy(A.rx, in.rx12, sizeof A.rx);
@@ -1072,7 +1198,7 @@ cudaError_t launch_fl(const Grid<float>& g, const FusedInputs& in, const float* 
         A.Tc = in.Tc;
         A.tcinv = in.tcinv;
     }
-    k_fused<M, TY, KIND, LF, TC><<<dim3(chunks, g.Nx / kTX, g.Ny / TY), L::THREADS, L::bytes, st>>>(maps, A);
+    k_fused<M, TY, KIND, LF, TC><<<grid, L::THREADS, L::bytes, st>>>(maps, A);
     return cudaGetLastError();
 }
 
